@@ -1,0 +1,699 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle of the 1D3V PIC Monte Carlo time step.
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU-baseline timing).  Independent of
+ * the GPU library: no shared code, headers, tables or helpers.
+ *
+ * What one time step computes, in the order this oracle takes it (the paper's PIC
+ * cycle, Section 2 and Fig. "diagram"; the gather/update of Listing 7):
+ *   for every live particle, species by species, in ascending id order:
+ *     1. gather   a = A[j] + f*(A[j+1]-A[j])        (Listing 7, moveb(): linear gather
+ *                                                    of the pre-scaled acceleration A)
+ *     2. push     u += a (B = 0), or the Boris rotation (B != 0)   (Section 2, mover)
+ *     3. move     f += u; the integer part of f moves the particle across cells
+ *                 (Listing 7: x += nstep*vx with x the in-cell offset)
+ *     4. wall     absorbing walls with flux counters, periodic, or absorption followed
+ *                 by volume re-injection                 (Section 2, plasma-wall phase)
+ *     5. MCC      null-collision Monte Carlo against a uniform neutral background
+ *                                                        (Section 2, collision phase)
+ *   then the particles created by ionization are appended,
+ *   then the cloud-in-cell charge deposit (Section 2, density phase),
+ *   then the Poisson solve by the Thomas algorithm and E = -grad(phi) (Section 2, field
+ *   solver: "in 1D ... a tridiagonal matrix").
+ *
+ * The paper gives neither the push in a magnetic field, nor the collision model,
+ * nor the interpolation weights, nor the wall treatment; the readings taken here are:
+ * Boris (1970) rotation; null-collision MCC (Skullerud 1968, Vahedi & Surendra 1995)
+ * with integer acceptance thresholds on Philox4x32-10 words; linear (CIC) weights;
+ * Gauss's law over the half cell at the wall nodes.  All arithmetic is FP64 and the
+ * file is compiled without floating-point contraction.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TWO_PI 6.283185307179586476925286766559
+#define TWO32 4294967296.0
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10.  Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
+ * 1, 2, 3", SC'11, Section 4.  One round: two 32x32->64 multiplications of counter
+ * words 0 and 2 by the round multipliers; the new words are
+ *   (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2), hi(M0*c0) ^ c3 ^ k1, lo(M0*c0)),
+ * and the key is bumped by the Weyl constants between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = M0 * (uint64_t)c0;
+        uint64_t p1 = M1 * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Draw of one purpose for one particle in one step: counter (id, step_hi, step_lo,
+ * purpose), key = seed. */
+static void draw(const orc_sim* s, uint32_t id, int64_t step, uint32_t purpose, uint32_t w[4]);
+
+/* 32-bit word -> uniform double on the open interval (0,1): (w + 1/2) / 2^32. */
+static double uniform(uint32_t w) { return ((double)w + 0.5) / TWO32; }
+
+/* Box-Muller (1958): two uniforms -> two standard normals. */
+static void box_muller(uint32_t wa, uint32_t wb, double* z0, double* z1)
+{
+    double r = sqrt(-2.0 * log(uniform(wa)));
+    double th = TWO_PI * uniform(wb);
+    *z0 = r * cos(th);
+    *z1 = r * sin(th);
+}
+
+/* Unit vector uniform on the sphere: cos(theta) = 1 - 2 u0 about the x axis (the wall
+ * normal), azimuth 2 pi u1. */
+static void iso_dir(uint32_t w0, uint32_t w1, double n[3])
+{
+    double ct = 1.0 - 2.0 * uniform(w0);
+    double st = sqrt(1.0 - ct * ct);
+    double ph = TWO_PI * uniform(w1);
+    n[0] = ct;
+    n[1] = st * cos(ph);
+    n[2] = st * sin(ph);
+}
+
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n, cap;
+    int32_t* cell;
+    double* off;
+    double *ux, *uy, *uz; /* cells per step */
+    uint32_t* id;
+    unsigned char* alive;
+} orc_store;
+
+typedef struct {
+    uint32_t parent;    /* parent id: children are numbered by the rank of this id */
+    int32_t esp, isp;   /* species of the new electron and of the new ion */
+    int32_t cell;
+    double off;
+    double e[3], i[3];  /* velocities (cells per step) */
+} orc_birth;
+
+struct orc_sim {
+    orc_params p;
+    int32_t N;
+    int64_t step;
+    uint32_t next_id;
+    orc_store st[ORC_MAX_SPECIES];
+    /* per-species constants, derived once from the parameters */
+    double accel[ORC_MAX_SPECIES];   /* c_s: A = c_s * E (cells/step^2 per unit E) */
+    double tvec[ORC_MAX_SPECIES][3]; /* Boris t = (q/m) B dt/2 */
+    double svec[ORC_MAX_SPECIES][3]; /* Boris s = 2 t / (1 + t.t) */
+    double kefac[ORC_MAX_SPECIES];   /* w m (dx/dt)^2 / 2: energy per (cells/step)^2 */
+    double vinj[ORC_MAX_SPECIES];    /* sqrt(T_s/m_s) in cells/step */
+    uint32_t cand[ORC_MAX_SPECIES];  /* candidate threshold floor(P * 2^32) */
+    uint64_t slot_end[ORC_MAX_PROC]; /* cumulative slot bound of each process */
+    double thr_u2[ORC_MAX_PROC];     /* energy threshold as |u|^2 */
+    double vneutral;                 /* sqrt(T_n/m_n) in cells/step */
+    int has_B;
+    /* grid */
+    double* dens;   /* nspecies * (N+1): summed CIC weights per node */
+    double* A;      /* nspecies * (N+1): pre-scaled acceleration on nodes */
+    double *phi, *E, *rho;
+    int fields_ready;
+    /* counters */
+    int64_t wall_count[ORC_MAX_SPECIES][2];
+    double wall_energy[ORC_MAX_SPECIES][2];
+    int64_t collisions[ORC_MAX_PROC];
+    /* births of the current step */
+    orc_birth* births;
+    int64_t nbirths, capbirths;
+};
+
+static void draw(const orc_sim* s, uint32_t id, int64_t step, uint32_t purpose, uint32_t w[4])
+{
+    uint32_t ctr[4] = {id, (uint32_t)((uint64_t)step >> 32), (uint32_t)step, purpose};
+    uint32_t key[2] = {(uint32_t)s->p.seed, (uint32_t)(s->p.seed >> 32)};
+    orc_philox4x32_10(ctr, key, w);
+}
+
+static int store_reserve(orc_store* a, int64_t cap)
+{
+    if (cap <= a->cap) return 0;
+    int64_t nc = a->cap ? a->cap : 16;
+    while (nc < cap) nc *= 2;
+    void* p;
+#define GROW(f, T) p = realloc(a->f, (size_t)nc * sizeof(T)); if (!p) return -2; a->f = (T*)p;
+    GROW(cell, int32_t) GROW(off, double) GROW(ux, double) GROW(uy, double)
+    GROW(uz, double) GROW(id, uint32_t) GROW(alive, unsigned char)
+#undef GROW
+    a->cap = nc;
+    return 0;
+}
+
+static void store_free(orc_store* a)
+{
+    free(a->cell); free(a->off); free(a->ux); free(a->uy); free(a->uz);
+    free(a->id); free(a->alive);
+    memset(a, 0, sizeof(*a));
+}
+
+orc_sim* orc_create(const orc_params* p)
+{
+    if (!p || p->ncells < 1 || p->nspecies < 1 || p->nspecies > ORC_MAX_SPECIES ||
+        p->nproc < 0 || p->nproc > ORC_MAX_PROC || !(p->dx > 0) || !(p->dt > 0) ||
+        !(p->eps0 > 0) || p->bc < 0 || p->bc > 2 || p->field < 0 || p->field > 2)
+        return NULL;
+    if (p->bc == ORC_BC_PERIODIC && p->field == ORC_FIELD_POISSON) return NULL;
+    for (int k = 0; k < p->nproc; ++k) {
+        const orc_process* q = &p->proc[k];
+        if (q->species < 0 || q->species >= p->nspecies || !(q->nu >= 0)) return NULL;
+        if (q->kind == ORC_PROC_ELASTIC && !(p->sp[q->species].mass <= 0.25 * p->m_neutral))
+            return NULL;
+        if (q->kind == ORC_PROC_IONIZE && (q->product < 0 || q->product >= p->nspecies))
+            return NULL;
+        if (q->kind < 0 || q->kind > 2) return NULL;
+    }
+    for (int i = 0; i < p->nspecies; ++i)
+        if (!(p->sp[i].mass > 0)) return NULL;
+
+    orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+    if (!s) return NULL;
+    s->p = *p;
+    s->N = p->ncells;
+    const int N = s->N, S = p->nspecies;
+    s->dens = (double*)calloc((size_t)S * (N + 1), sizeof(double));
+    s->A = (double*)calloc((size_t)S * (N + 1), sizeof(double));
+    s->phi = (double*)calloc((size_t)(N + 1), sizeof(double));
+    s->E = (double*)calloc((size_t)(N + 1), sizeof(double));
+    s->rho = (double*)calloc((size_t)(N + 1), sizeof(double));
+    if (!s->dens || !s->A || !s->phi || !s->E || !s->rho) {
+        orc_destroy(s);
+        return NULL;
+    }
+
+    const double vs = p->dt / p->dx; /* physical velocity -> cells per step */
+    const double Bsq = p->B[0] * p->B[0] + p->B[1] * p->B[1] + p->B[2] * p->B[2];
+    s->has_B = Bsq > 0.0;
+    for (int i = 0; i < S; ++i) {
+        const orc_species* q = &p->sp[i];
+        const double qm = q->charge / q->mass;
+        s->accel[i] = qm * (p->dt * p->dt / p->dx);
+        const double qmh = qm * (0.5 * p->dt);
+        for (int k = 0; k < 3; ++k) s->tvec[i][k] = qmh * p->B[k];
+        const double tt = s->tvec[i][0] * s->tvec[i][0] + s->tvec[i][1] * s->tvec[i][1] +
+                          s->tvec[i][2] * s->tvec[i][2];
+        const double sf = 2.0 / (1.0 + tt);
+        for (int k = 0; k < 3; ++k) s->svec[i][k] = sf * s->tvec[i][k];
+        const double dxdt = p->dx / p->dt;
+        s->kefac[i] = 0.5 * q->mass * q->weight * (dxdt * dxdt);
+        s->vinj[i] = sqrt(q->temperature / q->mass) * vs;
+        /* null-collision candidate probability over one step: 1 - exp(-nu_max dt) */
+        double numax = 0.0;
+        for (int k = 0; k < p->nproc; ++k)
+            if (p->proc[k].species == i) numax += p->proc[k].nu;
+        double P = -expm1(-numax * p->dt);
+        double T = floor(P * TWO32);
+        s->cand[i] = numax > 0.0 ? (T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T) : 0u;
+        /* fixed slots of [0, 2^32) for the processes of this species, in list order */
+        double cum = 0.0;
+        int last = -1;
+        for (int k = 0; k < p->nproc; ++k) {
+            if (p->proc[k].species != i) continue;
+            cum += p->proc[k].nu;
+            s->slot_end[k] = (uint64_t)floor(cum / numax * TWO32);
+            last = k;
+        }
+        if (last >= 0) s->slot_end[last] = (uint64_t)1 << 32;
+    }
+    for (int k = 0; k < p->nproc; ++k) {
+        const double m = p->sp[p->proc[k].species].mass;
+        s->thr_u2[k] = (2.0 * p->proc[k].threshold / m) * (vs * vs);
+    }
+    s->vneutral = p->m_neutral > 0 ? sqrt(p->T_neutral / p->m_neutral) * vs : 0.0;
+    return s;
+}
+
+void orc_destroy(orc_sim* s)
+{
+    if (!s) return;
+    for (int i = 0; i < ORC_MAX_SPECIES; ++i) store_free(&s->st[i]);
+    free(s->dens); free(s->A); free(s->phi); free(s->E); free(s->rho); free(s->births);
+    free(s);
+}
+
+typedef struct { uint32_t id; int64_t at; } id_at;
+static int cmp_id_at(const void* a, const void* b)
+{
+    const id_at *x = (const id_at*)a, *y = (const id_at*)b;
+    if (x->id != y->id) return x->id < y->id ? -1 : 1;
+    return x->at < y->at ? -1 : (x->at > y->at);
+}
+
+int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const double* off,
+             const double* vx, const double* vy, const double* vz, const uint32_t* id)
+{
+    if (!s || sp < 0 || sp >= s->p.nspecies || n < 0) return -1;
+    if (n > 0 && (!cell || !off || !vx || !vy || !vz)) return -1;
+    for (int64_t k = 0; k < n; ++k)
+        if (cell[k] < 0 || cell[k] >= s->N || !(off[k] >= 0.0 && off[k] < 1.0)) return -1;
+    orc_store* a = &s->st[sp];
+    a->n = 0;
+    if (store_reserve(a, n > 0 ? n : 1)) return -2;
+    id_at* order = (id_at*)malloc((size_t)(n > 0 ? n : 1) * sizeof(id_at));
+    if (!order) return -2;
+    for (int64_t k = 0; k < n; ++k) {
+        order[k].id = id ? id[k] : s->next_id + (uint32_t)k;
+        order[k].at = k;
+    }
+    qsort(order, (size_t)n, sizeof(id_at), cmp_id_at);
+    const double vs = s->p.dt / s->p.dx;
+    for (int64_t r = 0; r < n; ++r) {
+        int64_t k = order[r].at;
+        a->cell[r] = cell[k];
+        a->off[r] = off[k];
+        a->ux[r] = vx[k] * vs;
+        a->uy[r] = vy[k] * vs;
+        a->uz[r] = vz[k] * vs;
+        a->id[r] = order[r].id;
+        a->alive[r] = 1;
+        if (order[r].id >= s->next_id) s->next_id = order[r].id + 1;
+    }
+    a->n = n;
+    free(order);
+    s->fields_ready = 0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Density phase: cloud-in-cell weights, (1-f) to node j and f to node j+1, summed in
+ * ascending id order per species. */
+static void deposit(orc_sim* s)
+{
+    const int N = s->N;
+    for (int sp = 0; sp < s->p.nspecies; ++sp) {
+        double* d = s->dens + (size_t)sp * (N + 1);
+        for (int j = 0; j <= N; ++j) d[j] = 0.0;
+        const orc_store* a = &s->st[sp];
+        for (int64_t k = 0; k < a->n; ++k) {
+            if (!a->alive[k]) continue;
+            const int j = a->cell[k];
+            const double f = a->off[k];
+            d[j] += 1.0 - f;
+            d[j + 1] += f;
+        }
+        if (s->p.bc == ORC_BC_PERIODIC) { /* node N is node 0 */
+            d[0] += d[N];
+            d[N] = d[0];
+        }
+    }
+}
+
+int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* phi, double* E)
+{
+    if (N < 1 || !rho || !phi || !E || !(dx > 0) || !(eps0 > 0)) return -1;
+    const int M = N - 1; /* interior unknowns phi[1..N-1] */
+    phi[0] = 0.0;
+    phi[N] = 0.0;
+    if (M >= 1) {
+        double* cp = (double*)malloc((size_t)(M + 1) * sizeof(double));
+        double* dp = (double*)malloc((size_t)(M + 1) * sizeof(double));
+        if (!cp || !dp) { free(cp); free(dp); return -2; }
+        /* Thomas algorithm on a_i = -1, b_i = 2, c_i = -1, d_i = dx^2 rho_i / eps0 */
+        const double a = -1.0, b = 2.0, c = -1.0;
+        double d1 = dx * dx * rho[1] / eps0;
+        cp[1] = c / b;
+        dp[1] = d1 / b;
+        for (int i = 2; i <= M; ++i) {
+            const double di = dx * dx * rho[i] / eps0;
+            const double m = b - a * cp[i - 1];
+            cp[i] = c / m;
+            dp[i] = (di - a * dp[i - 1]) / m;
+        }
+        phi[M] = dp[M];
+        for (int i = M - 1; i >= 1; --i) phi[i] = dp[i] - cp[i] * phi[i + 1];
+        free(cp);
+        free(dp);
+    }
+    /* E = -dphi/dx: centred inside; at a wall node Gauss's law over the half cell
+     * next to the wall, whose charge per area is rho_wall * dx/2. */
+    for (int j = 1; j < N; ++j) E[j] = (phi[j - 1] - phi[j + 1]) / (2.0 * dx);
+    E[0] = -(phi[1] - phi[0]) / dx - rho[0] * dx / (2.0 * eps0);
+    E[N] = -(phi[N] - phi[N - 1]) / dx + rho[N] * dx / (2.0 * eps0);
+    return 0;
+}
+
+/* Field phase: charge density from the deposit, Poisson solve, then the pre-scaled
+ * accelerations A_s = c_s E used by the gather. */
+static int solve_fields(orc_sim* s)
+{
+    const int N = s->N, S = s->p.nspecies;
+    const double dx = s->p.dx;
+    if (s->p.field == ORC_FIELD_POISSON) {
+        for (int j = 0; j <= N; ++j) {
+            double q = 0.0;
+            for (int sp = 0; sp < S; ++sp)
+                q += s->p.sp[sp].charge * s->p.sp[sp].weight * s->dens[(size_t)sp * (N + 1) + j];
+            /* interior node: cell volume dx; wall node: half cell */
+            s->rho[j] = (j == 0 || j == N) ? q / (0.5 * dx) : q / dx;
+        }
+        int rc = orc_poisson(N, dx, s->p.eps0, s->rho, s->phi, s->E);
+        if (rc) return rc;
+    } else {
+        const double e = s->p.field == ORC_FIELD_EXTERNAL ? s->p.E_ext : 0.0;
+        for (int j = 0; j <= N; ++j) {
+            s->E[j] = e;
+            s->phi[j] = -e * ((double)j * dx);
+            s->rho[j] = 0.0;
+        }
+    }
+    for (int sp = 0; sp < S; ++sp)
+        for (int j = 0; j <= N; ++j) s->A[(size_t)sp * (N + 1) + j] = s->accel[sp] * s->E[j];
+    s->fields_ready = 1;
+    return 0;
+}
+
+static int ensure_fields(orc_sim* s)
+{
+    if (s->fields_ready) return 0;
+    deposit(s);
+    return solve_fields(s);
+}
+
+static int add_birth(orc_sim* s, const orc_birth* b)
+{
+    if (s->nbirths == s->capbirths) {
+        int64_t nc = s->capbirths ? 2 * s->capbirths : 64;
+        void* p = realloc(s->births, (size_t)nc * sizeof(orc_birth));
+        if (!p) return -2;
+        s->births = (orc_birth*)p;
+        s->capbirths = nc;
+    }
+    s->births[s->nbirths++] = *b;
+    return 0;
+}
+
+static int cmp_birth(const void* a, const void* b)
+{
+    const orc_birth *x = (const orc_birth*)a, *y = (const orc_birth*)b;
+    return x->parent < y->parent ? -1 : (x->parent > y->parent);
+}
+
+/* Collision phase for one particle (null-collision MCC).  Returns 0 or < 0. */
+static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
+{
+    const uint32_t id = a->id[k];
+    uint32_t w[4];
+    draw(s, id, s->step, ORC_RNG_COLLIDE, w);
+    if (!(w[0] < s->cand[sp])) return 0; /* no candidate this step */
+    int proc = -1;
+    for (int q = 0; q < s->p.nproc; ++q) {
+        if (s->p.proc[q].species != sp) continue;
+        if ((uint64_t)w[1] < s->slot_end[q]) { proc = q; break; }
+    }
+    if (proc < 0) return 0;
+    double ux = a->ux[k], uy = a->uy[k], uz = a->uz[k];
+    const double u2 = ux * ux + uy * uy + uz * uz;
+    if (!(u2 >= s->thr_u2[proc])) return 0; /* below threshold: null collision */
+    const orc_process* P = &s->p.proc[proc];
+    uint32_t r[4];
+    if (P->kind == ORC_PROC_ELASTIC) {
+        /* isotropic new direction n; speed loss for the scattering angle chi between
+         * the old and the new direction: |u'| = |u| sqrt(1 - 2 (m/M)(1 - cos chi)) */
+        draw(s, id, s->step, ORC_RNG_SCATTER, r);
+        double n[3];
+        iso_dir(r[0], r[1], n);
+        const double speed = sqrt(u2);
+        if (speed > 0.0) {
+            const double cchi = (ux * n[0] + uy * n[1] + uz * n[2]) / speed;
+            const double mr = s->p.sp[sp].mass / s->p.m_neutral;
+            const double fac = sqrt(1.0 - 2.0 * mr * (1.0 - cchi));
+            const double sp2 = speed * fac;
+            a->ux[k] = sp2 * n[0];
+            a->uy[k] = sp2 * n[1];
+            a->uz[k] = sp2 * n[2];
+        }
+    } else if (P->kind == ORC_PROC_CX) {
+        /* charge exchange: the ion takes the velocity of a background neutral */
+        draw(s, id, s->step, ORC_RNG_MAXWELL, r);
+        double z0, z1, z2, z3;
+        box_muller(r[0], r[1], &z0, &z1);
+        box_muller(r[2], r[3], &z2, &z3);
+        a->ux[k] = z0 * s->vneutral;
+        a->uy[k] = z1 * s->vneutral;
+        a->uz[k] = z2 * s->vneutral;
+    } else { /* ORC_PROC_IONIZE */
+        /* the incident electron pays the threshold; the rest is shared equally by the
+         * two outgoing electrons, both isotropic; the ion is a background neutral */
+        const double us = sqrt(0.5 * (u2 - s->thr_u2[proc]));
+        double n1[3], n2[3];
+        draw(s, id, s->step, ORC_RNG_SCATTER, r);
+        iso_dir(r[0], r[1], n1);
+        draw(s, id, s->step, ORC_RNG_IONIZE_E, r);
+        iso_dir(r[0], r[1], n2);
+        uint32_t ri[4];
+        draw(s, id, s->step, ORC_RNG_IONIZE_I, ri);
+        double z0, z1, z2, z3;
+        box_muller(ri[0], ri[1], &z0, &z1);
+        box_muller(ri[2], ri[3], &z2, &z3);
+        a->ux[k] = us * n1[0];
+        a->uy[k] = us * n1[1];
+        a->uz[k] = us * n1[2];
+        orc_birth b;
+        b.parent = id;
+        b.esp = sp;
+        b.isp = P->product;
+        b.cell = a->cell[k];
+        b.off = a->off[k];
+        b.e[0] = us * n2[0]; b.e[1] = us * n2[1]; b.e[2] = us * n2[2];
+        b.i[0] = z0 * s->vneutral; b.i[1] = z1 * s->vneutral; b.i[2] = z2 * s->vneutral;
+        int rc = add_birth(s, &b);
+        if (rc) return rc;
+    }
+    s->collisions[proc] += 1;
+    return 0;
+}
+
+/* Volume source: the absorbed particle re-enters at a uniform position with a
+ * Maxwellian velocity of its species' source temperature. */
+static void reinject(orc_sim* s, int sp, orc_store* a, int64_t k)
+{
+    uint32_t r[4], q[4];
+    draw(s, a->id[k], s->step, ORC_RNG_INJECT_A, r);
+    draw(s, a->id[k], s->step, ORC_RNG_INJECT_B, q);
+    const double x = uniform(r[0]) * (double)s->N;
+    double fl = floor(x);
+    int j = (int)fl;
+    double f = x - fl;
+    if (j >= s->N) { j = s->N - 1; f = 0.0; }
+    double z0, z1, z2, z3;
+    box_muller(r[1], r[2], &z0, &z1);
+    box_muller(q[0], q[1], &z2, &z3);
+    a->cell[k] = j;
+    a->off[k] = f;
+    a->ux[k] = z0 * s->vinj[sp];
+    a->uy[k] = z1 * s->vinj[sp];
+    a->uz[k] = z2 * s->vinj[sp];
+}
+
+static int one_step(orc_sim* s)
+{
+    const int N = s->N, S = s->p.nspecies;
+    int rc = ensure_fields(s);
+    if (rc) return rc;
+    s->nbirths = 0;
+    for (int sp = 0; sp < S; ++sp) {
+        orc_store* a = &s->st[sp];
+        const double* A = s->A + (size_t)sp * (N + 1);
+        const double* t = s->tvec[sp];
+        const double* sv = s->svec[sp];
+        for (int64_t k = 0; k < a->n; ++k) {
+            if (!a->alive[k]) continue;
+            int j = a->cell[k];
+            double f = a->off[k];
+            /* 1. gather (Listing 7) */
+            const double acc = A[j] + f * (A[j + 1] - A[j]);
+            /* 2. push */
+            if (!s->has_B) {
+                a->ux[k] = a->ux[k] + acc;
+            } else {
+                const double half = 0.5 * acc;
+                const double mx = a->ux[k] + half, my = a->uy[k], mz = a->uz[k];
+                const double px = mx + (my * t[2] - mz * t[1]);
+                const double py = my + (mz * t[0] - mx * t[2]);
+                const double pz = mz + (mx * t[1] - my * t[0]);
+                const double qx = mx + (py * sv[2] - pz * sv[1]);
+                const double qy = my + (pz * sv[0] - px * sv[2]);
+                const double qz = mz + (px * sv[1] - py * sv[0]);
+                a->ux[k] = qx + half;
+                a->uy[k] = qy;
+                a->uz[k] = qz;
+            }
+            /* 3. move (Listing 7: x += nstep*vx, x the in-cell offset) */
+            const double xn = f + a->ux[k];
+            const double fl = floor(xn);
+            f = xn - fl;
+            j += (int)fl;
+            if (f >= 1.0) { /* xn a tiny negative number: f rounded up to 1 */
+                f = 0.0;
+                j += 1;
+            }
+            a->cell[k] = j;
+            a->off[k] = f;
+            /* 4. walls */
+            int reinjected = 0;
+            if (j < 0 || j >= N) {
+                if (s->p.bc == ORC_BC_PERIODIC) {
+                    while (j < 0) j += N;
+                    while (j >= N) j -= N;
+                    a->cell[k] = j;
+                } else {
+                    const int wall = j < 0 ? 0 : 1;
+                    const double u2 = a->ux[k] * a->ux[k] + a->uy[k] * a->uy[k] +
+                                      a->uz[k] * a->uz[k];
+                    s->wall_count[sp][wall] += 1;
+                    s->wall_energy[sp][wall] += s->kefac[sp] * u2;
+                    if (s->p.bc == ORC_BC_SOURCE) {
+                        reinject(s, sp, a, k);
+                        reinjected = 1;
+                    } else {
+                        a->alive[k] = 0;
+                        continue;
+                    }
+                }
+            }
+            /* 5. Monte Carlo collisions */
+            if (!reinjected) {
+                rc = collide(s, sp, a, k);
+                if (rc) return rc;
+            }
+        }
+    }
+    /* creation: children numbered by the rank of the parent id among this step's
+     * ionizing parents; electron 2r, ion 2r+1 after the largest id so far */
+    if (s->nbirths > 0) {
+        qsort(s->births, (size_t)s->nbirths, sizeof(orc_birth), cmp_birth);
+        const uint32_t base = s->next_id;
+        for (int64_t r = 0; r < s->nbirths; ++r) {
+            const orc_birth* b = &s->births[r];
+            for (int c = 0; c < 2; ++c) {
+                const int sp = c == 0 ? b->esp : b->isp;
+                const double* u = c == 0 ? b->e : b->i;
+                orc_store* a = &s->st[sp];
+                if (store_reserve(a, a->n + 1)) return -2;
+                const int64_t k = a->n++;
+                a->cell[k] = b->cell;
+                a->off[k] = b->off;
+                a->ux[k] = u[0];
+                a->uy[k] = u[1];
+                a->uz[k] = u[2];
+                a->id[k] = base + (uint32_t)(2 * r + c);
+                a->alive[k] = 1;
+            }
+        }
+        s->next_id = base + (uint32_t)(2 * s->nbirths);
+    }
+    /* drop absorbed particles (ids stay ascending) */
+    for (int sp = 0; sp < S; ++sp) {
+        orc_store* a = &s->st[sp];
+        int64_t m = 0;
+        for (int64_t k = 0; k < a->n; ++k) {
+            if (!a->alive[k]) continue;
+            if (m != k) {
+                a->cell[m] = a->cell[k]; a->off[m] = a->off[k];
+                a->ux[m] = a->ux[k]; a->uy[m] = a->uy[k]; a->uz[m] = a->uz[k];
+                a->id[m] = a->id[k]; a->alive[m] = 1;
+            }
+            ++m;
+        }
+        a->n = m;
+    }
+    deposit(s);
+    rc = solve_fields(s);
+    if (rc) return rc;
+    s->step += 1;
+    return 0;
+}
+
+int orc_step(orc_sim* s, int64_t nsteps)
+{
+    if (!s || nsteps < 0) return -1;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        int rc = one_step(s);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+int64_t orc_count(const orc_sim* s, int32_t sp)
+{
+    if (!s || sp < 0 || sp >= s->p.nspecies) return -1;
+    return s->st[sp].n;
+}
+
+int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx,
+            double* vy, double* vz, uint32_t* id)
+{
+    if (!s || sp < 0 || sp >= s->p.nspecies) return -1;
+    const orc_store* a = &s->st[sp];
+    const double iv = s->p.dx / s->p.dt; /* cells per step -> physical */
+    for (int64_t k = 0; k < a->n; ++k) {
+        if (cell) cell[k] = a->cell[k];
+        if (off) off[k] = a->off[k];
+        if (vx) vx[k] = a->ux[k] * iv;
+        if (vy) vy[k] = a->uy[k] * iv;
+        if (vz) vz[k] = a->uz[k] * iv;
+        if (id) id[k] = a->id[k];
+    }
+    return 0;
+}
+
+int orc_moments_get(orc_sim* s, orc_moments* m, double* density, double* phi, double* E)
+{
+    if (!s || !m) return -1;
+    int rc = ensure_fields(s);
+    if (rc) return rc;
+    const int N = s->N, S = s->p.nspecies;
+    memset(m, 0, sizeof(*m));
+    m->step = s->step;
+    for (int sp = 0; sp < S; ++sp) {
+        const orc_store* a = &s->st[sp];
+        double ke = 0.0;
+        int64_t live = 0;
+        for (int64_t k = 0; k < a->n; ++k) {
+            if (!a->alive[k]) continue;
+            ++live;
+            ke += s->kefac[sp] * (a->ux[k] * a->ux[k] + a->uy[k] * a->uy[k] + a->uz[k] * a->uz[k]);
+        }
+        m->live[sp] = live;
+        m->kinetic[sp] = ke;
+        for (int w = 0; w < 2; ++w) {
+            m->wall_count[sp][w] = s->wall_count[sp][w];
+            m->wall_energy[sp][w] = s->wall_energy[sp][w];
+        }
+        if (density) {
+            const double* d = s->dens + (size_t)sp * (N + 1);
+            const double wdx = s->p.sp[sp].weight / s->p.dx;
+            for (int j = 0; j <= N; ++j) {
+                const int wall = (j == 0 || j == N) && s->p.bc != ORC_BC_PERIODIC;
+                density[(size_t)sp * (N + 1) + j] = wall ? 2.0 * wdx * d[j] : wdx * d[j];
+            }
+        }
+    }
+    for (int q = 0; q < s->p.nproc; ++q) m->collisions[q] = s->collisions[q];
+    if (phi) memcpy(phi, s->phi, (size_t)(N + 1) * sizeof(double));
+    if (E) memcpy(E, s->E, (size_t)(N + 1) * sizeof(double));
+    return 0;
+}

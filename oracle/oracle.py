@@ -1,0 +1,178 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline
+leg use it to produce expected values.  Nothing in the GPU library imports it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List
+
+import numpy as np
+
+from . import build as _build
+
+MAX_SPECIES = 4
+MAX_PROC = 8
+
+
+class _Species(C.Structure):
+    _fields_ = [("charge", C.c_double), ("mass", C.c_double), ("weight", C.c_double),
+                ("temperature", C.c_double)]
+
+
+class _Process(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("species", C.c_int32), ("product", C.c_int32),
+                ("pad", C.c_int32), ("nu", C.c_double), ("threshold", C.c_double)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("ncells", C.c_int32), ("bc", C.c_int32), ("field", C.c_int32),
+                ("nspecies", C.c_int32), ("dx", C.c_double), ("dt", C.c_double),
+                ("eps0", C.c_double), ("E_ext", C.c_double), ("B", C.c_double * 3),
+                ("T_neutral", C.c_double), ("m_neutral", C.c_double),
+                ("sp", _Species * MAX_SPECIES), ("nproc", C.c_int32), ("pad", C.c_int32),
+                ("proc", _Process * MAX_PROC), ("seed", C.c_uint64)]
+
+
+class _Moments(C.Structure):
+    _fields_ = [("step", C.c_int64), ("live", C.c_int64 * MAX_SPECIES),
+                ("wall_count", (C.c_int64 * 2) * MAX_SPECIES),
+                ("wall_energy", (C.c_double * 2) * MAX_SPECIES),
+                ("collisions", C.c_int64 * MAX_PROC),
+                ("kinetic", C.c_double * MAX_SPECIES)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(_Params)]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        P = C.c_void_p
+        L.orc_load.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P, P, P, P, P, P]
+        L.orc_step.argtypes = [C.c_void_p, C.c_int64]
+        L.orc_count.restype = C.c_int64
+        L.orc_count.argtypes = [C.c_void_p, C.c_int32]
+        L.orc_get.argtypes = [C.c_void_p, C.c_int32, P, P, P, P, P, P]
+        L.orc_moments_get.argtypes = [C.c_void_p, C.POINTER(_Moments), P, P, P]
+        L.orc_philox4x32_10.argtypes = [P, P, P]
+        L.orc_poisson.argtypes = [C.c_int32, C.c_double, C.c_double, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def params_struct(phys) -> _Params:
+    p = _Params()
+    p.ncells = phys.ncells
+    p.bc = phys.bc
+    p.field = phys.field
+    p.nspecies = len(phys.species)
+    p.dx, p.dt, p.eps0, p.E_ext = phys.dx, phys.dt, phys.eps0, phys.E_ext
+    for k in range(3):
+        p.B[k] = phys.B[k]
+    p.T_neutral, p.m_neutral = phys.T_neutral, phys.m_neutral
+    for i, s in enumerate(phys.species):
+        p.sp[i] = _Species(s.charge, s.mass, s.weight, s.temperature)
+    p.nproc = len(phys.processes)
+    for k, q in enumerate(phys.processes):
+        p.proc[k] = _Process(q.kind, q.species, q.product, 0, q.nu, q.threshold)
+    p.seed = phys.seed
+    return p
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one 4-word counter under one 2-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def poisson(rho, dx: float, eps0: float = 1.0):
+    """Thomas solve of the grounded Dirichlet problem; returns (phi, E)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    N = len(rho) - 1
+    phi = np.zeros(N + 1)
+    E = np.zeros(N + 1)
+    rc = lib().orc_poisson(N, dx, eps0, _ptr(rho), _ptr(phi), _ptr(E))
+    if rc:
+        raise RuntimeError("orc_poisson failed: %d" % rc)
+    return phi, E
+
+
+class Oracle:
+    """One bounded-plasma instance advanced by the FP64 CPU oracle."""
+
+    def __init__(self, phys):
+        self.phys = phys
+        self._p = params_struct(phys)
+        self._h = lib().orc_create(C.byref(self._p))
+        if not self._h:
+            raise ValueError("oracle rejected the parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_destroy(h)
+            self._h = None
+
+    def load(self, species: int, ld) -> None:
+        arrs = [np.ascontiguousarray(ld.cell, dtype=np.int32),
+                np.ascontiguousarray(ld.off, dtype=np.float64),
+                np.ascontiguousarray(ld.vx, dtype=np.float64),
+                np.ascontiguousarray(ld.vy, dtype=np.float64),
+                np.ascontiguousarray(ld.vz, dtype=np.float64),
+                None if ld.id is None else np.ascontiguousarray(ld.id, dtype=np.uint32)]
+        rc = lib().orc_load(self._h, species, len(arrs[0]), *[_ptr(a) for a in arrs])
+        if rc:
+            raise ValueError("orc_load failed: %d" % rc)
+
+    def load_all(self, loads: List) -> None:
+        for i, ld in enumerate(loads):
+            self.load(i, ld)
+
+    def step(self, n: int = 1) -> None:
+        rc = lib().orc_step(self._h, n)
+        if rc:
+            raise RuntimeError("orc_step failed: %d" % rc)
+
+    def particles(self, species: int) -> dict:
+        n = lib().orc_count(self._h, species)
+        out = dict(cell=np.zeros(n, np.int32), off=np.zeros(n), vx=np.zeros(n),
+                   vy=np.zeros(n), vz=np.zeros(n), id=np.zeros(n, np.uint32))
+        rc = lib().orc_get(self._h, species, *[_ptr(out[k]) for k in
+                                                ("cell", "off", "vx", "vy", "vz", "id")])
+        if rc:
+            raise RuntimeError("orc_get failed: %d" % rc)
+        return out
+
+    def moments(self) -> dict:
+        m = _Moments()
+        N = self.phys.ncells
+        S = len(self.phys.species)
+        dens = np.zeros(S * (N + 1))
+        phi = np.zeros(N + 1)
+        E = np.zeros(N + 1)
+        rc = lib().orc_moments_get(self._h, C.byref(m), _ptr(dens), _ptr(phi), _ptr(E))
+        if rc:
+            raise RuntimeError("orc_moments_get failed: %d" % rc)
+        nproc = len(self.phys.processes)
+        return dict(step=m.step,
+                    live=np.array(m.live[:S], dtype=np.int64),
+                    wall_count=np.array([list(m.wall_count[i]) for i in range(S)], np.int64),
+                    wall_energy=np.array([list(m.wall_energy[i]) for i in range(S)]),
+                    collisions=np.array(m.collisions[:nproc], dtype=np.int64),
+                    kinetic=np.array(m.kinetic[:S]),
+                    density=dens.reshape(S, N + 1), phi=phi, E=E)
