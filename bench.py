@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU PIC-MCC time step: particle-steps/s on one GB300 (or N
+independent replicas under torchrun), with the HBM roofline fraction of the mover
+kernel, the end-to-end rate through the C ABI with host buffers, and the FP64 CPU
+oracle timed on the host cores.
+
+Workload (default): the large bounded plasma, 65,536 cells, 1,500 particles per cell
+per species, electrons + ions (196,608,000 particles), FP32 particle state, fixed-point
+deposit, FP64 integer-exact Poisson solve, elastic + charge-exchange null-collision
+MCC, counting sort every 20 steps.  The particle state (4.7 GB) is far larger than
+L2, so no L2 flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2404_10270_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s (gather+push+MCC+deposit), FP32 vs FP64 form, % HBM roofline"
+UNIT = "particle-steps/s"
+# algorithmic bytes per particle-step of the mover (B = 0, constant collision
+# frequency): read cell, off, vx, id (16 B), write cell, off, vx (12 B) in FP32;
+# read cell(4) off(8) vx(8) id(4), write cell(4) off(8) vx(8) in FP64.
+MOVER_BYTES = {"f32": 28, "f64": 44}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel: str, precision: str):
+    """DRAM bytes per particle of the mover from the committed ncu summary, if one
+    matches the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "mover_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        ent = d[precision]
+        from paper_2404_10270_gb300.build import SRC
+        import hashlib
+        h = hashlib.sha256()
+        for f in ("mover.cuh", "common.cuh", "mover_f32.cu", "mover_f64.cu"):
+            with open(os.path.join(SRC, f), "rb") as fh:
+                h.update(fh.read())
+        if ent.get("source_sha256") != h.hexdigest():
+            return None
+        return float(ent["dram_bytes_per_particle"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for name, v in zip(names, s[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_rate(phys: W.Physics, cells: int, seconds: float, seed: int):
+    """Oracle p-steps/s on a slice of `cells` cells of the workload (same ppc and
+    physics), stepping until `seconds` of CPU time are spent (at least 2 steps)."""
+    from oracle.oracle import Oracle
+    import dataclasses
+    sl = dataclasses.replace(phys, ncells=cells)
+    loads = W.initial_load(sl, seed=seed)
+    o = Oracle(sl)
+    o.load_all(loads)
+    o.step(1)  # first field solve and warm caches
+    n = sum(len(x) for x in loads)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        o.step(1)
+        k += 1
+        el = time.perf_counter() - t0
+        if k >= 2 and el >= seconds:
+            break
+    live = int(o.moments()["live"].sum())
+    return (n + live) / 2 * k / el, k, n, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    phys = W.bounded_large()
+    cells = args.ref_cells
+    rates = []
+    n = None
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_rate(phys, cells, 0.0, seed=1)
+    total_ps, total_t = 0.0, 0.0
+    for k in range(args.steps):
+        r, nsteps, n, el = oracle_rate(phys, cells, 0.0, seed=1 + k)
+        total_ps += r * el
+        total_t += el
+    value = total_ps / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "bounded_large slice: %d of 65536 cells, 1500 ppc/species" % cells,
+                   "particles_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "FP64 CPU oracle, each step = 2 time steps of a %d-cell slice "
+                                   "(%d particles) of the bounded_large workload" % (cells, n)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def pinned(a: np.ndarray):
+    import torch
+    t = torch.empty(a.shape, dtype={np.dtype(np.int32): torch.int32, np.dtype(np.float64): torch.float64,
+                                     np.dtype(np.uint32): torch.int32}[a.dtype], pin_memory=True)
+    v = t.numpy().view(a.dtype)
+    v[...] = a
+    return t, v
+
+
+def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, world, dev):
+    import torch
+    import torch.distributed as dist
+    sim.step(warmup)
+    sim.sync()
+    live0 = sum(sim.count(0, s) for s in range(len(phys.species)))
+    sim.profile(True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev) as clk:
+        start.record()
+        sim.step(steps)
+        end.record()
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    live1 = sum(sim.count(0, s) for s in range(len(phys.species)))
+    mover_n, mover_ms = sim.kernel_time(0)
+    field_n, field_ms = sim.kernel_time(1)
+    sort_n, sort_ms = sim.kernel_time(2)
+    other_n, other_ms = sim.kernel_time(3)
+    kernels, _ = sim.kernel_time(4)
+    sim.profile(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    p = torch.tensor([(live0 + live1) / 2 * steps], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    psteps = float(p.item())
+    hbm, src = peaks()
+    per_launch_bytes = MOVER_BYTES[precision_name] * (live0 + live1) / 2
+    avg_mover_ms = mover_ms / max(mover_n, 1)
+    achieved = per_launch_bytes / (avg_mover_ms * 1e-3) / 1e9
+    traffic = profiled_traffic("k_move", precision_name)
+    return {
+        "value": psteps / (ms_max * 1e-3),
+        "ms_per_step": ms_max / steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"
+                     if src == "measured" else "fallback 6.8 TB/s",
+                     "traffic": None if traffic is None else traffic * (live0 + live1) / 2,
+                     "kernel": "k_move<%s>" % ("float" if precision_name == "f32" else "double"),
+                     "bytes_per_particle": MOVER_BYTES[precision_name],
+                     "avg_launch_ms": avg_mover_ms},
+        "kernel_ms": {"mover": mover_ms, "field": field_ms, "sort": sort_ms, "other": other_ms,
+                      "mover_launches": mover_n, "sort_launch_groups": sort_n},
+        "gpu_launches": kernels,
+        "clocks": clk.summary(),
+        "live": [live0, live1],
+    }
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __import__("__graft_entry__").build()
+    from paper_2404_10270_gb300 import capi
+    t_setup = time.perf_counter()
+    phys = W.bounded_large(ncells=args.cells, ppc=args.ppc, seed=1 + rank)
+    loads = W.initial_load(phys, seed=1 + rank)
+    n = sum(len(x) for x in loads)
+    # pinned host copies of the inputs (end-to-end measurement)
+    host = []
+    for ld in loads:
+        host.append({k: pinned(getattr(ld, k)) for k in ("cell", "off", "vx", "vy", "vz", "id")})
+    sim = capi.Sim(phys, precision=capi.FP32, sort_interval=args.sort)
+    for s, h in enumerate(host):
+        sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
+    setup_s = time.perf_counter() - t_setup
+    res = measure_form(sim, phys, args.steps, args.warmup, n, "f32", rank, world, local)
+
+    # end to end through the public API with host buffers: load from pinned host
+    # memory, K steps, read every particle and the moments back to pinned memory
+    outs = []
+    for ld in loads:
+        m = len(ld)
+        outs.append({k: pinned(np.zeros(m, dt))[1] for k, dt in
+                     (("cell", np.int32), ("off", np.float64), ("vx", np.float64),
+                      ("vy", np.float64), ("vz", np.float64), ("id", np.uint32))})
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for s, h in enumerate(host):
+        sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
+    sim.step(args.steps)
+    mom = sim.moments(0)
+    d2h = 0
+    import ctypes as C
+    for s in range(len(phys.species)):
+        o = outs[s]
+        got = C.c_int64()
+        cap = len(o["cell"])
+        capi._check(capi.lib().pic_get_particles(sim._h, 0, s, cap, *[o[k].ctypes.data for k in
+                    ("cell", "off", "vx", "vy", "vz", "id")], 0, C.byref(got)), sim._h)
+        d2h += got.value * 40
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = n * world * args.steps / float(e2e_t.item())
+    h2d = n * 40
+    assert mom["step"] > 0
+
+    fp64 = None
+    if not args.no_fp64:
+        sim.close()
+        del sim
+        sim64 = capi.Sim(phys, precision=capi.FP64, sort_interval=args.sort)
+        for s, h in enumerate(host):
+            sim64.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
+        r64 = measure_form(sim64, phys, max(args.steps // 4, 4), min(args.warmup, 3), n, "f64",
+                           rank, world, local)
+        sim64.close()
+        fp64 = {k: r64[k] for k in ("value", "ms_per_step", "roofline", "clocks")}
+        fp64["dtype"] = "f64"
+    else:
+        sim.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, k, ns, el = oracle_rate(phys, args.cpu_cells, args.cpu_seconds, seed=1)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 CPU oracle, %d time steps of a %d-cell slice (%d particles, same "
+                         "ppc and physics) of the workload, %.1f s" % (k, args.cpu_cells, ns, el)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "bounded_large: %d cells, %d particles/cell/species, e+i "
+                                   "(m_i/m_e 100), elastic + charge-exchange MCC at 0.01 w_pe, "
+                                   "grounded absorbing walls, FP32 state, int64 fixed-point deposit, "
+                                   "FP64 Poisson, sort every %d steps" % (args.cells, args.ppc, args.sort),
+                       "particles_per_gpu": n, "cells": args.cells, "sort_interval": args.sort,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state %.1f GB per GPU > L2 (no flush needed)" % (n * 24 / 1e9)},
+            "roofline": res["roofline"],
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps,
+                    "what": "pic_load_particles from pinned host + %d steps + pic_moments + "
+                            "pic_get_particles to pinned host" % args.steps},
+            "gpu_launches": res["gpu_launches"],
+            "clocks": res["clocks"],
+            "kernel_ms": res["kernel_ms"],
+            "fp64_form": fp64,
+            "setup_s": setup_s,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=65536)
+    ap.add_argument("--ppc", type=int, default=1500)
+    ap.add_argument("--sort", type=int, default=20)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-cells", type=int, default=1024)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-cells", type=int, default=256)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

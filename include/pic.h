@@ -1,0 +1,201 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) particle-in-cell Monte Carlo time step.
+ *
+ * The library advances a batch of independent 1D3V bounded-plasma instances through
+ * the PIC cycle of Williams et al., arXiv 2404.10270, Section 2 (density deposit,
+ * field solve, collisions and plasma-wall interaction, particle mover), with the
+ * linear field gather and the position update of the moveb() mover (Listing 7).
+ * One call of pic_step() runs, for every particle of every instance:
+ *   gather -> push (leapfrog, or Boris rotation when B != 0) -> move -> wall ->
+ *   null-collision Monte Carlo collision -> cloud-in-cell deposit,
+ * then, per instance, the Poisson solve with E = -grad(phi) (Section 2, "Field
+ * Solver"), and every `sort_interval` steps a counting sort of the particles by cell
+ * (the locality the paper's "natural sorting" layout provides, Section 2, Fig.
+ * "BIT1_sorting").
+ *
+ * Units are normalised: eps0 = e = m_e = n0 = lambda_D = omega_pe = 1 (T_e = 1).
+ * A position is the BIT1 pair (cell j, in-cell offset f in [0,1)), Section 2 and
+ * Listing 7.  Velocities cross this interface in units of lambda_D * omega_pe.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an int status (PIC_OK or a negative pic_status).  No C++
+ *    exception, abort or exit crosses the interface.
+ *  - Input pointers are borrowed for the duration of the call; data is copied in.
+ *    Output buffers belong to the caller.  `on_device` = 1 means the pointers are CUDA
+ *    device pointers valid on the handle's device; 0 means host memory (pinned or
+ *    pageable).
+ *  - The handle owns all device memory it allocates and releases it in pic_destroy.
+ *  - A handle is used by one host thread at a time.  Work is ordered on the handle's
+ *    stream (the borrowed `cuda_stream` of pic_config, or a stream the library owns).
+ *  - pic_step only enqueues work.  Errors detected on the device (capacity
+ *    overflow, non-finite state, invalid loaded particles) are latched in a device
+ *    status word and reported by the next synchronising call (pic_sync, pic_moments,
+ *    pic_get_particles, pic_charge_raw); from then on every call except pic_destroy
+ *    and pic_last_error returns PIC_ESTATE.
+ */
+#ifndef PIC_H
+#define PIC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PIC_API __attribute__((visibility("default")))
+#else
+#define PIC_API
+#endif
+
+#define PIC_MAX_SPECIES 4
+#define PIC_MAX_PROC 8
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = -1,     /* invalid argument or configuration */
+    PIC_ENOMEM = -2,     /* device or host allocation failed */
+    PIC_ECUDA = -3,      /* a CUDA runtime call failed */
+    PIC_ECAPACITY = -4,  /* a species segment or the event buffer overflowed */
+    PIC_ENONFINITE = -5, /* a particle velocity became Inf/NaN */
+    PIC_ETIMEOUT = -6,   /* a bounded device wait ran out */
+    PIC_ESTATE = -7      /* the handle is in the error state */
+} pic_status;
+
+enum { PIC_FP32 = 0, PIC_FP64 = 1 };                          /* particle state precision */
+enum { PIC_BC_ABSORB = 0, PIC_BC_PERIODIC = 1, PIC_BC_SOURCE = 2 };
+enum { PIC_FIELD_POISSON = 0, PIC_FIELD_NONE = 1, PIC_FIELD_EXTERNAL = 2 };
+enum { PIC_PROC_ELASTIC = 0, PIC_PROC_CX = 1, PIC_PROC_IONIZE = 2 };
+
+/* One species of one instance. */
+typedef struct {
+    double charge;      /* q_s in units of e */
+    double mass;        /* m_s in units of m_e */
+    double weight;      /* w_s, physical particles per unit area per macro-particle */
+    double temperature; /* T_s of the volume source's Maxwellian (PIC_BC_SOURCE) */
+    int64_t capacity;   /* particle slots reserved (>= largest load + creations) */
+} pic_species;
+
+/* One collision process against the uniform neutral background (null-collision
+ * Monte Carlo; the paper's collision phase, Section 2).  The collision frequency is
+ * `nu` for projectile energies at or above `threshold` and 0 below. */
+typedef struct {
+    int32_t kind;      /* PIC_PROC_* */
+    int32_t species;   /* projectile species */
+    int32_t product;   /* PIC_PROC_IONIZE: species of the created ion, else -1 */
+    int32_t pad;
+    double nu;         /* units of omega_pe */
+    double threshold;  /* units of T_e */
+} pic_process;
+
+/* One bounded-plasma instance: cells 0..ncells-1, nodes 0..ncells, walls at the
+ * first and last node. */
+typedef struct {
+    int32_t ncells;
+    int32_t bc;        /* PIC_BC_* */
+    int32_t field;     /* PIC_FIELD_* (PIC_FIELD_POISSON needs a non-periodic bc) */
+    int32_t nspecies;  /* 1..PIC_MAX_SPECIES */
+    double dx, dt, eps0;
+    double E_ext;      /* uniform field for PIC_FIELD_EXTERNAL */
+    double B[3];       /* uniform magnetic field; x is the wall normal */
+    double T_neutral;  /* neutral background temperature (units of T_e) */
+    double m_neutral;  /* neutral background mass (units of m_e) */
+    pic_species sp[PIC_MAX_SPECIES];
+    int32_t nproc;
+    int32_t pad;
+    pic_process proc[PIC_MAX_PROC];
+    uint64_t seed;     /* Philox4x32-10 key of this instance */
+} pic_instance;
+
+typedef struct {
+    int32_t n_instances;        /* >= 1 */
+    int32_t precision;          /* PIC_FP32 or PIC_FP64 */
+    int32_t sort_interval;      /* sort by cell every this many steps; 0 = never */
+    int32_t block;              /* mover threads per block; 0 = library choice */
+    const pic_instance* inst;   /* n_instances entries, copied */
+    void* cuda_stream;          /* borrowed cudaStream_t; NULL = library-owned stream */
+} pic_config;
+
+typedef struct pic_handle pic_handle;
+
+/* Per-instance diagnostics of the current step. */
+typedef struct {
+    int64_t step;                              /* steps taken since creation */
+    int64_t live[PIC_MAX_SPECIES];             /* particles alive */
+    int64_t wall_count[PIC_MAX_SPECIES][2];    /* absorbed at [left, right] wall */
+    double wall_energy[PIC_MAX_SPECIES][2];    /* sum of w m v^2/2 of absorbed particles */
+    int64_t collisions[PIC_MAX_PROC];          /* real collision events per process */
+    double kinetic[PIC_MAX_SPECIES];           /* sum of w m v^2/2 over live particles */
+} pic_moments_out;
+
+/* Create a handle: validates the configuration, allocates the particle store
+ * (structure of arrays, capacity per species segment), the grid arrays and the
+ * counters on the current CUDA device.  *out is set only on success. */
+PIC_API int pic_create(const pic_config* cfg, pic_handle** out);
+
+/* Replace the particles of (instance, species) with n particles: cell[k] in
+ * [0, ncells), off[k] in [0, 1), physical velocities.  id == NULL numbers them after
+ * the largest id of the instance so far.  n must not exceed the species capacity
+ * (else PIC_ECAPACITY).  Invalid cell/offset values are reported as PIC_EINVAL by the
+ * next synchronising call.  Marks the fields stale: the next pic_step first deposits
+ * all particles and solves the field. */
+PIC_API int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                       const int32_t* cell, const double* off, const double* vx,
+                       const double* vy, const double* vz, const uint32_t* id,
+                       int32_t on_device);
+
+/* Enqueue nsteps time steps of every instance on the handle's stream. */
+PIC_API int pic_step(pic_handle* h, int64_t nsteps);
+
+/* Wait for the handle's stream and report latched device errors. */
+PIC_API int pic_sync(pic_handle* h);
+
+/* Diagnostics of instance `inst` (synchronises).  Optional host arrays (NULL to skip),
+ * each indexed by node 0..ncells: `density` nspecies*(ncells+1) number densities
+ * (species-major; the wall nodes are normalised by the half cell next to the wall),
+ * `phi` the potential and `E` the field of the current step. */
+PIC_API int pic_moments(pic_handle* h, int32_t inst, pic_moments_out* out, double* density,
+                double* phi, double* E);
+
+/* Number of live particles of (inst, species) (synchronises). */
+PIC_API int pic_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n);
+
+/* Copy out the live particles of (inst, species) in storage order: *n_out receives
+ * their number, which must not exceed `capacity` (else PIC_ECAPACITY, nothing
+ * written).  Any output pointer may be NULL.  Velocities are physical. */
+PIC_API int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
+                      int32_t* cell, double* off, double* vx, double* vy, double* vz,
+                      uint32_t* id, int32_t on_device, int64_t* n_out);
+
+/* The fixed-point charge deposit of the last step for instance `inst`: host array of
+ * nspecies*(ncells+1) int64 node sums, in units where every live particle adds
+ * exactly *unit (2^24 in the FP32 form, 2^48 in the FP64 form) split over the two
+ * nodes of its cell (synchronises). */
+PIC_API int pic_charge_raw(pic_handle* h, int32_t inst, int64_t* out, int64_t* unit);
+
+/* Kernel timing: when enabled, every kernel launch of pic_step is bracketed by CUDA
+ * events on the handle's stream.  pic_kernel_time returns, for kernel class `which`
+ * (0 mover, 1 field, 2 sort, 3 other), the number of timed launch groups and their
+ * total milliseconds since the last pic_profile call (synchronises); `which` = 4
+ * returns the number of kernels the library launched since then (total_ms = 0). */
+PIC_API int pic_profile(pic_handle* h, int32_t enable);
+PIC_API int pic_kernel_time(pic_handle* h, int32_t which, int64_t* launches, double* total_ms);
+
+/* Destroy the handle and release its memory.  NULL-safe; always returns PIC_OK. */
+PIC_API int pic_destroy(pic_handle* h);
+
+/* Text of the last error on this handle (or of the last failed pic_create when h is
+ * NULL).  The string lives until the next call on the handle. */
+PIC_API const char* pic_last_error(const pic_handle* h);
+
+/* The library's Philox4x32-10 generator (Salmon et al., SC'11), run on the GPU:
+ * out[4k..4k+3] = Philox4x32-10(ctr[4k..4k+3], key) for k < n.  Exposes the exact
+ * generator that keys every random draw of the time step by (seed, particle id,
+ * step, purpose), so that it can be checked on its own.  `stream` is a borrowed
+ * cudaStream_t (NULL = default stream); the call synchronises it. */
+PIC_API int pic_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t n,
+               int32_t on_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,173 @@
+// common.cuh -- device-side data structures and helpers of the PIC-MCC library.
+//
+// Layout in HBM (one handle):
+//   * particle store, structure of arrays, two copies (the counting sort scatters
+//     from one into the other and the roles swap):  cell int32, off T, ux/uy/uz T,
+//     id uint32, T = float (FP32 form) or double (FP64 form).  Velocities are kept
+//     in cells per step (u = v dt/dx) so that the move is the paper's
+//     x += nstep*vx (Listing 7) with x the in-cell offset.  A slot with cell < 0 is
+//     empty.  Every (instance, species) pair owns one contiguous segment whose base
+//     and capacity are multiples of 64 slots, so 128-bit loads of four particles
+//     never straddle segments.
+//   * per segment, node arrays of ncells+1 entries: the pre-scaled acceleration
+//     A = c_s E (type T) used by the gather, and the fixed-point charge deposit
+//     (uint64, two copies: the one being accumulated and the last complete one).
+//   * per instance, E on the nodes (double) and scratch for the field solve.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pic.h"
+
+namespace bitpic {
+
+constexpr int kMaxSpecies = PIC_MAX_SPECIES;
+constexpr int kMaxProc = PIC_MAX_PROC;
+constexpr int kSegAlign = 64;  // slots
+
+// Device status word bits (latched, reported by synchronising calls).
+enum : unsigned {
+    kErrCapacity = 1u,
+    kErrNonFinite = 2u,
+    kErrInput = 4u,
+    kErrEvents = 8u,
+    kErrTimeout = 16u,
+};
+
+// Philox counter word 3: what a draw is for.
+enum : uint32_t {
+    kRngCollide = 0, kRngScatter = 1, kRngMaxwell = 2, kRngInjectA = 3, kRngInjectB = 4,
+    kRngIonizeE = 5, kRngIonizeI = 6,
+};
+
+// Per-segment (instance, species) constants, derived on the host from pic_instance.
+struct SegParams {
+    int32_t inst;          // instance index
+    int32_t species;       // species index within the instance
+    int32_t ncells;        // N of the instance
+    int32_t bc;            // PIC_BC_*
+    int64_t base;          // first slot of the segment
+    int64_t cap;           // slots (multiple of kSegAlign)
+    int64_t node;          // first entry of this segment's node arrays
+    int64_t inode;         // first entry of the instance's node arrays (E)
+    uint32_t key0, key1;   // Philox key = instance seed
+    double accel;          // c_s = (q/m) dt^2/dx: A = c_s E in cells/step^2
+    double t[3], s[3];     // Boris: t = (q/m) B dt/2, s = 2t/(1+t.t)
+    double kefac;          // w m (dx/dt)^2 / 2: energy of |u|^2 = 1 (cells/step)^2
+    double vinj;           // sqrt(T_s/m_s) in cells/step (volume source)
+    double vneutral;       // sqrt(T_n/m_n) in cells/step
+    double mratio;         // m_s / m_neutral (elastic energy transfer)
+    uint32_t cand;         // null-collision candidate threshold floor(P * 2^32)
+    int32_t nproc;         // processes of this species (list order)
+    int32_t proc[kMaxProc];        // instance-level index of each process
+    int32_t kind[kMaxProc];        // PIC_PROC_*
+    int32_t product[kMaxProc];     // ionization: segment index of the new ion
+    uint64_t slot_end[kMaxProc];   // cumulative slot bounds in [0, 2^32]
+    double thr_u2[kMaxProc];       // energy threshold as |u|^2 (cells/step)^2
+    int32_t collide;       // any process
+    int32_t pad;
+};
+
+struct InstParams {
+    int32_t ncells;
+    int32_t field;         // PIC_FIELD_*
+    int32_t seg0;          // first segment
+    int32_t nseg;          // segments (= nspecies)
+    int64_t inode;         // first entry of E
+    int64_t ev_base;       // first entry in the ionization event buffer
+    int64_t ev_cap;        // event buffer entries of this instance
+    double lambda;         // E = lambda * G (integer field numerator G)
+    int32_t z[kMaxSpecies]; // charge q_s w_s in integer multiples of the unit delta
+};
+
+struct Event {            // one ionization event awaiting child ids
+    uint32_t parent;
+    uint32_t pad;
+    int64_t slot_e;       // global slot of the new electron
+    int64_t slot_i;       // global slot of the new ion
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// products on counter words 0 and 2, mixed with words 1, 3 and the key; the key is
+// bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Draw of one purpose for particle `id` in step `step`.
+__device__ __forceinline__ uint4 draw(uint32_t id, int64_t step, uint32_t purpose,
+                                      uint32_t k0, uint32_t k1)
+{
+    return philox4x32_10(make_uint4(id, (uint32_t)((uint64_t)step >> 32), (uint32_t)step, purpose),
+                         k0, k1);
+}
+
+// ---------------------------------------------------------------------------
+// 128-bit integers (the field solve is exact integer arithmetic).
+typedef __int128 i128;
+
+// Correctly rounded i128 -> double: keep the top 64 significant bits with a sticky
+// bit for everything shifted out, convert with round-to-nearest, rescale exactly.
+__device__ __forceinline__ double i128_to_double(i128 x)
+{
+    const bool neg = x < 0;
+    unsigned __int128 m = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    const uint64_t hi = (uint64_t)(m >> 64);
+    double r;
+    if (hi == 0) {
+        r = __ull2double_rn((uint64_t)m);
+    } else {
+        const int sh = 64 - __clzll((long long)hi);  // 1..64 bits in the high word
+        uint64_t t = (uint64_t)(m >> sh);
+        const unsigned __int128 rest = m & (((unsigned __int128)1 << sh) - 1);
+        if (rest != 0) t |= 1u;
+        r = __ull2double_rn(t) * __longlong_as_double((long long)(1023 + sh) << 52);
+    }
+    return neg ? -r : r;
+}
+
+__device__ __forceinline__ i128 shfl_up_i128(i128 v, int d)
+{
+    const uint64_t lo = (uint64_t)v, hi = (uint64_t)((unsigned __int128)v >> 64);
+    const uint64_t l2 = __shfl_up_sync(0xffffffffu, lo, d);
+    const uint64_t h2 = __shfl_up_sync(0xffffffffu, hi, d);
+    return (i128)(((unsigned __int128)h2 << 64) | l2);
+}
+
+__device__ __forceinline__ i128 shfl_i128(i128 v, int src)
+{
+    const uint64_t lo = (uint64_t)v, hi = (uint64_t)((unsigned __int128)v >> 64);
+    const uint64_t l2 = __shfl_sync(0xffffffffu, lo, src);
+    const uint64_t h2 = __shfl_sync(0xffffffffu, hi, src);
+    return (i128)(((unsigned __int128)h2 << 64) | l2);
+}
+
+__device__ __forceinline__ void set_error(unsigned* err, unsigned bit) { atomicOr(err, bit); }
+
+// Segment of tile t: the last s with tile_start[s] <= t (tile_start has nseg+1 entries).
+__device__ __forceinline__ int find_segment(const int64_t* __restrict__ tile_start, int nseg,
+                                            int64_t t)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace bitpic

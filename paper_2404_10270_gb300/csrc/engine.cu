@@ -1,0 +1,1024 @@
+// engine.cu -- the handle behind the C ABI (include/pic.h): validation, memory
+// layout, the per-step launch sequence and the synchronising queries.
+//
+// Launch sequence of one time step (all on the handle's stream):
+//   k_tiles     round each segment's slot count to a whole quad, build the tile list
+//   k_move      gather, push, move, wall, MCC, fixed-point deposit (mover.cuh)
+//   k_births    number this step's ionization products (only with ionization)
+//   k_field     exact integer Poisson solve -> E -> pre-scaled accelerations, and
+//               hand-over of the deposit (field.cu)
+//   every `sort_interval` steps: k_tiles, histogram, scan, scatter (sort.cu).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mover.cuh"
+
+using namespace bitpic;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Store {
+    int32_t* cell = nullptr;
+    void* off = nullptr;
+    void* ux = nullptr;
+    void* uy = nullptr;
+    void* uz = nullptr;
+    uint32_t* id = nullptr;
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct pic_handle {
+    int precision = PIC_FP32;
+    int ninst = 0, nseg = 0, sort_interval = 0, nt = 256, grid_move = 0, sms = 0;
+    size_t tsize = 4;
+    std::vector<pic_instance> inst;
+    std::vector<SegParams> segh;
+    std::vector<InstParams> insth;
+    int64_t total_cap = 0, seg_nodes = 0, inst_nodes = 0, max_cap = 0, ev_total = 0;
+    int max_nodes = 0;
+    bool any_poisson = false, any_mag = false, any_ionize = false;
+
+    SegParams* segd = nullptr;
+    InstParams* instd = nullptr;
+    Store st[2];
+    int cur = 0;
+    void* accel = nullptr;
+    unsigned long long *dep = nullptr, *dep_last = nullptr;
+    double* E = nullptr;
+    i128 *R = nullptr, *UN = nullptr;
+    unsigned* hist = nullptr;
+    unsigned long long *newn = nullptr, *seg_n = nullptr, *seg_live = nullptr, *hwm_alt = nullptr;
+    int64_t *seg_nmove = nullptr, *tile_start = nullptr;
+    unsigned long long *wall_count = nullptr, *collisions = nullptr, *ev_count = nullptr,
+                       *next_id = nullptr;
+    double* wall_energy = nullptr;
+    Event* events = nullptr;
+    unsigned* err = nullptr;
+    int64_t* step_d = nullptr;
+    double *kin = nullptr, *phi_d = nullptr;
+    std::vector<void*> allocs;
+
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t step_h = 0;
+    bool stale = true;
+    int state = PIC_OK;
+    std::string last_error;
+
+    bool profiling = false;
+    struct Timed { int cls; cudaEvent_t a, b; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t launches[4] = {0, 0, 0, 0};
+    double ms[4] = {0, 0, 0, 0};
+    int64_t kernels = 0;  // kernel launches since the last pic_profile call
+};
+
+namespace {
+
+int fail(pic_handle* h, int code, const std::string& msg)
+{
+    if (h) {
+        h->last_error = msg;
+        if (code == PIC_ECUDA) h->state = PIC_ECUDA;
+    } else {
+        g_create_error = msg;
+    }
+    return code;
+}
+
+#define CUDA_TRY(h, expr)                                                            \
+    do {                                                                             \
+        cudaError_t e_ = (expr);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail((h), PIC_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int check_state(pic_handle* h)
+{
+    if (!h) return PIC_EINVAL;
+    if (h->state != PIC_OK) {
+        if (h->last_error.empty()) h->last_error = "handle is in the error state";
+        return PIC_ESTATE;
+    }
+    return PIC_OK;
+}
+
+template <typename T>
+int dalloc(pic_handle* h, T** p, size_t count)
+{
+    void* q = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, PIC_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return PIC_OK;
+}
+
+cudaEvent_t take_event(pic_handle* h)
+{
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Span {
+    pic_handle* h;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Span(pic_handle* hh, int c) : h(hh), cls(c)
+    {
+        if (h->profiling) {
+            a = take_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~Span()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, h->stream);
+            h->timed.push_back({cls, a, b});
+        }
+    }
+};
+
+// --- validation -------------------------------------------------------------------
+int validate_instance(const pic_instance& I, int idx, std::string* why)
+{
+    auto bad = [&](const std::string& m) {
+        *why = "instance " + std::to_string(idx) + ": " + m;
+        return PIC_EINVAL;
+    };
+    if (I.ncells < 1 || I.ncells > (1 << 24)) return bad("ncells must be in [1, 2^24]");
+    if (I.nspecies < 1 || I.nspecies > PIC_MAX_SPECIES) return bad("nspecies must be 1..4");
+    if (!(I.dx > 0) || !(I.dt > 0) || !(I.eps0 > 0)) return bad("dx, dt, eps0 must be > 0");
+    if (I.bc < 0 || I.bc > 2) return bad("invalid bc");
+    if (I.field < 0 || I.field > 2) return bad("invalid field mode");
+    if (I.field == PIC_FIELD_POISSON && I.bc == PIC_BC_PERIODIC)
+        return bad("the grounded Poisson solve needs walls (bc != PERIODIC)");
+    for (int s = 0; s < I.nspecies; ++s) {
+        if (!(I.sp[s].mass > 0) || !std::isfinite(I.sp[s].charge) || !(I.sp[s].weight >= 0))
+            return bad("species " + std::to_string(s) + ": mass > 0, finite charge, weight >= 0");
+        if (I.sp[s].capacity < 0) return bad("negative capacity");
+        if (!(I.sp[s].temperature >= 0)) return bad("temperature must be >= 0");
+    }
+    if (I.nproc < 0 || I.nproc > PIC_MAX_PROC) return bad("nproc must be 0..8");
+    for (int k = 0; k < I.nproc; ++k) {
+        const pic_process& P = I.proc[k];
+        if (P.kind < 0 || P.kind > 2) return bad("process kind");
+        if (P.species < 0 || P.species >= I.nspecies) return bad("process species");
+        if (!(P.nu >= 0) || !(P.threshold >= 0)) return bad("process nu/threshold must be >= 0");
+        if (P.kind == PIC_PROC_ELASTIC && !(I.sp[P.species].mass <= 0.25 * I.m_neutral))
+            return bad("elastic scattering needs m_s <= m_neutral / 4");
+        if (P.kind == PIC_PROC_IONIZE &&
+            (P.product < 0 || P.product >= I.nspecies || P.product == P.species))
+            return bad("ionization needs a product species other than the projectile");
+        if ((P.kind == PIC_PROC_CX || P.kind == PIC_PROC_IONIZE) && !(I.m_neutral > 0))
+            return bad("charge exchange / ionization need m_neutral > 0");
+    }
+    return PIC_OK;
+}
+
+// Derive the per-segment constants.  The expressions mirror the definitions in the
+// mover: A = c_s E with c_s = (q/m) dt^2/dx; Boris t = (q/m) B dt/2, s = 2t/(1+t.t);
+// candidate probability P = 1 - exp(-nu_max dt) as floor(P 2^32).
+void seg_constants(const pic_instance& I, int s, SegParams* P)
+{
+    const pic_species& S = I.sp[s];
+    const double vs = I.dt / I.dx;
+    const double qm = S.charge / S.mass;
+    P->accel = qm * (I.dt * I.dt / I.dx);
+    const double qmh = qm * (0.5 * I.dt);
+    for (int k = 0; k < 3; ++k) P->t[k] = qmh * I.B[k];
+    const double tt = P->t[0] * P->t[0] + P->t[1] * P->t[1] + P->t[2] * P->t[2];
+    const double sf = 2.0 / (1.0 + tt);
+    for (int k = 0; k < 3; ++k) P->s[k] = sf * P->t[k];
+    const double dxdt = I.dx / I.dt;
+    P->kefac = 0.5 * S.mass * S.weight * (dxdt * dxdt);
+    P->vinj = std::sqrt(S.temperature / S.mass) * vs;
+    P->vneutral = I.m_neutral > 0 ? std::sqrt(I.T_neutral / I.m_neutral) * vs : 0.0;
+    P->mratio = I.m_neutral > 0 ? S.mass / I.m_neutral : 0.0;
+    double numax = 0.0;
+    for (int k = 0; k < I.nproc; ++k)
+        if (I.proc[k].species == s) numax += I.proc[k].nu;
+    const double Pc = -std::expm1(-numax * I.dt);
+    const double T = std::floor(Pc * 4294967296.0);
+    P->cand = numax > 0.0 ? (T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T) : 0u;
+    P->nproc = 0;
+    double cum = 0.0;
+    for (int k = 0; k < I.nproc; ++k) {
+        if (I.proc[k].species != s) continue;
+        const int q = P->nproc++;
+        cum += I.proc[k].nu;
+        P->proc[q] = k;
+        P->kind[q] = I.proc[k].kind;
+        P->product[q] = I.proc[k].product;  // species index; remapped to a segment later
+        P->slot_end[q] = (uint64_t)std::floor(cum / numax * 4294967296.0);
+        P->thr_u2[q] = (2.0 * I.proc[k].threshold / S.mass) * (vs * vs);
+    }
+    if (P->nproc > 0) P->slot_end[P->nproc - 1] = (uint64_t)1 << 32;
+    P->collide = (P->nproc > 0 && P->cand > 0) ? 1 : 0;
+    P->key0 = (uint32_t)I.seed;
+    P->key1 = (uint32_t)(I.seed >> 32);
+}
+
+// Charge of each species as an exact integer multiple of a common unit delta
+// (needed by the integer field solve).
+int charge_units(const pic_instance& I, double* delta, int32_t z[PIC_MAX_SPECIES], std::string* why)
+{
+    double d = 0.0;
+    for (int s = 0; s < I.nspecies; ++s) {
+        const double qw = std::fabs(I.sp[s].charge * I.sp[s].weight);
+        if (qw > 0 && (d == 0.0 || qw < d)) d = qw;
+    }
+    if (d == 0.0) d = 1.0;
+    for (int s = 0; s < I.nspecies; ++s) {
+        const double qw = I.sp[s].charge * I.sp[s].weight;
+        const double r = std::nearbyint(qw / d);
+        if (std::fabs(r) > 1048576.0 || r * d != qw) {
+            *why = "Poisson field: species charges q*w must be integer multiples of a common unit";
+            return PIC_EINVAL;
+        }
+        z[s] = (int32_t)r;
+    }
+    *delta = d;
+    return PIC_OK;
+}
+
+MoveArgs move_args(pic_handle* h)
+{
+    MoveArgs a;
+    const Store& S = h->st[h->cur];
+    a.cell = S.cell;
+    a.off = S.off;
+    a.ux = S.ux;
+    a.uy = S.uy;
+    a.uz = S.uz;
+    a.id = S.id;
+    a.seg = h->segd;
+    a.inst = h->instd;
+    a.nseg = h->nseg;
+    a.tile_start = h->tile_start;
+    a.seg_nmove = h->seg_nmove;
+    a.seg_n = h->seg_n;
+    a.seg_live = h->seg_live;
+    a.accel = h->accel;
+    a.dep = h->dep;
+    a.wall_count = h->wall_count;
+    a.wall_energy = h->wall_energy;
+    a.collisions = h->collisions;
+    a.events = h->events;
+    a.ev_count = h->ev_count;
+    a.err = h->err;
+    a.step = h->step_d;
+    return a;
+}
+
+FieldArgs field_args(pic_handle* h)
+{
+    FieldArgs f;
+    f.seg = h->segd;
+    f.inst = h->instd;
+    f.ninst = h->ninst;
+    f.max_nodes = h->max_nodes;
+    f.dep = h->dep;
+    f.dep_last = h->dep_last;
+    f.accel = h->accel;
+    f.precision = h->precision;
+    f.E = h->E;
+    f.R = h->R;
+    f.UN = h->UN;
+    f.step = h->step_d;
+    f.any_poisson = h->any_poisson ? 1 : 0;
+    return f;
+}
+
+int launch_move(pic_handle* h, bool move)
+{
+    const MoveArgs a = move_args(h);
+    const bool mag = move && h->any_mag;
+    Span sp(h, 0);
+    h->kernels += 1;
+    const cudaError_t e = h->precision == PIC_FP64
+                              ? launch_move_f64(a, mag, move, h->nt, h->grid_move, h->stream)
+                              : launch_move_f32(a, mag, move, h->nt, h->grid_move, h->stream);
+    CUDA_TRY(h, e);
+    return PIC_OK;
+}
+
+int launch_tiles_h(pic_handle* h)
+{
+    Span sp(h, 3);
+    h->kernels += 1;
+    CUDA_TRY(h, launch_tiles(h->segd, h->seg_n, h->seg_nmove, h->tile_start, h->nseg, h->nt, h->stream));
+    return PIC_OK;
+}
+
+int ensure_fields(pic_handle* h)
+{
+    if (!h->stale) return PIC_OK;
+    int rc = launch_tiles_h(h);
+    if (rc) return rc;
+    if ((rc = launch_move(h, false))) return rc;
+    {
+        Span sp(h, 1);
+        h->kernels += h->any_poisson ? 2 : 1;
+        CUDA_TRY(h, launch_field(field_args(h), false, h->stream));
+    }
+    h->stale = false;
+    return PIC_OK;
+}
+
+int do_sort(pic_handle* h)
+{
+    int rc = launch_tiles_h(h);
+    if (rc) return rc;
+    Span sp(h, 2);
+    CUDA_TRY(h, cudaMemsetAsync(h->hist, 0, sizeof(unsigned) * (size_t)h->seg_nodes, h->stream));
+    SortArgs a;
+    a.seg = h->segd;
+    a.nseg = h->nseg;
+    a.precision = h->precision;
+    a.tile_start = h->tile_start;
+    a.seg_nmove = h->seg_nmove;
+    a.seg_n = h->seg_n;
+    a.seg_live = h->seg_live;
+    a.hwm_alt = h->hwm_alt;
+    a.hist = h->hist;
+    a.newn = h->newn;
+    for (int b = 0; b < 2; ++b) {
+        a.cell[b] = h->st[b].cell;
+        a.off[b] = h->st[b].off;
+        a.ux[b] = h->st[b].ux;
+        a.uy[b] = h->st[b].uy;
+        a.uz[b] = h->st[b].uz;
+        a.id[b] = h->st[b].id;
+    }
+    a.src = h->cur;
+    a.max_cap = h->max_cap;
+    a.max_cells = h->max_nodes - 1;
+    h->kernels += 4;
+    CUDA_TRY(h, launch_sort(a, h->nt, h->grid_move, h->stream));
+    h->cur = 1 - h->cur;
+    return PIC_OK;
+}
+
+// Synchronise and translate a latched device error.
+int sync_check(pic_handle* h)
+{
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    unsigned e = 0;
+    CUDA_TRY(h, cudaMemcpy(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (e == 0) return PIC_OK;
+    int code = PIC_ECUDA;
+    std::string msg;
+    if (e & kErrInput) { code = PIC_EINVAL; msg = "loaded particle with cell outside [0, ncells) or offset outside [0, 1)"; }
+    else if (e & kErrCapacity) { code = PIC_ECAPACITY; msg = "particle creation overflowed a species segment, the event buffer or the 32-bit ids"; }
+    else if (e & kErrNonFinite) { code = PIC_ENONFINITE; msg = "a particle velocity became non-finite"; }
+    else if (e & kErrTimeout) { code = PIC_ETIMEOUT; msg = "a bounded device wait ran out"; }
+    h->state = code;
+    h->last_error = msg;
+    return code;
+}
+
+int collect_times(pic_handle* h)
+{
+    if (h->timed.empty()) return PIC_OK;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (auto& t : h->timed) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        h->ms[t.cls] += ms;
+        h->launches[t.cls] += 1;
+        h->event_pool.push_back(t.a);
+        h->event_pool.push_back(t.b);
+    }
+    h->timed.clear();
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_create(const pic_config* cfg, pic_handle** out)
+{
+    g_create_error.clear();
+    if (!cfg || !out || !cfg->inst || cfg->n_instances < 1)
+        return fail(nullptr, PIC_EINVAL, "pic_create: null config/out/instances or n_instances < 1");
+    if (cfg->precision != PIC_FP32 && cfg->precision != PIC_FP64)
+        return fail(nullptr, PIC_EINVAL, "precision must be PIC_FP32 or PIC_FP64");
+    if (cfg->sort_interval < 0) return fail(nullptr, PIC_EINVAL, "sort_interval must be >= 0");
+    if (cfg->block != 0 && cfg->block != 128 && cfg->block != 256 && cfg->block != 512)
+        return fail(nullptr, PIC_EINVAL, "block must be 0, 128, 256 or 512");
+    for (int i = 0; i < cfg->n_instances; ++i) {
+        std::string why;
+        if (validate_instance(cfg->inst[i], i, &why)) return fail(nullptr, PIC_EINVAL, why);
+    }
+    pic_handle* h = new (std::nothrow) pic_handle();
+    if (!h) return fail(nullptr, PIC_ENOMEM, "host allocation failed");
+    auto bail = [&](int rc) {
+        g_create_error = h->last_error;
+        pic_destroy(h);
+        return rc;
+    };
+    h->precision = cfg->precision;
+    h->tsize = cfg->precision == PIC_FP64 ? 8 : 4;
+    h->sort_interval = cfg->sort_interval;
+    h->nt = cfg->block ? cfg->block : 256;
+    h->ninst = cfg->n_instances;
+    h->inst.assign(cfg->inst, cfg->inst + cfg->n_instances);
+    const double S = cfg->precision == PIC_FP64 ? 281474976710656.0 : 16777216.0;
+
+    // segment and node layout
+    int64_t slot = 0, snode = 0, inode = 0, ev = 0;
+    for (int i = 0; i < h->ninst; ++i) {
+        const pic_instance& I = h->inst[i];
+        InstParams ip;
+        std::memset(&ip, 0, sizeof(ip));
+        ip.ncells = I.ncells;
+        ip.field = I.field;
+        ip.seg0 = (int32_t)h->segh.size();
+        ip.nseg = I.nspecies;
+        ip.inode = inode;
+        double delta = 1.0;
+        if (I.field == PIC_FIELD_POISSON) {
+            std::string why;
+            if (charge_units(I, &delta, ip.z, &why)) {
+                h->last_error = "instance " + std::to_string(i) + ": " + why;
+                return bail(PIC_EINVAL);
+            }
+            h->any_poisson = true;
+        }
+        ip.lambda = delta / (2.0 * (double)I.ncells * S * I.eps0);
+        bool ionize = false;
+        int64_t evcap = 0;
+        for (int k = 0; k < I.nproc; ++k)
+            if (I.proc[k].kind == PIC_PROC_IONIZE) {
+                ionize = true;
+                evcap = std::max<int64_t>(evcap, round_up(std::max<int64_t>(I.sp[I.proc[k].species].capacity, 1), kSegAlign));
+            }
+        ip.ev_base = ev;
+        ip.ev_cap = ionize ? evcap : 0;
+        ev += ip.ev_cap;
+        h->any_ionize |= ionize;
+        if (I.B[0] != 0.0 || I.B[1] != 0.0 || I.B[2] != 0.0) h->any_mag = true;
+        for (int s = 0; s < I.nspecies; ++s) {
+            SegParams P;
+            std::memset(&P, 0, sizeof(P));
+            P.inst = i;
+            P.species = s;
+            P.ncells = I.ncells;
+            P.bc = I.bc;
+            P.base = slot;
+            P.cap = round_up(std::max<int64_t>(I.sp[s].capacity, 4), kSegAlign);
+            P.node = snode;
+            P.inode = inode;
+            seg_constants(I, s, &P);
+            for (int q = 0; q < P.nproc; ++q)
+                if (P.kind[q] == PIC_PROC_IONIZE) P.product[q] = ip.seg0 + P.product[q];
+            slot += P.cap;
+            snode += round_up(I.ncells + 1, 4);
+            h->max_cap = std::max(h->max_cap, P.cap);
+            h->segh.push_back(P);
+        }
+        inode += I.ncells + 1;
+        h->max_nodes = std::max(h->max_nodes, I.ncells + 1);
+        h->insth.push_back(ip);
+    }
+    h->nseg = (int)h->segh.size();
+    h->total_cap = slot;
+    h->seg_nodes = snode;
+    h->inst_nodes = inode;
+    h->ev_total = ev;
+
+    if (cfg->cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            h->last_error = "cudaStreamCreate failed";
+            return bail(PIC_ECUDA);
+        }
+        h->own_stream = true;
+    }
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        h->last_error = "no CUDA device";
+        return bail(PIC_ECUDA);
+    }
+    h->sms = prop.multiProcessorCount;
+    const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, h->nt)
+                                             : move_blocks_per_sm_f32(h->any_mag, h->nt);
+    h->grid_move = h->sms * std::max(bps, 1);
+
+    // device memory
+    int rc = PIC_OK;
+    const size_t T = h->tsize;
+    for (int b = 0; b < 2 && rc == PIC_OK; ++b) {
+        Store& st = h->st[b];
+        char *o = nullptr, *x = nullptr, *y = nullptr, *z = nullptr;
+        if ((rc = dalloc(h, &st.cell, (size_t)slot))) break;
+        if ((rc = dalloc(h, &o, (size_t)slot * T))) break;
+        if ((rc = dalloc(h, &x, (size_t)slot * T))) break;
+        if ((rc = dalloc(h, &y, (size_t)slot * T))) break;
+        if ((rc = dalloc(h, &z, (size_t)slot * T))) break;
+        if ((rc = dalloc(h, &st.id, (size_t)slot))) break;
+        st.off = o; st.ux = x; st.uy = y; st.uz = z;
+    }
+    char* acc = nullptr;
+    if (rc == PIC_OK) rc = dalloc(h, &acc, (size_t)snode * T);
+    h->accel = acc;
+    if (rc == PIC_OK) rc = dalloc(h, &h->dep, (size_t)snode);
+    if (rc == PIC_OK) rc = dalloc(h, &h->dep_last, (size_t)snode);
+    if (rc == PIC_OK) rc = dalloc(h, &h->hist, (size_t)snode);
+    if (rc == PIC_OK) rc = dalloc(h, &h->E, (size_t)inode);
+    if (rc == PIC_OK) rc = dalloc(h, &h->R, (size_t)inode);
+    if (rc == PIC_OK) rc = dalloc(h, &h->UN, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->phi_d, (size_t)h->max_nodes);
+    if (rc == PIC_OK) rc = dalloc(h, &h->segd, (size_t)h->nseg);
+    if (rc == PIC_OK) rc = dalloc(h, &h->instd, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->newn, (size_t)h->nseg);
+    if (rc == PIC_OK) rc = dalloc(h, &h->seg_n, (size_t)h->nseg);
+    if (rc == PIC_OK) rc = dalloc(h, &h->seg_live, (size_t)h->nseg);
+    if (rc == PIC_OK) rc = dalloc(h, &h->hwm_alt, (size_t)h->nseg);
+    if (rc == PIC_OK) rc = dalloc(h, &h->seg_nmove, (size_t)h->nseg);
+    if (rc == PIC_OK) rc = dalloc(h, &h->tile_start, (size_t)h->nseg + 1);
+    if (rc == PIC_OK) rc = dalloc(h, &h->wall_count, (size_t)h->nseg * 2);
+    if (rc == PIC_OK) rc = dalloc(h, &h->wall_energy, (size_t)h->nseg * 2);
+    if (rc == PIC_OK) rc = dalloc(h, &h->collisions, (size_t)h->ninst * kMaxProc);
+    if (rc == PIC_OK) rc = dalloc(h, &h->events, (size_t)std::max<int64_t>(ev, 1));
+    if (rc == PIC_OK) rc = dalloc(h, &h->ev_count, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->next_id, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->err, 1);
+    if (rc == PIC_OK) rc = dalloc(h, &h->step_d, 1);
+    if (rc == PIC_OK) rc = dalloc(h, &h->kin, (size_t)PIC_MAX_SPECIES);
+    if (rc) return bail(rc);
+
+    cudaStream_t s = h->stream;
+    auto z = [&](void* p, size_t bytes) { return cudaMemsetAsync(p, 0, bytes, s); };
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = z(h->st[b].off, (size_t)slot * T);
+        if (e == cudaSuccess) e = z(h->st[b].ux, (size_t)slot * T);
+        if (e == cudaSuccess) e = z(h->st[b].uy, (size_t)slot * T);
+        if (e == cudaSuccess) e = z(h->st[b].uz, (size_t)slot * T);
+        if (e == cudaSuccess) e = z(h->st[b].id, (size_t)slot * 4);
+        if (e == cudaSuccess) e = launch_fill_i32(h->st[b].cell, 0, slot, -1, s);
+    }
+    if (e == cudaSuccess) e = z(h->accel, (size_t)snode * T);
+    if (e == cudaSuccess) e = z(h->dep, (size_t)snode * 8);
+    if (e == cudaSuccess) e = z(h->dep_last, (size_t)snode * 8);
+    if (e == cudaSuccess) e = z(h->E, (size_t)inode * 8);
+    if (e == cudaSuccess) e = z(h->R, (size_t)inode * 16);
+    if (e == cudaSuccess) e = z(h->UN, (size_t)h->ninst * 16);
+    if (e == cudaSuccess) e = z(h->seg_n, (size_t)h->nseg * 8);
+    if (e == cudaSuccess) e = z(h->seg_live, (size_t)h->nseg * 8);
+    if (e == cudaSuccess) e = z(h->hwm_alt, (size_t)h->nseg * 8);
+    if (e == cudaSuccess) e = z(h->wall_count, (size_t)h->nseg * 16);
+    if (e == cudaSuccess) e = z(h->wall_energy, (size_t)h->nseg * 16);
+    if (e == cudaSuccess) e = z(h->collisions, (size_t)h->ninst * kMaxProc * 8);
+    if (e == cudaSuccess) e = z(h->ev_count, (size_t)h->ninst * 8);
+    if (e == cudaSuccess) e = z(h->next_id, (size_t)h->ninst * 8);
+    if (e == cudaSuccess) e = z(h->err, 4);
+    if (e == cudaSuccess) e = z(h->step_d, 8);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->segd, h->segh.data(), sizeof(SegParams) * h->segh.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->instd, h->insth.data(), sizeof(InstParams) * h->insth.size(),
+                            cudaMemcpyHostToDevice, s);
+    // constant fields: none (A = 0) or a uniform external field
+    if (e == cudaSuccess) {
+        std::vector<double> Eh((size_t)inode, 0.0);
+        std::vector<char> Ah((size_t)snode * T, 0);
+        for (int i = 0; i < h->ninst; ++i) {
+            const pic_instance& I = h->inst[i];
+            if (I.field != PIC_FIELD_EXTERNAL) continue;
+            for (int j = 0; j <= I.ncells; ++j) Eh[h->insth[i].inode + j] = I.E_ext;
+            for (int k = 0; k < I.nspecies; ++k) {
+                const SegParams& P = h->segh[h->insth[i].seg0 + k];
+                for (int j = 0; j <= I.ncells; ++j) {
+                    const double a = P.accel * I.E_ext;
+                    if (T == 8) reinterpret_cast<double*>(Ah.data())[P.node + j] = a;
+                    else reinterpret_cast<float*>(Ah.data())[P.node + j] = (float)a;
+                }
+            }
+        }
+        e = cudaMemcpyAsync(h->E, Eh.data(), Eh.size() * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->accel, Ah.data(), Ah.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        h->last_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
+        return bail(PIC_ECUDA);
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                       const int32_t* cell, const double* off, const double* vx,
+                       const double* vy, const double* vz, const uint32_t* id,
+                       int32_t on_device)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || n < 0)
+        return fail(h, PIC_EINVAL, "pic_load_particles: bad instance/species/count");
+    if (n > 0 && (!cell || !off || !vx || !vy || !vz))
+        return fail(h, PIC_EINVAL, "pic_load_particles: null input array");
+    const int si = h->insth[inst].seg0 + species;
+    const SegParams& P = h->segh[si];
+    if (n > P.cap) return fail(h, PIC_ECAPACITY, "pic_load_particles: n exceeds the species capacity");
+    cudaStream_t s = h->stream;
+    // staging of host input
+    void* stage = nullptr;
+    const int32_t* dc = cell;
+    const double *doff = off, *dvx = vx, *dvy = vy, *dvz = vz;
+    const uint32_t* did = id;
+    if (!on_device && n > 0) {
+        const size_t bytes = (size_t)n * (4 + 8 * 4) + (id ? (size_t)n * 4 : 0) + 64;
+        CUDA_TRY(h, cudaMallocAsync(&stage, bytes, s));
+        char* p = static_cast<char*>(stage);
+        auto put = [&](const void* src, size_t b) {
+            char* d = p;
+            p += (b + 15) / 16 * 16;
+            return cudaMemcpyAsync(d, src, b, cudaMemcpyHostToDevice, s) == cudaSuccess ? d : nullptr;
+        };
+        const size_t nb8 = (size_t)n * 8;
+        dc = (const int32_t*)put(cell, (size_t)n * 4);
+        doff = (const double*)put(off, nb8);
+        dvx = (const double*)put(vx, nb8);
+        dvy = (const double*)put(vy, nb8);
+        dvz = (const double*)put(vz, nb8);
+        did = id ? (const uint32_t*)put(id, (size_t)n * 4) : nullptr;
+        if (!dc || !doff || !dvx || !dvy || !dvz || (id && !did)) {
+            cudaFreeAsync(stage, s);
+            return fail(h, PIC_ECUDA, "pic_load_particles: host-to-device copy failed");
+        }
+    }
+    // automatic ids continue after the largest id of the instance
+    unsigned long long id0 = 0;
+    if (!id) {
+        CUDA_TRY(h, cudaMemcpyAsync(&id0, h->next_id + inst, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        if (id0 + (unsigned long long)n > 0xFFFFFFFFull)
+            return fail(h, PIC_ECAPACITY, "pic_load_particles: 32-bit particle ids exhausted");
+    }
+    LoadArgs l;
+    l.cell = dc;
+    l.off = doff;
+    l.vx = dvx;
+    l.vy = dvy;
+    l.vz = dvz;
+    l.id = did;
+    l.n = n;
+    l.id0 = (uint32_t)id0;
+    l.vscale = h->inst[inst].dt / h->inst[inst].dx;
+    l.base = P.base;
+    l.cap = P.cap;
+    l.ncells = P.ncells;
+    const Store& S = h->st[h->cur];
+    l.s_cell = S.cell;
+    l.s_off = S.off;
+    l.s_ux = S.ux;
+    l.s_uy = S.uy;
+    l.s_uz = S.uz;
+    l.s_id = S.id;
+    l.err = h->err;
+    l.precision = h->precision;
+    CUDA_TRY(h, launch_load(l, s));
+    // the other copy of the segment holds nothing
+    CUDA_TRY(h, launch_fill_i32(h->st[1 - h->cur].cell, P.base, P.base + P.cap, -1, s));
+    // counts and the next automatic id
+    std::vector<unsigned long long> nn(1, (unsigned long long)n);
+    CUDA_TRY(h, cudaMemcpyAsync(h->seg_n + si, nn.data(), 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->seg_live + si, nn.data(), 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemsetAsync(h->hwm_alt + si, 0, 8, s));
+    if (stage) CUDA_TRY(h, cudaFreeAsync(stage, s));
+    unsigned long long nid = 0;
+    if (id) {
+        // largest loaded id + 1 (host input scanned here; device input on the host copy)
+        std::vector<uint32_t> tmp;
+        const uint32_t* hid = id;
+        if (on_device && n > 0) {
+            tmp.resize((size_t)n);
+            CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), id, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(h, cudaStreamSynchronize(s));
+            hid = tmp.data();
+        }
+        for (int64_t k = 0; k < n; ++k) nid = std::max<unsigned long long>(nid, (unsigned long long)hid[k] + 1);
+        unsigned long long cur = 0;
+        CUDA_TRY(h, cudaMemcpyAsync(&cur, h->next_id + inst, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        nid = std::max(nid, cur);
+    } else {
+        nid = id0 + (unsigned long long)n;
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->next_id + inst, &nid, 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    h->stale = true;
+    return PIC_OK;
+}
+
+int pic_step(pic_handle* h, int64_t nsteps)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(h, PIC_EINVAL, "pic_step: nsteps < 0");
+    if ((rc = ensure_fields(h))) return rc;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if ((rc = launch_tiles_h(h))) return rc;
+        if ((rc = launch_move(h, true))) return rc;
+        if (h->any_ionize) {
+            Span sp(h, 3);
+            h->kernels += 1;
+            CUDA_TRY(h, launch_births(h->instd, h->ninst, h->events, h->ev_count, h->next_id,
+                                      h->st[h->cur].id, h->err, h->stream));
+        }
+        {
+            Span sp(h, 1);
+            h->kernels += h->any_poisson ? 2 : 1;
+            CUDA_TRY(h, launch_field(field_args(h), true, h->stream));
+        }
+        h->step_h += 1;
+        if (h->sort_interval > 0 && h->step_h % h->sort_interval == 0)
+            if ((rc = do_sort(h))) return rc;
+    }
+    return PIC_OK;
+}
+
+int pic_sync(pic_handle* h)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    return sync_check(h);
+}
+
+int pic_moments(pic_handle* h, int32_t inst, pic_moments_out* out, double* density,
+                double* phi, double* E)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (inst < 0 || inst >= h->ninst || !out) return fail(h, PIC_EINVAL, "pic_moments: bad arguments");
+    if ((rc = ensure_fields(h))) return rc;
+    const pic_instance& I = h->inst[inst];
+    const InstParams& ip = h->insth[inst];
+    const int ns = I.nspecies, N = I.ncells;
+    cudaStream_t s = h->stream;
+    CUDA_TRY(h, cudaMemsetAsync(h->kin, 0, sizeof(double) * PIC_MAX_SPECIES, s));
+    const Store& S = h->st[h->cur];
+    int64_t maxslots = 0;
+    for (int k = 0; k < ns; ++k) maxslots = std::max(maxslots, h->segh[ip.seg0 + k].cap);
+    CUDA_TRY(h, launch_kinetic(h->segd, ip.seg0, ns, maxslots, S.cell, S.ux, S.uy, S.uz,
+                               h->precision, h->kin, s));
+    if (phi && I.field == PIC_FIELD_POISSON)
+        CUDA_TRY(h, launch_potential(field_args(h), inst, I.dx, h->phi_d, s));
+    if ((rc = sync_check(h))) return rc;
+
+    std::memset(out, 0, sizeof(*out));
+    int64_t step = 0;
+    std::vector<unsigned long long> live(ns), wc(2 * ns), col(kMaxProc);
+    std::vector<double> we(2 * ns), kin(ns);
+    CUDA_TRY(h, cudaMemcpy(&step, h->step_d, 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(live.data(), h->seg_live + ip.seg0, 8 * ns, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(wc.data(), h->wall_count + 2 * ip.seg0, 16 * ns, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(we.data(), h->wall_energy + 2 * ip.seg0, 16 * ns, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(col.data(), h->collisions + (size_t)inst * kMaxProc, 8 * kMaxProc, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(kin.data(), h->kin, 8 * ns, cudaMemcpyDeviceToHost));
+    out->step = step;
+    for (int k = 0; k < ns; ++k) {
+        out->live[k] = (int64_t)live[k];
+        out->wall_count[k][0] = (int64_t)wc[2 * k];
+        out->wall_count[k][1] = (int64_t)wc[2 * k + 1];
+        out->wall_energy[k][0] = we[2 * k];
+        out->wall_energy[k][1] = we[2 * k + 1];
+        out->kinetic[k] = kin[k];
+    }
+    for (int q = 0; q < I.nproc; ++q) out->collisions[q] = (int64_t)col[q];
+    if (density) {
+        const double Sunit = h->precision == PIC_FP64 ? 281474976710656.0 : 16777216.0;
+        std::vector<unsigned long long> d((size_t)(N + 1));
+        for (int k = 0; k < ns; ++k) {
+            const SegParams& P = h->segh[ip.seg0 + k];
+            CUDA_TRY(h, cudaMemcpy(d.data(), h->dep_last + P.node, 8 * (size_t)(N + 1), cudaMemcpyDeviceToHost));
+            const double wdx = I.sp[k].weight / I.dx;
+            double* o = density + (size_t)k * (N + 1);
+            for (int j = 0; j <= N; ++j) o[j] = wdx * ((double)d[j] / Sunit);
+            if (I.bc == PIC_BC_PERIODIC) {
+                const double v = wdx * ((double)(d[0] + d[N]) / Sunit);
+                o[0] = v;
+                o[N] = v;
+            } else {
+                o[0] *= 2.0;
+                o[N] *= 2.0;
+            }
+        }
+    }
+    if (E) CUDA_TRY(h, cudaMemcpy(E, h->E + ip.inode, 8 * (size_t)(N + 1), cudaMemcpyDeviceToHost));
+    if (phi) {
+        if (I.field == PIC_FIELD_POISSON) {
+            CUDA_TRY(h, cudaMemcpy(phi, h->phi_d, 8 * (size_t)(N + 1), cudaMemcpyDeviceToHost));
+        } else {
+            const double e0 = I.field == PIC_FIELD_EXTERNAL ? I.E_ext : 0.0;
+            for (int j = 0; j <= N; ++j) phi[j] = -e0 * ((double)j * I.dx);
+        }
+    }
+    return PIC_OK;
+}
+
+int pic_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || !n)
+        return fail(h, PIC_EINVAL, "pic_count: bad arguments");
+    if ((rc = sync_check(h))) return rc;
+    unsigned long long v = 0;
+    CUDA_TRY(h, cudaMemcpy(&v, h->seg_live + h->insth[inst].seg0 + species, 8, cudaMemcpyDeviceToHost));
+    *n = (int64_t)v;
+    return PIC_OK;
+}
+
+int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
+                      int32_t* cell, double* off, double* vx, double* vy, double* vz,
+                      uint32_t* id, int32_t on_device, int64_t* n_out)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || !n_out)
+        return fail(h, PIC_EINVAL, "pic_get_particles: bad arguments");
+    if ((rc = sync_check(h))) return rc;
+    const int si = h->insth[inst].seg0 + species;
+    const SegParams& P = h->segh[si];
+    unsigned long long live = 0, nslots = 0;
+    CUDA_TRY(h, cudaMemcpy(&live, h->seg_live + si, 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(&nslots, h->seg_n + si, 8, cudaMemcpyDeviceToHost));
+    *n_out = (int64_t)live;
+    if ((int64_t)live > capacity) return fail(h, PIC_ECAPACITY, "pic_get_particles: capacity too small");
+    nslots = std::min<unsigned long long>(((nslots + 3) & ~3ull), (unsigned long long)P.cap);
+    cudaStream_t s = h->stream;
+    const int64_t nb = ((int64_t)nslots + 1023) / 1024;
+    const size_t n = (size_t)std::max<unsigned long long>(live, 1);
+    char* tmp = nullptr;
+    const size_t scratch = (size_t)(nb + 1) * 8;
+    const size_t outb = on_device ? 0 : n * (4 + 8 * 4 + 4) + 7 * 16;
+    CUDA_TRY(h, cudaMallocAsync((void**)&tmp, scratch + outb, s));
+    GetArgs g;
+    const Store& S = h->st[h->cur];
+    g.s_cell = S.cell;
+    g.s_off = S.off;
+    g.s_ux = S.ux;
+    g.s_uy = S.uy;
+    g.s_uz = S.uz;
+    g.s_id = S.id;
+    g.base = P.base;
+    g.nslots = (int64_t)nslots;
+    g.vscale_inv = h->inst[inst].dx / h->inst[inst].dt;
+    g.precision = h->precision;
+    g.block_count = reinterpret_cast<unsigned long long*>(tmp);
+    g.capacity = (int64_t)live;
+    if (on_device) {
+        g.cell = cell; g.off = off; g.vx = vx; g.vy = vy; g.vz = vz; g.id = id;
+    } else {
+        char* p = tmp + (scratch + 15) / 16 * 16;
+        auto take = [&](size_t b) { char* d = p; p += (b + 15) / 16 * 16; return d; };
+        g.cell = cell ? (int32_t*)take(n * 4) : nullptr;
+        g.off = off ? (double*)take(n * 8) : nullptr;
+        g.vx = vx ? (double*)take(n * 8) : nullptr;
+        g.vy = vy ? (double*)take(n * 8) : nullptr;
+        g.vz = vz ? (double*)take(n * 8) : nullptr;
+        g.id = id ? (uint32_t*)take(n * 4) : nullptr;
+    }
+    CUDA_TRY(h, launch_get(g, s));
+    if (!on_device && live > 0) {
+        const size_t m = (size_t)live;
+        if (cell) CUDA_TRY(h, cudaMemcpyAsync(cell, g.cell, m * 4, cudaMemcpyDeviceToHost, s));
+        if (off) CUDA_TRY(h, cudaMemcpyAsync(off, g.off, m * 8, cudaMemcpyDeviceToHost, s));
+        if (vx) CUDA_TRY(h, cudaMemcpyAsync(vx, g.vx, m * 8, cudaMemcpyDeviceToHost, s));
+        if (vy) CUDA_TRY(h, cudaMemcpyAsync(vy, g.vy, m * 8, cudaMemcpyDeviceToHost, s));
+        if (vz) CUDA_TRY(h, cudaMemcpyAsync(vz, g.vz, m * 8, cudaMemcpyDeviceToHost, s));
+        if (id) CUDA_TRY(h, cudaMemcpyAsync(id, g.id, m * 4, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(h, cudaFreeAsync(tmp, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    return PIC_OK;
+}
+
+int pic_charge_raw(pic_handle* h, int32_t inst, int64_t* out, int64_t* unit)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (inst < 0 || inst >= h->ninst || !out || !unit) return fail(h, PIC_EINVAL, "pic_charge_raw: bad arguments");
+    if ((rc = ensure_fields(h))) return rc;
+    if ((rc = sync_check(h))) return rc;
+    const InstParams& ip = h->insth[inst];
+    const int N = h->inst[inst].ncells;
+    for (int k = 0; k < ip.nseg; ++k) {
+        const SegParams& P = h->segh[ip.seg0 + k];
+        CUDA_TRY(h, cudaMemcpy(out + (size_t)k * (N + 1), h->dep_last + P.node, 8 * (size_t)(N + 1),
+                               cudaMemcpyDeviceToHost));
+    }
+    *unit = h->precision == PIC_FP64 ? (int64_t)1 << 48 : (int64_t)1 << 24;
+    return PIC_OK;
+}
+
+int pic_profile(pic_handle* h, int32_t enable)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if ((rc = collect_times(h))) return rc;
+    h->profiling = enable != 0;
+    for (int k = 0; k < 4; ++k) {
+        h->launches[k] = 0;
+        h->ms[k] = 0.0;
+    }
+    h->kernels = 0;
+    return PIC_OK;
+}
+
+int pic_kernel_time(pic_handle* h, int32_t which, int64_t* launches, double* total_ms)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (which < 0 || which > 4 || !launches || !total_ms) return fail(h, PIC_EINVAL, "pic_kernel_time: bad arguments");
+    if ((rc = collect_times(h))) return rc;
+    if (which == 4) {
+        *launches = h->kernels;
+        *total_ms = 0.0;
+        return PIC_OK;
+    }
+    *launches = h->launches[which];
+    *total_ms = h->ms[which];
+    return PIC_OK;
+}
+
+int pic_destroy(pic_handle* h)
+{
+    if (!h) return PIC_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& t : h->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    cudaGetLastError();
+    delete h;
+    return PIC_OK;
+}
+
+const char* pic_last_error(const pic_handle* h)
+{
+    return h ? h->last_error.c_str() : g_create_error.c_str();
+}
+
+int pic_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t n, int32_t on_device,
+               void* stream)
+{
+    g_create_error.clear();
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(nullptr, PIC_EINVAL, "pic_philox: bad arguments");
+    if (n == 0) return PIC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint32_t* dc = ctr;
+    uint32_t* dout = out;
+    void* tmp = nullptr;
+    const size_t b = (size_t)n * 16;
+    if (!on_device) {
+        if (cudaMallocAsync(&tmp, 2 * b, s) != cudaSuccess) return fail(nullptr, PIC_ENOMEM, "pic_philox: allocation failed");
+        dc = static_cast<uint32_t*>(tmp);
+        dout = static_cast<uint32_t*>(tmp) + 4 * n;
+        if (cudaMemcpyAsync((void*)dc, ctr, b, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(nullptr, PIC_ECUDA, "pic_philox: copy failed");
+    }
+    cudaError_t e = launch_philox(key, dc, dout, n, s);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, dout, b, cudaMemcpyDeviceToHost, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, std::string("pic_philox: ") + cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+}  // extern "C"

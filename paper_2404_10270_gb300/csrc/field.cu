@@ -1,0 +1,292 @@
+// field.cu -- field phase (Poisson solve and E = -grad phi, Section 2 "Field Solver")
+// plus the per-step bookkeeping kernels (tile list, ionization ids).
+//
+// Field solve.  The deposit gives, per instance and node j, the integer
+// Z_j = sum_s z_s D_s[j], where D_s is species s's fixed-point deposit (unit S per
+// particle) and z_s = q_s w_s / delta is an exact small integer.  The grounded
+// Dirichlet problem
+//     -phi[j-1] + 2 phi[j] - phi[j+1] = kappa Z_j  (1 <= j <= N-1),  phi[0] = phi[N] = 0,
+// kappa = delta dx / (S eps0), has the exact solution phi[j+1] - phi[j] = kappa (U/N - R_j)
+// with R_j = sum_{1<=k<=j} Z_k (R_0 = 0) and U = sum_{m=0}^{N-1} R_m = sum_k (N-k) Z_k.
+// Hence, with lambda = delta / (2 N S eps0) and every numerator an exact 128-bit integer:
+//     E_j = lambda (N (R_{j-1} + R_j) - 2U)             inside (centred difference),
+//     E_0 = lambda (-2U - 2N Z_0),  E_N = lambda (2N R_{N-1} - 2U + 2N Z_N)
+// (Gauss's law over the half cell at each wall).  This is the tridiagonal solve the
+// paper names, carried out as one prefix sum and one weighted sum, so it is
+// independent of launch geometry and rounds only once, at the conversion to FP64.
+#include "kernels.h"
+#include "mover.cuh"
+
+namespace bitpic {
+
+namespace {
+
+constexpr int kFieldThreads = 1024;
+
+__device__ __forceinline__ i128 warp_incl_scan(i128 v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const i128 t = shfl_up_i128(v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ i128 warp_sum(i128 v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const uint64_t lo = (uint64_t)v, hi = (uint64_t)((unsigned __int128)v >> 64);
+        const uint64_t l2 = __shfl_xor_sync(0xffffffffu, lo, d);
+        const uint64_t h2 = __shfl_xor_sync(0xffffffffu, hi, d);
+        v += (i128)(((unsigned __int128)h2 << 64) | l2);
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one i128 per thread; returns the exclusive prefix and
+// the block total.  All threads of the block must call it.
+__device__ i128 block_excl_scan(i128 v, i128* total, i128* sh /* >= 33 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const i128 inc = warp_incl_scan(v);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        i128 w = lane < nw ? sh[lane] : (i128)0;
+        const i128 wi = warp_incl_scan(w);
+        if (lane < nw) sh[lane] = wi - w;  // exclusive warp offsets
+        if (lane == nw - 1) sh[32] = wi;
+    }
+    __syncthreads();
+    const i128 out = sh[warp] + inc - v;
+    *total = sh[32];
+    __syncthreads();
+    return out;
+}
+
+__device__ i128 block_sum(i128 v, i128* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    i128 t = 0;
+    if (warp == 0) {
+        t = lane < nw ? sh[lane] : (i128)0;
+        t = warp_sum(t);
+        if (lane == 0) sh[32] = t;
+    }
+    __syncthreads();
+    t = sh[32];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ i128 node_charge(const FieldArgs& f, const InstParams& I, int j)
+{
+    i128 z = 0;
+    for (int k = 0; k < I.nseg; ++k) {
+        const SegParams& P = f.seg[I.seg0 + k];
+        z += (i128)I.z[k] * (i128)(long long)f.dep[P.node + j];
+    }
+    return z;
+}
+
+// One block per instance: R_j (prefix of the interior charge) and U.
+__global__ void __launch_bounds__(kFieldThreads) k_field_scan(const FieldArgs f)
+{
+    __shared__ i128 sh[33];
+    const InstParams I = f.inst[blockIdx.x];
+    if (I.field != PIC_FIELD_POISSON) return;
+    const int N = I.ncells;
+    const int nn = N + 1;
+    const int C = (nn + blockDim.x - 1) / blockDim.x;
+    const int j0 = min(nn, (int)threadIdx.x * C), j1 = min(nn, j0 + C);
+    i128 sum = 0, wsum = 0;
+    for (int j = j0; j < j1; ++j) {
+        if (j == 0 || j == N) continue;
+        const i128 z = node_charge(f, I, j);
+        sum += z;
+        wsum += (i128)(N - j) * z;
+    }
+    i128 tot;
+    i128 run = block_excl_scan(sum, &tot, sh);
+    const i128 U = block_sum(wsum, sh);
+    for (int j = j0; j < j1; ++j) {
+        if (j != 0 && j != N) run += node_charge(f, I, j);
+        f.R[I.inode + j] = run;
+    }
+    if (threadIdx.x == 0) f.UN[blockIdx.x] = U;
+}
+
+// One thread per node: E, the pre-scaled accelerations, and the deposit hand-over.
+template <typename T>
+__global__ void k_field_emit(const FieldArgs f, int advance)
+{
+    const int b = blockIdx.y;
+    const InstParams& I = f.inst[b];
+    const int N = I.ncells;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (advance && b == 0 && j == 0) *f.step += 1;
+    if (j > N) return;
+    i128 zj = 0;
+    for (int k = 0; k < I.nseg; ++k) {
+        const SegParams& P = f.seg[I.seg0 + k];
+        const unsigned long long d = f.dep[P.node + j];
+        f.dep_last[P.node + j] = d;
+        f.dep[P.node + j] = 0ull;
+        zj += (i128)I.z[k] * (i128)(long long)d;
+    }
+    if (I.field != PIC_FIELD_POISSON) return;
+    const i128 U = f.UN[b];
+    const i128 NN = (i128)N;
+    i128 G;
+    if (j == 0)
+        G = -2 * U - 2 * NN * zj;
+    else if (j == N)
+        G = 2 * NN * f.R[I.inode + N - 1] - 2 * U + 2 * NN * zj;
+    else
+        G = NN * (f.R[I.inode + j - 1] + f.R[I.inode + j]) - 2 * U;
+    const double E = I.lambda * i128_to_double(G);
+    f.E[I.inode + j] = E;
+    T* acc = static_cast<T*>(f.accel);
+    for (int k = 0; k < I.nseg; ++k) {
+        const SegParams& P = f.seg[I.seg0 + k];
+        acc[P.node + j] = (T)(P.accel * E);
+    }
+}
+
+// phi_j = 2 dx lambda (j U - N U_j), U_j = sum_{m<j} R_m.
+__global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, int b,
+                                                             double dx, double* phi)
+{
+    __shared__ i128 sh[33];
+    const InstParams I = f.inst[b];
+    const int N = I.ncells;
+    const int nn = N + 1;
+    const int C = (nn + blockDim.x - 1) / blockDim.x;
+    const int j0 = min(nn, (int)threadIdx.x * C), j1 = min(nn, j0 + C);
+    i128 sum = 0;
+    for (int j = j0; j < j1; ++j) sum += f.R[I.inode + j];
+    i128 tot;
+    i128 run = block_excl_scan(sum, &tot, sh);  // U_{j0}
+    const i128 U = f.UN[b];
+    for (int j = j0; j < j1; ++j) {
+        const i128 Phi = (i128)j * U - (i128)N * run;
+        phi[j] = (2.0 * dx * I.lambda) * i128_to_double(Phi);
+        run += f.R[I.inode + j];
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned long long* seg_n,
+                                                int64_t* seg_nmove, int64_t* tile_start, int nseg,
+                                                int tile_quads)
+{
+    __shared__ i128 sh[33];
+    const int C = (nseg + blockDim.x - 1) / blockDim.x;
+    const int s0 = min(nseg, (int)threadIdx.x * C), s1 = min(nseg, s0 + C);
+    int64_t local = 0;
+    for (int s = s0; s < s1; ++s) {
+        // an overflowing creation (already latched as an error) may have pushed the
+        // count past the capacity: never walk beyond the segment
+        const unsigned long long cap = (unsigned long long)seg[s].cap;
+        const unsigned long long n4 = min((seg_n[s] + 3ull) & ~3ull, cap);
+        seg_n[s] = n4;
+        seg_nmove[s] = (int64_t)n4;
+        const int64_t quads = (int64_t)(n4 >> 2);
+        local += (quads + tile_quads - 1) / tile_quads;
+    }
+    i128 tot;
+    int64_t run = (int64_t)block_excl_scan((i128)local, &tot, sh);
+    for (int s = s0; s < s1; ++s) {
+        tile_start[s] = run;
+        const int64_t quads = seg_nmove[s] >> 2;
+        run += (quads + tile_quads - 1) / tile_quads;
+    }
+    if (threadIdx.x == 0) tile_start[nseg] = (int64_t)tot;
+}
+
+// Children of this step's ionization events are numbered after the largest id so
+// far: electron 2r, ion 2r+1, r = rank of the parent id among this step's events.
+__global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* events,
+                                                unsigned long long* ev_count,
+                                                unsigned long long* next_id, uint32_t* id,
+                                                unsigned* err)
+{
+    __shared__ uint32_t sp[1024];
+    const int b = blockIdx.x;
+    const InstParams& I = inst[b];
+    const unsigned long long cnt = ev_count[b];
+    if (cnt == 0) return;
+    const int64_t n = (int64_t)min(cnt, (unsigned long long)I.ev_cap);
+    const Event* ev = events + I.ev_base;
+    const unsigned long long base = next_id[b];
+    if (base + 2ull * (unsigned long long)n > 0xFFFFFFFFull) {
+        if (threadIdx.x == 0) set_error(err, kErrCapacity);
+        return;
+    }
+    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const uint32_t p = i < n ? ev[i].parent : 0u;
+        int64_t rank = 0;
+        for (int64_t k0 = 0; k0 < n; k0 += 1024) {
+            const int64_t m = min((int64_t)1024, n - k0);
+            __syncthreads();
+            for (int64_t k = threadIdx.x; k < m; k += blockDim.x) sp[k] = ev[k0 + k].parent;
+            __syncthreads();
+            if (i < n)
+                for (int64_t k = 0; k < m; ++k) rank += sp[k] < p;
+        }
+        if (i < n) {
+            id[ev[i].slot_e] = (uint32_t)(base + 2ull * (unsigned long long)rank);
+            id[ev[i].slot_i] = (uint32_t)(base + 2ull * (unsigned long long)rank + 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        next_id[b] = base + 2ull * (unsigned long long)n;
+        ev_count[b] = 0ull;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_field(const FieldArgs& f, bool advance_step, cudaStream_t st)
+{
+    if (f.any_poisson) k_field_scan<<<f.ninst, kFieldThreads, 0, st>>>(f);
+    dim3 grid((unsigned)((f.max_nodes + 255) / 256), (unsigned)f.ninst);
+    if (f.precision == PIC_FP64)
+        k_field_emit<double><<<grid, 256, 0, st>>>(f, advance_step ? 1 : 0);
+    else
+        k_field_emit<float><<<grid, 256, 0, st>>>(f, advance_step ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* phi,
+                             cudaStream_t st)
+{
+    k_potential<<<1, kFieldThreads, 0, st>>>(f, inst, dx, phi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
+                         int64_t* tile_start, int nseg, int tile_quads, cudaStream_t st)
+{
+    k_tiles<<<1, 1024, 0, st>>>(seg, seg_n, seg_nmove, tile_start, nseg, tile_quads);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_births(const InstParams* inst, int ninst, Event* events,
+                          unsigned long long* ev_count, unsigned long long* next_id,
+                          uint32_t* id, unsigned* err, cudaStream_t st)
+{
+    k_births<<<ninst, 256, 0, st>>>(inst, events, ev_count, next_id, id, err);
+    return cudaGetLastError();
+}
+
+}  // namespace bitpic

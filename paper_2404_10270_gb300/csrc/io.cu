@@ -1,0 +1,232 @@
+// io.cu -- loading particles into the store, reading them back, diagnostics and the
+// stand-alone Philox kernel.
+#include "kernels.h"
+#include "mover.cuh"
+
+namespace bitpic {
+
+namespace {
+
+// Load: velocities physical -> cells per step (u = v dt/dx); invalid cells or
+// offsets are latched as kErrInput.  Slots [n, cap) become empty.
+template <typename T>
+__global__ void k_load(const LoadArgs l)
+{
+    T* off = static_cast<T*>(l.s_off);
+    T* ux = static_cast<T*>(l.s_ux);
+    T* uy = static_cast<T*>(l.s_uy);
+    T* uz = static_cast<T*>(l.s_uz);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < l.cap; k += stride) {
+        const int64_t g = l.base + k;
+        if (k < l.n) {
+            const int c = l.cell[k];
+            const double f = l.off[k];
+            const bool ok = c >= 0 && c < l.ncells && f >= 0.0 && f < 1.0;
+            if (!ok) set_error(l.err, kErrInput);
+            T ft = (T)f;
+            int cc = c;
+            if (ft >= T(1)) {  // an offset just below 1 that rounds up in FP32
+                ft = T(0);
+                cc = c + 1;
+                if (cc >= l.ncells) {
+                    cc = l.ncells - 1;
+                    ft = (T)0.99999994f;
+                }
+            }
+            l.s_cell[g] = ok ? cc : -1;
+            off[g] = ft;
+            ux[g] = (T)(l.vx[k] * l.vscale);
+            uy[g] = (T)(l.vy[k] * l.vscale);
+            uz[g] = (T)(l.vz[k] * l.vscale);
+            l.s_id[g] = l.id ? l.id[k] : l.id0 + (uint32_t)k;
+        } else {
+            l.s_cell[g] = -1;
+        }
+    }
+}
+
+__global__ void k_get_count(const int32_t* cell, int64_t base, int64_t nslots,
+                            unsigned long long* block_count)
+{
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool live = k < nslots && cell[base + k] >= 0;
+    const unsigned b = __ballot_sync(0xffffffffu, live);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&cnt, __popc(b));
+    __syncthreads();
+    if (threadIdx.x == 0) block_count[blockIdx.x] = (unsigned long long)cnt;
+}
+
+// exclusive scan of nb block counts (single block), total in block_count[nb]
+__global__ void __launch_bounds__(1024) k_get_scan(unsigned long long* bc, int64_t nb)
+{
+    __shared__ unsigned long long sh[33];
+    const int64_t C = (nb + blockDim.x - 1) / blockDim.x;
+    const int64_t i0 = min(nb, (int64_t)threadIdx.x * C), i1 = min(nb, i0 + C);
+    unsigned long long local = 0;
+    for (int64_t i = i0; i < i1; ++i) local += bc[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long inc = local;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = sh[lane];
+        unsigned long long wi = w;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += t;
+        }
+        sh[lane] = wi - w;
+        if (lane == 31) sh[32] = wi;
+    }
+    __syncthreads();
+    unsigned long long run = sh[warp] + inc - local;
+    for (int64_t i = i0; i < i1; ++i) {
+        const unsigned long long v = bc[i];
+        bc[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) bc[nb] = sh[32];
+}
+
+template <typename T>
+__global__ void k_get_write(const GetArgs g)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool live = k < g.nslots && g.s_cell[g.base + k] >= 0;
+    const unsigned b = __ballot_sync(0xffffffffu, live);
+    __shared__ int woff[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) woff[warp] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int r = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int t = woff[w];
+            woff[w] = r;
+            r += t;
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const int64_t o = (int64_t)g.block_count[blockIdx.x] + woff[warp] + __popc(b & lt);
+    if (o >= g.capacity) return;
+    const int64_t s = g.base + k;
+    if (g.cell) g.cell[o] = g.s_cell[s];
+    if (g.off) g.off[o] = (double)static_cast<const T*>(g.s_off)[s];
+    if (g.vx) g.vx[o] = (double)static_cast<const T*>(g.s_ux)[s] * g.vscale_inv;
+    if (g.vy) g.vy[o] = (double)static_cast<const T*>(g.s_uy)[s] * g.vscale_inv;
+    if (g.vz) g.vz[o] = (double)static_cast<const T*>(g.s_uz)[s] * g.vscale_inv;
+    if (g.id) g.id[o] = g.s_id[s];
+}
+
+template <typename T>
+__global__ void k_kinetic(const SegParams* seg, int s0, const int32_t* cell, const T* ux,
+                          const T* uy, const T* uz, double* out)
+{
+    const int s = s0 + blockIdx.y;
+    const SegParams& P = seg[s];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P.cap; k += stride) {
+        const int64_t g = P.base + k;
+        if (cell[g] < 0) continue;
+        const double a = ux[g], b = uy[g], c = uz[g];
+        acc += a * a + b * b + c * c;
+    }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        atomicAdd(out + blockIdx.y, P.kefac * t);
+    }
+}
+
+__global__ void k_philox(uint64_t key, const uint4* ctr, uint4* out, int64_t n)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) out[k] = philox4x32_10(ctr[k], (uint32_t)key, (uint32_t)(key >> 32));
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t lo, int64_t hi, int32_t v)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < hi; k += stride) p[k] = v;
+}
+
+int grid_for(int64_t n, int nt, int cap = 152 * 32)
+{
+    const int64_t g = (n + nt - 1) / nt;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+cudaError_t launch_load(const LoadArgs& l, cudaStream_t st)
+{
+    const int g = grid_for(l.cap, 256);
+    if (l.precision == PIC_FP64)
+        k_load<double><<<g, 256, 0, st>>>(l);
+    else
+        k_load<float><<<g, 256, 0, st>>>(l);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get(const GetArgs& g, cudaStream_t st)
+{
+    const int64_t nb = (g.nslots + 1023) / 1024;
+    if (nb == 0) return cudaSuccess;
+    k_get_count<<<(unsigned)nb, 1024, 0, st>>>(g.s_cell, g.base, g.nslots, g.block_count);
+    k_get_scan<<<1, 1024, 0, st>>>(g.block_count, nb);
+    if (g.precision == PIC_FP64)
+        k_get_write<double><<<(unsigned)nb, 1024, 0, st>>>(g);
+    else
+        k_get_write<float><<<(unsigned)nb, 1024, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic(const SegParams* seg, int s0, int ns, int64_t max_slots,
+                           const int32_t* cell, const void* ux, const void* uy,
+                           const void* uz, int precision, double* out, cudaStream_t st)
+{
+    dim3 grid((unsigned)grid_for(max_slots, 256, 1024), (unsigned)ns);
+    if (precision == PIC_FP64)
+        k_kinetic<double><<<grid, 256, 0, st>>>(seg, s0, cell, (const double*)ux,
+                                                 (const double*)uy, (const double*)uz, out);
+    else
+        k_kinetic<float><<<grid, 256, 0, st>>>(seg, s0, cell, (const float*)ux,
+                                                (const float*)uy, (const float*)uz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t n,
+                          cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    k_philox<<<g, 256, 0, st>>>(key, reinterpret_cast<const uint4*>(ctr),
+                                reinterpret_cast<uint4*>(out), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_i32(int32_t* p, int64_t lo, int64_t hi, int32_t v, cudaStream_t st)
+{
+    if (hi <= lo) return cudaSuccess;
+    k_fill_i32<<<grid_for(hi - lo, 256), 256, 0, st>>>(p, lo, hi, v);
+    return cudaGetLastError();
+}
+
+}  // namespace bitpic

@@ -1,0 +1,135 @@
+// kernels.h -- host-side launchers of the device kernels (one translation unit each
+// for the FP32 mover, the FP64 mover, the field phase, the sort and the I/O kernels).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bitpic {
+
+struct MoveArgs;
+
+// ---- mover (mover_f32.cu, mover_f64.cu) ---------------------------------------
+// `move` = false deposits the loaded particles without moving them (the density
+// phase of the initial field).  Returns the launch error.
+cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, int nt, int grid,
+                            cudaStream_t st);
+cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, int nt, int grid,
+                            cudaStream_t st);
+// resident blocks per SM of the mover variant (0 on error)
+int move_blocks_per_sm_f32(bool mag, int nt);
+int move_blocks_per_sm_f64(bool mag, int nt);
+
+// ---- field phase and bookkeeping (field.cu) -------------------------------------
+struct FieldArgs {
+    const SegParams* seg;
+    const InstParams* inst;
+    int ninst;
+    int max_nodes;                    // max ncells+1 over instances
+    unsigned long long* dep;          // accumulating deposit (zeroed by emit)
+    unsigned long long* dep_last;     // copy of the last complete deposit
+    void* accel;                      // T node arrays per segment
+    int precision;                    // PIC_FP32 / PIC_FP64
+    double* E;                        // per instance node arrays
+    i128* R;                          // per instance node arrays: prefix charge sums
+    i128* UN;                         // per instance: sum of R over nodes 0..N-1
+    int64_t* step;                    // incremented once per emit
+    int any_poisson;
+};
+cudaError_t launch_field(const FieldArgs& f, bool advance_step, cudaStream_t st);
+// potential of instance `inst` (FIELD_POISSON) into phi[0..N]
+cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* phi,
+                             cudaStream_t st);
+
+// Round each segment's slot count up to a whole quad, snapshot it as the count to
+// move, and build the tile prefix (tiles of `tile_quads` quads).
+cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
+                         int64_t* tile_start, int nseg, int tile_quads, cudaStream_t st);
+
+// Number this step's ionization products by the rank of their parent id.
+cudaError_t launch_births(const InstParams* inst, int ninst, Event* events,
+                          unsigned long long* ev_count, unsigned long long* next_id,
+                          uint32_t* id, unsigned* err, cudaStream_t st);
+
+// ---- sort (sort.cu) ---------------------------------------------------------------
+struct SortArgs {
+    const SegParams* seg;
+    int nseg;
+    int precision;
+    const int64_t* tile_start;
+    const int64_t* seg_nmove;
+    unsigned long long* seg_n;
+    unsigned long long* seg_live;
+    unsigned long long* hwm_alt;      // slots in use of the other copy
+    unsigned* hist;                   // per segment node arrays (cells), zeroed
+    unsigned long long* newn;         // per segment live count after the sort
+    // source and destination stores
+    int32_t* cell[2];
+    void* off[2];
+    void* ux[2];
+    void* uy[2];
+    void* uz[2];
+    uint32_t* id[2];
+    int src;
+    int64_t max_cap;                  // largest segment capacity
+    int max_cells;
+};
+cudaError_t launch_sort(const SortArgs& s, int nt, int grid, cudaStream_t st);
+
+// ---- I/O and diagnostics (io.cu) -------------------------------------------------
+struct LoadArgs {
+    const int32_t* cell;
+    const double* off;
+    const double* vx;
+    const double* vy;
+    const double* vz;
+    const uint32_t* id;     // NULL: id0 + k
+    int64_t n;
+    uint32_t id0;
+    double vscale;          // dt/dx
+    int64_t base, cap;
+    int ncells;
+    int32_t* s_cell;
+    void* s_off;
+    void* s_ux;
+    void* s_uy;
+    void* s_uz;
+    uint32_t* s_id;
+    unsigned* err;
+    int precision;
+};
+cudaError_t launch_load(const LoadArgs& l, cudaStream_t st);
+
+struct GetArgs {
+    const int32_t* s_cell;
+    const void* s_off;
+    const void* s_ux;
+    const void* s_uy;
+    const void* s_uz;
+    const uint32_t* s_id;
+    int64_t base, nslots;
+    double vscale_inv;      // dx/dt
+    int precision;
+    int32_t* cell;
+    double* off;
+    double* vx;
+    double* vy;
+    double* vz;
+    uint32_t* id;
+    unsigned long long* block_count;  // scratch, ceil(nslots/1024)+1 entries
+    int64_t capacity;                 // entries of the output arrays
+};
+cudaError_t launch_get(const GetArgs& g, cudaStream_t st);
+
+// sum of kefac |u|^2 over live particles of segments [s0, s0+ns) into out[ns]
+cudaError_t launch_kinetic(const SegParams* seg, int s0, int ns, int64_t max_slots,
+                           const int32_t* cell, const void* ux, const void* uy,
+                           const void* uz, int precision, double* out, cudaStream_t st);
+
+cudaError_t launch_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t n,
+                          cudaStream_t st);
+
+// fill int32 array p[lo, hi) with v
+cudaError_t launch_fill_i32(int32_t* p, int64_t lo, int64_t hi, int32_t v, cudaStream_t st);
+
+}  // namespace bitpic

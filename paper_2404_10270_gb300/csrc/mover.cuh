@@ -1,0 +1,560 @@
+// mover.cuh -- the fused per-particle time step ("particle mover" of the paper,
+// Section 2 and Listing 7) for one precision T:
+//
+//   gather   a = A[j] + f (A[j+1] - A[j])           (Listing 7, moveb())
+//   push     u += a, or the Boris rotation when B != 0 (Boris 1970)
+//   move     f += u_x; the integer part moves the particle across cells
+//   wall     absorbing (flux counters), periodic, or absorb + volume re-injection
+//   MCC      null collision: Philox(id, step, COLLIDE) word 0 < floor(P 2^32)
+//            selects a candidate, word 1 a process slot; energy thresholds,
+//            elastic / charge-exchange / ionization kinematics
+//   deposit  cloud-in-cell in fixed point: node j gets S - Q, node j+1 gets
+//            Q = rint(f S), so every particle adds exactly S (S = 2^24 FP32,
+//            2^48 FP64); warp-reduced per node, then shared-memory tile, then one
+//            64-bit atomic per node and block into HBM.
+//
+// Work decomposition: a tile is blockDim.x quads of four consecutive particles of
+// one segment (instance, species); each thread loads its quad with 128-bit
+// accesses.  A persistent grid walks the tiles of all segments.  Per tile the
+// block stages the acceleration of the cells its particles occupy in shared
+// memory, and a window of deposit accumulators around them.
+#pragma once
+#include <climits>
+
+#include "common.cuh"
+
+namespace bitpic {
+
+constexpr int kTileNodes = 512;   // staged nodes per tile (wider tiles use HBM/L2)
+constexpr int kDepMargin = 2;     // deposit window margin around the gather tile
+constexpr int kWarpSpan = 8;      // nodes a warp reduces in registers
+constexpr int kDeadCell = -(1 << 30);
+
+struct MoveArgs {
+    int32_t* cell;
+    void* off;
+    void* ux;
+    void* uy;
+    void* uz;
+    uint32_t* id;
+    const SegParams* seg;
+    const InstParams* inst;
+    int nseg;
+    const int64_t* tile_start;          // nseg+1 prefix of tiles
+    const int64_t* seg_nmove;           // slots of each segment moved this step
+    unsigned long long* seg_n;          // slots in use (appends for created particles)
+    unsigned long long* seg_live;       // live particles
+    const void* accel;                  // T, segment node arrays
+    unsigned long long* dep;            // fixed-point deposit, segment node arrays
+    unsigned long long* wall_count;     // [nseg][2]
+    double* wall_energy;                // [nseg][2]
+    unsigned long long* collisions;     // [ninst][kMaxProc]
+    Event* events;
+    unsigned long long* ev_count;       // [ninst]
+    unsigned* err;
+    const int64_t* step;
+};
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+    static constexpr bool wide = false;
+    static __device__ __forceinline__ uint64_t qright(float f)
+    {
+        return (uint64_t)__float2uint_rn(f * 16777216.0f);
+    }
+    static constexpr uint64_t S = 1ull << 24;
+    // (w + 1/2) 2^-32 rounded to float, kept below 1
+    static __device__ __forceinline__ float uni(uint32_t w)
+    {
+        return fminf(__fmaf_rn(__uint2float_rn(w), 0x1p-32f, 0x1p-33f), 0x1.fffffep-1f);
+    }
+    static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c)
+    {
+        sincospif(2.0f * u, s, c);
+    }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+};
+template <> struct Prec<double> {
+    static constexpr bool wide = true;
+    static __device__ __forceinline__ uint64_t qright(double f)
+    {
+        return __double2ull_rn(f * 281474976710656.0);
+    }
+    static constexpr uint64_t S = 1ull << 48;
+    static __device__ __forceinline__ double uni(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+    static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c)
+    {
+        const double th = 6.283185307179586476925286766559 * u;
+        *s = sin(th);
+        *c = cos(th);
+    }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+};
+
+__device__ __forceinline__ void ld4(const float* p, float v[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4])
+{
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4])
+{
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Unit vector uniform on the sphere, polar axis x (the wall normal).
+template <typename T>
+__device__ __forceinline__ void iso_dir(uint32_t w0, uint32_t w1, T n[3])
+{
+    const T ct = T(1) - T(2) * Prec<T>::uni(w0);
+    const T st = Prec<T>::sqrt_(T(1) - ct * ct);
+    T sp, cp;
+    Prec<T>::sincos2pi(Prec<T>::uni(w1), &sp, &cp);
+    n[0] = ct;
+    n[1] = st * cp;
+    n[2] = st * sp;
+}
+
+// Box-Muller (1958).
+template <typename T>
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z1)
+{
+    const T r = Prec<T>::sqrt_(T(-2) * Prec<T>::log_(Prec<T>::uni(wa)));
+    T s, c;
+    Prec<T>::sincos2pi(Prec<T>::uni(wb), &s, &c);
+    *z0 = r * c;
+    *z1 = r * s;
+}
+
+// Add v fixed-point charge units to node `node` of the current segment: into the
+// shared window when it covers the node, else straight into HBM.
+__device__ __forceinline__ void add_node(int node, unsigned long long v, bool use_smem,
+                                         unsigned long long* s_dep, int dlo, int dspan,
+                                         unsigned long long* gdep)
+{
+    if (use_smem) {
+        const int i = node - dlo;
+        if (i >= 0 && i < dspan) {
+            atomicAdd(s_dep + i, v);
+            return;
+        }
+    }
+    atomicAdd(gdep + node, v);
+}
+
+// Warp-level deposit of four particles per lane.  When the warp's particles touch at
+// most kWarpSpan nodes (the usual case once particles are sorted by cell) each node
+// total is formed by a register reduction across the warp and added by one lane.
+template <bool WIDE>
+__device__ __forceinline__ void warp_deposit(const int jd[4], const uint64_t ql[4],
+                                             const uint64_t qr[4], bool use_smem,
+                                             unsigned long long* s_dep, int dlo, int dspan,
+                                             unsigned long long* gdep)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int lmin = INT_MAX, lmax = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (jd[k] >= 0) {
+            lmin = min(lmin, jd[k]);
+            lmax = max(lmax, jd[k]);
+        }
+    const int wmin = __reduce_min_sync(FULL, lmin);
+    if (wmin == INT_MAX) return;
+    const int wmax = __reduce_max_sync(FULL, lmax);
+    const int nspan = wmax - wmin + 2;
+    if (nspan <= kWarpSpan) {
+        unsigned long long mine = 0;
+        for (int n = 0; n < nspan; ++n) {
+            const int node = wmin + n;
+            if (!WIDE) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    v += jd[k] == node ? (uint32_t)ql[k] : 0u;
+                    v += jd[k] + 1 == node ? (uint32_t)qr[k] : 0u;
+                }
+                // at most 128 particles x 2^24 < 2^32
+                const uint32_t t = __reduce_add_sync(FULL, v);
+                if (lane == n) mine = t;
+            } else {
+                // 48-bit charges: reduce the high and low 24-bit halves separately
+                uint32_t lo = 0, hi = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint64_t a = jd[k] == node ? ql[k] : 0ull;
+                    const uint64_t b = jd[k] + 1 == node ? qr[k] : 0ull;
+                    lo += (uint32_t)(a & 0xFFFFFFu) + (uint32_t)(b & 0xFFFFFFu);
+                    hi += (uint32_t)(a >> 24) + (uint32_t)(b >> 24);
+                }
+                const uint32_t tl = __reduce_add_sync(FULL, lo);
+                const uint32_t th = __reduce_add_sync(FULL, hi);
+                if (lane == n) mine = ((unsigned long long)th << 24) + tl;
+            }
+        }
+        if (lane < nspan && mine != 0) add_node(wmin + lane, mine, use_smem, s_dep, dlo, dspan, gdep);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (jd[k] >= 0) {
+                add_node(jd[k], ql[k], use_smem, s_dep, dlo, dspan, gdep);
+                add_node(jd[k] + 1, qr[k], use_smem, s_dep, dlo, dspan, gdep);
+            }
+    }
+}
+
+// Null-collision Monte Carlo for one particle (velocity u in cells/step, after the
+// move).  Returns true when u changed.  Ionization appends two particles.
+template <typename T>
+__device__ __noinline__ bool collide(const MoveArgs& a, const SegParams& P, int s,
+                                     uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
+                                     T& uz)
+{
+    const uint4 w = draw(id, step, kRngCollide, P.key0, P.key1);
+    if (!(w.x < P.cand)) return false;
+    int q = -1;
+    for (int k = 0; k < P.nproc; ++k)
+        if ((uint64_t)w.y < P.slot_end[k]) { q = k; break; }
+    if (q < 0) return false;
+    const T u2 = ux * ux + uy * uy + uz * uz;
+    if (!(u2 >= (T)P.thr_u2[q])) return false;  // below threshold: null event
+    const int kind = P.kind[q];
+    if (kind == PIC_PROC_ELASTIC) {
+        const uint4 r = draw(id, step, kRngScatter, P.key0, P.key1);
+        T n[3];
+        iso_dir<T>(r.x, r.y, n);
+        const T speed = Prec<T>::sqrt_(u2);
+        if (speed > T(0)) {
+            const T cchi = (ux * n[0] + uy * n[1] + uz * n[2]) / speed;
+            const T fac = Prec<T>::sqrt_(T(1) - T(2) * (T)P.mratio * (T(1) - cchi));
+            const T sp2 = speed * fac;
+            ux = sp2 * n[0];
+            uy = sp2 * n[1];
+            uz = sp2 * n[2];
+        }
+    } else if (kind == PIC_PROC_CX) {
+        const uint4 r = draw(id, step, kRngMaxwell, P.key0, P.key1);
+        T z0, z1, z2, z3;
+        box_muller<T>(r.x, r.y, &z0, &z1);
+        box_muller<T>(r.z, r.w, &z2, &z3);
+        const T vn = (T)P.vneutral;
+        ux = z0 * vn;
+        uy = z1 * vn;
+        uz = z2 * vn;
+    } else {  // PIC_PROC_IONIZE
+        const T us = Prec<T>::sqrt_(T(0.5) * (u2 - (T)P.thr_u2[q]));
+        T n1[3], n2[3];
+        const uint4 r1 = draw(id, step, kRngScatter, P.key0, P.key1);
+        iso_dir<T>(r1.x, r1.y, n1);
+        const uint4 r2 = draw(id, step, kRngIonizeE, P.key0, P.key1);
+        iso_dir<T>(r2.x, r2.y, n2);
+        const uint4 ri = draw(id, step, kRngIonizeI, P.key0, P.key1);
+        T z0, z1, z2, z3;
+        box_muller<T>(ri.x, ri.y, &z0, &z1);
+        box_muller<T>(ri.z, ri.w, &z2, &z3);
+        ux = us * n1[0];
+        uy = us * n1[1];
+        uz = us * n1[2];
+        // append the new electron (this segment) and the new ion (product segment)
+        const int si = P.product[q];
+        const SegParams& Pi = a.seg[si];
+        const unsigned long long ke = atomicAdd(a.seg_n + s, 1ull);
+        const unsigned long long ki = atomicAdd(a.seg_n + si, 1ull);
+        const InstParams& I = a.inst[P.inst];
+        const unsigned long long ev = atomicAdd(a.ev_count + P.inst, 1ull);
+        if (ke >= (unsigned long long)P.cap || ki >= (unsigned long long)Pi.cap ||
+            ev >= (unsigned long long)I.ev_cap) {
+            set_error(a.err, kErrCapacity);
+        } else {
+            const T vn = (T)P.vneutral;
+            const int64_t ge = P.base + (int64_t)ke, gi = Pi.base + (int64_t)ki;
+            T* off = static_cast<T*>(a.off);
+            T* vx = static_cast<T*>(a.ux);
+            T* vy = static_cast<T*>(a.uy);
+            T* vz = static_cast<T*>(a.uz);
+            a.cell[ge] = j; off[ge] = f;
+            vx[ge] = us * n2[0]; vy[ge] = us * n2[1]; vz[ge] = us * n2[2];
+            a.id[ge] = 0xFFFFFFFFu;
+            a.cell[gi] = j; off[gi] = f;
+            vx[gi] = z0 * vn; vy[gi] = z1 * vn; vz[gi] = z2 * vn;
+            a.id[gi] = 0xFFFFFFFFu;
+            Event e;
+            e.parent = id;
+            e.pad = 0;
+            e.slot_e = ge;
+            e.slot_i = gi;
+            a.events[I.ev_base + (int64_t)ev] = e;
+            atomicAdd(a.seg_live + s, 1ull);
+            atomicAdd(a.seg_live + si, 1ull);
+            // the children's charge joins this step's deposit
+            const uint64_t qr = Prec<T>::qright(f), ql = Prec<T>::S - qr;
+            atomicAdd(a.dep + P.node + j, (unsigned long long)ql);
+            atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
+            atomicAdd(a.dep + Pi.node + j, (unsigned long long)ql);
+            atomicAdd(a.dep + Pi.node + j + 1, (unsigned long long)qr);
+        }
+    }
+    atomicAdd(a.collisions + (int64_t)P.inst * kMaxProc + P.proc[q], 1ull);
+    return true;
+}
+
+template <typename T, int NT, bool MAG, bool MOVE>
+__global__ void __launch_bounds__(NT) k_move(const MoveArgs a)
+{
+    constexpr int NW = NT / 32;
+    __shared__ T s_acc[kTileNodes + 1];
+    __shared__ unsigned long long s_dep[kTileNodes + 2 + 2 * kDepMargin];
+    __shared__ int s_red[2][NW];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T* const offp = static_cast<T*>(a.off);
+    T* const uxp = static_cast<T*>(a.ux);
+    T* const uyp = static_cast<T*>(a.uy);
+    T* const uzp = static_cast<T*>(a.uz);
+    const T* const accp = static_cast<const T*>(a.accel);
+    const int64_t step = MOVE ? *a.step : 0;
+    const int64_t total = a.tile_start[a.nseg];
+
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int s = find_segment(a.tile_start, a.nseg, tile);
+        const SegParams& P = a.seg[s];
+        // per-segment scalars in registers (the particle stores below may alias P)
+        const int N = P.ncells;
+        const int bc = P.bc;
+        const int collides = P.collide;
+        const uint32_t cand = P.cand, key0 = P.key0, key1 = P.key1;
+        const int64_t node0 = P.node;
+        const int64_t quad = (tile - a.tile_start[s]) * NT + tid;
+        const int64_t nq = (a.seg_nmove[s] + 3) >> 2;
+        const bool act = quad < nq;
+        const int64_t slot = P.base + 4 * quad;
+        const bool need_id = MOVE && (collides || bc == PIC_BC_SOURCE);
+        T bt[3] = {T(0), T(0), T(0)}, bs[3] = {T(0), T(0), T(0)};
+        if (MAG) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                bt[d] = (T)P.t[d];
+                bs[d] = (T)P.s[d];
+            }
+        }
+
+        int c[4];
+        T f[4], ux[4], uy[4], uz[4];
+        uint32_t idv[4] = {0u, 0u, 0u, 0u};
+        if (act) {
+            const int4 cc = *reinterpret_cast<const int4*>(a.cell + slot);
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+            ld4(offp + slot, f);
+            if (MOVE) ld4(uxp + slot, ux);
+            if (MOVE && MAG) {
+                ld4(uyp + slot, uy);
+                ld4(uzp + slot, uz);
+            }
+            if (need_id) {
+                const uint4 ii = *reinterpret_cast<const uint4*>(a.id + slot);
+                idv[0] = ii.x; idv[1] = ii.y; idv[2] = ii.z; idv[3] = ii.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { c[k] = -1; f[k] = T(0); ux[k] = T(0); }
+        }
+        if (!(MOVE && MAG)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { uy[k] = T(0); uz[k] = T(0); }
+        }
+
+        // cells occupied by this tile's live particles
+        int lmin = INT_MAX, lmax = INT_MIN;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (c[k] >= 0) {
+                lmin = min(lmin, c[k]);
+                lmax = max(lmax, c[k]);
+            }
+        lmin = __reduce_min_sync(0xffffffffu, lmin);
+        lmax = __reduce_max_sync(0xffffffffu, lmax);
+        if (lane == 0) {
+            s_red[0][warp] = lmin;
+            s_red[1][warp] = lmax;
+        }
+        __syncthreads();
+        int bmin = INT_MAX, bmax = INT_MIN;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            bmin = min(bmin, s_red[0][w]);
+            bmax = max(bmax, s_red[1][w]);
+        }
+        const bool any = bmin <= bmax;
+        const int span = any ? bmax - bmin + 2 : 0;  // nodes bmin..bmax+1
+        const bool use_smem = any && span <= kTileNodes;
+        const int dlo = bmin - kDepMargin;
+        const int dspan = span + 2 * kDepMargin;
+        if (use_smem) {
+            if (MOVE)
+                for (int i = tid; i < span; i += NT) s_acc[i] = accp[node0 + bmin + i];
+            for (int i = tid; i < dspan; i += NT) s_dep[i] = 0ull;
+        }
+        __syncthreads();
+
+        int jd[4];
+        uint64_t ql[4], qr[4];
+        unsigned dirty_v = 0;  // bit k: uy/uz of particle k changed (non-MAG path)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            jd[k] = kDeadCell;
+            ql[k] = 0;
+            qr[k] = 0;
+            if (c[k] < 0) continue;
+            int j = c[k];
+            T fk = f[k];
+            if (MOVE) {
+                // 1. gather (Listing 7)
+                T a0, a1;
+                if (use_smem) {
+                    a0 = s_acc[j - bmin];
+                    a1 = s_acc[j + 1 - bmin];
+                } else {
+                    a0 = __ldg(accp + node0 + j);
+                    a1 = __ldg(accp + node0 + j + 1);
+                }
+                const T acc = a0 + fk * (a1 - a0);
+                // 2. push
+                if (!MAG) {
+                    ux[k] = ux[k] + acc;
+                } else {
+                    const T half = T(0.5) * acc;
+                    const T t0 = bt[0], t1 = bt[1], t2 = bt[2];
+                    const T s0 = bs[0], s1 = bs[1], s2 = bs[2];
+                    const T mx = ux[k] + half, my = uy[k], mz = uz[k];
+                    const T px = mx + (my * t2 - mz * t1);
+                    const T py = my + (mz * t0 - mx * t2);
+                    const T pz = mz + (mx * t1 - my * t0);
+                    const T qx = mx + (py * s2 - pz * s1);
+                    const T qy = my + (pz * s0 - px * s2);
+                    const T qz = mz + (px * s1 - py * s0);
+                    ux[k] = qx + half;
+                    uy[k] = qy;
+                    uz[k] = qz;
+                }
+                if (!isfinite(ux[k])) set_error(a.err, kErrNonFinite);
+                // 3. move (Listing 7: x += nstep*vx, x the in-cell offset)
+                const T xn = fk + ux[k];
+                const T fl = Prec<T>::floor_(xn);
+                fk = xn - fl;
+                j += (int)fl;
+                if (fk >= T(1)) {  // xn a tiny negative number: f rounded up to 1
+                    fk = T(0);
+                    j += 1;
+                }
+                // 4. walls
+                bool reinjected = false;
+                if (j < 0 || j >= N) {
+                    if (bc == PIC_BC_PERIODIC) {
+                        j %= N;
+                        if (j < 0) j += N;
+                    } else {
+                        if (!MAG) {
+                            uy[k] = uyp[slot + k];
+                            uz[k] = uzp[slot + k];
+                        }
+                        const int wall = j < 0 ? 0 : 1;
+                        const double u2 = (double)ux[k] * (double)ux[k] +
+                                          (double)uy[k] * (double)uy[k] +
+                                          (double)uz[k] * (double)uz[k];
+                        atomicAdd(a.wall_count + 2 * s + wall, 1ull);
+                        atomicAdd(a.wall_energy + 2 * s + wall, P.kefac * u2);
+                        if (bc == PIC_BC_SOURCE) {
+                            const uint4 r = draw(idv[k], step, kRngInjectA, key0, key1);
+                            const uint4 q2 = draw(idv[k], step, kRngInjectB, key0, key1);
+                            const T x = Prec<T>::uni(r.x) * (T)N;
+                            const T fx = Prec<T>::floor_(x);
+                            j = (int)fx;
+                            fk = x - fx;
+                            if (j >= N) { j = N - 1; fk = T(0); }
+                            T z0, z1, z2, z3;
+                            box_muller<T>(r.y, r.z, &z0, &z1);
+                            box_muller<T>(q2.x, q2.y, &z2, &z3);
+                            const T vi = (T)P.vinj;
+                            ux[k] = z0 * vi;
+                            uy[k] = z1 * vi;
+                            uz[k] = z2 * vi;
+                            reinjected = true;
+                            dirty_v |= 1u << k;
+                        } else {
+                            c[k] = -1;
+                            atomicAdd(a.seg_live + s, ~0ull);  // -1
+                            f[k] = fk;
+                            continue;
+                        }
+                    }
+                }
+                // 5. Monte Carlo collisions
+                if (!reinjected && collides) {
+                    if (!MAG) {
+                        // only the rare candidate needs the transverse velocity
+                        const uint4 w = draw(idv[k], step, kRngCollide, key0, key1);
+                        if (w.x < cand) {
+                            T vy = uyp[slot + k], vz = uzp[slot + k];
+                            if (collide<T>(a, P, s, idv[k], step, j, fk, ux[k], vy, vz)) {
+                                uyp[slot + k] = vy;
+                                uzp[slot + k] = vz;
+                            }
+                        }
+                    } else {
+                        collide<T>(a, P, s, idv[k], step, j, fk, ux[k], uy[k], uz[k]);
+                    }
+                }
+                c[k] = j;
+                f[k] = fk;
+            }
+            // 6. deposit
+            jd[k] = j;
+            qr[k] = Prec<T>::qright(fk);
+            ql[k] = Prec<T>::S - qr[k];
+        }
+
+        if (MOVE && act) {
+            *reinterpret_cast<int4*>(a.cell + slot) = make_int4(c[0], c[1], c[2], c[3]);
+            st4(offp + slot, f);
+            st4(uxp + slot, ux);
+            if (MAG) {
+                st4(uyp + slot, uy);
+                st4(uzp + slot, uz);
+            } else if (dirty_v) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (dirty_v & (1u << k)) {
+                        uyp[slot + k] = uy[k];
+                        uzp[slot + k] = uz[k];
+                    }
+            }
+        }
+
+        warp_deposit<Prec<T>::wide>(jd, ql, qr, use_smem, s_dep, dlo, dspan, a.dep + node0);
+        __syncthreads();
+        if (use_smem) {
+            for (int i = tid; i < dspan; i += NT) {
+                const unsigned long long v = s_dep[i];
+                const int node = dlo + i;
+                if (v != 0ull && node >= 0 && node <= N) atomicAdd(a.dep + node0 + node, v);
+            }
+        }
+    }
+}
+
+}  // namespace bitpic

@@ -1,0 +1,51 @@
+// mover_f32.cu -- instantiations of the fused mover for float particle state.
+#include "kernels.h"
+#include "mover.cuh"
+
+namespace bitpic {
+
+namespace {
+template <int NT>
+cudaError_t go(const MoveArgs& a, bool mag, bool move, int grid, cudaStream_t st)
+{
+    if (move) {
+        if (mag)
+            k_move<float, NT, true, true><<<grid, NT, 0, st>>>(a);
+        else
+            k_move<float, NT, false, true><<<grid, NT, 0, st>>>(a);
+    } else {
+        k_move<float, NT, false, false><<<grid, NT, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int NT>
+int occupancy(bool mag)
+{
+    int n = 0;
+    cudaError_t e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true>, NT, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true>, NT, 0);
+    return e == cudaSuccess ? n : 0;
+}
+}  // namespace
+
+cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, int nt, int grid,
+                            cudaStream_t st)
+{
+    switch (nt) {
+        case 128: return go<128>(a, mag, move, grid, st);
+        case 512: return go<512>(a, mag, move, grid, st);
+        default: return go<256>(a, mag, move, grid, st);
+    }
+}
+
+int move_blocks_per_sm_f32(bool mag, int nt)
+{
+    switch (nt) {
+        case 128: return occupancy<128>(mag);
+        case 512: return occupancy<512>(mag);
+        default: return occupancy<256>(mag);
+    }
+}
+
+}  // namespace bitpic

@@ -1,0 +1,190 @@
+// sort.cu -- periodic counting sort of every segment by cell.
+//
+// The paper keeps particles in per-cell lists ("natural sorting", Section 2, Fig.
+// "BIT1_sorting") so that particles near in space are near in memory.  Here the same
+// locality comes from a compact structure-of-arrays store that is re-sorted by cell
+// every few steps: histogram of cells -> exclusive scan per segment -> scatter into
+// the second copy of the store, which drops the empty slots left by absorbed
+// particles.  Results of the time step do not depend on particle order (deposits
+// are integer, random draws are keyed by particle id), so the order inside a cell
+// is free.
+#include "kernels.h"
+#include "mover.cuh"
+
+namespace bitpic {
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_hist(const SortArgs a)
+{
+    const int32_t* cell = a.cell[a.src];
+    const int64_t total = a.tile_start[a.nseg];
+    const int lane = threadIdx.x & 31;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int s = find_segment(a.tile_start, a.nseg, tile);
+        const SegParams& P = a.seg[s];
+        const int64_t quad = (tile - a.tile_start[s]) * NT + threadIdx.x;
+        const int64_t nq = a.seg_nmove[s] >> 2;
+        int c[4] = {-1, -1, -1, -1};
+        if (quad < nq) {
+            const int4 cc = *reinterpret_cast<const int4*>(cell + P.base + 4 * quad);
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int key = c[k] >= 0 ? c[k] : -1 - lane;  // empty slots never group
+            const unsigned grp = __match_any_sync(0xffffffffu, key);
+            if (c[k] >= 0 && lane == __ffs(grp) - 1)
+                atomicAdd(a.hist + P.node + c[k], (unsigned)__popc(grp));
+        }
+    }
+}
+
+// One block per segment: exclusive scan of the cell histogram in place.
+__global__ void __launch_bounds__(1024) k_cell_scan(const SortArgs a)
+{
+    __shared__ unsigned long long sh[33];
+    const SegParams& P = a.seg[blockIdx.x];
+    const int N = P.ncells;
+    const int C = (N + blockDim.x - 1) / blockDim.x;
+    const int j0 = min(N, (int)threadIdx.x * C), j1 = min(N, j0 + C);
+    unsigned long long local = 0;
+    for (int j = j0; j < j1; ++j) local += a.hist[P.node + j];
+    // block exclusive scan (64-bit)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long inc = local;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        const unsigned long long w = lane < nw ? sh[lane] : 0ull;
+        unsigned long long wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += t;
+        }
+        if (lane < nw) sh[lane] = wi - w;
+        if (lane == nw - 1) sh[32] = wi;
+    }
+    __syncthreads();
+    unsigned long long run = sh[warp] + inc - local;
+    for (int j = j0; j < j1; ++j) {
+        const unsigned h = a.hist[P.node + j];
+        a.hist[P.node + j] = (unsigned)run;
+        run += h;
+    }
+    if (threadIdx.x == 0) a.newn[blockIdx.x] = sh[32];
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
+{
+    const int src = a.src, dst = 1 - a.src;
+    const int32_t* cell = a.cell[src];
+    const T* off = static_cast<const T*>(a.off[src]);
+    const T* ux = static_cast<const T*>(a.ux[src]);
+    const T* uy = static_cast<const T*>(a.uy[src]);
+    const T* uz = static_cast<const T*>(a.uz[src]);
+    const uint32_t* id = a.id[src];
+    int32_t* dcell = a.cell[dst];
+    T* doff = static_cast<T*>(a.off[dst]);
+    T* dux = static_cast<T*>(a.ux[dst]);
+    T* duy = static_cast<T*>(a.uy[dst]);
+    T* duz = static_cast<T*>(a.uz[dst]);
+    uint32_t* did = a.id[dst];
+    const int64_t total = a.tile_start[a.nseg];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int s = find_segment(a.tile_start, a.nseg, tile);
+        const SegParams& P = a.seg[s];
+        const int64_t quad = (tile - a.tile_start[s]) * NT + threadIdx.x;
+        const int64_t nq = a.seg_nmove[s] >> 2;
+        const int64_t slot = P.base + 4 * quad;
+        int c[4] = {-1, -1, -1, -1};
+        if (quad < nq) {
+            const int4 cc = *reinterpret_cast<const int4*>(cell + slot);
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool live = c[k] >= 0;
+            const int key = live ? c[k] : -1 - lane;
+            const unsigned grp = __match_any_sync(0xffffffffu, key);
+            const int leader = __ffs(grp) - 1;
+            unsigned base = 0;
+            if (live && lane == leader) base = atomicAdd(a.hist + P.node + c[k], (unsigned)__popc(grp));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (live) {
+                const int64_t from = slot + k;
+                const int64_t to = P.base + (int64_t)base + __popc(grp & lt);
+                dcell[to] = c[k];
+                doff[to] = off[from];
+                dux[to] = ux[from];
+                duy[to] = uy[from];
+                duz[to] = uz[from];
+                did[to] = id[from];
+            }
+        }
+    }
+}
+
+// Per segment: mark the destination's slots past the new count empty, then adopt the
+// new count.  The destination copy may still hold particles up to its own earlier
+// high-water mark.
+__global__ void k_sort_finish(const SortArgs a)
+{
+    const int s = blockIdx.x;
+    const SegParams& P = a.seg[s];
+    const unsigned long long nnew = a.newn[s];
+    const unsigned long long old = a.seg_n[s];
+    const unsigned long long hw = min(max(old, a.hwm_alt[s]), (unsigned long long)P.cap);
+    int32_t* dcell = a.cell[1 - a.src];
+    for (unsigned long long i = nnew + threadIdx.x; i < hw; i += blockDim.x) dcell[P.base + (int64_t)i] = -1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.hwm_alt[s] = old;
+        a.seg_n[s] = nnew;
+        a.seg_live[s] = nnew;
+    }
+}
+
+template <int NT>
+cudaError_t run_sort(const SortArgs& a, int grid, cudaStream_t st)
+{
+    k_hist<NT><<<grid, NT, 0, st>>>(a);
+    k_cell_scan<<<a.nseg, 1024, 0, st>>>(a);
+    if (a.precision == PIC_FP64)
+        k_scatter<double, NT><<<grid, NT, 0, st>>>(a);
+    else
+        k_scatter<float, NT><<<grid, NT, 0, st>>>(a);
+    k_sort_finish<<<a.nseg, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sort(const SortArgs& a, int nt, int grid, cudaStream_t st)
+{
+    switch (nt) {
+        case 128: return run_sort<128>(a, grid, st);
+        case 512: return run_sort<512>(a, grid, st);
+        default: return run_sort<256>(a, grid, st);
+    }
+}
+
+}  // namespace bitpic

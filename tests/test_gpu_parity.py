@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances are the accuracy contract of the method's two forms:
+  * FP64 form: particles matched by id within 1e-12 relative over 100 steps, wall
+    absorption counts and collision event counts bit-exact;
+  * FP32 form (FP32 state, fixed-point deposit, FP64 field): 1e-5 relative over 10 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2404_10270_gb300 import capi
+from paper_2404_10270_gb300 import workloads as W
+from tests.gpu_common import by_id, ensure_built, particle_errors, requires_gpu, run_gpu, run_oracle
+from tests.helpers import read_kat
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def test_philox_known_answers_and_oracle():
+    from oracle.oracle import philox as ophilox
+    ensure_built()
+    for ctr, key, out in read_kat():
+        k = key[0] | (key[1] << 32)
+        np.testing.assert_array_equal(capi.philox(np.array([ctr]), k)[0], np.array(out, np.uint32))
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(3000, 4), dtype=np.uint64).astype(np.uint32)
+    key = 0x1234_5678_9ABC_DEF0
+    got = capi.philox(ctr, key)
+    kw = np.array([key & 0xFFFFFFFF, key >> 32], np.uint32)
+    for i in range(0, 3000, 97):
+        np.testing.assert_array_equal(got[i], ophilox(ctr[i], kw))
+
+
+@pytest.mark.parametrize("precision,steps,tol", [(capi.FP64, 100, 1e-12), (capi.FP32, 10, 1e-5)])
+def test_bounded_small_parity(precision, steps, tol):
+    phys = W.bounded_small()
+    loads = W.initial_load(phys, seed=1)
+    g, gm = run_gpu(phys, loads, steps, precision, sort_interval=20)
+    o, om = run_oracle(phys, loads, steps)
+    for s, (ex, ev) in enumerate(particle_errors(phys, g, o)):
+        assert ex < tol and ev < tol, (s, ex, ev)
+    assert gm["step"] == om["step"] == steps
+    if precision == capi.FP64:
+        np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
+        np.testing.assert_array_equal(gm["collisions"], om["collisions"])
+        np.testing.assert_array_equal(gm["live"], om["live"])
+        assert om["collisions"].sum() > 0 and om["wall_count"].sum() > 0
+        np.testing.assert_allclose(gm["wall_energy"], om["wall_energy"], rtol=1e-12)
+        np.testing.assert_allclose(gm["kinetic"], om["kinetic"], rtol=1e-12)
+        scale = np.abs(om["E"]).max()
+        np.testing.assert_allclose(gm["E"], om["E"], rtol=0, atol=1e-11 * scale)
+        np.testing.assert_allclose(gm["phi"], om["phi"], rtol=0, atol=1e-11 * np.abs(om["phi"]).max())
+        np.testing.assert_allclose(gm["density"], om["density"], rtol=1e-13, atol=1e-13)
+    else:
+        # counts can differ only by particles within rounding of a wall
+        assert np.abs(gm["wall_count"] - om["wall_count"]).sum() <= 2
+        np.testing.assert_allclose(gm["kinetic"], om["kinetic"], rtol=1e-5)
+        scale = np.abs(om["E"]).max()
+        np.testing.assert_allclose(gm["E"], om["E"], rtol=0, atol=1e-5 * scale)
+        np.testing.assert_allclose(gm["density"], om["density"], rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_initial_field_matches_oracle(precision):
+    phys = W.bounded_small(ncells=300, ppc=37, seed=3)  # ragged tiles
+    loads = W.initial_load(phys, seed=3)
+    g, gm = run_gpu(phys, loads, 0, precision)
+    o, om = run_oracle(phys, loads, 0)
+    tol = 1e-12 if precision == capi.FP64 else 1e-6
+    np.testing.assert_allclose(gm["E"], om["E"], rtol=0, atol=tol * np.abs(om["E"]).max())
+    np.testing.assert_allclose(gm["density"], om["density"], rtol=0, atol=tol)
+    np.testing.assert_allclose(gm["phi"], om["phi"], rtol=0, atol=tol * np.abs(om["phi"]).max())
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_deposit_is_exact_fixed_point(precision):
+    """Every live particle adds exactly one unit S split over its two nodes."""
+    ensure_built()
+    phys = W.bounded_small(ncells=64, ppc=33, seed=5)
+    loads = W.initial_load(phys, seed=5)
+    runs = []
+    for rep in range(2):
+        sim = capi.Sim(phys, precision=precision, sort_interval=7)
+        sim.load_all(loads)
+        sim.step(15)
+        raw, unit = sim.charge_raw(0)
+        m = sim.moments(0)
+        for s in range(2):
+            assert int(raw[s].sum()) == int(m["live"][s]) * unit
+        runs.append(raw.copy())
+        sim.close()
+    np.testing.assert_array_equal(runs[0], runs[1])  # run-to-run deterministic
+
+
+def test_batch_instance_equals_instance_alone():
+    ensure_built()
+    physs = [W.bounded_small(ncells=n, ppc=p, seed=sd) for n, p, sd in
+             ((64, 20, 11), (100, 13, 12), (37, 50, 13))]
+    loads = [W.initial_load(p, seed=i + 20) for i, p in enumerate(physs)]
+    sim = capi.Sim(physs, precision=capi.FP64, sort_interval=5)
+    for i, ld in enumerate(loads):
+        sim.load_all(ld, inst=i)
+    sim.step(30)
+    batch = [[by_id(sim.particles(i, s)) for s in range(2)] for i in range(3)]
+    bm = [sim.moments(i) for i in range(3)]
+    sim.close()
+    for i, (p, ld) in enumerate(zip(physs, loads)):
+        g, m = run_gpu(p, ld, 30, capi.FP64, sort_interval=5)
+        for s in range(2):
+            a = by_id(g[s])
+            for k in a:
+                np.testing.assert_array_equal(a[k], batch[i][s][k])
+        np.testing.assert_array_equal(m["collisions"], bm[i]["collisions"])
+        np.testing.assert_array_equal(m["E"], bm[i]["E"])
+
+
+def test_results_do_not_depend_on_launch_shape_or_sort_interval():
+    phys = W.bounded_small(ncells=96, ppc=40, seed=7)
+    loads = W.initial_load(phys, seed=7)
+    ref = None
+    for block, sort in ((256, 0), (128, 5), (512, 20), (256, 1)):
+        g, m = run_gpu(phys, loads, 25, capi.FP64, sort_interval=sort, block=block)
+        cur = ([by_id(x) for x in g], m)
+        if ref is None:
+            ref = cur
+            continue
+        for a, b in zip(ref[0], cur[0]):
+            for k in a:
+                np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(ref[1]["E"], cur[1]["E"])
+        np.testing.assert_array_equal(ref[1]["collisions"], cur[1]["collisions"])
+
+
+def test_load_order_does_not_matter():
+    phys = W.bounded_small(ncells=32, ppc=25, seed=9)
+    loads = W.initial_load(phys, seed=9)
+    rng = np.random.default_rng(9)
+    perm = [ld.take(rng.permutation(len(ld))) for ld in loads]
+    a, am = run_gpu(phys, loads, 20, capi.FP64)
+    b, bm = run_gpu(phys, perm, 20, capi.FP64)
+    for x, y in zip(a, b):
+        x, y = by_id(x), by_id(y)
+        for k in x:
+            np.testing.assert_array_equal(x[k], y[k])
+    np.testing.assert_array_equal(am["E"], bm["E"])
+
+
+def test_magnetized_source_with_ionization_fp64_parity():
+    """Boris push, volume re-injection, elastic + ionization + charge exchange."""
+    phys = W.magnetized_source(ncells=64, ppc=40, seed=2, nu=0.2, capacity_factor=3.0)
+    loads = W.initial_load(phys, seed=2)
+    steps = 100
+    g, gm = run_gpu(phys, loads, steps, capi.FP64, sort_interval=10)
+    o, om = run_oracle(phys, loads, steps)
+    assert om["collisions"][1] > 0  # some ionization happened
+    np.testing.assert_array_equal(gm["collisions"], om["collisions"])
+    np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
+    np.testing.assert_array_equal(gm["live"], om["live"])
+    for s, (ex, ev) in enumerate(particle_errors(phys, g, o)):
+        assert ex < 1e-12 and ev < 1e-12, (s, ex, ev)
+
+
+def test_magnetized_source_fp32_parity():
+    phys = W.magnetized_source(ncells=64, ppc=40, seed=4, nu=0.2, capacity_factor=3.0)
+    loads = W.initial_load(phys, seed=4)
+    g, gm = run_gpu(phys, loads, 10, capi.FP32, sort_interval=5)
+    o, om = run_oracle(phys, loads, 10)
+    np.testing.assert_array_equal(gm["live"], om["live"])
+    for s, (ex, ev) in enumerate(particle_errors(phys, g, o)):
+        assert ex < 1e-5 and ev < 1e-5, (s, ex, ev)
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_edge_cases_empty_single_cell_and_ragged(precision):
+    # a single cell; an empty species; counts that are not multiples of 4 or a tile
+    sp = [W.Species("e", -1.0, 1.0, 0.1, 1.0, 3), W.Species("i", 1.0, 100.0, 0.1, 1.0, 0)]
+    phys = W.Physics(ncells=1, dx=0.5, dt=0.05, species=sp,
+                     processes=[W.Process(W.PROC_ELASTIC, 0, 0.5)], m_neutral=100.0, seed=3)
+    loads = W.initial_load(phys, seed=3)
+    g, gm = run_gpu(phys, loads, 30, precision)
+    o, om = run_oracle(phys, loads, 30)
+    np.testing.assert_array_equal(gm["live"], om["live"])
+    np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
+    tol = 1e-12 if precision == capi.FP64 else 1e-5
+    for ex, ev in particle_errors(phys, g, o):
+        assert ex < tol and ev < tol
+    # ragged: 1, 5, 1027 particles
+    for n in (1, 5, 1027):
+        phys = W.bounded_small(ncells=50, ppc=max(1, -(-n // 50)), seed=n)
+        ld = W.initial_load(phys, seed=n)
+        ld = [x.take(np.arange(min(n, len(x)))) for x in ld]
+        g, gm = run_gpu(phys, ld, 12, precision)
+        o, om = run_oracle(phys, ld, 12)
+        np.testing.assert_array_equal(gm["live"], om["live"])
+        for ex, ev in particle_errors(phys, g, o):
+            assert ex < tol and ev < tol
+
+
+def test_invalid_load_is_reported_then_state_is_sticky():
+    ensure_built()
+    phys = W.bounded_small(ncells=16, ppc=4)
+    loads = W.initial_load(phys)
+    loads[0].cell[3] = 99  # outside [0, 16)
+    sim = capi.Sim(phys, precision=capi.FP32)
+    sim.load_all(loads)
+    with pytest.raises(capi.PicError) as e:
+        sim.sync()
+    assert e.value.code == -1
+    with pytest.raises(capi.PicError) as e:
+        sim.step(1)
+    assert e.value.code == -7
+    sim.close()
+
+
+def test_capacity_overflow_is_reported():
+    ensure_built()
+    phys = W.magnetized_source(ncells=16, ppc=20, nu=5.0, capacity_factor=1.0)
+    loads = W.initial_load(phys)
+    sim = capi.Sim(phys, precision=capi.FP32)
+    sim.load_all(loads)
+    sim.step(40)
+    with pytest.raises(capi.PicError) as e:
+        sim.sync()
+    assert e.value.code == -4
+    sim.close()
