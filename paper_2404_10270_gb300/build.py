@@ -45,7 +45,7 @@ def _deps():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.environ.get("BITPIC_NVCC_EXTRA"):
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in _deps())
@@ -56,6 +56,7 @@ def _compile(unit: str, extra, verbose: bool) -> str:
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"),
            "-c", os.path.join(SRC, unit), "-o", obj, *extra]
+    cmd += os.environ.get("BITPIC_NVCC_EXTRA", "").split()
     if verbose:
         cmd.append("-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

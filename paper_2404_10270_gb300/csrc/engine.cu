@@ -329,7 +329,7 @@ int launch_tiles_h(pic_handle* h)
 {
     Span sp(h, 3);
     h->kernels += 1;
-    CUDA_TRY(h, launch_tiles(h->segd, h->seg_n, h->seg_nmove, h->tile_start, h->nseg, h->nt, h->stream));
+    CUDA_TRY(h, launch_tiles(h->segd, h->seg_n, h->seg_nmove, h->tile_start, h->nseg, 32, h->stream));
     return PIC_OK;
 }
 

@@ -10,14 +10,15 @@
 //            elastic / charge-exchange / ionization kinematics
 //   deposit  cloud-in-cell in fixed point: node j gets S - Q, node j+1 gets
 //            Q = rint(f S), so every particle adds exactly S (S = 2^24 FP32,
-//            2^48 FP64); warp-reduced per node, then shared-memory tile, then one
-//            64-bit atomic per node and block into HBM.
+//            2^48 FP64); reduced per node across the warp in registers, then one
+//            64-bit reduction per node and warp into HBM.
 //
-// Work decomposition: a tile is blockDim.x quads of four consecutive particles of
-// one segment (instance, species); each thread loads its quad with 128-bit
-// accesses.  A persistent grid walks the tiles of all segments.  Per tile the
-// block stages the acceleration of the cells its particles occupy in shared
-// memory, and a window of deposit accumulators around them.
+// Work decomposition: a tile is 32 quads of four consecutive particles of one
+// segment (instance, species), owned by one warp; each lane loads its quad with
+// 128-bit accesses.  Warps walk the tiles of all segments independently.  The
+// acceleration of the nodes a warp touches is staged in registers and exchanged by
+// warp shuffles; there is no block-level barrier anywhere in the step, so an SM keeps
+// the loads of many tiles in flight (the kernel is bound by HBM, not by latency).
 #pragma once
 #include <climits>
 
@@ -25,9 +26,11 @@
 
 namespace bitpic {
 
-constexpr int kTileNodes = 512;   // staged nodes per tile (wider tiles use HBM/L2)
-constexpr int kDepMargin = 2;     // deposit window margin around the gather tile
 constexpr int kWarpSpan = 8;      // nodes a warp reduces in registers
+#ifndef BITPIC_MOVE_MIN_WARPS
+#define BITPIC_MOVE_MIN_WARPS 24
+#endif
+constexpr int kMoveMinWarps = BITPIC_MOVE_MIN_WARPS;  // resident warps per SM the mover is built for
 constexpr int kDeadCell = -(1 << 30);
 
 struct MoveArgs {
@@ -57,7 +60,7 @@ struct MoveArgs {
 
 template <typename T> struct Prec;
 template <> struct Prec<float> {
-    static constexpr bool wide = false;
+    using Q = uint32_t;  // fixed-point charge of one particle (< 2^25)
     static __device__ __forceinline__ uint64_t qright(float f)
     {
         return (uint64_t)__float2uint_rn(f * 16777216.0f);
@@ -77,7 +80,7 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
 };
 template <> struct Prec<double> {
-    static constexpr bool wide = true;
+    using Q = uint64_t;  // fixed-point charge of one particle (< 2^49)
     static __device__ __forceinline__ uint64_t qright(double f)
     {
         return __double2ull_rn(f * 281474976710656.0);
@@ -140,30 +143,13 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z
     *z1 = r * s;
 }
 
-// Add v fixed-point charge units to node `node` of the current segment: into the
-// shared window when it covers the node, else straight into HBM.
-__device__ __forceinline__ void add_node(int node, unsigned long long v, bool use_smem,
-                                         unsigned long long* s_dep, int dlo, int dspan,
-                                         unsigned long long* gdep)
-{
-    if (use_smem) {
-        const int i = node - dlo;
-        if (i >= 0 && i < dspan) {
-            atomicAdd(s_dep + i, v);
-            return;
-        }
-    }
-    atomicAdd(gdep + node, v);
-}
-
-// Warp-level deposit of four particles per lane.  When the warp's particles touch at
-// most kWarpSpan nodes (the usual case once particles are sorted by cell) each node
-// total is formed by a register reduction across the warp and added by one lane.
-template <bool WIDE>
-__device__ __forceinline__ void warp_deposit(const int jd[4], const uint64_t ql[4],
-                                             const uint64_t qr[4], bool use_smem,
-                                             unsigned long long* s_dep, int dlo, int dspan,
-                                             unsigned long long* gdep)
+// Warp-level deposit of four particles per lane.  The warp's particles usually touch
+// a handful of nodes (particles are sorted by cell); each node total is then formed
+// by a register reduction across the warp and added to HBM by one lane with a single
+// 64-bit reduction (no return value, so the warp does not wait for it).
+template <typename Q>
+__device__ __forceinline__ void warp_deposit(const int jd[4], const Q ql[4], const Q qr[4],
+                                             unsigned long long* __restrict__ gdep)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -182,7 +168,7 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const uint64_t ql[
         unsigned long long mine = 0;
         for (int n = 0; n < nspan; ++n) {
             const int node = wmin + n;
-            if (!WIDE) {
+            if (sizeof(Q) == 4) {
                 uint32_t v = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -197,8 +183,8 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const uint64_t ql[
                 uint32_t lo = 0, hi = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const uint64_t a = jd[k] == node ? ql[k] : 0ull;
-                    const uint64_t b = jd[k] + 1 == node ? qr[k] : 0ull;
+                    const uint64_t a = jd[k] == node ? (uint64_t)ql[k] : 0ull;
+                    const uint64_t b = jd[k] + 1 == node ? (uint64_t)qr[k] : 0ull;
                     lo += (uint32_t)(a & 0xFFFFFFu) + (uint32_t)(b & 0xFFFFFFu);
                     hi += (uint32_t)(a >> 24) + (uint32_t)(b >> 24);
                 }
@@ -207,13 +193,13 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const uint64_t ql[
                 if (lane == n) mine = ((unsigned long long)th << 24) + tl;
             }
         }
-        if (lane < nspan && mine != 0) add_node(wmin + lane, mine, use_smem, s_dep, dlo, dspan, gdep);
+        if (lane < nspan && mine != 0) atomicAdd(gdep + wmin + lane, mine);
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (jd[k] >= 0) {
-                add_node(jd[k], ql[k], use_smem, s_dep, dlo, dspan, gdep);
-                add_node(jd[k] + 1, qr[k], use_smem, s_dep, dlo, dspan, gdep);
+                atomicAdd(gdep + jd[k], (unsigned long long)ql[k]);
+                atomicAdd(gdep + jd[k] + 1, (unsigned long long)qr[k]);
             }
     }
 }
@@ -313,15 +299,54 @@ __device__ __noinline__ bool collide(const MoveArgs& a, const SegParams& P, int 
     return true;
 }
 
-template <typename T, int NT, bool MAG, bool MOVE>
-__global__ void __launch_bounds__(NT) k_move(const MoveArgs a)
+// Wall phase for a particle that left [0, N) (rare): counts and energy of the
+// absorbed particle, then either absorption (returns 2), or volume re-injection with a
+// new position and Maxwellian velocity (returns 1).  Periodic walls are handled inline.
+template <typename T>
+__device__ __noinline__ int wall_event(const MoveArgs& a, const SegParams& P, int s, uint32_t id,
+                                       int64_t step, int& j, T& f, T& ux, T& uy, T& uz)
 {
-    constexpr int NW = NT / 32;
-    __shared__ T s_acc[kTileNodes + 1];
-    __shared__ unsigned long long s_dep[kTileNodes + 2 + 2 * kDepMargin];
-    __shared__ int s_red[2][NW];
+    const int wall = j < 0 ? 0 : 1;
+    const double u2 = (double)ux * (double)ux + (double)uy * (double)uy + (double)uz * (double)uz;
+    atomicAdd(a.wall_count + 2 * s + wall, 1ull);
+    atomicAdd(a.wall_energy + 2 * s + wall, P.kefac * u2);
+    if (P.bc != PIC_BC_SOURCE) {
+        atomicAdd(a.seg_live + s, ~0ull);  // -1
+        return 2;
+    }
+    const int N = P.ncells;
+    const uint4 r = draw(id, step, kRngInjectA, P.key0, P.key1);
+    const uint4 q2 = draw(id, step, kRngInjectB, P.key0, P.key1);
+    const T x = Prec<T>::uni(r.x) * (T)N;
+    const T fx = Prec<T>::floor_(x);
+    j = (int)fx;
+    f = x - fx;
+    if (j >= N) {
+        j = N - 1;
+        f = T(0);
+    }
+    T z0, z1, z2, z3;
+    box_muller<T>(r.y, r.z, &z0, &z1);
+    box_muller<T>(q2.x, q2.y, &z2, &z3);
+    const T vi = (T)P.vinj;
+    ux = z0 * vi;
+    uy = z1 * vi;
+    uz = z2 * vi;
+    return 1;
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// The fused time step.  Work unit: a warp tile of 32 quads (128 consecutive particles
+// of one segment); each lane owns one quad and moves it with 128-bit accesses.  Warps
+// walk the tiles of all segments independently (no block-level barrier), so every SM
+// keeps many tiles' loads in flight.  The acceleration of the nodes a warp's
+// particles occupy is staged in registers: one coalesced load of the warp's node span,
+// then each particle picks its two nodes by warp shuffle.
+template <typename T, int NT, bool MAG, bool MOVE>
+__global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32)) k_move(const MoveArgs a)
+{
+    using Q = typename Prec<T>::Q;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     T* const offp = static_cast<T*>(a.off);
     T* const uxp = static_cast<T*>(a.ux);
     T* const uyp = static_cast<T*>(a.uy);
@@ -329,35 +354,29 @@ __global__ void __launch_bounds__(NT) k_move(const MoveArgs a)
     const T* const accp = static_cast<const T*>(a.accel);
     const int64_t step = MOVE ? *a.step : 0;
     const int64_t total = a.tile_start[a.nseg];
+    const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
 
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
+         tile += wstride) {
         const int s = find_segment(a.tile_start, a.nseg, tile);
         const SegParams& P = a.seg[s];
-        // per-segment scalars in registers (the particle stores below may alias P)
         const int N = P.ncells;
         const int bc = P.bc;
         const int collides = P.collide;
         const uint32_t cand = P.cand, key0 = P.key0, key1 = P.key1;
         const int64_t node0 = P.node;
-        const int64_t quad = (tile - a.tile_start[s]) * NT + tid;
-        const int64_t nq = (a.seg_nmove[s] + 3) >> 2;
+        const int64_t quad = (tile - a.tile_start[s]) * 32 + lane;
+        const int64_t nq = a.seg_nmove[s] >> 2;
         const bool act = quad < nq;
         const int64_t slot = P.base + 4 * quad;
         const bool need_id = MOVE && (collides || bc == PIC_BC_SOURCE);
-        T bt[3] = {T(0), T(0), T(0)}, bs[3] = {T(0), T(0), T(0)};
-        if (MAG) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                bt[d] = (T)P.t[d];
-                bs[d] = (T)P.s[d];
-            }
-        }
 
-        int c[4];
-        T f[4], ux[4], uy[4], uz[4];
+        int c[4] = {-1, -1, -1, -1};
+        T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
+        T uy[4] = {T(0), T(0), T(0), T(0)}, uz[4] = {T(0), T(0), T(0), T(0)};
         uint32_t idv[4] = {0u, 0u, 0u, 0u};
         if (act) {
-            const int4 cc = *reinterpret_cast<const int4*>(a.cell + slot);
+            const int4 cc = __ldcs(reinterpret_cast<const int4*>(a.cell + slot));
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
             ld4(offp + slot, f);
             if (MOVE) ld4(uxp + slot, ux);
@@ -366,80 +385,57 @@ __global__ void __launch_bounds__(NT) k_move(const MoveArgs a)
                 ld4(uzp + slot, uz);
             }
             if (need_id) {
-                const uint4 ii = *reinterpret_cast<const uint4*>(a.id + slot);
+                const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(a.id + slot));
                 idv[0] = ii.x; idv[1] = ii.y; idv[2] = ii.z; idv[3] = ii.w;
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { c[k] = -1; f[k] = T(0); ux[k] = T(0); }
         }
-        if (!(MOVE && MAG)) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { uy[k] = T(0); uz[k] = T(0); }
-        }
-
-        // cells occupied by this tile's live particles
-        int lmin = INT_MAX, lmax = INT_MIN;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (c[k] >= 0) {
-                lmin = min(lmin, c[k]);
-                lmax = max(lmax, c[k]);
-            }
-        lmin = __reduce_min_sync(0xffffffffu, lmin);
-        lmax = __reduce_max_sync(0xffffffffu, lmax);
-        if (lane == 0) {
-            s_red[0][warp] = lmin;
-            s_red[1][warp] = lmax;
-        }
-        __syncthreads();
-        int bmin = INT_MAX, bmax = INT_MIN;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            bmin = min(bmin, s_red[0][w]);
-            bmax = max(bmax, s_red[1][w]);
-        }
-        const bool any = bmin <= bmax;
-        const int span = any ? bmax - bmin + 2 : 0;  // nodes bmin..bmax+1
-        const bool use_smem = any && span <= kTileNodes;
-        const int dlo = bmin - kDepMargin;
-        const int dspan = span + 2 * kDepMargin;
-        if (use_smem) {
-            if (MOVE)
-                for (int i = tid; i < span; i += NT) s_acc[i] = accp[node0 + bmin + i];
-            for (int i = tid; i < dspan; i += NT) s_dep[i] = 0ull;
-        }
-        __syncthreads();
 
         int jd[4];
-        uint64_t ql[4], qr[4];
-        unsigned dirty_v = 0;  // bit k: uy/uz of particle k changed (non-MAG path)
+        Q ql[4], qr[4];
+        if (MOVE) {
+            // stage the acceleration of the warp's node span in registers
+            int lmin = INT_MAX, lmax = INT_MIN;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            jd[k] = kDeadCell;
-            ql[k] = 0;
-            qr[k] = 0;
-            if (c[k] < 0) continue;
-            int j = c[k];
-            T fk = f[k];
-            if (MOVE) {
+            for (int k = 0; k < 4; ++k)
+                if (c[k] >= 0) {
+                    lmin = min(lmin, c[k]);
+                    lmax = max(lmax, c[k]);
+                }
+            const int wmin = __reduce_min_sync(FULL, lmin);
+            const int wmax = __reduce_max_sync(FULL, lmax);
+            const bool staged = wmin != INT_MAX && wmax - wmin + 2 <= 32;
+            T av = T(0);
+            if (staged && lane <= wmax - wmin + 1) av = __ldg(accp + node0 + wmin + lane);
+            unsigned dirty = 0;  // bit k: uy/uz of particle k changed (non-MAG path)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
                 // 1. gather (Listing 7)
                 T a0, a1;
-                if (use_smem) {
-                    a0 = s_acc[j - bmin];
-                    a1 = s_acc[j + 1 - bmin];
+                if (staged) {
+                    const int i = c[k] >= 0 ? c[k] - wmin : 0;
+                    a0 = __shfl_sync(FULL, av, i);
+                    a1 = __shfl_sync(FULL, av, i + 1);
+                } else if (c[k] >= 0) {
+                    a0 = __ldg(accp + node0 + c[k]);
+                    a1 = __ldg(accp + node0 + c[k] + 1);
                 } else {
-                    a0 = __ldg(accp + node0 + j);
-                    a1 = __ldg(accp + node0 + j + 1);
+                    a0 = T(0);
+                    a1 = T(0);
                 }
+                jd[k] = kDeadCell;
+                ql[k] = 0;
+                qr[k] = 0;
+                if (c[k] < 0) continue;
+                int j = c[k];
+                T fk = f[k];
                 const T acc = a0 + fk * (a1 - a0);
                 // 2. push
                 if (!MAG) {
                     ux[k] = ux[k] + acc;
                 } else {
                     const T half = T(0.5) * acc;
-                    const T t0 = bt[0], t1 = bt[1], t2 = bt[2];
-                    const T s0 = bs[0], s1 = bs[1], s2 = bs[2];
+                    const T t0 = (T)P.t[0], t1 = (T)P.t[1], t2 = (T)P.t[2];
+                    const T s0 = (T)P.s[0], s1 = (T)P.s[1], s2 = (T)P.s[2];
                     const T mx = ux[k] + half, my = uy[k], mz = uz[k];
                     const T px = mx + (my * t2 - mz * t1);
                     const T py = my + (mz * t0 - mx * t2);
@@ -468,92 +464,66 @@ __global__ void __launch_bounds__(NT) k_move(const MoveArgs a)
                         j %= N;
                         if (j < 0) j += N;
                     } else {
-                        if (!MAG) {
-                            uy[k] = uyp[slot + k];
-                            uz[k] = uzp[slot + k];
-                        }
-                        const int wall = j < 0 ? 0 : 1;
-                        const double u2 = (double)ux[k] * (double)ux[k] +
-                                          (double)uy[k] * (double)uy[k] +
-                                          (double)uz[k] * (double)uz[k];
-                        atomicAdd(a.wall_count + 2 * s + wall, 1ull);
-                        atomicAdd(a.wall_energy + 2 * s + wall, P.kefac * u2);
-                        if (bc == PIC_BC_SOURCE) {
-                            const uint4 r = draw(idv[k], step, kRngInjectA, key0, key1);
-                            const uint4 q2 = draw(idv[k], step, kRngInjectB, key0, key1);
-                            const T x = Prec<T>::uni(r.x) * (T)N;
-                            const T fx = Prec<T>::floor_(x);
-                            j = (int)fx;
-                            fk = x - fx;
-                            if (j >= N) { j = N - 1; fk = T(0); }
-                            T z0, z1, z2, z3;
-                            box_muller<T>(r.y, r.z, &z0, &z1);
-                            box_muller<T>(q2.x, q2.y, &z2, &z3);
-                            const T vi = (T)P.vinj;
-                            ux[k] = z0 * vi;
-                            uy[k] = z1 * vi;
-                            uz[k] = z2 * vi;
-                            reinjected = true;
-                            dirty_v |= 1u << k;
-                        } else {
+                        T vy = MAG ? uy[k] : uyp[slot + k];
+                        T vz = MAG ? uz[k] : uzp[slot + k];
+                        const int r = wall_event<T>(a, P, s, idv[k], step, j, fk, ux[k], vy, vz);
+                        if (r == 2) {
                             c[k] = -1;
-                            atomicAdd(a.seg_live + s, ~0ull);  // -1
                             f[k] = fk;
                             continue;
                         }
+                        uy[k] = vy;
+                        uz[k] = vz;
+                        dirty |= 1u << k;
+                        reinjected = true;
                     }
                 }
-                // 5. Monte Carlo collisions
+                // 5. Monte Carlo collisions (Philox word 0 against the candidate threshold;
+                // the rare candidate continues out of line)
                 if (!reinjected && collides) {
-                    if (!MAG) {
-                        // only the rare candidate needs the transverse velocity
-                        const uint4 w = draw(idv[k], step, kRngCollide, key0, key1);
-                        if (w.x < cand) {
-                            T vy = uyp[slot + k], vz = uzp[slot + k];
-                            if (collide<T>(a, P, s, idv[k], step, j, fk, ux[k], vy, vz)) {
-                                uyp[slot + k] = vy;
-                                uzp[slot + k] = vz;
-                            }
+                    const uint4 w = draw(idv[k], step, kRngCollide, key0, key1);
+                    if (w.x < cand) {
+                        T vy = MAG ? uy[k] : uyp[slot + k];
+                        T vz = MAG ? uz[k] : uzp[slot + k];
+                        if (collide<T>(a, P, s, idv[k], step, j, fk, ux[k], vy, vz)) {
+                            uy[k] = vy;
+                            uz[k] = vz;
+                            dirty |= 1u << k;
                         }
-                    } else {
-                        collide<T>(a, P, s, idv[k], step, j, fk, ux[k], uy[k], uz[k]);
                     }
                 }
                 c[k] = j;
                 f[k] = fk;
+                // 6. deposit of the new position
+                jd[k] = j;
+                qr[k] = (Q)Prec<T>::qright(fk);
+                ql[k] = (Q)Prec<T>::S - qr[k];
             }
-            // 6. deposit
-            jd[k] = j;
-            qr[k] = Prec<T>::qright(fk);
-            ql[k] = Prec<T>::S - qr[k];
-        }
-
-        if (MOVE && act) {
-            *reinterpret_cast<int4*>(a.cell + slot) = make_int4(c[0], c[1], c[2], c[3]);
-            st4(offp + slot, f);
-            st4(uxp + slot, ux);
-            if (MAG) {
-                st4(uyp + slot, uy);
-                st4(uzp + slot, uz);
-            } else if (dirty_v) {
+            if (act) {
+                __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
+                st4(offp + slot, f);
+                st4(uxp + slot, ux);
+                if (MAG) {
+                    st4(uyp + slot, uy);
+                    st4(uzp + slot, uz);
+                } else if (dirty) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (dirty_v & (1u << k)) {
-                        uyp[slot + k] = uy[k];
-                        uzp[slot + k] = uz[k];
-                    }
+                    for (int k = 0; k < 4; ++k)
+                        if (dirty & (1u << k)) {
+                            uyp[slot + k] = uy[k];
+                            uzp[slot + k] = uz[k];
+                        }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                jd[k] = c[k] >= 0 ? c[k] : kDeadCell;
+                qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
+                ql[k] = c[k] >= 0 ? (Q)(Prec<T>::S - qr[k]) : (Q)0;
             }
         }
-
-        warp_deposit<Prec<T>::wide>(jd, ql, qr, use_smem, s_dep, dlo, dspan, a.dep + node0);
-        __syncthreads();
-        if (use_smem) {
-            for (int i = tid; i < dspan; i += NT) {
-                const unsigned long long v = s_dep[i];
-                const int node = dlo + i;
-                if (v != 0ull && node >= 0 && node <= N) atomicAdd(a.dep + node0 + node, v);
-            }
-        }
+        warp_deposit<Q>(jd, ql, qr, a.dep + node0);
     }
 }
 

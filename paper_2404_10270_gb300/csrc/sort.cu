@@ -28,10 +28,12 @@ __global__ void __launch_bounds__(NT) k_hist(const SortArgs a)
     const int32_t* cell = a.cell[a.src];
     const int64_t total = a.tile_start[a.nseg];
     const int lane = threadIdx.x & 31;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
+    for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
+         tile += wstride) {
         const int s = find_segment(a.tile_start, a.nseg, tile);
         const SegParams& P = a.seg[s];
-        const int64_t quad = (tile - a.tile_start[s]) * NT + threadIdx.x;
+        const int64_t quad = (tile - a.tile_start[s]) * 32 + lane;
         const int64_t nq = a.seg_nmove[s] >> 2;
         int c[4] = {-1, -1, -1, -1};
         if (quad < nq) {
@@ -109,10 +111,12 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
     const int64_t total = a.tile_start[a.nseg];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
+    for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
+         tile += wstride) {
         const int s = find_segment(a.tile_start, a.nseg, tile);
         const SegParams& P = a.seg[s];
-        const int64_t quad = (tile - a.tile_start[s]) * NT + threadIdx.x;
+        const int64_t quad = (tile - a.tile_start[s]) * 32 + lane;
         const int64_t nq = a.seg_nmove[s] >> 2;
         const int64_t slot = P.base + 4 * quad;
         int c[4] = {-1, -1, -1, -1};
