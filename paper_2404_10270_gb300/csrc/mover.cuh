@@ -26,7 +26,6 @@
 
 namespace bitpic {
 
-constexpr int kWarpSpan = 8;      // nodes a warp reduces in registers
 #ifndef BITPIC_MOVE_MIN_WARPS
 #define BITPIC_MOVE_MIN_WARPS 24
 #endif
@@ -143,12 +142,16 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z
     *z1 = r * s;
 }
 
-// Warp-level deposit of four particles per lane.  The warp's particles usually touch
-// a handful of nodes (particles are sorted by cell); each node total is then formed
-// by a register reduction across the warp and added to HBM by one lane with a single
-// 64-bit reduction (no return value, so the warp does not wait for it).
+// Warp-level deposit of four particles per lane.  With Q = rint(f S) the charge of
+// one particle is S - Q on node j and Q on node j+1, so the total on node c is
+//     S n_c - R_c + R_{c-1},   n_c = particles in cell c,  R_c = sum of their Q.
+// The warp's particles usually sit in a few neighbouring cells (they are sorted by
+// cell), so per occupied cell the warp forms n_c and R_c by register reductions; lane
+// l then owns node wmin + l, takes R_{c-1} from lane l-1 by shuffle, and adds the node
+// total to HBM with one 64-bit reduction (no return value, so nothing waits on it).
 template <typename Q>
-__device__ __forceinline__ void warp_deposit(const int jd[4], const Q ql[4], const Q qr[4],
+__device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
+                                             unsigned long long S,
                                              unsigned long long* __restrict__ gdep)
 {
     const unsigned FULL = 0xffffffffu;
@@ -163,42 +166,58 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q ql[4], con
     const int wmin = __reduce_min_sync(FULL, lmin);
     if (wmin == INT_MAX) return;
     const int wmax = __reduce_max_sync(FULL, lmax);
-    const int nspan = wmax - wmin + 2;
-    if (nspan <= kWarpSpan) {
-        unsigned long long mine = 0;
-        for (int n = 0; n < nspan; ++n) {
-            const int node = wmin + n;
+    const int ncell = wmax - wmin + 1;
+    if (ncell < 32) {
+        unsigned long long myR = 0;  // R_c of cell wmin + lane
+        uint32_t myn = 0;            // n_c of cell wmin + lane
+        for (int i = 0; i < ncell; ++i) {
+            const int cidx = wmin + i;
+            uint32_t n = 0;
             if (sizeof(Q) == 4) {
-                uint32_t v = 0;
+                uint32_t r = 0;  // at most 128 x 2^24 < 2^32
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    v += jd[k] == node ? (uint32_t)ql[k] : 0u;
-                    v += jd[k] + 1 == node ? (uint32_t)qr[k] : 0u;
+                    const bool in = jd[k] == cidx;
+                    r += in ? (uint32_t)qr[k] : 0u;
+                    n += in ? 1u : 0u;
                 }
-                // at most 128 particles x 2^24 < 2^32
-                const uint32_t t = __reduce_add_sync(FULL, v);
-                if (lane == n) mine = t;
+                const uint32_t tr = __reduce_add_sync(FULL, r);
+                const uint32_t tn = __reduce_add_sync(FULL, n);
+                if (lane == i) {
+                    myR = tr;
+                    myn = tn;
+                }
             } else {
                 // 48-bit charges: reduce the high and low 24-bit halves separately
                 uint32_t lo = 0, hi = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const uint64_t a = jd[k] == node ? (uint64_t)ql[k] : 0ull;
-                    const uint64_t b = jd[k] + 1 == node ? (uint64_t)qr[k] : 0ull;
-                    lo += (uint32_t)(a & 0xFFFFFFu) + (uint32_t)(b & 0xFFFFFFu);
-                    hi += (uint32_t)(a >> 24) + (uint32_t)(b >> 24);
+                    const bool in = jd[k] == cidx;
+                    const uint64_t q = in ? (uint64_t)qr[k] : 0ull;
+                    lo += (uint32_t)(q & 0xFFFFFFu);
+                    hi += (uint32_t)(q >> 24);
+                    n += in ? 1u : 0u;
                 }
                 const uint32_t tl = __reduce_add_sync(FULL, lo);
                 const uint32_t th = __reduce_add_sync(FULL, hi);
-                if (lane == n) mine = ((unsigned long long)th << 24) + tl;
+                const uint32_t tn = __reduce_add_sync(FULL, n);
+                if (lane == i) {
+                    myR = ((unsigned long long)th << 24) + tl;
+                    myn = tn;
+                }
             }
         }
-        if (lane < nspan && mine != 0) atomicAdd(gdep + wmin + lane, mine);
+        const unsigned long long prevR = __shfl_up_sync(FULL, myR, 1);
+        if (lane <= ncell) {
+            const unsigned long long tot =
+                S * (unsigned long long)myn - myR + (lane > 0 ? prevR : 0ull);
+            if (tot != 0) atomicAdd(gdep + wmin + lane, tot);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (jd[k] >= 0) {
-                atomicAdd(gdep + jd[k], (unsigned long long)ql[k]);
+                atomicAdd(gdep + jd[k], S - (unsigned long long)qr[k]);
                 atomicAdd(gdep + jd[k] + 1, (unsigned long long)qr[k]);
             }
     }
@@ -335,14 +354,64 @@ __device__ __noinline__ int wall_event(const MoveArgs& a, const SegParams& P, in
     return 1;
 }
 
+// The state of one lane's quad, copied out of registers only for the rare handler.
+template <typename T>
+struct Quad {
+    int c[4];
+    T f[4], ux[4], uy[4], uz[4];
+};
+
+// Rare events of one quad, in particle order: wall hits (bit k of `wall`) and
+// null-collision candidates (bit k of `cand`, Philox word 0 already below the
+// candidate threshold).  Out of line so that the hot loop keeps its state in
+// registers.  Returns the bits of particles whose uy/uz changed (non-MAG callers
+// store those).
+template <typename T, bool MAG>
+__device__ __noinline__ unsigned rare_events(const MoveArgs& a, const SegParams& P, int s,
+                                             int64_t step, int64_t slot, unsigned wall,
+                                             unsigned cand, const uint32_t* idv, Quad<T>* q)
+{
+    const T* uyp = static_cast<const T*>(a.uy);
+    const T* uzp = static_cast<const T*>(a.uz);
+    unsigned dirty = 0;
+    for (int k = 0; k < 4; ++k) {
+        const unsigned bit = 1u << k;
+        if (!((wall | cand) & bit)) continue;
+        T vy = MAG ? q->uy[k] : uyp[slot + k];
+        T vz = MAG ? q->uz[k] : uzp[slot + k];
+        int j = q->c[k];
+        T f = q->f[k];
+        T vx = q->ux[k];
+        if (wall & bit) {
+            const int r = wall_event<T>(a, P, s, idv[k], step, j, f, vx, vy, vz);
+            if (r == 2) {
+                q->c[k] = -1;
+                continue;
+            }
+        } else if (collide<T>(a, P, s, idv[k], step, j, f, vx, vy, vz)) {
+        } else {
+            continue;
+        }
+        q->c[k] = j;
+        q->f[k] = f;
+        q->ux[k] = vx;
+        q->uy[k] = vy;
+        q->uz[k] = vz;
+        dirty |= bit;
+    }
+    return dirty;
+}
+
 // The fused time step.  Work unit: a warp tile of 32 quads (128 consecutive particles
 // of one segment); each lane owns one quad and moves it with 128-bit accesses.  Warps
 // walk the tiles of all segments independently (no block-level barrier), so every SM
 // keeps many tiles' loads in flight.  The acceleration of the nodes a warp's
 // particles occupy is staged in registers: one coalesced load of the warp's node span,
-// then each particle picks its two nodes by warp shuffle.
+// then each particle picks its two nodes by warp shuffle.  The loop over the quad is
+// free of calls; walls and collision candidates are flagged and handled out of line.
 template <typename T, int NT, bool MAG, bool MOVE>
-__global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32)) k_move(const MoveArgs a)
+__global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32))
+k_move(const __grid_constant__ MoveArgs a)
 {
     using Q = typename Prec<T>::Q;
     const unsigned FULL = 0xffffffffu;
@@ -390,8 +459,6 @@ __global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32)) k_move(const Mo
             }
         }
 
-        int jd[4];
-        Q ql[4], qr[4];
         if (MOVE) {
             // stage the acceleration of the warp's node span in registers
             int lmin = INT_MAX, lmax = INT_MIN;
@@ -406,7 +473,7 @@ __global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32)) k_move(const Mo
             const bool staged = wmin != INT_MAX && wmax - wmin + 2 <= 32;
             T av = T(0);
             if (staged && lane <= wmax - wmin + 1) av = __ldg(accp + node0 + wmin + lane);
-            unsigned dirty = 0;  // bit k: uy/uz of particle k changed (non-MAG path)
+            unsigned wallbits = 0, candbits = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 // 1. gather (Listing 7)
@@ -422,9 +489,6 @@ __global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32)) k_move(const Mo
                     a0 = T(0);
                     a1 = T(0);
                 }
-                jd[k] = kDeadCell;
-                ql[k] = 0;
-                qr[k] = 0;
                 if (c[k] < 0) continue;
                 int j = c[k];
                 T fk = f[k];
@@ -457,47 +521,37 @@ __global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32)) k_move(const Mo
                     fk = T(0);
                     j += 1;
                 }
-                // 4. walls
-                bool reinjected = false;
+                c[k] = j;
+                f[k] = fk;
+                // 4. walls (absorption and re-injection out of line)
                 if (j < 0 || j >= N) {
                     if (bc == PIC_BC_PERIODIC) {
                         j %= N;
                         if (j < 0) j += N;
+                        c[k] = j;
                     } else {
-                        T vy = MAG ? uy[k] : uyp[slot + k];
-                        T vz = MAG ? uz[k] : uzp[slot + k];
-                        const int r = wall_event<T>(a, P, s, idv[k], step, j, fk, ux[k], vy, vz);
-                        if (r == 2) {
-                            c[k] = -1;
-                            f[k] = fk;
-                            continue;
-                        }
-                        uy[k] = vy;
-                        uz[k] = vz;
-                        dirty |= 1u << k;
-                        reinjected = true;
+                        wallbits |= 1u << k;
+                        continue;
                     }
                 }
-                // 5. Monte Carlo collisions (Philox word 0 against the candidate threshold;
-                // the rare candidate continues out of line)
-                if (!reinjected && collides) {
+                // 5. null-collision candidate: Philox word 0 against floor(P 2^32)
+                if (collides) {
                     const uint4 w = draw(idv[k], step, kRngCollide, key0, key1);
-                    if (w.x < cand) {
-                        T vy = MAG ? uy[k] : uyp[slot + k];
-                        T vz = MAG ? uz[k] : uzp[slot + k];
-                        if (collide<T>(a, P, s, idv[k], step, j, fk, ux[k], vy, vz)) {
-                            uy[k] = vy;
-                            uz[k] = vz;
-                            dirty |= 1u << k;
-                        }
-                    }
+                    if (w.x < cand) candbits |= 1u << k;
                 }
-                c[k] = j;
-                f[k] = fk;
-                // 6. deposit of the new position
-                jd[k] = j;
-                qr[k] = (Q)Prec<T>::qright(fk);
-                ql[k] = (Q)Prec<T>::S - qr[k];
+            }
+            unsigned dirty = 0;
+            if (wallbits | candbits) {
+                Quad<T> q;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    q.c[k] = c[k]; q.f[k] = f[k]; q.ux[k] = ux[k]; q.uy[k] = uy[k]; q.uz[k] = uz[k];
+                }
+                dirty = rare_events<T, MAG>(a, P, s, step, slot, wallbits, candbits, idv, &q);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    c[k] = q.c[k]; f[k] = q.f[k]; ux[k] = q.ux[k]; uy[k] = q.uy[k]; uz[k] = q.uz[k];
+                }
             }
             if (act) {
                 __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
@@ -515,15 +569,16 @@ __global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32)) k_move(const Mo
                         }
                 }
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                jd[k] = c[k] >= 0 ? c[k] : kDeadCell;
-                qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
-                ql[k] = c[k] >= 0 ? (Q)(Prec<T>::S - qr[k]) : (Q)0;
-            }
         }
-        warp_deposit<Q>(jd, ql, qr, a.dep + node0);
+        // 6. deposit of the (new) positions
+        int jd[4];
+        Q qr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            jd[k] = c[k] >= 0 ? c[k] : kDeadCell;
+            qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
+        }
+        warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0);
     }
 }
 
