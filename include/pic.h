@@ -195,6 +195,32 @@ PIC_API const char* pic_last_error(const pic_handle* h);
 PIC_API int pic_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t n,
                int32_t on_device, void* stream);
 
+/* Allocation-free field solve (the paper has no counterpart; it exists for callers
+ * that cannot allocate device memory: code running while a CUDA graph is being
+ * captured, latency-critical loops in which an allocation could block or fragment,
+ * and host frameworks that own all device memory through their own pools).
+ * Computes, for one instance of `ncells` cells (at most 65536), the field E on nodes
+ * 0..ncells from its fixed-point charge deposits, exactly as the handle's field phase
+ * does: the grounded Dirichlet Poisson problem solved in 128-bit integers, E = -grad
+ * phi with Gauss's law over the wall half cells.
+ *   charge  device array, nspecies x (ncells+1) int64, species-major: the per-node
+ *           deposits in units where one particle adds `unit` (the layout and unit
+ *           pic_charge_raw returns);
+ *   z       host array of nspecies integers: species charge q_s w_s = z_s * delta;
+ *   eps0    vacuum permittivity;  E  device array of ncells+1 doubles (output);
+ *   stream  borrowed cudaStream_t (NULL = default stream); the call only enqueues.
+ * Allocates nothing: its scratch (one 128-bit sum per node) is a static device array
+ * of the library, 1 MB on every GPU that loads it, held until the process exits.  The
+ * first call on a device looks up that array's device address (with the device
+ * current), so make the first call before any stream capture.  Every call on a device
+ * shares the array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  Returns PIC_EINVAL for ncells outside
+ * [1, 65536] or bad arguments, PIC_ECUDA if a launch fails; the message is available
+ * from pic_last_error(NULL). */
+PIC_API int pic_field_solve_noalloc(int32_t ncells, int32_t nspecies, const int64_t* charge,
+                                    const int32_t* z, double delta, int64_t unit, double eps0,
+                                    double* E, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ UNITS = {
     "sort.cu": ["-fmad=false"],
     "io.cu": ["-fmad=false"],
     "engine.cu": ["-fmad=false"],
+    "noalloc.cu": ["-fmad=false"],
 }
 
 

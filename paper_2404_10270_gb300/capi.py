@@ -27,7 +27,8 @@ STATUS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA",
 
 EXPORTS = ("pic_create", "pic_load_particles", "pic_step", "pic_sync", "pic_moments",
            "pic_count", "pic_get_particles", "pic_charge_raw", "pic_profile",
-           "pic_kernel_time", "pic_destroy", "pic_last_error", "pic_philox")
+           "pic_kernel_time", "pic_destroy", "pic_last_error", "pic_philox",
+           "pic_field_solve_noalloc")
 
 
 class PicError(RuntimeError):
@@ -96,6 +97,7 @@ def lib():
         L.pic_last_error.argtypes = [P]
         L.pic_last_error.restype = C.c_char_p
         L.pic_philox.argtypes = [C.c_uint64, P, P, I64, I32, P]
+        L.pic_field_solve_noalloc.argtypes = [I32, I32, P, P, C.c_double, I64, C.c_double, P, P]
         _lib = L
     return _lib
 

@@ -37,6 +37,12 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+namespace bitpic {
+// The message pic_last_error(NULL) returns (failed pic_create, pic_philox,
+// pic_field_solve_noalloc).
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace bitpic
+
 struct pic_handle {
     int precision = PIC_FP32;
     int ninst = 0, nseg = 0, sort_interval = 0, nt = 256, grid_move = 0, sms = 0;
