@@ -34,9 +34,10 @@ from paper_2404_10270_gb300 import workloads as W  # noqa: E402
 METRIC = "particle-steps/s (gather+push+MCC+deposit), FP32 vs FP64 form, % HBM roofline"
 UNIT = "particle-steps/s"
 # algorithmic bytes per particle-step of the mover (B = 0, constant collision
-# frequency): read cell, off, vx, id (16 B), write cell, off, vx (12 B) in FP32;
-# read cell(4) off(8) vx(8) id(4), write cell(4) off(8) vx(8) in FP64.
-MOVER_BYTES = {"f32": 28, "f64": 44}
+# frequency): read cell word, off, vx (12 B), write them (12 B) in FP32; read and write
+# cell word (4) off (8) vx (8) in FP64.  The id is read only at collision-clock events
+# (about one step in 127) and vy/vz only on collisions and wall hits.
+MOVER_BYTES = {"f32": 24, "f64": 40}
 
 
 def peaks():
@@ -300,7 +301,7 @@ def _run_ours(args, stream, rank, world, local):
         got = C.c_int64()
         cap = len(o["cell"])
         capi._check(capi.lib().pic_get_particles(sim._h, 0, s, cap, *[o[k].ctypes.data for k in
-                    ("cell", "off", "vx", "vy", "vz", "id")], 0, C.byref(got)), sim._h)
+                    ("cell", "off", "vx", "vy", "vz", "id")], None, 0, C.byref(got)), sim._h)
         d2h += got.value * 40
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0

@@ -21,9 +21,11 @@
  *  - Every call returns an int status (PIC_OK or a negative pic_status).  No C++
  *    exception, abort or exit crosses the interface.
  *  - Input pointers are borrowed for the duration of the call; data is copied in.
- *    Output buffers belong to the caller.  `on_device` = 1 means the pointers are CUDA
- *    device pointers valid on the handle's device; 0 means host memory (pinned or
- *    pageable).
+ *    Output buffers belong to the caller.  `flags` of the particle calls: PIC_DEVICE
+ *    means the pointers are CUDA device pointers valid on the handle's device (else
+ *    host memory, pinned or pageable); PIC_CELL_UNITS means velocities are in the
+ *    library's internal unit, cells per time step (u = v dt/dx), which makes a
+ *    get/load round trip exact (checkpoints); otherwise they are physical.
  *  - The handle owns all device memory it allocates and releases it in pic_destroy.
  *  - A handle is used by one host thread at a time.  Work is ordered on the handle's
  *    stream (the borrowed `cuda_stream` of pic_config, or a stream the library owns).
@@ -62,6 +64,7 @@ typedef enum {
 } pic_status;
 
 enum { PIC_FP32 = 0, PIC_FP64 = 1 };                          /* particle state precision */
+enum { PIC_DEVICE = 1, PIC_CELL_UNITS = 2 };                  /* flags of load/get */
 enum { PIC_BC_ABSORB = 0, PIC_BC_PERIODIC = 1, PIC_BC_SOURCE = 2 };
 enum { PIC_FIELD_POISSON = 0, PIC_FIELD_NONE = 1, PIC_FIELD_EXTERNAL = 2 };
 enum { PIC_PROC_ELASTIC = 0, PIC_PROC_CX = 1, PIC_PROC_IONIZE = 2 };
@@ -125,6 +128,7 @@ typedef struct {
     double wall_energy[PIC_MAX_SPECIES][2];    /* sum of w m v^2/2 of absorbed particles */
     int64_t collisions[PIC_MAX_PROC];          /* real collision events per process */
     double kinetic[PIC_MAX_SPECIES];           /* sum of w m v^2/2 over live particles */
+    int64_t next_id;                           /* id the next created particle gets */
 } pic_moments_out;
 
 /* Create a handle: validates the configuration, allocates the particle store
@@ -134,14 +138,18 @@ PIC_API int pic_create(const pic_config* cfg, pic_handle** out);
 
 /* Replace the particles of (instance, species) with n particles: cell[k] in
  * [0, ncells), off[k] in [0, 1), physical velocities.  id == NULL numbers them after
- * the largest id of the instance so far.  n must not exceed the species capacity
- * (else PIC_ECAPACITY).  Invalid cell/offset values are reported as PIC_EINVAL by the
- * next synchronising call.  Marks the fields stale: the next pic_step first deposits
- * all particles and solves the field. */
+ * the largest id of the instance so far.  state == NULL starts every particle's
+ * collision clock at 0 (its next step draws); otherwise state[k] is the clock that
+ * pic_get_particles returned (bits 0-6: steps to skip before the particle's next
+ * collision event step; bit 7: that event step is a collision candidate), which makes
+ * a checkpoint/restart continue bit-identically.  n must not exceed the species
+ * capacity (else PIC_ECAPACITY).  Invalid cell/offset values are reported as
+ * PIC_EINVAL by the next synchronising call.  Marks the fields stale: the next
+ * pic_step first deposits all particles and solves the field. */
 PIC_API int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
-                       const int32_t* cell, const double* off, const double* vx,
-                       const double* vy, const double* vz, const uint32_t* id,
-                       int32_t on_device);
+                               const int32_t* cell, const double* off, const double* vx,
+                               const double* vy, const double* vz, const uint32_t* id,
+                               const uint8_t* state, int32_t flags);
 
 /* Enqueue nsteps time steps of every instance on the handle's stream. */
 PIC_API int pic_step(pic_handle* h, int64_t nsteps);
@@ -161,10 +169,18 @@ PIC_API int pic_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n);
 
 /* Copy out the live particles of (inst, species) in storage order: *n_out receives
  * their number, which must not exceed `capacity` (else PIC_ECAPACITY, nothing
- * written).  Any output pointer may be NULL.  Velocities are physical. */
+ * written).  Any output pointer may be NULL.  Velocities are physical; `state`
+ * receives each particle's collision clock (see pic_load_particles). */
 PIC_API int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
-                      int32_t* cell, double* off, double* vx, double* vy, double* vz,
-                      uint32_t* id, int32_t on_device, int64_t* n_out);
+                              int32_t* cell, double* off, double* vx, double* vy, double* vz,
+                              uint32_t* id, uint8_t* state, int32_t flags, int64_t* n_out);
+
+/* Restore the counters a checkpoint needs besides the particles: the step count of
+ * the handle (it keys every random draw) and, when next_id is not NULL, the next
+ * particle id of each of the n_instances instances (ids given to ionization
+ * products).  Together with pic_load_particles(..., state, ...) of every species this
+ * continues a run bit-identically. */
+PIC_API int pic_restore_counters(pic_handle* h, int64_t step, const uint64_t* next_id);
 
 /* The fixed-point charge deposit of the last step for instance `inst`: host array of
  * nspecies*(ncells+1) int64 node sums, in units where every live particle adds

@@ -24,7 +24,9 @@
  * The paper gives neither the push in a magnetic field, nor the collision model,
  * nor the interpolation weights, nor the wall treatment; the readings taken here are:
  * Boris (1970) rotation; null-collision MCC (Skullerud 1968, Vahedi & Surendra 1995)
- * with integer acceptance thresholds on Philox4x32-10 words; linear (CIC) weights;
+ * whose candidate steps are drawn as geometric runs from Philox4x32-10 words with
+ * integer thresholds, and whose process selection uses fixed integer slots; linear
+ * (CIC) weights;
  * Gauss's law over the half cell at the wall nodes.  All arithmetic is FP64 and the
  * file is compiled without floating-point contraction.
  */
@@ -35,6 +37,7 @@
 #include <string.h>
 
 #define TWO_PI 6.283185307179586476925286766559
+#define ORC_GAP_MAX 127
 #define TWO32 4294967296.0
 
 /* ------------------------------------------------------------------------- */
@@ -101,6 +104,7 @@ typedef struct {
     double *ux, *uy, *uz; /* cells per step */
     uint32_t* id;
     unsigned char* alive;
+    uint8_t* mcc;  /* collision clock: bits 0-6 steps to skip, bit 7 candidate pending */
 } orc_store;
 
 typedef struct {
@@ -123,7 +127,8 @@ struct orc_sim {
     double svec[ORC_MAX_SPECIES][3]; /* Boris s = 2 t / (1 + t.t) */
     double kefac[ORC_MAX_SPECIES];   /* w m (dx/dt)^2 / 2: energy per (cells/step)^2 */
     double vinj[ORC_MAX_SPECIES];    /* sqrt(T_s/m_s) in cells/step */
-    uint32_t cand[ORC_MAX_SPECIES];  /* candidate threshold floor(P * 2^32) */
+    int collides[ORC_MAX_SPECIES];   /* species has collision processes */
+    uint32_t gapT[ORC_MAX_SPECIES][ORC_GAP_MAX + 1]; /* floor((1-P)^g 2^32), g = 1..127 */
     uint64_t slot_end[ORC_MAX_PROC]; /* cumulative slot bound of each process */
     double thr_u2[ORC_MAX_PROC];     /* energy threshold as |u|^2 */
     double vneutral;                 /* sqrt(T_n/m_n) in cells/step */
@@ -157,7 +162,7 @@ static int store_reserve(orc_store* a, int64_t cap)
     void* p;
 #define GROW(f, T) p = realloc(a->f, (size_t)nc * sizeof(T)); if (!p) return -2; a->f = (T*)p;
     GROW(cell, int32_t) GROW(off, double) GROW(ux, double) GROW(uy, double)
-    GROW(uz, double) GROW(id, uint32_t) GROW(alive, unsigned char)
+    GROW(uz, double) GROW(id, uint32_t) GROW(alive, unsigned char) GROW(mcc, uint8_t)
 #undef GROW
     a->cap = nc;
     return 0;
@@ -166,7 +171,7 @@ static int store_reserve(orc_store* a, int64_t cap)
 static void store_free(orc_store* a)
 {
     free(a->cell); free(a->off); free(a->ux); free(a->uy); free(a->uz);
-    free(a->id); free(a->alive);
+    free(a->id); free(a->alive); free(a->mcc);
     memset(a, 0, sizeof(*a));
 }
 
@@ -224,9 +229,15 @@ orc_sim* orc_create(const orc_params* p)
         double numax = 0.0;
         for (int k = 0; k < p->nproc; ++k)
             if (p->proc[k].species == i) numax += p->proc[k].nu;
-        double P = -expm1(-numax * p->dt);
-        double T = floor(P * TWO32);
-        s->cand[i] = numax > 0.0 ? (T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T) : 0u;
+        /* candidate steps form a Bernoulli sequence with P = 1 - exp(-nu_max dt); the
+         * probability of g candidate-free steps in a row is (1-P)^g = exp(-g nu_max dt) */
+        s->collides[i] = numax > 0.0;
+        const double x = numax * p->dt;
+        for (int g = 1; g <= ORC_GAP_MAX; ++g) {
+            const double T = floor(exp(-(double)g * x) * TWO32);
+            s->gapT[i][g] = T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T;
+        }
+        s->gapT[i][0] = 0xFFFFFFFFu;
         /* fixed slots of [0, 2^32) for the processes of this species, in list order */
         double cum = 0.0;
         int last = -1;
@@ -263,7 +274,8 @@ static int cmp_id_at(const void* a, const void* b)
 }
 
 int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const double* off,
-             const double* vx, const double* vy, const double* vz, const uint32_t* id)
+             const double* vx, const double* vy, const double* vz, const uint32_t* id,
+             const uint8_t* mcc)
 {
     if (!s || sp < 0 || sp >= s->p.nspecies || n < 0) return -1;
     if (n > 0 && (!cell || !off || !vx || !vy || !vz)) return -1;
@@ -289,6 +301,7 @@ int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const doubl
         a->uz[r] = vz[k] * vs;
         a->id[r] = order[r].id;
         a->alive[r] = 1;
+        a->mcc[r] = mcc ? mcc[k] : 0;
         if (order[r].id >= s->next_id) s->next_id = order[r].id + 1;
     }
     a->n = n;
@@ -411,17 +424,61 @@ static int cmp_birth(const void* a, const void* b)
     return x->parent < y->parent ? -1 : (x->parent > y->parent);
 }
 
-/* Collision phase for one particle (null-collision MCC).  Returns 0 or < 0. */
+/* Number of candidate-free steps, counted from the current one, that the word w
+ * encodes: g = #{k in 1..127 : w < floor((1-P)^k 2^32)}, so P(g >= k) = (1-P)^k
+ * (geometric, truncated at 127). */
+static int gap_steps(const orc_sim* s, int sp, uint32_t w)
+{
+    int g = 0;
+    for (int k = 1; k <= ORC_GAP_MAX; ++k) {
+        if (w < s->gapT[sp][k]) g = k;
+        else break;
+    }
+    return g;
+}
+
+static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel);
+
+/* Collision phase for one particle (null-collision MCC).  Whether a step holds a
+ * collision candidate is a Bernoulli(P) sequence per particle; instead of one draw per
+ * step the particle carries its clock: C steps to skip, and whether the next event
+ * step is a candidate.  At an event step without a pending candidate (a test) the
+ * draw COLLIDE(id, step) word 0 gives the candidate-free run g starting at this step:
+ * g = 0 is a candidate now, 0 < g < 127 a candidate g steps later, g = 127 none in the
+ * next 127 steps and a new test then.  A candidate selects its process with word 1 of
+ * COLLIDE(id, step) of its own step; the step after a candidate is a test.
+ * Returns 0 or < 0. */
 static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
 {
-    const uint32_t id = a->id[k];
+    if (!s->collides[sp]) return 0;
+    const uint8_t m = a->mcc[k];
+    const int C = m & 0x7F, pending = m >> 7;
+    if (C > 0) {
+        a->mcc[k] = (uint8_t)((C - 1) | (pending << 7));
+        return 0;
+    }
     uint32_t w[4];
-    draw(s, id, s->step, ORC_RNG_COLLIDE, w);
-    if (!(w[0] < s->cand[sp])) return 0; /* no candidate this step */
+    draw(s, a->id[k], s->step, ORC_RNG_COLLIDE, w);
+    if (!pending) {
+        const int g = gap_steps(s, sp, w[0]);
+        if (g > 0) {
+            a->mcc[k] = g < ORC_GAP_MAX ? (uint8_t)((g - 1) | 0x80) : (uint8_t)(ORC_GAP_MAX - 1);
+            return 0;
+        }
+    }
+    a->mcc[k] = 0;
+    return candidate(s, sp, a, k, w[1]);
+}
+
+/* A collision candidate: process slot from the selection word, energy threshold
+ * (below it the event is a null collision), kinematics. */
+static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel)
+{
+    const uint32_t id = a->id[k];
     int proc = -1;
     for (int q = 0; q < s->p.nproc; ++q) {
         if (s->p.proc[q].species != sp) continue;
-        if ((uint64_t)w[1] < s->slot_end[q]) { proc = q; break; }
+        if ((uint64_t)wsel < s->slot_end[q]) { proc = q; break; }
     }
     if (proc < 0) return 0;
     double ux = a->ux[k], uy = a->uy[k], uz = a->uz[k];
@@ -503,6 +560,7 @@ static void reinject(orc_sim* s, int sp, orc_store* a, int64_t k)
     box_muller(q[0], q[1], &z2, &z3);
     a->cell[k] = j;
     a->off[k] = f;
+    a->mcc[k] = 0;
     a->ux[k] = z0 * s->vinj[sp];
     a->uy[k] = z1 * s->vinj[sp];
     a->uz[k] = z2 * s->vinj[sp];
@@ -601,6 +659,7 @@ static int one_step(orc_sim* s)
                 a->uz[k] = u[2];
                 a->id[k] = base + (uint32_t)(2 * r + c);
                 a->alive[k] = 1;
+                a->mcc[k] = 0;
             }
         }
         s->next_id = base + (uint32_t)(2 * s->nbirths);
@@ -614,7 +673,7 @@ static int one_step(orc_sim* s)
             if (m != k) {
                 a->cell[m] = a->cell[k]; a->off[m] = a->off[k];
                 a->ux[m] = a->ux[k]; a->uy[m] = a->uy[k]; a->uz[m] = a->uz[k];
-                a->id[m] = a->id[k]; a->alive[m] = 1;
+                a->id[m] = a->id[k]; a->alive[m] = 1; a->mcc[m] = a->mcc[k];
             }
             ++m;
         }
@@ -644,7 +703,7 @@ int64_t orc_count(const orc_sim* s, int32_t sp)
 }
 
 int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx,
-            double* vy, double* vz, uint32_t* id)
+            double* vy, double* vz, uint32_t* id, uint8_t* mcc)
 {
     if (!s || sp < 0 || sp >= s->p.nspecies) return -1;
     const orc_store* a = &s->st[sp];
@@ -656,6 +715,7 @@ int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx
         if (vy) vy[k] = a->uy[k] * iv;
         if (vz) vz[k] = a->uz[k] * iv;
         if (id) id[k] = a->id[k];
+        if (mcc) mcc[k] = a->mcc[k];
     }
     return 0;
 }

@@ -78,9 +78,11 @@ void orc_destroy(orc_sim* s);
 
 /* Replace species `sp` with n particles.  cell/off are the BIT1 (j, f) pair,
  * velocities are physical.  id == NULL assigns consecutive ids after all ids
- * loaded so far.  Returns 0 or a negative error. */
+ * loaded so far.  mcc: per-particle collision clock (bits 0-6 steps to skip, bit 7
+ * candidate pending), NULL = 0 (the next step draws).  Returns 0 or a negative error. */
 int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const double* off,
-             const double* vx, const double* vy, const double* vz, const uint32_t* id);
+             const double* vx, const double* vy, const double* vz, const uint32_t* id,
+             const uint8_t* mcc);
 
 /* Advance nsteps time steps.  Returns 0 or a negative error. */
 int orc_step(orc_sim* s, int64_t nsteps);
@@ -88,7 +90,7 @@ int orc_step(orc_sim* s, int64_t nsteps);
 int64_t orc_count(const orc_sim* s, int32_t sp);
 /* Copy out species sp sorted by ascending id (capacity = orc_count). */
 int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx,
-            double* vy, double* vz, uint32_t* id);
+            double* vy, double* vz, uint32_t* id, uint8_t* mcc);
 
 typedef struct {
     int64_t step;

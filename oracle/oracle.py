@@ -56,11 +56,11 @@ def lib():
         L.orc_create.argtypes = [C.POINTER(_Params)]
         L.orc_destroy.argtypes = [C.c_void_p]
         P = C.c_void_p
-        L.orc_load.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P, P, P, P, P, P]
+        L.orc_load.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P, P, P, P, P, P, P]
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
         L.orc_count.restype = C.c_int64
         L.orc_count.argtypes = [C.c_void_p, C.c_int32]
-        L.orc_get.argtypes = [C.c_void_p, C.c_int32, P, P, P, P, P, P]
+        L.orc_get.argtypes = [C.c_void_p, C.c_int32, P, P, P, P, P, P, P]
         L.orc_moments_get.argtypes = [C.c_void_p, C.POINTER(_Moments), P, P, P]
         L.orc_philox4x32_10.argtypes = [P, P, P]
         L.orc_poisson.argtypes = [C.c_int32, C.c_double, C.c_double, P, P, P]
@@ -134,7 +134,9 @@ class Oracle:
                 np.ascontiguousarray(ld.vx, dtype=np.float64),
                 np.ascontiguousarray(ld.vy, dtype=np.float64),
                 np.ascontiguousarray(ld.vz, dtype=np.float64),
-                None if ld.id is None else np.ascontiguousarray(ld.id, dtype=np.uint32)]
+                None if ld.id is None else np.ascontiguousarray(ld.id, dtype=np.uint32),
+                None if getattr(ld, "state", None) is None else
+                np.ascontiguousarray(ld.state, dtype=np.uint8)]
         rc = lib().orc_load(self._h, species, len(arrs[0]), *[_ptr(a) for a in arrs])
         if rc:
             raise ValueError("orc_load failed: %d" % rc)
@@ -151,9 +153,10 @@ class Oracle:
     def particles(self, species: int) -> dict:
         n = lib().orc_count(self._h, species)
         out = dict(cell=np.zeros(n, np.int32), off=np.zeros(n), vx=np.zeros(n),
-                   vy=np.zeros(n), vz=np.zeros(n), id=np.zeros(n, np.uint32))
+                   vy=np.zeros(n), vz=np.zeros(n), id=np.zeros(n, np.uint32),
+                   state=np.zeros(n, np.uint8))
         rc = lib().orc_get(self._h, species, *[_ptr(out[k]) for k in
-                                                ("cell", "off", "vx", "vy", "vz", "id")])
+                                                ("cell", "off", "vx", "vy", "vz", "id", "state")])
         if rc:
             raise RuntimeError("orc_get failed: %d" % rc)
         return out

@@ -21,12 +21,13 @@ LIB_PATH = os.path.join(HERE, "_native", "libbitpic.so")
 MAX_SPECIES = 4
 MAX_PROC = 8
 FP32, FP64 = 0, 1
+DEVICE, CELL_UNITS = 1, 2  # flags of load / get
 
 STATUS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA",
           -4: "PIC_ECAPACITY", -5: "PIC_ENONFINITE", -6: "PIC_ETIMEOUT", -7: "PIC_ESTATE"}
 
 EXPORTS = ("pic_create", "pic_load_particles", "pic_step", "pic_sync", "pic_moments",
-           "pic_count", "pic_get_particles", "pic_charge_raw", "pic_profile",
+           "pic_count", "pic_get_particles", "pic_restore_counters", "pic_charge_raw", "pic_profile",
            "pic_kernel_time", "pic_destroy", "pic_last_error", "pic_philox",
            "pic_field_solve_noalloc")
 
@@ -67,7 +68,7 @@ class pic_moments_out(C.Structure):
                 ("wall_count", (C.c_int64 * 2) * MAX_SPECIES),
                 ("wall_energy", (C.c_double * 2) * MAX_SPECIES),
                 ("collisions", C.c_int64 * MAX_PROC),
-                ("kinetic", C.c_double * MAX_SPECIES)]
+                ("kinetic", C.c_double * MAX_SPECIES), ("next_id", C.c_int64)]
 
 
 _lib = None
@@ -83,13 +84,14 @@ def lib():
         L = C.CDLL(LIB_PATH)
         P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
         L.pic_create.argtypes = [C.POINTER(pic_config), C.POINTER(C.c_void_p)]
-        L.pic_load_particles.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, I32]
+        L.pic_load_particles.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, P, I32]
         L.pic_step.argtypes = [P, I64]
         L.pic_sync.argtypes = [P]
         L.pic_moments.argtypes = [P, I32, C.POINTER(pic_moments_out), P, P, P]
         L.pic_count.argtypes = [P, I32, I32, C.POINTER(C.c_int64)]
-        L.pic_get_particles.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, I32,
+        L.pic_get_particles.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, P, I32,
                                         C.POINTER(C.c_int64)]
+        L.pic_restore_counters.argtypes = [P, I64, P]
         L.pic_charge_raw.argtypes = [P, I32, P, C.POINTER(C.c_int64)]
         L.pic_profile.argtypes = [P, I32]
         L.pic_kernel_time.argtypes = [P, I32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
@@ -201,21 +203,27 @@ class Sim:
         self.close()
 
     # -- calls ----------------------------------------------------------------------
-    def load(self, inst: int, species: int, ld) -> None:
+    def load(self, inst: int, species: int, ld, cell_units: bool = False) -> None:
         """Load particles from a workloads.Load (numpy, host) or an object with the
-        same fields as CUDA tensors (cell int32, off/vx/vy/vz float64, id uint32/int32)."""
+        same fields as CUDA tensors (cell int32, off/vx/vy/vz float64, id uint32/int32).
+        cell_units: velocities are in cells per step (as particles(..., cell_units=True)
+        returns them), for exact checkpoints."""
         arrs = [ld.cell, ld.off, ld.vx, ld.vy, ld.vz]
         if isinstance(ld.cell, np.ndarray):
             arrs = [np.ascontiguousarray(ld.cell, np.int32)] + \
                    [np.ascontiguousarray(a, np.float64) for a in arrs[1:]]
             ids = None if ld.id is None else np.ascontiguousarray(ld.id, np.uint32)
+            st = getattr(ld, "state", None)
+            st = None if st is None else np.ascontiguousarray(st, np.uint8)
             dev = 0
         else:
             ids = ld.id
+            st = getattr(ld, "state", None)
             dev = 1 if _on_device(ld.cell) else 0
         n = len(arrs[0])
+        flags = (DEVICE if dev else 0) | (CELL_UNITS if cell_units else 0)
         _check(lib().pic_load_particles(self._h, inst, species, n, *[_ptr(a) for a in arrs],
-                                        _ptr(ids), dev), self._h)
+                                        _ptr(ids), _ptr(st), flags), self._h)
 
     def load_all(self, loads: List, inst: int = 0) -> None:
         for s, ld in enumerate(loads):
@@ -232,15 +240,18 @@ class Sim:
         _check(lib().pic_count(self._h, inst, species, C.byref(n)), self._h)
         return n.value
 
-    def particles(self, inst: int, species: int) -> Dict[str, np.ndarray]:
-        """Live particles of (inst, species) in storage order (host numpy)."""
+    def particles(self, inst: int, species: int, cell_units: bool = False) -> Dict[str, np.ndarray]:
+        """Live particles of (inst, species) in storage order (host numpy); velocities
+        physical, or in cells per step with cell_units=True."""
         n = self.count(inst, species)
         out = dict(cell=np.zeros(n, np.int32), off=np.zeros(n), vx=np.zeros(n),
-                   vy=np.zeros(n), vz=np.zeros(n), id=np.zeros(n, np.uint32))
+                   vy=np.zeros(n), vz=np.zeros(n), id=np.zeros(n, np.uint32),
+                   state=np.zeros(n, np.uint8))
         got = C.c_int64()
         _check(lib().pic_get_particles(self._h, inst, species, n,
-                                       *[_ptr(out[k]) for k in ("cell", "off", "vx", "vy", "vz", "id")],
-                                       0, C.byref(got)), self._h)
+                                       *[_ptr(out[k]) for k in ("cell", "off", "vx", "vy", "vz",
+                                                                "id", "state")],
+                                       CELL_UNITS if cell_units else 0, C.byref(got)), self._h)
         assert got.value == n
         return out
 
@@ -256,8 +267,13 @@ class Sim:
                     wall_count=np.array([list(m.wall_count[i]) for i in range(S)], np.int64),
                     wall_energy=np.array([list(m.wall_energy[i]) for i in range(S)]),
                     collisions=np.array(m.collisions[:len(p.processes)], np.int64),
-                    kinetic=np.array(m.kinetic[:S]),
+                    kinetic=np.array(m.kinetic[:S]), next_id=m.next_id,
                     density=dens.reshape(S, N + 1), phi=phi, E=E)
+
+    def restore_counters(self, step: int, next_id=None) -> None:
+        """Set the step count and (optionally) each instance's next particle id."""
+        arr = None if next_id is None else np.ascontiguousarray(next_id, np.uint64)
+        _check(lib().pic_restore_counters(self._h, step, _ptr(arr)), self._h)
 
     def charge_raw(self, inst: int = 0):
         p = self.phys[inst]

@@ -25,6 +25,16 @@ constexpr int kMaxSpecies = PIC_MAX_SPECIES;
 constexpr int kMaxProc = PIC_MAX_PROC;
 constexpr int kSegAlign = 64;  // slots
 
+// The cell word of a particle: bits 0-22 the cell index j, bits 23-29 the collision
+// clock count (steps to skip before the next collision event step), bit 30 "the next
+// event step is a collision candidate", bit 31 set = empty slot (the word is -1).
+constexpr uint32_t kCellMask = (1u << 23) - 1u;
+constexpr int kClockShift = 23;
+constexpr uint32_t kClockCount = 0x7Fu;
+constexpr uint32_t kClockPending = 0x80u;
+constexpr int kGapMax = 127;
+constexpr int kMaxCells = (1 << 23) - 1;
+
 // Device status word bits (latched, reported by synchronising calls).
 enum : unsigned {
     kErrCapacity = 1u,
@@ -57,7 +67,7 @@ struct SegParams {
     double vinj;           // sqrt(T_s/m_s) in cells/step (volume source)
     double vneutral;       // sqrt(T_n/m_n) in cells/step
     double mratio;         // m_s / m_neutral (elastic energy transfer)
-    uint32_t cand;         // null-collision candidate threshold floor(P * 2^32)
+    uint32_t gap[kGapMax + 1];     // gap[g] = floor((1-P)^g 2^32), P = 1 - exp(-nu_max dt)
     int32_t nproc;         // processes of this species (list order)
     int32_t proc[kMaxProc];        // instance-level index of each process
     int32_t kind[kMaxProc];        // PIC_PROC_*
@@ -65,14 +75,18 @@ struct SegParams {
     uint64_t slot_end[kMaxProc];   // cumulative slot bounds in [0, 2^32]
     double thr_u2[kMaxProc];       // energy threshold as |u|^2 (cells/step)^2
     int32_t collide;       // any process
-    int32_t pad;
+    int32_t pad2;
 };
+
+constexpr int kChunk = 2048;  // nodes per block of the field solve
 
 struct InstParams {
     int32_t ncells;
     int32_t field;         // PIC_FIELD_*
     int32_t seg0;          // first segment
     int32_t nseg;          // segments (= nspecies)
+    int32_t chunk0;        // first field-solve chunk of this instance
+    int32_t nchunk;        // chunks of ncells+1 nodes
     int64_t inode;         // first entry of E
     int64_t ev_base;       // first entry in the ionization event buffer
     int64_t ev_cap;        // event buffer entries of this instance
@@ -106,6 +120,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
                        (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
     }
     return c;
+}
+
+// Number of candidate-free steps, counted from the current one, that the word w
+// encodes: the largest g <= 127 with w < gap[g] (0 if none), so P(g >= k) = (1-P)^k.
+__device__ __forceinline__ int gap_steps(const uint32_t* __restrict__ gap, uint32_t w)
+{
+    if (w < __ldg(gap + kGapMax)) return kGapMax;
+    int lo = 0, hi = kGapMax;  // w < gap[lo] (gap[0] = 2^32-1 > any w that got here), w >= gap[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (w < __ldg(gap + mid)) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // Draw of one purpose for particle `id` in step `step`.

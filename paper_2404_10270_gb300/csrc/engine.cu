@@ -61,7 +61,10 @@ struct pic_handle {
     void* accel = nullptr;
     unsigned long long *dep = nullptr, *dep_last = nullptr;
     double* E = nullptr;
-    i128 *R = nullptr, *UN = nullptr;
+    i128* UN = nullptr;
+    int nchunks = 0;
+    int* chunk_inst = nullptr;
+    i128 *part_sum = nullptr, *part_w = nullptr, *part_off = nullptr;
     unsigned* hist = nullptr;
     unsigned long long *newn = nullptr, *seg_n = nullptr, *seg_live = nullptr, *hwm_alt = nullptr;
     int64_t *seg_nmove = nullptr, *tile_start = nullptr;
@@ -81,6 +84,10 @@ struct pic_handle {
     int state = PIC_OK;
     std::string last_error;
 
+    // CUDA graphs of one sort cycle (sort_interval steps + the sort), one per store copy
+    bool graphs = true;
+    cudaGraphExec_t cycle[2] = {nullptr, nullptr};
+    int64_t cycle_kernels = 0;
     bool profiling = false;
     struct Timed { int cls; cudaEvent_t a, b; };
     std::vector<Timed> timed;
@@ -174,7 +181,7 @@ int validate_instance(const pic_instance& I, int idx, std::string* why)
         *why = "instance " + std::to_string(idx) + ": " + m;
         return PIC_EINVAL;
     };
-    if (I.ncells < 1 || I.ncells > (1 << 24)) return bad("ncells must be in [1, 2^24]");
+    if (I.ncells < 1 || I.ncells > kMaxCells) return bad("ncells must be in [1, 2^23 - 1]");
     if (I.nspecies < 1 || I.nspecies > PIC_MAX_SPECIES) return bad("nspecies must be 1..4");
     if (!(I.dx > 0) || !(I.dt > 0) || !(I.eps0 > 0)) return bad("dx, dt, eps0 must be > 0");
     if (I.bc < 0 || I.bc > 2) return bad("invalid bc");
@@ -226,9 +233,14 @@ void seg_constants(const pic_instance& I, int s, SegParams* P)
     double numax = 0.0;
     for (int k = 0; k < I.nproc; ++k)
         if (I.proc[k].species == s) numax += I.proc[k].nu;
-    const double Pc = -std::expm1(-numax * I.dt);
-    const double T = std::floor(Pc * 4294967296.0);
-    P->cand = numax > 0.0 ? (T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T) : 0u;
+    // candidate steps: Bernoulli(P), P = 1 - exp(-nu_max dt); a run of g candidate-free
+    // steps has probability (1-P)^g = exp(-g nu_max dt)
+    const double x = numax * I.dt;
+    P->gap[0] = 0xFFFFFFFFu;
+    for (int g = 1; g <= kGapMax; ++g) {
+        const double T = std::floor(std::exp(-(double)g * x) * 4294967296.0);
+        P->gap[g] = T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T;
+    }
     P->nproc = 0;
     double cum = 0.0;
     for (int k = 0; k < I.nproc; ++k) {
@@ -242,7 +254,7 @@ void seg_constants(const pic_instance& I, int s, SegParams* P)
         P->thr_u2[q] = (2.0 * I.proc[k].threshold / S.mass) * (vs * vs);
     }
     if (P->nproc > 0) P->slot_end[P->nproc - 1] = (uint64_t)1 << 32;
-    P->collide = (P->nproc > 0 && P->cand > 0) ? 1 : 0;
+    P->collide = (P->nproc > 0 && numax > 0.0) ? 1 : 0;
     P->key0 = (uint32_t)I.seed;
     P->key1 = (uint32_t)(I.seed >> 32);
 }
@@ -311,8 +323,12 @@ FieldArgs field_args(pic_handle* h)
     f.accel = h->accel;
     f.precision = h->precision;
     f.E = h->E;
-    f.R = h->R;
     f.UN = h->UN;
+    f.chunk_inst = h->chunk_inst;
+    f.nchunks = h->nchunks;
+    f.part_sum = h->part_sum;
+    f.part_w = h->part_w;
+    f.part_off = h->part_off;
     f.step = h->step_d;
     f.any_poisson = h->any_poisson ? 1 : 0;
     return f;
@@ -347,7 +363,7 @@ int ensure_fields(pic_handle* h)
     if ((rc = launch_move(h, false))) return rc;
     {
         Span sp(h, 1);
-        h->kernels += h->any_poisson ? 2 : 1;
+        h->kernels += h->any_poisson ? 3 : 1;
         CUDA_TRY(h, launch_field(field_args(h), false, h->stream));
     }
     h->stale = false;
@@ -466,6 +482,9 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         ip.seg0 = (int32_t)h->segh.size();
         ip.nseg = I.nspecies;
         ip.inode = inode;
+        ip.chunk0 = h->nchunks;
+        ip.nchunk = (I.ncells + 1 + kChunk - 1) / kChunk;
+        h->nchunks += ip.nchunk;
         double delta = 1.0;
         if (I.field == PIC_FIELD_POISSON) {
             std::string why;
@@ -558,8 +577,11 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->dep_last, (size_t)snode);
     if (rc == PIC_OK) rc = dalloc(h, &h->hist, (size_t)snode);
     if (rc == PIC_OK) rc = dalloc(h, &h->E, (size_t)inode);
-    if (rc == PIC_OK) rc = dalloc(h, &h->R, (size_t)inode);
     if (rc == PIC_OK) rc = dalloc(h, &h->UN, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->chunk_inst, (size_t)h->nchunks);
+    if (rc == PIC_OK) rc = dalloc(h, &h->part_sum, (size_t)h->nchunks);
+    if (rc == PIC_OK) rc = dalloc(h, &h->part_w, (size_t)h->nchunks);
+    if (rc == PIC_OK) rc = dalloc(h, &h->part_off, (size_t)h->nchunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->phi_d, (size_t)h->max_nodes);
     if (rc == PIC_OK) rc = dalloc(h, &h->segd, (size_t)h->nseg);
     if (rc == PIC_OK) rc = dalloc(h, &h->instd, (size_t)h->ninst);
@@ -595,8 +617,15 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (e == cudaSuccess) e = z(h->dep, (size_t)snode * 8);
     if (e == cudaSuccess) e = z(h->dep_last, (size_t)snode * 8);
     if (e == cudaSuccess) e = z(h->E, (size_t)inode * 8);
-    if (e == cudaSuccess) e = z(h->R, (size_t)inode * 16);
     if (e == cudaSuccess) e = z(h->UN, (size_t)h->ninst * 16);
+    if (e == cudaSuccess) e = z(h->part_sum, (size_t)h->nchunks * 16);
+    if (e == cudaSuccess) e = z(h->part_w, (size_t)h->nchunks * 16);
+    if (e == cudaSuccess) e = z(h->part_off, (size_t)h->nchunks * 16);
+    std::vector<int> ci((size_t)h->nchunks);
+    for (int i = 0; i < h->ninst; ++i)
+        for (int c = 0; c < h->insth[i].nchunk; ++c) ci[(size_t)h->insth[i].chunk0 + c] = i;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->chunk_inst, ci.data(), sizeof(int) * ci.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = z(h->seg_n, (size_t)h->nseg * 8);
     if (e == cudaSuccess) e = z(h->seg_live, (size_t)h->nseg * 8);
     if (e == cudaSuccess) e = z(h->hwm_alt, (size_t)h->nseg * 8);
@@ -646,8 +675,9 @@ int pic_create(const pic_config* cfg, pic_handle** out)
 int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
                        const int32_t* cell, const double* off, const double* vx,
                        const double* vy, const double* vz, const uint32_t* id,
-                       int32_t on_device)
+                       const uint8_t* state, int32_t flags)
 {
+    const bool on_device = (flags & PIC_DEVICE) != 0;
     int rc = check_state(h);
     if (rc) return rc;
     if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || n < 0)
@@ -663,8 +693,10 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     const int32_t* dc = cell;
     const double *doff = off, *dvx = vx, *dvy = vy, *dvz = vz;
     const uint32_t* did = id;
+    const uint8_t* dstate = state;
     if (!on_device && n > 0) {
-        const size_t bytes = (size_t)n * (4 + 8 * 4) + (id ? (size_t)n * 4 : 0) + 64;
+        const size_t bytes = (size_t)n * (4 + 8 * 4) + (id ? (size_t)n * 4 : 0) +
+                             (state ? (size_t)n : 0) + 128;
         CUDA_TRY(h, cudaMallocAsync(&stage, bytes, s));
         char* p = static_cast<char*>(stage);
         auto put = [&](const void* src, size_t b) {
@@ -679,7 +711,8 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
         dvy = (const double*)put(vy, nb8);
         dvz = (const double*)put(vz, nb8);
         did = id ? (const uint32_t*)put(id, (size_t)n * 4) : nullptr;
-        if (!dc || !doff || !dvx || !dvy || !dvz || (id && !did)) {
+        dstate = state ? (const uint8_t*)put(state, (size_t)n) : nullptr;
+        if (!dc || !doff || !dvx || !dvy || !dvz || (id && !did) || (state && !dstate)) {
             cudaFreeAsync(stage, s);
             return fail(h, PIC_ECUDA, "pic_load_particles: host-to-device copy failed");
         }
@@ -699,9 +732,10 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     l.vy = dvy;
     l.vz = dvz;
     l.id = did;
+    l.state = dstate;
     l.n = n;
     l.id0 = (uint32_t)id0;
-    l.vscale = h->inst[inst].dt / h->inst[inst].dx;
+    l.vscale = (flags & PIC_CELL_UNITS) ? 1.0 : h->inst[inst].dt / h->inst[inst].dx;
     l.base = P.base;
     l.cap = P.cap;
     l.ncells = P.ncells;
@@ -748,29 +782,87 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     return PIC_OK;
 }
 
+namespace {
+
+// Enqueue one time step (and the sort when it falls due).
+int enqueue_step(pic_handle* h)
+{
+    int rc;
+    if ((rc = launch_tiles_h(h))) return rc;
+    if ((rc = launch_move(h, true))) return rc;
+    if (h->any_ionize) {
+        Span sp(h, 3);
+        h->kernels += 1;
+        CUDA_TRY(h, launch_births(h->instd, h->ninst, h->events, h->ev_count, h->next_id,
+                                  h->st[h->cur].id, h->err, h->stream));
+    }
+    {
+        Span sp(h, 1);
+        h->kernels += h->any_poisson ? 3 : 1;
+        CUDA_TRY(h, launch_field(field_args(h), true, h->stream));
+    }
+    h->step_h += 1;
+    if (h->sort_interval > 0 && h->step_h % h->sort_interval == 0)
+        if ((rc = do_sort(h))) return rc;
+    return PIC_OK;
+}
+
+// Capture one sort cycle starting from store copy h->cur: sort_interval steps whose
+// last one ends with the sort (which makes the other copy current).  Every kernel
+// reads the step count and segment sizes from device memory, so the same graph
+// replays every cycle that starts from this copy.
+int capture_cycle(pic_handle* h)
+{
+    const int c0 = h->cur;
+    const int64_t step0 = h->step_h, k0 = h->kernels;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = PIC_OK;
+    for (int n = 0; n < h->sort_interval && rc == PIC_OK; ++n) rc = enqueue_step(h);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->step_h = step0;
+    h->cur = c0;
+    h->cycle_kernels = h->kernels - k0;
+    h->kernels = k0;
+    if (rc != PIC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(h, PIC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(h, PIC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    h->cycle[c0] = ex;
+    return PIC_OK;
+}
+
+}  // namespace
+
 int pic_step(pic_handle* h, int64_t nsteps)
 {
     int rc = check_state(h);
     if (rc) return rc;
     if (nsteps < 0) return fail(h, PIC_EINVAL, "pic_step: nsteps < 0");
     if ((rc = ensure_fields(h))) return rc;
-    for (int64_t n = 0; n < nsteps; ++n) {
-        if ((rc = launch_tiles_h(h))) return rc;
-        if ((rc = launch_move(h, true))) return rc;
-        if (h->any_ionize) {
-            Span sp(h, 3);
-            h->kernels += 1;
-            CUDA_TRY(h, launch_births(h->instd, h->ninst, h->events, h->ev_count, h->next_id,
-                                      h->st[h->cur].id, h->err, h->stream));
+    const int64_t K = h->sort_interval;
+    const bool graphs = h->graphs && !h->profiling && K > 0 && h->stream != nullptr;
+    int64_t n = 0;
+    while (n < nsteps) {
+        if (graphs && h->step_h % K == 0 && nsteps - n >= K) {
+            if (!h->cycle[h->cur] && (rc = capture_cycle(h))) return rc;
+            CUDA_TRY(h, cudaGraphLaunch(h->cycle[h->cur], h->stream));
+            h->kernels += h->cycle_kernels;
+            h->step_h += K;
+            h->cur = 1 - h->cur;
+            n += K;
+            continue;
         }
-        {
-            Span sp(h, 1);
-            h->kernels += h->any_poisson ? 2 : 1;
-            CUDA_TRY(h, launch_field(field_args(h), true, h->stream));
-        }
-        h->step_h += 1;
-        if (h->sort_interval > 0 && h->step_h % h->sort_interval == 0)
-            if ((rc = do_sort(h))) return rc;
+        if ((rc = enqueue_step(h))) return rc;
+        ++n;
     }
     return PIC_OK;
 }
@@ -813,7 +905,10 @@ int pic_moments(pic_handle* h, int32_t inst, pic_moments_out* out, double* densi
     CUDA_TRY(h, cudaMemcpy(we.data(), h->wall_energy + 2 * ip.seg0, 16 * ns, cudaMemcpyDeviceToHost));
     CUDA_TRY(h, cudaMemcpy(col.data(), h->collisions + (size_t)inst * kMaxProc, 8 * kMaxProc, cudaMemcpyDeviceToHost));
     CUDA_TRY(h, cudaMemcpy(kin.data(), h->kin, 8 * ns, cudaMemcpyDeviceToHost));
+    unsigned long long nid = 0;
+    CUDA_TRY(h, cudaMemcpy(&nid, h->next_id + inst, 8, cudaMemcpyDeviceToHost));
     out->step = step;
+    out->next_id = (int64_t)nid;
     for (int k = 0; k < ns; ++k) {
         out->live[k] = (int64_t)live[k];
         out->wall_count[k][0] = (int64_t)wc[2 * k];
@@ -869,8 +964,9 @@ int pic_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n)
 
 int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
                       int32_t* cell, double* off, double* vx, double* vy, double* vz,
-                      uint32_t* id, int32_t on_device, int64_t* n_out)
+                      uint32_t* id, uint8_t* state, int32_t flags, int64_t* n_out)
 {
+    const bool on_device = (flags & PIC_DEVICE) != 0;
     int rc = check_state(h);
     if (rc) return rc;
     if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || !n_out)
@@ -889,7 +985,7 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
     const size_t n = (size_t)std::max<unsigned long long>(live, 1);
     char* tmp = nullptr;
     const size_t scratch = (size_t)(nb + 1) * 8;
-    const size_t outb = on_device ? 0 : n * (4 + 8 * 4 + 4) + 7 * 16;
+    const size_t outb = on_device ? 0 : n * (4 + 8 * 4 + 4 + 1) + 8 * 16;
     CUDA_TRY(h, cudaMallocAsync((void**)&tmp, scratch + outb, s));
     GetArgs g;
     const Store& S = h->st[h->cur];
@@ -901,12 +997,12 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
     g.s_id = S.id;
     g.base = P.base;
     g.nslots = (int64_t)nslots;
-    g.vscale_inv = h->inst[inst].dx / h->inst[inst].dt;
+    g.vscale_inv = (flags & PIC_CELL_UNITS) ? 1.0 : h->inst[inst].dx / h->inst[inst].dt;
     g.precision = h->precision;
     g.block_count = reinterpret_cast<unsigned long long*>(tmp);
     g.capacity = (int64_t)live;
     if (on_device) {
-        g.cell = cell; g.off = off; g.vx = vx; g.vy = vy; g.vz = vz; g.id = id;
+        g.cell = cell; g.off = off; g.vx = vx; g.vy = vy; g.vz = vz; g.id = id; g.state = state;
     } else {
         char* p = tmp + (scratch + 15) / 16 * 16;
         auto take = [&](size_t b) { char* d = p; p += (b + 15) / 16 * 16; return d; };
@@ -916,6 +1012,7 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
         g.vy = vy ? (double*)take(n * 8) : nullptr;
         g.vz = vz ? (double*)take(n * 8) : nullptr;
         g.id = id ? (uint32_t*)take(n * 4) : nullptr;
+        g.state = state ? (uint8_t*)take(n) : nullptr;
     }
     CUDA_TRY(h, launch_get(g, s));
     if (!on_device && live > 0) {
@@ -926,9 +1023,26 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
         if (vy) CUDA_TRY(h, cudaMemcpyAsync(vy, g.vy, m * 8, cudaMemcpyDeviceToHost, s));
         if (vz) CUDA_TRY(h, cudaMemcpyAsync(vz, g.vz, m * 8, cudaMemcpyDeviceToHost, s));
         if (id) CUDA_TRY(h, cudaMemcpyAsync(id, g.id, m * 4, cudaMemcpyDeviceToHost, s));
+        if (state) CUDA_TRY(h, cudaMemcpyAsync(state, g.state, m, cudaMemcpyDeviceToHost, s));
     }
     CUDA_TRY(h, cudaFreeAsync(tmp, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
+    return PIC_OK;
+}
+
+int pic_restore_counters(pic_handle* h, int64_t step, const uint64_t* next_id)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (step < 0) return fail(h, PIC_EINVAL, "pic_restore_counters: step < 0");
+    if ((rc = sync_check(h))) return rc;
+    CUDA_TRY(h, cudaMemcpy(h->step_d, &step, 8, cudaMemcpyHostToDevice));
+    if (next_id) {
+        for (int i = 0; i < h->ninst; ++i)
+            if (next_id[i] > 0xFFFFFFFFull) return fail(h, PIC_EINVAL, "pic_restore_counters: next_id >= 2^32");
+        CUDA_TRY(h, cudaMemcpy(h->next_id, next_id, 8 * (size_t)h->ninst, cudaMemcpyHostToDevice));
+    }
+    h->step_h = step;
     return PIC_OK;
 }
 
@@ -989,6 +1103,8 @@ int pic_destroy(pic_handle* h)
         cudaEventDestroy(t.b);
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
+    for (auto& g : h->cycle)
+        if (g) cudaGraphExecDestroy(g);
     for (void* p : h->allocs) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     cudaGetLastError();

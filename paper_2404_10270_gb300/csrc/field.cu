@@ -87,81 +87,141 @@ __device__ i128 block_sum(i128 v, i128* sh)
     return t;
 }
 
-__device__ __forceinline__ i128 node_charge(const FieldArgs& f, const InstParams& I, int j)
+// Interior charge Z'_j of node j of instance I, from the deposit array `dep`
+// (Z'_0 = Z'_N = 0: the wall nodes do not enter the Dirichlet system).
+__device__ __forceinline__ i128 node_charge(const FieldArgs& f, const InstParams& I, int j,
+                                           const unsigned long long* dep)
 {
     i128 z = 0;
     for (int k = 0; k < I.nseg; ++k) {
         const SegParams& P = f.seg[I.seg0 + k];
-        z += (i128)I.z[k] * (i128)(long long)f.dep[P.node + j];
+        z += (i128)I.z[k] * (i128)(long long)dep[P.node + j];
     }
     return z;
 }
 
-// One block per instance: R_j (prefix of the interior charge) and U.
-__global__ void __launch_bounds__(kFieldThreads) k_field_scan(const FieldArgs f)
+// The solve runs over chunks of kChunk nodes (one block each):
+//   k_field_partial  per chunk: S_c = sum of Z' and W_c = sum of (N-j) Z' over the chunk;
+//   k_field_chunks   per instance: exclusive prefix of S_c over its chunks, U = sum of W_c;
+//   k_field_emit     per chunk: in-block scan of Z' + chunk prefix = R_j, then E_j and the
+//                    accelerations; also hands the deposit over for the next step.
+constexpr int kChunkThreads = 256;
+constexpr int kChunkPer = 8;  // nodes per thread
+static_assert(kChunk == kChunkThreads * kChunkPer, "chunk layout");
+
+__global__ void __launch_bounds__(kChunkThreads) k_field_partial(const FieldArgs f)
 {
     __shared__ i128 sh[33];
-    const InstParams I = f.inst[blockIdx.x];
+    const int c = blockIdx.x;
+    const int b = f.chunk_inst[c];
+    const InstParams& I = f.inst[b];
     if (I.field != PIC_FIELD_POISSON) return;
     const int N = I.ncells;
-    const int nn = N + 1;
-    const int C = (nn + blockDim.x - 1) / blockDim.x;
-    const int j0 = min(nn, (int)threadIdx.x * C), j1 = min(nn, j0 + C);
+    const int a = (c - I.chunk0) * kChunk;
+    const int j0 = a + threadIdx.x * kChunkPer;
     i128 sum = 0, wsum = 0;
-    for (int j = j0; j < j1; ++j) {
-        if (j == 0 || j == N) continue;
-        const i128 z = node_charge(f, I, j);
+#pragma unroll
+    for (int t = 0; t < kChunkPer; ++t) {
+        const int j = j0 + t;
+        if (j <= 0 || j >= N) continue;
+        const i128 z = node_charge(f, I, j, f.dep);
         sum += z;
         wsum += (i128)(N - j) * z;
+    }
+    const i128 S = block_sum(sum, sh);
+    const i128 Wt = block_sum(wsum, sh);
+    if (threadIdx.x == 0) {
+        f.part_sum[c] = S;
+        f.part_w[c] = Wt;
+    }
+}
+
+__global__ void __launch_bounds__(kChunkThreads) k_field_chunks(const FieldArgs f)
+{
+    __shared__ i128 sh[33];
+    const InstParams& I = f.inst[blockIdx.x];
+    if (I.field != PIC_FIELD_POISSON) return;
+    const int nc = I.nchunk;
+    const int C = (nc + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(nc, (int)threadIdx.x * C), c1 = min(nc, c0 + C);
+    i128 sum = 0, wsum = 0;
+    for (int c = c0; c < c1; ++c) {
+        sum += f.part_sum[I.chunk0 + c];
+        wsum += f.part_w[I.chunk0 + c];
     }
     i128 tot;
     i128 run = block_excl_scan(sum, &tot, sh);
     const i128 U = block_sum(wsum, sh);
-    for (int j = j0; j < j1; ++j) {
-        if (j != 0 && j != N) run += node_charge(f, I, j);
-        f.R[I.inode + j] = run;
+    for (int c = c0; c < c1; ++c) {
+        const i128 v = f.part_sum[I.chunk0 + c];
+        f.part_off[I.chunk0 + c] = run;
+        run += v;
     }
     if (threadIdx.x == 0) f.UN[blockIdx.x] = U;
 }
 
-// One thread per node: E, the pre-scaled accelerations, and the deposit hand-over.
 template <typename T>
-__global__ void k_field_emit(const FieldArgs f, int advance)
+__global__ void __launch_bounds__(kChunkThreads) k_field_emit(const FieldArgs f, int advance)
 {
-    const int b = blockIdx.y;
+    __shared__ i128 sh[33];
+    const int c = blockIdx.x;
+    if (advance && c == 0 && threadIdx.x == 0) *f.step += 1;
+    const int b = f.chunk_inst[c];
     const InstParams& I = f.inst[b];
     const int N = I.ncells;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (advance && b == 0 && j == 0) *f.step += 1;
-    if (j > N) return;
-    i128 zj = 0;
-    for (int k = 0; k < I.nseg; ++k) {
-        const SegParams& P = f.seg[I.seg0 + k];
-        const unsigned long long d = f.dep[P.node + j];
-        f.dep_last[P.node + j] = d;
-        f.dep[P.node + j] = 0ull;
-        zj += (i128)I.z[k] * (i128)(long long)d;
+    const int a = (c - I.chunk0) * kChunk;
+    const int j0 = a + threadIdx.x * kChunkPer;
+    const bool poisson = I.field == PIC_FIELD_POISSON;
+    i128 z[kChunkPer];
+    i128 run = 0;
+#pragma unroll
+    for (int t = 0; t < kChunkPer; ++t) {
+        const int j = j0 + t;
+        z[t] = 0;
+        if (j > N) continue;
+        // the deposit hand-over: keep the last complete deposit, clear for the next step
+        for (int k = 0; k < I.nseg; ++k) {
+            const SegParams& P = f.seg[I.seg0 + k];
+            const unsigned long long d = f.dep[P.node + j];
+            f.dep_last[P.node + j] = d;
+            f.dep[P.node + j] = 0ull;
+            z[t] += (i128)I.z[k] * (i128)(long long)d;
+        }
+        if (j > 0 && j < N) run += z[t];
     }
-    if (I.field != PIC_FIELD_POISSON) return;
+    if (!poisson) return;  // uniform per block: one instance per chunk
+    i128 tot;
+    const i128 off = f.part_off[c] + block_excl_scan(run, &tot, sh);
     const i128 U = f.UN[b];
     const i128 NN = (i128)N;
-    i128 G;
-    if (j == 0)
-        G = -2 * U - 2 * NN * zj;
-    else if (j == N)
-        G = 2 * NN * f.R[I.inode + N - 1] - 2 * U + 2 * NN * zj;
-    else
-        G = NN * (f.R[I.inode + j - 1] + f.R[I.inode + j]) - 2 * U;
-    const double E = I.lambda * i128_to_double(G);
-    f.E[I.inode + j] = E;
+    i128 Rprev = off;  // R_{j0-1}
     T* acc = static_cast<T*>(f.accel);
-    for (int k = 0; k < I.nseg; ++k) {
-        const SegParams& P = f.seg[I.seg0 + k];
-        acc[P.node + j] = (T)(P.accel * E);
+#pragma unroll
+    for (int t = 0; t < kChunkPer; ++t) {
+        const int j = j0 + t;
+        if (j > N) break;
+        const i128 zi = (j > 0 && j < N) ? z[t] : (i128)0;
+        const i128 R = Rprev + zi;
+        i128 G;
+        if (j == 0)
+            G = -2 * U - 2 * NN * z[t];
+        else if (j == N)
+            G = 2 * NN * Rprev - 2 * U + 2 * NN * z[t];
+        else
+            G = NN * (Rprev + R) - 2 * U;
+        const double E = I.lambda * i128_to_double(G);
+        f.E[I.inode + j] = E;
+        for (int k = 0; k < I.nseg; ++k) {
+            const SegParams& P = f.seg[I.seg0 + k];
+            acc[P.node + j] = (T)(P.accel * E);
+        }
+        Rprev = R;
     }
 }
 
-// phi_j = 2 dx lambda (j U - N U_j), U_j = sum_{m<j} R_m.
+// Potential for the diagnostics (one block, on demand), from the last complete
+// deposit: R_j and U as in the solve, then phi_j = 2 dx lambda (j U - N U_j),
+// U_j = sum_{m<j} R_m.
 __global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, int b,
                                                              double dx, double* phi)
 {
@@ -171,15 +231,30 @@ __global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, 
     const int nn = N + 1;
     const int C = (nn + blockDim.x - 1) / blockDim.x;
     const int j0 = min(nn, (int)threadIdx.x * C), j1 = min(nn, j0 + C);
-    i128 sum = 0;
-    for (int j = j0; j < j1; ++j) sum += f.R[I.inode + j];
+    // pass 1: R at the start of this thread's run, U
+    i128 sum = 0, wsum = 0;
+    for (int j = j0; j < j1; ++j) {
+        if (j == 0 || j == N) continue;
+        const i128 z = node_charge(f, I, j, f.dep_last);
+        sum += z;
+        wsum += (i128)(N - j) * z;
+    }
     i128 tot;
-    i128 run = block_excl_scan(sum, &tot, sh);  // U_{j0}
-    const i128 U = f.UN[b];
+    const i128 R0 = block_excl_scan(sum, &tot, sh);
+    const i128 U = block_sum(wsum, sh);
+    // pass 2: sum of R over this thread's run, then the exclusive prefix U_{j0}
+    i128 R = R0, rsum = 0;
+    for (int j = j0; j < j1; ++j) {
+        if (j != 0 && j != N) R += node_charge(f, I, j, f.dep_last);
+        rsum += R;
+    }
+    i128 run = block_excl_scan(rsum, &tot, sh);
+    R = R0;
     for (int j = j0; j < j1; ++j) {
         const i128 Phi = (i128)j * U - (i128)N * run;
         phi[j] = (2.0 * dx * I.lambda) * i128_to_double(Phi);
-        run += f.R[I.inode + j];
+        if (j != 0 && j != N) R += node_charge(f, I, j, f.dep_last);
+        run += R;
     }
 }
 
@@ -258,12 +333,14 @@ __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* e
 
 cudaError_t launch_field(const FieldArgs& f, bool advance_step, cudaStream_t st)
 {
-    if (f.any_poisson) k_field_scan<<<f.ninst, kFieldThreads, 0, st>>>(f);
-    dim3 grid((unsigned)((f.max_nodes + 255) / 256), (unsigned)f.ninst);
+    if (f.any_poisson) {
+        k_field_partial<<<f.nchunks, kChunkThreads, 0, st>>>(f);
+        k_field_chunks<<<f.ninst, kChunkThreads, 0, st>>>(f);
+    }
     if (f.precision == PIC_FP64)
-        k_field_emit<double><<<grid, 256, 0, st>>>(f, advance_step ? 1 : 0);
+        k_field_emit<double><<<f.nchunks, kChunkThreads, 0, st>>>(f, advance_step ? 1 : 0);
     else
-        k_field_emit<float><<<grid, 256, 0, st>>>(f, advance_step ? 1 : 0);
+        k_field_emit<float><<<f.nchunks, kChunkThreads, 0, st>>>(f, advance_step ? 1 : 0);
     return cudaGetLastError();
 }
 

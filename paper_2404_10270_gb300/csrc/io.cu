@@ -34,11 +34,13 @@ __global__ void k_load(const LoadArgs l)
                     ft = (T)0.99999994f;
                 }
             }
-            l.s_cell[g] = ok ? cc : -1;
+            // cell word: index | collision clock (bits 0-6 count, bit 7 pending)
+            const uint32_t clk = l.state ? (uint32_t)l.state[k] : 0u;
+            l.s_cell[g] = ok ? (int)((uint32_t)cc | (clk << kClockShift)) : -1;
             off[g] = ft;
-            ux[g] = (T)(l.vx[k] * l.vscale);
-            uy[g] = (T)(l.vy[k] * l.vscale);
-            uz[g] = (T)(l.vz[k] * l.vscale);
+            ux[g] = l.vscale == 1.0 ? (T)l.vx[k] : (T)(l.vx[k] * l.vscale);
+            uy[g] = l.vscale == 1.0 ? (T)l.vy[k] : (T)(l.vy[k] * l.vscale);
+            uz[g] = l.vscale == 1.0 ? (T)l.vz[k] : (T)(l.vz[k] * l.vscale);
             l.s_id[g] = l.id ? l.id[k] : l.id0 + (uint32_t)k;
         } else {
             l.s_cell[g] = -1;
@@ -121,7 +123,9 @@ __global__ void k_get_write(const GetArgs g)
     const int64_t o = (int64_t)g.block_count[blockIdx.x] + woff[warp] + __popc(b & lt);
     if (o >= g.capacity) return;
     const int64_t s = g.base + k;
-    if (g.cell) g.cell[o] = g.s_cell[s];
+    const uint32_t word = (uint32_t)g.s_cell[s];
+    if (g.cell) g.cell[o] = (int)(word & kCellMask);
+    if (g.state) g.state[o] = (uint8_t)(word >> kClockShift);
     if (g.off) g.off[o] = (double)static_cast<const T*>(g.s_off)[s];
     if (g.vx) g.vx[o] = (double)static_cast<const T*>(g.s_ux)[s] * g.vscale_inv;
     if (g.vy) g.vy[o] = (double)static_cast<const T*>(g.s_uy)[s] * g.vscale_inv;

@@ -31,8 +31,14 @@ struct FieldArgs {
     void* accel;                      // T node arrays per segment
     int precision;                    // PIC_FP32 / PIC_FP64
     double* E;                        // per instance node arrays
-    i128* R;                          // per instance node arrays: prefix charge sums
     i128* UN;                         // per instance: sum of R over nodes 0..N-1
+    // chunks of kChunk nodes: instance of each chunk, and per chunk the partial
+    // sums of the interior charge, of the weighted charge, and the chunk's prefix
+    const int* chunk_inst;
+    int nchunks;
+    i128* part_sum;
+    i128* part_w;
+    i128* part_off;
     int64_t* step;                    // incremented once per emit
     int any_poisson;
 };
@@ -84,6 +90,7 @@ struct LoadArgs {
     const double* vy;
     const double* vz;
     const uint32_t* id;     // NULL: id0 + k
+    const uint8_t* state;   // collision clocks, NULL: 0
     int64_t n;
     uint32_t id0;
     double vscale;          // dt/dx
@@ -116,6 +123,7 @@ struct GetArgs {
     double* vy;
     double* vz;
     uint32_t* id;
+    uint8_t* state;
     unsigned long long* block_count;  // scratch, ceil(nslots/1024)+1 entries
     int64_t capacity;                 // entries of the output arrays
 };

@@ -15,7 +15,9 @@
 //
 // Work decomposition: a tile is 32 quads of four consecutive particles of one
 // segment (instance, species), owned by one warp; each lane loads its quad with
-// 128-bit accesses.  Warps walk the tiles of all segments independently.  The
+// 128-bit accesses.  The particle id is not streamed: the collision clock (bits
+// 23-30 of the cell word) makes Philox draws happen about once per 127 steps per
+// particle, and only then, or at a wall, is the id read.  Warps walk the tiles of all segments independently.  The
 // acceleration of the nodes a warp touches is staged in registers and exchanged by
 // warp shuffles; there is no block-level barrier anywhere in the step, so an SM keeps
 // the loads of many tiles in flight (the kernel is bound by HBM, not by latency).
@@ -27,7 +29,7 @@
 namespace bitpic {
 
 #ifndef BITPIC_MOVE_MIN_WARPS
-#define BITPIC_MOVE_MIN_WARPS 24
+#define BITPIC_MOVE_MIN_WARPS 48
 #endif
 constexpr int kMoveMinWarps = BITPIC_MOVE_MIN_WARPS;  // resident warps per SM the mover is built for
 constexpr int kDeadCell = -(1 << 30);
@@ -223,18 +225,18 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
     }
 }
 
-// Null-collision Monte Carlo for one particle (velocity u in cells/step, after the
-// move).  Returns true when u changed.  Ionization appends two particles.
+// A null-collision candidate of one particle (velocity u in cells/step, after the
+// move): process slot from the selection word `wsel`, energy threshold (below it the
+// event is a null collision), kinematics.  Returns true when u changed.  Ionization
+// appends two particles.
 template <typename T>
 __device__ __noinline__ bool collide(const MoveArgs& a, const SegParams& P, int s,
                                      uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
-                                     T& uz)
+                                     T& uz, uint32_t wsel)
 {
-    const uint4 w = draw(id, step, kRngCollide, P.key0, P.key1);
-    if (!(w.x < P.cand)) return false;
     int q = -1;
     for (int k = 0; k < P.nproc; ++k)
-        if ((uint64_t)w.y < P.slot_end[k]) { q = k; break; }
+        if ((uint64_t)wsel < P.slot_end[k]) { q = k; break; }
     if (q < 0) return false;
     const T u2 = ux * ux + uy * uy + uz * uz;
     if (!(u2 >= (T)P.thr_u2[q])) return false;  // below threshold: null event
@@ -362,14 +364,15 @@ struct Quad {
 };
 
 // Rare events of one quad, in particle order: wall hits (bit k of `wall`) and
-// null-collision candidates (bit k of `cand`, Philox word 0 already below the
-// candidate threshold).  Out of line so that the hot loop keeps its state in
+// null-collision candidates (bit k of `cand`; the selection word is word 1 of the
+// step's COLLIDE draw).  Out of line so that the hot loop keeps its state in
 // registers.  Returns the bits of particles whose uy/uz changed (non-MAG callers
-// store those).
+// store those).  q->c holds cell words; a candidate or a re-injection restarts the
+// particle's collision clock.
 template <typename T, bool MAG>
 __device__ __noinline__ unsigned rare_events(const MoveArgs& a, const SegParams& P, int s,
                                              int64_t step, int64_t slot, unsigned wall,
-                                             unsigned cand, const uint32_t* idv, Quad<T>* q)
+                                             unsigned cand, Quad<T>* q)
 {
     const T* uyp = static_cast<const T*>(a.uy);
     const T* uzp = static_cast<const T*>(a.uz);
@@ -377,20 +380,23 @@ __device__ __noinline__ unsigned rare_events(const MoveArgs& a, const SegParams&
     for (int k = 0; k < 4; ++k) {
         const unsigned bit = 1u << k;
         if (!((wall | cand) & bit)) continue;
+        const uint32_t idk = a.id[slot + k];
         T vy = MAG ? q->uy[k] : uyp[slot + k];
         T vz = MAG ? q->uz[k] : uzp[slot + k];
-        int j = q->c[k];
+        // a wall hit carries its raw (out of range) cell index; others a cell word
+        int j = (wall & bit) ? q->c[k] : (int)((uint32_t)q->c[k] & kCellMask);
         T f = q->f[k];
         T vx = q->ux[k];
         if (wall & bit) {
-            const int r = wall_event<T>(a, P, s, idv[k], step, j, f, vx, vy, vz);
+            const int r = wall_event<T>(a, P, s, idk, step, j, f, vx, vy, vz);
             if (r == 2) {
                 q->c[k] = -1;
                 continue;
             }
-        } else if (collide<T>(a, P, s, idv[k], step, j, f, vx, vy, vz)) {
         } else {
-            continue;
+            q->c[k] = j;  // the step after a candidate draws again
+            const uint4 w = draw(idk, step, kRngCollide, P.key0, P.key1);
+            if (!collide<T>(a, P, s, idk, step, j, f, vx, vy, vz, w.y)) continue;
         }
         q->c[k] = j;
         q->f[k] = f;
@@ -432,18 +438,16 @@ k_move(const __grid_constant__ MoveArgs a)
         const int N = P.ncells;
         const int bc = P.bc;
         const int collides = P.collide;
-        const uint32_t cand = P.cand, key0 = P.key0, key1 = P.key1;
+        const uint32_t key0 = P.key0, key1 = P.key1;
         const int64_t node0 = P.node;
         const int64_t quad = (tile - a.tile_start[s]) * 32 + lane;
         const int64_t nq = a.seg_nmove[s] >> 2;
         const bool act = quad < nq;
         const int64_t slot = P.base + 4 * quad;
-        const bool need_id = MOVE && (collides || bc == PIC_BC_SOURCE);
 
         int c[4] = {-1, -1, -1, -1};
         T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
         T uy[4] = {T(0), T(0), T(0), T(0)}, uz[4] = {T(0), T(0), T(0), T(0)};
-        uint32_t idv[4] = {0u, 0u, 0u, 0u};
         if (act) {
             const int4 cc = __ldcs(reinterpret_cast<const int4*>(a.cell + slot));
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
@@ -453,10 +457,6 @@ k_move(const __grid_constant__ MoveArgs a)
                 ld4(uyp + slot, uy);
                 ld4(uzp + slot, uz);
             }
-            if (need_id) {
-                const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(a.id + slot));
-                idv[0] = ii.x; idv[1] = ii.y; idv[2] = ii.z; idv[3] = ii.w;
-            }
         }
 
         if (MOVE) {
@@ -465,8 +465,9 @@ k_move(const __grid_constant__ MoveArgs a)
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (c[k] >= 0) {
-                    lmin = min(lmin, c[k]);
-                    lmax = max(lmax, c[k]);
+                    const int jj = (int)((uint32_t)c[k] & kCellMask);
+                    lmin = min(lmin, jj);
+                    lmax = max(lmax, jj);
                 }
             const int wmin = __reduce_min_sync(FULL, lmin);
             const int wmax = __reduce_max_sync(FULL, lmax);
@@ -477,20 +478,22 @@ k_move(const __grid_constant__ MoveArgs a)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 // 1. gather (Listing 7)
+                const bool live = c[k] >= 0;
+                int j = (int)((uint32_t)c[k] & kCellMask);
+                uint32_t clk = ((uint32_t)c[k] >> kClockShift) & 0xFFu;
                 T a0, a1;
                 if (staged) {
-                    const int i = c[k] >= 0 ? c[k] - wmin : 0;
+                    const int i = live ? j - wmin : 0;
                     a0 = __shfl_sync(FULL, av, i);
                     a1 = __shfl_sync(FULL, av, i + 1);
-                } else if (c[k] >= 0) {
-                    a0 = __ldg(accp + node0 + c[k]);
-                    a1 = __ldg(accp + node0 + c[k] + 1);
+                } else if (live) {
+                    a0 = __ldg(accp + node0 + j);
+                    a1 = __ldg(accp + node0 + j + 1);
                 } else {
                     a0 = T(0);
                     a1 = T(0);
                 }
-                if (c[k] < 0) continue;
-                int j = c[k];
+                if (!live) continue;
                 T fk = f[k];
                 const T acc = a0 + fk * (a1 - a0);
                 // 2. push
@@ -521,24 +524,45 @@ k_move(const __grid_constant__ MoveArgs a)
                     fk = T(0);
                     j += 1;
                 }
-                c[k] = j;
                 f[k] = fk;
                 // 4. walls (absorption and re-injection out of line)
                 if (j < 0 || j >= N) {
                     if (bc == PIC_BC_PERIODIC) {
                         j %= N;
                         if (j < 0) j += N;
-                        c[k] = j;
                     } else {
+                        c[k] = j;  // out of range: the rare handler decides
                         wallbits |= 1u << k;
                         continue;
                     }
                 }
-                // 5. null-collision candidate: Philox word 0 against floor(P 2^32)
+                // 5. null collision.  The candidate steps of a particle form a
+                // Bernoulli(P) sequence; its clock counts the steps to skip before the
+                // next event step.  At an event step without a pending candidate (a
+                // test), Philox word 0 gives the candidate-free run g from this step:
+                // g = 0 candidate now, g < 127 a candidate g steps later, g = 127 none
+                // in the next 127 steps.  Candidates continue out of line.
                 if (collides) {
-                    const uint4 w = draw(idv[k], step, kRngCollide, key0, key1);
-                    if (w.x < cand) candbits |= 1u << k;
+                    if (clk & kClockCount) {
+                        clk -= 1u;
+                    } else if (clk & kClockPending) {
+                        candbits |= 1u << k;
+                        clk = 0u;
+                    } else {
+                        // a test step (about one step in 127): the id is read only here
+                        const uint32_t idk = __ldg(a.id + slot + k);
+                        const uint4 w = draw(idk, step, kRngCollide, key0, key1);
+                        const int g = gap_steps(P.gap, w.x);
+                        if (g == 0) {
+                            candbits |= 1u << k;
+                            clk = 0u;
+                        } else {
+                            clk = g < kGapMax ? ((uint32_t)(g - 1) | kClockPending)
+                                              : (uint32_t)(kGapMax - 1);
+                        }
+                    }
                 }
+                c[k] = (int)((uint32_t)j | (clk << kClockShift));
             }
             unsigned dirty = 0;
             if (wallbits | candbits) {
@@ -547,7 +571,7 @@ k_move(const __grid_constant__ MoveArgs a)
                 for (int k = 0; k < 4; ++k) {
                     q.c[k] = c[k]; q.f[k] = f[k]; q.ux[k] = ux[k]; q.uy[k] = uy[k]; q.uz[k] = uz[k];
                 }
-                dirty = rare_events<T, MAG>(a, P, s, step, slot, wallbits, candbits, idv, &q);
+                dirty = rare_events<T, MAG>(a, P, s, step, slot, wallbits, candbits, &q);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     c[k] = q.c[k]; f[k] = q.f[k]; ux[k] = q.ux[k]; uy[k] = q.uy[k]; uz[k] = q.uz[k];
@@ -575,7 +599,7 @@ k_move(const __grid_constant__ MoveArgs a)
         Q qr[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            jd[k] = c[k] >= 0 ? c[k] : kDeadCell;
+            jd[k] = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : kDeadCell;
             qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
         }
         warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0);

@@ -42,10 +42,11 @@ __global__ void __launch_bounds__(NT) k_hist(const SortArgs a)
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int key = c[k] >= 0 ? c[k] : -1 - lane;  // empty slots never group
+            // sort key: the cell index (empty slots get distinct keys and never group)
+            const int key = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
             const unsigned grp = __match_any_sync(0xffffffffu, key);
             if (c[k] >= 0 && lane == __ffs(grp) - 1)
-                atomicAdd(a.hist + P.node + c[k], (unsigned)__popc(grp));
+                atomicAdd(a.hist + P.node + key, (unsigned)__popc(grp));
         }
     }
 }
@@ -120,28 +121,36 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
         const int64_t nq = a.seg_nmove[s] >> 2;
         const int64_t slot = P.base + 4 * quad;
         int c[4] = {-1, -1, -1, -1};
+        T vo[4], vx[4], vy[4], vz[4];
+        uint32_t vi[4] = {0u, 0u, 0u, 0u};
         if (quad < nq) {
-            const int4 cc = *reinterpret_cast<const int4*>(cell + slot);
+            // the whole quad with 128-bit loads (the mover's access pattern)
+            const int4 cc = __ldcs(reinterpret_cast<const int4*>(cell + slot));
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+            ld4(off + slot, vo);
+            ld4(ux + slot, vx);
+            ld4(uy + slot, vy);
+            ld4(uz + slot, vz);
+            const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(id + slot));
+            vi[0] = ii.x; vi[1] = ii.y; vi[2] = ii.z; vi[3] = ii.w;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const bool live = c[k] >= 0;
-            const int key = live ? c[k] : -1 - lane;
+            const int key = live ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
             const unsigned grp = __match_any_sync(0xffffffffu, key);
             const int leader = __ffs(grp) - 1;
             unsigned base = 0;
-            if (live && lane == leader) base = atomicAdd(a.hist + P.node + c[k], (unsigned)__popc(grp));
+            if (live && lane == leader) base = atomicAdd(a.hist + P.node + key, (unsigned)__popc(grp));
             base = __shfl_sync(0xffffffffu, base, leader);
             if (live) {
-                const int64_t from = slot + k;
                 const int64_t to = P.base + (int64_t)base + __popc(grp & lt);
                 dcell[to] = c[k];
-                doff[to] = off[from];
-                dux[to] = ux[from];
-                duy[to] = uy[from];
-                duz[to] = uz[from];
-                did[to] = id[from];
+                doff[to] = vo[k];
+                dux[to] = vx[k];
+                duy[to] = vy[k];
+                duz[to] = vz[k];
+                did[to] = vi[k];
             }
         }
     }

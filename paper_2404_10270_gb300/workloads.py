@@ -19,12 +19,16 @@ Named workloads (bounded 1D plasma between grounded absorbing walls unless noted
                         ionization (threshold 0.68 T_e) + charge exchange at 0.01.
   * ``bounded_large``   65,536 cells, 1,500 ppc per species (196,608,000 particles),
                         physics of ``bounded_small``, sort every 20 steps.
+  * ``ensemble``        512 independent ``magnetized_source`` instances: cells
+                        log-uniform in [256, 8192], ppc uniform in [50, 400],
+                        m_i/m_e in {100, 1836}, B angle uniform in [0, 89] degrees,
+                        Philox seeds 1..512; instance parameters drawn with key 0.
 """
 from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -111,6 +115,24 @@ def bounded_large(ncells: int = 65536, ppc: int = 1500, seed: int = 1) -> Physic
     return bounded_small(ncells=ncells, ppc=ppc, seed=seed)
 
 
+def ensemble(n_instances: int = 512, key: int = 0, capacity_factor: float = 1.5,
+             scale: float = 1.0) -> List[Physics]:
+    """Batched ensemble of uneven bounded plasmas (magnetized, volume source,
+    elastic + ionization + charge exchange).  ``scale`` multiplies every instance's
+    particles per cell (scale < 1 gives a smaller ensemble of the same shape)."""
+    rng = np.random.Generator(np.random.Philox(key=key))
+    u = rng.random((n_instances, 4))
+    out = []
+    for i in range(n_instances):
+        cells = int(np.rint(256.0 * 32.0 ** u[i, 0]))
+        ppc = max(1, int(round((50 + int(np.floor(351.0 * u[i, 1]))) * scale)))
+        m_i = 100.0 if u[i, 2] < 0.5 else 1836.0
+        angle = 89.0 * u[i, 3]
+        out.append(magnetized_source(ncells=cells, ppc=ppc, seed=i + 1, m_i=m_i,
+                                     angle_deg=angle, capacity_factor=capacity_factor))
+    return out
+
+
 @dataclasses.dataclass
 class Load:
     cell: np.ndarray  # int32
@@ -119,13 +141,17 @@ class Load:
     vy: np.ndarray
     vz: np.ndarray
     id: np.ndarray    # uint32
+    # collision clock per particle (bits 0-6 steps to skip, bit 7 candidate pending);
+    # None = all zero, which is how a fresh load starts
+    state: Optional[np.ndarray] = None
 
     def __len__(self) -> int:
         return len(self.cell)
 
     def take(self, idx) -> "Load":
         return Load(self.cell[idx], self.off[idx], self.vx[idx], self.vy[idx],
-                    self.vz[idx], self.id[idx])
+                    self.vz[idx], self.id[idx],
+                    None if self.state is None else self.state[idx])
 
 
 def initial_load(phys: Physics, seed: int = 1, cells=None) -> List[Load]:

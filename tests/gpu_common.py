@@ -50,6 +50,14 @@ def by_id(p):
     return {k: v[order] for k, v in p.items()}
 
 
+def assert_same_clocks(gpu_parts, ora_parts):
+    """The collision clocks are integer state driven by id-keyed draws: identical."""
+    for g, o in zip(gpu_parts, ora_parts):
+        g, o = by_id(g), by_id(o)
+        np.testing.assert_array_equal(g["id"], o["id"])
+        np.testing.assert_array_equal(g["state"], o["state"])
+
+
 def particle_errors(phys, gpu_parts, ora_parts):
     """Max relative position and velocity error per species (ids must match)."""
     L = phys.length

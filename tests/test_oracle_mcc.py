@@ -75,6 +75,32 @@ def test_first_collision_step_is_geometric():
     assert abs(total / (60 * n) - P) < 5 * math.sqrt(P * (1 - P) / (60 * n))
 
 
+def test_collision_gaps_stay_geometric_beyond_the_clock_range():
+    """With P ~ 0.01 most runs without a candidate are longer than the 127 steps the
+    collision clock can hold; the first collision step must still be geometric."""
+    nu, dt, n, steps = 0.2, 0.05, 6000, 700
+    phys, ld = _gas(n, -1.0, 1.0, [W.Process(W.PROC_ELASTIC, 0, nu)], m_n=1e6, seed=21)
+    o = Oracle(phys)
+    o.load(0, ld)
+    prev = _vel(o.particles(0))
+    first = np.zeros(n, dtype=np.int64)
+    for k in range(1, steps + 1):
+        o.step(1)
+        v = _vel(o.particles(0))
+        first[(first == 0) & np.any(v != prev, axis=0)] = k
+        prev = v
+    P = -math.expm1(-nu * dt)
+    edges = np.array([1, 50, 100, 127, 128, 200, 254, 255, 300, 400, 500, 700])
+    obs, exp = [], []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        obs.append(((first >= lo) & (first < hi)).sum())
+        exp.append(n * ((1 - P) ** (lo - 1) - (1 - P) ** (hi - 1)))
+    obs.append((first == 0).sum() + (first >= edges[-1]).sum())
+    exp.append(n - sum(exp))
+    chi = stats.chisquare(obs, exp)
+    assert chi.pvalue > 1e-4, (chi, obs, exp)
+
+
 def test_charge_exchange_relaxes_ion_temperature():
     nu, n, m = 1.0, 40000, 100.0
     T0, Tn = 1.0, 0.05
