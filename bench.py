@@ -38,6 +38,12 @@ UNIT = "particle-steps/s"
 # cell word (4) off (8) vx (8) in FP64.  The id is read only at collision-clock events
 # (about one step in 127) and vy/vz only on collisions and wall hits.
 MOVER_BYTES = {"f32": 24, "f64": 40}
+# The FP64 form is bound by the FP64 pipe: per particle-step its hot path issues 12 FP64
+# instructions (gather 3, push 1, move 3, truncation 1, f >= 1 test 1, fixed-point charge
+# 2, finiteness test 1).  Peak: 2 FP64 instructions per SM per cycle (ncu's
+# peak_sustained of the dfma pipe on this GPU) x 152 SMs x 2.07 GHz.
+FP64_OPS_PER_PARTICLE = 12
+FP64_PEAK_INSTR_PER_S = 2 * 152 * 2.07e9
 
 
 def peaks():
@@ -193,12 +199,18 @@ def pinned(a: np.ndarray):
     return t, v
 
 
-def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, world, dev):
+def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, world, dev,
+                 bytes_per_particle=None):
     import torch
     import torch.distributed as dist
     sim.step(warmup)
     sim.sync()
-    live0 = sum(sim.count(0, s) for s in range(len(phys.species)))
+    physs = phys if isinstance(phys, list) else [phys]
+
+    def live_total():
+        return sum(sim.count(i, s) for i, p in enumerate(physs) for s in range(len(p.species)))
+
+    live0 = live_total()
     sim.profile(True)
     torch.cuda.synchronize()
     if world > 1:
@@ -210,7 +222,7 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
         end.record()
         torch.cuda.synchronize()
     ms = start.elapsed_time(end)
-    live1 = sum(sim.count(0, s) for s in range(len(phys.species)))
+    live1 = live_total()
     mover_n, mover_ms = sim.kernel_time(0)
     field_n, field_ms = sim.kernel_time(1)
     sort_n, sort_ms = sim.kernel_time(2)
@@ -225,19 +237,31 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
     ms_max = float(t.item())
     psteps = float(p.item())
     hbm, src = peaks()
-    per_launch_bytes = MOVER_BYTES[precision_name] * (live0 + live1) / 2
+    bpp = bytes_per_particle or MOVER_BYTES[precision_name]
+    per_launch_bytes = bpp * (live0 + live1) / 2
     avg_mover_ms = mover_ms / max(mover_n, 1)
     achieved = per_launch_bytes / (avg_mover_ms * 1e-3) / 1e9
-    traffic = profiled_traffic("k_move", precision_name)
+    traffic = profiled_traffic("k_move", precision_name) if bytes_per_particle is None else None
+    if precision_name == "f64":
+        ach = FP64_OPS_PER_PARTICLE * (live0 + live1) / 2 / (avg_mover_ms * 1e-3)
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_INSTR_PER_S,
+                "unit": "FP64 instr/s", "frac": ach / FP64_PEAK_INSTR_PER_S,
+                "peak_source": "derived: 2 FP64 instr/SM/cycle x 152 SMs x 2.07 GHz",
+                "kernel": "k_move<double>", "ops_per_particle": FP64_OPS_PER_PARTICLE,
+                "avg_launch_ms": avg_mover_ms,
+                "hbm": {"achieved_GBps": achieved, "frac_of_measured": achieved / hbm,
+                        "bytes_per_particle": MOVER_BYTES[precision_name]}}
+    else:
+        roof = None
     return {
         "value": psteps / (ms_max * 1e-3),
         "ms_per_step": ms_max / steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": roof or {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"
                      if src == "measured" else "fallback 6.8 TB/s",
                      "traffic": None if traffic is None else traffic * (live0 + live1) / 2,
                      "kernel": "k_move<%s>" % ("float" if precision_name == "f32" else "double"),
-                     "bytes_per_particle": MOVER_BYTES[precision_name],
+                     "bytes_per_particle": bpp,
                      "avg_launch_ms": avg_mover_ms},
         "kernel_ms": {"mover": mover_ms, "field": field_ms, "sort": sort_ms, "other": other_ms,
                       "mover_launches": mover_n, "sort_launch_groups": sort_n},
@@ -260,6 +284,40 @@ def run_ours(args):
         return _run_ours(args, stream.cuda_stream, rank, world, local)
 
 
+def measure_batched(args, stream, rank, world, local):
+    """The batched ensemble: 512 independent magnetized plasmas of uneven size (cells
+    log-uniform in [256, 8192], ppc in [50, 400]; volume source, elastic + ionization +
+    charge exchange, Boris push) in one handle, FP32 state.  Block size and sort
+    interval are chosen by the library's autotuner, which runs during the untimed
+    set-up steps."""
+    import concurrent.futures as cf
+    from paper_2404_10270_gb300 import capi
+    phys = W.ensemble(n_instances=args.batched_instances)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(8) as ex:
+        loads = list(ex.map(lambda ip: W.initial_load(ip[1], seed=ip[0] + 1 + 1000 * rank),
+                            enumerate(phys)))
+    n = sum(len(x) for ld in loads for x in ld)
+    sim = capi.Sim(phys, precision=capi.FP32, sort_interval=-1, block=0, stream=stream)
+    for i, ld in enumerate(loads):
+        sim.load_all(ld, inst=i)
+    del loads
+    sim.step(args.tune_steps)  # autotuning happens here (or the cached choice is used)
+    sim.sync()
+    setup = time.perf_counter() - t0
+    r = measure_form(sim, phys, args.batched_steps, 5, n, "f32", rank, world, local,
+                     bytes_per_particle=40)
+    sim.close()
+    return {"workload": "ensemble: %d instances, cells log-uniform [256, 8192], ppc [50, 400], "
+                        "m_i/m_e {100, 1836}, B angle [0, 89] deg, |B| = 2, volume source, "
+                        "elastic + ionization + charge exchange, FP32 state" % len(phys),
+            "particles_per_gpu": n, "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+            "steps": args.batched_steps, "roofline": r["roofline"], "gpu_launches": r["gpu_launches"],
+            "clocks": r["clocks"], "kernel_ms": r["kernel_ms"], "setup_s": setup,
+            "tuning": "block and sort interval by the library autotuner during %d set-up steps"
+                      % args.tune_steps}
+
+
 def _run_ours(args, stream, rank, world, local):
     import torch
     __import__("__graft_entry__").build()
@@ -272,7 +330,7 @@ def _run_ours(args, stream, rank, world, local):
     host = []
     for ld in loads:
         host.append({k: pinned(getattr(ld, k)) for k in ("cell", "off", "vx", "vy", "vz", "id")})
-    sim = capi.Sim(phys, precision=capi.FP32, sort_interval=args.sort, stream=stream)
+    sim = capi.Sim(phys, precision=capi.FP32, sort_interval=args.sort, block=256, stream=stream)
     for s, h in enumerate(host):
         sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
     setup_s = time.perf_counter() - t_setup
@@ -316,7 +374,8 @@ def _run_ours(args, stream, rank, world, local):
     if not args.no_fp64:
         sim.close()
         del sim
-        sim64 = capi.Sim(phys, precision=capi.FP64, sort_interval=args.sort, stream=stream)
+        sim64 = capi.Sim(phys, precision=capi.FP64, sort_interval=args.sort, block=256,
+                         stream=stream)
         for s, h in enumerate(host):
             sim64.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
         r64 = measure_form(sim64, phys, max(args.steps // 4, 4), min(args.warmup, 3), n, "f64",
@@ -326,6 +385,10 @@ def _run_ours(args, stream, rank, world, local):
         fp64["dtype"] = "f64"
     else:
         sim.close()
+
+    batched = None
+    if not args.no_batched:
+        batched = measure_batched(args, stream, rank, world, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -356,12 +419,30 @@ def _run_ours(args, stream, rank, world, local):
             "clocks": res["clocks"],
             "kernel_ms": res["kernel_ms"],
             "fp64_form": fp64,
+            "batched": batched,
             "setup_s": setup_s,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def profile_case(precision: str) -> int:
+    """The small case the ncu captures use: the bounded_large physics on 16,384 cells
+    (49,152,000 particles, state larger than L2), deposit-only launch + 6 steps."""
+    __import__("__graft_entry__").build()
+    from paper_2404_10270_gb300 import capi
+    phys = W.bounded_large(ncells=16384)
+    loads = W.initial_load(phys)
+    sim = capi.Sim(phys, precision=capi.FP64 if precision == "f64" else capi.FP32,
+                   sort_interval=20, block=256)
+    sim.load_all(loads)
+    sim.step(6)
+    sim.sync()
+    print("profile case ok", sim.count(0, 0) + sim.count(0, 1))
+    sim.close()
     return 0
 
 
@@ -376,10 +457,19 @@ def main():
     ap.add_argument("--sort", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-instances", type=int, default=512)
+    ap.add_argument("--batched-steps", type=int, default=40)
+    ap.add_argument("--tune-steps", type=int, default=300)
     ap.add_argument("--cpu-cells", type=int, default=1024)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-cells", type=int, default=256)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the small case the ncu captures use and exit")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.precision)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

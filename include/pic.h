@@ -112,8 +112,14 @@ typedef struct {
 typedef struct {
     int32_t n_instances;        /* >= 1 */
     int32_t precision;          /* PIC_FP32 or PIC_FP64 */
-    int32_t sort_interval;      /* sort by cell every this many steps; 0 = never */
-    int32_t block;              /* mover threads per block; 0 = library choice */
+    int32_t sort_interval;      /* sort by cell every this many steps; 0 = never;
+                                   -1 = autotune (10, 20, 40 or 80) */
+    int32_t block;              /* mover threads per block (128, 256, 512); 0 = autotune.
+                                   The autotuner times one sort cycle per candidate on the
+                                   first steps of the run (results do not depend on either
+                                   choice) and caches the choice per GPU and size bucket
+                                   in $BITPIC_TUNE_CACHE (default
+                                   $HOME/.cache/bitpic/autotune.json). */
     const pic_instance* inst;   /* n_instances entries, copied */
     void* cuda_stream;          /* borrowed cudaStream_t; NULL = library-owned stream */
 } pic_config;

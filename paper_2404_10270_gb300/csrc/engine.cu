@@ -11,9 +11,16 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
+
+#include <sys/stat.h>
 
 #include "kernels.h"
 #include "mover.cuh"
@@ -23,6 +30,8 @@ using namespace bitpic;
 namespace {
 
 thread_local std::string g_create_error;
+
+void mkdir_if_missing(const std::string& dir);
 
 struct Store {
     int32_t* cell = nullptr;
@@ -34,6 +43,11 @@ struct Store {
 };
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+void mkdir_if_missing(const std::string& dir)
+{
+    if (!dir.empty()) mkdir(dir.c_str(), 0755);  // fails harmlessly when it exists
+}
 
 }  // namespace
 
@@ -83,6 +97,15 @@ struct pic_handle {
     bool stale = true;
     int state = PIC_OK;
     std::string last_error;
+
+    // autotuning of the mover block size and the sort interval (see tune_step)
+    bool tune_block = false, tune_sort = false;
+    int tune_phase = 0;        // 0 idle/done, 1 block sizes, 2 sort intervals
+    int tune_idx = 0;          // candidate being measured
+    double tune_best = 1e300;  // best cost per step so far (ms)
+    int tune_best_val = 0;
+    std::string tune_key;
+    char gpu_name[256] = {0};
 
     // CUDA graphs of one sort cycle (sort_interval steps + the sort), one per store copy
     bool graphs = true;
@@ -438,6 +461,135 @@ int collect_times(pic_handle* h)
     return PIC_OK;
 }
 
+void set_block(pic_handle* h, int nt)
+{
+    h->nt = nt;
+    const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, nt)
+                                             : move_blocks_per_sm_f32(h->any_mag, nt);
+    h->grid_move = h->sms * std::max(bps, 1);
+}
+
+void drop_graphs(pic_handle* h)
+{
+    for (auto& g : h->cycle)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// ---- autotuner ----------------------------------------------------------------------
+// The time step's results do not depend on the mover block size or on the sort interval
+// (deposits are integer, random draws are keyed by particle id, the sort only permutes),
+// so the tuner measures candidates on the first steps of the real run: one sort cycle
+// per candidate, block sizes first (at sort interval 20), then sort intervals.  The
+// choice is cached per GPU and size bucket (precision, magnetised or not, log2 of the
+// particle count and of the mean cell count) in a JSON file: $BITPIC_TUNE_CACHE, else
+// $HOME/.cache/bitpic/autotune.json.
+const int kTuneBlocks[] = {128, 256, 512};
+const int kTuneSorts[] = {10, 20, 40, 80};
+std::mutex g_tune_mutex;
+
+std::string tune_cache_path()
+{
+    if (const char* p = std::getenv("BITPIC_TUNE_CACHE")) return p;
+    if (const char* home = std::getenv("HOME")) return std::string(home) + "/.cache/bitpic/autotune.json";
+    return "";
+}
+
+// The cache is a flat JSON object {"key": [block, sort_interval], ...}.
+std::map<std::string, std::pair<int, int>> tune_cache_read()
+{
+    std::map<std::string, std::pair<int, int>> m;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return m;
+    std::ifstream in(path);
+    if (!in) return m;
+    std::stringstream ss;
+    ss << in.rdbuf();
+    const std::string t = ss.str();
+    size_t i = 0;
+    while ((i = t.find('"', i)) != std::string::npos) {
+        const size_t j = t.find('"', i + 1);
+        if (j == std::string::npos) break;
+        const std::string key = t.substr(i + 1, j - i - 1);
+        int b = 0, k = 0;
+        const size_t lb = t.find('[', j);
+        if (lb == std::string::npos || std::sscanf(t.c_str() + lb, "[%d , %d]", &b, &k) != 2) break;
+        m[key] = {b, k};
+        i = t.find(']', lb);
+        if (i == std::string::npos) break;
+    }
+    return m;
+}
+
+void tune_cache_write(const std::map<std::string, std::pair<int, int>>& m)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);
+        std::string cur;
+        for (size_t k = 1; k <= dir.size(); ++k)  // mkdir -p, errors ignored
+            if (k == dir.size() || dir[k] == '/') {
+                cur = dir.substr(0, k);
+                mkdir_if_missing(cur);
+            }
+    }
+    const std::string tmp = path + ".tmp";
+    std::ofstream out(tmp);
+    if (!out) return;
+    out << "{\n";
+    size_t n = 0;
+    for (const auto& kv : m)
+        out << "  \"" << kv.first << "\": [" << kv.second.first << ", " << kv.second.second << "]"
+            << (++n < m.size() ? ",\n" : "\n");
+    out << "}\n";
+    out.close();
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+void tune_begin(pic_handle* h)
+{
+    int64_t np = 0, cells = 0;
+    for (const auto& I : h->inst) {
+        cells += I.ncells;
+        for (int s = 0; s < I.nspecies; ++s) np += I.sp[s].capacity;
+    }
+    const int lp = (int)std::floor(std::log2((double)std::max<int64_t>(np, 1)));
+    const int lc = (int)std::floor(std::log2((double)std::max<int64_t>(cells / h->ninst, 1)));
+    char key[400];
+    std::snprintf(key, sizeof(key), "%s|%s|%s|p%d|c%d", h->gpu_name,
+                  h->precision == PIC_FP64 ? "fp64" : "fp32", h->any_mag ? "mag" : "nomag", lp, lc);
+    h->tune_key = key;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    const auto m = tune_cache_read();
+    const auto it = m.find(h->tune_key);
+    if (it != m.end()) {
+        if (h->tune_block && (it->second.first == 128 || it->second.first == 256 || it->second.first == 512))
+            set_block(h, it->second.first);
+        if (h->tune_sort && it->second.second > 0) h->sort_interval = it->second.second;
+        h->tune_block = h->tune_sort = false;
+        return;
+    }
+    h->tune_phase = h->tune_block ? 1 : 2;
+    h->tune_idx = 0;
+    h->tune_best = 1e300;
+    if (h->tune_phase == 1) set_block(h, kTuneBlocks[0]);
+    else h->sort_interval = kTuneSorts[0];
+}
+
+void tune_finish(pic_handle* h)
+{
+    h->tune_phase = 0;
+    h->tune_block = h->tune_sort = false;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto m = tune_cache_read();
+    m[h->tune_key] = {h->nt, h->sort_interval};
+    tune_cache_write(m);
+}
+
 }  // namespace
 
 extern "C" {
@@ -449,7 +601,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         return fail(nullptr, PIC_EINVAL, "pic_create: null config/out/instances or n_instances < 1");
     if (cfg->precision != PIC_FP32 && cfg->precision != PIC_FP64)
         return fail(nullptr, PIC_EINVAL, "precision must be PIC_FP32 or PIC_FP64");
-    if (cfg->sort_interval < 0) return fail(nullptr, PIC_EINVAL, "sort_interval must be >= 0");
+    if (cfg->sort_interval < -1) return fail(nullptr, PIC_EINVAL, "sort_interval must be >= -1");
     if (cfg->block != 0 && cfg->block != 128 && cfg->block != 256 && cfg->block != 512)
         return fail(nullptr, PIC_EINVAL, "block must be 0, 128, 256 or 512");
     for (int i = 0; i < cfg->n_instances; ++i) {
@@ -465,7 +617,9 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     };
     h->precision = cfg->precision;
     h->tsize = cfg->precision == PIC_FP64 ? 8 : 4;
-    h->sort_interval = cfg->sort_interval;
+    h->tune_sort = cfg->sort_interval < 0;
+    h->tune_block = cfg->block == 0;
+    h->sort_interval = h->tune_sort ? 20 : cfg->sort_interval;
     h->nt = cfg->block ? cfg->block : 256;
     h->ninst = cfg->n_instances;
     h->inst.assign(cfg->inst, cfg->inst + cfg->n_instances);
@@ -495,12 +649,21 @@ int pic_create(const pic_config* cfg, pic_handle** out)
             h->any_poisson = true;
         }
         ip.lambda = delta / (2.0 * (double)I.ncells * S * I.eps0);
+        // ionization events per step are at most the candidates of the projectile
+        // species: about capacity x P per step; reserve 4x that, at least 4096
         bool ionize = false;
         int64_t evcap = 0;
         for (int k = 0; k < I.nproc; ++k)
             if (I.proc[k].kind == PIC_PROC_IONIZE) {
                 ionize = true;
-                evcap = std::max<int64_t>(evcap, round_up(std::max<int64_t>(I.sp[I.proc[k].species].capacity, 1), kSegAlign));
+                const int sp = I.proc[k].species;
+                double numax = 0.0;
+                for (int q = 0; q < I.nproc; ++q)
+                    if (I.proc[q].species == sp) numax += I.proc[q].nu;
+                const double P = -std::expm1(-numax * I.dt);
+                const double cap = (double)std::max<int64_t>(I.sp[sp].capacity, 1);
+                const int64_t want = (int64_t)std::ceil(cap * std::min(1.0, 4.0 * P));
+                evcap = std::max<int64_t>(evcap, std::max<int64_t>(4096, want));
             }
         ip.ev_base = ev;
         ip.ev_cap = ionize ? evcap : 0;
@@ -552,9 +715,9 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         return bail(PIC_ECUDA);
     }
     h->sms = prop.multiProcessorCount;
-    const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, h->nt)
-                                             : move_blocks_per_sm_f32(h->any_mag, h->nt);
-    h->grid_move = h->sms * std::max(bps, 1);
+    std::snprintf(h->gpu_name, sizeof(h->gpu_name), "%s", prop.name);
+    set_block(h, h->nt);
+    if (h->tune_block || h->tune_sort) tune_begin(h);
 
     // device memory
     int rc = PIC_OK;
@@ -848,10 +1011,52 @@ int pic_step(pic_handle* h, int64_t nsteps)
     if (rc) return rc;
     if (nsteps < 0) return fail(h, PIC_EINVAL, "pic_step: nsteps < 0");
     if ((rc = ensure_fields(h))) return rc;
-    const int64_t K = h->sort_interval;
-    const bool graphs = h->graphs && !h->profiling && K > 0 && h->stream != nullptr;
     int64_t n = 0;
     while (n < nsteps) {
+        const int64_t K = h->sort_interval;
+        // autotuning: time one whole sort cycle per candidate on the real run
+        if (h->tune_phase && K > 0 && h->step_h % K == 0 && nsteps - n >= K) {
+            cudaEvent_t ea = take_event(h), eb = take_event(h);
+            CUDA_TRY(h, cudaEventRecord(ea, h->stream));
+            for (int64_t k = 0; k < K; ++k)
+                if ((rc = enqueue_step(h))) return rc;
+            CUDA_TRY(h, cudaEventRecord(eb, h->stream));
+            CUDA_TRY(h, cudaEventSynchronize(eb));
+            float ms = 0.f;
+            CUDA_TRY(h, cudaEventElapsedTime(&ms, ea, eb));
+            h->event_pool.push_back(ea);
+            h->event_pool.push_back(eb);
+            n += K;
+            const double per = ms / (double)K;
+            if (h->tune_phase == 1) {
+                if (per < h->tune_best) { h->tune_best = per; h->tune_best_val = h->nt; }
+                if (++h->tune_idx < 3) {
+                    set_block(h, kTuneBlocks[h->tune_idx]);
+                } else {
+                    set_block(h, h->tune_best_val);
+                    if (h->tune_sort) {
+                        h->tune_phase = 2;
+                        h->tune_idx = 0;
+                        h->tune_best = 1e300;
+                        h->sort_interval = kTuneSorts[0];
+                    } else {
+                        tune_finish(h);
+                    }
+                }
+            } else {
+                if (per < h->tune_best) { h->tune_best = per; h->tune_best_val = (int)K; }
+                if (++h->tune_idx < 4) {
+                    h->sort_interval = kTuneSorts[h->tune_idx];
+                } else {
+                    h->sort_interval = h->tune_best_val;
+                    tune_finish(h);
+                }
+            }
+            drop_graphs(h);
+            continue;
+        }
+        const bool graphs = h->graphs && !h->profiling && !h->tune_phase && K > 0 &&
+                            h->stream != nullptr;
         if (graphs && h->step_h % K == 0 && nsteps - n >= K) {
             if (!h->cycle[h->cur] && (rc = capture_cycle(h))) return rc;
             CUDA_TRY(h, cudaGraphLaunch(h->cycle[h->cur], h->stream));
@@ -1103,8 +1308,7 @@ int pic_destroy(pic_handle* h)
         cudaEventDestroy(t.b);
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
-    for (auto& g : h->cycle)
-        if (g) cudaGraphExecDestroy(g);
+    drop_graphs(h);
     for (void* p : h->allocs) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     cudaGetLastError();

@@ -121,7 +121,7 @@ def test_create_rejects_invalid_instances(L, mutate, needle):
 
 def test_create_rejects_invalid_config(L):
     I = capi.instance_struct(W.bounded_small(ncells=16, ppc=4))
-    for kw in (dict(precision=7), dict(block=100), dict(sort_interval=-1)):
+    for kw in (dict(precision=7), dict(block=100), dict(sort_interval=-2)):
         rc, h = _create(L, [I], **kw)
         assert rc == -1 and not h.value
     assert L.pic_create(None, None) == -1

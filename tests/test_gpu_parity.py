@@ -160,6 +160,32 @@ def test_graph_replay_equals_direct_launches():
     assert am["step"] == bm["step"] == 20
 
 
+def test_autotuner_changes_nothing_but_speed(tmp_path, monkeypatch):
+    """block = 0 and sort_interval = -1 make the library time its candidates on the first
+    steps of the run; the particles must come out exactly as with a fixed choice, and
+    the choice lands in the cache file."""
+    import json
+    ensure_built()
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("BITPIC_TUNE_CACHE", str(cache))
+    phys = W.bounded_small(ncells=128, ppc=50, seed=15)
+    loads = W.initial_load(phys, seed=15)
+    runs = []
+    for block, sort in ((0, -1), (256, 20)):
+        sim = capi.Sim(phys, precision=capi.FP64, sort_interval=sort, block=block)
+        sim.load_all(loads)
+        sim.step(400)
+        runs.append([by_id(sim.particles(0, s)) for s in range(2)])
+        sim.close()
+    for x, y in zip(*runs):
+        for k in x:
+            np.testing.assert_array_equal(x[k], y[k])
+    entries = json.loads(cache.read_text())
+    assert len(entries) == 1
+    (block, sort), = entries.values()
+    assert block in (128, 256, 512) and sort in (10, 20, 40, 80)
+
+
 def test_load_order_does_not_matter():
     phys = W.bounded_small(ncells=32, ppc=25, seed=9)
     loads = W.initial_load(phys, seed=9)
