@@ -229,13 +229,8 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
     other_n, other_ms = sim.kernel_time(3)
     kernels, _ = sim.kernel_time(4)
     sim.profile(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    p = torch.tensor([(live0 + live1) / 2 * steps], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    psteps = float(p.item())
+    from paper_2404_10270_gb300.sharding import combine_timing
+    ms_max, psteps = combine_timing(ms, (live0 + live1) / 2 * steps, device="cuda")
     hbm, src = peaks()
     bpp = bytes_per_particle or MOVER_BYTES[precision_name]
     per_launch_bytes = bpp * (live0 + live1) / 2
@@ -292,11 +287,15 @@ def measure_batched(args, stream, rank, world, local):
     set-up steps."""
     import concurrent.futures as cf
     from paper_2404_10270_gb300 import capi
-    phys = W.ensemble(n_instances=args.batched_instances)
+    from paper_2404_10270_gb300.sharding import shard_instances
+    allphys = W.ensemble(n_instances=args.batched_instances)
+    # N GPUs: the instances are partitioned by particle count (no exchange between them)
+    mine = shard_instances([p.n_particles() for p in allphys], world)[rank]
+    phys = [allphys[i] for i in mine]
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(8) as ex:
-        loads = list(ex.map(lambda ip: W.initial_load(ip[1], seed=ip[0] + 1 + 1000 * rank),
-                            enumerate(phys)))
+        loads = list(ex.map(lambda ip: W.initial_load(ip[1], seed=ip[0] + 1),
+                            zip(mine, phys)))
     n = sum(len(x) for ld in loads for x in ld)
     sim = capi.Sim(phys, precision=capi.FP32, sort_interval=-1, block=0, stream=stream)
     for i, ld in enumerate(loads):
@@ -310,7 +309,8 @@ def measure_batched(args, stream, rank, world, local):
     sim.close()
     return {"workload": "ensemble: %d instances, cells log-uniform [256, 8192], ppc [50, 400], "
                         "m_i/m_e {100, 1836}, B angle [0, 89] deg, |B| = 2, volume source, "
-                        "elastic + ionization + charge exchange, FP32 state" % len(phys),
+                        "elastic + ionization + charge exchange, FP32 state" % len(allphys),
+            "scaling": "strong (instances partitioned by particle count over the GPUs)",
             "particles_per_gpu": n, "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
             "steps": args.batched_steps, "roofline": r["roofline"], "gpu_launches": r["gpu_launches"],
             "clocks": r["clocks"], "kernel_ms": r["kernel_ms"], "setup_s": setup,
