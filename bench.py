@@ -237,7 +237,7 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
     avg_mover_ms = mover_ms / max(mover_n, 1)
     achieved = per_launch_bytes / (avg_mover_ms * 1e-3) / 1e9
     traffic = profiled_traffic("k_move", precision_name) if bytes_per_particle is None else None
-    if precision_name == "f64":
+    if precision_name == "f64" and bytes_per_particle is None:
         ach = FP64_OPS_PER_PARTICLE * (live0 + live1) / 2 / (avg_mover_ms * 1e-3)
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_INSTR_PER_S,
                 "unit": "FP64 instr/s", "frac": ach / FP64_PEAK_INSTR_PER_S,
@@ -318,6 +318,84 @@ def measure_batched(args, stream, rank, world, local):
                       % args.tune_steps}
 
 
+def measure_small(args, stream):
+    """The small bounded plasma (256 cells, 51,200 particles): launch-latency bound; the
+    step loop runs as one replayed CUDA graph per sort cycle."""
+    import torch
+    from paper_2404_10270_gb300 import capi
+    phys = W.bounded_small()
+    loads = W.initial_load(phys, seed=1)
+    out = {}
+    for name, prec in (("fp32", capi.FP32), ("fp64", capi.FP64)):
+        sim = capi.Sim(phys, precision=prec, sort_interval=20, block=256, stream=stream)
+        sim.load_all(loads)
+        sim.step(100)
+        sim.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = sum(sim.count(0, s) for s in range(2))
+        a.record()
+        sim.step(1000)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        n1 = sum(sim.count(0, s) for s in range(2))
+        sim.close()
+        out[name] = {"value": (n0 + n1) / 2 * 1000 / (ms * 1e-3), "unit": UNIT,
+                     "us_per_step": ms, "steps": 1000}
+    out["workload"] = "bounded_small: 256 cells, 100 ppc/species, 51,200 particles, 1000 steps"
+    return out
+
+
+def run_c5(args):
+    """The memory-filling ensemble sweep: the batched ensemble scaled to ~150 GB of FP64
+    particle state (two copies, 1.5x capacity), run in the FP64 and the FP32 form; for 16
+    sampled instances the density, potential and wall-flux errors against the oracle."""
+    import concurrent.futures as cf
+    import torch
+    from paper_2404_10270_gb300 import capi
+    from oracle.oracle import Oracle
+    __import__("__graft_entry__").build()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        probe = W.ensemble(n_instances=512)
+        per = sum(p.n_particles() for p in probe) / 512
+        n_inst = int(args.c5_gb * 1e9 / (per * 40 * 1.5 * 2))
+        phys = W.ensemble(n_instances=n_inst)
+        with cf.ThreadPoolExecutor(16) as ex:
+            loads = list(ex.map(lambda ip: W.initial_load(ip[1], seed=ip[0] + 1), enumerate(phys)))
+        n = sum(len(x) for ld in loads for x in ld)
+        sample = list(range(0, n_inst, max(1, n_inst // 16)))[:16]
+        res = {"instances": n_inst, "particles": n, "sampled": sample}
+        # magnetized movers move cell word, offset and three velocities each way:
+        # 2 x (4 + 8 + 24) B in FP64, 2 x (4 + 4 + 12) B in FP32
+        for name, prec, bpp in (("fp64", capi.FP64, 72), ("fp32", capi.FP32, 40)):
+            sim = capi.Sim(phys, precision=prec, sort_interval=20, block=256, stream=stream)
+            for i, ld in enumerate(loads):
+                sim.load_all(ld, inst=i)
+            r = measure_form(sim, phys, args.steps, args.warmup, n,
+                             "f64" if prec == capi.FP64 else "f32", 0, 1, 0, bytes_per_particle=bpp)
+            total = args.steps + args.warmup
+            errs = []
+            for i in sample:
+                g = sim.moments(i)
+                o = Oracle(phys[i])
+                o.load_all(loads[i])
+                o.step(total)
+                om = o.moments()
+                dscale = np.abs(om["density"]).max()
+                pscale = max(np.abs(om["phi"]).max(), 1e-300)
+                errs.append({"inst": i,
+                             "density": float(np.abs(g["density"] - om["density"]).max() / dscale),
+                             "phi": float(np.abs(g["phi"] - om["phi"]).max() / pscale),
+                             "wall_flux": int(np.abs(g["wall_count"] - om["wall_count"]).sum()),
+                             "live": int(np.abs(g["live"] - om["live"]).sum())})
+            sim.close()
+            res[name] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
+                         "roofline": r["roofline"], "errors_vs_oracle_after_%d_steps" % total: errs}
+        print(json.dumps({"c5": res}), flush=True)
+    return 0
+
+
 def _run_ours(args, stream, rank, world, local):
     import torch
     __import__("__graft_entry__").build()
@@ -389,6 +467,7 @@ def _run_ours(args, stream, rank, world, local):
     batched = None
     if not args.no_batched:
         batched = measure_batched(args, stream, rank, world, local)
+    small = measure_small(args, stream) if rank == 0 and not args.no_small else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -420,6 +499,7 @@ def _run_ours(args, stream, rank, world, local):
             "kernel_ms": res["kernel_ms"],
             "fp64_form": fp64,
             "batched": batched,
+            "small": small,
             "setup_s": setup_s,
         }
         print(json.dumps(line), flush=True)
@@ -458,6 +538,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--c5", action="store_true", help="run the ~150 GB ensemble sweep instead")
+    ap.add_argument("--c5-gb", type=float, default=150.0)
     ap.add_argument("--batched-instances", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=40)
     ap.add_argument("--tune-steps", type=int, default=300)
@@ -470,6 +553,8 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         return profile_case(args.precision)
+    if args.c5:
+        return run_c5(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -443,11 +443,13 @@ static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel)
  * collision candidate is a Bernoulli(P) sequence per particle; instead of one draw per
  * step the particle carries its clock: C steps to skip, and whether the next event
  * step is a candidate.  At an event step without a pending candidate (a test) the
- * draw COLLIDE(id, step) word 0 gives the candidate-free run g starting at this step:
- * g = 0 is a candidate now, 0 < g < 127 a candidate g steps later, g = 127 none in the
- * next 127 steps and a new test then.  A candidate selects its process with word 1 of
- * COLLIDE(id, step) of its own step; the step after a candidate is a test.
- * Returns 0 or < 0. */
+ * draw COLLIDE(id, step) word 0 gives the candidate-free run g starting at this step,
+ * cut at the next step that is a multiple of 127 (D steps away): g = 0 is a candidate
+ * now, 0 < g < D a candidate g steps later, g = D none before that step, which then
+ * tests again.  (The cut keeps the tests of all particles on the same steps, and by
+ * the memorylessness of the sequence changes nothing in its distribution.)  A
+ * candidate selects its process with word 1 of COLLIDE(id, step) of its own step; the
+ * step after a candidate is a test.  Returns 0 or < 0. */
 static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
 {
     if (!s->collides[sp]) return 0;
@@ -460,9 +462,15 @@ static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
     uint32_t w[4];
     draw(s, a->id[k], s->step, ORC_RNG_COLLIDE, w);
     if (!pending) {
-        const int g = gap_steps(s, sp, w[0]);
+        const int D = ORC_GAP_MAX - (int)(s->step % ORC_GAP_MAX);
+        int g = gap_steps(s, sp, w[0]);
+        if (g > D) g = D;
+        if (g == D) {
+            a->mcc[k] = (uint8_t)(D - 1);
+            return 0;
+        }
         if (g > 0) {
-            a->mcc[k] = g < ORC_GAP_MAX ? (uint8_t)((g - 1) | 0x80) : (uint8_t)(ORC_GAP_MAX - 1);
+            a->mcc[k] = (uint8_t)((g - 1) | 0x80);
             return 0;
         }
     }

@@ -32,6 +32,14 @@ namespace bitpic {
 #define BITPIC_MOVE_MIN_WARPS 48
 #endif
 constexpr int kMoveMinWarps = BITPIC_MOVE_MIN_WARPS;  // resident warps per SM the mover is built for
+#ifndef BITPIC_MOVE_MIN_WARPS64
+#define BITPIC_MOVE_MIN_WARPS64 24
+#endif
+constexpr int kMoveMinWarps64 = BITPIC_MOVE_MIN_WARPS64;  // the same for the FP64 form
+#ifndef BITPIC_MOVE_MIN_WARPS_MAG
+#define BITPIC_MOVE_MIN_WARPS_MAG 32
+#endif
+constexpr int kMoveMinWarpsMag = BITPIC_MOVE_MIN_WARPS_MAG;  // cap for the Boris (3V) variant
 constexpr int kDeadCell = -(1 << 30);
 
 struct MoveArgs {
@@ -62,6 +70,7 @@ struct MoveArgs {
 template <typename T> struct Prec;
 template <> struct Prec<float> {
     using Q = uint32_t;  // fixed-point charge of one particle (< 2^25)
+    static constexpr int min_warps = kMoveMinWarps;  // memory bound: as many warps as fit
     static __device__ __forceinline__ uint64_t qright(float f)
     {
         return (uint64_t)__float2uint_rn(f * 16777216.0f);
@@ -79,12 +88,38 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float log_(float x) { return logf(x); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+    static __device__ __forceinline__ bool finite(float x) { return isfinite(x); }
+    // move (Listing 7: x += nstep*vx with x the in-cell offset): f' = f + u, the integer
+    // part of f' moves the particle across cells; an f' - floor(f') that rounds up to 1
+    // (f' a tiny negative number) is renormalised to the next cell
+    static __device__ __forceinline__ void move(float& f, float u, int& j)
+    {
+        const float xn = f + u;
+        const float fl = floorf(xn);
+        f = xn - fl;
+        j += (int)fl;
+        if (f >= 1.0f) {
+            f = 0.0f;
+            j += 1;
+        }
+    }
 };
 template <> struct Prec<double> {
     using Q = uint64_t;  // fixed-point charge of one particle (< 2^49)
+    static constexpr int min_warps = kMoveMinWarps64;  // FP64-pipe bound: registers first
+    // rint(f 2^48) for f in [0, 1), ties to even, from the bits: f = m 2^(e-1075), so
+    // f 2^48 = m / 2^(1027-e) rounded to nearest even (integer ALU only).
     static __device__ __forceinline__ uint64_t qright(double f)
     {
-        return __double2ull_rn(f * 281474976710656.0);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(f);
+        const int e = (int)(b >> 52);
+        const int sh = 1027 - e;
+        if (b == 0ull || sh >= 64) return 0ull;
+        const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        unsigned long long q = m >> sh;
+        const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) q += 1ull;
+        return q;
     }
     static constexpr uint64_t S = 1ull << 48;
     static __device__ __forceinline__ double uni(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
@@ -97,6 +132,56 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+    // Finiteness from the exponent bits (integer ALU; the FP64 pipe is this form's limit).
+    static __device__ __forceinline__ bool finite(double x)
+    {
+        return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
+    }
+    // The same move as the float form with the same rounding: floor(f'), f' - floor(f')
+    // and the truncation.  For the common -1 < f' < 2 the floor is read from the bits,
+    // and the subtraction of 0 or -1 or 1 is done as the identical IEEE operation (or
+    // skipped when it is exact), which saves three of this form's FP64 instructions.
+    static __device__ __forceinline__ void move(double& f, double u, int& j)
+    {
+        const double xn = f + u;
+        const long long b = __double_as_longlong(xn);
+        const int e = (int)((b >> 52) & 0x7FF);
+        if (e < 1023) {                                  // |f'| < 1
+            if (b >= 0 || (b & 0x7FFFFFFFFFFFFFFFll) == 0) {
+                f = __longlong_as_double(b & 0x7FFFFFFFFFFFFFFFll);  // f' - 0 (-0 -> +0)
+                return;
+            }
+            double fk = xn + 1.0;                        // f' - (-1)
+            j -= 1;
+            if (fk >= 1.0) {
+                fk = 0.0;
+                j += 1;
+            }
+            f = fk;
+            return;
+        }
+        if (e == 1023 && b >= 0) {                       // 1 <= f' < 2: exact f' - 1
+            f = xn - 1.0;
+            j += 1;
+            return;
+        }
+        const double fl = floor(xn);
+        double fk = xn - fl;
+        j += (int)fl;
+        if (fk >= 1.0) {
+            fk = 0.0;
+            j += 1;
+        }
+        f = fk;
+    }
+};
+
+// Resident blocks per SM each mover variant is compiled for (its register budget).
+template <typename T, bool MAG, int NT>
+struct MoveOccupancy {
+    static constexpr int warps =
+        MAG && kMoveMinWarpsMag < Prec<T>::min_warps ? kMoveMinWarpsMag : Prec<T>::min_warps;
+    static constexpr int blocks = warps / (NT / 32) > 0 ? warps / (NT / 32) : 1;
 };
 
 __device__ __forceinline__ void ld4(const float* p, float v[4])
@@ -416,7 +501,7 @@ __device__ __noinline__ unsigned rare_events(const MoveArgs& a, const SegParams&
 // then each particle picks its two nodes by warp shuffle.  The loop over the quad is
 // free of calls; walls and collision candidates are flagged and handled out of line.
 template <typename T, int NT, bool MAG, bool MOVE>
-__global__ void __launch_bounds__(NT, kMoveMinWarps / (NT / 32))
+__global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
     using Q = typename Prec<T>::Q;
@@ -428,6 +513,8 @@ k_move(const __grid_constant__ MoveArgs a)
     T* const uzp = static_cast<T*>(a.uz);
     const T* const accp = static_cast<const T*>(a.accel);
     const int64_t step = MOVE ? *a.step : 0;
+    // steps to the next multiple of kGapMax, where every clock without a candidate tests
+    const int dgrid = kGapMax - (int)(step % kGapMax);
     const int64_t total = a.tile_start[a.nseg];
     const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
 
@@ -514,16 +601,9 @@ k_move(const __grid_constant__ MoveArgs a)
                     uy[k] = qy;
                     uz[k] = qz;
                 }
-                if (!isfinite(ux[k])) set_error(a.err, kErrNonFinite);
+                if (!Prec<T>::finite(ux[k])) set_error(a.err, kErrNonFinite);
                 // 3. move (Listing 7: x += nstep*vx, x the in-cell offset)
-                const T xn = fk + ux[k];
-                const T fl = Prec<T>::floor_(xn);
-                fk = xn - fl;
-                j += (int)fl;
-                if (fk >= T(1)) {  // xn a tiny negative number: f rounded up to 1
-                    fk = T(0);
-                    j += 1;
-                }
+                Prec<T>::move(fk, ux[k], j);
                 f[k] = fk;
                 // 4. walls (absorption and re-injection out of line)
                 if (j < 0 || j >= N) {
@@ -539,9 +619,11 @@ k_move(const __grid_constant__ MoveArgs a)
                 // 5. null collision.  The candidate steps of a particle form a
                 // Bernoulli(P) sequence; its clock counts the steps to skip before the
                 // next event step.  At an event step without a pending candidate (a
-                // test), Philox word 0 gives the candidate-free run g from this step:
-                // g = 0 candidate now, g < 127 a candidate g steps later, g = 127 none
-                // in the next 127 steps.  Candidates continue out of line.
+                // test), Philox word 0 gives the candidate-free run g from this step,
+                // cut at the next multiple of 127 (D steps away): g = 0 candidate now,
+                // g < D a candidate g steps later, g = D none before then.  The cut puts
+                // the tests of all particles on the same steps, so a warp runs them
+                // together.  Candidates continue out of line.
                 if (collides) {
                     if (clk & kClockCount) {
                         clk -= 1u;
@@ -549,16 +631,16 @@ k_move(const __grid_constant__ MoveArgs a)
                         candbits |= 1u << k;
                         clk = 0u;
                     } else {
-                        // a test step (about one step in 127): the id is read only here
+                        // a test step: the id is read only here
                         const uint32_t idk = __ldg(a.id + slot + k);
                         const uint4 w = draw(idk, step, kRngCollide, key0, key1);
-                        const int g = gap_steps(P.gap, w.x);
+                        const int g = min(gap_steps(P.gap, w.x), dgrid);
                         if (g == 0) {
                             candbits |= 1u << k;
                             clk = 0u;
                         } else {
-                            clk = g < kGapMax ? ((uint32_t)(g - 1) | kClockPending)
-                                              : (uint32_t)(kGapMax - 1);
+                            clk = g < dgrid ? ((uint32_t)(g - 1) | kClockPending)
+                                            : (uint32_t)(dgrid - 1);
                         }
                     }
                 }

@@ -26,7 +26,8 @@ import pytest
 
 from paper_2404_10270_gb300 import capi
 from paper_2404_10270_gb300 import workloads as W
-from tests.gpu_common import assert_same_clocks, by_id, ensure_built, requires_gpu
+from tests.gpu_common import (assert_same_clocks, by_id, ensure_built, ionization_errors,
+                              oracle_with_ionization_record, requires_gpu)
 
 pytestmark = [pytest.mark.gpu, requires_gpu]
 
@@ -51,42 +52,6 @@ def _run_batch(phys, loads, precision, steps, sample):
     return out
 
 
-def _oracle_with_ionization_record(phys, loads, steps):
-    """Oracle run that also returns the ids of every ionization participant: products
-    (ids beyond the load) and electrons that lost more than the threshold energy in one
-    step (the parents)."""
-    from oracle.oracle import Oracle
-    o = Oracle(phys)
-    o.load_all(loads)
-    n0 = sum(len(x) for x in loads)
-    eiz = max([q.threshold for q in phys.processes if q.kind == W.PROC_IONIZE] + [0.0])
-    m_e = phys.species[0].mass
-    prev = by_id(o.particles(0))
-    parents = set()
-    for _ in range(steps):
-        o.step(1)
-        cur = by_id(o.particles(0))
-        old = cur["id"] < n0
-        idx = np.searchsorted(prev["id"], cur["id"][old])
-        e0 = 0.5 * m_e * (prev["vx"][idx] ** 2 + prev["vy"][idx] ** 2 + prev["vz"][idx] ** 2)
-        e1 = 0.5 * m_e * (cur["vx"][old] ** 2 + cur["vy"][old] ** 2 + cur["vz"][old] ** 2)
-        parents.update(cur["id"][old][e0 - e1 > eiz * (1 - 1e-6)].tolist())
-        prev = cur
-    return [o.particles(s) for s in range(2)], o.moments(), n0, parents
-
-
-def _errors(phys, g, o, s):
-    g, o = by_id(g), by_id(o)
-    np.testing.assert_array_equal(g["id"], o["id"])
-    xg = (g["cell"] + g["off"]) * phys.dx
-    xo = (o["cell"] + o["off"]) * phys.dx
-    ex = np.abs(xg - xo) / phys.length
-    vth = (phys.species[s].temperature / phys.species[s].mass) ** 0.5
-    dv = np.sqrt((g["vx"] - o["vx"]) ** 2 + (g["vy"] - o["vy"]) ** 2 + (g["vz"] - o["vz"]) ** 2)
-    vref = np.sqrt(o["vx"] ** 2 + o["vy"] ** 2 + o["vz"] ** 2)
-    return o["id"], ex, dv / np.maximum(vref, vth)
-
-
 @pytest.mark.parametrize("precision,steps,tol", [(capi.FP32, 10, 1e-5), (capi.FP64, 20, 1e-12)])
 def test_ensemble_sampled_instances_match_oracle(ensemble, precision, steps, tol):
     ensure_built()
@@ -95,15 +60,14 @@ def test_ensemble_sampled_instances_match_oracle(ensemble, precision, steps, tol
     got = _run_batch(phys, loads, precision, steps, sample)
     for i in sample:
         g, gm = got[i]
-        o, om, n0, parents = _oracle_with_ionization_record(phys[i], loads[i], steps)
+        o, om, n0, parents = oracle_with_ionization_record(phys[i], loads[i], steps)
         np.testing.assert_array_equal(gm["live"], om["live"])
         if precision == capi.FP64:
             np.testing.assert_array_equal(gm["collisions"], om["collisions"])
             np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
         t = tol if precision == capi.FP32 else tol * max(1.0, (phys[i].ncells / 256.0) ** 2)
         for s in range(2):
-            ids, ex, ev = _errors(phys[i], g[s], o[s], s)
-            involved = (ids >= n0) | np.isin(ids, np.fromiter(parents, np.int64, len(parents)))
+            ids, ex, ev, involved = ionization_errors(phys[i], g[s], o[s], s, n0, parents)
             assert ex.max() < t, (i, s, ex.max())
             assert ev[~involved].max(initial=0.0) < t, (i, s, ev[~involved].max())
             assert ev[involved].max(initial=0.0) < 100 * t, (i, s, ev[involved].max())

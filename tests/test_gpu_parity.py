@@ -312,3 +312,35 @@ def test_capacity_overflow_is_reported():
         sim.sync()
     assert e.value.code == -4
     sim.close()
+
+
+@pytest.mark.parametrize("precision,steps,tol", [(capi.FP64, 100, 1e-12), (capi.FP32, 10, 1e-5)])
+def test_magnetized_source_full_size(precision, steps, tol):
+    """The magnetized workload at its full size: 4096 cells x 200 particles/cell/species
+    (1,638,400 particles), oblique B, volume source, elastic + ionization + charge
+    exchange.  FP64 bound 1e-12 x max(1, (N/256)^2) (the oracle's Thomas conditioning);
+    ionization participants at 100x (ill-conditioned near-threshold energy split)."""
+    from tests.gpu_common import ionization_errors, oracle_with_ionization_record
+    ensure_built()
+    phys = W.magnetized_source(seed=1)
+    loads = W.initial_load(phys, seed=1)
+    sim = capi.Sim(phys, precision=precision, sort_interval=20)
+    sim.load_all(loads)
+    sim.step(steps)
+    g = [sim.particles(0, s) for s in range(2)]
+    gm = sim.moments(0)
+    sim.close()
+    o, om, n0, parents = oracle_with_ionization_record(phys, loads, steps)
+    np.testing.assert_array_equal(gm["live"], om["live"])
+    if precision == capi.FP64:
+        np.testing.assert_array_equal(gm["collisions"], om["collisions"])
+        np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
+        t = tol * max(1.0, (phys.ncells / 256.0) ** 2)
+    else:
+        t = tol
+    for s in range(2):
+        ids, ex, ev, involved = ionization_errors(phys, g[s], o[s], s, n0, parents)
+        assert ex.max() < t, (s, ex.max())
+        assert ev[~involved].max(initial=0.0) < t, (s, ev[~involved].max())
+        assert ev[involved].max(initial=0.0) < 100 * t, (s, ev[involved].max())
+    assert_same_clocks(g, o)
