@@ -38,11 +38,12 @@ UNIT = "particle-steps/s"
 # cell word (4) off (8) vx (8) in FP64.  The id is read only at collision-clock events
 # (about one step in 127) and vy/vz only on collisions and wall hits.
 MOVER_BYTES = {"f32": 24, "f64": 40}
-# The FP64 form is bound by the FP64 pipe: per particle-step its hot path issues 12 FP64
-# instructions (gather 3, push 1, move 3, truncation 1, f >= 1 test 1, fixed-point charge
-# 2, finiteness test 1).  Peak: 2 FP64 instructions per SM per cycle (ncu's
-# peak_sustained of the dfma pipe on this GPU) x 152 SMs x 2.07 GHz.
-FP64_OPS_PER_PARTICLE = 12
+# The FP64 form is bound by the FP64 pipe: per particle-step its hot path issues 4 FP64
+# instructions (gather: one fused multiply-add on the node pair; push: one add; move:
+# f + u, and the one add that takes f' - floor(f') with the floor read from the bits).
+# Peak: 2 FP64 instructions per SM per cycle (ncu's peak_sustained of the dfma pipe on
+# this GPU) x 152 SMs x 2.07 GHz.
+FP64_OPS_PER_PARTICLE = 4
 FP64_PEAK_INSTR_PER_S = 2 * 152 * 2.07e9
 
 
@@ -327,7 +328,8 @@ def measure_small(args, stream):
     loads = W.initial_load(phys, seed=1)
     out = {}
     for name, prec in (("fp32", capi.FP32), ("fp64", capi.FP64)):
-        sim = capi.Sim(phys, precision=prec, sort_interval=20, block=256, stream=stream)
+        sim = capi.Sim(phys, precision=prec, sort_interval=20, block=256,
+                           stream=stream)
         sim.load_all(loads)
         sim.step(100)
         sim.sync()
@@ -369,7 +371,8 @@ def run_c5(args):
         # magnetized movers move cell word, offset and three velocities each way:
         # 2 x (4 + 8 + 24) B in FP64, 2 x (4 + 4 + 12) B in FP32
         for name, prec, bpp in (("fp64", capi.FP64, 72), ("fp32", capi.FP32, 40)):
-            sim = capi.Sim(phys, precision=prec, sort_interval=20, block=256, stream=stream)
+            sim = capi.Sim(phys, precision=prec, sort_interval=20, block=256,
+                           stream=stream.cuda_stream)
             for i, ld in enumerate(loads):
                 sim.load_all(ld, inst=i)
             r = measure_form(sim, phys, args.steps, args.warmup, n,

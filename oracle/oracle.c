@@ -8,7 +8,8 @@
  * cycle, Section 2 and Fig. "diagram"; the gather/update of Listing 7):
  *   for every live particle, species by species, in ascending id order:
  *     1. gather   a = A[j] + f*(A[j+1]-A[j])        (Listing 7, moveb(): linear gather
- *                                                    of the pre-scaled acceleration A)
+ *                                                    of the pre-scaled acceleration A;
+ *                                                    f*(...) + A[j] is one fma)
  *     2. push     u += a (B = 0), or the Boris rotation (B != 0)   (Section 2, mover)
  *     3. move     f += u; the integer part of f moves the particle across cells
  *                 (Listing 7: x += nstep*vx with x the in-cell offset)
@@ -28,7 +29,9 @@
  * integer thresholds, and whose process selection uses fixed integer slots; linear
  * (CIC) weights;
  * Gauss's law over the half cell at the wall nodes.  All arithmetic is FP64 and the
- * file is compiled without floating-point contraction.
+ * file is compiled without floating-point contraction; the one fused operation is
+ * the gather's explicit fma() (the paper does not fix how its product-sum rounds;
+ * a C compiler on FMA hardware contracts it to one rounding).
  */
 #include "oracle.h"
 
@@ -589,8 +592,9 @@ static int one_step(orc_sim* s)
             if (!a->alive[k]) continue;
             int j = a->cell[k];
             double f = a->off[k];
-            /* 1. gather (Listing 7) */
-            const double acc = A[j] + f * (A[j + 1] - A[j]);
+            /* 1. gather (Listing 7): A[j] + f (A[j+1] - A[j]), the product and the sum
+             *    rounded once (fused multiply-add) */
+            const double acc = fma(f, A[j + 1] - A[j], A[j]);
             /* 2. push */
             if (!s->has_B) {
                 a->ux[k] = a->ux[k] + acc;

@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {
     "mover_f32.cu": [],
     "mover_f64.cu": ["-fmad=false"],
+    "events.cu": ["-fmad=false"],
     "field.cu": ["-fmad=false"],
     "sort.cu": ["-fmad=false"],
     "io.cu": ["-fmad=false"],

@@ -9,9 +9,10 @@
 //     empty.  Every (instance, species) pair owns one contiguous segment whose base
 //     and capacity are multiples of 64 slots, so 128-bit loads of four particles
 //     never straddle segments.
-//   * per segment, node arrays of ncells+1 entries: the pre-scaled acceleration
-//     A = c_s E (type T) used by the gather, and the fixed-point charge deposit
-//     (uint64, two copies: the one being accumulated and the last complete one).
+//   * per segment, node arrays of ncells+1 entries: the pre-scaled acceleration as
+//     pairs (A_j, A_{j+1} - A_j) of type T, A = c_s E, which the gather reads with one
+//     vector load, and the fixed-point charge deposit (uint64, two copies: the one
+//     being accumulated and the last complete one).
 //   * per instance, E on the nodes (double) and scratch for the field solve.
 #pragma once
 #include <cstdint>
@@ -93,6 +94,17 @@ struct InstParams {
     double lambda;         // E = lambda * G (integer field numerator G)
     int32_t z[kMaxSpecies]; // charge q_s w_s in integer multiples of the unit delta
 };
+
+// A particle the mover leaves to the event kernel (a null-collision candidate or a
+// wall hit), packed in 64 bits: kind in bits 0-1, segment in bits 2-23, store slot
+// in bits 24-63.
+enum : uint32_t { kRareCandidate = 0, kRareWallLow = 1, kRareWallHigh = 2 };
+constexpr int kRareSegBits = 22;
+constexpr int kMaxSegments = 1 << kRareSegBits;
+__host__ __device__ __forceinline__ uint64_t rare_pack(int64_t slot, int seg, uint32_t kind)
+{
+    return ((uint64_t)slot << 24) | ((uint64_t)(uint32_t)seg << 2) | (uint64_t)kind;
+}
 
 struct Event {            // one ionization event awaiting child ids
     uint32_t parent;

@@ -65,6 +65,7 @@ struct pic_handle {
     std::vector<SegParams> segh;
     std::vector<InstParams> insth;
     int64_t total_cap = 0, seg_nodes = 0, inst_nodes = 0, max_cap = 0, ev_total = 0;
+    int64_t rare_cap = 0;  // entries of the per-step rare-event queue
     int max_nodes = 0;
     bool any_poisson = false, any_mag = false, any_ionize = false;
 
@@ -86,6 +87,9 @@ struct pic_handle {
                        *next_id = nullptr;
     double* wall_energy = nullptr;
     Event* events = nullptr;
+    uint64_t* rare = nullptr;
+    unsigned long long* rare_count = nullptr;
+    int grid_events = 0;
     unsigned* err = nullptr;
     int64_t* step_d = nullptr;
     double *kin = nullptr, *phi_d = nullptr;
@@ -331,6 +335,9 @@ MoveArgs move_args(pic_handle* h)
     a.ev_count = h->ev_count;
     a.err = h->err;
     a.step = h->step_d;
+    a.rare = h->rare;
+    a.rare_count = h->rare_count;
+    a.rare_cap = h->rare_cap;
     return a;
 }
 
@@ -344,6 +351,7 @@ FieldArgs field_args(pic_handle* h)
     f.dep = h->dep;
     f.dep_last = h->dep_last;
     f.accel = h->accel;
+    f.seg_nodes = h->seg_nodes;
     f.precision = h->precision;
     f.E = h->E;
     f.UN = h->UN;
@@ -361,12 +369,19 @@ int launch_move(pic_handle* h, bool move)
 {
     const MoveArgs a = move_args(h);
     const bool mag = move && h->any_mag;
-    Span sp(h, 0);
-    h->kernels += 1;
-    const cudaError_t e = h->precision == PIC_FP64
-                              ? launch_move_f64(a, mag, move, h->nt, h->grid_move, h->stream)
-                              : launch_move_f32(a, mag, move, h->nt, h->grid_move, h->stream);
-    CUDA_TRY(h, e);
+    {
+        Span sp(h, 0);
+        h->kernels += 1;
+        const cudaError_t e = h->precision == PIC_FP64
+                                  ? launch_move_f64(a, mag, move, h->nt, h->grid_move, h->stream)
+                                  : launch_move_f32(a, mag, move, h->nt, h->grid_move, h->stream);
+        CUDA_TRY(h, e);
+    }
+    if (move) {
+        Span se(h, 3);
+        h->kernels += 1;
+        CUDA_TRY(h, launch_events(a, h->precision, h->grid_events, h->stream));
+    }
     return PIC_OK;
 }
 
@@ -374,7 +389,8 @@ int launch_tiles_h(pic_handle* h)
 {
     Span sp(h, 3);
     h->kernels += 1;
-    CUDA_TRY(h, launch_tiles(h->segd, h->seg_n, h->seg_nmove, h->tile_start, h->nseg, 32, h->stream));
+    CUDA_TRY(h, launch_tiles(h->segd, h->seg_n, h->seg_nmove, h->tile_start, h->nseg, 32,
+                             h->rare_count, h->stream));
     return PIC_OK;
 }
 
@@ -422,7 +438,7 @@ int do_sort(pic_handle* h)
     a.max_cap = h->max_cap;
     a.max_cells = h->max_nodes - 1;
     h->kernels += 4;
-    CUDA_TRY(h, launch_sort(a, h->nt, h->grid_move, h->stream));
+    CUDA_TRY(h, launch_sort(a, h->nt, h->sms, h->stream));
     h->cur = 1 - h->cur;
     return PIC_OK;
 }
@@ -439,6 +455,7 @@ int sync_check(pic_handle* h)
     if (e & kErrInput) { code = PIC_EINVAL; msg = "loaded particle with cell outside [0, ncells) or offset outside [0, 1)"; }
     else if (e & kErrCapacity) { code = PIC_ECAPACITY; msg = "particle creation overflowed a species segment, the event buffer or the 32-bit ids"; }
     else if (e & kErrNonFinite) { code = PIC_ENONFINITE; msg = "a particle velocity became non-finite"; }
+    else if (e & kErrEvents) { code = PIC_ECAPACITY; msg = "the rare-event queue of a step (wall hits and collision candidates) overflowed"; }
     else if (e & kErrTimeout) { code = PIC_ETIMEOUT; msg = "a bounded device wait ran out"; }
     h->state = code;
     h->last_error = msg;
@@ -687,6 +704,16 @@ int pic_create(const pic_config* cfg, pic_handle** out)
             slot += P.cap;
             snode += round_up(I.ncells + 1, 4);
             h->max_cap = std::max(h->max_cap, P.cap);
+            // rare-event queue: the collision candidates of a step (about cap x P;
+            // 4x that is reserved) and the wall hits (a sixteenth of the segment)
+            {
+                double numax = 0.0;
+                for (int q = 0; q < I.nproc; ++q)
+                    if (I.proc[q].species == s) numax += I.proc[q].nu;
+                const double Pc = -std::expm1(-numax * I.dt);
+                const double frac = std::min(1.0, 4.0 * Pc + (I.bc == PIC_BC_PERIODIC ? 0.0 : 1.0 / 16.0));
+                h->rare_cap += (int64_t)std::ceil((double)P.cap * frac);
+            }
             h->segh.push_back(P);
         }
         inode += I.ncells + 1;
@@ -694,6 +721,11 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         h->insth.push_back(ip);
     }
     h->nseg = (int)h->segh.size();
+    if (h->nseg >= kMaxSegments) {
+        h->last_error = "too many (instance, species) segments: at most " + std::to_string(kMaxSegments - 1);
+        return bail(PIC_EINVAL);
+    }
+    h->rare_cap = std::min<int64_t>(h->rare_cap + 65536, std::max<int64_t>(slot, 65536));
     h->total_cap = slot;
     h->seg_nodes = snode;
     h->inst_nodes = inode;
@@ -715,6 +747,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         return bail(PIC_ECUDA);
     }
     h->sms = prop.multiProcessorCount;
+    h->grid_events = (int)std::min<int64_t>((h->rare_cap + 127) / 128, (int64_t)16 * h->sms);
     std::snprintf(h->gpu_name, sizeof(h->gpu_name), "%s", prop.name);
     set_block(h, h->nt);
     if (h->tune_block || h->tune_sort) tune_begin(h);
@@ -734,7 +767,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         st.off = o; st.ux = x; st.uy = y; st.uz = z;
     }
     char* acc = nullptr;
-    if (rc == PIC_OK) rc = dalloc(h, &acc, (size_t)snode * T);
+    if (rc == PIC_OK) rc = dalloc(h, &acc, (size_t)snode * 2 * T);  // (A_j, A_{j+1} - A_j) pairs
     h->accel = acc;
     if (rc == PIC_OK) rc = dalloc(h, &h->dep, (size_t)snode);
     if (rc == PIC_OK) rc = dalloc(h, &h->dep_last, (size_t)snode);
@@ -759,6 +792,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->collisions, (size_t)h->ninst * kMaxProc);
     if (rc == PIC_OK) rc = dalloc(h, &h->events, (size_t)std::max<int64_t>(ev, 1));
     if (rc == PIC_OK) rc = dalloc(h, &h->ev_count, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->rare, (size_t)h->rare_cap);
+    if (rc == PIC_OK) rc = dalloc(h, &h->rare_count, 1);
     if (rc == PIC_OK) rc = dalloc(h, &h->next_id, (size_t)h->ninst);
     if (rc == PIC_OK) rc = dalloc(h, &h->err, 1);
     if (rc == PIC_OK) rc = dalloc(h, &h->step_d, 1);
@@ -776,7 +811,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         if (e == cudaSuccess) e = z(h->st[b].id, (size_t)slot * 4);
         if (e == cudaSuccess) e = launch_fill_i32(h->st[b].cell, 0, slot, -1, s);
     }
-    if (e == cudaSuccess) e = z(h->accel, (size_t)snode * T);
+    if (e == cudaSuccess) e = z(h->accel, (size_t)snode * 2 * T);
+    if (e == cudaSuccess) e = z(h->rare_count, 8);
     if (e == cudaSuccess) e = z(h->dep, (size_t)snode * 8);
     if (e == cudaSuccess) e = z(h->dep_last, (size_t)snode * 8);
     if (e == cudaSuccess) e = z(h->E, (size_t)inode * 8);
@@ -808,7 +844,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     // constant fields: none (A = 0) or a uniform external field
     if (e == cudaSuccess) {
         std::vector<double> Eh((size_t)inode, 0.0);
-        std::vector<char> Ah((size_t)snode * T, 0);
+        std::vector<char> Ah((size_t)snode * 2 * T, 0);  // pairs (A, 0): a uniform field
         for (int i = 0; i < h->ninst; ++i) {
             const pic_instance& I = h->inst[i];
             if (I.field != PIC_FIELD_EXTERNAL) continue;
@@ -817,8 +853,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
                 const SegParams& P = h->segh[h->insth[i].seg0 + k];
                 for (int j = 0; j <= I.ncells; ++j) {
                     const double a = P.accel * I.E_ext;
-                    if (T == 8) reinterpret_cast<double*>(Ah.data())[P.node + j] = a;
-                    else reinterpret_cast<float*>(Ah.data())[P.node + j] = (float)a;
+                    if (T == 8) reinterpret_cast<double*>(Ah.data())[2 * (P.node + j)] = a;
+                    else reinterpret_cast<float*>(Ah.data())[2 * (P.node + j)] = (float)a;
                 }
             }
         }

@@ -1,0 +1,216 @@
+// events.cuh -- the rare events of a time step, worked through after the mover:
+// null-collision candidates (Section 2: the MCC step of the PIC cycle; elastic,
+// charge-exchange and ionization kinematics) and particles that left through an
+// absorbing or source wall (flux and energy counters, re-injection of the volume
+// source).  The mover queues them (rare_pack) so that its own loop stays call-free;
+// here one thread takes one queued particle.  Collisions change only velocities, so
+// the mover has already deposited a candidate; a re-injected particle and the
+// children of an ionization are deposited here.  Everything this kernel adds is an
+// integer sum or keyed by particle id and step, so the order of the queue does not
+// change any result.
+#pragma once
+
+#include "mover.cuh"
+
+namespace bitpic {
+
+// Unit vector uniform on the sphere, polar axis x (the wall normal).
+template <typename T>
+__device__ __forceinline__ void iso_dir(uint32_t w0, uint32_t w1, T n[3])
+{
+    const T ct = T(1) - T(2) * Prec<T>::uni(w0);
+    const T st = Prec<T>::sqrt_(T(1) - ct * ct);
+    T sp, cp;
+    Prec<T>::sincos2pi(Prec<T>::uni(w1), &sp, &cp);
+    n[0] = ct;
+    n[1] = st * cp;
+    n[2] = st * sp;
+}
+
+// Box-Muller (1958).
+template <typename T>
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z1)
+{
+    const T r = Prec<T>::sqrt_(T(-2) * Prec<T>::log_(Prec<T>::uni(wa)));
+    T s, c;
+    Prec<T>::sincos2pi(Prec<T>::uni(wb), &s, &c);
+    *z0 = r * c;
+    *z1 = r * s;
+}
+
+// A null-collision candidate of one particle (velocity u in cells/step, after the
+// move): process slot from the selection word `wsel`, energy threshold (below it the
+// event is a null collision), kinematics.  Returns true when u changed.  Ionization
+// appends two particles.
+template <typename T>
+__device__ __forceinline__ bool collide(const MoveArgs& a, const SegParams& P, int s,
+                                     uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
+                                     T& uz, uint32_t wsel)
+{
+    int q = -1;
+    for (int k = 0; k < P.nproc; ++k)
+        if ((uint64_t)wsel < P.slot_end[k]) { q = k; break; }
+    if (q < 0) return false;
+    const T u2 = ux * ux + uy * uy + uz * uz;
+    if (!(u2 >= (T)P.thr_u2[q])) return false;  // below threshold: null event
+    const int kind = P.kind[q];
+    if (kind == PIC_PROC_ELASTIC) {
+        const uint4 r = draw(id, step, kRngScatter, P.key0, P.key1);
+        T n[3];
+        iso_dir<T>(r.x, r.y, n);
+        const T speed = Prec<T>::sqrt_(u2);
+        if (speed > T(0)) {
+            const T cchi = (ux * n[0] + uy * n[1] + uz * n[2]) / speed;
+            const T fac = Prec<T>::sqrt_(T(1) - T(2) * (T)P.mratio * (T(1) - cchi));
+            const T sp2 = speed * fac;
+            ux = sp2 * n[0];
+            uy = sp2 * n[1];
+            uz = sp2 * n[2];
+        }
+    } else if (kind == PIC_PROC_CX) {
+        const uint4 r = draw(id, step, kRngMaxwell, P.key0, P.key1);
+        T z0, z1, z2, z3;
+        box_muller<T>(r.x, r.y, &z0, &z1);
+        box_muller<T>(r.z, r.w, &z2, &z3);
+        const T vn = (T)P.vneutral;
+        ux = z0 * vn;
+        uy = z1 * vn;
+        uz = z2 * vn;
+    } else {  // PIC_PROC_IONIZE
+        const T us = Prec<T>::sqrt_(T(0.5) * (u2 - (T)P.thr_u2[q]));
+        T n1[3], n2[3];
+        const uint4 r1 = draw(id, step, kRngScatter, P.key0, P.key1);
+        iso_dir<T>(r1.x, r1.y, n1);
+        const uint4 r2 = draw(id, step, kRngIonizeE, P.key0, P.key1);
+        iso_dir<T>(r2.x, r2.y, n2);
+        const uint4 ri = draw(id, step, kRngIonizeI, P.key0, P.key1);
+        T z0, z1, z2, z3;
+        box_muller<T>(ri.x, ri.y, &z0, &z1);
+        box_muller<T>(ri.z, ri.w, &z2, &z3);
+        ux = us * n1[0];
+        uy = us * n1[1];
+        uz = us * n1[2];
+        // append the new electron (this segment) and the new ion (product segment)
+        const int si = P.product[q];
+        const SegParams& Pi = a.seg[si];
+        const unsigned long long ke = atomicAdd(a.seg_n + s, 1ull);
+        const unsigned long long ki = atomicAdd(a.seg_n + si, 1ull);
+        const InstParams& I = a.inst[P.inst];
+        const unsigned long long ev = atomicAdd(a.ev_count + P.inst, 1ull);
+        if (ke >= (unsigned long long)P.cap || ki >= (unsigned long long)Pi.cap ||
+            ev >= (unsigned long long)I.ev_cap) {
+            set_error(a.err, kErrCapacity);
+        } else {
+            const T vn = (T)P.vneutral;
+            const int64_t ge = P.base + (int64_t)ke, gi = Pi.base + (int64_t)ki;
+            T* off = static_cast<T*>(a.off);
+            T* vx = static_cast<T*>(a.ux);
+            T* vy = static_cast<T*>(a.uy);
+            T* vz = static_cast<T*>(a.uz);
+            a.cell[ge] = j; off[ge] = f;
+            vx[ge] = us * n2[0]; vy[ge] = us * n2[1]; vz[ge] = us * n2[2];
+            a.id[ge] = 0xFFFFFFFFu;
+            a.cell[gi] = j; off[gi] = f;
+            vx[gi] = z0 * vn; vy[gi] = z1 * vn; vz[gi] = z2 * vn;
+            a.id[gi] = 0xFFFFFFFFu;
+            Event e;
+            e.parent = id;
+            e.pad = 0;
+            e.slot_e = ge;
+            e.slot_i = gi;
+            a.events[I.ev_base + (int64_t)ev] = e;
+            atomicAdd(a.seg_live + s, 1ull);
+            atomicAdd(a.seg_live + si, 1ull);
+            // the children's charge joins this step's deposit
+            const uint64_t qr = Prec<T>::qright(f), ql = Prec<T>::S - qr;
+            atomicAdd(a.dep + P.node + j, (unsigned long long)ql);
+            atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
+            atomicAdd(a.dep + Pi.node + j, (unsigned long long)ql);
+            atomicAdd(a.dep + Pi.node + j + 1, (unsigned long long)qr);
+        }
+    }
+    atomicAdd(a.collisions + (int64_t)P.inst * kMaxProc + P.proc[q], 1ull);
+    return true;
+}
+
+// Wall phase for a particle that left [0, N) (rare): counts and energy of the
+// absorbed particle, then either absorption (returns 2), or volume re-injection with a
+// new position and Maxwellian velocity (returns 1).  Periodic walls are handled inline.
+template <typename T>
+__device__ __forceinline__ int wall_event(const MoveArgs& a, const SegParams& P, int s, uint32_t id,
+                                       int64_t step, int& j, T& f, T& ux, T& uy, T& uz)
+{
+    const int wall = j < 0 ? 0 : 1;
+    const double u2 = (double)ux * (double)ux + (double)uy * (double)uy + (double)uz * (double)uz;
+    atomicAdd(a.wall_count + 2 * s + wall, 1ull);
+    atomicAdd(a.wall_energy + 2 * s + wall, P.kefac * u2);
+    if (P.bc != PIC_BC_SOURCE) {
+        atomicAdd(a.seg_live + s, ~0ull);  // -1
+        return 2;
+    }
+    const int N = P.ncells;
+    const uint4 r = draw(id, step, kRngInjectA, P.key0, P.key1);
+    const uint4 q2 = draw(id, step, kRngInjectB, P.key0, P.key1);
+    const T x = Prec<T>::uni(r.x) * (T)N;
+    const T fx = Prec<T>::floor_(x);
+    j = (int)fx;
+    f = x - fx;
+    if (j >= N) {
+        j = N - 1;
+        f = T(0);
+    }
+    T z0, z1, z2, z3;
+    box_muller<T>(r.y, r.z, &z0, &z1);
+    box_muller<T>(q2.x, q2.y, &z2, &z3);
+    const T vi = (T)P.vinj;
+    ux = z0 * vi;
+    uy = z1 * vi;
+    uz = z2 * vi;
+    return 1;
+}
+
+// One thread per queued particle (grid-stride over this step's queue).
+template <typename T>
+__global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs a)
+{
+    const unsigned long long n = min(*a.rare_count, (unsigned long long)a.rare_cap);
+    const int64_t step = *a.step;
+    T* const offp = static_cast<T*>(a.off);
+    T* const uxp = static_cast<T*>(a.ux);
+    T* const uyp = static_cast<T*>(a.uy);
+    T* const uzp = static_cast<T*>(a.uz);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint64_t e = a.rare[i];
+        const uint32_t kind = (uint32_t)(e & 3u);
+        const int s = (int)((e >> 2) & (uint64_t)(kMaxSegments - 1));
+        const int64_t slot = (int64_t)(e >> 24);
+        const SegParams& P = a.seg[s];
+        const uint32_t id = a.id[slot];
+        T f = offp[slot], vx = uxp[slot], vy = uyp[slot], vz = uzp[slot];
+        if (kind == kRareCandidate) {
+            const int j = (int)((uint32_t)a.cell[slot] & kCellMask);
+            const uint4 w = draw(id, step, kRngCollide, P.key0, P.key1);
+            if (collide<T>(a, P, s, id, step, j, f, vx, vy, vz, w.y)) {
+                uxp[slot] = vx;
+                uyp[slot] = vy;
+                uzp[slot] = vz;
+            }
+        } else {
+            int j = kind == kRareWallLow ? -1 : P.ncells;
+            if (wall_event<T>(a, P, s, id, step, j, f, vx, vy, vz) == 1) {
+                // re-injected: back in the store with a fresh clock, deposited here
+                a.cell[slot] = j;
+                offp[slot] = f;
+                uxp[slot] = vx;
+                uyp[slot] = vy;
+                uzp[slot] = vz;
+                const uint64_t qr = Prec<T>::qright(f);
+                atomicAdd(a.dep + P.node + j, (unsigned long long)(Prec<T>::S - qr));
+                atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
+            }
+        }
+    }
+}
+
+}  // namespace bitpic

@@ -14,6 +14,8 @@
 // (Gauss's law over the half cell at each wall).  This is the tridiagonal solve the
 // paper names, carried out as one prefix sum and one weighted sum, so it is
 // independent of launch geometry and rounds only once, at the conversion to FP64.
+#include <algorithm>
+
 #include "kernels.h"
 #include "mover.cuh"
 
@@ -213,10 +215,22 @@ __global__ void __launch_bounds__(kChunkThreads) k_field_emit(const FieldArgs f,
         f.E[I.inode + j] = E;
         for (int k = 0; k < I.nseg; ++k) {
             const SegParams& P = f.seg[I.seg0 + k];
-            acc[P.node + j] = (T)(P.accel * E);
+            acc[2 * (P.node + j)] = (T)(P.accel * E);  // A_j of the pair; k_slopes adds the slope
         }
         Rprev = R;
     }
+}
+
+// Second member of every node pair: A_{j+1} - A_j, rounded in T from the two
+// rounded accelerations (the value the gather's difference would give).  One flat
+// pass over all segments' nodes; the entries past a segment's last cell are never
+// read by the gather.
+template <typename T>
+__global__ void __launch_bounds__(256) k_slopes(T* __restrict__ pairs, int64_t nnodes)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nnodes; n += stride)
+        pairs[2 * n + 1] = n + 1 < nnodes ? pairs[2 * n + 2] - pairs[2 * n] : T(0);
 }
 
 // Potential for the diagnostics (one block, on demand), from the last complete
@@ -260,8 +274,9 @@ __global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, 
 
 __global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned long long* seg_n,
                                                 int64_t* seg_nmove, int64_t* tile_start, int nseg,
-                                                int tile_quads)
+                                                int tile_quads, unsigned long long* rare_count)
 {
+    if (threadIdx.x == 0) *rare_count = 0ull;
     __shared__ i128 sh[33];
     const int C = (nseg + blockDim.x - 1) / blockDim.x;
     const int s0 = min(nseg, (int)threadIdx.x * C), s1 = min(nseg, s0 + C);
@@ -341,6 +356,13 @@ cudaError_t launch_field(const FieldArgs& f, bool advance_step, cudaStream_t st)
         k_field_emit<double><<<f.nchunks, kChunkThreads, 0, st>>>(f, advance_step ? 1 : 0);
     else
         k_field_emit<float><<<f.nchunks, kChunkThreads, 0, st>>>(f, advance_step ? 1 : 0);
+    if (f.any_poisson) {
+        const int grid = (int)std::min<int64_t>((f.seg_nodes + 255) / 256, 4096);
+        if (f.precision == PIC_FP64)
+            k_slopes<double><<<grid, 256, 0, st>>>(static_cast<double*>(f.accel), f.seg_nodes);
+        else
+            k_slopes<float><<<grid, 256, 0, st>>>(static_cast<float*>(f.accel), f.seg_nodes);
+    }
     return cudaGetLastError();
 }
 
@@ -352,9 +374,10 @@ cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* ph
 }
 
 cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
-                         int64_t* tile_start, int nseg, int tile_quads, cudaStream_t st)
+                         int64_t* tile_start, int nseg, int tile_quads,
+                         unsigned long long* rare_count, cudaStream_t st)
 {
-    k_tiles<<<1, 1024, 0, st>>>(seg, seg_n, seg_nmove, tile_start, nseg, tile_quads);
+    k_tiles<<<1, 1024, 0, st>>>(seg, seg_n, seg_nmove, tile_start, nseg, tile_quads, rare_count);
     return cudaGetLastError();
 }
 

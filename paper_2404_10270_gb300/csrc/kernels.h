@@ -16,6 +16,9 @@ cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, int nt, int 
                             cudaStream_t st);
 cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, int nt, int grid,
                             cudaStream_t st);
+// The rare events the mover queued this step (events.cu): collision candidates and
+// wall hits, one thread each, `grid` blocks of 128 threads.
+cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
 int move_blocks_per_sm_f32(bool mag, int nt);
 int move_blocks_per_sm_f64(bool mag, int nt);
@@ -28,7 +31,8 @@ struct FieldArgs {
     int max_nodes;                    // max ncells+1 over instances
     unsigned long long* dep;          // accumulating deposit (zeroed by emit)
     unsigned long long* dep_last;     // copy of the last complete deposit
-    void* accel;                      // T node arrays per segment
+    void* accel;                      // T pairs (A_j, A_{j+1} - A_j), node arrays per segment
+    int64_t seg_nodes;                // entries of the segment node arrays (all segments)
     int precision;                    // PIC_FP32 / PIC_FP64
     double* E;                        // per instance node arrays
     i128* UN;                         // per instance: sum of R over nodes 0..N-1
@@ -49,8 +53,10 @@ cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* ph
 
 // Round each segment's slot count up to a whole quad, snapshot it as the count to
 // move, and build the tile prefix (tiles of `tile_quads` quads).
+// Also empties the rare-event queue of the coming step.
 cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
-                         int64_t* tile_start, int nseg, int tile_quads, cudaStream_t st);
+                         int64_t* tile_start, int nseg, int tile_quads,
+                         unsigned long long* rare_count, cudaStream_t st);
 
 // Number this step's ionization products by the rank of their parent id.
 cudaError_t launch_births(const InstParams* inst, int ninst, Event* events,
@@ -80,7 +86,8 @@ struct SortArgs {
     int64_t max_cap;                  // largest segment capacity
     int max_cells;
 };
-cudaError_t launch_sort(const SortArgs& s, int nt, int grid, cudaStream_t st);
+// Grids are one resident wave of each kernel on `sms` multiprocessors.
+cudaError_t launch_sort(const SortArgs& s, int nt, int sms, cudaStream_t st);
 
 // ---- I/O and diagnostics (io.cu) -------------------------------------------------
 struct LoadArgs {

@@ -1,13 +1,16 @@
 // mover.cuh -- the fused per-particle time step ("particle mover" of the paper,
 // Section 2 and Listing 7) for one precision T:
 //
-//   gather   a = A[j] + f (A[j+1] - A[j])           (Listing 7, moveb())
+//   gather   a = A[j] + f (A[j+1] - A[j]), one fused multiply-add on the node pair
+//            (A_j, A_{j+1} - A_j)                   (Listing 7, moveb())
 //   push     u += a, or the Boris rotation when B != 0 (Boris 1970)
 //   move     f += u_x; the integer part moves the particle across cells
-//   wall     absorbing (flux counters), periodic, or absorb + volume re-injection
-//   MCC      null collision: Philox(id, step, COLLIDE) word 0 < floor(P 2^32)
-//            selects a candidate, word 1 a process slot; energy thresholds,
-//            elastic / charge-exchange / ionization kinematics
+//   wall     periodic wrap inline; a particle that leaves through an absorbing or
+//            source wall is queued for the event kernel and leaves the store
+//   MCC      null collision: the collision clock in the cell word says when the
+//            particle's next candidate step is; at a test step Philox(id, step,
+//            COLLIDE) word 0 sets the clock; a candidate is queued for the event
+//            kernel, which selects the process and does the kinematics
 //   deposit  cloud-in-cell in fixed point: node j gets S - Q, node j+1 gets
 //            Q = rint(f S), so every particle adds exactly S (S = 2^24 FP32,
 //            2^48 FP64); reduced per node across the warp in registers, then one
@@ -15,12 +18,15 @@
 //
 // Work decomposition: a tile is 32 quads of four consecutive particles of one
 // segment (instance, species), owned by one warp; each lane loads its quad with
-// 128-bit accesses.  The particle id is not streamed: the collision clock (bits
-// 23-30 of the cell word) makes Philox draws happen about once per 127 steps per
-// particle, and only then, or at a wall, is the id read.  Warps walk the tiles of all segments independently.  The
-// acceleration of the nodes a warp touches is staged in registers and exchanged by
-// warp shuffles; there is no block-level barrier anywhere in the step, so an SM keeps
-// the loads of many tiles in flight (the kernel is bound by HBM, not by latency).
+// 128-bit accesses.  The particle id is not streamed: it is read only at clock test
+// steps (once per 127 steps per particle) and by the event kernel.  Warps walk the
+// tiles of all segments independently, with no block-level barrier, so an SM keeps
+// the loads of many tiles in flight.  The loop has no calls: the rare events
+// (collision candidates, wall hits) go to a queue that the event kernel
+// (events.cuh) works through after the mover, so the common path keeps its whole
+// state in registers.  Velocity changes do not move a particle, so a candidate is
+// deposited here; a wall particle is deposited by the event kernel if it is
+// re-injected.
 #pragma once
 #include <climits>
 
@@ -33,13 +39,17 @@ namespace bitpic {
 #endif
 constexpr int kMoveMinWarps = BITPIC_MOVE_MIN_WARPS;  // resident warps per SM the mover is built for
 #ifndef BITPIC_MOVE_MIN_WARPS64
-#define BITPIC_MOVE_MIN_WARPS64 24
+#define BITPIC_MOVE_MIN_WARPS64 32
 #endif
 constexpr int kMoveMinWarps64 = BITPIC_MOVE_MIN_WARPS64;  // the same for the FP64 form
 #ifndef BITPIC_MOVE_MIN_WARPS_MAG
 #define BITPIC_MOVE_MIN_WARPS_MAG 32
 #endif
-constexpr int kMoveMinWarpsMag = BITPIC_MOVE_MIN_WARPS_MAG;  // cap for the Boris (3V) variant
+constexpr int kMoveMinWarpsMag = BITPIC_MOVE_MIN_WARPS_MAG;  // the Boris (3V) variant, FP32
+#ifndef BITPIC_MOVE_MIN_WARPS64_MAG
+#define BITPIC_MOVE_MIN_WARPS64_MAG 24
+#endif
+constexpr int kMoveMinWarps64Mag = BITPIC_MOVE_MIN_WARPS64_MAG;  // the Boris variant, FP64
 constexpr int kDeadCell = -(1 << 30);
 
 struct MoveArgs {
@@ -56,7 +66,7 @@ struct MoveArgs {
     const int64_t* seg_nmove;           // slots of each segment moved this step
     unsigned long long* seg_n;          // slots in use (appends for created particles)
     unsigned long long* seg_live;       // live particles
-    const void* accel;                  // T, segment node arrays
+    const void* accel;                  // T pairs (A_j, A_{j+1} - A_j), segment node arrays
     unsigned long long* dep;            // fixed-point deposit, segment node arrays
     unsigned long long* wall_count;     // [nseg][2]
     double* wall_energy;                // [nseg][2]
@@ -65,12 +75,18 @@ struct MoveArgs {
     unsigned long long* ev_count;       // [ninst]
     unsigned* err;
     const int64_t* step;
+    uint64_t* rare;                     // queue of rare events of this step (rare_pack)
+    unsigned long long* rare_count;     // entries queued this step
+    int64_t rare_cap;                   // queue entries
 };
 
 template <typename T> struct Prec;
 template <> struct Prec<float> {
     using Q = uint32_t;  // fixed-point charge of one particle (< 2^25)
+    using T2 = float2;
+    static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static constexpr int min_warps = kMoveMinWarps;  // memory bound: as many warps as fit
+    static constexpr int min_warps_mag = kMoveMinWarpsMag;
     static __device__ __forceinline__ uint64_t qright(float f)
     {
         return (uint64_t)__float2uint_rn(f * 16777216.0f);
@@ -106,7 +122,10 @@ template <> struct Prec<float> {
 };
 template <> struct Prec<double> {
     using Q = uint64_t;  // fixed-point charge of one particle (< 2^49)
+    using T2 = double2;
+    static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
     static constexpr int min_warps = kMoveMinWarps64;  // FP64-pipe bound: registers first
+    static constexpr int min_warps_mag = kMoveMinWarps64Mag;
     // rint(f 2^48) for f in [0, 1), ties to even, from the bits: f = m 2^(e-1075), so
     // f 2^48 = m / 2^(1027-e) rounded to nearest even (integer ALU only).
     static __device__ __forceinline__ uint64_t qright(double f)
@@ -132,37 +151,36 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
-    // Finiteness from the exponent bits (integer ALU; the FP64 pipe is this form's limit).
+    // Finiteness from the exponent bits of the high word (integer ALU; the FP64 pipe
+    // is this form's limit, and a test on the whole 64-bit pattern may be turned back
+    // into a floating-point comparison by the compiler).
     static __device__ __forceinline__ bool finite(double x)
     {
-        return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
+        return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000;
     }
-    // The same move as the float form with the same rounding: floor(f'), f' - floor(f')
-    // and the truncation.  For the common -1 < f' < 2 the floor is read from the bits,
-    // and the subtraction of 0 or -1 or 1 is done as the identical IEEE operation (or
-    // skipped when it is exact), which saves three of this form's FP64 instructions.
+    // The same move as the float form with the same rounding: f' - floor(f') and the
+    // truncation.  For the common -1 < f' < 2 the floor is read from the bits and
+    // f' - floor(f') is the one IEEE addition f' + c, c = +0, +1 or -1 (identical to
+    // the subtraction of 0, -1 or 1), for every lane alike: the FP64 pipe, this
+    // form's limit, sees one instruction whatever the warp's particles do.  A result
+    // that rounds up to 1 (f' a tiny negative number) is renormalised to the next
+    // cell from its bits.
     static __device__ __forceinline__ void move(double& f, double u, int& j)
     {
         const double xn = f + u;
-        const long long b = __double_as_longlong(xn);
-        const int e = (int)((b >> 52) & 0x7FF);
-        if (e < 1023) {                                  // |f'| < 1
-            if (b >= 0 || (b & 0x7FFFFFFFFFFFFFFFll) == 0) {
-                f = __longlong_as_double(b & 0x7FFFFFFFFFFFFFFFll);  // f' - 0 (-0 -> +0)
-                return;
-            }
-            double fk = xn + 1.0;                        // f' - (-1)
-            j -= 1;
-            if (fk >= 1.0) {
+        const int hi = __double2hiint(xn);
+        const int e = (hi >> 20) & 0x7FF;
+        if (__builtin_expect(e < 1023 || (e == 1023 && hi >= 0), 1)) {
+            const bool neg = hi < 0;   // -1 < f' < 0, or f' = -0
+            const bool up = e == 1023; // 1 <= f' < 2
+            const double c = __hiloint2double(neg ? 0x3FF00000 : (up ? (int)0xBFF00000u : 0), 0);
+            double fk = xn + c;
+            j += neg ? -1 : (up ? 1 : 0);
+            if (__double2hiint(fk) == 0x3FF00000) {  // fk in [0, 1]: this is fk == 1
                 fk = 0.0;
                 j += 1;
             }
             f = fk;
-            return;
-        }
-        if (e == 1023 && b >= 0) {                       // 1 <= f' < 2: exact f' - 1
-            f = xn - 1.0;
-            j += 1;
             return;
         }
         const double fl = floor(xn);
@@ -179,8 +197,7 @@ template <> struct Prec<double> {
 // Resident blocks per SM each mover variant is compiled for (its register budget).
 template <typename T, bool MAG, int NT>
 struct MoveOccupancy {
-    static constexpr int warps =
-        MAG && kMoveMinWarpsMag < Prec<T>::min_warps ? kMoveMinWarpsMag : Prec<T>::min_warps;
+    static constexpr int warps = MAG ? Prec<T>::min_warps_mag : Prec<T>::min_warps;
     static constexpr int blocks = warps / (NT / 32) > 0 ? warps / (NT / 32) : 1;
 };
 
@@ -203,30 +220,6 @@ __device__ __forceinline__ void st4(double* p, const double v[4])
 {
     reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-}
-
-// Unit vector uniform on the sphere, polar axis x (the wall normal).
-template <typename T>
-__device__ __forceinline__ void iso_dir(uint32_t w0, uint32_t w1, T n[3])
-{
-    const T ct = T(1) - T(2) * Prec<T>::uni(w0);
-    const T st = Prec<T>::sqrt_(T(1) - ct * ct);
-    T sp, cp;
-    Prec<T>::sincos2pi(Prec<T>::uni(w1), &sp, &cp);
-    n[0] = ct;
-    n[1] = st * cp;
-    n[2] = st * sp;
-}
-
-// Box-Muller (1958).
-template <typename T>
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z1)
-{
-    const T r = Prec<T>::sqrt_(T(-2) * Prec<T>::log_(Prec<T>::uni(wa)));
-    T s, c;
-    Prec<T>::sincos2pi(Prec<T>::uni(wb), &s, &c);
-    *z0 = r * c;
-    *z1 = r * s;
 }
 
 // Warp-level deposit of four particles per lane.  With Q = rint(f S) the charge of
@@ -310,214 +303,29 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
     }
 }
 
-// A null-collision candidate of one particle (velocity u in cells/step, after the
-// move): process slot from the selection word `wsel`, energy threshold (below it the
-// event is a null collision), kinematics.  Returns true when u changed.  Ionization
-// appends two particles.
-template <typename T>
-__device__ __noinline__ bool collide(const MoveArgs& a, const SegParams& P, int s,
-                                     uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
-                                     T& uz, uint32_t wsel)
-{
-    int q = -1;
-    for (int k = 0; k < P.nproc; ++k)
-        if ((uint64_t)wsel < P.slot_end[k]) { q = k; break; }
-    if (q < 0) return false;
-    const T u2 = ux * ux + uy * uy + uz * uz;
-    if (!(u2 >= (T)P.thr_u2[q])) return false;  // below threshold: null event
-    const int kind = P.kind[q];
-    if (kind == PIC_PROC_ELASTIC) {
-        const uint4 r = draw(id, step, kRngScatter, P.key0, P.key1);
-        T n[3];
-        iso_dir<T>(r.x, r.y, n);
-        const T speed = Prec<T>::sqrt_(u2);
-        if (speed > T(0)) {
-            const T cchi = (ux * n[0] + uy * n[1] + uz * n[2]) / speed;
-            const T fac = Prec<T>::sqrt_(T(1) - T(2) * (T)P.mratio * (T(1) - cchi));
-            const T sp2 = speed * fac;
-            ux = sp2 * n[0];
-            uy = sp2 * n[1];
-            uz = sp2 * n[2];
-        }
-    } else if (kind == PIC_PROC_CX) {
-        const uint4 r = draw(id, step, kRngMaxwell, P.key0, P.key1);
-        T z0, z1, z2, z3;
-        box_muller<T>(r.x, r.y, &z0, &z1);
-        box_muller<T>(r.z, r.w, &z2, &z3);
-        const T vn = (T)P.vneutral;
-        ux = z0 * vn;
-        uy = z1 * vn;
-        uz = z2 * vn;
-    } else {  // PIC_PROC_IONIZE
-        const T us = Prec<T>::sqrt_(T(0.5) * (u2 - (T)P.thr_u2[q]));
-        T n1[3], n2[3];
-        const uint4 r1 = draw(id, step, kRngScatter, P.key0, P.key1);
-        iso_dir<T>(r1.x, r1.y, n1);
-        const uint4 r2 = draw(id, step, kRngIonizeE, P.key0, P.key1);
-        iso_dir<T>(r2.x, r2.y, n2);
-        const uint4 ri = draw(id, step, kRngIonizeI, P.key0, P.key1);
-        T z0, z1, z2, z3;
-        box_muller<T>(ri.x, ri.y, &z0, &z1);
-        box_muller<T>(ri.z, ri.w, &z2, &z3);
-        ux = us * n1[0];
-        uy = us * n1[1];
-        uz = us * n1[2];
-        // append the new electron (this segment) and the new ion (product segment)
-        const int si = P.product[q];
-        const SegParams& Pi = a.seg[si];
-        const unsigned long long ke = atomicAdd(a.seg_n + s, 1ull);
-        const unsigned long long ki = atomicAdd(a.seg_n + si, 1ull);
-        const InstParams& I = a.inst[P.inst];
-        const unsigned long long ev = atomicAdd(a.ev_count + P.inst, 1ull);
-        if (ke >= (unsigned long long)P.cap || ki >= (unsigned long long)Pi.cap ||
-            ev >= (unsigned long long)I.ev_cap) {
-            set_error(a.err, kErrCapacity);
-        } else {
-            const T vn = (T)P.vneutral;
-            const int64_t ge = P.base + (int64_t)ke, gi = Pi.base + (int64_t)ki;
-            T* off = static_cast<T*>(a.off);
-            T* vx = static_cast<T*>(a.ux);
-            T* vy = static_cast<T*>(a.uy);
-            T* vz = static_cast<T*>(a.uz);
-            a.cell[ge] = j; off[ge] = f;
-            vx[ge] = us * n2[0]; vy[ge] = us * n2[1]; vz[ge] = us * n2[2];
-            a.id[ge] = 0xFFFFFFFFu;
-            a.cell[gi] = j; off[gi] = f;
-            vx[gi] = z0 * vn; vy[gi] = z1 * vn; vz[gi] = z2 * vn;
-            a.id[gi] = 0xFFFFFFFFu;
-            Event e;
-            e.parent = id;
-            e.pad = 0;
-            e.slot_e = ge;
-            e.slot_i = gi;
-            a.events[I.ev_base + (int64_t)ev] = e;
-            atomicAdd(a.seg_live + s, 1ull);
-            atomicAdd(a.seg_live + si, 1ull);
-            // the children's charge joins this step's deposit
-            const uint64_t qr = Prec<T>::qright(f), ql = Prec<T>::S - qr;
-            atomicAdd(a.dep + P.node + j, (unsigned long long)ql);
-            atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
-            atomicAdd(a.dep + Pi.node + j, (unsigned long long)ql);
-            atomicAdd(a.dep + Pi.node + j + 1, (unsigned long long)qr);
-        }
-    }
-    atomicAdd(a.collisions + (int64_t)P.inst * kMaxProc + P.proc[q], 1ull);
-    return true;
-}
-
-// Wall phase for a particle that left [0, N) (rare): counts and energy of the
-// absorbed particle, then either absorption (returns 2), or volume re-injection with a
-// new position and Maxwellian velocity (returns 1).  Periodic walls are handled inline.
-template <typename T>
-__device__ __noinline__ int wall_event(const MoveArgs& a, const SegParams& P, int s, uint32_t id,
-                                       int64_t step, int& j, T& f, T& ux, T& uy, T& uz)
-{
-    const int wall = j < 0 ? 0 : 1;
-    const double u2 = (double)ux * (double)ux + (double)uy * (double)uy + (double)uz * (double)uz;
-    atomicAdd(a.wall_count + 2 * s + wall, 1ull);
-    atomicAdd(a.wall_energy + 2 * s + wall, P.kefac * u2);
-    if (P.bc != PIC_BC_SOURCE) {
-        atomicAdd(a.seg_live + s, ~0ull);  // -1
-        return 2;
-    }
-    const int N = P.ncells;
-    const uint4 r = draw(id, step, kRngInjectA, P.key0, P.key1);
-    const uint4 q2 = draw(id, step, kRngInjectB, P.key0, P.key1);
-    const T x = Prec<T>::uni(r.x) * (T)N;
-    const T fx = Prec<T>::floor_(x);
-    j = (int)fx;
-    f = x - fx;
-    if (j >= N) {
-        j = N - 1;
-        f = T(0);
-    }
-    T z0, z1, z2, z3;
-    box_muller<T>(r.y, r.z, &z0, &z1);
-    box_muller<T>(q2.x, q2.y, &z2, &z3);
-    const T vi = (T)P.vinj;
-    ux = z0 * vi;
-    uy = z1 * vi;
-    uz = z2 * vi;
-    return 1;
-}
-
-// The state of one lane's quad, copied out of registers only for the rare handler.
-template <typename T>
-struct Quad {
-    int c[4];
-    T f[4], ux[4], uy[4], uz[4];
-};
-
-// Rare events of one quad, in particle order: wall hits (bit k of `wall`) and
-// null-collision candidates (bit k of `cand`; the selection word is word 1 of the
-// step's COLLIDE draw).  Out of line so that the hot loop keeps its state in
-// registers.  Returns the bits of particles whose uy/uz changed (non-MAG callers
-// store those).  q->c holds cell words; a candidate or a re-injection restarts the
-// particle's collision clock.
-template <typename T, bool MAG>
-__device__ __noinline__ unsigned rare_events(const MoveArgs& a, const SegParams& P, int s,
-                                             int64_t step, int64_t slot, unsigned wall,
-                                             unsigned cand, Quad<T>* q)
-{
-    const T* uyp = static_cast<const T*>(a.uy);
-    const T* uzp = static_cast<const T*>(a.uz);
-    unsigned dirty = 0;
-    for (int k = 0; k < 4; ++k) {
-        const unsigned bit = 1u << k;
-        if (!((wall | cand) & bit)) continue;
-        const uint32_t idk = a.id[slot + k];
-        T vy = MAG ? q->uy[k] : uyp[slot + k];
-        T vz = MAG ? q->uz[k] : uzp[slot + k];
-        // a wall hit carries its raw (out of range) cell index; others a cell word
-        int j = (wall & bit) ? q->c[k] : (int)((uint32_t)q->c[k] & kCellMask);
-        T f = q->f[k];
-        T vx = q->ux[k];
-        if (wall & bit) {
-            const int r = wall_event<T>(a, P, s, idk, step, j, f, vx, vy, vz);
-            if (r == 2) {
-                q->c[k] = -1;
-                continue;
-            }
-        } else {
-            q->c[k] = j;  // the step after a candidate draws again
-            const uint4 w = draw(idk, step, kRngCollide, P.key0, P.key1);
-            if (!collide<T>(a, P, s, idk, step, j, f, vx, vy, vz, w.y)) continue;
-        }
-        q->c[k] = j;
-        q->f[k] = f;
-        q->ux[k] = vx;
-        q->uy[k] = vy;
-        q->uz[k] = vz;
-        dirty |= bit;
-    }
-    return dirty;
-}
-
 // The fused time step.  Work unit: a warp tile of 32 quads (128 consecutive particles
 // of one segment); each lane owns one quad and moves it with 128-bit accesses.  Warps
 // walk the tiles of all segments independently (no block-level barrier), so every SM
-// keeps many tiles' loads in flight.  The acceleration of the nodes a warp's
-// particles occupy is staged in registers: one coalesced load of the warp's node span,
-// then each particle picks its two nodes by warp shuffle.  The loop over the quad is
-// free of calls; walls and collision candidates are flagged and handled out of line.
+// keeps many tiles' loads in flight.  The gather reads each particle's node pair with
+// one vector load (the node arrays are small and stay in L1/L2).  The loop is free of
+// calls; walls and collision candidates are queued for the event kernel.
 template <typename T, int NT, bool MAG, bool MOVE>
 __global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
     using Q = typename Prec<T>::Q;
-    const unsigned FULL = 0xffffffffu;
+    using T2 = typename Prec<T>::T2;
     const int lane = threadIdx.x & 31;
     T* const offp = static_cast<T*>(a.off);
     T* const uxp = static_cast<T*>(a.ux);
     T* const uyp = static_cast<T*>(a.uy);
     T* const uzp = static_cast<T*>(a.uz);
-    const T* const accp = static_cast<const T*>(a.accel);
+    const T2* const accp = static_cast<const T2*>(a.accel);
     const int64_t step = MOVE ? *a.step : 0;
     // steps to the next multiple of kGapMax, where every clock without a candidate tests
     const int dgrid = kGapMax - (int)(step % kGapMax);
     const int64_t total = a.tile_start[a.nseg];
     const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
-
     for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
          tile += wstride) {
         const int s = find_segment(a.tile_start, a.nseg, tile);
@@ -547,42 +355,16 @@ k_move(const __grid_constant__ MoveArgs a)
         }
 
         if (MOVE) {
-            // stage the acceleration of the warp's node span in registers
-            int lmin = INT_MAX, lmax = INT_MIN;
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (c[k] >= 0) {
-                    const int jj = (int)((uint32_t)c[k] & kCellMask);
-                    lmin = min(lmin, jj);
-                    lmax = max(lmax, jj);
-                }
-            const int wmin = __reduce_min_sync(FULL, lmin);
-            const int wmax = __reduce_max_sync(FULL, lmax);
-            const bool staged = wmin != INT_MAX && wmax - wmin + 2 <= 32;
-            T av = T(0);
-            if (staged && lane <= wmax - wmin + 1) av = __ldg(accp + node0 + wmin + lane);
-            unsigned wallbits = 0, candbits = 0;
+            unsigned cand = 0, wlo = 0, whi = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                // 1. gather (Listing 7)
-                const bool live = c[k] >= 0;
+                if (c[k] < 0) continue;
                 int j = (int)((uint32_t)c[k] & kCellMask);
-                uint32_t clk = ((uint32_t)c[k] >> kClockShift) & 0xFFu;
-                T a0, a1;
-                if (staged) {
-                    const int i = live ? j - wmin : 0;
-                    a0 = __shfl_sync(FULL, av, i);
-                    a1 = __shfl_sync(FULL, av, i + 1);
-                } else if (live) {
-                    a0 = __ldg(accp + node0 + j);
-                    a1 = __ldg(accp + node0 + j + 1);
-                } else {
-                    a0 = T(0);
-                    a1 = T(0);
-                }
-                if (!live) continue;
+                uint32_t clk = (uint32_t)c[k] >> kClockShift;
+                // 1. gather (Listing 7) from the node pair (A_j, A_{j+1} - A_j)
+                const T2 pr = __ldg(accp + node0 + j);
                 T fk = f[k];
-                const T acc = a0 + fk * (a1 - a0);
+                const T acc = Prec<T>::fma_(fk, pr.y, pr.x);
                 // 2. push
                 if (!MAG) {
                     ux[k] = ux[k] + acc;
@@ -605,14 +387,15 @@ k_move(const __grid_constant__ MoveArgs a)
                 // 3. move (Listing 7: x += nstep*vx, x the in-cell offset)
                 Prec<T>::move(fk, ux[k], j);
                 f[k] = fk;
-                // 4. walls (absorption and re-injection out of line)
+                // 4. walls: periodic wrap here; an absorbed or re-injected particle
+                // leaves the store and the event kernel takes over
                 if (j < 0 || j >= N) {
                     if (bc == PIC_BC_PERIODIC) {
                         j %= N;
                         if (j < 0) j += N;
                     } else {
-                        c[k] = j;  // out of range: the rare handler decides
-                        wallbits |= 1u << k;
+                        if (j < 0) wlo |= 1u << k; else whi |= 1u << k;
+                        c[k] = -1;
                         continue;
                     }
                 }
@@ -623,12 +406,12 @@ k_move(const __grid_constant__ MoveArgs a)
                 // cut at the next multiple of 127 (D steps away): g = 0 candidate now,
                 // g < D a candidate g steps later, g = D none before then.  The cut puts
                 // the tests of all particles on the same steps, so a warp runs them
-                // together.  Candidates continue out of line.
+                // together.  Candidates go to the event kernel.
                 if (collides) {
                     if (clk & kClockCount) {
                         clk -= 1u;
                     } else if (clk & kClockPending) {
-                        candbits |= 1u << k;
+                        cand |= 1u << k;
                         clk = 0u;
                     } else {
                         // a test step: the id is read only here
@@ -636,7 +419,7 @@ k_move(const __grid_constant__ MoveArgs a)
                         const uint4 w = draw(idk, step, kRngCollide, key0, key1);
                         const int g = min(gap_steps(P.gap, w.x), dgrid);
                         if (g == 0) {
-                            candbits |= 1u << k;
+                            cand |= 1u << k;
                             clk = 0u;
                         } else {
                             clk = g < dgrid ? ((uint32_t)(g - 1) | kClockPending)
@@ -646,19 +429,6 @@ k_move(const __grid_constant__ MoveArgs a)
                 }
                 c[k] = (int)((uint32_t)j | (clk << kClockShift));
             }
-            unsigned dirty = 0;
-            if (wallbits | candbits) {
-                Quad<T> q;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    q.c[k] = c[k]; q.f[k] = f[k]; q.ux[k] = ux[k]; q.uy[k] = uy[k]; q.uz[k] = uz[k];
-                }
-                dirty = rare_events<T, MAG>(a, P, s, step, slot, wallbits, candbits, &q);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    c[k] = q.c[k]; f[k] = q.f[k]; ux[k] = q.ux[k]; uy[k] = q.uy[k]; uz[k] = q.uz[k];
-                }
-            }
             if (act) {
                 __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
                 st4(offp + slot, f);
@@ -666,13 +436,23 @@ k_move(const __grid_constant__ MoveArgs a)
                 if (MAG) {
                     st4(uyp + slot, uy);
                     st4(uzp + slot, uz);
-                } else if (dirty) {
+                }
+            }
+            // queue the quad's rare events (a few lanes of a few tiles per step)
+            const unsigned ev = cand | wlo | whi;
+            if (ev) {
+                unsigned long long e = atomicAdd(a.rare_count, (unsigned long long)__popc(ev));
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (dirty & (1u << k)) {
-                            uyp[slot + k] = uy[k];
-                            uzp[slot + k] = uz[k];
-                        }
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned bit = 1u << k;
+                    if (!(ev & bit)) continue;
+                    const uint32_t kind = (cand & bit) ? kRareCandidate
+                                          : (wlo & bit) ? kRareWallLow : kRareWallHigh;
+                    if (e < (unsigned long long)a.rare_cap)
+                        a.rare[e] = rare_pack(slot + k, s, kind);
+                    else
+                        set_error(a.err, kErrEvents);
+                    ++e;
                 }
             }
         }

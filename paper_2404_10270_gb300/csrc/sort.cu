@@ -134,17 +134,26 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
             const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(id + slot));
             vi[0] = ii.x; vi[1] = ii.y; vi[2] = ii.z; vi[3] = ii.w;
         }
+        // group equal cells of each slot across the warp; the four reservations are
+        // independent, so they are all issued before the first one is waited for
+        unsigned grp[4], base[4];
+        int key[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const bool live = c[k] >= 0;
-            const int key = live ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
-            const unsigned grp = __match_any_sync(0xffffffffu, key);
-            const int leader = __ffs(grp) - 1;
-            unsigned base = 0;
-            if (live && lane == leader) base = atomicAdd(a.hist + P.node + key, (unsigned)__popc(grp));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (live) {
-                const int64_t to = P.base + (int64_t)base + __popc(grp & lt);
+            key[k] = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
+            grp[k] = __match_any_sync(0xffffffffu, key[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            base[k] = 0;
+            if (c[k] >= 0 && lane == __ffs(grp[k]) - 1)
+                base[k] = atomicAdd(a.hist + P.node + key[k], (unsigned)__popc(grp[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned b = __shfl_sync(0xffffffffu, base[k], __ffs(grp[k]) - 1);
+            if (c[k] >= 0) {
+                const int64_t to = P.base + (int64_t)b + __popc(grp[k] & lt);
                 dcell[to] = c[k];
                 doff[to] = vo[k];
                 dux[to] = vx[k];
@@ -176,27 +185,39 @@ __global__ void k_sort_finish(const SortArgs a)
     }
 }
 
-template <int NT>
-cudaError_t run_sort(const SortArgs& a, int grid, cudaStream_t st)
+// One resident wave of a grid-stride kernel: blocks per SM at full occupancy x SMs
+// (a second, partial wave would run its share of the tiles at a fraction of the
+// machine).
+template <typename K>
+int one_wave(K kernel, int nt, int sms)
 {
-    k_hist<NT><<<grid, NT, 0, st>>>(a);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, nt, 0) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb * sms;
+}
+
+template <int NT>
+cudaError_t run_sort(const SortArgs& a, int sms, cudaStream_t st)
+{
+    k_hist<NT><<<one_wave(k_hist<NT>, NT, sms), NT, 0, st>>>(a);
     k_cell_scan<<<a.nseg, 1024, 0, st>>>(a);
     if (a.precision == PIC_FP64)
-        k_scatter<double, NT><<<grid, NT, 0, st>>>(a);
+        k_scatter<double, NT><<<one_wave(k_scatter<double, NT>, NT, sms), NT, 0, st>>>(a);
     else
-        k_scatter<float, NT><<<grid, NT, 0, st>>>(a);
+        k_scatter<float, NT><<<one_wave(k_scatter<float, NT>, NT, sms), NT, 0, st>>>(a);
     k_sort_finish<<<a.nseg, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_sort(const SortArgs& a, int nt, int grid, cudaStream_t st)
+cudaError_t launch_sort(const SortArgs& a, int nt, int sms, cudaStream_t st)
 {
     switch (nt) {
-        case 128: return run_sort<128>(a, grid, st);
-        case 512: return run_sort<512>(a, grid, st);
-        default: return run_sort<256>(a, grid, st);
+        case 128: return run_sort<128>(a, sms, st);
+        case 512: return run_sort<512>(a, sms, st);
+        default: return run_sort<256>(a, sms, st);
     }
 }
 
