@@ -431,7 +431,10 @@ def _run_ours(args, stream, rank, world, local):
     t0 = time.perf_counter()
     for s, h in enumerate(host):
         sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
+    t_load = time.perf_counter()
     sim.step(args.steps)
+    sim.sync()
+    t_steps = time.perf_counter()
     mom = sim.moments(0)
     d2h = 0
     import ctypes as C
@@ -443,7 +446,9 @@ def _run_ours(args, stream, rank, world, local):
                     ("cell", "off", "vx", "vy", "vz", "id")], None, 0, C.byref(got)), sim._h)
         d2h += got.value * 40
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    t_end = time.perf_counter()
+    e2e_s = t_end - t0
+    e2e_parts = {"load_s": t_load - t0, "steps_s": t_steps - t_load, "read_back_s": t_end - t_steps}
     e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
@@ -496,7 +501,8 @@ def _run_ours(args, stream, rank, world, local):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps,
                     "what": "pic_load_particles from pinned host + %d steps + pic_moments + "
-                            "pic_get_particles to pinned host" % args.steps},
+                            "pic_get_particles to pinned host" % args.steps,
+                    "breakdown": e2e_parts},
             "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"],
             "kernel_ms": res["kernel_ms"],

@@ -79,7 +79,7 @@ struct SegParams {
     int32_t pad2;
 };
 
-constexpr int kChunk = 2048;  // nodes per block of the field solve
+constexpr int kChunk = 256;  // nodes per block of the field solve
 
 struct InstParams {
     int32_t ncells;

@@ -94,6 +94,8 @@ struct pic_handle {
     int64_t* step_d = nullptr;
     double *kin = nullptr, *phi_d = nullptr;
     std::vector<void*> allocs;
+    char* io = nullptr;       // staging of pic_load_particles / pic_get_particles host data
+    size_t io_bytes = 0;
 
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -125,6 +127,29 @@ struct pic_handle {
 };
 
 namespace {
+
+int fail(pic_handle* h, int code, const std::string& msg);
+
+// The handle's staging buffer for host transfers, grown on demand and kept (a fresh
+// allocation of gigabytes per call costs more than the copy).  The stream is drained
+// before a smaller buffer is given back.
+cudaError_t io_buffer(pic_handle* h, size_t bytes, char** out)
+{
+    if (bytes > h->io_bytes) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess && h->io) e = cudaFree(h->io);
+        h->io = nullptr;
+        h->io_bytes = 0;
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h->io, bytes);
+        if (e != cudaSuccess) {
+            h->io = nullptr;
+            return e;
+        }
+        h->io_bytes = bytes;
+    }
+    *out = h->io;
+    return cudaSuccess;
+}
 
 int fail(pic_handle* h, int code, const std::string& msg)
 {
@@ -896,8 +921,9 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     if (!on_device && n > 0) {
         const size_t bytes = (size_t)n * (4 + 8 * 4) + (id ? (size_t)n * 4 : 0) +
                              (state ? (size_t)n : 0) + 128;
-        CUDA_TRY(h, cudaMallocAsync(&stage, bytes, s));
-        char* p = static_cast<char*>(stage);
+        char* p = nullptr;
+        CUDA_TRY(h, io_buffer(h, bytes, &p));
+        stage = p;
         auto put = [&](const void* src, size_t b) {
             char* d = p;
             p += (b + 15) / 16 * 16;
@@ -911,10 +937,8 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
         dvz = (const double*)put(vz, nb8);
         did = id ? (const uint32_t*)put(id, (size_t)n * 4) : nullptr;
         dstate = state ? (const uint8_t*)put(state, (size_t)n) : nullptr;
-        if (!dc || !doff || !dvx || !dvy || !dvz || (id && !did) || (state && !dstate)) {
-            cudaFreeAsync(stage, s);
+        if (!dc || !doff || !dvx || !dvy || !dvz || (id && !did) || (state && !dstate))
             return fail(h, PIC_ECUDA, "pic_load_particles: host-to-device copy failed");
-        }
     }
     // automatic ids continue after the largest id of the instance
     unsigned long long id0 = 0;
@@ -947,6 +971,7 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     l.s_id = S.id;
     l.err = h->err;
     l.precision = h->precision;
+    l.next_id = h->next_id + inst;
     CUDA_TRY(h, launch_load(l, s));
     // the other copy of the segment holds nothing
     CUDA_TRY(h, launch_fill_i32(h->st[1 - h->cur].cell, P.base, P.base + P.cap, -1, s));
@@ -955,27 +980,12 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     CUDA_TRY(h, cudaMemcpyAsync(h->seg_n + si, nn.data(), 8, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->seg_live + si, nn.data(), 8, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemsetAsync(h->hwm_alt + si, 0, 8, s));
-    if (stage) CUDA_TRY(h, cudaFreeAsync(stage, s));
-    unsigned long long nid = 0;
-    if (id) {
-        // largest loaded id + 1 (host input scanned here; device input on the host copy)
-        std::vector<uint32_t> tmp;
-        const uint32_t* hid = id;
-        if (on_device && n > 0) {
-            tmp.resize((size_t)n);
-            CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), id, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(h, cudaStreamSynchronize(s));
-            hid = tmp.data();
-        }
-        for (int64_t k = 0; k < n; ++k) nid = std::max<unsigned long long>(nid, (unsigned long long)hid[k] + 1);
-        unsigned long long cur = 0;
-        CUDA_TRY(h, cudaMemcpyAsync(&cur, h->next_id + inst, 8, cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(h, cudaStreamSynchronize(s));
-        nid = std::max(nid, cur);
-    } else {
-        nid = id0 + (unsigned long long)n;
+    (void)stage;
+    if (!id) {
+        // with explicit ids k_load has raised the next id to max(id) + 1 itself
+        const unsigned long long nid = id0 + (unsigned long long)n;
+        CUDA_TRY(h, cudaMemcpyAsync(h->next_id + inst, &nid, 8, cudaMemcpyHostToDevice, s));
     }
-    CUDA_TRY(h, cudaMemcpyAsync(h->next_id + inst, &nid, 8, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h->stale = true;
     return PIC_OK;
@@ -1227,7 +1237,7 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
     char* tmp = nullptr;
     const size_t scratch = (size_t)(nb + 1) * 8;
     const size_t outb = on_device ? 0 : n * (4 + 8 * 4 + 4 + 1) + 8 * 16;
-    CUDA_TRY(h, cudaMallocAsync((void**)&tmp, scratch + outb, s));
+    CUDA_TRY(h, io_buffer(h, scratch + outb + 16, &tmp));
     GetArgs g;
     const Store& S = h->st[h->cur];
     g.s_cell = S.cell;
@@ -1266,7 +1276,6 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
         if (id) CUDA_TRY(h, cudaMemcpyAsync(id, g.id, m * 4, cudaMemcpyDeviceToHost, s));
         if (state) CUDA_TRY(h, cudaMemcpyAsync(state, g.state, m, cudaMemcpyDeviceToHost, s));
     }
-    CUDA_TRY(h, cudaFreeAsync(tmp, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     return PIC_OK;
 }
@@ -1346,6 +1355,7 @@ int pic_destroy(pic_handle* h)
     for (auto e : h->event_pool) cudaEventDestroy(e);
     drop_graphs(h);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->io) cudaFree(h->io);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     cudaGetLastError();
     delete h;

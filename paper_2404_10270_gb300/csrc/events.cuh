@@ -40,19 +40,20 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z
 
 // A null-collision candidate of one particle (velocity u in cells/step, after the
 // move): process slot from the selection word `wsel`, energy threshold (below it the
-// event is a null collision), kinematics.  Returns true when u changed.  Ionization
-// appends two particles.
+// event is a null collision), kinematics.  Returns the instance-level index of the
+// process that took place (u changed), or -1 for a null event.  Ionization appends two
+// particles.  The caller counts the collision.
 template <typename T>
-__device__ __forceinline__ bool collide(const MoveArgs& a, const SegParams& P, int s,
-                                     uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
-                                     T& uz, uint32_t wsel)
+__device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, int s,
+                                    uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
+                                    T& uz, uint32_t wsel)
 {
     int q = -1;
     for (int k = 0; k < P.nproc; ++k)
         if ((uint64_t)wsel < P.slot_end[k]) { q = k; break; }
-    if (q < 0) return false;
+    if (q < 0) return -1;
     const T u2 = ux * ux + uy * uy + uz * uz;
-    if (!(u2 >= (T)P.thr_u2[q])) return false;  // below threshold: null event
+    if (!(u2 >= (T)P.thr_u2[q])) return -1;  // below threshold: null event
     const int kind = P.kind[q];
     if (kind == PIC_PROC_ELASTIC) {
         const uint4 r = draw(id, step, kRngScatter, P.key0, P.key1);
@@ -129,20 +130,19 @@ __device__ __forceinline__ bool collide(const MoveArgs& a, const SegParams& P, i
             atomicAdd(a.dep + Pi.node + j + 1, (unsigned long long)qr);
         }
     }
-    atomicAdd(a.collisions + (int64_t)P.inst * kMaxProc + P.proc[q], 1ull);
-    return true;
+    return P.proc[q];
 }
 
-// Wall phase for a particle that left [0, N) (rare): counts and energy of the
-// absorbed particle, then either absorption (returns 2), or volume re-injection with a
-// new position and Maxwellian velocity (returns 1).  Periodic walls are handled inline.
+// Wall phase for a particle that left [0, N) (rare): energy of the absorbed particle
+// (the caller counts it), then either absorption (returns 2), or volume re-injection
+// with a new position and Maxwellian velocity (returns 1).  Periodic walls are handled
+// in the mover.
 template <typename T>
 __device__ __forceinline__ int wall_event(const MoveArgs& a, const SegParams& P, int s, uint32_t id,
                                        int64_t step, int& j, T& f, T& ux, T& uy, T& uz)
 {
     const int wall = j < 0 ? 0 : 1;
     const double u2 = (double)ux * (double)ux + (double)uy * (double)uy + (double)uz * (double)uz;
-    atomicAdd(a.wall_count + 2 * s + wall, 1ull);
     atomicAdd(a.wall_energy + 2 * s + wall, P.kefac * u2);
     if (P.bc != PIC_BC_SOURCE) {
         atomicAdd(a.seg_live + s, ~0ull);  // -1
@@ -169,7 +169,18 @@ __device__ __forceinline__ int wall_event(const MoveArgs& a, const SegParams& P,
     return 1;
 }
 
-// One thread per queued particle (grid-stride over this step's queue).
+// Add `key`'s count once per group of lanes with the same key (key < 0: nothing).
+// Same-address atomics from every event would queue behind each other in L2.
+__device__ __forceinline__ void count_by_key(unsigned long long* counts, int key)
+{
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1)
+        atomicAdd(counts + key, (unsigned long long)__popc(grp));
+}
+
+// One thread per queued particle.  The loop is uniform across each warp (every lane
+// takes the same iterations), so that the collision and wall counts can be combined
+// per warp before they reach memory.
 template <typename T>
 __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs a)
 {
@@ -179,37 +190,48 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
     T* const uxp = static_cast<T*>(a.ux);
     T* const uyp = static_cast<T*>(a.uy);
     T* const uzp = static_cast<T*>(a.uz);
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint64_t e = a.rare[i];
-        const uint32_t kind = (uint32_t)(e & 3u);
-        const int s = (int)((e >> 2) & (uint64_t)(kMaxSegments - 1));
-        const int64_t slot = (int64_t)(e >> 24);
-        const SegParams& P = a.seg[s];
-        const uint32_t id = a.id[slot];
-        T f = offp[slot], vx = uxp[slot], vy = uyp[slot], vz = uzp[slot];
-        if (kind == kRareCandidate) {
-            const int j = (int)((uint32_t)a.cell[slot] & kCellMask);
-            const uint4 w = draw(id, step, kRngCollide, P.key0, P.key1);
-            if (collide<T>(a, P, s, id, step, j, f, vx, vy, vz, w.y)) {
-                uxp[slot] = vx;
-                uyp[slot] = vy;
-                uzp[slot] = vz;
-            }
-        } else {
-            int j = kind == kRareWallLow ? -1 : P.ncells;
-            if (wall_event<T>(a, P, s, id, step, j, f, vx, vy, vz) == 1) {
-                // re-injected: back in the store with a fresh clock, deposited here
-                a.cell[slot] = j;
-                offp[slot] = f;
-                uxp[slot] = vx;
-                uyp[slot] = vy;
-                uzp[slot] = vz;
-                const uint64_t qr = Prec<T>::qright(f);
-                atomicAdd(a.dep + P.node + j, (unsigned long long)(Prec<T>::S - qr));
-                atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
+    const unsigned long long lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         w < n; w += stride) {
+        const unsigned long long i = w + lane;
+        int ckey = -1, wkey = -1;  // collision counter, wall counter
+        if (i < n) {
+            const uint64_t e = a.rare[i];
+            const uint32_t kind = (uint32_t)(e & 3u);
+            const int s = (int)((e >> 2) & (uint64_t)(kMaxSegments - 1));
+            const int64_t slot = (int64_t)(e >> 24);
+            const SegParams& P = a.seg[s];
+            const uint32_t id = a.id[slot];
+            T f = offp[slot], vx = uxp[slot], vy = uyp[slot], vz = uzp[slot];
+            if (kind == kRareCandidate) {
+                const int j = (int)((uint32_t)a.cell[slot] & kCellMask);
+                const uint4 wd = draw(id, step, kRngCollide, P.key0, P.key1);
+                const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y);
+                if (p >= 0) {
+                    uxp[slot] = vx;
+                    uyp[slot] = vy;
+                    uzp[slot] = vz;
+                    ckey = P.inst * kMaxProc + p;
+                }
+            } else {
+                int j = kind == kRareWallLow ? -1 : P.ncells;
+                wkey = 2 * s + (kind == kRareWallLow ? 0 : 1);
+                if (wall_event<T>(a, P, s, id, step, j, f, vx, vy, vz) == 1) {
+                    // re-injected: back in the store with a fresh clock, deposited here
+                    a.cell[slot] = j;
+                    offp[slot] = f;
+                    uxp[slot] = vx;
+                    uyp[slot] = vy;
+                    uzp[slot] = vz;
+                    const uint64_t qr = Prec<T>::qright(f);
+                    atomicAdd(a.dep + P.node + j, (unsigned long long)(Prec<T>::S - qr));
+                    atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
+                }
             }
         }
+        count_by_key(a.collisions, ckey);
+        count_by_key(a.wall_count, wkey);
     }
 }
 

@@ -108,7 +108,7 @@ __device__ __forceinline__ i128 node_charge(const FieldArgs& f, const InstParams
 //   k_field_emit     per chunk: in-block scan of Z' + chunk prefix = R_j, then E_j and the
 //                    accelerations; also hands the deposit over for the next step.
 constexpr int kChunkThreads = 256;
-constexpr int kChunkPer = 8;  // nodes per thread
+constexpr int kChunkPer = 1;  // nodes per thread
 static_assert(kChunk == kChunkThreads * kChunkPer, "chunk layout");
 
 __global__ void __launch_bounds__(kChunkThreads) k_field_partial(const FieldArgs f)

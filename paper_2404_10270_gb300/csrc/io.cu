@@ -45,6 +45,13 @@ __global__ void k_load(const LoadArgs l)
         } else {
             l.s_cell[g] = -1;
         }
+        if (l.id) {
+            // the next automatic id follows the largest loaded one (cap and the grid
+            // stride are multiples of 32, so every lane of a warp is here together)
+            const unsigned m = __reduce_max_sync(0xffffffffu, k < l.n ? l.id[k] : 0u);
+            const unsigned any = __ballot_sync(0xffffffffu, k < l.n);
+            if (any && (threadIdx.x & 31) == 0) atomicMax(l.next_id, (unsigned long long)m + 1ull);
+        }
     }
 }
 

@@ -111,6 +111,7 @@ struct LoadArgs {
     uint32_t* s_id;
     unsigned* err;
     int precision;
+    unsigned long long* next_id;  // instance's next automatic id: raised to max(id) + 1
 };
 cudaError_t launch_load(const LoadArgs& l, cudaStream_t st);
 

@@ -50,7 +50,6 @@ constexpr int kMoveMinWarpsMag = BITPIC_MOVE_MIN_WARPS_MAG;  // the Boris (3V) v
 #define BITPIC_MOVE_MIN_WARPS64_MAG 24
 #endif
 constexpr int kMoveMinWarps64Mag = BITPIC_MOVE_MIN_WARPS64_MAG;  // the Boris variant, FP64
-constexpr int kDeadCell = -(1 << 30);
 
 struct MoveArgs {
     int32_t* cell;
@@ -229,6 +228,8 @@ __device__ __forceinline__ void st4(double* p, const double v[4])
 // cell), so per occupied cell the warp forms n_c and R_c by register reductions; lane
 // l then owns node wmin + l, takes R_{c-1} from lane l-1 by shuffle, and adds the node
 // total to HBM with one 64-bit reduction (no return value, so nothing waits on it).
+// jd = -1 marks an empty slot: as unsigned it is never the minimum of a live cell, as
+// signed never the maximum, and it matches no cell.
 template <typename Q>
 __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
                                              unsigned long long S,
@@ -236,15 +237,16 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    int lmin = INT_MAX, lmax = INT_MIN;
+    unsigned lmin = 0xFFFFFFFFu;
+    int lmax = -1;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (jd[k] >= 0) {
-            lmin = min(lmin, jd[k]);
-            lmax = max(lmax, jd[k]);
-        }
-    const int wmin = __reduce_min_sync(FULL, lmin);
-    if (wmin == INT_MAX) return;
+    for (int k = 0; k < 4; ++k) {
+        lmin = min(lmin, (unsigned)jd[k]);
+        lmax = max(lmax, jd[k]);
+    }
+    const unsigned wminu = __reduce_min_sync(FULL, lmin);
+    if (wminu == 0xFFFFFFFFu) return;  // no live particle in the tile
+    const int wmin = (int)wminu;
     const int wmax = __reduce_max_sync(FULL, lmax);
     const int ncell = wmax - wmin + 1;
     if (ncell < 32) {
@@ -456,12 +458,12 @@ k_move(const __grid_constant__ MoveArgs a)
                 }
             }
         }
-        // 6. deposit of the (new) positions
+        // 6. deposit of the (new) positions; an empty slot (cell word < 0) gets jd = -1
         int jd[4];
         Q qr[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            jd[k] = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : kDeadCell;
+            jd[k] = (c[k] >> 31) | (int)((uint32_t)c[k] & kCellMask);
             qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
         }
         warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0);
