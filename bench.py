@@ -429,8 +429,10 @@ def _run_ours(args, stream, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
+    t_sp = []
     for s, h in enumerate(host):
         sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
+        t_sp.append(time.perf_counter())
     t_load = time.perf_counter()
     sim.step(args.steps)
     sim.sync()
@@ -448,7 +450,8 @@ def _run_ours(args, stream, rank, world, local):
     torch.cuda.synchronize()
     t_end = time.perf_counter()
     e2e_s = t_end - t0
-    e2e_parts = {"load_s": t_load - t0, "steps_s": t_steps - t_load, "read_back_s": t_end - t_steps}
+    e2e_parts = {"load_s": t_load - t0, "load_species_s": [b - a for a, b in zip([t0] + t_sp[:-1], t_sp)],
+                 "steps_s": t_steps - t_load, "read_back_s": t_end - t_steps}
     e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
@@ -535,6 +538,26 @@ def profile_case(precision: str) -> int:
     return 0
 
 
+def profile_ensemble(scale: float) -> int:
+    """The small batched case the ncu captures of the magnetized mover use: the 512-instance
+    ensemble with every instance's particles per cell scaled by `scale` (0.1: ~5e7
+    particles, state larger than L2), deposit-only launch + 6 steps."""
+    import concurrent.futures as cf
+    __import__("__graft_entry__").build()
+    from paper_2404_10270_gb300 import capi
+    phys = W.ensemble(n_instances=512, scale=scale)
+    with cf.ThreadPoolExecutor(16) as ex:
+        loads = list(ex.map(lambda ip: W.initial_load(ip[1], seed=ip[0] + 1), enumerate(phys)))
+    sim = capi.Sim(phys, precision=capi.FP32, sort_interval=20, block=256)
+    for i, ld in enumerate(loads):
+        sim.load_all(ld, inst=i)
+    sim.step(6)
+    sim.sync()
+    print("profile ensemble ok", sum(len(x) for ld in loads for x in ld))
+    sim.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,9 +582,13 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small case the ncu captures use and exit")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--profile-ensemble", type=float, default=None, metavar="SCALE",
+                    help="run the small batched case the ncu captures use and exit")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case(args.precision)
+    if args.profile_ensemble is not None:
+        return profile_ensemble(args.profile_ensemble)
     if args.c5:
         return run_c5(args)
     if args.warmup < 3:

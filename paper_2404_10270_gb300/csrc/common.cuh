@@ -64,6 +64,7 @@ struct SegParams {
     uint32_t key0, key1;   // Philox key = instance seed
     double accel;          // c_s = (q/m) dt^2/dx: A = c_s E in cells/step^2
     double t[3], s[3];     // Boris: t = (q/m) B dt/2, s = 2t/(1+t.t)
+    float tf[3], sf[3];    // the same rounded to float (the FP32 form's values)
     double kefac;          // w m (dx/dt)^2 / 2: energy of |u|^2 = 1 (cells/step)^2
     double vinj;           // sqrt(T_s/m_s) in cells/step (volume source)
     double vneutral;       // sqrt(T_n/m_n) in cells/step
@@ -202,6 +203,25 @@ __device__ __forceinline__ int find_segment(const int64_t* __restrict__ tile_sta
                                             int64_t t)
 {
     int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The segment of tile t for a walker whose tiles only increase: from its previous
+// segment s (tiles [tile_start[s], end) with end = tile_start[s+1] cached by the
+// caller), a few steps forward, else a binary search over the rest.
+__device__ __forceinline__ int advance_segment(const int64_t* __restrict__ tile_start, int nseg,
+                                               int s, int64_t t)
+{
+#pragma unroll 1
+    for (int it = 0; it < 3; ++it) {
+        if (s + 1 >= nseg || __ldg(tile_start + s + 1) > t) return s;
+        ++s;
+    }
+    int lo = s, hi = nseg - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(tile_start + mid) <= t) lo = mid; else hi = mid - 1;

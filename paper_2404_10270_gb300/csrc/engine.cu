@@ -277,6 +277,10 @@ void seg_constants(const pic_instance& I, int s, SegParams* P)
     const double tt = P->t[0] * P->t[0] + P->t[1] * P->t[1] + P->t[2] * P->t[2];
     const double sf = 2.0 / (1.0 + tt);
     for (int k = 0; k < 3; ++k) P->s[k] = sf * P->t[k];
+    for (int k = 0; k < 3; ++k) {
+        P->tf[k] = (float)P->t[k];
+        P->sf[k] = (float)P->s[k];
+    }
     const double dxdt = I.dx / I.dt;
     P->kefac = 0.5 * S.mass * S.weight * (dxdt * dxdt);
     P->vinj = std::sqrt(S.temperature / S.mass) * vs;

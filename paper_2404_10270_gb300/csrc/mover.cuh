@@ -84,6 +84,9 @@ template <> struct Prec<float> {
     using Q = uint32_t;  // fixed-point charge of one particle (< 2^25)
     using T2 = float2;
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    // Boris vectors t, s of the segment in this precision
+    static __device__ __forceinline__ float bt(const SegParams& P, int k) { return P.tf[k]; }
+    static __device__ __forceinline__ float bs(const SegParams& P, int k) { return P.sf[k]; }
     static constexpr int min_warps = kMoveMinWarps;  // memory bound: as many warps as fit
     static constexpr int min_warps_mag = kMoveMinWarpsMag;
     static __device__ __forceinline__ uint64_t qright(float f)
@@ -123,6 +126,8 @@ template <> struct Prec<double> {
     using Q = uint64_t;  // fixed-point charge of one particle (< 2^49)
     using T2 = double2;
     static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double bt(const SegParams& P, int k) { return P.t[k]; }
+    static __device__ __forceinline__ double bs(const SegParams& P, int k) { return P.s[k]; }
     static constexpr int min_warps = kMoveMinWarps64;  // FP64-pipe bound: registers first
     static constexpr int min_warps_mag = kMoveMinWarps64Mag;
     // rint(f 2^48) for f in [0, 1), ties to even, from the bits: f = m 2^(e-1075), so
@@ -328,16 +333,22 @@ k_move(const __grid_constant__ MoveArgs a)
     const int dgrid = kGapMax - (int)(step % kGapMax);
     const int64_t total = a.tile_start[a.nseg];
     const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
+    int s = 0;                         // segment of the previous tile (tiles only increase)
+    int64_t s_begin = 0, s_end = -1;   // its tiles
     for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
          tile += wstride) {
-        const int s = find_segment(a.tile_start, a.nseg, tile);
+        if (tile >= s_end) {
+            s = advance_segment(a.tile_start, a.nseg, s, tile);
+            s_begin = __ldg(a.tile_start + s);
+            s_end = __ldg(a.tile_start + s + 1);
+        }
         const SegParams& P = a.seg[s];
         const int N = P.ncells;
         const int bc = P.bc;
         const int collides = P.collide;
         const uint32_t key0 = P.key0, key1 = P.key1;
         const int64_t node0 = P.node;
-        const int64_t quad = (tile - a.tile_start[s]) * 32 + lane;
+        const int64_t quad = (tile - s_begin) * 32 + lane;
         const int64_t nq = a.seg_nmove[s] >> 2;
         const bool act = quad < nq;
         const int64_t slot = P.base + 4 * quad;
@@ -372,8 +383,8 @@ k_move(const __grid_constant__ MoveArgs a)
                     ux[k] = ux[k] + acc;
                 } else {
                     const T half = T(0.5) * acc;
-                    const T t0 = (T)P.t[0], t1 = (T)P.t[1], t2 = (T)P.t[2];
-                    const T s0 = (T)P.s[0], s1 = (T)P.s[1], s2 = (T)P.s[2];
+                    const T t0 = Prec<T>::bt(P, 0), t1 = Prec<T>::bt(P, 1), t2 = Prec<T>::bt(P, 2);
+                    const T s0 = Prec<T>::bs(P, 0), s1 = Prec<T>::bs(P, 1), s2 = Prec<T>::bs(P, 2);
                     const T mx = ux[k] + half, my = uy[k], mz = uz[k];
                     const T px = mx + (my * t2 - mz * t1);
                     const T py = my + (mz * t0 - mx * t2);
