@@ -17,6 +17,8 @@ __global__ void k_load(const LoadArgs l)
     T* uy = static_cast<T*>(l.s_uy);
     T* uz = static_cast<T*>(l.s_uz);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t idmax = 0;  // largest loaded id seen by this thread
+    bool any = false;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < l.cap; k += stride) {
         const int64_t g = l.base + k;
         if (k < l.n) {
@@ -45,13 +47,16 @@ __global__ void k_load(const LoadArgs l)
         } else {
             l.s_cell[g] = -1;
         }
-        if (l.id) {
-            // the next automatic id follows the largest loaded one (cap and the grid
-            // stride are multiples of 32, so every lane of a warp is here together)
-            const unsigned m = __reduce_max_sync(0xffffffffu, k < l.n ? l.id[k] : 0u);
-            const unsigned any = __ballot_sync(0xffffffffu, k < l.n);
-            if (any && (threadIdx.x & 31) == 0) atomicMax(l.next_id, (unsigned long long)m + 1ull);
+        if (l.id && k < l.n) {
+            idmax = max(idmax, l.id[k]);
+            any = true;
         }
+    }
+    // the next automatic id follows the largest loaded one: one atomic per warp
+    if (l.id) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, idmax);
+        if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0)
+            atomicMax(l.next_id, (unsigned long long)m + 1ull);
     }
 }
 

@@ -314,6 +314,43 @@ def test_capacity_overflow_is_reported():
     sim.close()
 
 
+def _wall_flood(n_per_cell):
+    """Four cells, one species so hot (|u| ~ 100 cells/step) that nearly every particle
+    reaches a wall in the first step: the rare-event queue takes one entry per particle."""
+    sp = [W.Species("e", -1.0, 1.0, 0.5 / n_per_cell, 1.0e6, n_per_cell)]
+    return W.Physics(ncells=4, dx=0.5, dt=0.05, species=sp, processes=[],
+                     field=W.FIELD_NONE, seed=5)
+
+
+def test_wall_flood_within_the_queue_matches_oracle():
+    # 60,000 particles: within the queue's 65,536-entry floor
+    ensure_built()
+    phys = _wall_flood(15000)
+    loads = W.initial_load(phys, seed=5)
+    g, gm = run_gpu(phys, loads, 2, capi.FP64)
+    o, om = run_oracle(phys, loads, 2)
+    np.testing.assert_array_equal(gm["live"], om["live"])
+    np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
+    assert gm["wall_count"].sum() > 0.95 * 60000
+    np.testing.assert_allclose(gm["wall_energy"], om["wall_energy"], rtol=1e-12)
+
+
+def test_rare_event_queue_overflow_is_reported():
+    # 300,000 particles hitting the walls in one step overflow the queue (65,536 + a
+    # sixteenth of the capacity): the step reports PIC_ECAPACITY, nothing is dropped silently
+    ensure_built()
+    phys = _wall_flood(75000)
+    loads = W.initial_load(phys, seed=5)
+    sim = capi.Sim(phys, precision=capi.FP32)
+    sim.load_all(loads)
+    sim.step(1)
+    with pytest.raises(capi.PicError) as e:
+        sim.sync()
+    assert e.value.code == -4
+    assert "rare-event queue" in str(e.value)
+    sim.close()
+
+
 @pytest.mark.parametrize("precision,steps,tol", [(capi.FP64, 100, 1e-12), (capi.FP32, 10, 1e-5)])
 def test_magnetized_source_full_size(precision, steps, tol):
     """The magnetized workload at its full size: 4096 cells x 200 particles/cell/species
