@@ -93,6 +93,19 @@ __global__ void __launch_bounds__(1024) k_cell_scan(const SortArgs a)
     if (threadIdx.x == 0) a.newn[blockIdx.x] = sh[32];
 }
 
+// One lane's quad in flight through the scatter.
+template <typename T>
+struct SortQuad {
+    int c[4];
+    T vo[4], vx[4], vy[4], vz[4];
+    uint32_t vi[4];
+    int s;
+    int64_t slot;
+};
+
+// Scatter.  Each warp keeps the loads of its next tile in flight while it reserves the
+// destinations of the current one (an atomic round trip through L2 per cell group),
+// so the reservation latency does not stall the stream of loads.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
 {
@@ -113,55 +126,67 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
-    for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
-         tile += wstride) {
-        const int s = find_segment(a.tile_start, a.nseg, tile);
-        const SegParams& P = a.seg[s];
-        const int64_t quad = (tile - a.tile_start[s]) * 32 + lane;
-        const int64_t nq = a.seg_nmove[s] >> 2;
-        const int64_t slot = P.base + 4 * quad;
-        int c[4] = {-1, -1, -1, -1};
-        T vo[4], vx[4], vy[4], vz[4];
-        uint32_t vi[4] = {0u, 0u, 0u, 0u};
-        if (quad < nq) {
-            // the whole quad with 128-bit loads (the mover's access pattern)
-            const int4 cc = __ldcs(reinterpret_cast<const int4*>(cell + slot));
-            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
-            ld4(off + slot, vo);
-            ld4(ux + slot, vx);
-            ld4(uy + slot, vy);
-            ld4(uz + slot, vz);
-            const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(id + slot));
-            vi[0] = ii.x; vi[1] = ii.y; vi[2] = ii.z; vi[3] = ii.w;
+    int ls = 0;                            // segment walk of the loads (tiles only increase)
+    int64_t ls_begin = 0, ls_end = -1;
+    auto load = [&](int64_t tile, SortQuad<T>& q) {
+        if (tile >= ls_end) {
+            ls = advance_segment(a.tile_start, a.nseg, ls, tile);
+            ls_begin = __ldg(a.tile_start + ls);
+            ls_end = __ldg(a.tile_start + ls + 1);
         }
+        q.s = ls;
+        const int64_t quad = (tile - ls_begin) * 32 + lane;
+        q.slot = a.seg[ls].base + 4 * quad;
+        q.c[0] = q.c[1] = q.c[2] = q.c[3] = -1;
+        if (quad < (a.seg_nmove[ls] >> 2)) {
+            // the whole quad with 128-bit loads (the mover's access pattern)
+            const int4 cc = __ldcs(reinterpret_cast<const int4*>(cell + q.slot));
+            q.c[0] = cc.x; q.c[1] = cc.y; q.c[2] = cc.z; q.c[3] = cc.w;
+            ld4(off + q.slot, q.vo);
+            ld4(ux + q.slot, q.vx);
+            ld4(uy + q.slot, q.vy);
+            ld4(uz + q.slot, q.vz);
+            const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(id + q.slot));
+            q.vi[0] = ii.x; q.vi[1] = ii.y; q.vi[2] = ii.z; q.vi[3] = ii.w;
+        }
+    };
+    int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+    SortQuad<T> cur;
+    if (tile < total) load(tile, cur);
+    for (; tile < total; tile += wstride) {
+        SortQuad<T> nxt;
+        nxt.c[0] = nxt.c[1] = nxt.c[2] = nxt.c[3] = -1;
+        if (tile + wstride < total) load(tile + wstride, nxt);
+        const SegParams& P = a.seg[cur.s];
         // group equal cells of each slot across the warp; the four reservations are
         // independent, so they are all issued before the first one is waited for
         unsigned grp[4], base[4];
         int key[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            key[k] = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
+            key[k] = cur.c[k] >= 0 ? (int)((uint32_t)cur.c[k] & kCellMask) : -1 - lane;
             grp[k] = __match_any_sync(0xffffffffu, key[k]);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             base[k] = 0;
-            if (c[k] >= 0 && lane == __ffs(grp[k]) - 1)
+            if (cur.c[k] >= 0 && lane == __ffs(grp[k]) - 1)
                 base[k] = atomicAdd(a.hist + P.node + key[k], (unsigned)__popc(grp[k]));
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const unsigned b = __shfl_sync(0xffffffffu, base[k], __ffs(grp[k]) - 1);
-            if (c[k] >= 0) {
+            if (cur.c[k] >= 0) {
                 const int64_t to = P.base + (int64_t)b + __popc(grp[k] & lt);
-                dcell[to] = c[k];
-                doff[to] = vo[k];
-                dux[to] = vx[k];
-                duy[to] = vy[k];
-                duz[to] = vz[k];
-                did[to] = vi[k];
+                dcell[to] = cur.c[k];
+                doff[to] = cur.vo[k];
+                dux[to] = cur.vx[k];
+                duy[to] = cur.vy[k];
+                duz[to] = cur.vz[k];
+                did[to] = cur.vi[k];
             }
         }
+        cur = nxt;
     }
 }
 
