@@ -76,6 +76,11 @@ typedef struct {
     double weight;      /* w_s, physical particles per unit area per macro-particle */
     double temperature; /* T_s of the volume source's Maxwellian (PIC_BC_SOURCE) */
     int64_t capacity;   /* particle slots reserved (>= largest load + creations) */
+    int32_t nstep;      /* subcycling (Listing 7's x += nstep*vx): the species is advanced
+                           on the steps that are multiples of nstep, with time step
+                           nstep*dt, and deposited every step; 0 or 1 = every step
+                           (at most 4096) */
+    int32_t pad;
 } pic_species;
 
 /* One collision process against the uniform neutral background (null-collision
@@ -104,7 +109,9 @@ typedef struct {
     double m_neutral;  /* neutral background mass (units of m_e) */
     pic_species sp[PIC_MAX_SPECIES];
     int32_t nproc;
-    int32_t pad;
+    int32_t smooth;    /* 1: the density smoother (Section 2's "Density Smoother" phase):
+                          a 1-2-1 binomial filter of the interior node charge densities
+                          before the field solve, wall nodes unfiltered; 0: off */
     pic_process proc[PIC_MAX_PROC];
     uint64_t seed;     /* Philox4x32-10 key of this instance */
 } pic_instance;

@@ -130,11 +130,14 @@ struct orc_sim {
     double svec[ORC_MAX_SPECIES][3]; /* Boris s = 2 t / (1 + t.t) */
     double kefac[ORC_MAX_SPECIES];   /* w m (dx/dt)^2 / 2: energy per (cells/step)^2 */
     double vinj[ORC_MAX_SPECIES];    /* sqrt(T_s/m_s) in cells/step */
+    /* (with subcycling every "step" of a species above is its own step K dt) */
     int collides[ORC_MAX_SPECIES];   /* species has collision processes */
     uint32_t gapT[ORC_MAX_SPECIES][ORC_GAP_MAX + 1]; /* floor((1-P)^g 2^32), g = 1..127 */
     uint64_t slot_end[ORC_MAX_PROC]; /* cumulative slot bound of each process */
     double thr_u2[ORC_MAX_PROC];     /* energy threshold as |u|^2 */
-    double vneutral;                 /* sqrt(T_n/m_n) in cells/step */
+    double vneutral[ORC_MAX_SPECIES]; /* sqrt(T_n/m_n) in cells per step of the species */
+    int64_t nstep[ORC_MAX_SPECIES];  /* subcycling factor K >= 1 */
+    double vs[ORC_MAX_SPECIES];      /* physical velocity -> cells per step of the species */
     int has_B;
     /* grid */
     double* dens;   /* nspecies * (N+1): summed CIC weights per node */
@@ -195,7 +198,7 @@ orc_sim* orc_create(const orc_params* p)
         if (q->kind < 0 || q->kind > 2) return NULL;
     }
     for (int i = 0; i < p->nspecies; ++i)
-        if (!(p->sp[i].mass > 0)) return NULL;
+        if (!(p->sp[i].mass > 0) || p->sp[i].nstep < 0 || p->sp[i].nstep > 4096) return NULL;
 
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
@@ -212,20 +215,24 @@ orc_sim* orc_create(const orc_params* p)
         return NULL;
     }
 
-    const double vs = p->dt / p->dx; /* physical velocity -> cells per step */
     const double Bsq = p->B[0] * p->B[0] + p->B[1] * p->B[1] + p->B[2] * p->B[2];
     s->has_B = Bsq > 0.0;
     for (int i = 0; i < S; ++i) {
         const orc_species* q = &p->sp[i];
+        /* subcycling: the species' own time step is K dt (Listing 7's nstep) */
+        s->nstep[i] = q->nstep > 1 ? q->nstep : 1;
+        const double dt = (double)s->nstep[i] * p->dt;
+        const double vs = dt / p->dx; /* physical velocity -> cells per step */
+        s->vs[i] = vs;
         const double qm = q->charge / q->mass;
-        s->accel[i] = qm * (p->dt * p->dt / p->dx);
-        const double qmh = qm * (0.5 * p->dt);
+        s->accel[i] = qm * (dt * dt / p->dx);
+        const double qmh = qm * (0.5 * dt);
         for (int k = 0; k < 3; ++k) s->tvec[i][k] = qmh * p->B[k];
         const double tt = s->tvec[i][0] * s->tvec[i][0] + s->tvec[i][1] * s->tvec[i][1] +
                           s->tvec[i][2] * s->tvec[i][2];
         const double sf = 2.0 / (1.0 + tt);
         for (int k = 0; k < 3; ++k) s->svec[i][k] = sf * s->tvec[i][k];
-        const double dxdt = p->dx / p->dt;
+        const double dxdt = p->dx / dt;
         s->kefac[i] = 0.5 * q->mass * q->weight * (dxdt * dxdt);
         s->vinj[i] = sqrt(q->temperature / q->mass) * vs;
         /* null-collision candidate probability over one step: 1 - exp(-nu_max dt) */
@@ -235,7 +242,7 @@ orc_sim* orc_create(const orc_params* p)
         /* candidate steps form a Bernoulli sequence with P = 1 - exp(-nu_max dt); the
          * probability of g candidate-free steps in a row is (1-P)^g = exp(-g nu_max dt) */
         s->collides[i] = numax > 0.0;
-        const double x = numax * p->dt;
+        const double x = numax * dt;
         for (int g = 1; g <= ORC_GAP_MAX; ++g) {
             const double T = floor(exp(-(double)g * x) * TWO32);
             s->gapT[i][g] = T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T;
@@ -253,10 +260,12 @@ orc_sim* orc_create(const orc_params* p)
         if (last >= 0) s->slot_end[last] = (uint64_t)1 << 32;
     }
     for (int k = 0; k < p->nproc; ++k) {
-        const double m = p->sp[p->proc[k].species].mass;
-        s->thr_u2[k] = (2.0 * p->proc[k].threshold / m) * (vs * vs);
+        const int sp = p->proc[k].species;
+        const double m = p->sp[sp].mass;
+        s->thr_u2[k] = (2.0 * p->proc[k].threshold / m) * (s->vs[sp] * s->vs[sp]);
     }
-    s->vneutral = p->m_neutral > 0 ? sqrt(p->T_neutral / p->m_neutral) * vs : 0.0;
+    for (int i = 0; i < S; ++i)
+        s->vneutral[i] = p->m_neutral > 0 ? sqrt(p->T_neutral / p->m_neutral) * s->vs[i] : 0.0;
     return s;
 }
 
@@ -294,7 +303,7 @@ int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const doubl
         order[k].at = k;
     }
     qsort(order, (size_t)n, sizeof(id_at), cmp_id_at);
-    const double vs = s->p.dt / s->p.dx;
+    const double vs = s->vs[sp];
     for (int64_t r = 0; r < n; ++r) {
         int64_t k = order[r].at;
         a->cell[r] = cell[k];
@@ -373,6 +382,19 @@ int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* ph
 
 /* Field phase: charge density from the deposit, Poisson solve, then the pre-scaled
  * accelerations A_s = c_s E used by the gather. */
+/* Density smoother (Section 2's "Density Smoother" phase): a 1-2-1 binomial filter
+ * of the interior node densities rho[1..N-1], the wall nodes (half cells) kept. */
+void orc_smooth(int32_t N, double* rho)
+{
+    if (N < 2) return;
+    double prev = rho[0];
+    for (int j = 1; j < N; ++j) {
+        const double cur = rho[j];
+        rho[j] = 0.25 * prev + 0.5 * cur + 0.25 * rho[j + 1];
+        prev = cur;
+    }
+}
+
 static int solve_fields(orc_sim* s)
 {
     const int N = s->N, S = s->p.nspecies;
@@ -385,6 +407,7 @@ static int solve_fields(orc_sim* s)
             /* interior node: cell volume dx; wall node: half cell */
             s->rho[j] = (j == 0 || j == N) ? q / (0.5 * dx) : q / dx;
         }
+        if (s->p.smooth) orc_smooth(N, s->rho);
         int rc = orc_poisson(N, dx, s->p.eps0, s->rho, s->phi, s->E);
         if (rc) return rc;
     } else {
@@ -465,7 +488,8 @@ static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
     uint32_t w[4];
     draw(s, a->id[k], s->step, ORC_RNG_COLLIDE, w);
     if (!pending) {
-        const int D = ORC_GAP_MAX - (int)(s->step % ORC_GAP_MAX);
+        /* the grid of test steps counts the species' own steps (step / K) */
+        const int D = ORC_GAP_MAX - (int)((s->step / s->nstep[sp]) % ORC_GAP_MAX);
         int g = gap_steps(s, sp, w[0]);
         if (g > D) g = D;
         if (g == D) {
@@ -519,9 +543,9 @@ static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel)
         double z0, z1, z2, z3;
         box_muller(r[0], r[1], &z0, &z1);
         box_muller(r[2], r[3], &z2, &z3);
-        a->ux[k] = z0 * s->vneutral;
-        a->uy[k] = z1 * s->vneutral;
-        a->uz[k] = z2 * s->vneutral;
+        a->ux[k] = z0 * s->vneutral[sp];
+        a->uy[k] = z1 * s->vneutral[sp];
+        a->uz[k] = z2 * s->vneutral[sp];
     } else { /* ORC_PROC_IONIZE */
         /* the incident electron pays the threshold; the rest is shared equally by the
          * two outgoing electrons, both isotropic; the ion is a background neutral */
@@ -546,7 +570,9 @@ static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel)
         b.cell = a->cell[k];
         b.off = a->off[k];
         b.e[0] = us * n2[0]; b.e[1] = us * n2[1]; b.e[2] = us * n2[2];
-        b.i[0] = z0 * s->vneutral; b.i[1] = z1 * s->vneutral; b.i[2] = z2 * s->vneutral;
+        /* the ion's velocity in its own species' units */
+        const double vn = s->vneutral[P->product];
+        b.i[0] = z0 * vn; b.i[1] = z1 * vn; b.i[2] = z2 * vn;
         int rc = add_birth(s, &b);
         if (rc) return rc;
     }
@@ -584,6 +610,8 @@ static int one_step(orc_sim* s)
     if (rc) return rc;
     s->nbirths = 0;
     for (int sp = 0; sp < S; ++sp) {
+        /* subcycling: a species moves on the steps that are multiples of its K */
+        if (s->step % s->nstep[sp] != 0) continue;
         orc_store* a = &s->st[sp];
         const double* A = s->A + (size_t)sp * (N + 1);
         const double* t = s->tvec[sp];
@@ -719,7 +747,7 @@ int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx
 {
     if (!s || sp < 0 || sp >= s->p.nspecies) return -1;
     const orc_store* a = &s->st[sp];
-    const double iv = s->p.dx / s->p.dt; /* cells per step -> physical */
+    const double iv = s->p.dx / ((double)s->nstep[sp] * s->p.dt); /* cells per step -> physical */
     for (int64_t k = 0; k < a->n; ++k) {
         if (cell) cell[k] = a->cell[k];
         if (off) off[k] = a->off[k];

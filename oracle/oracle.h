@@ -42,6 +42,10 @@ typedef struct {
     double mass;        /* m_s in units of m_e */
     double weight;      /* w_s: physical particles per unit area per macro-particle */
     double temperature; /* T_s (units of T_e) of the volume source's Maxwellian */
+    int32_t nstep;      /* subcycling (Listing 7's x += nstep*vx): advanced on the steps
+                           that are multiples of nstep with time step nstep*dt; 0 or 1 =
+                           every step */
+    int32_t pad;
 } orc_species;
 
 typedef struct {
@@ -65,7 +69,7 @@ typedef struct {
     double m_neutral;   /* neutral background mass */
     orc_species sp[ORC_MAX_SPECIES];
     int32_t nproc;
-    int32_t pad;
+    int32_t smooth;     /* 1: 1-2-1 filter of the interior charge density before Poisson */
     orc_process proc[ORC_MAX_PROC];
     uint64_t seed;      /* Philox key */
 } orc_params;
@@ -108,6 +112,10 @@ int orc_moments_get(orc_sim* s, orc_moments* m, double* density, double* phi, do
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the published
  * round function. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Density smoother: 1-2-1 binomial filter of rho[1..N-1] in place (N+1 entries; the
+ * wall entries rho[0], rho[N] are kept). */
+void orc_smooth(int32_t N, double* rho);
 
 /* Dirichlet Poisson problem of the field phase: -phi[j-1]+2phi[j]-phi[j+1] =
  * dx^2 rho[j]/eps0 for 1<=j<=N-1, phi[0]=phi[N]=0, by the Thomas algorithm, then

@@ -19,7 +19,7 @@ MAX_PROC = 8
 
 class _Species(C.Structure):
     _fields_ = [("charge", C.c_double), ("mass", C.c_double), ("weight", C.c_double),
-                ("temperature", C.c_double)]
+                ("temperature", C.c_double), ("nstep", C.c_int32), ("pad", C.c_int32)]
 
 
 class _Process(C.Structure):
@@ -32,7 +32,7 @@ class _Params(C.Structure):
                 ("nspecies", C.c_int32), ("dx", C.c_double), ("dt", C.c_double),
                 ("eps0", C.c_double), ("E_ext", C.c_double), ("B", C.c_double * 3),
                 ("T_neutral", C.c_double), ("m_neutral", C.c_double),
-                ("sp", _Species * MAX_SPECIES), ("nproc", C.c_int32), ("pad", C.c_int32),
+                ("sp", _Species * MAX_SPECIES), ("nproc", C.c_int32), ("smooth", C.c_int32),
                 ("proc", _Process * MAX_PROC), ("seed", C.c_uint64)]
 
 
@@ -64,6 +64,8 @@ def lib():
         L.orc_moments_get.argtypes = [C.c_void_p, C.POINTER(_Moments), P, P, P]
         L.orc_philox4x32_10.argtypes = [P, P, P]
         L.orc_poisson.argtypes = [C.c_int32, C.c_double, C.c_double, P, P, P]
+        L.orc_smooth.argtypes = [C.c_int32, P]
+        L.orc_smooth.restype = None
         _lib = L
     return _lib
 
@@ -83,8 +85,9 @@ def params_struct(phys) -> _Params:
         p.B[k] = phys.B[k]
     p.T_neutral, p.m_neutral = phys.T_neutral, phys.m_neutral
     for i, s in enumerate(phys.species):
-        p.sp[i] = _Species(s.charge, s.mass, s.weight, s.temperature)
+        p.sp[i] = _Species(s.charge, s.mass, s.weight, s.temperature, s.nstep, 0)
     p.nproc = len(phys.processes)
+    p.smooth = phys.smooth
     for k, q in enumerate(phys.processes):
         p.proc[k] = _Process(q.kind, q.species, q.product, 0, q.nu, q.threshold)
     p.seed = phys.seed
@@ -110,6 +113,13 @@ def poisson(rho, dx: float, eps0: float = 1.0):
     if rc:
         raise RuntimeError("orc_poisson failed: %d" % rc)
     return phi, E
+
+
+def smooth(rho):
+    """The density smoother (1-2-1 filter of the interior entries); returns a copy."""
+    out = np.array(rho, dtype=np.float64, copy=True)
+    lib().orc_smooth(len(out) - 1, _ptr(out))
+    return out
 
 
 class Oracle:

@@ -40,7 +40,8 @@ class PicError(RuntimeError):
 
 class pic_species(C.Structure):
     _fields_ = [("charge", C.c_double), ("mass", C.c_double), ("weight", C.c_double),
-                ("temperature", C.c_double), ("capacity", C.c_int64)]
+                ("temperature", C.c_double), ("capacity", C.c_int64), ("nstep", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class pic_process(C.Structure):
@@ -53,7 +54,7 @@ class pic_instance(C.Structure):
                 ("nspecies", C.c_int32), ("dx", C.c_double), ("dt", C.c_double),
                 ("eps0", C.c_double), ("E_ext", C.c_double), ("B", C.c_double * 3),
                 ("T_neutral", C.c_double), ("m_neutral", C.c_double),
-                ("sp", pic_species * MAX_SPECIES), ("nproc", C.c_int32), ("pad", C.c_int32),
+                ("sp", pic_species * MAX_SPECIES), ("nproc", C.c_int32), ("smooth", C.c_int32),
                 ("proc", pic_process * MAX_PROC), ("seed", C.c_uint64)]
 
 
@@ -145,8 +146,10 @@ def instance_struct(phys: W.Physics, capacity: Optional[Sequence[int]] = None) -
     I.T_neutral, I.m_neutral = phys.T_neutral, phys.m_neutral
     for i, s in enumerate(phys.species):
         cap = capacity[i] if capacity is not None else int(s.ppc * phys.ncells * s.capacity_factor)
-        I.sp[i] = pic_species(s.charge, s.mass, s.weight, s.temperature, max(int(cap), 4))
+        I.sp[i] = pic_species(s.charge, s.mass, s.weight, s.temperature, max(int(cap), 4),
+                              s.nstep, 0)
     I.nproc = len(phys.processes)
+    I.smooth = phys.smooth
     for k, q in enumerate(phys.processes):
         I.proc[k] = pic_process(q.kind, q.species, q.product, 0, q.nu, q.threshold)
     I.seed = phys.seed

@@ -77,7 +77,7 @@ struct SegParams {
     uint64_t slot_end[kMaxProc];   // cumulative slot bounds in [0, 2^32]
     double thr_u2[kMaxProc];       // energy threshold as |u|^2 (cells/step)^2
     int32_t collide;       // any process
-    int32_t pad2;
+    int32_t nstep;         // subcycling: moved on the steps that are multiples of nstep
 };
 
 constexpr int kChunk = 256;  // nodes per block of the field solve
@@ -94,6 +94,8 @@ struct InstParams {
     int64_t ev_cap;        // event buffer entries of this instance
     double lambda;         // E = lambda * G (integer field numerator G)
     int32_t z[kMaxSpecies]; // charge q_s w_s in integer multiples of the unit delta
+    int32_t smooth;        // density smoother on: the field uses 4x the filtered charges
+    int32_t pad;
 };
 
 // A particle the mover leaves to the event kernel (a null-collision candidate or a

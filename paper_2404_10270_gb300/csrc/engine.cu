@@ -67,7 +67,7 @@ struct pic_handle {
     int64_t total_cap = 0, seg_nodes = 0, inst_nodes = 0, max_cap = 0, ev_total = 0;
     int64_t rare_cap = 0;  // entries of the per-step rare-event queue
     int max_nodes = 0;
-    bool any_poisson = false, any_mag = false, any_ionize = false;
+    bool any_poisson = false, any_mag = false, any_ionize = false, any_subcycle = false;
 
     SegParams* segd = nullptr;
     InstParams* instd = nullptr;
@@ -80,6 +80,8 @@ struct pic_handle {
     int nchunks = 0;
     int* chunk_inst = nullptr;
     i128 *part_sum = nullptr, *part_w = nullptr, *part_off = nullptr;
+    i128* zs = nullptr;  // smoothed node charges (instances with the density smoother)
+    bool any_smooth = false;
     unsigned* hist = nullptr;
     unsigned long long *newn = nullptr, *seg_n = nullptr, *seg_live = nullptr, *hwm_alt = nullptr;
     int64_t *seg_nmove = nullptr, *tile_start = nullptr;
@@ -245,8 +247,10 @@ int validate_instance(const pic_instance& I, int idx, std::string* why)
             return bad("species " + std::to_string(s) + ": mass > 0, finite charge, weight >= 0");
         if (I.sp[s].capacity < 0) return bad("negative capacity");
         if (!(I.sp[s].temperature >= 0)) return bad("temperature must be >= 0");
+        if (I.sp[s].nstep < 0 || I.sp[s].nstep > 4096) return bad("nstep must be 0..4096");
     }
     if (I.nproc < 0 || I.nproc > PIC_MAX_PROC) return bad("nproc must be 0..8");
+    if (I.smooth != 0 && I.smooth != 1) return bad("smooth must be 0 or 1");
     for (int k = 0; k < I.nproc; ++k) {
         const pic_process& P = I.proc[k];
         if (P.kind < 0 || P.kind > 2) return bad("process kind");
@@ -263,16 +267,26 @@ int validate_instance(const pic_instance& I, int idx, std::string* why)
     return PIC_OK;
 }
 
+// Subcycling factor of species s (>= 1).
+int species_nstep(const pic_instance& I, int s)
+{
+    return I.sp[s].nstep > 1 ? I.sp[s].nstep : 1;
+}
+
 // Derive the per-segment constants.  The expressions mirror the definitions in the
 // mover: A = c_s E with c_s = (q/m) dt^2/dx; Boris t = (q/m) B dt/2, s = 2t/(1+t.t);
 // candidate probability P = 1 - exp(-nu_max dt) as floor(P 2^32).
 void seg_constants(const pic_instance& I, int s, SegParams* P)
 {
     const pic_species& S = I.sp[s];
-    const double vs = I.dt / I.dx;
+    // subcycling: the species' own time step is nstep * dt (Listing 7's x += nstep*vx);
+    // every per-step constant below is for that step
+    P->nstep = species_nstep(I, s);
+    const double dt = (double)P->nstep * I.dt;
+    const double vs = dt / I.dx;
     const double qm = S.charge / S.mass;
-    P->accel = qm * (I.dt * I.dt / I.dx);
-    const double qmh = qm * (0.5 * I.dt);
+    P->accel = qm * (dt * dt / I.dx);
+    const double qmh = qm * (0.5 * dt);
     for (int k = 0; k < 3; ++k) P->t[k] = qmh * I.B[k];
     const double tt = P->t[0] * P->t[0] + P->t[1] * P->t[1] + P->t[2] * P->t[2];
     const double sf = 2.0 / (1.0 + tt);
@@ -281,7 +295,7 @@ void seg_constants(const pic_instance& I, int s, SegParams* P)
         P->tf[k] = (float)P->t[k];
         P->sf[k] = (float)P->s[k];
     }
-    const double dxdt = I.dx / I.dt;
+    const double dxdt = I.dx / dt;
     P->kefac = 0.5 * S.mass * S.weight * (dxdt * dxdt);
     P->vinj = std::sqrt(S.temperature / S.mass) * vs;
     P->vneutral = I.m_neutral > 0 ? std::sqrt(I.T_neutral / I.m_neutral) * vs : 0.0;
@@ -291,7 +305,7 @@ void seg_constants(const pic_instance& I, int s, SegParams* P)
         if (I.proc[k].species == s) numax += I.proc[k].nu;
     // candidate steps: Bernoulli(P), P = 1 - exp(-nu_max dt); a run of g candidate-free
     // steps has probability (1-P)^g = exp(-g nu_max dt)
-    const double x = numax * I.dt;
+    const double x = numax * dt;
     P->gap[0] = 0xFFFFFFFFu;
     for (int g = 1; g <= kGapMax; ++g) {
         const double T = std::floor(std::exp(-(double)g * x) * 4294967296.0);
@@ -391,6 +405,7 @@ FieldArgs field_args(pic_handle* h)
     f.part_off = h->part_off;
     f.step = h->step_d;
     f.any_poisson = h->any_poisson ? 1 : 0;
+    f.zs = h->zs;
     return f;
 }
 
@@ -402,8 +417,8 @@ int launch_move(pic_handle* h, bool move)
         Span sp(h, 0);
         h->kernels += 1;
         const cudaError_t e = h->precision == PIC_FP64
-                                  ? launch_move_f64(a, mag, move, h->nt, h->grid_move, h->stream)
-                                  : launch_move_f32(a, mag, move, h->nt, h->grid_move, h->stream);
+                                  ? launch_move_f64(a, mag, move, h->any_subcycle, h->nt, h->grid_move, h->stream)
+                                  : launch_move_f32(a, mag, move, h->any_subcycle, h->nt, h->grid_move, h->stream);
         CUDA_TRY(h, e);
     }
     if (move) {
@@ -695,6 +710,12 @@ int pic_create(const pic_config* cfg, pic_handle** out)
             h->any_poisson = true;
         }
         ip.lambda = delta / (2.0 * (double)I.ncells * S * I.eps0);
+        // the smoother's integer charges are 4x the filtered ones (exact power of two)
+        ip.smooth = (I.field == PIC_FIELD_POISSON && I.smooth) ? 1 : 0;
+        if (ip.smooth) {
+            ip.lambda *= 0.25;
+            h->any_smooth = true;
+        }
         // ionization events per step are at most the candidates of the projectile
         // species: about capacity x P per step; reserve 4x that, at least 4096
         bool ionize = false;
@@ -706,7 +727,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
                 double numax = 0.0;
                 for (int q = 0; q < I.nproc; ++q)
                     if (I.proc[q].species == sp) numax += I.proc[q].nu;
-                const double P = -std::expm1(-numax * I.dt);
+                const double P = -std::expm1(-numax * I.dt * species_nstep(I, sp));
                 const double cap = (double)std::max<int64_t>(I.sp[sp].capacity, 1);
                 const int64_t want = (int64_t)std::ceil(cap * std::min(1.0, 4.0 * P));
                 evcap = std::max<int64_t>(evcap, std::max<int64_t>(4096, want));
@@ -716,6 +737,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         ev += ip.ev_cap;
         h->any_ionize |= ionize;
         if (I.B[0] != 0.0 || I.B[1] != 0.0 || I.B[2] != 0.0) h->any_mag = true;
+        for (int s = 0; s < I.nspecies; ++s)
+            if (species_nstep(I, s) > 1) h->any_subcycle = true;
         for (int s = 0; s < I.nspecies; ++s) {
             SegParams P;
             std::memset(&P, 0, sizeof(P));
@@ -739,7 +762,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
                 double numax = 0.0;
                 for (int q = 0; q < I.nproc; ++q)
                     if (I.proc[q].species == s) numax += I.proc[q].nu;
-                const double Pc = -std::expm1(-numax * I.dt);
+                const double Pc = -std::expm1(-numax * I.dt * species_nstep(I, s));
                 const double frac = std::min(1.0, 4.0 * Pc + (I.bc == PIC_BC_PERIODIC ? 0.0 : 1.0 / 16.0));
                 h->rare_cap += (int64_t)std::ceil((double)P.cap * frac);
             }
@@ -807,6 +830,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->part_sum, (size_t)h->nchunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->part_w, (size_t)h->nchunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->part_off, (size_t)h->nchunks);
+    if (rc == PIC_OK && h->any_smooth) rc = dalloc(h, &h->zs, (size_t)inode);
     if (rc == PIC_OK) rc = dalloc(h, &h->phi_d, (size_t)h->max_nodes);
     if (rc == PIC_OK) rc = dalloc(h, &h->segd, (size_t)h->nseg);
     if (rc == PIC_OK) rc = dalloc(h, &h->instd, (size_t)h->ninst);
@@ -962,7 +986,9 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     l.state = dstate;
     l.n = n;
     l.id0 = (uint32_t)id0;
-    l.vscale = (flags & PIC_CELL_UNITS) ? 1.0 : h->inst[inst].dt / h->inst[inst].dx;
+    l.vscale = (flags & PIC_CELL_UNITS)
+                   ? 1.0
+                   : (double)species_nstep(h->inst[inst], species) * h->inst[inst].dt / h->inst[inst].dx;
     l.base = P.base;
     l.cap = P.cap;
     l.ncells = P.ncells;
@@ -1252,7 +1278,9 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
     g.s_id = S.id;
     g.base = P.base;
     g.nslots = (int64_t)nslots;
-    g.vscale_inv = (flags & PIC_CELL_UNITS) ? 1.0 : h->inst[inst].dx / h->inst[inst].dt;
+    g.vscale_inv = (flags & PIC_CELL_UNITS)
+                       ? 1.0
+                       : h->inst[inst].dx / ((double)species_nstep(h->inst[inst], species) * h->inst[inst].dt);
     g.precision = h->precision;
     g.block_count = reinterpret_cast<unsigned long long*>(tmp);
     g.capacity = (int64_t)live;

@@ -102,7 +102,7 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
             ev >= (unsigned long long)I.ev_cap) {
             set_error(a.err, kErrCapacity);
         } else {
-            const T vn = (T)P.vneutral;
+            const T vn = (T)Pi.vneutral;  // the ion's velocity in its own species' units
             const int64_t ge = P.base + (int64_t)ke, gi = Pi.base + (int64_t)ki;
             T* off = static_cast<T*>(a.off);
             T* vx = static_cast<T*>(a.ux);

@@ -102,6 +102,22 @@ __device__ __forceinline__ i128 node_charge(const FieldArgs& f, const InstParams
     return z;
 }
 
+// Density smoother (Section 2's "Density Smoother" phase), in the integer charges: the
+// 1-2-1 filter of the interior node densities, wall nodes (half cells, density 2Z/dx)
+// kept, times 4 so that it stays exact:
+//     Z''_j = Z_{j-1} w_{j-1} + 2 Z_j + Z_{j+1} w_{j+1},  w = 2 at a wall node, else 1,
+//     Z''_0 = 4 Z_0, Z''_N = 4 Z_N;
+// lambda carries the 1/4.  Node charges of [0, N] only (dep is not being written).
+__device__ __forceinline__ i128 smoothed_charge(const FieldArgs& f, const InstParams& I, int j,
+                                                const unsigned long long* dep)
+{
+    const int N = I.ncells;
+    const i128 zc = node_charge(f, I, j, dep);
+    if (j == 0 || j == N) return 4 * zc;
+    const i128 zl = node_charge(f, I, j - 1, dep), zr = node_charge(f, I, j + 1, dep);
+    return (j - 1 == 0 ? 2 * zl : zl) + 2 * zc + (j + 1 == N ? 2 * zr : zr);
+}
+
 // The solve runs over chunks of kChunk nodes (one block each):
 //   k_field_partial  per chunk: S_c = sum of Z' and W_c = sum of (N-j) Z' over the chunk;
 //   k_field_chunks   per instance: exclusive prefix of S_c over its chunks, U = sum of W_c;
@@ -125,8 +141,16 @@ __global__ void __launch_bounds__(kChunkThreads) k_field_partial(const FieldArgs
 #pragma unroll
     for (int t = 0; t < kChunkPer; ++t) {
         const int j = j0 + t;
-        if (j <= 0 || j >= N) continue;
-        const i128 z = node_charge(f, I, j, f.dep);
+        if (j < 0 || j > N) continue;
+        i128 z;
+        if (I.smooth) {
+            // the filtered charges of all nodes, walls included, for the emit phase
+            z = smoothed_charge(f, I, j, f.dep);
+            f.zs[I.inode + j] = z;
+        } else {
+            z = node_charge(f, I, j, f.dep);
+        }
+        if (j == 0 || j == N) continue;
         sum += z;
         wsum += (i128)(N - j) * z;
     }
@@ -189,6 +213,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_field_emit(const FieldArgs f,
             f.dep[P.node + j] = 0ull;
             z[t] += (i128)I.z[k] * (i128)(long long)d;
         }
+        if (I.smooth && poisson) z[t] = f.zs[I.inode + j];
         if (j > 0 && j < N) run += z[t];
     }
     if (!poisson) return;  // uniform per block: one instance per chunk
@@ -247,9 +272,12 @@ __global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, 
     const int j0 = min(nn, (int)threadIdx.x * C), j1 = min(nn, j0 + C);
     // pass 1: R at the start of this thread's run, U
     i128 sum = 0, wsum = 0;
+    auto charge = [&](int j) {
+        return I.smooth ? smoothed_charge(f, I, j, f.dep_last) : node_charge(f, I, j, f.dep_last);
+    };
     for (int j = j0; j < j1; ++j) {
         if (j == 0 || j == N) continue;
-        const i128 z = node_charge(f, I, j, f.dep_last);
+        const i128 z = charge(j);
         sum += z;
         wsum += (i128)(N - j) * z;
     }
@@ -259,7 +287,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, 
     // pass 2: sum of R over this thread's run, then the exclusive prefix U_{j0}
     i128 R = R0, rsum = 0;
     for (int j = j0; j < j1; ++j) {
-        if (j != 0 && j != N) R += node_charge(f, I, j, f.dep_last);
+        if (j != 0 && j != N) R += charge(j);
         rsum += R;
     }
     i128 run = block_excl_scan(rsum, &tot, sh);
@@ -267,7 +295,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, 
     for (int j = j0; j < j1; ++j) {
         const i128 Phi = (i128)j * U - (i128)N * run;
         phi[j] = (2.0 * dx * I.lambda) * i128_to_double(Phi);
-        if (j != 0 && j != N) R += node_charge(f, I, j, f.dep_last);
+        if (j != 0 && j != N) R += charge(j);
         run += R;
     }
 }

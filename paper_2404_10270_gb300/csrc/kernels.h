@@ -11,10 +11,11 @@ struct MoveArgs;
 
 // ---- mover (mover_f32.cu, mover_f64.cu) ---------------------------------------
 // `move` = false deposits the loaded particles without moving them (the density
-// phase of the initial field).  Returns the launch error.
-cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, int nt, int grid,
+// phase of the initial field); `sub`: some species is subcycled.  Returns the launch
+// error.
+cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, int nt, int grid,
                             cudaStream_t st);
-cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, int nt, int grid,
+cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, int nt, int grid,
                             cudaStream_t st);
 // The rare events the mover queued this step (events.cu): collision candidates and
 // wall hits, one thread each, `grid` blocks of 128 threads.
@@ -44,6 +45,8 @@ struct FieldArgs {
     i128* part_w;
     i128* part_off;
     int64_t* step;                    // incremented once per emit
+    i128* zs;                         // per instance node arrays: 4x the smoothed node
+                                      // charge (instances with the smoother), else unused
     int any_poisson;
 };
 cudaError_t launch_field(const FieldArgs& f, bool advance_step, cudaStream_t st);

@@ -316,7 +316,9 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
 // keeps many tiles' loads in flight.  The gather reads each particle's node pair with
 // one vector load (the node arrays are small and stay in L1/L2).  The loop is free of
 // calls; walls and collision candidates are queued for the event kernel.
-template <typename T, int NT, bool MAG, bool MOVE>
+// SUB: some species of the batch is subcycled (else every segment moves every step and
+// the clock grid is the global one, computed once).
+template <typename T, int NT, bool MAG, bool MOVE, bool SUB>
 __global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
@@ -329,18 +331,28 @@ k_move(const __grid_constant__ MoveArgs a)
     T* const uzp = static_cast<T*>(a.uz);
     const T2* const accp = static_cast<const T2*>(a.accel);
     const int64_t step = MOVE ? *a.step : 0;
-    // steps to the next multiple of kGapMax, where every clock without a candidate tests
-    const int dgrid = kGapMax - (int)(step % kGapMax);
     const int64_t total = a.tile_start[a.nseg];
     const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
     int s = 0;                         // segment of the previous tile (tiles only increase)
     int64_t s_begin = 0, s_end = -1;   // its tiles
+    bool moves = MOVE;                 // the segment moves this step (subcycling)
+    // steps (of the segment's species) to the next multiple of kGapMax
+    int dgrid = kGapMax - (int)(step % kGapMax);
     for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
          tile += wstride) {
         if (tile >= s_end) {
             s = advance_segment(a.tile_start, a.nseg, s, tile);
             s_begin = __ldg(a.tile_start + s);
             s_end = __ldg(a.tile_start + s + 1);
+            if (MOVE && SUB) {
+                // a species with subcycling factor K moves on the steps that are multiples
+                // of K; its collision clock counts its own steps (step / K), and at the
+                // multiples of kGapMax of those every clock without a candidate tests
+                const int ks = a.seg[s].nstep;
+                const int64_t own = ks == 1 ? step : step / ks;
+                moves = ks == 1 || own * ks == step;
+                dgrid = kGapMax - (int)(own % kGapMax);
+            }
         }
         const SegParams& P = a.seg[s];
         const int N = P.ncells;
@@ -360,14 +372,14 @@ k_move(const __grid_constant__ MoveArgs a)
             const int4 cc = __ldcs(reinterpret_cast<const int4*>(a.cell + slot));
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
             ld4(offp + slot, f);
-            if (MOVE) ld4(uxp + slot, ux);
-            if (MOVE && MAG) {
+            if (MOVE && (!SUB || moves)) ld4(uxp + slot, ux);
+            if (MOVE && MAG && (!SUB || moves)) {
                 ld4(uyp + slot, uy);
                 ld4(uzp + slot, uz);
             }
         }
 
-        if (MOVE) {
+        if (MOVE && (!SUB || moves)) {
             unsigned cand = 0, wlo = 0, whi = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {

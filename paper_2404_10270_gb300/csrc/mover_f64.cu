@@ -6,15 +6,22 @@ namespace bitpic {
 
 namespace {
 template <int NT>
-cudaError_t go(const MoveArgs& a, bool mag, bool move, int grid, cudaStream_t st)
+cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, int grid, cudaStream_t st)
 {
     if (move) {
-        if (mag)
-            k_move<double, NT, true, true><<<grid, NT, 0, st>>>(a);
-        else
-            k_move<double, NT, false, true><<<grid, NT, 0, st>>>(a);
+        if (mag) {
+            if (sub)
+                k_move<double, NT, true, true, true><<<grid, NT, 0, st>>>(a);
+            else
+                k_move<double, NT, true, true, false><<<grid, NT, 0, st>>>(a);
+        } else {
+            if (sub)
+                k_move<double, NT, false, true, true><<<grid, NT, 0, st>>>(a);
+            else
+                k_move<double, NT, false, true, false><<<grid, NT, 0, st>>>(a);
+        }
     } else {
-        k_move<double, NT, false, false><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, false, false, false><<<grid, NT, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -23,19 +30,19 @@ template <int NT>
 int occupancy(bool mag)
 {
     int n = 0;
-    cudaError_t e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true>, NT, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true>, NT, 0);
+    cudaError_t e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false>, NT, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true, false>, NT, 0);
     return e == cudaSuccess ? n : 0;
 }
 }  // namespace
 
-cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, int nt, int grid,
+cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, int nt, int grid,
                             cudaStream_t st)
 {
     switch (nt) {
-        case 128: return go<128>(a, mag, move, grid, st);
-        case 512: return go<512>(a, mag, move, grid, st);
-        default: return go<256>(a, mag, move, grid, st);
+        case 128: return go<128>(a, mag, move, sub, grid, st);
+        case 512: return go<512>(a, mag, move, sub, grid, st);
+        default: return go<256>(a, mag, move, sub, grid, st);
     }
 }
 

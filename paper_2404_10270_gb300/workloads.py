@@ -47,6 +47,7 @@ class Species:
     temperature: float
     ppc: int = 0                 # particles per cell at load time
     capacity_factor: float = 1.0  # slots reserved per loaded particle (creation slack)
+    nstep: int = 1                # subcycling: advanced every nstep steps with nstep*dt
 
 
 @dataclasses.dataclass
@@ -74,6 +75,7 @@ class Physics:
     m_neutral: float = 100.0
     seed: int = 1
     sort_interval: int = 20
+    smooth: int = 0           # 1: density smoother (1-2-1 filter) before the field solve
 
     @property
     def length(self) -> float:
@@ -85,10 +87,12 @@ class Physics:
 
 def bounded_small(ncells: int = 256, ppc: int = 100, seed: int = 1,
                   m_i: float = 100.0, nu: float = 0.01, dx: float = 0.5,
-                  dt: float = 0.05) -> Physics:
-    """Grounded absorbing walls, electrons + ions, elastic e-n and i-n charge exchange."""
+                  dt: float = 0.05, ion_nstep: int = 1) -> Physics:
+    """Grounded absorbing walls, electrons + ions, elastic e-n and i-n charge exchange.
+    ion_nstep > 1 subcycles the ions (advanced every ion_nstep steps)."""
     w = dx / ppc
-    sp = [Species("e", -1.0, 1.0, w, 1.0, ppc), Species("i", 1.0, m_i, w, 1.0, ppc)]
+    sp = [Species("e", -1.0, 1.0, w, 1.0, ppc),
+          Species("i", 1.0, m_i, w, 1.0, ppc, nstep=ion_nstep)]
     pr = [Process(PROC_ELASTIC, 0, nu), Process(PROC_CX, 1, nu)]
     return Physics(ncells=ncells, dx=dx, dt=dt, species=sp, processes=pr,
                    T_neutral=1.0 / 20.0, m_neutral=m_i, seed=seed)
@@ -96,13 +100,14 @@ def bounded_small(ncells: int = 256, ppc: int = 100, seed: int = 1,
 
 def magnetized_source(ncells: int = 4096, ppc: int = 200, seed: int = 1,
                       m_i: float = 1836.0, angle_deg: float = 80.0, B: float = 2.0,
-                      nu: float = 0.01, capacity_factor: float = 1.5) -> Physics:
+                      nu: float = 0.01, capacity_factor: float = 1.5,
+                      ion_nstep: int = 1) -> Physics:
     """Oblique magnetic field, volume source, elastic + ionization + charge exchange."""
     dx, dt = 0.5, 0.05
     w = dx / ppc
     th = math.radians(angle_deg)
     sp = [Species("e", -1.0, 1.0, w, 1.0, ppc, capacity_factor),
-          Species("i", 1.0, m_i, w, 1.0, ppc, capacity_factor)]
+          Species("i", 1.0, m_i, w, 1.0, ppc, capacity_factor, nstep=ion_nstep)]
     pr = [Process(PROC_ELASTIC, 0, nu), Process(PROC_IONIZE, 0, nu, 13.6 / 20.0, 1),
           Process(PROC_CX, 1, nu)]
     return Physics(ncells=ncells, dx=dx, dt=dt, species=sp, processes=pr, bc=BC_SOURCE,
