@@ -67,7 +67,7 @@ enum { PIC_FP32 = 0, PIC_FP64 = 1 };                          /* particle state 
 enum { PIC_DEVICE = 1, PIC_CELL_UNITS = 2 };                  /* flags of load/get */
 enum { PIC_BC_ABSORB = 0, PIC_BC_PERIODIC = 1, PIC_BC_SOURCE = 2 };
 enum { PIC_FIELD_POISSON = 0, PIC_FIELD_NONE = 1, PIC_FIELD_EXTERNAL = 2 };
-enum { PIC_PROC_ELASTIC = 0, PIC_PROC_CX = 1, PIC_PROC_IONIZE = 2 };
+enum { PIC_PROC_ELASTIC = 0, PIC_PROC_CX = 1, PIC_PROC_IONIZE = 2, PIC_PROC_EXCITE = 3 };
 
 /* One species of one instance. */
 typedef struct {
@@ -77,9 +77,10 @@ typedef struct {
     double temperature; /* T_s of the volume source's Maxwellian (PIC_BC_SOURCE) */
     int64_t capacity;   /* particle slots reserved (>= largest load + creations) */
     int32_t nstep;      /* subcycling (Listing 7's x += nstep*vx): the species is advanced
-                           on the steps that are multiples of nstep, with time step
-                           nstep*dt, and deposited every step; 0 or 1 = every step
-                           (at most 4096) */
+                           with time step nstep*dt on the steps n (counted from 0) with
+                           (n+1) mod nstep = 0, so that every species is at the same time
+                           at the multiples of nstep*dt, and deposited every step; 0 or
+                           1 = every step (at most 4096) */
     int32_t pad;
 } pic_species;
 
@@ -87,7 +88,8 @@ typedef struct {
  * Monte Carlo; the paper's collision phase, Section 2).  The collision frequency is
  * `nu` for projectile energies at or above `threshold` and 0 below. */
 typedef struct {
-    int32_t kind;      /* PIC_PROC_* */
+    int32_t kind;      /* PIC_PROC_*; PIC_PROC_EXCITE: energy loss of `threshold`, new
+                          direction uniform on the sphere */
     int32_t species;   /* projectile species */
     int32_t product;   /* PIC_PROC_IONIZE: species of the created ion, else -1 */
     int32_t pad;
@@ -114,6 +116,16 @@ typedef struct {
                           before the field solve, wall nodes unfiltered; 0: off */
     pic_process proc[PIC_MAX_PROC];
     uint64_t seed;     /* Philox4x32-10 key of this instance */
+    /* Neutral target species (the paper's test case, Section 3 Table 1: electrons, D+ and
+       D neutrals as particles): 0 = every process collides with the uniform background;
+       k+1 = species k (charge 0) is the target of every process: a candidate in cell j is
+       kept with probability min(1, n_j / nref), n_j the live target particles whose cell
+       was j at the start of the step, and an ionization turns the live target particle of
+       cell j with the smallest id into the product ion (same id, position and velocity),
+       creating one electron.  The target species must move only on the sort steps: its
+       nstep equals the sort interval. */
+    int32_t target;
+    int32_t nref;      /* target particles per cell at which the processes' nu apply */
 } pic_instance;
 
 typedef struct {

@@ -112,7 +112,9 @@ typedef struct {
 
 typedef struct {
     uint32_t parent;    /* parent id: children are numbered by the rank of this id */
-    int32_t esp, isp;   /* species of the new electron and of the new ion */
+    int32_t esp, isp;   /* species of the new electron and of the new ion (-1: the ion is
+                           a converted target particle) */
+    int32_t psp;        /* product ion species of the process */
     int32_t cell;
     double off;
     double e[3], i[3];  /* velocities (cells per step) */
@@ -139,6 +141,12 @@ struct orc_sim {
     int64_t nstep[ORC_MAX_SPECIES];  /* subcycling factor K >= 1 */
     double vs[ORC_MAX_SPECIES];      /* physical velocity -> cells per step of the species */
     int has_B;
+    /* neutral target species (p.target = k+1): per cell j, the live target particles
+     * whose cell was j at the start of the step, as positions in the target store in
+     * ascending id order (tfirst[j] .. tfirst[j+1]-1 of tlist) */
+    int64_t* tlist;
+    int64_t* tfirst;
+    int64_t tcap;
     /* grid */
     double* dens;   /* nspecies * (N+1): summed CIC weights per node */
     double* A;      /* nspecies * (N+1): pre-scaled acceleration on nodes */
@@ -195,8 +203,10 @@ orc_sim* orc_create(const orc_params* p)
             return NULL;
         if (q->kind == ORC_PROC_IONIZE && (q->product < 0 || q->product >= p->nspecies))
             return NULL;
-        if (q->kind < 0 || q->kind > 2) return NULL;
+        if (q->kind < 0 || q->kind > 3) return NULL;
     }
+    if (p->target < 0 || p->target > p->nspecies) return NULL;
+    if (p->target > 0 && (p->sp[p->target - 1].charge != 0.0 || p->nref < 1)) return NULL;
     for (int i = 0; i < p->nspecies; ++i)
         if (!(p->sp[i].mass > 0) || p->sp[i].nstep < 0 || p->sp[i].nstep > 4096) return NULL;
 
@@ -274,6 +284,7 @@ void orc_destroy(orc_sim* s)
     if (!s) return;
     for (int i = 0; i < ORC_MAX_SPECIES; ++i) store_free(&s->st[i]);
     free(s->dens); free(s->A); free(s->phi); free(s->E); free(s->rho); free(s->births);
+    free(s->tlist); free(s->tfirst);
     free(s);
 }
 
@@ -463,7 +474,8 @@ static int gap_steps(const orc_sim* s, int sp, uint32_t w)
     return g;
 }
 
-static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel);
+static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel,
+                     uint32_t wdens);
 
 /* Collision phase for one particle (null-collision MCC).  Whether a step holds a
  * collision candidate is a Bernoulli(P) sequence per particle; instead of one draw per
@@ -488,8 +500,9 @@ static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
     uint32_t w[4];
     draw(s, a->id[k], s->step, ORC_RNG_COLLIDE, w);
     if (!pending) {
-        /* the grid of test steps counts the species' own steps (step / K) */
-        const int D = ORC_GAP_MAX - (int)((s->step / s->nstep[sp]) % ORC_GAP_MAX);
+        /* the grid of test steps counts the species' own steps ((step+1)/K - 1) */
+        const int64_t own = (s->step + 1) / s->nstep[sp] - 1;
+        const int D = ORC_GAP_MAX - (int)(own % ORC_GAP_MAX);
         int g = gap_steps(s, sp, w[0]);
         if (g > D) g = D;
         if (g == D) {
@@ -502,14 +515,24 @@ static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
         }
     }
     a->mcc[k] = 0;
-    return candidate(s, sp, a, k, w[1]);
+    return candidate(s, sp, a, k, w[1], w[2]);
 }
 
-/* A collision candidate: process slot from the selection word, energy threshold
- * (below it the event is a null collision), kinematics. */
-static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel)
+/* A collision candidate: with a particle target, first the target density: kept with
+ * probability min(1, n_j / nref) by the word wdens against floor(n_j 2^32 / nref) (n_j
+ * the live target particles whose cell was j at the start of the step, j the
+ * candidate's cell); then the process slot from the selection word, the energy
+ * threshold (below it the event is a null collision), kinematics. */
+static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel,
+                     uint32_t wdens)
 {
     const uint32_t id = a->id[k];
+    if (s->p.target) {
+        const int j = a->cell[k];
+        const uint64_t nj = (uint64_t)(s->tfirst[j + 1] - s->tfirst[j]);
+        const uint64_t nr = (uint64_t)s->p.nref;
+        if (nj < nr && (uint64_t)wdens >= (nj << 32) / nr) return 0;
+    }
     int proc = -1;
     for (int q = 0; q < s->p.nproc; ++q) {
         if (s->p.proc[q].species != sp) continue;
@@ -546,6 +569,16 @@ static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel)
         a->ux[k] = z0 * s->vneutral[sp];
         a->uy[k] = z1 * s->vneutral[sp];
         a->uz[k] = z2 * s->vneutral[sp];
+    } else if (P->kind == ORC_PROC_EXCITE) {
+        /* excitation: the electron loses the threshold energy and leaves in a direction
+         * uniform on the sphere */
+        draw(s, id, s->step, ORC_RNG_SCATTER, r);
+        double n[3];
+        iso_dir(r[0], r[1], n);
+        const double sp2 = sqrt(u2 - s->thr_u2[proc]);
+        a->ux[k] = sp2 * n[0];
+        a->uy[k] = sp2 * n[1];
+        a->uz[k] = sp2 * n[2];
     } else { /* ORC_PROC_IONIZE */
         /* the incident electron pays the threshold; the rest is shared equally by the
          * two outgoing electrons, both isotropic; the ion is a background neutral */
@@ -566,7 +599,10 @@ static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel)
         orc_birth b;
         b.parent = id;
         b.esp = sp;
-        b.isp = P->product;
+        /* with a particle target the ion is the converted target particle (after the
+         * particle loop), not a new particle */
+        b.isp = s->p.target ? -1 : P->product;
+        b.psp = P->product;
         b.cell = a->cell[k];
         b.off = a->off[k];
         b.e[0] = us * n2[0]; b.e[1] = us * n2[1]; b.e[2] = us * n2[2];
@@ -603,15 +639,115 @@ static void reinject(orc_sim* s, int sp, orc_store* a, int64_t k)
     a->uz[k] = z2 * s->vinj[sp];
 }
 
+/* The live target particles by their cell at the start of the step, ascending ids
+ * within a cell (the target store is kept in ascending id order). */
+static int index_targets(orc_sim* s)
+{
+    const int N = s->N;
+    const orc_store* a = &s->st[s->p.target - 1];
+    if (a->n + 1 > s->tcap) {
+        void* q = realloc(s->tlist, (size_t)(a->n + 1) * sizeof(int64_t));
+        if (!q) return -2;
+        s->tlist = (int64_t*)q;
+        s->tcap = a->n + 1;
+    }
+    if (!s->tfirst) {
+        s->tfirst = (int64_t*)calloc((size_t)N + 2, sizeof(int64_t));
+        if (!s->tfirst) return -2;
+    }
+    memset(s->tfirst, 0, ((size_t)N + 2) * sizeof(int64_t));
+    for (int64_t k = 0; k < a->n; ++k)
+        if (a->alive[k]) s->tfirst[a->cell[k] + 1] += 1;
+    for (int j = 0; j < N; ++j) s->tfirst[j + 1] += s->tfirst[j];
+    int64_t* cur = (int64_t*)malloc(((size_t)N + 1) * sizeof(int64_t));
+    if (!cur) return -2;
+    memcpy(cur, s->tfirst, ((size_t)N + 1) * sizeof(int64_t));
+    for (int64_t k = 0; k < a->n; ++k)
+        if (a->alive[k]) s->tlist[cur[a->cell[k]]++] = k;
+    free(cur);
+    return 0;
+}
+
+/* Reorder a store by ascending id (after target particles joined it as ions). */
+static int store_sort_by_id(orc_store* a)
+{
+    if (a->n < 2) return 0;
+    id_at* order = (id_at*)malloc((size_t)a->n * sizeof(id_at));
+    orc_store b;
+    memset(&b, 0, sizeof(b));
+    if (!order || store_reserve(&b, a->n)) {
+        free(order);
+        store_free(&b);
+        return -2;
+    }
+    for (int64_t k = 0; k < a->n; ++k) {
+        order[k].id = a->id[k];
+        order[k].at = k;
+    }
+    qsort(order, (size_t)a->n, sizeof(id_at), cmp_id_at);
+    for (int64_t r = 0; r < a->n; ++r) {
+        const int64_t k = order[r].at;
+        b.cell[r] = a->cell[k]; b.off[r] = a->off[k];
+        b.ux[r] = a->ux[k]; b.uy[r] = a->uy[k]; b.uz[r] = a->uz[k];
+        b.id[r] = a->id[k]; b.alive[r] = a->alive[k]; b.mcc[r] = a->mcc[k];
+    }
+    b.n = a->n;
+    free(order);
+    store_free(a);
+    *a = b;
+    return 0;
+}
+
+/* Ionization against the particle target: in each cell j, the r_j ionizations of the
+ * step (r_j electrons of cell j) turn the first r_j live target particles of cell j
+ * (as of the start of the step, smallest ids first) into product ions: same id,
+ * position and physical velocity, collision clock 0.  A cell with fewer targets than
+ * ionizations converts what it has. */
+static int convert_targets(orc_sim* s)
+{
+    const int t = s->p.target - 1, N = s->N;
+    orc_store* a = &s->st[t];
+    int64_t* taken = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+    if (!taken) return -2;
+    int touched[ORC_MAX_SPECIES] = {0};
+    for (int64_t r = 0; r < s->nbirths; ++r) {
+        const orc_birth* b = &s->births[r];
+        if (b->isp >= 0) continue;
+        const int j = b->cell;
+        if (taken[j] >= s->tfirst[j + 1] - s->tfirst[j]) continue;
+        const int64_t v = s->tlist[s->tfirst[j] + taken[j]++];
+        orc_store* ion = &s->st[b->psp];
+        if (store_reserve(ion, ion->n + 1)) { free(taken); return -2; }
+        const int64_t m = ion->n++;
+        const double ratio = (double)s->nstep[b->psp] / (double)s->nstep[t];
+        ion->cell[m] = a->cell[v];
+        ion->off[m] = a->off[v];
+        ion->ux[m] = a->ux[v] * ratio;
+        ion->uy[m] = a->uy[v] * ratio;
+        ion->uz[m] = a->uz[v] * ratio;
+        ion->id[m] = a->id[v];
+        ion->alive[m] = 1;
+        ion->mcc[m] = 0;
+        a->alive[v] = 0;
+        touched[b->psp] = 1;
+    }
+    free(taken);
+    for (int sp = 0; sp < s->p.nspecies; ++sp)
+        if (touched[sp] && store_sort_by_id(&s->st[sp])) return -2;
+    return 0;
+}
+
 static int one_step(orc_sim* s)
 {
     const int N = s->N, S = s->p.nspecies;
     int rc = ensure_fields(s);
     if (rc) return rc;
     s->nbirths = 0;
+    if (s->p.target && (rc = index_targets(s))) return rc;
     for (int sp = 0; sp < S; ++sp) {
-        /* subcycling: a species moves on the steps that are multiples of its K */
-        if (s->step % s->nstep[sp] != 0) continue;
+        /* subcycling: a species with factor K moves on the steps n with (n+1) mod K = 0,
+         * so that all species meet at the multiples of K dt */
+        if ((s->step + 1) % s->nstep[sp] != 0) continue;
         orc_store* a = &s->st[sp];
         const double* A = s->A + (size_t)sp * (N + 1);
         const double* t = s->tvec[sp];
@@ -680,13 +816,16 @@ static int one_step(orc_sim* s)
         }
     }
     /* creation: children numbered by the rank of the parent id among this step's
-     * ionizing parents; electron 2r, ion 2r+1 after the largest id so far */
+     * ionizing parents; electron 2r, ion 2r+1 after the largest id so far (with a
+     * particle target only the electron is new: id r; the ion is a converted target) */
     if (s->nbirths > 0) {
         qsort(s->births, (size_t)s->nbirths, sizeof(orc_birth), cmp_birth);
+        if (s->p.target && (rc = convert_targets(s))) return rc;
         const uint32_t base = s->next_id;
+        const int per = s->p.target ? 1 : 2;
         for (int64_t r = 0; r < s->nbirths; ++r) {
             const orc_birth* b = &s->births[r];
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < per; ++c) {
                 const int sp = c == 0 ? b->esp : b->isp;
                 const double* u = c == 0 ? b->e : b->i;
                 orc_store* a = &s->st[sp];
@@ -697,12 +836,12 @@ static int one_step(orc_sim* s)
                 a->ux[k] = u[0];
                 a->uy[k] = u[1];
                 a->uz[k] = u[2];
-                a->id[k] = base + (uint32_t)(2 * r + c);
+                a->id[k] = base + (uint32_t)(per * r + c);
                 a->alive[k] = 1;
                 a->mcc[k] = 0;
             }
         }
-        s->next_id = base + (uint32_t)(2 * s->nbirths);
+        s->next_id = base + (uint32_t)(per * s->nbirths);
     }
     /* drop absorbed particles (ids stay ascending) */
     for (int sp = 0; sp < S; ++sp) {

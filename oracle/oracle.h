@@ -28,7 +28,7 @@ extern "C" {
 
 enum { ORC_BC_ABSORB = 0, ORC_BC_PERIODIC = 1, ORC_BC_SOURCE = 2 };
 enum { ORC_FIELD_POISSON = 0, ORC_FIELD_NONE = 1, ORC_FIELD_EXTERNAL = 2 };
-enum { ORC_PROC_ELASTIC = 0, ORC_PROC_CX = 1, ORC_PROC_IONIZE = 2 };
+enum { ORC_PROC_ELASTIC = 0, ORC_PROC_CX = 1, ORC_PROC_IONIZE = 2, ORC_PROC_EXCITE = 3 };
 /* Philox counter word 3 ("purpose") of every draw the step makes. */
 enum { ORC_RNG_COLLIDE = 0, ORC_RNG_SCATTER = 1, ORC_RNG_MAXWELL = 2,
        ORC_RNG_INJECT_A = 3, ORC_RNG_INJECT_B = 4, ORC_RNG_IONIZE_E = 5,
@@ -42,8 +42,8 @@ typedef struct {
     double mass;        /* m_s in units of m_e */
     double weight;      /* w_s: physical particles per unit area per macro-particle */
     double temperature; /* T_s (units of T_e) of the volume source's Maxwellian */
-    int32_t nstep;      /* subcycling (Listing 7's x += nstep*vx): advanced on the steps
-                           that are multiples of nstep with time step nstep*dt; 0 or 1 =
+    int32_t nstep;      /* subcycling (Listing 7's x += nstep*vx): advanced with time step
+                           nstep*dt on the steps n with (n+1) mod nstep = 0; 0 or 1 =
                            every step */
     int32_t pad;
 } orc_species;
@@ -72,6 +72,9 @@ typedef struct {
     int32_t smooth;     /* 1: 1-2-1 filter of the interior charge density before Poisson */
     orc_process proc[ORC_MAX_PROC];
     uint64_t seed;      /* Philox key */
+    int32_t target;     /* 0: uniform neutral background; k+1: species k (charge 0) is the
+                           particle target of every process (see orc_step) */
+    int32_t nref;       /* target particles per cell at which the processes' nu apply */
 } orc_params;
 
 typedef struct orc_sim orc_sim;

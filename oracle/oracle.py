@@ -33,7 +33,8 @@ class _Params(C.Structure):
                 ("eps0", C.c_double), ("E_ext", C.c_double), ("B", C.c_double * 3),
                 ("T_neutral", C.c_double), ("m_neutral", C.c_double),
                 ("sp", _Species * MAX_SPECIES), ("nproc", C.c_int32), ("smooth", C.c_int32),
-                ("proc", _Process * MAX_PROC), ("seed", C.c_uint64)]
+                ("proc", _Process * MAX_PROC), ("seed", C.c_uint64), ("target", C.c_int32),
+                ("nref", C.c_int32)]
 
 
 class _Moments(C.Structure):
@@ -91,6 +92,7 @@ def params_struct(phys) -> _Params:
     for k, q in enumerate(phys.processes):
         p.proc[k] = _Process(q.kind, q.species, q.product, 0, q.nu, q.threshold)
     p.seed = phys.seed
+    p.target, p.nref = phys.target, phys.nref
     return p
 
 

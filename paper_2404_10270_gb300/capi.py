@@ -55,7 +55,8 @@ class pic_instance(C.Structure):
                 ("eps0", C.c_double), ("E_ext", C.c_double), ("B", C.c_double * 3),
                 ("T_neutral", C.c_double), ("m_neutral", C.c_double),
                 ("sp", pic_species * MAX_SPECIES), ("nproc", C.c_int32), ("smooth", C.c_int32),
-                ("proc", pic_process * MAX_PROC), ("seed", C.c_uint64)]
+                ("proc", pic_process * MAX_PROC), ("seed", C.c_uint64), ("target", C.c_int32),
+                ("nref", C.c_int32)]
 
 
 class pic_config(C.Structure):
@@ -153,6 +154,7 @@ def instance_struct(phys: W.Physics, capacity: Optional[Sequence[int]] = None) -
     for k, q in enumerate(phys.processes):
         I.proc[k] = pic_process(q.kind, q.species, q.product, 0, q.nu, q.threshold)
     I.seed = phys.seed
+    I.target, I.nref = phys.target, phys.nref
     return I
 
 

@@ -77,7 +77,7 @@ struct SegParams {
     uint64_t slot_end[kMaxProc];   // cumulative slot bounds in [0, 2^32]
     double thr_u2[kMaxProc];       // energy threshold as |u|^2 (cells/step)^2
     int32_t collide;       // any process
-    int32_t nstep;         // subcycling: moved on the steps that are multiples of nstep
+    int32_t nstep;         // subcycling: moved on the steps n with (n+1) mod nstep = 0
 };
 
 constexpr int kChunk = 256;  // nodes per block of the field solve

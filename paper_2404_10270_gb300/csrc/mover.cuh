@@ -345,13 +345,14 @@ k_move(const __grid_constant__ MoveArgs a)
             s_begin = __ldg(a.tile_start + s);
             s_end = __ldg(a.tile_start + s + 1);
             if (MOVE && SUB) {
-                // a species with subcycling factor K moves on the steps that are multiples
-                // of K; its collision clock counts its own steps (step / K), and at the
-                // multiples of kGapMax of those every clock without a candidate tests
+                // a species with subcycling factor K moves on the steps n with
+                // (n+1) mod K = 0 (all species meet at the multiples of K dt); its
+                // collision clock counts its own steps, (n+1)/K - 1, and at the multiples
+                // of kGapMax of those every clock without a candidate tests
                 const int ks = a.seg[s].nstep;
-                const int64_t own = ks == 1 ? step : step / ks;
-                moves = ks == 1 || own * ks == step;
-                dgrid = kGapMax - (int)(own % kGapMax);
+                const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
+                moves = ks == 1 || q * ks == step + 1;
+                dgrid = kGapMax - (int)((q - 1) % kGapMax);
             }
         }
         const SegParams& P = a.seg[s];

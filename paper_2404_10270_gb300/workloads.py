@@ -35,7 +35,7 @@ import numpy as np
 # enums, identical in meaning on both sides of the library boundary
 BC_ABSORB, BC_PERIODIC, BC_SOURCE = 0, 1, 2
 FIELD_POISSON, FIELD_NONE, FIELD_EXTERNAL = 0, 1, 2
-PROC_ELASTIC, PROC_CX, PROC_IONIZE = 0, 1, 2
+PROC_ELASTIC, PROC_CX, PROC_IONIZE, PROC_EXCITE = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -47,7 +47,7 @@ class Species:
     temperature: float
     ppc: int = 0                 # particles per cell at load time
     capacity_factor: float = 1.0  # slots reserved per loaded particle (creation slack)
-    nstep: int = 1                # subcycling: advanced every nstep steps with nstep*dt
+    nstep: int = 1                # subcycling: advanced with nstep*dt on steps n, (n+1) % nstep == 0
 
 
 @dataclasses.dataclass
@@ -76,6 +76,8 @@ class Physics:
     seed: int = 1
     sort_interval: int = 20
     smooth: int = 0           # 1: density smoother (1-2-1 filter) before the field solve
+    target: int = 0           # k+1: species k (neutral particles) is the collision target
+    nref: int = 0             # target particles per cell at which the processes' nu apply
 
     @property
     def length(self) -> float:
@@ -113,6 +115,27 @@ def magnetized_source(ncells: int = 4096, ppc: int = 200, seed: int = 1,
     return Physics(ncells=ncells, dx=dx, dt=dt, species=sp, processes=pr, bc=BC_SOURCE,
                    B=(B * math.cos(th), B * math.sin(th), 0.0), T_neutral=1.0 / 20.0,
                    m_neutral=m_i, seed=seed)
+
+
+def ionization_case(ncells: int = 100000, ppc: int = 100, seed: int = 1,
+                    nu_el: float = 0.01, nu_exc: float = 0.002, nu_iz: float = 0.002,
+                    m_d: float = 3670.0, sort_interval: int = 20,
+                    dx: float = 0.5, dt: float = 0.05) -> Physics:
+    """The paper's test case (Section 3, Table 1) in normalized units: a periodic
+    unbounded plasma of electrons, D+ ions and D neutrals, all particles, uniform at
+    equal densities (ppc each); T_e = T_i = 1 (20 eV), T_n = 0.05 (1 eV); no field solve
+    and no smoother; electron-neutral elastic, excitation (10.2 eV) and ionization
+    (13.6 eV) against the neutral particles, which the ionizations deplete.  The
+    neutrals move once per sort cycle (nstep = sort_interval)."""
+    w = dx / ppc
+    sp = [Species("e", -1.0, 1.0, w, 1.0, ppc, 2.0),
+          Species("D+", 1.0, m_d, w, 1.0, ppc, 2.0),
+          Species("D", 0.0, m_d, w, 0.05, ppc, 1.0, nstep=sort_interval)]
+    pr = [Process(PROC_ELASTIC, 0, nu_el), Process(PROC_EXCITE, 0, nu_exc, 10.2 / 20.0),
+          Process(PROC_IONIZE, 0, nu_iz, 13.6 / 20.0, 1)]
+    return Physics(ncells=ncells, dx=dx, dt=dt, species=sp, processes=pr, bc=BC_PERIODIC,
+                   field=FIELD_NONE, T_neutral=0.05, m_neutral=m_d, seed=seed,
+                   sort_interval=sort_interval, target=3, nref=ppc)
 
 
 def bounded_large(ncells: int = 65536, ppc: int = 1500, seed: int = 1) -> Physics:

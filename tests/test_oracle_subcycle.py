@@ -1,9 +1,10 @@
 """Pins of the oracle's per-species subcycling (Listing 7's x += nstep*vx) against
 closed forms.
 
-A species with subcycling factor K is advanced on the steps n = 0, K, 2K, ... with
-the time step K dt and deposited every step, so after n steps it has made ceil(n/K)
-moves of K dt each: free streaming gives x = x_0 + ceil(n/K) K v dt; in a uniform field
+A species with subcycling factor K is advanced on the steps n = K-1, 2K-1, ... (so that
+every species is at the same time at the multiples of K dt) with the time step K dt and
+deposited every step, so after n steps it has made floor(n/K) moves of K dt each: free
+streaming gives x = x_0 + floor(n/K) K v dt; in a uniform field
 the leapfrog with step K dt gives, after m moves, v_m = v_0 + m a K dt and
 x_m = x_0 + m K dt v_0 + a (K dt)^2 m (m+1)/2; and the candidate steps of its collision
 clock are a Bernoulli sequence on its own steps with P = 1 - exp(-nu K dt).  K = 1 is
@@ -41,7 +42,7 @@ def test_subcycled_free_streaming(K, steps):
     o.load(0, _load(cell, off, v))
     o.step(steps)
     p = o.particles(0)
-    moves = -(-steps // K)
+    moves = steps // K
     expect = (cell + off) * phys.dx + moves * K * v * phys.dt
     assert np.max(np.abs(positions(p, phys.dx) - expect)) < 1e-12 * steps
     # velocities are returned in physical units whatever K is
@@ -65,20 +66,20 @@ def test_subcycled_uniform_field_ballistic(K):
     x_expect = (cell + off) * phys.dx + m * h * v + a * h * h * m * (m + 1) / 2
     np.testing.assert_allclose(positions(p, phys.dx), x_expect, rtol=0, atol=1e-10)
     np.testing.assert_allclose(p["vx"], v + m * a * h, rtol=0, atol=1e-12)
-    # step m K moves again; the K - 1 steps after it change nothing
-    o.step(1)
-    q1 = o.particles(0)
-    assert np.any(q1["off"] != p["off"])
+    # the next K - 1 steps change nothing; the K-th moves again
     o.step(K - 1)
-    q2 = o.particles(0)
+    q1 = o.particles(0)
     for k in ("cell", "off", "vx"):
-        np.testing.assert_array_equal(q2[k], q1[k])
+        np.testing.assert_array_equal(q1[k], p[k])
+    o.step(1)
+    q2 = o.particles(0)
+    assert np.any(q2["off"] != p["off"])
 
 
 def test_subcycled_collision_rate_uses_the_species_step():
     """Elastic collisions at frequency nu: a species with K = 4 collides on its own
     steps with P = 1 - exp(-4 nu dt) per move, so over n steps the expected count is
-    ceil(n/4) N P (an elastic event changes the direction only, never the count)."""
+    floor(n/4) N P (an elastic event changes the direction only, never the count)."""
     K, nu, dt = 4, 0.02, 0.05
     ppc, ncells = 400, 64
     sp = [W.Species("e", -1.0, 1.0, 0.5 / ppc, 1.0, ppc, nstep=K)]
@@ -93,7 +94,7 @@ def test_subcycled_collision_rate_uses_the_species_step():
     got = o.moments()["collisions"][0]
     npart = ppc * ncells
     P = -math.expm1(-nu * K * dt)
-    expect = math.ceil(steps / K) * npart * P
+    expect = (steps // K) * npart * P
     sd = math.sqrt(expect * (1 - P))
     assert abs(got - expect) < 4 * sd, (got, expect, sd)
     # the same physics without subcycling collides about K times as often per move
