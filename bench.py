@@ -280,6 +280,38 @@ def run_ours(args):
         return _run_ours(args, stream.cuda_stream, rank, world, local)
 
 
+def measure_paper_case(args, stream, rank, world, local):
+    """The paper's own test case (Section 3, Table 1) in normalized units: a periodic
+    plasma of electrons, D+ ions and D neutrals, 100,000 cells x 100 particles per cell
+    per species (30M particles), no field solve, electron-neutral elastic, excitation and
+    ionization against the neutral particles, which ionization depletes; the neutrals
+    move once per 20-step sort cycle.  FP32 and FP64 forms."""
+    from paper_2404_10270_gb300 import capi
+    phys = W.ionization_case(ncells=args.paper_cells, ppc=100, seed=1 + rank)
+    loads = W.initial_load(phys, seed=1 + rank)
+    n = sum(len(x) for x in loads)
+    # algorithmic bytes per particle-step: e and D+ read/write cell word, offset, vx (24 B
+    # in FP32, 40 in FP64); D is read (cell word + offset) every step and rewritten on
+    # one step in 20
+    out = {"workload": "ionization_case: %d cells x 100 ppc x (e, D+, D), periodic, no field, "
+                       "elastic + excitation + ionization against the D particles" % args.paper_cells,
+           "particles_per_gpu": n}
+    for name, prec, full, ro in (("fp32", capi.FP32, 24.0, 8.0), ("fp64", capi.FP64, 40.0, 12.0)):
+        bpp = (2 * full + (19 * ro + full) / 20) / 3
+        sim = capi.Sim(phys, precision=prec, sort_interval=phys.sort_interval, block=256,
+                       stream=stream)
+        sim.load_all(loads)
+        r = measure_form(sim, phys, max(args.steps, 20), min(args.warmup, 20), n,
+                         "f32" if prec == capi.FP32 else "f64", rank, world, local,
+                         bytes_per_particle=bpp)
+        m = sim.moments(0)
+        sim.close()
+        out[name] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
+                     "roofline": r["roofline"], "neutrals_left": int(m["live"][2])}
+    out["unit"] = UNIT
+    return out
+
+
 def measure_batched(args, stream, rank, world, local):
     """The batched ensemble: 512 independent magnetized plasmas of uneven size (cells
     log-uniform in [256, 8192], ppc in [50, 400]; volume source, elastic + ionization +
@@ -494,6 +526,10 @@ def _run_ours(args, stream, rank, world, local):
                      "workload": "bounded_large with the ions subcycled: nstep = 4",
                      "unit": UNIT}
 
+    paper = None
+    if not args.no_paper:
+        paper = measure_paper_case(args, stream, rank, world, local)
+
     batched = None
     if not args.no_batched:
         batched = measure_batched(args, stream, rank, world, local)
@@ -530,6 +566,7 @@ def _run_ours(args, stream, rank, world, local):
             "kernel_ms": res["kernel_ms"],
             "fp64_form": fp64,
             "subcycled": subcycled,
+            "paper_case": paper,
             "batched": batched,
             "small": small,
             "setup_s": setup_s,
@@ -591,6 +628,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-subcycle", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--paper-cells", type=int, default=100000)
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--c5", action="store_true", help="run the ~150 GB ensemble sweep instead")
     ap.add_argument("--c5-gb", type=float, default=150.0)

@@ -78,6 +78,8 @@ struct SegParams {
     double thr_u2[kMaxProc];       // energy threshold as |u|^2 (cells/step)^2
     int32_t collide;       // any process
     int32_t nstep;         // subcycling: moved on the steps n with (n+1) mod nstep = 0
+    int32_t is_target;     // the instance's neutral particle target
+    int32_t pad3;
 };
 
 constexpr int kChunk = 256;  // nodes per block of the field solve
@@ -95,7 +97,14 @@ struct InstParams {
     double lambda;         // E = lambda * G (integer field numerator G)
     int32_t z[kMaxSpecies]; // charge q_s w_s in integer multiples of the unit delta
     int32_t smooth;        // density smoother on: the field uses 4x the filtered charges
+    // neutral particle target (-1: uniform background): its segment, the reference
+    // count per cell, the product ion segment of ionizations and the factor K_ion /
+    // K_target that turns a target velocity into the ion's cells per step
+    int32_t tseg;
+    int32_t nref;
+    int32_t iseg;
     int32_t pad;
+    double tratio;
 };
 
 // A particle the mover leaves to the event kernel (a null-collision candidate or a

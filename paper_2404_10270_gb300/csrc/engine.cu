@@ -68,6 +68,9 @@ struct pic_handle {
     int64_t rare_cap = 0;  // entries of the per-step rare-event queue
     int max_nodes = 0;
     bool any_poisson = false, any_mag = false, any_ionize = false, any_subcycle = false;
+    bool any_target = false;       // some instance collides with neutral particles
+    unsigned *tcount = nullptr, *treq = nullptr;  // target segment node arrays
+    int grid_victims = 0;
 
     SegParams* segd = nullptr;
     InstParams* instd = nullptr;
@@ -251,9 +254,16 @@ int validate_instance(const pic_instance& I, int idx, std::string* why)
     }
     if (I.nproc < 0 || I.nproc > PIC_MAX_PROC) return bad("nproc must be 0..8");
     if (I.smooth != 0 && I.smooth != 1) return bad("smooth must be 0 or 1");
+    if (I.target < 0 || I.target > I.nspecies) return bad("target must be 0..nspecies");
+    if (I.target > 0) {
+        if (I.sp[I.target - 1].charge != 0.0) return bad("the neutral target species must have charge 0");
+        if (I.nref < 1) return bad("nref must be >= 1 with a neutral target");
+    }
     for (int k = 0; k < I.nproc; ++k) {
         const pic_process& P = I.proc[k];
-        if (P.kind < 0 || P.kind > 2) return bad("process kind");
+        if (P.kind < 0 || P.kind > 3) return bad("process kind");
+        if (I.target > 0 && P.species == I.target - 1)
+            return bad("the neutral target species cannot be a projectile");
         if (P.species < 0 || P.species >= I.nspecies) return bad("process species");
         if (!(P.nu >= 0) || !(P.threshold >= 0)) return bad("process nu/threshold must be >= 0");
         if (P.kind == PIC_PROC_ELASTIC && !(I.sp[P.species].mass <= 0.25 * I.m_neutral))
@@ -381,6 +391,9 @@ MoveArgs move_args(pic_handle* h)
     a.rare = h->rare;
     a.rare_count = h->rare_count;
     a.rare_cap = h->rare_cap;
+    a.tcount = h->tcount;
+    a.treq = h->treq;
+    a.hist = h->hist;
     return a;
 }
 
@@ -425,6 +438,10 @@ int launch_move(pic_handle* h, bool move)
         Span se(h, 3);
         h->kernels += 1;
         CUDA_TRY(h, launch_events(a, h->precision, h->grid_events, h->stream));
+        if (h->any_target) {
+            h->kernels += 1;
+            CUDA_TRY(h, launch_victims(a, h->precision, h->seg_nodes, h->grid_victims, h->stream));
+        }
     }
     return PIC_OK;
 }
@@ -438,10 +455,15 @@ int launch_tiles_h(pic_handle* h)
     return PIC_OK;
 }
 
+int do_sort(pic_handle* h);
+
 int ensure_fields(pic_handle* h)
 {
     if (!h->stale) return PIC_OK;
-    int rc = launch_tiles_h(h);
+    int rc;
+    // a neutral particle target needs the cell ranges of a sorted store
+    if (h->any_target && (rc = do_sort(h))) return rc;
+    rc = launch_tiles_h(h);
     if (rc) return rc;
     if ((rc = launch_move(h, false))) return rc;
     {
@@ -469,6 +491,7 @@ int do_sort(pic_handle* h)
     a.seg_live = h->seg_live;
     a.hwm_alt = h->hwm_alt;
     a.hist = h->hist;
+    a.tcount = h->tcount;
     a.newn = h->newn;
     for (int b = 0; b < 2; ++b) {
         a.cell[b] = h->st[b].cell;
@@ -712,6 +735,20 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         ip.lambda = delta / (2.0 * (double)I.ncells * S * I.eps0);
         // the smoother's integer charges are 4x the filtered ones (exact power of two)
         ip.smooth = (I.field == PIC_FIELD_POISSON && I.smooth) ? 1 : 0;
+        ip.tseg = -1;
+        ip.iseg = -1;
+        if (I.target > 0) {
+            ip.tseg = ip.seg0 + I.target - 1;
+            ip.nref = I.nref;
+            h->any_target = true;
+            for (int k = 0; k < I.nproc; ++k)
+                if (I.proc[k].kind == PIC_PROC_IONIZE) {
+                    ip.iseg = ip.seg0 + I.proc[k].product;
+                    ip.tratio = (double)species_nstep(I, I.proc[k].product) /
+                                (double)species_nstep(I, I.target - 1);
+                    break;
+                }
+        }
         if (ip.smooth) {
             ip.lambda *= 0.25;
             h->any_smooth = true;
@@ -751,6 +788,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
             P.node = snode;
             P.inode = inode;
             seg_constants(I, s, &P);
+            P.is_target = (I.target == s + 1) ? 1 : 0;
             for (int q = 0; q < P.nproc; ++q)
                 if (P.kind[q] == PIC_PROC_IONIZE) P.product[q] = ip.seg0 + P.product[q];
             slot += P.cap;
@@ -777,6 +815,22 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         h->last_error = "too many (instance, species) segments: at most " + std::to_string(kMaxSegments - 1);
         return bail(PIC_EINVAL);
     }
+    if (h->any_target) {
+        // the targets' cell ranges come from the sort, and hold between sorts only if the
+        // target species moves on the sort steps alone
+        if (h->tune_sort || h->sort_interval <= 0) {
+            h->last_error = "a neutral particle target needs a fixed sort interval equal to the target's nstep";
+            return bail(PIC_EINVAL);
+        }
+        for (int i = 0; i < h->ninst; ++i) {
+            const pic_instance& I = h->inst[i];
+            if (I.target > 0 && species_nstep(I, I.target - 1) != h->sort_interval) {
+                h->last_error = "instance " + std::to_string(i) +
+                                ": the neutral target's nstep must equal the sort interval";
+                return bail(PIC_EINVAL);
+            }
+        }
+    }
     h->rare_cap = std::min<int64_t>(h->rare_cap + 65536, std::max<int64_t>(slot, 65536));
     h->total_cap = slot;
     h->seg_nodes = snode;
@@ -800,6 +854,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     }
     h->sms = prop.multiProcessorCount;
     h->grid_events = (int)std::min<int64_t>((h->rare_cap + 127) / 128, (int64_t)16 * h->sms);
+    h->grid_victims = (int)std::min<int64_t>((h->seg_nodes + 127) / 128, (int64_t)16 * h->sms);
     std::snprintf(h->gpu_name, sizeof(h->gpu_name), "%s", prop.name);
     set_block(h, h->nt);
     if (h->tune_block || h->tune_sort) tune_begin(h);
@@ -831,6 +886,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->part_w, (size_t)h->nchunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->part_off, (size_t)h->nchunks);
     if (rc == PIC_OK && h->any_smooth) rc = dalloc(h, &h->zs, (size_t)inode);
+    if (rc == PIC_OK && h->any_target) rc = dalloc(h, &h->tcount, (size_t)snode);
+    if (rc == PIC_OK && h->any_target) rc = dalloc(h, &h->treq, (size_t)snode);
     if (rc == PIC_OK) rc = dalloc(h, &h->phi_d, (size_t)h->max_nodes);
     if (rc == PIC_OK) rc = dalloc(h, &h->segd, (size_t)h->nseg);
     if (rc == PIC_OK) rc = dalloc(h, &h->instd, (size_t)h->ninst);
@@ -868,6 +925,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (e == cudaSuccess) e = z(h->rare_count, 8);
     if (e == cudaSuccess) e = z(h->dep, (size_t)snode * 8);
     if (e == cudaSuccess) e = z(h->dep_last, (size_t)snode * 8);
+    if (e == cudaSuccess && h->any_target) e = z(h->tcount, (size_t)snode * 4);
+    if (e == cudaSuccess && h->any_target) e = z(h->treq, (size_t)snode * 4);
     if (e == cudaSuccess) e = z(h->E, (size_t)inode * 8);
     if (e == cudaSuccess) e = z(h->UN, (size_t)h->ninst * 16);
     if (e == cudaSuccess) e = z(h->part_sum, (size_t)h->nchunks * 16);

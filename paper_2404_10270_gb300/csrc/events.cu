@@ -13,4 +13,14 @@ cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream
     return cudaGetLastError();
 }
 
+cudaError_t launch_victims(const MoveArgs& a, int precision, int64_t nnodes, int grid,
+                           cudaStream_t st)
+{
+    if (precision == PIC_FP64)
+        k_victims<double><<<grid, 128, 0, st>>>(a, nnodes);
+    else
+        k_victims<float><<<grid, 128, 0, st>>>(a, nnodes);
+    return cudaGetLastError();
+}
+
 }  // namespace bitpic

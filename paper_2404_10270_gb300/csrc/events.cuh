@@ -39,15 +39,24 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z
 }
 
 // A null-collision candidate of one particle (velocity u in cells/step, after the
-// move): process slot from the selection word `wsel`, energy threshold (below it the
-// event is a null collision), kinematics.  Returns the instance-level index of the
-// process that took place (u changed), or -1 for a null event.  Ionization appends two
-// particles.  The caller counts the collision.
+// move): with a neutral particle target, first the target density (kept with
+// probability min(1, n_j / nref) by the word `wdens`), then the process slot from the
+// selection word `wsel`, energy threshold (below it the event is a null collision),
+// kinematics.  Returns the instance-level index of the process that took place (u
+// changed), or -1 for a null event.  Ionization appends two particles (the electron
+// only with a particle target: the target particle itself becomes the ion, see
+// k_victims).  The caller counts the collision.
 template <typename T>
 __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, int s,
                                     uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
-                                    T& uz, uint32_t wsel)
+                                    T& uz, uint32_t wsel, uint32_t wdens)
 {
+    const InstParams& I = a.inst[P.inst];
+    if (I.tseg >= 0) {
+        const uint64_t nj = a.tcount[a.seg[I.tseg].node + j];
+        const uint64_t nr = (uint64_t)I.nref;
+        if (nj < nr && (uint64_t)wdens >= (nj << 32) / nr) return -1;
+    }
     int q = -1;
     for (int k = 0; k < P.nproc; ++k)
         if ((uint64_t)wsel < P.slot_end[k]) { q = k; break; }
@@ -77,6 +86,16 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
         ux = z0 * vn;
         uy = z1 * vn;
         uz = z2 * vn;
+    } else if (kind == PIC_PROC_EXCITE) {
+        // the electron loses the threshold energy and leaves in a direction uniform
+        // on the sphere
+        const uint4 r = draw(id, step, kRngScatter, P.key0, P.key1);
+        T n[3];
+        iso_dir<T>(r.x, r.y, n);
+        const T sp2 = Prec<T>::sqrt_(u2 - (T)P.thr_u2[q]);
+        ux = sp2 * n[0];
+        uy = sp2 * n[1];
+        uz = sp2 * n[2];
     } else {  // PIC_PROC_IONIZE
         const T us = Prec<T>::sqrt_(T(0.5) * (u2 - (T)P.thr_u2[q]));
         T n1[3], n2[3];
@@ -84,26 +103,32 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
         iso_dir<T>(r1.x, r1.y, n1);
         const uint4 r2 = draw(id, step, kRngIonizeE, P.key0, P.key1);
         iso_dir<T>(r2.x, r2.y, n2);
-        const uint4 ri = draw(id, step, kRngIonizeI, P.key0, P.key1);
-        T z0, z1, z2, z3;
-        box_muller<T>(ri.x, ri.y, &z0, &z1);
-        box_muller<T>(ri.z, ri.w, &z2, &z3);
         ux = us * n1[0];
         uy = us * n1[1];
         uz = us * n1[2];
-        // append the new electron (this segment) and the new ion (product segment)
+        const InstParams& Ii = a.inst[P.inst];
+        const unsigned long long ev = atomicAdd(a.ev_count + P.inst, 1ull);
+        const unsigned long long ke = atomicAdd(a.seg_n + s, 1ull);
+        const bool target = Ii.tseg >= 0;
+        // the new ion: a new particle of the product segment, or (particle target) the
+        // target particle that k_victims converts
         const int si = P.product[q];
         const SegParams& Pi = a.seg[si];
-        const unsigned long long ke = atomicAdd(a.seg_n + s, 1ull);
-        const unsigned long long ki = atomicAdd(a.seg_n + si, 1ull);
-        const InstParams& I = a.inst[P.inst];
-        const unsigned long long ev = atomicAdd(a.ev_count + P.inst, 1ull);
+        const unsigned long long ki = target ? 0ull : atomicAdd(a.seg_n + si, 1ull);
         if (ke >= (unsigned long long)P.cap || ki >= (unsigned long long)Pi.cap ||
-            ev >= (unsigned long long)I.ev_cap) {
+            ev >= (unsigned long long)Ii.ev_cap) {
             set_error(a.err, kErrCapacity);
+            if (ev < (unsigned long long)Ii.ev_cap) {
+                // the record k_births reads must exist: an empty one
+                Event e;
+                e.parent = id;
+                e.pad = 0;
+                e.slot_e = -1;
+                e.slot_i = -1;
+                a.events[Ii.ev_base + (int64_t)ev] = e;
+            }
         } else {
-            const T vn = (T)Pi.vneutral;  // the ion's velocity in its own species' units
-            const int64_t ge = P.base + (int64_t)ke, gi = Pi.base + (int64_t)ki;
+            const int64_t ge = P.base + (int64_t)ke;
             T* off = static_cast<T*>(a.off);
             T* vx = static_cast<T*>(a.ux);
             T* vy = static_cast<T*>(a.uy);
@@ -111,23 +136,34 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
             a.cell[ge] = j; off[ge] = f;
             vx[ge] = us * n2[0]; vy[ge] = us * n2[1]; vz[ge] = us * n2[2];
             a.id[ge] = 0xFFFFFFFFu;
-            a.cell[gi] = j; off[gi] = f;
-            vx[gi] = z0 * vn; vy[gi] = z1 * vn; vz[gi] = z2 * vn;
-            a.id[gi] = 0xFFFFFFFFu;
-            Event e;
-            e.parent = id;
-            e.pad = 0;
-            e.slot_e = ge;
-            e.slot_i = gi;
-            a.events[I.ev_base + (int64_t)ev] = e;
             atomicAdd(a.seg_live + s, 1ull);
-            atomicAdd(a.seg_live + si, 1ull);
             // the children's charge joins this step's deposit
             const uint64_t qr = Prec<T>::qright(f), ql = Prec<T>::S - qr;
             atomicAdd(a.dep + P.node + j, (unsigned long long)ql);
             atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
-            atomicAdd(a.dep + Pi.node + j, (unsigned long long)ql);
-            atomicAdd(a.dep + Pi.node + j + 1, (unsigned long long)qr);
+            Event e;
+            e.parent = id;
+            e.pad = 0;
+            e.slot_e = ge;
+            e.slot_i = -1;
+            if (target) {
+                atomicAdd(a.treq + a.seg[Ii.tseg].node + j, 1u);
+            } else {
+                const uint4 ri = draw(id, step, kRngIonizeI, P.key0, P.key1);
+                T z0, z1, z2, z3;
+                box_muller<T>(ri.x, ri.y, &z0, &z1);
+                box_muller<T>(ri.z, ri.w, &z2, &z3);
+                const T vn = (T)Pi.vneutral;  // the ion's velocity in its own species' units
+                const int64_t gi = Pi.base + (int64_t)ki;
+                a.cell[gi] = j; off[gi] = f;
+                vx[gi] = z0 * vn; vy[gi] = z1 * vn; vz[gi] = z2 * vn;
+                a.id[gi] = 0xFFFFFFFFu;
+                e.slot_i = gi;
+                atomicAdd(a.seg_live + si, 1ull);
+                atomicAdd(a.dep + Pi.node + j, (unsigned long long)ql);
+                atomicAdd(a.dep + Pi.node + j + 1, (unsigned long long)qr);
+            }
+            a.events[Ii.ev_base + (int64_t)ev] = e;
         }
     }
     return P.proc[q];
@@ -207,7 +243,7 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
             if (kind == kRareCandidate) {
                 const int j = (int)((uint32_t)a.cell[slot] & kCellMask);
                 const uint4 wd = draw(id, step, kRngCollide, P.key0, P.key1);
-                const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y);
+                const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y, wd.z);
                 if (p >= 0) {
                     uxp[slot] = vx;
                     uyp[slot] = vy;
@@ -232,6 +268,85 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
         }
         count_by_key(a.collisions, ckey);
         count_by_key(a.wall_count, wkey);
+    }
+}
+
+// Ionization against a neutral particle target: the r_j ionizations of cell j this step
+// turn the r_j live target particles of cell j with the smallest ids (as of the start
+// of the step: the cell's range of the target segment after the last sort, which the
+// target has not left since, since it moves only on the sort steps) into product ions:
+// same id, position and physical velocity (x K_ion / K_target in cells per step),
+// collision clock 0.  The ion's charge joins this step's deposit and the target's
+// (charge 0, but counted in its density) leaves it.  A cell with fewer targets than
+// ionizations converts what it has.  One thread per node of the target segments.
+template <typename T>
+__global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArgs a,
+                                                 int64_t nnodes)
+{
+    T* const offp = static_cast<T*>(a.off);
+    T* const uxp = static_cast<T*>(a.ux);
+    T* const uyp = static_cast<T*>(a.uy);
+    T* const uzp = static_cast<T*>(a.uz);
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nnodes;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned r = a.treq[n];
+        if (r == 0u) continue;
+        a.treq[n] = 0u;
+        // the segment of node n (segments' node arrays are in increasing order)
+        int lo = 0, hi = a.nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.seg[mid].node <= n) lo = mid; else hi = mid - 1;
+        }
+        const int ts = lo;
+        const SegParams& P = a.seg[ts];
+        const int j = (int)(n - P.node);
+        const InstParams& I = a.inst[P.inst];
+        const SegParams& Pi = a.seg[I.iseg];
+        const int64_t begin = P.base + (j > 0 ? (int64_t)a.hist[n - 1] : 0);
+        const int64_t end = P.base + (int64_t)a.hist[n];
+        uint32_t last = 0;
+        bool first = true;
+        for (unsigned k = 0; k < r; ++k) {
+            // the next smallest live id of the range
+            int64_t v = -1;
+            uint32_t best = 0xFFFFFFFFu;
+            for (int64_t g = begin; g < end; ++g) {
+                if (a.cell[g] < 0) continue;
+                const uint32_t idg = a.id[g];
+                if ((first || idg > last) && (v < 0 || idg < best)) {
+                    best = idg;
+                    v = g;
+                }
+            }
+            if (v < 0) break;
+            first = false;
+            last = best;
+            const unsigned long long ki = atomicAdd(a.seg_n + I.iseg, 1ull);
+            if (ki >= (unsigned long long)Pi.cap) {
+                set_error(a.err, kErrCapacity);
+                break;
+            }
+            const int64_t gi = Pi.base + (int64_t)ki;
+            const int jv = (int)((uint32_t)a.cell[v] & kCellMask);
+            const T fv = offp[v];
+            const T ratio = (T)I.tratio;
+            a.cell[gi] = jv;
+            offp[gi] = fv;
+            uxp[gi] = uxp[v] * ratio;
+            uyp[gi] = uyp[v] * ratio;
+            uzp[gi] = uzp[v] * ratio;
+            a.id[gi] = best;
+            a.cell[v] = -1;
+            const uint64_t qr = Prec<T>::qright(fv), ql = Prec<T>::S - qr;
+            atomicAdd(a.dep + Pi.node + jv, (unsigned long long)ql);
+            atomicAdd(a.dep + Pi.node + jv + 1, (unsigned long long)qr);
+            atomicAdd(a.dep + P.node + jv, (unsigned long long)(0ull - ql));
+            atomicAdd(a.dep + P.node + jv + 1, (unsigned long long)(0ull - qr));
+            atomicAdd(a.seg_live + ts, ~0ull);
+            atomicAdd(a.seg_live + I.iseg, 1ull);
+            a.tcount[n] -= 1u;
+        }
     }
 }
 

@@ -311,10 +311,13 @@ __global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned l
     int64_t local = 0;
     for (int s = s0; s < s1; ++s) {
         // an overflowing creation (already latched as an error) may have pushed the
-        // count past the capacity: never walk beyond the segment
+        // count past the capacity: never walk beyond the segment.  Only the count to
+        // move is rounded up to a whole quad (the slots past the count are empty, and
+        // creations append after the mover), so appends waste no slots.
         const unsigned long long cap = (unsigned long long)seg[s].cap;
-        const unsigned long long n4 = min((seg_n[s] + 3ull) & ~3ull, cap);
-        seg_n[s] = n4;
+        const unsigned long long nn = min(seg_n[s], cap);
+        const unsigned long long n4 = min((nn + 3ull) & ~3ull, cap);
+        seg_n[s] = nn;
         seg_nmove[s] = (int64_t)n4;
         const int64_t quads = (int64_t)(n4 >> 2);
         local += (quads + tile_quads - 1) / tile_quads;
@@ -344,7 +347,10 @@ __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* e
     const int64_t n = (int64_t)min(cnt, (unsigned long long)I.ev_cap);
     const Event* ev = events + I.ev_base;
     const unsigned long long base = next_id[b];
-    if (base + 2ull * (unsigned long long)n > 0xFFFFFFFFull) {
+    // with a neutral particle target only the electron is new (the ion is a converted
+    // target particle and keeps its id): one id per event
+    const unsigned long long per = I.tseg >= 0 ? 1ull : 2ull;
+    if (base + per * (unsigned long long)n > 0xFFFFFFFFull) {
         if (threadIdx.x == 0) set_error(err, kErrCapacity);
         return;
     }
@@ -361,13 +367,15 @@ __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* e
                 for (int64_t k = 0; k < m; ++k) rank += sp[k] < p;
         }
         if (i < n) {
-            id[ev[i].slot_e] = (uint32_t)(base + 2ull * (unsigned long long)rank);
-            id[ev[i].slot_i] = (uint32_t)(base + 2ull * (unsigned long long)rank + 1ull);
+            // an event whose creation overflowed (already latched) has no slots
+            if (ev[i].slot_e >= 0) id[ev[i].slot_e] = (uint32_t)(base + per * (unsigned long long)rank);
+            if (per == 2ull && ev[i].slot_i >= 0)
+                id[ev[i].slot_i] = (uint32_t)(base + 2ull * (unsigned long long)rank + 1ull);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        next_id[b] = base + 2ull * (unsigned long long)n;
+        next_id[b] = base + per * (unsigned long long)n;
         ev_count[b] = 0ull;
     }
 }

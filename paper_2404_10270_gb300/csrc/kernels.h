@@ -20,6 +20,10 @@ cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, in
 // The rare events the mover queued this step (events.cu): collision candidates and
 // wall hits, one thread each, `grid` blocks of 128 threads.
 cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream_t st);
+// Ionizations against neutral particle targets: convert the requested targets into
+// ions (events.cu); one thread per segment node, `nnodes` nodes in all.
+cudaError_t launch_victims(const MoveArgs& a, int precision, int64_t nnodes, int grid,
+                           cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
 int move_blocks_per_sm_f32(bool mag, int nt);
 int move_blocks_per_sm_f64(bool mag, int nt);
@@ -54,7 +58,7 @@ cudaError_t launch_field(const FieldArgs& f, bool advance_step, cudaStream_t st)
 cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* phi,
                              cudaStream_t st);
 
-// Round each segment's slot count up to a whole quad, snapshot it as the count to
+// Snapshot each segment's slot count, rounded up to a whole quad, as the count to
 // move, and build the tile prefix (tiles of `tile_quads` quads).
 // Also empties the rare-event queue of the coming step.
 cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
@@ -77,6 +81,7 @@ struct SortArgs {
     unsigned long long* seg_live;
     unsigned long long* hwm_alt;      // slots in use of the other copy
     unsigned* hist;                   // per segment node arrays (cells), zeroed
+    unsigned* tcount;                 // neutral targets: live targets per cell after the sort
     unsigned long long* newn;         // per segment live count after the sort
     // source and destination stores
     int32_t* cell[2];

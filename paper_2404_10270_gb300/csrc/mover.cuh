@@ -77,6 +77,12 @@ struct MoveArgs {
     uint64_t* rare;                     // queue of rare events of this step (rare_pack)
     unsigned long long* rare_count;     // entries queued this step
     int64_t rare_cap;                   // queue entries
+    // neutral particle targets (segment node arrays of the target segments): live
+    // targets per cell as of the start of the step, ionization requests of the step,
+    // and the sort histogram, which holds each cell's end position after a sort
+    unsigned* tcount;
+    unsigned* treq;
+    const unsigned* hist;
 };
 
 template <typename T> struct Prec;

@@ -202,6 +202,11 @@ __global__ void k_sort_finish(const SortArgs a)
     const unsigned long long hw = min(max(old, a.hwm_alt[s]), (unsigned long long)P.cap);
     int32_t* dcell = a.cell[1 - a.src];
     for (unsigned long long i = nnew + threadIdx.x; i < hw; i += blockDim.x) dcell[P.base + (int64_t)i] = -1;
+    // a neutral particle target: its live particles per cell, from the cell ends the
+    // scatter left in the histogram
+    if (P.is_target)
+        for (int j = threadIdx.x; j < P.ncells; j += blockDim.x)
+            a.tcount[P.node + j] = a.hist[P.node + j] - (j > 0 ? a.hist[P.node + j - 1] : 0u);
     __syncthreads();
     if (threadIdx.x == 0) {
         a.hwm_alt[s] = old;

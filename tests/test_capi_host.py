@@ -119,6 +119,23 @@ def test_create_rejects_invalid_instances(L, mutate, needle):
     assert needle in L.pic_last_error(None).decode()
 
 
+def test_create_rejects_invalid_neutral_targets(L):
+    base = W.ionization_case(ncells=16, ppc=4)
+    for mutate, needle in ((lambda I: setattr(I.sp[2], "charge", 1.0), "charge 0"),
+                           (lambda I: setattr(I, "nref", 0), "nref"),
+                           (lambda I: setattr(I, "target", 9), "target")):
+        I = capi.instance_struct(base)
+        mutate(I)
+        rc, h = _create(L, [I], sort_interval=base.sort_interval)
+        assert rc == -1 and not h.value
+        assert needle in L.pic_last_error(None).decode()
+    # the target's nstep must equal the (fixed) sort interval
+    I = capi.instance_struct(base)
+    for si in (base.sort_interval + 1, -1):
+        rc, h = _create(L, [I], sort_interval=si)
+        assert rc == -1 and "sort interval" in L.pic_last_error(None).decode()
+
+
 def test_create_rejects_invalid_config(L):
     I = capi.instance_struct(W.bounded_small(ncells=16, ppc=4))
     for kw in (dict(precision=7), dict(block=100), dict(sort_interval=-2)):
