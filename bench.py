@@ -423,7 +423,8 @@ def run_c5(args):
                 sim.load_all(ld, inst=i)
             r = measure_form(sim, phys, args.steps, args.warmup, n,
                              "f64" if prec == capi.FP64 else "f32", 0, 1, 0, bytes_per_particle=bpp)
-            total = args.steps + args.warmup
+            # measure_form runs the warm-up, the timed steps, then as many profiled steps
+            total = args.warmup + 2 * args.steps
             errs = []
             for i in sample:
                 g = sim.moments(i)

@@ -765,12 +765,14 @@ static int one_step(orc_sim* s)
             } else {
                 const double half = 0.5 * acc;
                 const double mx = a->ux[k] + half, my = a->uy[k], mz = a->uz[k];
-                const double px = mx + (my * t[2] - mz * t[1]);
-                const double py = my + (mz * t[0] - mx * t[2]);
-                const double pz = mz + (mx * t[1] - my * t[0]);
-                const double qx = mx + (py * sv[2] - pz * sv[1]);
-                const double qy = my + (pz * sv[0] - px * sv[2]);
-                const double qz = mz + (px * sv[1] - py * sv[0]);
+                /* v' = v + v x t, then v+ = v + v' x s, each component as two fused
+                 * multiply-adds: m_x + m_y t_z - m_z t_y = fma(m_y, t_z, fma(-m_z, t_y, m_x)) */
+                const double px = fma(my, t[2], fma(-mz, t[1], mx));
+                const double py = fma(mz, t[0], fma(-mx, t[2], my));
+                const double pz = fma(mx, t[1], fma(-my, t[0], mz));
+                const double qx = fma(py, sv[2], fma(-pz, sv[1], mx));
+                const double qy = fma(pz, sv[0], fma(-px, sv[2], my));
+                const double qz = fma(px, sv[1], fma(-py, sv[0], mz));
                 a->ux[k] = qx + half;
                 a->uy[k] = qy;
                 a->uz[k] = qz;

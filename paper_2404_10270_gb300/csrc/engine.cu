@@ -2,11 +2,16 @@
 // layout, the per-step launch sequence and the synchronising queries.
 //
 // Launch sequence of one time step (all on the handle's stream):
-//   k_tiles     round each segment's slot count to a whole quad, build the tile list
-//   k_move      gather, push, move, wall, MCC, fixed-point deposit (mover.cuh)
+//   k_tiles     snapshot each segment's slot count (rounded to a whole quad), build the
+//               tile list, empty the rare-event queue
+//   k_move      gather, push, move, periodic wrap, collision clock, fixed-point deposit;
+//               walls and collision candidates are queued (mover.cuh)
+//   k_events    the queued walls and candidates: counters, re-injection, kinematics,
+//               creations (events.cuh)
+//   k_victims   neutral particle targets: the ionized targets become ions (events.cuh)
 //   k_births    number this step's ionization products (only with ionization)
-//   k_field     exact integer Poisson solve -> E -> pre-scaled accelerations, and
-//               hand-over of the deposit (field.cu)
+//   k_field     exact integer Poisson solve (optional smoother) -> E -> node pairs of
+//               pre-scaled accelerations, and hand-over of the deposit (field.cu)
 //   every `sort_interval` steps: k_tiles, histogram, scan, scatter (sort.cu).
 #include <algorithm>
 #include <cmath>

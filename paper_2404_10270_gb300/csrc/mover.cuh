@@ -405,12 +405,14 @@ k_move(const __grid_constant__ MoveArgs a)
                     const T t0 = Prec<T>::bt(P, 0), t1 = Prec<T>::bt(P, 1), t2 = Prec<T>::bt(P, 2);
                     const T s0 = Prec<T>::bs(P, 0), s1 = Prec<T>::bs(P, 1), s2 = Prec<T>::bs(P, 2);
                     const T mx = ux[k] + half, my = uy[k], mz = uz[k];
-                    const T px = mx + (my * t2 - mz * t1);
-                    const T py = my + (mz * t0 - mx * t2);
-                    const T pz = mz + (mx * t1 - my * t0);
-                    const T qx = mx + (py * s2 - pz * s1);
-                    const T qy = my + (pz * s0 - px * s2);
-                    const T qz = mz + (px * s1 - py * s0);
+                    // v' = v + v x t, v+ = v + v' x s, each component as two fused
+                    // multiply-adds (m_x + m_y t_z - m_z t_y = fma(m_y, t_z, fma(-m_z, t_y, m_x)))
+                    const T px = Prec<T>::fma_(my, t2, Prec<T>::fma_(-mz, t1, mx));
+                    const T py = Prec<T>::fma_(mz, t0, Prec<T>::fma_(-mx, t2, my));
+                    const T pz = Prec<T>::fma_(mx, t1, Prec<T>::fma_(-my, t0, mz));
+                    const T qx = Prec<T>::fma_(py, s2, Prec<T>::fma_(-pz, s1, mx));
+                    const T qy = Prec<T>::fma_(pz, s0, Prec<T>::fma_(-px, s2, my));
+                    const T qz = Prec<T>::fma_(px, s1, Prec<T>::fma_(-py, s0, mz));
                     ux[k] = qx + half;
                     uy[k] = qy;
                     uz[k] = qz;
