@@ -44,6 +44,9 @@ MOVER_BYTES = {"f32": 24, "f64": 40}
 # Peak: 2 FP64 instructions per SM per cycle (ncu's peak_sustained of the dfma pipe on
 # this GPU) x 152 SMs x 2.07 GHz.
 FP64_OPS_PER_PARTICLE = 4
+# With B != 0 (Boris): gather 1, half step 1, v + a/2 1, the two cross-product updates
+# 6 x 2 fused multiply-adds, the last half step 1, the move 2.
+FP64_OPS_PER_PARTICLE_BORIS = 18
 FP64_PEAK_INSTR_PER_S = 2 * 152 * 2.07e9
 
 
@@ -442,6 +445,14 @@ def run_c5(args):
             sim.close()
             res[name] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
                          "roofline": r["roofline"], "errors_vs_oracle_after_%d_steps" % total: errs}
+            if prec == capi.FP64:
+                # the FP64 Boris form is bound by the FP64 pipe
+                live = sum(r["live"]) / 2
+                ach = FP64_OPS_PER_PARTICLE_BORIS * live / (r["roofline"]["avg_launch_ms"] * 1e-3)
+                res[name]["roofline_fp64_pipe"] = {
+                    "bound": "alu", "achieved": ach, "peak": FP64_PEAK_INSTR_PER_S,
+                    "unit": "FP64 instr/s", "frac": ach / FP64_PEAK_INSTR_PER_S,
+                    "ops_per_particle": FP64_OPS_PER_PARTICLE_BORIS}
         print(json.dumps({"c5": res}), flush=True)
     return 0
 
