@@ -457,6 +457,44 @@ def run_c5(args):
     return 0
 
 
+def _e2e_pass(sim, host, outs, phys, args, world):
+    """One end-to-end pass through the public API: load every species from pinned host
+    memory, args.steps steps, the moments, every particle read back to pinned host
+    memory.  Returns (seconds, max over ranks; breakdown; moments; bytes read back)."""
+    import ctypes as C
+    import torch
+    from paper_2404_10270_gb300 import capi
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    t_sp = []
+    for s, h in enumerate(host):
+        sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
+        t_sp.append(time.perf_counter())
+    t_load = time.perf_counter()
+    sim.step(args.steps)
+    sim.sync()
+    t_steps = time.perf_counter()
+    mom = sim.moments(0)
+    d2h = 0
+    for s in range(len(phys.species)):
+        o = outs[s]
+        got = C.c_int64()
+        cap = len(o["cell"])
+        capi._check(capi.lib().pic_get_particles(sim._h, 0, s, cap, *[o[k].ctypes.data for k in
+                    ("cell", "off", "vx", "vy", "vz", "id")], None, 0, C.byref(got)), sim._h)
+        d2h += got.value * 40
+    torch.cuda.synchronize()
+    t_end = time.perf_counter()
+    parts = {"load_s": t_load - t0, "load_species_s": [b - a for a, b in zip([t0] + t_sp[:-1], t_sp)],
+             "steps_s": t_steps - t_load, "read_back_s": t_end - t_steps}
+    e2e_t = torch.tensor([t_end - t0], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    return float(e2e_t.item()), parts, mom, d2h
+
+
 def _run_ours(args, stream, rank, world, local):
     import torch
     __import__("__graft_entry__").build()
@@ -483,40 +521,18 @@ def _run_ours(args, stream, rank, world, local):
     res = measure_form(sim, phys, args.steps, args.warmup, n, "f32", rank, world, local)
 
     # end to end through the public API with host buffers: load from pinned host
-    # memory, K steps, read every particle and the moments back to pinned memory
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    t_sp = []
-    for s, h in enumerate(host):
-        sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
-        t_sp.append(time.perf_counter())
-    t_load = time.perf_counter()
-    sim.step(args.steps)
-    sim.sync()
-    t_steps = time.perf_counter()
-    mom = sim.moments(0)
-    d2h = 0
-    import ctypes as C
-    for s in range(len(phys.species)):
-        o = outs[s]
-        got = C.c_int64()
-        cap = len(o["cell"])
-        capi._check(capi.lib().pic_get_particles(sim._h, 0, s, cap, *[o[k].ctypes.data for k in
-                    ("cell", "off", "vx", "vy", "vz", "id")], None, 0, C.byref(got)), sim._h)
-        d2h += got.value * 40
-    torch.cuda.synchronize()
-    t_end = time.perf_counter()
-    e2e_s = t_end - t0
-    e2e_parts = {"load_s": t_load - t0, "load_species_s": [b - a for a, b in zip([t0] + t_sp[:-1], t_sp)],
-                 "steps_s": t_steps - t_load, "read_back_s": t_end - t_steps}
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = n * world * args.steps / float(e2e_t.item())
+    # memory, K steps, read every particle and the moments back to pinned memory; three
+    # passes (the host's copy bandwidth varies with other traffic on the shared host),
+    # the median is reported and every pass listed
+    e2e_passes = []
+    for _ in range(3):
+        e2e_passes.append(_e2e_pass(sim, host, outs, phys, args, world))
+    e2e_passes.sort(key=lambda x: x[0])
+    e2e_s, e2e_parts, mom, d2h = e2e_passes[1]
+    e2e_value = n * world * args.steps / e2e_s
     h2d = n * 40
     assert mom["step"] > 0
+    e2e_parts["passes_s"] = [p[0] for p in e2e_passes]
 
     fp64 = None
     if not args.no_fp64:
@@ -588,7 +604,7 @@ def _run_ours(args, stream, rank, world, local):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps,
                     "what": "pic_load_particles from pinned host + %d steps + pic_moments + "
-                            "pic_get_particles to pinned host" % args.steps,
+                            "pic_get_particles to pinned host; median of 3 passes" % args.steps,
                     "breakdown": e2e_parts},
             "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"],
@@ -644,6 +660,20 @@ def profile_ensemble(scale: float) -> int:
     return 0
 
 
+def profile_paper(steps: int) -> int:
+    """The paper's test case alone (FP32), for launch lists: load + `steps` steps."""
+    __import__("__graft_entry__").build()
+    from paper_2404_10270_gb300 import capi
+    phys = W.ionization_case()
+    sim = capi.Sim(phys, precision=capi.FP32, sort_interval=phys.sort_interval, block=256)
+    sim.load_all(W.initial_load(phys))
+    sim.step(steps)
+    sim.sync()
+    print("profile paper case ok", [sim.count(0, s) for s in range(3)])
+    sim.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -671,6 +701,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small case the ncu captures use and exit")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--profile-paper", type=int, default=0, metavar="STEPS",
+                    help="run the paper's test case alone for STEPS steps and exit")
     ap.add_argument("--profile-ensemble", type=float, default=None, metavar="SCALE",
                     help="run the small batched case the ncu captures use and exit")
     args = ap.parse_args()
@@ -678,6 +710,8 @@ def main():
         return profile_case(args.precision)
     if args.profile_ensemble is not None:
         return profile_ensemble(args.profile_ensemble)
+    if args.profile_paper:
+        return profile_paper(args.profile_paper)
     if args.c5:
         return run_c5(args)
     if args.warmup < 3:

@@ -79,7 +79,7 @@ struct SegParams {
     int32_t collide;       // any process
     int32_t nstep;         // subcycling: moved on the steps n with (n+1) mod nstep = 0
     int32_t is_target;     // the instance's neutral particle target
-    int32_t pad3;
+    int32_t mag;           // the instance has a magnetic field (Boris push)
 };
 
 constexpr int kChunk = 256;  // nodes per block of the field solve

@@ -95,6 +95,9 @@ struct pic_handle {
     int64_t *seg_nmove = nullptr, *tile_start = nullptr;
     unsigned long long *wall_count = nullptr, *collisions = nullptr, *ev_count = nullptr,
                        *next_id = nullptr;
+    unsigned* births_done = nullptr;  // per instance: blocks of k_births that finished
+    unsigned long long* cell_part = nullptr;  // sort: per segment and 4096-cell chunk
+    int cell_chunks = 1;
     double* wall_energy = nullptr;
     Event* events = nullptr;
     uint64_t* rare = nullptr;
@@ -496,7 +499,10 @@ int do_sort(pic_handle* h)
     a.seg_live = h->seg_live;
     a.hwm_alt = h->hwm_alt;
     a.hist = h->hist;
-    a.tcount = h->tcount;
+    a.tcount = h->any_target ? h->tcount : nullptr;
+    a.cell_part = h->cell_part;
+    a.cell_chunks = h->cell_chunks;
+    a.seg_nodes = h->seg_nodes;
     a.newn = h->newn;
     for (int b = 0; b < 2; ++b) {
         a.cell[b] = h->st[b].cell;
@@ -509,7 +515,7 @@ int do_sort(pic_handle* h)
     a.src = h->cur;
     a.max_cap = h->max_cap;
     a.max_cells = h->max_nodes - 1;
-    h->kernels += 4;
+    h->kernels += h->any_target ? 6 : 5;
     CUDA_TRY(h, launch_sort(a, h->nt, h->sms, h->stream));
     h->cur = 1 - h->cur;
     return PIC_OK;
@@ -794,6 +800,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
             P.inode = inode;
             seg_constants(I, s, &P);
             P.is_target = (I.target == s + 1) ? 1 : 0;
+            P.mag = (I.B[0] != 0.0 || I.B[1] != 0.0 || I.B[2] != 0.0) ? 1 : 0;
             for (int q = 0; q < P.nproc; ++q)
                 if (P.kind[q] == PIC_PROC_IONIZE) P.product[q] = ip.seg0 + P.product[q];
             slot += P.cap;
@@ -910,6 +917,9 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->rare, (size_t)h->rare_cap);
     if (rc == PIC_OK) rc = dalloc(h, &h->rare_count, 1);
     if (rc == PIC_OK) rc = dalloc(h, &h->next_id, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->births_done, (size_t)h->ninst);
+    h->cell_chunks = (h->max_nodes + 4095) / 4096;
+    if (rc == PIC_OK) rc = dalloc(h, &h->cell_part, (size_t)h->nseg * h->cell_chunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->err, 1);
     if (rc == PIC_OK) rc = dalloc(h, &h->step_d, 1);
     if (rc == PIC_OK) rc = dalloc(h, &h->kin, (size_t)PIC_MAX_SPECIES);
@@ -950,6 +960,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (e == cudaSuccess) e = z(h->collisions, (size_t)h->ninst * kMaxProc * 8);
     if (e == cudaSuccess) e = z(h->ev_count, (size_t)h->ninst * 8);
     if (e == cudaSuccess) e = z(h->next_id, (size_t)h->ninst * 8);
+    if (e == cudaSuccess) e = z(h->births_done, (size_t)h->ninst * 4);
     if (e == cudaSuccess) e = z(h->err, 4);
     if (e == cudaSuccess) e = z(h->step_d, 8);
     if (e == cudaSuccess)
@@ -1097,7 +1108,7 @@ int enqueue_step(pic_handle* h)
         Span sp(h, 3);
         h->kernels += 1;
         CUDA_TRY(h, launch_births(h->instd, h->ninst, h->events, h->ev_count, h->next_id,
-                                  h->st[h->cur].id, h->err, h->stream));
+                                  h->st[h->cur].id, h->err, h->births_done, h->stream));
     }
     {
         Span sp(h, 1);

@@ -278,74 +278,93 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
 // same id, position and physical velocity (x K_ion / K_target in cells per step),
 // collision clock 0.  The ion's charge joins this step's deposit and the target's
 // (charge 0, but counted in its density) leaves it.  A cell with fewer targets than
-// ionizations converts what it has.  One thread per node of the target segments.
+// ionizations converts what it has.  Each warp looks at 32 nodes of the target segments
+// and, for every one with requests, scans the cell's range together (32 entries per
+// pass) for the next smallest live id.
 template <typename T>
 __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArgs a,
                                                  int64_t nnodes)
 {
+    const unsigned FULL = 0xffffffffu;
     T* const offp = static_cast<T*>(a.off);
     T* const uxp = static_cast<T*>(a.ux);
     T* const uyp = static_cast<T*>(a.uy);
     T* const uzp = static_cast<T*>(a.uz);
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nnodes;
-         n += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned r = a.treq[n];
-        if (r == 0u) continue;
-        a.treq[n] = 0u;
-        // the segment of node n (segments' node arrays are in increasing order)
-        int lo = 0, hi = a.nseg - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.seg[mid].node <= n) lo = mid; else hi = mid - 1;
-        }
-        const int ts = lo;
-        const SegParams& P = a.seg[ts];
-        const int j = (int)(n - P.node);
-        const InstParams& I = a.inst[P.inst];
-        const SegParams& Pi = a.seg[I.iseg];
-        const int64_t begin = P.base + (j > 0 ? (int64_t)a.hist[n - 1] : 0);
-        const int64_t end = P.base + (int64_t)a.hist[n];
-        uint32_t last = 0;
-        bool first = true;
-        for (unsigned k = 0; k < r; ++k) {
-            // the next smallest live id of the range
-            int64_t v = -1;
-            uint32_t best = 0xFFFFFFFFu;
-            for (int64_t g = begin; g < end; ++g) {
-                if (a.cell[g] < 0) continue;
-                const uint32_t idg = a.id[g];
-                if ((first || idg > last) && (v < 0 || idg < best)) {
-                    best = idg;
-                    v = g;
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; n0 < nnodes;
+         n0 += wstride) {
+        const int64_t mine = n0 + lane;
+        const unsigned myr = mine < nnodes ? a.treq[mine] : 0u;
+        unsigned todo = __ballot_sync(FULL, myr != 0u);
+        while (todo) {
+            const int L = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int64_t n = n0 + L;
+            const unsigned r = __shfl_sync(FULL, myr, L);
+            if (lane == L) a.treq[n] = 0u;
+            // the segment of node n (segments' node arrays are in increasing order)
+            int lo = 0, hi = a.nseg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.seg[mid].node <= n) lo = mid; else hi = mid - 1;
+            }
+            const int ts = lo;
+            const SegParams& P = a.seg[ts];
+            const int j = (int)(n - P.node);
+            const InstParams& I = a.inst[P.inst];
+            const SegParams& Pi = a.seg[I.iseg];
+            const int64_t begin = P.base + (j > 0 ? (int64_t)a.hist[n - 1] : 0);
+            const int64_t end = P.base + (int64_t)a.hist[n];
+            uint32_t last = 0;
+            bool first = true;
+            for (unsigned k = 0; k < r; ++k) {
+                // the next smallest live id of the range, 32 entries per pass
+                uint32_t best = 0xFFFFFFFFu;
+                int64_t v = -1;
+                for (int64_t g0 = begin; g0 < end; g0 += 32) {
+                    const int64_t g = g0 + lane;
+                    if (g < end && a.cell[g] >= 0) {
+                        const uint32_t idg = a.id[g];
+                        if ((first || idg > last) && idg < best) {
+                            best = idg;
+                            v = g;
+                        }
+                    }
                 }
+                const uint32_t wbest = __reduce_min_sync(FULL, best);
+                const unsigned owner = __ballot_sync(FULL, v >= 0 && best == wbest);
+                if (owner == 0u) break;  // no live target left in the cell
+                first = false;
+                last = wbest;
+                if (lane == __ffs(owner) - 1) {
+                    const unsigned long long ki = atomicAdd(a.seg_n + I.iseg, 1ull);
+                    if (ki >= (unsigned long long)Pi.cap) {
+                        set_error(a.err, kErrCapacity);
+                    } else {
+                        const int64_t gi = Pi.base + (int64_t)ki;
+                        const int jv = (int)((uint32_t)a.cell[v] & kCellMask);
+                        const T fv = offp[v];
+                        const T ratio = (T)I.tratio;
+                        a.cell[gi] = jv;
+                        offp[gi] = fv;
+                        uxp[gi] = uxp[v] * ratio;
+                        uyp[gi] = uyp[v] * ratio;
+                        uzp[gi] = uzp[v] * ratio;
+                        a.id[gi] = wbest;
+                        a.cell[v] = -1;
+                        const uint64_t qr = Prec<T>::qright(fv), ql = Prec<T>::S - qr;
+                        atomicAdd(a.dep + Pi.node + jv, (unsigned long long)ql);
+                        atomicAdd(a.dep + Pi.node + jv + 1, (unsigned long long)qr);
+                        atomicAdd(a.dep + P.node + jv, (unsigned long long)(0ull - ql));
+                        atomicAdd(a.dep + P.node + jv + 1, (unsigned long long)(0ull - qr));
+                        atomicAdd(a.seg_live + ts, ~0ull);
+                        atomicAdd(a.seg_live + I.iseg, 1ull);
+                        a.tcount[n] -= 1u;
+                    }
+                }
+                __syncwarp();
             }
-            if (v < 0) break;
-            first = false;
-            last = best;
-            const unsigned long long ki = atomicAdd(a.seg_n + I.iseg, 1ull);
-            if (ki >= (unsigned long long)Pi.cap) {
-                set_error(a.err, kErrCapacity);
-                break;
-            }
-            const int64_t gi = Pi.base + (int64_t)ki;
-            const int jv = (int)((uint32_t)a.cell[v] & kCellMask);
-            const T fv = offp[v];
-            const T ratio = (T)I.tratio;
-            a.cell[gi] = jv;
-            offp[gi] = fv;
-            uxp[gi] = uxp[v] * ratio;
-            uyp[gi] = uyp[v] * ratio;
-            uzp[gi] = uzp[v] * ratio;
-            a.id[gi] = best;
-            a.cell[v] = -1;
-            const uint64_t qr = Prec<T>::qright(fv), ql = Prec<T>::S - qr;
-            atomicAdd(a.dep + Pi.node + jv, (unsigned long long)ql);
-            atomicAdd(a.dep + Pi.node + jv + 1, (unsigned long long)qr);
-            atomicAdd(a.dep + P.node + jv, (unsigned long long)(0ull - ql));
-            atomicAdd(a.dep + P.node + jv + 1, (unsigned long long)(0ull - qr));
-            atomicAdd(a.seg_live + ts, ~0ull);
-            atomicAdd(a.seg_live + I.iseg, 1ull);
-            a.tcount[n] -= 1u;
         }
     }
 }

@@ -24,6 +24,7 @@ namespace bitpic {
 namespace {
 
 constexpr int kFieldThreads = 1024;
+constexpr int kBirthParts = 16;  // blocks per instance that rank its ionization events
 
 __device__ __forceinline__ i128 warp_incl_scan(i128 v)
 {
@@ -333,13 +334,17 @@ __global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned l
 }
 
 // Children of this step's ionization events are numbered after the largest id so
-// far: electron 2r, ion 2r+1, r = rank of the parent id among this step's events.
+// far: electron 2r, ion 2r+1, r = rank of the parent id among this step's events (with
+// a neutral particle target only the electron is new: id r).  Blocks (instance, part):
+// each part ranks a share of the instance's events against all of them; the last part
+// to finish advances the instance's next id.
 __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* events,
                                                 unsigned long long* ev_count,
                                                 unsigned long long* next_id, uint32_t* id,
-                                                unsigned* err)
+                                                unsigned* err, unsigned* done)
 {
     __shared__ uint32_t sp[1024];
+    __shared__ bool last;
     const int b = blockIdx.x;
     const InstParams& I = inst[b];
     const unsigned long long cnt = ev_count[b];
@@ -347,14 +352,13 @@ __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* e
     const int64_t n = (int64_t)min(cnt, (unsigned long long)I.ev_cap);
     const Event* ev = events + I.ev_base;
     const unsigned long long base = next_id[b];
-    // with a neutral particle target only the electron is new (the ion is a converted
-    // target particle and keeps its id): one id per event
     const unsigned long long per = I.tseg >= 0 ? 1ull : 2ull;
     if (base + per * (unsigned long long)n > 0xFFFFFFFFull) {
         if (threadIdx.x == 0) set_error(err, kErrCapacity);
         return;
     }
-    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.y * blockDim.x; i0 < n; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
         const uint32_t p = i < n ? ev[i].parent : 0u;
         int64_t rank = 0;
@@ -375,8 +379,14 @@ __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* e
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(done + b, 1u) == gridDim.y - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
         next_id[b] = base + per * (unsigned long long)n;
         ev_count[b] = 0ull;
+        done[b] = 0u;
     }
 }
 
@@ -419,9 +429,9 @@ cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_
 
 cudaError_t launch_births(const InstParams* inst, int ninst, Event* events,
                           unsigned long long* ev_count, unsigned long long* next_id,
-                          uint32_t* id, unsigned* err, cudaStream_t st)
+                          uint32_t* id, unsigned* err, unsigned* done, cudaStream_t st)
 {
-    k_births<<<ninst, 256, 0, st>>>(inst, events, ev_count, next_id, id, err);
+    k_births<<<dim3(ninst, kBirthParts), 256, 0, st>>>(inst, events, ev_count, next_id, id, err, done);
     return cudaGetLastError();
 }
 

@@ -66,9 +66,10 @@ cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_
                          unsigned long long* rare_count, cudaStream_t st);
 
 // Number this step's ionization products by the rank of their parent id.
+// `done`: one zeroed counter per instance (left zeroed).
 cudaError_t launch_births(const InstParams* inst, int ninst, Event* events,
                           unsigned long long* ev_count, unsigned long long* next_id,
-                          uint32_t* id, unsigned* err, cudaStream_t st);
+                          uint32_t* id, unsigned* err, unsigned* done, cudaStream_t st);
 
 // ---- sort (sort.cu) ---------------------------------------------------------------
 struct SortArgs {
@@ -82,7 +83,11 @@ struct SortArgs {
     unsigned long long* hwm_alt;      // slots in use of the other copy
     unsigned* hist;                   // per segment node arrays (cells), zeroed
     unsigned* tcount;                 // neutral targets: live targets per cell after the sort
+                                      // (null: no target segment)
+    int64_t seg_nodes;                // entries of the segment node arrays
     unsigned long long* newn;         // per segment live count after the sort
+    unsigned long long* cell_part;    // per segment and chunk of 4096 cells: the chunk's count
+    int cell_chunks;                  // chunks of the largest segment
     // source and destination stores
     int32_t* cell[2];
     void* off[2];

@@ -342,6 +342,7 @@ k_move(const __grid_constant__ MoveArgs a)
     int s = 0;                         // segment of the previous tile (tiles only increase)
     int64_t s_begin = 0, s_end = -1;   // its tiles
     bool moves = MOVE;                 // the segment moves this step (subcycling)
+    bool smag = MAG;                   // the segment's instance is magnetized
     // steps (of the segment's species) to the next multiple of kGapMax
     int dgrid = kGapMax - (int)(step % kGapMax);
     for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
@@ -350,6 +351,9 @@ k_move(const __grid_constant__ MoveArgs a)
             s = advance_segment(a.tile_start, a.nseg, s, tile);
             s_begin = __ldg(a.tile_start + s);
             s_end = __ldg(a.tile_start + s + 1);
+            // in a batch that mixes magnetized and unmagnetized instances, the latter
+            // keep the plain push (and never touch uy, uz), as they would alone
+            if (MAG) smag = a.seg[s].mag != 0;
             if (MOVE && SUB) {
                 // a species with subcycling factor K moves on the steps n with
                 // (n+1) mod K = 0 (all species meet at the multiples of K dt); its
@@ -380,7 +384,7 @@ k_move(const __grid_constant__ MoveArgs a)
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
             ld4(offp + slot, f);
             if (MOVE && (!SUB || moves)) ld4(uxp + slot, ux);
-            if (MOVE && MAG && (!SUB || moves)) {
+            if (MOVE && MAG && smag && (!SUB || moves)) {
                 ld4(uyp + slot, uy);
                 ld4(uzp + slot, uz);
             }
@@ -398,7 +402,7 @@ k_move(const __grid_constant__ MoveArgs a)
                 T fk = f[k];
                 const T acc = Prec<T>::fma_(fk, pr.y, pr.x);
                 // 2. push
-                if (!MAG) {
+                if (!MAG || !smag) {
                     ux[k] = ux[k] + acc;
                 } else {
                     const T half = T(0.5) * acc;
@@ -467,7 +471,7 @@ k_move(const __grid_constant__ MoveArgs a)
                 __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
                 st4(offp + slot, f);
                 st4(uxp + slot, ux);
-                if (MAG) {
+                if (MAG && smag) {
                     st4(uyp + slot, uy);
                     st4(uzp + slot, uz);
                 }

@@ -8,6 +8,8 @@
 // particles.  Results of the time step do not depend on particle order (deposits
 // are integer, random draws are keyed by particle id), so the order inside a cell
 // is free.
+#include <algorithm>
+
 #include "kernels.h"
 #include "mover.cuh"
 
@@ -51,19 +53,19 @@ __global__ void __launch_bounds__(NT) k_hist(const SortArgs a)
     }
 }
 
-// One block per segment: exclusive scan of the cell histogram in place.
-__global__ void __launch_bounds__(1024) k_cell_scan(const SortArgs a)
+// Exclusive scan of the cell histogram of every segment in place, in chunks of
+// kCellChunk cells (blocks (segment, chunk), coalesced): k_cell_partial sums each chunk,
+// k_cell_scan adds the sums of the segment's earlier chunks and scans its own.
+constexpr int kCellThreads = 1024;
+constexpr int kCellRounds = 4;
+constexpr int kCellChunk = kCellThreads * kCellRounds;
+
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long v,
+                                                            unsigned long long* total,
+                                                            unsigned long long* sh /* 33 */)
 {
-    __shared__ unsigned long long sh[33];
-    const SegParams& P = a.seg[blockIdx.x];
-    const int N = P.ncells;
-    const int C = (N + blockDim.x - 1) / blockDim.x;
-    const int j0 = min(N, (int)threadIdx.x * C), j1 = min(N, j0 + C);
-    unsigned long long local = 0;
-    for (int j = j0; j < j1; ++j) local += a.hist[P.node + j];
-    // block exclusive scan (64-bit)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long inc = local;
+    unsigned long long inc = v;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, d);
@@ -84,13 +86,52 @@ __global__ void __launch_bounds__(1024) k_cell_scan(const SortArgs a)
         if (lane == nw - 1) sh[32] = wi;
     }
     __syncthreads();
-    unsigned long long run = sh[warp] + inc - local;
-    for (int j = j0; j < j1; ++j) {
-        const unsigned h = a.hist[P.node + j];
-        a.hist[P.node + j] = (unsigned)run;
-        run += h;
+    const unsigned long long out = sh[warp] + inc - v;
+    *total = sh[32];
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_cell_partial(const SortArgs a)
+{
+    __shared__ unsigned long long sh[33];
+    const SegParams& P = a.seg[blockIdx.x];
+    const int c = blockIdx.y;
+    const int N = P.ncells;
+    if ((int64_t)c * kCellChunk >= N) return;
+    unsigned long long local = 0;
+#pragma unroll
+    for (int r = 0; r < kCellRounds; ++r) {
+        const int j = c * kCellChunk + r * kCellThreads + threadIdx.x;
+        if (j < N) local += a.hist[P.node + j];
     }
-    if (threadIdx.x == 0) a.newn[blockIdx.x] = sh[32];
+    unsigned long long tot;
+    block_scan_u64(local, &tot, sh);
+    if (threadIdx.x == 0) a.cell_part[(int64_t)blockIdx.x * a.cell_chunks + c] = tot;
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_cell_scan(const SortArgs a)
+{
+    __shared__ unsigned long long sh[33];
+    const SegParams& P = a.seg[blockIdx.x];
+    const int c = blockIdx.y;
+    const int N = P.ncells;
+    const int nch = (N + kCellChunk - 1) / kCellChunk;
+    if (c >= nch) return;
+    const unsigned long long* part = a.cell_part + (int64_t)blockIdx.x * a.cell_chunks;
+    unsigned long long run = 0;
+    for (int k = threadIdx.x; k < c; k += blockDim.x) run += part[k];
+    unsigned long long off;
+    block_scan_u64(run, &off, sh);  // off = the sum of all earlier chunks
+    for (int r = 0; r < kCellRounds; ++r) {
+        const int j = c * kCellChunk + r * kCellThreads + threadIdx.x;
+        const unsigned h = j < N ? a.hist[P.node + j] : 0u;
+        unsigned long long tot;
+        const unsigned long long ex = block_scan_u64(h, &tot, sh);
+        if (j < N) a.hist[P.node + j] = (unsigned)(off + ex);
+        off += tot;
+    }
+    if (c == nch - 1 && threadIdx.x == 0) a.newn[blockIdx.x] = off;
 }
 
 // One lane's quad in flight through the scatter.
@@ -202,11 +243,6 @@ __global__ void k_sort_finish(const SortArgs a)
     const unsigned long long hw = min(max(old, a.hwm_alt[s]), (unsigned long long)P.cap);
     int32_t* dcell = a.cell[1 - a.src];
     for (unsigned long long i = nnew + threadIdx.x; i < hw; i += blockDim.x) dcell[P.base + (int64_t)i] = -1;
-    // a neutral particle target: its live particles per cell, from the cell ends the
-    // scatter left in the histogram
-    if (P.is_target)
-        for (int j = threadIdx.x; j < P.ncells; j += blockDim.x)
-            a.tcount[P.node + j] = a.hist[P.node + j] - (j > 0 ? a.hist[P.node + j - 1] : 0u);
     __syncthreads();
     if (threadIdx.x == 0) {
         a.hwm_alt[s] = old;
@@ -227,16 +263,38 @@ int one_wave(K kernel, int nt, int sms)
     return nb * sms;
 }
 
+// Neutral particle targets: the live particles of every cell, from the cell ends the
+// scatter left in the histogram.  One thread per node of all segments.
+__global__ void __launch_bounds__(256) k_target_counts(const SortArgs a)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < a.seg_nodes; n += stride) {
+        int lo = 0, hi = a.nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.seg[mid].node <= n) lo = mid; else hi = mid - 1;
+        }
+        const SegParams& P = a.seg[lo];
+        const int j = (int)(n - P.node);
+        if (!P.is_target || j >= P.ncells) continue;
+        a.tcount[n] = a.hist[n] - (j > 0 ? a.hist[n - 1] : 0u);
+    }
+}
+
 template <int NT>
 cudaError_t run_sort(const SortArgs& a, int sms, cudaStream_t st)
 {
     k_hist<NT><<<one_wave(k_hist<NT>, NT, sms), NT, 0, st>>>(a);
-    k_cell_scan<<<a.nseg, 1024, 0, st>>>(a);
+    const dim3 cg(a.nseg, a.cell_chunks);
+    k_cell_partial<<<cg, kCellThreads, 0, st>>>(a);
+    k_cell_scan<<<cg, kCellThreads, 0, st>>>(a);
     if (a.precision == PIC_FP64)
         k_scatter<double, NT><<<one_wave(k_scatter<double, NT>, NT, sms), NT, 0, st>>>(a);
     else
         k_scatter<float, NT><<<one_wave(k_scatter<float, NT>, NT, sms), NT, 0, st>>>(a);
     k_sort_finish<<<a.nseg, 256, 0, st>>>(a);
+    if (a.tcount)
+        k_target_counts<<<(int)std::min<int64_t>((a.seg_nodes + 255) / 256, 64 * sms), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -78,3 +78,29 @@ def test_subcycled_checkpoint_restart_off_the_cycle():
     for x, y in zip(want, got):
         for k in x:
             np.testing.assert_array_equal(x[k], y[k])
+
+
+def test_subcycled_and_smoothed_instances_in_a_batch_equal_alone():
+    ensure_built()
+    a = W.bounded_small(ncells=64, ppc=40, seed=5, ion_nstep=3)
+    b = W.magnetized_source(ncells=48, ppc=30, seed=6, nu=0.2, capacity_factor=3.0, ion_nstep=5)
+    b.smooth = 1
+    c = W.bounded_small(ncells=32, ppc=20, seed=7)
+    phys = [a, b, c]
+    loads = [W.initial_load(p, seed=p.seed) for p in phys]
+    steps = 33
+    sim = capi.Sim(phys, precision=capi.FP64, sort_interval=10)
+    for i, ld in enumerate(loads):
+        sim.load_all(ld, inst=i)
+    sim.step(steps)
+    batch = [[by_id(sim.particles(i, s)) for s in range(2)] for i in range(3)]
+    sim.close()
+    for i, p in enumerate(phys):
+        s1 = capi.Sim(p, precision=capi.FP64, sort_interval=10)
+        s1.load_all(loads[i])
+        s1.step(steps)
+        alone = [by_id(s1.particles(0, s)) for s in range(2)]
+        s1.close()
+        for x, y in zip(alone, batch[i]):
+            for k in x:
+                np.testing.assert_array_equal(x[k], y[k])

@@ -52,3 +52,34 @@ def test_depletion_to_exhaustion_fp64():
         assert ex < 1e-12 and ev < 1e-12, (s, ex, ev)
     for s in range(3):
         np.testing.assert_array_equal(np.sort(g[s]["id"]), np.sort(o[s]["id"]))
+
+
+def test_target_instances_in_a_batch_equal_alone():
+    """Two Table-1 instances of different sizes and seeds, plus a plain bounded plasma,
+    in one handle: each target instance gives exactly what it gives alone (every count,
+    every particle bit for bit)."""
+    from tests.gpu_common import ensure_built
+    ensure_built()
+    a = W.ionization_case(ncells=128, ppc=48, nu_iz=0.1, nu_exc=0.05, nu_el=0.05, seed=3)
+    b = W.ionization_case(ncells=96, ppc=64, nu_iz=0.2, nu_exc=0.0, nu_el=0.1, seed=4)
+    phys = [a, b]
+    loads = [W.initial_load(p, seed=p.seed) for p in phys]
+    steps = 45
+    sim = capi.Sim(phys, precision=capi.FP64, sort_interval=20)
+    for i, ld in enumerate(loads):
+        sim.load_all(ld, inst=i)
+    sim.step(steps)
+    batch = [([by_id(sim.particles(i, s)) for s in range(3)], sim.moments(i)) for i in range(2)]
+    sim.close()
+    for i, p in enumerate(phys):
+        s1 = capi.Sim(p, precision=capi.FP64, sort_interval=20)
+        s1.load_all(loads[i])
+        s1.step(steps)
+        alone = [by_id(s1.particles(0, s)) for s in range(3)]
+        m = s1.moments(0)
+        s1.close()
+        np.testing.assert_array_equal(batch[i][1]["live"], m["live"])
+        np.testing.assert_array_equal(batch[i][1]["collisions"], m["collisions"])
+        for x, y in zip(alone, batch[i][0]):
+            for k in x:
+                np.testing.assert_array_equal(x[k], y[k])
