@@ -74,6 +74,7 @@ struct pic_handle {
     int max_nodes = 0;
     bool any_poisson = false, any_mag = false, any_ionize = false, any_subcycle = false;
     bool any_target = false;       // some instance collides with neutral particles
+    bool any_unmag = false;        // some instance has no magnetic field
     unsigned *tcount = nullptr, *treq = nullptr;  // target segment node arrays
     int grid_victims = 0;
 
@@ -438,8 +439,10 @@ int launch_move(pic_handle* h, bool move)
         Span sp(h, 0);
         h->kernels += 1;
         const cudaError_t e = h->precision == PIC_FP64
-                                  ? launch_move_f64(a, mag, move, h->any_subcycle, h->nt, h->grid_move, h->stream)
-                                  : launch_move_f32(a, mag, move, h->any_subcycle, h->nt, h->grid_move, h->stream);
+                                  ? launch_move_f64(a, mag, move, h->any_subcycle, h->any_unmag, h->nt,
+                                                    h->grid_move, h->stream)
+                                  : launch_move_f32(a, mag, move, h->any_subcycle, h->any_unmag, h->nt,
+                                                    h->grid_move, h->stream);
         CUDA_TRY(h, e);
     }
     if (move) {
@@ -785,6 +788,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         ev += ip.ev_cap;
         h->any_ionize |= ionize;
         if (I.B[0] != 0.0 || I.B[1] != 0.0 || I.B[2] != 0.0) h->any_mag = true;
+        else h->any_unmag = true;
         for (int s = 0; s < I.nspecies; ++s)
             if (species_nstep(I, s) > 1) h->any_subcycle = true;
         for (int s = 0; s < I.nspecies; ++s) {

@@ -11,12 +11,12 @@ struct MoveArgs;
 
 // ---- mover (mover_f32.cu, mover_f64.cu) ---------------------------------------
 // `move` = false deposits the loaded particles without moving them (the density
-// phase of the initial field); `sub`: some species is subcycled.  Returns the launch
-// error.
-cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, int nt, int grid,
-                            cudaStream_t st);
-cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, int nt, int grid,
-                            cudaStream_t st);
+// phase of the initial field); `sub`: some species is subcycled; `mixed`: magnetized and
+// unmagnetized instances in one batch.  Returns the launch error.
+cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int nt,
+                            int grid, cudaStream_t st);
+cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int nt,
+                            int grid, cudaStream_t st);
 // The rare events the mover queued this step (events.cu): collision candidates and
 // wall hits, one thread each, `grid` blocks of 128 threads.
 cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream_t st);

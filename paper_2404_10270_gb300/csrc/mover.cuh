@@ -323,8 +323,9 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
 // one vector load (the node arrays are small and stay in L1/L2).  The loop is free of
 // calls; walls and collision candidates are queued for the event kernel.
 // SUB: some species of the batch is subcycled (else every segment moves every step and
-// the clock grid is the global one, computed once).
-template <typename T, int NT, bool MAG, bool MOVE, bool SUB>
+// the clock grid is the global one, computed once).  MIXED (with MAG): the batch mixes
+// magnetized and unmagnetized instances, so the push is chosen per segment.
+template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED>
 __global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
@@ -353,7 +354,7 @@ k_move(const __grid_constant__ MoveArgs a)
             s_end = __ldg(a.tile_start + s + 1);
             // in a batch that mixes magnetized and unmagnetized instances, the latter
             // keep the plain push (and never touch uy, uz), as they would alone
-            if (MAG) smag = a.seg[s].mag != 0;
+            if (MAG && MIXED) smag = a.seg[s].mag != 0;
             if (MOVE && SUB) {
                 // a species with subcycling factor K moves on the steps n with
                 // (n+1) mod K = 0 (all species meet at the multiples of K dt); its

@@ -5,44 +5,46 @@
 namespace bitpic {
 
 namespace {
-template <int NT>
-cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, int grid, cudaStream_t st)
+template <int NT, bool SUB>
+cudaError_t go_sub(const MoveArgs& a, bool mag, bool mixed, int grid, cudaStream_t st)
 {
-    if (move) {
-        if (mag) {
-            if (sub)
-                k_move<float, NT, true, true, true><<<grid, NT, 0, st>>>(a);
-            else
-                k_move<float, NT, true, true, false><<<grid, NT, 0, st>>>(a);
-        } else {
-            if (sub)
-                k_move<float, NT, false, true, true><<<grid, NT, 0, st>>>(a);
-            else
-                k_move<float, NT, false, true, false><<<grid, NT, 0, st>>>(a);
-        }
-    } else {
-        k_move<float, NT, false, false, false><<<grid, NT, 0, st>>>(a);
-    }
+    if (!mag)
+        k_move<float, NT, false, true, SUB, false><<<grid, NT, 0, st>>>(a);
+    else if (mixed)
+        k_move<float, NT, true, true, SUB, true><<<grid, NT, 0, st>>>(a);
+    else
+        k_move<float, NT, true, true, SUB, false><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int grid,
+               cudaStream_t st)
+{
+    if (!move) {
+        k_move<float, NT, false, false, false, false><<<grid, NT, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    return sub ? go_sub<NT, true>(a, mag, mixed, grid, st) : go_sub<NT, false>(a, mag, mixed, grid, st);
 }
 
 template <int NT>
 int occupancy(bool mag)
 {
     int n = 0;
-    cudaError_t e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true, false>, NT, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false>, NT, 0);
+    cudaError_t e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true, false, false>, NT, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false, false>, NT, 0);
     return e == cudaSuccess ? n : 0;
 }
 }  // namespace
 
-cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, int nt, int grid,
-                            cudaStream_t st)
+cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int nt,
+                            int grid, cudaStream_t st)
 {
     switch (nt) {
-        case 128: return go<128>(a, mag, move, sub, grid, st);
-        case 512: return go<512>(a, mag, move, sub, grid, st);
-        default: return go<256>(a, mag, move, sub, grid, st);
+        case 128: return go<128>(a, mag, move, sub, mixed, grid, st);
+        case 512: return go<512>(a, mag, move, sub, mixed, grid, st);
+        default: return go<256>(a, mag, move, sub, mixed, grid, st);
     }
 }
 
