@@ -245,6 +245,7 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
     sort_n, sort_ms = sim.kernel_time(2)
     other_n, other_ms = sim.kernel_time(3)
     kernels, _ = sim.kernel_time(4)
+    smove_n, smove_ms = sim.kernel_time(5)
     sim.profile(False)
     from paper_2404_10270_gb300.sharding import combine_timing
     ms_max, psteps = combine_timing(ms, (live0 + live1) / 2 * steps, device="cuda")
@@ -276,7 +277,8 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
                      "bytes_per_particle": bpp,
                      "avg_launch_ms": avg_mover_ms},
         "kernel_ms": {"mover": mover_ms, "field": field_ms, "sort": sort_ms, "other": other_ms,
-                      "mover_launches": mover_n, "sort_launch_groups": sort_n,
+                      "sorting_mover": smove_ms, "mover_launches": mover_n,
+                      "sorting_mover_launches": smove_n, "sort_launch_groups": sort_n,
                       "ms_per_step_with_kernel_events": ms_profiled / steps},
         "gpu_launches": kernels,
         "clocks": clk.summary(),

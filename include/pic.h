@@ -215,9 +215,10 @@ PIC_API int pic_charge_raw(pic_handle* h, int32_t inst, int64_t* out, int64_t* u
 
 /* Kernel timing: when enabled, every kernel launch of pic_step is bracketed by CUDA
  * events on the handle's stream.  pic_kernel_time returns, for kernel class `which`
- * (0 mover, 1 field, 2 sort, 3 other), the number of timed launch groups and their
- * total milliseconds since the last pic_profile call (synchronises); `which` = 4
- * returns the number of kernels the library launched since then (total_ms = 0). */
+ * (0 mover, 1 field, 2 sort, 3 other, 5 the mover of a step that also sorts the store),
+ * the number of timed launch groups and their total milliseconds since the last
+ * pic_profile call (synchronises); `which` = 4 returns the number of kernels the
+ * library launched since then (total_ms = 0). */
 PIC_API int pic_profile(pic_handle* h, int32_t enable);
 PIC_API int pic_kernel_time(pic_handle* h, int32_t which, int64_t* launches, double* total_ms);
 

@@ -292,7 +292,8 @@ class Sim:
         _check(lib().pic_profile(self._h, 1 if enable else 0), self._h)
 
     def kernel_time(self, which: int):
-        """(launches, total_ms) of kernel class 0 mover, 1 field, 2 sort, 3 other."""
+        """(launches, total_ms) of kernel class 0 mover, 1 field, 2 sort, 3 other,
+        5 the mover of a sort step; class 4 gives (kernels launched, 0)."""
         n = C.c_int64()
         ms = C.c_double()
         _check(lib().pic_kernel_time(self._h, which, C.byref(n), C.byref(ms)), self._h)

@@ -12,7 +12,12 @@
 //   k_births    number this step's ionization products (only with ionization)
 //   k_field     exact integer Poisson solve (optional smoother) -> E -> node pairs of
 //               pre-scaled accelerations, and hand-over of the deposit (field.cu)
-//   every `sort_interval` steps: k_tiles, histogram, scan, scatter (sort.cu).
+//   the sort, every `sort_interval` steps: the step before counts the particles per cell
+//   at its end (k_move's deposit, k_events); the sort step scans the counts
+//   (k_cell_partial, k_cell_scan), its mover writes every particle into its cell-ordered
+//   slot of the other store copy, and k_sort_finish adopts the new counts before
+//   k_events.  Otherwise (neutral targets, sort interval 1, no counts from the step
+//   before) the separate sort follows the step: k_tiles, histogram, scan, scatter.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -115,6 +120,11 @@ struct pic_handle {
     bool own_stream = false;
     int64_t step_h = 0;
     bool stale = true;
+    // the sort folded into the time step: the last step before a sort counted the
+    // particles per cell into `hist` (cleared by anything that changes the store from
+    // the host, and by the sort that used it); grid of the sorting mover
+    bool hist_ready = false;
+    int grid_sort = 0;
     int state = PIC_OK;
     std::string last_error;
 
@@ -135,8 +145,10 @@ struct pic_handle {
     struct Timed { int cls; cudaEvent_t a, b; };
     std::vector<Timed> timed;
     std::vector<cudaEvent_t> event_pool;
-    int64_t launches[4] = {0, 0, 0, 0};
-    double ms[4] = {0, 0, 0, 0};
+    // per kernel class: 0 mover, 1 field, 2 sort, 3 other, 5 the mover of a sort step
+    // (index 4 is unused: pic_kernel_time(4) reports the kernel count)
+    int64_t launches[6] = {0, 0, 0, 0, 0, 0};
+    double ms[6] = {0, 0, 0, 0, 0, 0};
     int64_t kernels = 0;  // kernel launches since the last pic_profile call
 };
 
@@ -403,6 +415,42 @@ MoveArgs move_args(pic_handle* h)
     a.tcount = h->tcount;
     a.treq = h->treq;
     a.hist = h->hist;
+    a.hist_out = nullptr;
+    a.cursor = nullptr;
+    a.dcell = nullptr;
+    a.doff = a.dux = a.duy = a.duz = nullptr;
+    a.did = nullptr;
+    return a;
+}
+
+SortArgs sort_args(pic_handle* h)
+{
+    SortArgs a;
+    a.seg = h->segd;
+    a.nseg = h->nseg;
+    a.precision = h->precision;
+    a.tile_start = h->tile_start;
+    a.seg_nmove = h->seg_nmove;
+    a.seg_n = h->seg_n;
+    a.seg_live = h->seg_live;
+    a.hwm_alt = h->hwm_alt;
+    a.hist = h->hist;
+    a.tcount = h->any_target ? h->tcount : nullptr;
+    a.cell_part = h->cell_part;
+    a.cell_chunks = h->cell_chunks;
+    a.seg_nodes = h->seg_nodes;
+    a.newn = h->newn;
+    for (int b = 0; b < 2; ++b) {
+        a.cell[b] = h->st[b].cell;
+        a.off[b] = h->st[b].off;
+        a.ux[b] = h->st[b].ux;
+        a.uy[b] = h->st[b].uy;
+        a.uz[b] = h->st[b].uz;
+        a.id[b] = h->st[b].id;
+    }
+    a.src = h->cur;
+    a.max_cap = h->max_cap;
+    a.max_cells = h->max_nodes - 1;
     return a;
 }
 
@@ -431,19 +479,54 @@ FieldArgs field_args(pic_handle* h)
     return f;
 }
 
-int launch_move(pic_handle* h, bool move)
+// Phases of a time step with respect to the sort folded into it.
+enum StepPhase { kPlain = 0, kCount = 1, kSortStep = 2 };
+
+// The mover (and, for a time step, the event kernels).  kCount: the step also counts the
+// particles per cell at its end into `hist`; kSortStep: the step scans those counts,
+// moves every particle into its sorted slot of the other store copy, adopts the new
+// counts and makes that copy current before the event kernels run on it.
+int launch_move(pic_handle* h, bool move, int phase = kPlain)
 {
-    const MoveArgs a = move_args(h);
+    MoveArgs a = move_args(h);
     const bool mag = move && h->any_mag;
+    const bool sort = move && phase == kSortStep;
+    SortArgs sa;
+    if (move && phase == kCount) {
+        CUDA_TRY(h, cudaMemsetAsync(h->hist, 0, sizeof(unsigned) * (size_t)h->seg_nodes, h->stream));
+        a.hist_out = h->hist;
+    }
+    if (sort) {
+        sa = sort_args(h);
+        Span sp(h, 2);
+        h->kernels += 2;
+        CUDA_TRY(h, launch_sort_scan(sa, h->stream));
+        const Store& D = h->st[1 - h->cur];
+        a.cursor = h->hist;
+        a.dcell = D.cell;
+        a.doff = D.off;
+        a.dux = D.ux;
+        a.duy = D.uy;
+        a.duz = D.uz;
+        a.did = D.id;
+    }
     {
-        Span sp(h, 0);
+        Span sp(h, sort ? 5 : 0);
         h->kernels += 1;
+        const int grid = sort ? h->grid_sort : h->grid_move;
         const cudaError_t e = h->precision == PIC_FP64
-                                  ? launch_move_f64(a, mag, move, h->any_subcycle, h->any_unmag, h->nt,
-                                                    h->grid_move, h->stream)
-                                  : launch_move_f32(a, mag, move, h->any_subcycle, h->any_unmag, h->nt,
-                                                    h->grid_move, h->stream);
+                                  ? launch_move_f64(a, mag, move, h->any_subcycle, h->any_unmag, sort,
+                                                    h->nt, grid, h->stream)
+                                  : launch_move_f32(a, mag, move, h->any_subcycle, h->any_unmag, sort,
+                                                    h->nt, grid, h->stream);
         CUDA_TRY(h, e);
+    }
+    if (sort) {
+        Span sp(h, 2);
+        h->kernels += 1;
+        CUDA_TRY(h, launch_sort_finish(sa, h->stream));
+        h->cur = 1 - h->cur;
+        a = move_args(h);  // the event kernels work on the sorted copy
     }
     if (move) {
         Span se(h, 3);
@@ -472,6 +555,7 @@ int ensure_fields(pic_handle* h)
 {
     if (!h->stale) return PIC_OK;
     int rc;
+    h->hist_ready = false;
     // a neutral particle target needs the cell ranges of a sorted store
     if (h->any_target && (rc = do_sort(h))) return rc;
     rc = launch_tiles_h(h);
@@ -486,38 +570,16 @@ int ensure_fields(pic_handle* h)
     return PIC_OK;
 }
 
+// The separate sort (histogram, scan, scatter, finish): neutral targets, sort interval
+// 1, and a sort due with no histogram counted by the step before.
 int do_sort(pic_handle* h)
 {
     int rc = launch_tiles_h(h);
     if (rc) return rc;
     Span sp(h, 2);
     CUDA_TRY(h, cudaMemsetAsync(h->hist, 0, sizeof(unsigned) * (size_t)h->seg_nodes, h->stream));
-    SortArgs a;
-    a.seg = h->segd;
-    a.nseg = h->nseg;
-    a.precision = h->precision;
-    a.tile_start = h->tile_start;
-    a.seg_nmove = h->seg_nmove;
-    a.seg_n = h->seg_n;
-    a.seg_live = h->seg_live;
-    a.hwm_alt = h->hwm_alt;
-    a.hist = h->hist;
-    a.tcount = h->any_target ? h->tcount : nullptr;
-    a.cell_part = h->cell_part;
-    a.cell_chunks = h->cell_chunks;
-    a.seg_nodes = h->seg_nodes;
-    a.newn = h->newn;
-    for (int b = 0; b < 2; ++b) {
-        a.cell[b] = h->st[b].cell;
-        a.off[b] = h->st[b].off;
-        a.ux[b] = h->st[b].ux;
-        a.uy[b] = h->st[b].uy;
-        a.uz[b] = h->st[b].uz;
-        a.id[b] = h->st[b].id;
-    }
-    a.src = h->cur;
-    a.max_cap = h->max_cap;
-    a.max_cells = h->max_nodes - 1;
+    const SortArgs a = sort_args(h);
+    h->hist_ready = false;
     h->kernels += h->any_target ? 6 : 5;
     CUDA_TRY(h, launch_sort(a, h->nt, h->sms, h->stream));
     h->cur = 1 - h->cur;
@@ -562,9 +624,12 @@ int collect_times(pic_handle* h)
 void set_block(pic_handle* h, int nt)
 {
     h->nt = nt;
-    const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, nt)
-                                             : move_blocks_per_sm_f32(h->any_mag, nt);
+    const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, false, nt)
+                                             : move_blocks_per_sm_f32(h->any_mag, false, nt);
     h->grid_move = h->sms * std::max(bps, 1);
+    const int bss = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, true, nt)
+                                             : move_blocks_per_sm_f32(h->any_mag, true, nt);
+    h->grid_sort = h->sms * std::max(bss, 1);
 }
 
 void drop_graphs(pic_handle* h)
@@ -1097,17 +1162,34 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     }
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h->stale = true;
+    h->hist_ready = false;
     return PIC_OK;
 }
 
 namespace {
 
-// Enqueue one time step (and the sort when it falls due).
+// Enqueue one time step (and the sort when it falls due).  A sort falls due at the end of
+// every step n with (n+1) mod sort_interval = 0.  It is folded into that step (the
+// mover writes the particles in cell order into the other copy) when the step before
+// counted the particles per cell; else (neutral targets, which need their cell ranges
+// from the sort at the end of the step; sort interval 1; a run that starts on the
+// sort step) the separate sort follows the step.
 int enqueue_step(pic_handle* h)
 {
     int rc;
+    const int64_t K = h->sort_interval;
+    const bool fold = K >= 2 && !h->any_target;
+    int phase = kPlain;
+    bool sort_after = false;
+    if (K > 0 && (h->step_h + 1) % K == 0) {
+        if (fold && h->hist_ready) phase = kSortStep;
+        else sort_after = true;
+    } else if (fold && (h->step_h + 2) % K == 0) {
+        phase = kCount;
+    }
     if ((rc = launch_tiles_h(h))) return rc;
-    if ((rc = launch_move(h, true))) return rc;
+    if ((rc = launch_move(h, true, phase))) return rc;
+    h->hist_ready = phase == kCount;
     if (h->any_ionize) {
         Span sp(h, 3);
         h->kernels += 1;
@@ -1120,8 +1202,7 @@ int enqueue_step(pic_handle* h)
         CUDA_TRY(h, launch_field(field_args(h), true, h->stream));
     }
     h->step_h += 1;
-    if (h->sort_interval > 0 && h->step_h % h->sort_interval == 0)
-        if ((rc = do_sort(h))) return rc;
+    if (sort_after && (rc = do_sort(h))) return rc;
     return PIC_OK;
 }
 
@@ -1132,6 +1213,7 @@ int enqueue_step(pic_handle* h)
 int capture_cycle(pic_handle* h)
 {
     const int c0 = h->cur;
+    const bool hr0 = h->hist_ready;
     const int64_t step0 = h->step_h, k0 = h->kernels;
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = PIC_OK;
@@ -1140,6 +1222,7 @@ int capture_cycle(pic_handle* h)
     const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->step_h = step0;
     h->cur = c0;
+    h->hist_ready = hr0;
     h->cycle_kernels = h->kernels - k0;
     h->kernels = k0;
     if (rc != PIC_OK) {
@@ -1208,6 +1291,7 @@ int pic_step(pic_handle* h, int64_t nsteps)
                 }
             }
             drop_graphs(h);
+            h->hist_ready = false;
             continue;
         }
         const bool graphs = h->graphs && !h->profiling && !h->tune_phase && K > 0 &&
@@ -1218,6 +1302,7 @@ int pic_step(pic_handle* h, int64_t nsteps)
             h->kernels += h->cycle_kernels;
             h->step_h += K;
             h->cur = 1 - h->cur;
+            h->hist_ready = false;
             n += K;
             continue;
         }
@@ -1404,6 +1489,7 @@ int pic_restore_counters(pic_handle* h, int64_t step, const uint64_t* next_id)
         CUDA_TRY(h, cudaMemcpy(h->next_id, next_id, 8 * (size_t)h->ninst, cudaMemcpyHostToDevice));
     }
     h->step_h = step;
+    h->hist_ready = false;
     return PIC_OK;
 }
 
@@ -1431,7 +1517,7 @@ int pic_profile(pic_handle* h, int32_t enable)
     if (rc) return rc;
     if ((rc = collect_times(h))) return rc;
     h->profiling = enable != 0;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 6; ++k) {
         h->launches[k] = 0;
         h->ms[k] = 0.0;
     }
@@ -1443,7 +1529,7 @@ int pic_kernel_time(pic_handle* h, int32_t which, int64_t* launches, double* tot
 {
     int rc = check_state(h);
     if (rc) return rc;
-    if (which < 0 || which > 4 || !launches || !total_ms) return fail(h, PIC_EINVAL, "pic_kernel_time: bad arguments");
+    if (which < 0 || which > 5 || !launches || !total_ms) return fail(h, PIC_EINVAL, "pic_kernel_time: bad arguments");
     if ((rc = collect_times(h))) return rc;
     if (which == 4) {
         *launches = h->kernels;

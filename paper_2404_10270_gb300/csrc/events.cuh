@@ -5,7 +5,8 @@
 // source).  The mover queues them (rare_pack) so that its own loop stays call-free;
 // here one thread takes one queued particle.  Collisions change only velocities, so
 // the mover has already deposited a candidate; a re-injected particle and the
-// children of an ionization are deposited here.  Everything this kernel adds is an
+// children of an ionization are deposited here (and, on the step before a sort,
+// counted in the cell histogram).  Everything this kernel adds is an
 // integer sum or keyed by particle id and step, so the order of the queue does not
 // change any result.
 #pragma once
@@ -141,6 +142,7 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
             const uint64_t qr = Prec<T>::qright(f), ql = Prec<T>::S - qr;
             atomicAdd(a.dep + P.node + j, (unsigned long long)ql);
             atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
+            if (a.hist_out) atomicAdd(a.hist_out + P.node + j, 1u);
             Event e;
             e.parent = id;
             e.pad = 0;
@@ -162,6 +164,7 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
                 atomicAdd(a.seg_live + si, 1ull);
                 atomicAdd(a.dep + Pi.node + j, (unsigned long long)ql);
                 atomicAdd(a.dep + Pi.node + j + 1, (unsigned long long)qr);
+                if (a.hist_out) atomicAdd(a.hist_out + Pi.node + j, 1u);
             }
             a.events[Ii.ev_base + (int64_t)ev] = e;
         }
@@ -263,6 +266,7 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                     const uint64_t qr = Prec<T>::qright(f);
                     atomicAdd(a.dep + P.node + j, (unsigned long long)(Prec<T>::S - qr));
                     atomicAdd(a.dep + P.node + j + 1, (unsigned long long)qr);
+                    if (a.hist_out) atomicAdd(a.hist_out + P.node + j, 1u);
                 }
             }
         }

@@ -12,11 +12,12 @@ struct MoveArgs;
 // ---- mover (mover_f32.cu, mover_f64.cu) ---------------------------------------
 // `move` = false deposits the loaded particles without moving them (the density
 // phase of the initial field); `sub`: some species is subcycled; `mixed`: magnetized and
-// unmagnetized instances in one batch.  Returns the launch error.
-cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int nt,
-                            int grid, cudaStream_t st);
-cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int nt,
-                            int grid, cudaStream_t st);
+// unmagnetized instances in one batch; `sort`: the step also sorts the store by cell
+// into the other copy (MoveArgs.cursor, .d*).  Returns the launch error.
+cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
+                            bool sort, int nt, int grid, cudaStream_t st);
+cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
+                            bool sort, int nt, int grid, cudaStream_t st);
 // The rare events the mover queued this step (events.cu): collision candidates and
 // wall hits, one thread each, `grid` blocks of 128 threads.
 cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream_t st);
@@ -25,8 +26,8 @@ cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream
 cudaError_t launch_victims(const MoveArgs& a, int precision, int64_t nnodes, int grid,
                            cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
-int move_blocks_per_sm_f32(bool mag, int nt);
-int move_blocks_per_sm_f64(bool mag, int nt);
+int move_blocks_per_sm_f32(bool mag, bool sort, int nt);
+int move_blocks_per_sm_f64(bool mag, bool sort, int nt);
 
 // ---- field phase and bookkeeping (field.cu) -------------------------------------
 struct FieldArgs {
@@ -101,6 +102,11 @@ struct SortArgs {
 };
 // Grids are one resident wave of each kernel on `sms` multiprocessors.
 cudaError_t launch_sort(const SortArgs& s, int nt, int sms, cudaStream_t st);
+// The sort folded into a time step: the exclusive scan of the cell histogram the step
+// before counted (`hist`, in place, and each segment's total into `newn`) before the
+// sorting mover, and the new counts and the destination's empty tail after it.
+cudaError_t launch_sort_scan(const SortArgs& s, cudaStream_t st);
+cudaError_t launch_sort_finish(const SortArgs& s, cudaStream_t st);
 
 // ---- I/O and diagnostics (io.cu) -------------------------------------------------
 struct LoadArgs {

@@ -83,6 +83,18 @@ struct MoveArgs {
     unsigned* tcount;
     unsigned* treq;
     const unsigned* hist;
+    // the sort folded into the time step: the step before a sort counts each cell's
+    // particles at the end of the step into `hist_out` (null: no counting); the sort
+    // step reserves each particle's slot in the other store copy from `cursor` (the
+    // scanned counts, by the cell at the start of the step) and writes it there
+    unsigned* hist_out;
+    unsigned* cursor;
+    int32_t* dcell;
+    void* doff;
+    void* dux;
+    void* duy;
+    void* duz;
+    uint32_t* did;
 };
 
 template <typename T> struct Prec;
@@ -244,7 +256,8 @@ __device__ __forceinline__ void st4(double* p, const double v[4])
 template <typename Q>
 __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
                                              unsigned long long S,
-                                             unsigned long long* __restrict__ gdep)
+                                             unsigned long long* __restrict__ gdep,
+                                             unsigned* __restrict__ ghist)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -306,13 +319,63 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
                 S * (unsigned long long)myn - myR + (lane > 0 ? prevR : 0ull);
             if (tot != 0) atomicAdd(gdep + wmin + lane, tot);
         }
+        // the particles per cell, for a sort in the next step
+        if (ghist && lane < ncell && myn != 0u) atomicAdd(ghist + wmin + lane, myn);
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (jd[k] >= 0) {
                 atomicAdd(gdep + jd[k], S - (unsigned long long)qr[k]);
                 atomicAdd(gdep + jd[k] + 1, (unsigned long long)qr[k]);
+                if (ghist) atomicAdd(ghist + jd[k], 1u);
             }
+    }
+}
+
+// Sort step: the slot of each particle that was in the quad at the start of the step
+// (-1: none) from its group's reservation and its rank in the group; a reservation past
+// the segment (a histogram that does not match the store, which no path produces) is
+// refused and latched rather than written.
+__device__ __forceinline__ void sort_destinations(const MoveArgs& a, const SegParams& P,
+                                                  const unsigned grp[4], const unsigned rbase[4],
+                                                  unsigned had, int64_t to[4])
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned b = __shfl_sync(0xffffffffu, rbase[k], __ffs(grp[k]) - 1);
+        to[k] = -1;
+        if (had & (1u << k)) {
+            const int64_t r = (int64_t)b + __popc(grp[k] & lt);
+            if (r < P.cap) to[k] = P.base + r;
+            else set_error(a.err, kErrCapacity);
+        }
+    }
+}
+
+// Sort step: the quad's particles into their slots of the other store copy (a particle
+// that left through a wall goes there as an empty slot with its velocity, for the event
+// kernel).
+template <typename T>
+__device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4], const int c[4],
+                                           const T f[4], const T ux[4], const T uy[4],
+                                           const T uz[4], const uint32_t id[4])
+{
+    T* const doff = static_cast<T*>(a.doff);
+    T* const dux = static_cast<T*>(a.dux);
+    T* const duy = static_cast<T*>(a.duy);
+    T* const duz = static_cast<T*>(a.duz);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (to[k] < 0) continue;
+        const int64_t g = to[k];
+        a.dcell[g] = c[k];
+        doff[g] = f[k];
+        dux[g] = ux[k];
+        duy[g] = uy[k];
+        duz[g] = uz[k];
+        a.did[g] = id[k];
     }
 }
 
@@ -324,9 +387,12 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
 // calls; walls and collision candidates are queued for the event kernel.
 // SUB: some species of the batch is subcycled (else every segment moves every step and
 // the clock grid is the global one, computed once).  MIXED (with MAG): the batch mixes
-// magnetized and unmagnetized instances, so the push is chosen per segment.
-template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED>
-__global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT>::blocks)
+// magnetized and unmagnetized instances, so the push is chosen per segment.  SORT: the
+// step that ends a sort cycle; every particle goes to its slot of the other store copy
+// (reserved from `cursor` by its cell at the start of the step, the order of a counting
+// sort) instead of back to its own.
+template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool SORT>
+__global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG || SORT, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
     using Q = typename Prec<T>::Q;
@@ -380,16 +446,36 @@ k_move(const __grid_constant__ MoveArgs a)
         int c[4] = {-1, -1, -1, -1};
         T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
         T uy[4] = {T(0), T(0), T(0), T(0)}, uz[4] = {T(0), T(0), T(0), T(0)};
+        uint32_t idq[4] = {0u, 0u, 0u, 0u};
         if (act) {
             const int4 cc = __ldcs(reinterpret_cast<const int4*>(a.cell + slot));
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
             ld4(offp + slot, f);
-            if (MOVE && (!SUB || moves)) ld4(uxp + slot, ux);
-            if (MOVE && MAG && smag && (!SUB || moves)) {
+            if (SORT || (MOVE && (!SUB || moves))) ld4(uxp + slot, ux);
+            if (SORT || (MOVE && MAG && smag && (!SUB || moves))) {
                 ld4(uyp + slot, uy);
                 ld4(uzp + slot, uz);
             }
+            if (SORT) {
+                const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(a.id + slot));
+                idq[0] = ii.x; idq[1] = ii.y; idq[2] = ii.z; idq[3] = ii.w;
+            }
         }
+        // sort step: reserve each particle's slot by its cell at the start of the step
+        // (equal cells of a quad position grouped across the warp, one counter update per
+        // group); the reservations are waited for only after the move
+        unsigned grp[4] = {0u, 0u, 0u, 0u}, rbase[4] = {0u, 0u, 0u, 0u}, had = 0u;
+        if (SORT) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int key = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
+                grp[k] = __match_any_sync(0xffffffffu, key);
+                if (c[k] >= 0) had |= 1u << k;
+                if (c[k] >= 0 && lane == __ffs(grp[k]) - 1)
+                    rbase[k] = atomicAdd(a.cursor + node0 + key, (unsigned)__popc(grp[k]));
+            }
+        }
+        int64_t to[4] = {-1, -1, -1, -1};
 
         if (MOVE && (!SUB || moves)) {
             unsigned cand = 0, wlo = 0, whi = 0;
@@ -454,7 +540,7 @@ k_move(const __grid_constant__ MoveArgs a)
                         clk = 0u;
                     } else {
                         // a test step: the id is read only here
-                        const uint32_t idk = __ldg(a.id + slot + k);
+                        const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
                         const uint4 w = draw(idk, step, kRngCollide, key0, key1);
                         const int g = min(gap_steps(P.gap, w.x), dgrid);
                         if (g == 0) {
@@ -468,7 +554,10 @@ k_move(const __grid_constant__ MoveArgs a)
                 }
                 c[k] = (int)((uint32_t)j | (clk << kClockShift));
             }
-            if (act) {
+            if (SORT) {
+                sort_destinations(a, P, grp, rbase, had, to);
+                sort_write<T>(a, to, c, f, ux, uy, uz, idq);
+            } else if (act) {
                 __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
                 st4(offp + slot, f);
                 st4(uxp + slot, ux);
@@ -487,13 +576,20 @@ k_move(const __grid_constant__ MoveArgs a)
                     if (!(ev & bit)) continue;
                     const uint32_t kind = (cand & bit) ? kRareCandidate
                                           : (wlo & bit) ? kRareWallLow : kRareWallHigh;
-                    if (e < (unsigned long long)a.rare_cap)
-                        a.rare[e] = rare_pack(slot + k, s, kind);
+                    if (SORT && to[k] < 0) {
+                        // refused destination (capacity error latched): nothing to queue
+                    } else if (e < (unsigned long long)a.rare_cap)
+                        a.rare[e] = rare_pack(SORT ? to[k] : slot + k, s, kind);
                     else
                         set_error(a.err, kErrEvents);
                     ++e;
                 }
             }
+        }
+        else if (SORT) {
+            // a segment that does not move this step (subcycling) is still sorted
+            sort_destinations(a, P, grp, rbase, had, to);
+            sort_write<T>(a, to, c, f, ux, uy, uz, idq);
         }
         // 6. deposit of the (new) positions; an empty slot (cell word < 0) gets jd = -1
         int jd[4];
@@ -503,7 +599,8 @@ k_move(const __grid_constant__ MoveArgs a)
             jd[k] = (c[k] >> 31) | (int)((uint32_t)c[k] & kCellMask);
             qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
         }
-        warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0);
+        warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0,
+                        a.hist_out ? a.hist_out + node0 : nullptr);
     }
 }
 

@@ -5,55 +5,64 @@
 namespace bitpic {
 
 namespace {
-template <int NT, bool SUB>
+template <int NT, bool SUB, bool SORT>
 cudaError_t go_sub(const MoveArgs& a, bool mag, bool mixed, int grid, cudaStream_t st)
 {
     if (!mag)
-        k_move<double, NT, false, true, SUB, false><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, false, true, SUB, false, SORT><<<grid, NT, 0, st>>>(a);
     else if (mixed)
-        k_move<double, NT, true, true, SUB, true><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, true, true, SUB, true, SORT><<<grid, NT, 0, st>>>(a);
     else
-        k_move<double, NT, true, true, SUB, false><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, true, true, SUB, false, SORT><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int NT>
-cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int grid,
+cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, bool sort, int grid,
                cudaStream_t st)
 {
     if (!move) {
-        k_move<double, NT, false, false, false, false><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, false, false, false, false, false><<<grid, NT, 0, st>>>(a);
         return cudaGetLastError();
     }
-    return sub ? go_sub<NT, true>(a, mag, mixed, grid, st) : go_sub<NT, false>(a, mag, mixed, grid, st);
+    if (sort)
+        return sub ? go_sub<NT, true, true>(a, mag, mixed, grid, st)
+                   : go_sub<NT, false, true>(a, mag, mixed, grid, st);
+    return sub ? go_sub<NT, true, false>(a, mag, mixed, grid, st)
+               : go_sub<NT, false, false>(a, mag, mixed, grid, st);
 }
 
 template <int NT>
-int occupancy(bool mag)
+int occupancy(bool mag, bool sort)
 {
     int n = 0;
-    cudaError_t e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false, false>, NT, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true, false, false>, NT, 0);
+    cudaError_t e;
+    if (sort)
+        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false, false, true>, NT, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true, false, false, true>, NT, 0);
+    else
+        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false, false, false>, NT, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true, false, false, false>, NT, 0);
     return e == cudaSuccess ? n : 0;
 }
 }  // namespace
 
-cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, int nt,
-                            int grid, cudaStream_t st)
+cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
+                            bool sort, int nt, int grid, cudaStream_t st)
 {
     switch (nt) {
-        case 128: return go<128>(a, mag, move, sub, mixed, grid, st);
-        case 512: return go<512>(a, mag, move, sub, mixed, grid, st);
-        default: return go<256>(a, mag, move, sub, mixed, grid, st);
+        case 128: return go<128>(a, mag, move, sub, mixed, sort, grid, st);
+        case 512: return go<512>(a, mag, move, sub, mixed, sort, grid, st);
+        default: return go<256>(a, mag, move, sub, mixed, sort, grid, st);
     }
 }
 
-int move_blocks_per_sm_f64(bool mag, int nt)
+int move_blocks_per_sm_f64(bool mag, bool sort, int nt)
 {
     switch (nt) {
-        case 128: return occupancy<128>(mag);
-        case 512: return occupancy<512>(mag);
-        default: return occupancy<256>(mag);
+        case 128: return occupancy<128>(mag, sort);
+        case 512: return occupancy<512>(mag, sort);
+        default: return occupancy<256>(mag, sort);
     }
 }
 

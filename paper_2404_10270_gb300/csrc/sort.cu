@@ -7,7 +7,9 @@
 // the second copy of the store, which drops the empty slots left by absorbed
 // particles.  Results of the time step do not depend on particle order (deposits
 // are integer, random draws are keyed by particle id), so the order inside a cell
-// is free.
+// is free.  Usually the histogram comes from the step before the sort and the scatter
+// is done by the sort step's mover (mover.cuh); this file then runs only the scan and
+// the finish, and the whole sort below serves the remaining cases.
 #include <algorithm>
 
 #include "kernels.h"
@@ -299,6 +301,20 @@ cudaError_t run_sort(const SortArgs& a, int sms, cudaStream_t st)
 }
 
 }  // namespace
+
+cudaError_t launch_sort_scan(const SortArgs& a, cudaStream_t st)
+{
+    const dim3 cg(a.nseg, a.cell_chunks);
+    k_cell_partial<<<cg, kCellThreads, 0, st>>>(a);
+    k_cell_scan<<<cg, kCellThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_finish(const SortArgs& a, cudaStream_t st)
+{
+    k_sort_finish<<<a.nseg, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sort(const SortArgs& a, int nt, int sms, cudaStream_t st)
 {
