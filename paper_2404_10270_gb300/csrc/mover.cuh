@@ -223,25 +223,29 @@ struct MoveOccupancy {
     static constexpr int blocks = warps / (NT / 32) > 0 ? warps / (NT / 32) : 1;
 };
 
+// The quad's four values of one array with one 128-bit access (two for double).  The
+// particle arrays are streamed (each byte is read and written once per step, and the
+// store is far larger than L2), so the accesses carry the evict-first hint and leave L2
+// to the node arrays, the deposit and the rare-event queue.
 __device__ __forceinline__ void ld4(const float* p, float v[4])
 {
-    const float4 t = *reinterpret_cast<const float4*>(p);
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 __device__ __forceinline__ void ld4(const double* p, double v[4])
 {
-    const double2 a = reinterpret_cast<const double2*>(p)[0];
-    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 __device__ __forceinline__ void st4(float* p, const float v[4])
 {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
 }
 __device__ __forceinline__ void st4(double* p, const double v[4])
 {
-    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+    __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
 }
 
 // Warp-level deposit of four particles per lane.  With Q = rint(f S) the charge of
@@ -356,7 +360,8 @@ __device__ __forceinline__ void sort_destinations(const MoveArgs& a, const SegPa
 
 // Sort step: the quad's particles into their slots of the other store copy (a particle
 // that left through a wall goes there as an empty slot with its velocity, for the event
-// kernel).
+// kernel).  Streaming stores: the next step reads the copy back from HBM anyway, and
+// evict-first lines leave L2 to the partly written lines of other warps' runs.
 template <typename T>
 __device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4], const int c[4],
                                            const T f[4], const T ux[4], const T uy[4],
@@ -370,12 +375,12 @@ __device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4
     for (int k = 0; k < 4; ++k) {
         if (to[k] < 0) continue;
         const int64_t g = to[k];
-        a.dcell[g] = c[k];
-        doff[g] = f[k];
-        dux[g] = ux[k];
-        duy[g] = uy[k];
-        duz[g] = uz[k];
-        a.did[g] = id[k];
+        __stcs(a.dcell + g, c[k]);
+        __stcs(doff + g, f[k]);
+        __stcs(dux + g, ux[k]);
+        __stcs(duy + g, uy[k]);
+        __stcs(duz + g, uz[k]);
+        __stcs(a.did + g, id[k]);
     }
 }
 

@@ -301,11 +301,12 @@ def test_invalid_load_is_reported_then_state_is_sticky():
     sim.close()
 
 
-def test_capacity_overflow_is_reported():
+@pytest.mark.parametrize("sort", [0, 3])
+def test_capacity_overflow_is_reported(sort):
     ensure_built()
     phys = W.magnetized_source(ncells=16, ppc=20, nu=5.0, capacity_factor=1.0)
     loads = W.initial_load(phys)
-    sim = capi.Sim(phys, precision=capi.FP32)
+    sim = capi.Sim(phys, precision=capi.FP32, sort_interval=sort)
     sim.load_all(loads)
     sim.step(40)
     with pytest.raises(capi.PicError) as e:
@@ -322,12 +323,14 @@ def _wall_flood(n_per_cell):
                      field=W.FIELD_NONE, seed=5)
 
 
-def test_wall_flood_within_the_queue_matches_oracle():
-    # 60,000 particles: within the queue's 65,536-entry floor
+@pytest.mark.parametrize("sort", [0, 2])
+def test_wall_flood_within_the_queue_matches_oracle(sort):
+    # 60,000 particles: within the queue's 65,536-entry floor; with sort interval 2 the
+    # second step is a sort step
     ensure_built()
     phys = _wall_flood(15000)
     loads = W.initial_load(phys, seed=5)
-    g, gm = run_gpu(phys, loads, 2, capi.FP64)
+    g, gm = run_gpu(phys, loads, 2, capi.FP64, sort_interval=sort)
     o, om = run_oracle(phys, loads, 2)
     np.testing.assert_array_equal(gm["live"], om["live"])
     np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
