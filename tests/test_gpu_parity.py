@@ -315,6 +315,29 @@ def test_capacity_overflow_is_reported(sort):
     sim.close()
 
 
+def test_fp64_move_rounds_exactly_like_the_oracle():
+    """With no field and no collisions the FP64 step is the move alone: f' = f + u and
+    f' - floor(f').  For -1 < f' < 2 the GPU reads the floor from the bits and forms
+    f' - floor(f') as one addition of 0 or +-1; that must round exactly as the
+    subtraction does, so after many crossings in both directions, landings close to a
+    cell edge and moves of more than a cell, every position is the oracle's bit for
+    bit."""
+    ensure_built()
+    n = 400
+    sp = [W.Species("e", -1.0, 1.0, 0.5 / n, 30.0, n)]  # |u| ~ 0.55 cells per step
+    phys = W.Physics(ncells=64, dx=0.5, dt=0.05, species=sp, processes=[],
+                     bc=W.BC_PERIODIC, field=W.FIELD_NONE, seed=11)
+    loads = W.initial_load(phys, seed=11)
+    g, _ = run_gpu(phys, loads, 60, capi.FP64, sort_interval=7)
+    o, _ = run_oracle(phys, loads, 60)
+    g, o = by_id(g[0]), by_id(o[0])
+    np.testing.assert_array_equal(g["id"], o["id"])
+    np.testing.assert_array_equal(g["cell"], o["cell"])
+    np.testing.assert_array_equal(g["off"].view(np.uint64), o["off"].view(np.uint64))
+    np.testing.assert_array_equal(g["vx"], o["vx"])
+    assert (np.abs(loads[0].vx) * phys.dt / phys.dx > 1).any()  # some move past a cell
+
+
 def _wall_flood(n_per_cell):
     """Four cells, one species so hot (|u| ~ 100 cells/step) that nearly every particle
     reaches a wall in the first step: the rare-event queue takes one entry per particle."""
