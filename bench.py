@@ -401,12 +401,12 @@ def measure_small(args, stream):
 
 def run_c5(args):
     """The memory-filling ensemble sweep: the batched ensemble scaled to ~150 GB of FP64
-    particle state (two copies, 1.5x capacity), run in the FP64 and the FP32 form; for 16
-    sampled instances the density, potential and wall-flux errors against the oracle."""
+    particle state (two copies, 1.5x capacity), run in the FP64 and the FP32 form.  Its
+    cpu_baseline leg steps 16 sampled instances with the oracle (timed on one host core),
+    and both forms' density, potential and wall-flux errors are taken against those runs."""
     import concurrent.futures as cf
     import torch
     from paper_2404_10270_gb300 import capi
-    from oracle.oracle import Oracle
     __import__("__graft_entry__").build()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -419,6 +419,9 @@ def run_c5(args):
         n = sum(len(x) for ld in loads for x in ld)
         sample = list(range(0, n_inst, max(1, n_inst // 16)))[:16]
         res = {"instances": n_inst, "particles": n, "sampled": sample}
+        # measure_form runs the warm-up, the timed steps, then as many profiled steps
+        total = args.warmup + 2 * args.steps
+        gpu_moments = {}
         # magnetized movers move cell word, offset and three velocities each way:
         # 2 x (4 + 8 + 24) B in FP64, 2 x (4 + 4 + 12) B in FP32
         for name, prec, bpp in (("fp64", capi.FP64, 72), ("fp32", capi.FP32, 40)):
@@ -428,25 +431,10 @@ def run_c5(args):
                 sim.load_all(ld, inst=i)
             r = measure_form(sim, phys, args.steps, args.warmup, n,
                              "f64" if prec == capi.FP64 else "f32", 0, 1, 0, bytes_per_particle=bpp)
-            # measure_form runs the warm-up, the timed steps, then as many profiled steps
-            total = args.warmup + 2 * args.steps
-            errs = []
-            for i in sample:
-                g = sim.moments(i)
-                o = Oracle(phys[i])
-                o.load_all(loads[i])
-                o.step(total)
-                om = o.moments()
-                dscale = np.abs(om["density"]).max()
-                pscale = max(np.abs(om["phi"]).max(), 1e-300)
-                errs.append({"inst": i,
-                             "density": float(np.abs(g["density"] - om["density"]).max() / dscale),
-                             "phi": float(np.abs(g["phi"] - om["phi"]).max() / pscale),
-                             "wall_flux": int(np.abs(g["wall_count"] - om["wall_count"]).sum()),
-                             "live": int(np.abs(g["live"] - om["live"]).sum())})
+            gpu_moments[name] = {i: sim.moments(i) for i in sample}
             sim.close()
             res[name] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
-                         "roofline": r["roofline"], "errors_vs_oracle_after_%d_steps" % total: errs}
+                         "roofline": r["roofline"]}
             if prec == capi.FP64:
                 # the FP64 Boris form is bound by the FP64 pipe
                 live = sum(r["live"]) / 2
@@ -455,8 +443,45 @@ def run_c5(args):
                     "bound": "alu", "achieved": ach, "peak": FP64_PEAK_INSTR_PER_S,
                     "unit": "FP64 instr/s", "frac": ach / FP64_PEAK_INSTR_PER_S,
                     "ops_per_particle": FP64_OPS_PER_PARTICLE_BORIS}
+        # cpu_baseline leg: the oracle steps the sampled instances as far as the GPU runs
+        # went; its moments are the reference for both forms' errors
+        ora, psteps, t_cpu = cpu_oracle_instances([phys[i] for i in sample],
+                                                  [loads[i] for i in sample], total)
+        res["cpu_baseline"] = {"value": psteps / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "FP64 CPU oracle, %d time steps of the %d sampled instances "
+                                         "(%.3g particle-steps, %.1f s)" % (total, len(sample), psteps, t_cpu)}
+        for name in ("fp64", "fp32"):
+            errs = []
+            for i, om in zip(sample, ora):
+                g = gpu_moments[name][i]
+                dscale = np.abs(om["density"]).max()
+                pscale = max(np.abs(om["phi"]).max(), 1e-300)
+                errs.append({"inst": i,
+                             "density": float(np.abs(g["density"] - om["density"]).max() / dscale),
+                             "phi": float(np.abs(g["phi"] - om["phi"]).max() / pscale),
+                             "wall_flux": int(np.abs(g["wall_count"] - om["wall_count"]).sum()),
+                             "live": int(np.abs(g["live"] - om["live"]).sum())})
+            res[name]["errors_vs_oracle_after_%d_steps" % total] = errs
         print(json.dumps({"c5": res}), flush=True)
     return 0
+
+
+def cpu_oracle_instances(physs, loads, steps):
+    """cpu_baseline leg of the ensemble sweep: the FP64 CPU oracle steps each instance
+    (one host core); returns their moments, the particle-steps done and the seconds."""
+    from oracle.oracle import Oracle
+    out, psteps, t = [], 0, 0.0
+    for ph, ld in zip(physs, loads):
+        o = Oracle(ph)
+        o.load_all(ld)
+        n0 = sum(len(x.id) for x in ld)
+        t0 = time.perf_counter()
+        o.step(steps)
+        t += time.perf_counter() - t0
+        m = o.moments()
+        psteps += (n0 + int(np.sum(m["live"]))) / 2 * steps
+        out.append(m)
+    return out, psteps, t
 
 
 def _e2e_pass(sim, host, outs, phys, args, world):
