@@ -107,10 +107,10 @@ struct InstParams {
     double tratio;
 };
 
-// A particle the mover leaves to the event kernel (a null-collision candidate or a
-// wall hit), packed in 64 bits: kind in bits 0-1, segment in bits 2-23, store slot
-// in bits 24-63.
-enum : uint32_t { kRareCandidate = 0, kRareWallLow = 1, kRareWallHigh = 2 };
+// A particle the mover leaves to the event kernel (a null-collision candidate, a wall
+// hit, or a collision-clock test that the mover variant without the test left over),
+// packed in 64 bits: kind in bits 0-1, segment in bits 2-23, store slot in bits 24-63.
+enum : uint32_t { kRareCandidate = 0, kRareWallLow = 1, kRareWallHigh = 2, kRareTest = 3 };
 constexpr int kRareSegBits = 22;
 constexpr int kMaxSegments = 1 << kRareSegBits;
 __host__ __device__ __forceinline__ uint64_t rare_pack(int64_t slot, int seg, uint32_t kind)

@@ -1,8 +1,9 @@
 // events.cuh -- the rare events of a time step, worked through after the mover:
 // null-collision candidates (Section 2: the MCC step of the PIC cycle; elastic,
-// charge-exchange and ionization kinematics) and particles that left through an
-// absorbing or source wall (flux and energy counters, re-injection of the volume
-// source).  The mover queues them (rare_pack) so that its own loop stays call-free;
+// charge-exchange and ionization kinematics), collision-clock tests that the mover
+// variant without the inline test left (a candidate of this same step when the draw says
+// so) and particles that left through an absorbing or source wall (flux and energy
+// counters, re-injection of the volume source).  The mover queues them (rare_pack) so that its own loop stays call-free;
 // here one thread takes one queued particle.  Collisions change only velocities, so
 // the mover has already deposited a candidate; a re-injected particle and the
 // children of an ionization are deposited here (and, on the step before a sort,
@@ -225,6 +226,9 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
 {
     const unsigned long long n = min(*a.rare_count, (unsigned long long)a.rare_cap);
     const int64_t step = *a.step;
+    // the movers of this step have read it: from the next step on, clocks that need a
+    // test off the common test steps are queued again
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.test_all) *a.test_all = 0;
     T* const offp = static_cast<T*>(a.off);
     T* const uxp = static_cast<T*>(a.ux);
     T* const uyp = static_cast<T*>(a.uy);
@@ -242,18 +246,44 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
             const int64_t slot = (int64_t)(e >> 24);
             const SegParams& P = a.seg[s];
             const uint32_t id = a.id[slot];
-            T f = offp[slot], vx = uxp[slot], vy = uyp[slot], vz = uzp[slot];
-            if (kind == kRareCandidate) {
+            // a clock test needs only the id and the cell word; the state is read when the
+            // particle collides or left through a wall
+            T f = T(0), vx = T(0), vy = T(0), vz = T(0);
+            if (kind == kRareCandidate || kind == kRareTest) {
                 const int j = (int)((uint32_t)a.cell[slot] & kCellMask);
                 const uint4 wd = draw(id, step, kRngCollide, P.key0, P.key1);
-                const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y, wd.z);
-                if (p >= 0) {
-                    uxp[slot] = vx;
-                    uyp[slot] = vy;
-                    uzp[slot] = vz;
-                    ckey = P.inst * kMaxProc + p;
+                bool now = kind == kRareCandidate;
+                if (!now) {
+                    // the clock test the mover left: word 0 gives the candidate-free run
+                    // from this step, cut at the species' next multiple of kGapMax steps
+                    const int ks = P.nstep;
+                    const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
+                    const int dgrid = kGapMax - (int)((q - 1) % kGapMax);
+                    const int g = min(gap_steps(P.gap, wd.x), dgrid);
+                    now = g == 0;
+                    const uint32_t clk = g == 0 ? 0u
+                                         : g < dgrid ? ((uint32_t)(g - 1) | kClockPending)
+                                                     : (uint32_t)(dgrid - 1);
+                    a.cell[slot] = (int)((uint32_t)j | (clk << kClockShift));
+                }
+                if (now) {
+                    f = offp[slot];
+                    vx = uxp[slot];
+                    vy = uyp[slot];
+                    vz = uzp[slot];
+                    const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y, wd.z);
+                    if (p >= 0) {
+                        uxp[slot] = vx;
+                        uyp[slot] = vy;
+                        uzp[slot] = vz;
+                        ckey = P.inst * kMaxProc + p;
+                    }
                 }
             } else {
+                f = offp[slot];
+                vx = uxp[slot];
+                vy = uyp[slot];
+                vz = uzp[slot];
                 int j = kind == kRareWallLow ? -1 : P.ncells;
                 wkey = 2 * s + (kind == kRareWallLow ? 0 : 1);
                 if (wall_event<T>(a, P, s, id, step, j, f, vx, vy, vz) == 1) {

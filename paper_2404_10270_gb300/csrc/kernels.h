@@ -13,13 +13,15 @@ struct MoveArgs;
 // `move` = false deposits the loaded particles without moving them (the density
 // phase of the initial field); `sub`: some species is subcycled; `mixed`: magnetized and
 // unmagnetized instances in one batch; `sort`: the step also sorts the store by cell
-// into the other copy (MoveArgs.cursor, .d*).  Returns the launch error.
+// into the other copy (MoveArgs.cursor, .d*); `lean` (FP32, a plain step of a batch
+// without subcycling or magnetic field): the variant that queues collision-clock tests
+// for the event kernel instead of drawing them inline.  Returns the launch error.
 cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
-                            bool sort, int nt, int grid, cudaStream_t st);
+                            bool sort, bool lean, int nt, int grid, cudaStream_t st);
 cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
                             bool sort, int nt, int grid, cudaStream_t st);
-// The rare events the mover queued this step (events.cu): collision candidates and
-// wall hits, one thread each, `grid` blocks of 128 threads.
+// The rare events the mover queued this step (events.cu): collision candidates, clock
+// tests and wall hits, one thread each, `grid` blocks of 128 threads.
 cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // Ionizations against neutral particle targets: convert the requested targets into
 // ions (events.cu); one thread per segment node, `nnodes` nodes in all.

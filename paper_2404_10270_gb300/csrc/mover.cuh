@@ -89,6 +89,14 @@ struct MoveArgs {
     // scanned counts, by the cell at the start of the step) and writes it there
     unsigned* hist_out;
     unsigned* cursor;
+    // the collision-clock test: on the steps that are multiples of kGapMax every clock
+    // without a candidate tests, and after a load (`test_all` set) any clock may.  With
+    // `pair` set both variants are launched for the step: the one with the test inline
+    // runs on those steps, the one that queues the few other tests for the event kernel
+    // on the rest, and each returns at once on the steps that are not its own (0: the
+    // variant launched runs).
+    int* test_all;
+    int pair;
     int32_t* dcell;
     void* doff;
     void* dux;
@@ -396,7 +404,10 @@ __device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4
 // step that ends a sort cycle; every particle goes to its slot of the other store copy
 // (reserved from `cursor` by its cell at the start of the step, the order of a counting
 // sort) instead of back to its own.
-template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool SORT>
+// TEST: the collision-clock test (a Philox draw and a table search) runs inline;
+// without it a particle whose clock needs a test is queued for the event kernel, which
+// keeps the common path free of the draw's code and registers.
+template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool SORT, bool TEST>
 __global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG || SORT, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
@@ -409,6 +420,11 @@ k_move(const __grid_constant__ MoveArgs a)
     T* const uzp = static_cast<T*>(a.uz);
     const T2* const accp = static_cast<const T2*>(a.accel);
     const int64_t step = MOVE ? *a.step : 0;
+    if (MOVE && !SORT && !SUB && a.pair) {
+        // every clock without a candidate tests on the multiples of kGapMax
+        const bool tstep = step % kGapMax == 0 || *a.test_all != 0;
+        if (tstep != TEST) return;
+    }
     const int64_t total = a.tile_start[a.nseg];
     const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
     int s = 0;                         // segment of the previous tile (tiles only increase)
@@ -483,7 +499,7 @@ k_move(const __grid_constant__ MoveArgs a)
         int64_t to[4] = {-1, -1, -1, -1};
 
         if (MOVE && (!SUB || moves)) {
-            unsigned cand = 0, wlo = 0, whi = 0;
+            unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (c[k] < 0) continue;
@@ -543,6 +559,11 @@ k_move(const __grid_constant__ MoveArgs a)
                     } else if (clk & kClockPending) {
                         cand |= 1u << k;
                         clk = 0u;
+                    } else if (!TEST) {
+                        // a test off the common test steps (the clock of a particle that
+                        // was a candidate, was loaded or was created in the last step):
+                        // the event kernel draws it, with this step's counter
+                        tst |= 1u << k;
                     } else {
                         // a test step: the id is read only here
                         const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
@@ -572,7 +593,7 @@ k_move(const __grid_constant__ MoveArgs a)
                 }
             }
             // queue the quad's rare events (a few lanes of a few tiles per step)
-            const unsigned ev = cand | wlo | whi;
+            const unsigned ev = cand | wlo | whi | tst;
             if (ev) {
                 unsigned long long e = atomicAdd(a.rare_count, (unsigned long long)__popc(ev));
 #pragma unroll
@@ -580,6 +601,7 @@ k_move(const __grid_constant__ MoveArgs a)
                     const unsigned bit = 1u << k;
                     if (!(ev & bit)) continue;
                     const uint32_t kind = (cand & bit) ? kRareCandidate
+                                          : (tst & bit) ? kRareTest
                                           : (wlo & bit) ? kRareWallLow : kRareWallHigh;
                     if (SORT && to[k] < 0) {
                         // refused destination (capacity error latched): nothing to queue

@@ -5,31 +5,35 @@
 namespace bitpic {
 
 namespace {
-template <int NT, bool SUB, bool SORT>
+template <int NT, bool SUB, bool SORT, bool TEST>
 cudaError_t go_sub(const MoveArgs& a, bool mag, bool mixed, int grid, cudaStream_t st)
 {
     if (!mag)
-        k_move<float, NT, false, true, SUB, false, SORT><<<grid, NT, 0, st>>>(a);
+        k_move<float, NT, false, true, SUB, false, SORT, TEST><<<grid, NT, 0, st>>>(a);
     else if (mixed)
-        k_move<float, NT, true, true, SUB, true, SORT><<<grid, NT, 0, st>>>(a);
+        k_move<float, NT, true, true, SUB, true, SORT, TEST><<<grid, NT, 0, st>>>(a);
     else
-        k_move<float, NT, true, true, SUB, false, SORT><<<grid, NT, 0, st>>>(a);
+        k_move<float, NT, true, true, SUB, false, SORT, TEST><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int NT>
-cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, bool sort, int grid,
-               cudaStream_t st)
+cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, bool sort,
+               bool lean, int grid, cudaStream_t st)
 {
     if (!move) {
-        k_move<float, NT, false, false, false, false, false><<<grid, NT, 0, st>>>(a);
+        k_move<float, NT, false, false, false, false, false, true><<<grid, NT, 0, st>>>(a);
         return cudaGetLastError();
     }
     if (sort)
-        return sub ? go_sub<NT, true, true>(a, mag, mixed, grid, st)
-                   : go_sub<NT, false, true>(a, mag, mixed, grid, st);
-    return sub ? go_sub<NT, true, false>(a, mag, mixed, grid, st)
-               : go_sub<NT, false, false>(a, mag, mixed, grid, st);
+        return sub ? go_sub<NT, true, true, true>(a, mag, mixed, grid, st)
+                   : go_sub<NT, false, true, true>(a, mag, mixed, grid, st);
+    if (sub) return go_sub<NT, true, false, true>(a, mag, mixed, grid, st);
+    if (lean && !mag) {
+        k_move<float, NT, false, true, false, false, false, false><<<grid, NT, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    return go_sub<NT, false, false, true>(a, mag, mixed, grid, st);
 }
 
 template <int NT>
@@ -38,22 +42,22 @@ int occupancy(bool mag, bool sort)
     int n = 0;
     cudaError_t e;
     if (sort)
-        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true, false, false, true>, NT, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false, false, true>, NT, 0);
+        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true, false, false, true, true>, NT, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false, false, true, true>, NT, 0);
     else
-        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true, false, false, false>, NT, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false, false, false>, NT, 0);
+        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true, false, false, false, true>, NT, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false, false, false, true>, NT, 0);
     return e == cudaSuccess ? n : 0;
 }
 }  // namespace
 
 cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
-                            bool sort, int nt, int grid, cudaStream_t st)
+                            bool sort, bool lean, int nt, int grid, cudaStream_t st)
 {
     switch (nt) {
-        case 128: return go<128>(a, mag, move, sub, mixed, sort, grid, st);
-        case 512: return go<512>(a, mag, move, sub, mixed, sort, grid, st);
-        default: return go<256>(a, mag, move, sub, mixed, sort, grid, st);
+        case 128: return go<128>(a, mag, move, sub, mixed, sort, lean, grid, st);
+        case 512: return go<512>(a, mag, move, sub, mixed, sort, lean, grid, st);
+        default: return go<256>(a, mag, move, sub, mixed, sort, lean, grid, st);
     }
 }
 
