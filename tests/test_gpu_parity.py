@@ -338,6 +338,46 @@ def test_fp64_move_rounds_exactly_like_the_oracle():
     assert (np.abs(loads[0].vx) * phys.dt / phys.dx > 1).any()  # some move past a cell
 
 
+def test_mover_pair_changes_no_result(monkeypatch):
+    """Plain FP32 steps of large batches use the mover pair: on the clock-test steps
+    (multiples of 127) and after a load the variant with the collision-clock draw
+    inline, on the others the variant that queues the few clocks needing a draw for the
+    event kernel.  Both orders of work give the same state, bit for bit: over 260 steps
+    (two clock-test steps, graph-replayed sort cycles) and a reload of the state."""
+    ensure_built()
+    phys = W.bounded_small(ncells=200, ppc=60, seed=4)
+    loads = W.initial_load(phys, seed=4)
+
+    def run(min_slots):
+        monkeypatch.setenv("BITPIC_PAIR_MIN_SLOTS", str(min_slots))
+        a = capi.Sim(phys, precision=capi.FP32, sort_interval=20)
+        a.load_all(loads)
+        a.step(150)
+        snap = [a.particles(0, s, cell_units=True) for s in range(2)]
+        m = a.moments(0)
+        a.close()
+        b = capi.Sim(phys, precision=capi.FP32, sort_interval=20)
+        for s, p in enumerate(snap):
+            b.load(0, s, W.Load(p["cell"], p["off"], p["vx"], p["vy"], p["vz"], p["id"],
+                                p["state"]), cell_units=True)
+        b.restore_counters(m["step"], [m["next_id"]])
+        b.step(110)
+        out = [by_id(b.particles(0, s, cell_units=True)) for s in range(2)]
+        mm = b.moments(0)
+        b.close()
+        return out, mm
+
+    a, ma = run(0)
+    b, mb = run(1 << 62)
+    for x, y in zip(a, b):
+        assert set(x) == set(y)
+        for k in x:
+            np.testing.assert_array_equal(x[k], y[k], err_msg=k)
+    for k in ("wall_count", "collisions", "live", "density", "E"):
+        np.testing.assert_array_equal(ma[k], mb[k], err_msg=k)
+    assert ma["collisions"].sum() > 0
+
+
 def _wall_flood(n_per_cell):
     """Four cells, one species so hot (|u| ~ 100 cells/step) that nearly every particle
     reaches a wall in the first step: the rare-event queue takes one entry per particle."""
