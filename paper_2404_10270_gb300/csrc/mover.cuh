@@ -189,12 +189,12 @@ template <> struct Prec<double> {
         return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000;
     }
     // The same move as the float form with the same rounding: f' - floor(f') and the
-    // truncation.  For the common -1 < f' < 2 the floor is read from the bits and
-    // f' - floor(f') is the one IEEE addition f' + c, c = +0, +1 or -1 (identical to
-    // the subtraction of 0, -1 or 1), for every lane alike: the FP64 pipe, this
-    // form's limit, sees one instruction whatever the warp's particles do.  A result
-    // that rounds up to 1 (f' a tiny negative number) is renormalised to the next
-    // cell from its bits.
+    // truncation.  For the common -1 < f' < 2 the floor is read from the bits, and only
+    // a particle that crossed a cell edge needs f' - floor(f'): the one IEEE addition
+    // f' + c, c = +1 or -1 (identical to the subtraction of -1 or 1).  The FP64 pipe is
+    // this form's limit, so the addition sits in a branch that a warp takes only when
+    // one of its particles crossed (most ion warps do not).  A result that rounds up to
+    // 1 (f' a tiny negative number) is renormalised to the next cell from its bits.
     static __device__ __forceinline__ void move(double& f, double u, int& j)
     {
         const double xn = f + u;
@@ -203,12 +203,14 @@ template <> struct Prec<double> {
         if (__builtin_expect(e < 1023 || (e == 1023 && hi >= 0), 1)) {
             const bool neg = hi < 0;   // -1 < f' < 0, or f' = -0
             const bool up = e == 1023; // 1 <= f' < 2
-            const double c = __hiloint2double(neg ? 0x3FF00000 : (up ? (int)0xBFF00000u : 0), 0);
-            double fk = xn + c;
-            j += neg ? -1 : (up ? 1 : 0);
-            if (__double2hiint(fk) == 0x3FF00000) {  // fk in [0, 1]: this is fk == 1
-                fk = 0.0;
-                j += 1;
+            double fk = xn;            // 0 <= f' < 1: f' itself
+            if (__builtin_expect(neg || up, 0)) {
+                fk = xn + __hiloint2double(neg ? 0x3FF00000 : (int)0xBFF00000u, 0);
+                j += neg ? -1 : 1;
+                if (__double2hiint(fk) == 0x3FF00000) {  // fk in [0, 1]: this is fk == 1
+                    fk = 0.0;
+                    j += 1;
+                }
             }
             f = fk;
             return;
