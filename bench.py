@@ -38,15 +38,16 @@ UNIT = "particle-steps/s"
 # cell word (4) off (8) vx (8) in FP64.  The id is read only at collision-clock events
 # (about one step in 127) and vy/vz only on collisions and wall hits.
 MOVER_BYTES = {"f32": 24, "f64": 40}
-# The FP64 form is bound by the FP64 pipe: per particle-step its hot path issues 4 FP64
-# instructions (gather: one fused multiply-add on the node pair; push: one add; move:
-# f + u, and the one add that takes f' - floor(f') with the floor read from the bits).
+# FP64 work of the FP64 form per particle-step: gather, one fused multiply-add on the
+# node pair; push, one add; move, f + u.  (The add that takes f' - floor(f') is needed
+# only by a particle that crossed a cell edge, a few per cent of them: not counted.)
 # Peak: 2 FP64 instructions per SM per cycle (ncu's peak_sustained of the dfma pipe on
-# this GPU) x 152 SMs x 2.07 GHz.
-FP64_OPS_PER_PARTICLE = 4
+# this GPU) x 152 SMs x 2.07 GHz.  The form is reported against whichever of the FP64
+# pipe and HBM it uses the larger fraction of.
+FP64_OPS_PER_PARTICLE = 3
 # With B != 0 (Boris): gather 1, half step 1, v + a/2 1, the two cross-product updates
-# 6 x 2 fused multiply-adds, the last half step 1, the move 2.
-FP64_OPS_PER_PARTICLE_BORIS = 18
+# 6 x 2 fused multiply-adds, the last half step 1, the move 1.
+FP64_OPS_PER_PARTICLE_BORIS = 17
 FP64_PEAK_INSTR_PER_S = 2 * 152 * 2.07e9
 
 
@@ -255,17 +256,16 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
     avg_mover_ms = mover_ms / max(mover_n, 1)
     achieved = per_launch_bytes / (avg_mover_ms * 1e-3) / 1e9
     traffic = profiled_traffic("k_move", precision_name) if bytes_per_particle is None else None
+    roof = None
     if precision_name == "f64" and bytes_per_particle is None:
         ach = FP64_OPS_PER_PARTICLE * (live0 + live1) / 2 / (avg_mover_ms * 1e-3)
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_INSTR_PER_S,
-                "unit": "FP64 instr/s", "frac": ach / FP64_PEAK_INSTR_PER_S,
-                "peak_source": "derived: 2 FP64 instr/SM/cycle x 152 SMs x 2.07 GHz",
-                "kernel": "k_move<double>", "ops_per_particle": FP64_OPS_PER_PARTICLE,
-                "avg_launch_ms": avg_mover_ms,
-                "hbm": {"achieved_GBps": achieved, "frac_of_measured": achieved / hbm,
-                        "bytes_per_particle": MOVER_BYTES[precision_name]}}
-    else:
-        roof = None
+        pipe = {"achieved": ach, "peak": FP64_PEAK_INSTR_PER_S, "unit": "FP64 instr/s",
+                "frac": ach / FP64_PEAK_INSTR_PER_S, "ops_per_particle": FP64_OPS_PER_PARTICLE,
+                "peak_source": "derived: 2 FP64 instr/SM/cycle x 152 SMs x 2.07 GHz"}
+        if pipe["frac"] > achieved / hbm:
+            roof = dict(bound="alu", **pipe, kernel="k_move<double>", avg_launch_ms=avg_mover_ms,
+                        hbm={"achieved_GBps": achieved, "frac_of_measured": achieved / hbm,
+                             "bytes_per_particle": MOVER_BYTES[precision_name]})
     return {
         "value": psteps / (ms_max * 1e-3),
         "ms_per_step": ms_max / steps,
@@ -275,7 +275,9 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
                      "traffic": None if traffic is None else traffic * (live0 + live1) / 2,
                      "kernel": "k_move<%s>" % ("float" if precision_name == "f32" else "double"),
                      "bytes_per_particle": bpp,
-                     "avg_launch_ms": avg_mover_ms},
+                     "avg_launch_ms": avg_mover_ms,
+                     **({"fp64_pipe": pipe} if precision_name == "f64" and bytes_per_particle is None
+                        else {})},
         "kernel_ms": {"mover": mover_ms, "field": field_ms, "sort": sort_ms, "other": other_ms,
                       "sorting_mover": smove_ms, "mover_launches": mover_n,
                       "sorting_mover_launches": smove_n, "sort_launch_groups": sort_n,
