@@ -894,14 +894,18 @@ int pic_create(const pic_config* cfg, pic_handle** out)
             slot += P.cap;
             snode += round_up(I.ncells + 1, 4);
             h->max_cap = std::max(h->max_cap, P.cap);
-            // rare-event queue: the collision candidates of a step (about cap x P;
-            // 4x that is reserved) and the wall hits (a sixteenth of the segment)
+            // rare-event queue: the collision candidates of a step and the clock tests
+            // that follow them and ionization (about cap x P each; 4x P is reserved),
+            // and the wall hits (a sixteenth of the segment; twice that with a volume
+            // source, whose re-injected particles may have their clock tests queued on
+            // the next step)
             {
                 double numax = 0.0;
                 for (int q = 0; q < I.nproc; ++q)
                     if (I.proc[q].species == s) numax += I.proc[q].nu;
                 const double Pc = -std::expm1(-numax * I.dt * species_nstep(I, s));
-                const double frac = std::min(1.0, 4.0 * Pc + (I.bc == PIC_BC_PERIODIC ? 0.0 : 1.0 / 16.0));
+                const double wall = I.bc == PIC_BC_PERIODIC ? 0.0 : (I.bc == PIC_BC_SOURCE ? 2.0 : 1.0) / 16.0;
+                const double frac = std::min(1.0, 4.0 * Pc + wall);
                 h->rare_cap += (int64_t)std::ceil((double)P.cap * frac);
             }
             h->segh.push_back(P);
