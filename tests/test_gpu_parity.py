@@ -34,6 +34,64 @@ def test_philox_known_answers_and_oracle():
         np.testing.assert_array_equal(got[i], ophilox(ctr[i], kw))
 
 
+_CURAND_PHILOX = r"""
+#include <cstdint>
+#include <curand_kernel.h>
+__global__ void k_ref(const uint4* c, const uint2* k, uint4* o, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = curand_Philox4x32_10(c[i], k[i]);
+}
+extern "C" int curand_philox(const uint32_t* c, const uint32_t* k, uint32_t* o, int n)
+{
+    uint4 *dc = nullptr, *dout = nullptr;
+    uint2* dk = nullptr;
+    cudaError_t e = cudaMalloc(&dc, 16 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dk, 8 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 16 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, c, 16 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, k, 8 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_ref<<<(n + 127) / 128, 128>>>(dc, dk, dout, n);
+        e = cudaMemcpy(o, dout, 16 * (size_t)n, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(dc);
+    cudaFree(dk);
+    cudaFree(dout);
+    return (int)e;
+}
+"""
+
+
+def test_oracle_philox_matches_curand(tmp_path):
+    """The oracle's Philox4x32-10 against the CUDA toolkit's own (cuRAND's device
+    function, called on random counters and keys): an independent implementation of
+    the published generator.  The GPU path is checked against the oracle above."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    from oracle.oracle import philox as ophilox
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    src = tmp_path / "curand_philox.cu"
+    src.write_text(_CURAND_PHILOX)
+    so = tmp_path / "libcurand_philox.so"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-Xcompiler",
+                    "-fPIC", "-o", str(so), str(src)], check=True, capture_output=True)
+    lib = C.CDLL(str(so))
+    rng = np.random.default_rng(7)
+    n = 4096
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0], key[0] = 0, 0
+    ctr[1], key[1] = 0xFFFFFFFF, 0xFFFFFFFF
+    out = np.zeros((n, 4), np.uint32)
+    P = C.POINTER(C.c_uint32)
+    rc = lib.curand_philox(ctr.ctypes.data_as(P), key.ctypes.data_as(P), out.ctypes.data_as(P), n)
+    assert rc == 0
+    for i in list(range(0, n, 37)) + [0, 1]:
+        np.testing.assert_array_equal(ophilox(ctr[i], key[i]), out[i])
+
+
 @pytest.mark.parametrize("precision,steps,tol", [(capi.FP64, 100, 1e-12), (capi.FP32, 10, 1e-5)])
 def test_bounded_small_parity(precision, steps, tol):
     phys = W.bounded_small()
@@ -249,8 +307,11 @@ def test_checkpoint_restart_is_bit_identical(precision):
             np.testing.assert_array_equal(x[k], y[k])
 
 
-def test_magnetized_source_fp32_parity():
-    phys = W.magnetized_source(ncells=64, ppc=40, seed=4, nu=0.2, capacity_factor=3.0)
+@pytest.mark.parametrize("B", [2.0, 0.0])
+def test_magnetized_source_fp32_parity(B):
+    # B = 0: the plain push, and in a batch large enough (or with the tests' setting) the
+    # mover pair, whose queued clock tests include re-injected particles and products
+    phys = W.magnetized_source(ncells=64, ppc=40, seed=4, nu=0.2, capacity_factor=3.0, B=B)
     loads = W.initial_load(phys, seed=4)
     g, gm = run_gpu(phys, loads, 10, capi.FP32, sort_interval=5)
     o, om = run_oracle(phys, loads, 10)
@@ -338,14 +399,20 @@ def test_fp64_move_rounds_exactly_like_the_oracle():
     assert (np.abs(loads[0].vx) * phys.dt / phys.dx > 1).any()  # some move past a cell
 
 
-def test_mover_pair_changes_no_result(monkeypatch):
+@pytest.mark.parametrize("case", ["bounded", "source"])
+def test_mover_pair_changes_no_result(monkeypatch, case):
     """Plain FP32 steps of large batches use the mover pair: on the clock-test steps
     (multiples of 127) and after a load the variant with the collision-clock draw
     inline, on the others the variant that queues the few clocks needing a draw for the
-    event kernel.  Both orders of work give the same state, bit for bit: over 260 steps
-    (two clock-test steps, graph-replayed sort cycles) and a reload of the state."""
+    event kernel (after a candidate, and for re-injected particles and ionization
+    products, which start with a fresh clock).  Both orders of work give the same
+    state, bit for bit: over 260 steps (two clock-test steps, graph-replayed sort
+    cycles) and a reload of the state."""
     ensure_built()
-    phys = W.bounded_small(ncells=200, ppc=60, seed=4)
+    if case == "bounded":
+        phys = W.bounded_small(ncells=200, ppc=60, seed=4)
+    else:  # volume source and ionization without magnetic field
+        phys = W.magnetized_source(ncells=64, ppc=60, seed=4, B=0.0, nu=0.05, capacity_factor=3.0)
     loads = W.initial_load(phys, seed=4)
 
     def run(min_slots):
