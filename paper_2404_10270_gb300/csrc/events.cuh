@@ -1,15 +1,15 @@
 // events.cuh -- the rare events of a time step, worked through after the mover:
 // null-collision candidates (Section 2: the MCC step of the PIC cycle; elastic,
 // charge-exchange and ionization kinematics), collision-clock tests that the mover
-// variant without the inline test left (a candidate of this same step when the draw says
-// so) and particles that left through an absorbing or source wall (flux and energy
-// counters, re-injection of the volume source).  The mover queues them (rare_pack) so that its own loop stays call-free;
-// here one thread takes one queued particle.  Collisions change only velocities, so
-// the mover has already deposited a candidate; a re-injected particle and the
-// children of an ionization are deposited here (and, on the step before a sort,
-// counted in the cell histogram).  Everything this kernel adds is an
-// integer sum or keyed by particle id and step, so the order of the queue does not
-// change any result.
+// variant without the inline test left (a candidate of this same step when the draw
+// says so) and particles that left through an absorbing or source wall (flux and
+// energy counters, re-injection of the volume source).  The mover queues them
+// (rare_pack) so that its own loop stays call-free; here one thread takes one queued
+// particle.  Collisions change only velocities, so the mover has already deposited a
+// candidate; a re-injected particle and the children of an ionization are deposited
+// here (and, on the step before a sort, counted in the cell histogram).  Everything
+// this kernel adds is an integer sum or keyed by particle id and step, so the order
+// of the queue does not change any result.
 #pragma once
 
 #include "mover.cuh"

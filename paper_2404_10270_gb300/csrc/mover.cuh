@@ -563,8 +563,9 @@ k_move(const __grid_constant__ MoveArgs a)
                         clk = 0u;
                     } else if (!TEST) {
                         // a test off the common test steps (the clock of a particle that
-                        // was a candidate, was loaded or was created in the last step):
-                        // the event kernel draws it, with this step's counter
+                        // was a candidate in the last step, or was re-injected or created
+                        // by ionization then): the event kernel draws it, with this
+                        // step's counter
                         tst |= 1u << k;
                     } else {
                         // a test step: the id is read only here
