@@ -139,11 +139,12 @@ typedef struct {
                                    choice) and caches the choice per GPU and size bucket
                                    in $BITPIC_TUNE_CACHE (default
                                    $HOME/.cache/bitpic/autotune.json).  An FP32 batch
-                                   without magnetic field or subcycling and with at
-                                   least $BITPIC_PAIR_MIN_SLOTS particle slots (default
-                                   2^24) moves its particles with a mover variant that
-                                   leaves most collision-clock draws to the event
-                                   kernel; this too changes no result. */
+                                   without magnetic field, whose colliding species move
+                                   on every step, with at least $BITPIC_PAIR_MIN_SLOTS
+                                   particle slots (default 2^24) moves its particles
+                                   with a mover variant that leaves most collision-clock
+                                   draws to the event kernel; this too changes no
+                                   result. */
     const pic_instance* inst;   /* n_instances entries, copied */
     void* cuda_stream;          /* borrowed cudaStream_t; NULL = library-owned stream */
 } pic_config;

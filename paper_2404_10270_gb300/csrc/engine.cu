@@ -113,6 +113,7 @@ struct pic_handle {
     int64_t* step_d = nullptr;
     int* test_all = nullptr;  // nonzero: every clock may need a test in the next step (after a load)
     int64_t pair_min = (int64_t)1 << 24;  // particle slots from which plain FP32 steps use the mover pair
+    bool pair_ok = true;                  // every colliding species moves on every step
     double *kin = nullptr, *phi_d = nullptr;
     std::vector<void*> allocs;
     char* io = nullptr;       // staging of pic_load_particles / pic_get_particles host data
@@ -517,16 +518,18 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
     {
         Span sp(h, sort ? 5 : 0);
         const int grid = sort ? h->grid_sort : h->grid_move;
-        // a plain FP32 step of a batch without subcycling or magnetic field launches the
-        // mover with the clock test inline and the one that queues the tests (the draw's
-        // code and registers cost the common path of this variant 6 %; the FP64 form is
-        // bound by its FP64 pipe and the Boris variant holds its registers anyway, so
-        // they keep the test inline).  The step count (and a load since the last step)
-        // decides on the device which of the two runs, so one captured sort cycle serves
-        // every cycle.  The partner that returns at once costs about 3 us, more than the
-        // 6 % saves below some 16 M particle slots.
-        const bool pair = move && !sort && !h->any_subcycle && !h->any_mag &&
-                          h->precision == PIC_FP32 && h->total_cap >= h->pair_min;
+        // a plain FP32 step of a batch without magnetic field launches the mover with the
+        // clock test inline and the one that queues the tests (the draw's code and
+        // registers cost the common path of this variant 6 %; the FP64 form is bound by
+        // its FP64 pipe and the Boris variant holds its registers anyway, so they keep the
+        // test inline).  The step count (and a load since the last step) decides on the
+        // device which of the two runs, so one captured sort cycle serves every cycle.
+        // The partner that returns at once costs about 3 us, more than the 6 % saves
+        // below some 16 M particle slots.  A batch with a subcycled colliding species
+        // (its candidates and tests bunched on its moving steps) keeps the test inline;
+        // subcycled species that never collide, like neutral targets, do not matter.
+        const bool pair = move && !sort && !h->any_mag && h->precision == PIC_FP32 &&
+                          h->total_cap >= h->pair_min && h->pair_ok;
         a.pair = pair ? 1 : 0;
         for (int v = 0; v < (pair ? 2 : 1); ++v) {
             h->kernels += 1;
@@ -938,6 +941,9 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     h->rare_cap = std::min<int64_t>(h->rare_cap + 65536, std::max<int64_t>(slot, 65536));
     h->total_cap = slot;
     if (const char* pm = std::getenv("BITPIC_PAIR_MIN_SLOTS")) h->pair_min = std::atoll(pm);
+    for (int i = 0; i < h->ninst; ++i)
+        for (int q = 0; q < h->inst[i].nproc; ++q)
+            if (species_nstep(h->inst[i], h->inst[i].proc[q].species) > 1) h->pair_ok = false;
     h->seg_nodes = snode;
     h->inst_nodes = inode;
     h->ev_total = ev;

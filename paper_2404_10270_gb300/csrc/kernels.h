@@ -14,8 +14,8 @@ struct MoveArgs;
 // phase of the initial field); `sub`: some species is subcycled; `mixed`: magnetized and
 // unmagnetized instances in one batch; `sort`: the step also sorts the store by cell
 // into the other copy (MoveArgs.cursor, .d*); `lean` (FP32, a plain step of a batch
-// without subcycling or magnetic field): the variant that queues collision-clock tests
-// for the event kernel instead of drawing them inline.  Returns the launch error.
+// without magnetic field): the variant that queues collision-clock tests for the event
+// kernel instead of drawing them inline.  Returns the launch error.
 cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
                             bool sort, bool lean, int nt, int grid, cudaStream_t st);
 cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,

@@ -422,8 +422,9 @@ k_move(const __grid_constant__ MoveArgs a)
     T* const uzp = static_cast<T*>(a.uz);
     const T2* const accp = static_cast<const T2*>(a.accel);
     const int64_t step = MOVE ? *a.step : 0;
-    if (MOVE && !SORT && !SUB && a.pair) {
-        // every clock without a candidate tests on the multiples of kGapMax
+    if (MOVE && !SORT && a.pair) {
+        // every clock without a candidate tests on the multiples of kGapMax (a pair is
+        // launched only when every colliding species moves on every step)
         const bool tstep = step % kGapMax == 0 || *a.test_all != 0;
         if (tstep != TEST) return;
     }

@@ -28,11 +28,14 @@ cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, boo
     if (sort)
         return sub ? go_sub<NT, true, true, true>(a, mag, mixed, grid, st)
                    : go_sub<NT, false, true, true>(a, mag, mixed, grid, st);
-    if (sub) return go_sub<NT, true, false, true>(a, mag, mixed, grid, st);
     if (lean && !mag) {
-        k_move<float, NT, false, true, false, false, false, false><<<grid, NT, 0, st>>>(a);
+        if (sub)
+            k_move<float, NT, false, true, true, false, false, false><<<grid, NT, 0, st>>>(a);
+        else
+            k_move<float, NT, false, true, false, false, false, false><<<grid, NT, 0, st>>>(a);
         return cudaGetLastError();
     }
+    if (sub) return go_sub<NT, true, false, true>(a, mag, mixed, grid, st);
     return go_sub<NT, false, false, true>(a, mag, mixed, grid, st);
 }
 

@@ -399,31 +399,41 @@ def test_fp64_move_rounds_exactly_like_the_oracle():
     assert (np.abs(loads[0].vx) * phys.dt / phys.dx > 1).any()  # some move past a cell
 
 
-@pytest.mark.parametrize("case", ["bounded", "source"])
+@pytest.mark.parametrize("case", ["bounded", "source", "target"])
 def test_mover_pair_changes_no_result(monkeypatch, case):
     """Plain FP32 steps of large batches use the mover pair: on the clock-test steps
     (multiples of 127) and after a load the variant with the collision-clock draw
     inline, on the others the variant that queues the few clocks needing a draw for the
     event kernel (after a candidate, and for re-injected particles and ionization
-    products, which start with a fresh clock).  Both orders of work give the same
-    state, bit for bit: over 260 steps (two clock-test steps, graph-replayed sort
-    cycles) and a reload of the state."""
+    products, which start with a fresh clock).  Both orders of work give the same state,
+    bit for bit: over 260 steps (clock-test steps, graph-replayed sort cycles) and, but
+    for the neutral-target case (its subcycled neutrals never draw), a reload of the
+    state."""
     ensure_built()
     if case == "bounded":
         phys = W.bounded_small(ncells=200, ppc=60, seed=4)
-    else:  # volume source and ionization without magnetic field
+    elif case == "source":  # volume source and ionization without magnetic field
         phys = W.magnetized_source(ncells=64, ppc=60, seed=4, B=0.0, nu=0.05, capacity_factor=3.0)
+    else:  # the paper's case: neutral particle targets moved on the sort steps
+        phys = W.ionization_case(ncells=300, ppc=40, seed=4, nu_iz=0.05)
     loads = W.initial_load(phys, seed=4)
+    K = phys.sort_interval if case == "target" else 20
 
     def run(min_slots):
         monkeypatch.setenv("BITPIC_PAIR_MIN_SLOTS", str(min_slots))
-        a = capi.Sim(phys, precision=capi.FP32, sort_interval=20)
+        a = capi.Sim(phys, precision=capi.FP32, sort_interval=K)
         a.load_all(loads)
+        if case == "target":
+            a.step(260)
+            out = [by_id(a.particles(0, s, cell_units=True)) for s in range(len(phys.species))]
+            mm = a.moments(0)
+            a.close()
+            return out, mm
         a.step(150)
         snap = [a.particles(0, s, cell_units=True) for s in range(2)]
         m = a.moments(0)
         a.close()
-        b = capi.Sim(phys, precision=capi.FP32, sort_interval=20)
+        b = capi.Sim(phys, precision=capi.FP32, sort_interval=K)
         for s, p in enumerate(snap):
             b.load(0, s, W.Load(p["cell"], p["off"], p["vx"], p["vy"], p["vz"], p["id"],
                                 p["state"]), cell_units=True)
