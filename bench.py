@@ -198,6 +198,7 @@ def run_reference(args):
 def pinned(a: np.ndarray):
     import torch
     t = torch.empty(a.shape, dtype={np.dtype(np.int32): torch.int32, np.dtype(np.float64): torch.float64,
+                                     np.dtype(np.float32): torch.float32,
                                      np.dtype(np.uint32): torch.int32}[a.dtype], pin_memory=True)
     v = t.numpy().view(a.dtype)
     v[...] = a
@@ -489,7 +490,9 @@ def cpu_oracle_instances(physs, loads, steps):
 def _e2e_pass(sim, host, outs, phys, args, world):
     """One end-to-end pass through the public API: load every species from pinned host
     memory, args.steps steps, the moments, every particle read back to pinned host
-    memory.  Returns (seconds, max over ranks; breakdown; moments; bytes read back)."""
+    memory.  The FP32 form's data travel as float (pic_load_particles_f32,
+    pic_get_particles_f32: 24 B per particle each way).  Returns (seconds, max over
+    ranks; breakdown; moments; bytes read back)."""
     import ctypes as C
     import torch
     from paper_2404_10270_gb300 import capi
@@ -511,9 +514,11 @@ def _e2e_pass(sim, host, outs, phys, args, world):
         o = outs[s]
         got = C.c_int64()
         cap = len(o["cell"])
-        capi._check(capi.lib().pic_get_particles(sim._h, 0, s, cap, *[o[k].ctypes.data for k in
+        f32 = o["off"].dtype == np.float32
+        get = capi.lib().pic_get_particles_f32 if f32 else capi.lib().pic_get_particles
+        capi._check(get(sim._h, 0, s, cap, *[o[k].ctypes.data for k in
                     ("cell", "off", "vx", "vy", "vz", "id")], None, 0, C.byref(got)), sim._h)
-        d2h += got.value * 40
+        d2h += got.value * (24 if f32 else 40)
     torch.cuda.synchronize()
     t_end = time.perf_counter()
     parts = {"load_s": t_load - t0, "load_species_s": [b - a for a, b in zip([t0] + t_sp[:-1], t_sp)],
@@ -532,17 +537,23 @@ def _run_ours(args, stream, rank, world, local):
     phys = W.bounded_large(ncells=args.cells, ppc=args.ppc, seed=1 + rank)
     loads = W.initial_load(phys, seed=1 + rank)
     n = sum(len(x) for x in loads)
-    # pinned host copies of the inputs (end-to-end measurement)
+    # pinned host copies of the inputs in double (the loads outside the timed regions)
     host = []
     for ld in loads:
         host.append({k: pinned(getattr(ld, k)) for k in ("cell", "off", "vx", "vy", "vz", "id")})
-    # pinned host buffers of the end-to-end pass (allocated here, outside every timed region)
-    outs = []
+    # the end-to-end pass's inputs and outputs in pinned host memory, in the FP32 form's
+    # own precision (float offsets and velocities; an offset that rounds up to 1 in float
+    # is kept just below it), all allocated here, outside every timed region
+    host32, outs = [], []
     for ld in loads:
         m = len(ld)
+        off32 = np.minimum(ld.off.astype(np.float32), np.float32(1.0) - np.float32(2.0 ** -24))
+        host32.append({"cell": pinned(ld.cell), "off": pinned(off32),
+                       "vx": pinned(ld.vx.astype(np.float32)), "vy": pinned(ld.vy.astype(np.float32)),
+                       "vz": pinned(ld.vz.astype(np.float32)), "id": pinned(ld.id)})
         outs.append({k: pinned(np.zeros(m, dt))[1] for k, dt in
-                     (("cell", np.int32), ("off", np.float64), ("vx", np.float64),
-                      ("vy", np.float64), ("vz", np.float64), ("id", np.uint32))})
+                     (("cell", np.int32), ("off", np.float32), ("vx", np.float32),
+                      ("vy", np.float32), ("vz", np.float32), ("id", np.uint32))})
     sim = capi.Sim(phys, precision=capi.FP32, sort_interval=args.sort, block=256, stream=stream)
     for s, h in enumerate(host):
         sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
@@ -555,11 +566,11 @@ def _run_ours(args, stream, rank, world, local):
     # the median is reported and every pass listed
     e2e_passes = []
     for _ in range(3):
-        e2e_passes.append(_e2e_pass(sim, host, outs, phys, args, world))
+        e2e_passes.append(_e2e_pass(sim, host32, outs, phys, args, world))
     e2e_passes.sort(key=lambda x: x[0])
     e2e_s, e2e_parts, mom, d2h = e2e_passes[1]
     e2e_value = n * world * args.steps / e2e_s
-    h2d = n * 40
+    h2d = n * 24  # cell, id (4 B each) and four floats per particle
     assert mom["step"] > 0
     e2e_parts["passes_s"] = [p[0] for p in e2e_passes]
 
@@ -632,8 +643,9 @@ def _run_ours(args, stream, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps,
-                    "what": "pic_load_particles from pinned host + %d steps + pic_moments + "
-                            "pic_get_particles to pinned host; median of 3 passes" % args.steps,
+                    "what": "pic_load_particles_f32 from pinned host + %d steps + pic_moments + "
+                            "pic_get_particles_f32 to pinned host (the FP32 form's data as float: "
+                            "24 B per particle each way); median of 3 passes" % args.steps,
                     "breakdown": e2e_parts},
             "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"],

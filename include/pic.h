@@ -182,6 +182,15 @@ PIC_API int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int
                                const double* vy, const double* vz, const uint32_t* id,
                                const uint8_t* state, int32_t flags);
 
+/* pic_load_particles with offsets and velocities in float: the same call with 24
+ * instead of 40 bytes per particle through the host link, for callers whose data is
+ * single precision (the FP32 form keeps its state in float anyway).  Each offset must
+ * be below 1 as a float; the FP64 form widens the values exactly. */
+PIC_API int pic_load_particles_f32(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                                   const int32_t* cell, const float* off, const float* vx,
+                                   const float* vy, const float* vz, const uint32_t* id,
+                                   const uint8_t* state, int32_t flags);
+
 /* Enqueue nsteps time steps of every instance on the handle's stream. */
 PIC_API int pic_step(pic_handle* h, int64_t nsteps);
 
@@ -205,6 +214,14 @@ PIC_API int pic_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n);
 PIC_API int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
                               int32_t* cell, double* off, double* vx, double* vy, double* vz,
                               uint32_t* id, uint8_t* state, int32_t flags, int64_t* n_out);
+
+/* pic_get_particles into float offsets and velocities (each value formed in double, as
+ * pic_get_particles returns it, and rounded once to float; an FP64-form offset just
+ * below 1 can round to 1).  Same arguments and errors otherwise. */
+PIC_API int pic_get_particles_f32(pic_handle* h, int32_t inst, int32_t species,
+                                  int64_t capacity, int32_t* cell, float* off, float* vx,
+                                  float* vy, float* vz, uint32_t* id, uint8_t* state,
+                                  int32_t flags, int64_t* n_out);
 
 /* Restore the counters a checkpoint needs besides the particles: the step count of
  * the handle (it keys every random draw) and, when next_id is not NULL, the next

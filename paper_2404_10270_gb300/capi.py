@@ -26,10 +26,10 @@ DEVICE, CELL_UNITS = 1, 2  # flags of load / get
 STATUS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA",
           -4: "PIC_ECAPACITY", -5: "PIC_ENONFINITE", -6: "PIC_ETIMEOUT", -7: "PIC_ESTATE"}
 
-EXPORTS = ("pic_create", "pic_load_particles", "pic_step", "pic_sync", "pic_moments",
-           "pic_count", "pic_get_particles", "pic_restore_counters", "pic_charge_raw", "pic_profile",
-           "pic_kernel_time", "pic_destroy", "pic_last_error", "pic_philox",
-           "pic_field_solve_noalloc")
+EXPORTS = ("pic_create", "pic_load_particles", "pic_load_particles_f32", "pic_step", "pic_sync",
+           "pic_moments", "pic_count", "pic_get_particles", "pic_get_particles_f32",
+           "pic_restore_counters", "pic_charge_raw", "pic_profile", "pic_kernel_time",
+           "pic_destroy", "pic_last_error", "pic_philox", "pic_field_solve_noalloc")
 
 
 class PicError(RuntimeError):
@@ -87,12 +87,15 @@ def lib():
         P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
         L.pic_create.argtypes = [C.POINTER(pic_config), C.POINTER(C.c_void_p)]
         L.pic_load_particles.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, P, I32]
+        L.pic_load_particles_f32.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, P, I32]
         L.pic_step.argtypes = [P, I64]
         L.pic_sync.argtypes = [P]
         L.pic_moments.argtypes = [P, I32, C.POINTER(pic_moments_out), P, P, P]
         L.pic_count.argtypes = [P, I32, I32, C.POINTER(C.c_int64)]
         L.pic_get_particles.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, P, I32,
                                         C.POINTER(C.c_int64)]
+        L.pic_get_particles_f32.argtypes = [P, I32, I32, I64, P, P, P, P, P, P, P, I32,
+                                            C.POINTER(C.c_int64)]
         L.pic_restore_counters.argtypes = [P, I64, P]
         L.pic_charge_raw.argtypes = [P, I32, P, C.POINTER(C.c_int64)]
         L.pic_profile.argtypes = [P, I32]
@@ -210,13 +213,17 @@ class Sim:
     # -- calls ----------------------------------------------------------------------
     def load(self, inst: int, species: int, ld, cell_units: bool = False) -> None:
         """Load particles from a workloads.Load (numpy, host) or an object with the
-        same fields as CUDA tensors (cell int32, off/vx/vy/vz float64, id uint32/int32).
-        cell_units: velocities are in cells per step (as particles(..., cell_units=True)
-        returns them), for exact checkpoints."""
+        same fields as CUDA tensors (cell int32, off/vx/vy/vz float64 or float32, id
+        uint32/int32).  Float32 offsets and velocities (all four) go through
+        pic_load_particles_f32, the rest through pic_load_particles.  cell_units:
+        velocities are in cells per step (as particles(..., cell_units=True) returns
+        them), for exact checkpoints."""
         arrs = [ld.cell, ld.off, ld.vx, ld.vy, ld.vz]
+        f32 = all(str(getattr(a, "dtype", "")).endswith("float32") for a in arrs[1:])
         if isinstance(ld.cell, np.ndarray):
+            ft = np.float32 if f32 else np.float64
             arrs = [np.ascontiguousarray(ld.cell, np.int32)] + \
-                   [np.ascontiguousarray(a, np.float64) for a in arrs[1:]]
+                   [np.ascontiguousarray(a, ft) for a in arrs[1:]]
             ids = None if ld.id is None else np.ascontiguousarray(ld.id, np.uint32)
             st = getattr(ld, "state", None)
             st = None if st is None else np.ascontiguousarray(st, np.uint8)
@@ -227,8 +234,9 @@ class Sim:
             dev = 1 if _on_device(ld.cell) else 0
         n = len(arrs[0])
         flags = (DEVICE if dev else 0) | (CELL_UNITS if cell_units else 0)
-        _check(lib().pic_load_particles(self._h, inst, species, n, *[_ptr(a) for a in arrs],
-                                        _ptr(ids), _ptr(st), flags), self._h)
+        fn = lib().pic_load_particles_f32 if f32 else lib().pic_load_particles
+        _check(fn(self._h, inst, species, n, *[_ptr(a) for a in arrs], _ptr(ids), _ptr(st),
+                  flags), self._h)
 
     def load_all(self, loads: List, inst: int = 0) -> None:
         for s, ld in enumerate(loads):
@@ -245,18 +253,21 @@ class Sim:
         _check(lib().pic_count(self._h, inst, species, C.byref(n)), self._h)
         return n.value
 
-    def particles(self, inst: int, species: int, cell_units: bool = False) -> Dict[str, np.ndarray]:
+    def particles(self, inst: int, species: int, cell_units: bool = False,
+                  dtype=np.float64) -> Dict[str, np.ndarray]:
         """Live particles of (inst, species) in storage order (host numpy); velocities
-        physical, or in cells per step with cell_units=True."""
+        physical, or in cells per step with cell_units=True.  dtype=np.float32 reads
+        offsets and velocities through pic_get_particles_f32."""
         n = self.count(inst, species)
-        out = dict(cell=np.zeros(n, np.int32), off=np.zeros(n), vx=np.zeros(n),
-                   vy=np.zeros(n), vz=np.zeros(n), id=np.zeros(n, np.uint32),
+        ft = np.dtype(dtype)
+        out = dict(cell=np.zeros(n, np.int32), off=np.zeros(n, ft), vx=np.zeros(n, ft),
+                   vy=np.zeros(n, ft), vz=np.zeros(n, ft), id=np.zeros(n, np.uint32),
                    state=np.zeros(n, np.uint8))
         got = C.c_int64()
-        _check(lib().pic_get_particles(self._h, inst, species, n,
-                                       *[_ptr(out[k]) for k in ("cell", "off", "vx", "vy", "vz",
-                                                                "id", "state")],
-                                       CELL_UNITS if cell_units else 0, C.byref(got)), self._h)
+        fn = lib().pic_get_particles_f32 if ft == np.float32 else lib().pic_get_particles
+        _check(fn(self._h, inst, species, n,
+                  *[_ptr(out[k]) for k in ("cell", "off", "vx", "vy", "vz", "id", "state")],
+                  CELL_UNITS if cell_units else 0, C.byref(got)), self._h)
         assert got.value == n
         return out
 

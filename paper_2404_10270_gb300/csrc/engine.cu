@@ -1100,12 +1100,16 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     return PIC_OK;
 }
 
-int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
-                       const int32_t* cell, const double* off, const double* vx,
-                       const double* vy, const double* vz, const uint32_t* id,
-                       const uint8_t* state, int32_t flags)
+namespace {
+// pic_load_particles and pic_load_particles_f32: offsets and velocities in double, or in
+// float with host_f32 (hb bytes per value).
+int load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                   const int32_t* cell, const void* off, const void* vx, const void* vy,
+                   const void* vz, const uint32_t* id, const uint8_t* state, int32_t flags,
+                   bool host_f32)
 {
     const bool on_device = (flags & PIC_DEVICE) != 0;
+    const size_t hb = host_f32 ? 4 : 8;
     int rc = check_state(h);
     if (rc) return rc;
     if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || n < 0)
@@ -1119,11 +1123,11 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     // staging of host input
     void* stage = nullptr;
     const int32_t* dc = cell;
-    const double *doff = off, *dvx = vx, *dvy = vy, *dvz = vz;
+    const void *doff = off, *dvx = vx, *dvy = vy, *dvz = vz;
     const uint32_t* did = id;
     const uint8_t* dstate = state;
     if (!on_device && n > 0) {
-        const size_t bytes = (size_t)n * (4 + 8 * 4) + (id ? (size_t)n * 4 : 0) +
+        const size_t bytes = (size_t)n * (4 + hb * 4) + (id ? (size_t)n * 4 : 0) +
                              (state ? (size_t)n : 0) + 128;
         char* p = nullptr;
         CUDA_TRY(h, io_buffer(h, bytes, &p));
@@ -1133,12 +1137,12 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
             p += (b + 15) / 16 * 16;
             return cudaMemcpyAsync(d, src, b, cudaMemcpyHostToDevice, s) == cudaSuccess ? d : nullptr;
         };
-        const size_t nb8 = (size_t)n * 8;
+        const size_t nbh = (size_t)n * hb;
         dc = (const int32_t*)put(cell, (size_t)n * 4);
-        doff = (const double*)put(off, nb8);
-        dvx = (const double*)put(vx, nb8);
-        dvy = (const double*)put(vy, nb8);
-        dvz = (const double*)put(vz, nb8);
+        doff = put(off, nbh);
+        dvx = put(vx, nbh);
+        dvy = put(vy, nbh);
+        dvz = put(vz, nbh);
         did = id ? (const uint32_t*)put(id, (size_t)n * 4) : nullptr;
         dstate = state ? (const uint8_t*)put(state, (size_t)n) : nullptr;
         if (!dc || !doff || !dvx || !dvy || !dvz || (id && !did) || (state && !dstate))
@@ -1158,6 +1162,7 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     l.vx = dvx;
     l.vy = dvy;
     l.vz = dvz;
+    l.host_f32 = host_f32 ? 1 : 0;
     l.id = did;
     l.state = dstate;
     l.n = n;
@@ -1198,6 +1203,24 @@ int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     h->stale = true;
     h->hist_ready = false;
     return PIC_OK;
+}
+
+}  // namespace
+
+int pic_load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                       const int32_t* cell, const double* off, const double* vx,
+                       const double* vy, const double* vz, const uint32_t* id,
+                       const uint8_t* state, int32_t flags)
+{
+    return load_particles(h, inst, species, n, cell, off, vx, vy, vz, id, state, flags, false);
+}
+
+int pic_load_particles_f32(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                           const int32_t* cell, const float* off, const float* vx,
+                           const float* vy, const float* vz, const uint32_t* id,
+                           const uint8_t* state, int32_t flags)
+{
+    return load_particles(h, inst, species, n, cell, off, vx, vy, vz, id, state, flags, true);
 }
 
 namespace {
@@ -1441,11 +1464,15 @@ int pic_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n)
     return PIC_OK;
 }
 
-int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
-                      int32_t* cell, double* off, double* vx, double* vy, double* vz,
-                      uint32_t* id, uint8_t* state, int32_t flags, int64_t* n_out)
+namespace {
+// pic_get_particles and pic_get_particles_f32: offsets and velocities in double, or in
+// float with host_f32 (hb bytes per value).
+int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
+                  int32_t* cell, void* off, void* vx, void* vy, void* vz, uint32_t* id,
+                  uint8_t* state, int32_t flags, int64_t* n_out, bool host_f32)
 {
     const bool on_device = (flags & PIC_DEVICE) != 0;
+    const size_t hb = host_f32 ? 4 : 8;
     int rc = check_state(h);
     if (rc) return rc;
     if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || !n_out)
@@ -1464,7 +1491,7 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
     const size_t n = (size_t)std::max<unsigned long long>(live, 1);
     char* tmp = nullptr;
     const size_t scratch = (size_t)(nb + 1) * 8;
-    const size_t outb = on_device ? 0 : n * (4 + 8 * 4 + 4 + 1) + 8 * 16;
+    const size_t outb = on_device ? 0 : n * (4 + hb * 4 + 4 + 1) + 8 * 16;
     CUDA_TRY(h, io_buffer(h, scratch + outb + 16, &tmp));
     GetArgs g;
     const Store& S = h->st[h->cur];
@@ -1482,16 +1509,17 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
     g.precision = h->precision;
     g.block_count = reinterpret_cast<unsigned long long*>(tmp);
     g.capacity = (int64_t)live;
+    g.host_f32 = host_f32 ? 1 : 0;
     if (on_device) {
         g.cell = cell; g.off = off; g.vx = vx; g.vy = vy; g.vz = vz; g.id = id; g.state = state;
     } else {
         char* p = tmp + (scratch + 15) / 16 * 16;
         auto take = [&](size_t b) { char* d = p; p += (b + 15) / 16 * 16; return d; };
         g.cell = cell ? (int32_t*)take(n * 4) : nullptr;
-        g.off = off ? (double*)take(n * 8) : nullptr;
-        g.vx = vx ? (double*)take(n * 8) : nullptr;
-        g.vy = vy ? (double*)take(n * 8) : nullptr;
-        g.vz = vz ? (double*)take(n * 8) : nullptr;
+        g.off = off ? take(n * hb) : nullptr;
+        g.vx = vx ? take(n * hb) : nullptr;
+        g.vy = vy ? take(n * hb) : nullptr;
+        g.vz = vz ? take(n * hb) : nullptr;
         g.id = id ? (uint32_t*)take(n * 4) : nullptr;
         g.state = state ? (uint8_t*)take(n) : nullptr;
     }
@@ -1499,15 +1527,32 @@ int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capa
     if (!on_device && live > 0) {
         const size_t m = (size_t)live;
         if (cell) CUDA_TRY(h, cudaMemcpyAsync(cell, g.cell, m * 4, cudaMemcpyDeviceToHost, s));
-        if (off) CUDA_TRY(h, cudaMemcpyAsync(off, g.off, m * 8, cudaMemcpyDeviceToHost, s));
-        if (vx) CUDA_TRY(h, cudaMemcpyAsync(vx, g.vx, m * 8, cudaMemcpyDeviceToHost, s));
-        if (vy) CUDA_TRY(h, cudaMemcpyAsync(vy, g.vy, m * 8, cudaMemcpyDeviceToHost, s));
-        if (vz) CUDA_TRY(h, cudaMemcpyAsync(vz, g.vz, m * 8, cudaMemcpyDeviceToHost, s));
+        if (off) CUDA_TRY(h, cudaMemcpyAsync(off, g.off, m * hb, cudaMemcpyDeviceToHost, s));
+        if (vx) CUDA_TRY(h, cudaMemcpyAsync(vx, g.vx, m * hb, cudaMemcpyDeviceToHost, s));
+        if (vy) CUDA_TRY(h, cudaMemcpyAsync(vy, g.vy, m * hb, cudaMemcpyDeviceToHost, s));
+        if (vz) CUDA_TRY(h, cudaMemcpyAsync(vz, g.vz, m * hb, cudaMemcpyDeviceToHost, s));
         if (id) CUDA_TRY(h, cudaMemcpyAsync(id, g.id, m * 4, cudaMemcpyDeviceToHost, s));
         if (state) CUDA_TRY(h, cudaMemcpyAsync(state, g.state, m, cudaMemcpyDeviceToHost, s));
     }
     CUDA_TRY(h, cudaStreamSynchronize(s));
     return PIC_OK;
+}
+}  // namespace
+
+int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
+                      int32_t* cell, double* off, double* vx, double* vy, double* vz,
+                      uint32_t* id, uint8_t* state, int32_t flags, int64_t* n_out)
+{
+    return get_particles(h, inst, species, capacity, cell, off, vx, vy, vz, id, state, flags,
+                         n_out, false);
+}
+
+int pic_get_particles_f32(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
+                          int32_t* cell, float* off, float* vx, float* vy, float* vz,
+                          uint32_t* id, uint8_t* state, int32_t flags, int64_t* n_out)
+{
+    return get_particles(h, inst, species, capacity, cell, off, vx, vy, vz, id, state, flags,
+                         n_out, true);
 }
 
 int pic_restore_counters(pic_handle* h, int64_t step, const uint64_t* next_id)

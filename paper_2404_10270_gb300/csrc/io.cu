@@ -8,10 +8,15 @@ namespace bitpic {
 namespace {
 
 // Load: velocities physical -> cells per step (u = v dt/dx); invalid cells or
-// offsets are latched as kErrInput.  Slots [n, cap) become empty.
-template <typename T>
+// offsets are latched as kErrInput.  Slots [n, cap) become empty.  T: the store's
+// precision, H: the caller's (double, or float).
+template <typename T, typename H>
 __global__ void k_load(const LoadArgs l)
 {
+    const H* const in_off = static_cast<const H*>(l.off);
+    const H* const in_vx = static_cast<const H*>(l.vx);
+    const H* const in_vy = static_cast<const H*>(l.vy);
+    const H* const in_vz = static_cast<const H*>(l.vz);
     T* off = static_cast<T*>(l.s_off);
     T* ux = static_cast<T*>(l.s_ux);
     T* uy = static_cast<T*>(l.s_uy);
@@ -23,7 +28,7 @@ __global__ void k_load(const LoadArgs l)
         const int64_t g = l.base + k;
         if (k < l.n) {
             const int c = l.cell[k];
-            const double f = l.off[k];
+            const double f = (double)in_off[k];
             const bool ok = c >= 0 && c < l.ncells && f >= 0.0 && f < 1.0;
             if (!ok) set_error(l.err, kErrInput);
             T ft = (T)f;
@@ -40,9 +45,10 @@ __global__ void k_load(const LoadArgs l)
             const uint32_t clk = l.state ? (uint32_t)l.state[k] : 0u;
             l.s_cell[g] = ok ? (int)((uint32_t)cc | (clk << kClockShift)) : -1;
             off[g] = ft;
-            ux[g] = l.vscale == 1.0 ? (T)l.vx[k] : (T)(l.vx[k] * l.vscale);
-            uy[g] = l.vscale == 1.0 ? (T)l.vy[k] : (T)(l.vy[k] * l.vscale);
-            uz[g] = l.vscale == 1.0 ? (T)l.vz[k] : (T)(l.vz[k] * l.vscale);
+            const double vx = (double)in_vx[k], vy = (double)in_vy[k], vz = (double)in_vz[k];
+            ux[g] = l.vscale == 1.0 ? (T)vx : (T)(vx * l.vscale);
+            uy[g] = l.vscale == 1.0 ? (T)vy : (T)(vy * l.vscale);
+            uz[g] = l.vscale == 1.0 ? (T)vz : (T)(vz * l.vscale);
             l.s_id[g] = l.id ? l.id[k] : l.id0 + (uint32_t)k;
         } else {
             l.s_cell[g] = -1;
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(1024) k_get_scan(unsigned long long* bc, int64
     if (threadIdx.x == 0) bc[nb] = sh[32];
 }
 
-template <typename T>
+template <typename T, typename H>
 __global__ void k_get_write(const GetArgs g)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -138,10 +144,11 @@ __global__ void k_get_write(const GetArgs g)
     const uint32_t word = (uint32_t)g.s_cell[s];
     if (g.cell) g.cell[o] = (int)(word & kCellMask);
     if (g.state) g.state[o] = (uint8_t)(word >> kClockShift);
-    if (g.off) g.off[o] = (double)static_cast<const T*>(g.s_off)[s];
-    if (g.vx) g.vx[o] = (double)static_cast<const T*>(g.s_ux)[s] * g.vscale_inv;
-    if (g.vy) g.vy[o] = (double)static_cast<const T*>(g.s_uy)[s] * g.vscale_inv;
-    if (g.vz) g.vz[o] = (double)static_cast<const T*>(g.s_uz)[s] * g.vscale_inv;
+    // in double, then rounded once to the caller's type
+    if (g.off) static_cast<H*>(g.off)[o] = (H)(double)static_cast<const T*>(g.s_off)[s];
+    if (g.vx) static_cast<H*>(g.vx)[o] = (H)((double)static_cast<const T*>(g.s_ux)[s] * g.vscale_inv);
+    if (g.vy) static_cast<H*>(g.vy)[o] = (H)((double)static_cast<const T*>(g.s_uy)[s] * g.vscale_inv);
+    if (g.vz) static_cast<H*>(g.vz)[o] = (H)((double)static_cast<const T*>(g.s_uz)[s] * g.vscale_inv);
     if (g.id) g.id[o] = g.s_id[s];
 }
 
@@ -194,10 +201,13 @@ int grid_for(int64_t n, int nt, int cap = 152 * 32)
 cudaError_t launch_load(const LoadArgs& l, cudaStream_t st)
 {
     const int g = grid_for(l.cap, 256);
-    if (l.precision == PIC_FP64)
-        k_load<double><<<g, 256, 0, st>>>(l);
-    else
-        k_load<float><<<g, 256, 0, st>>>(l);
+    if (l.precision == PIC_FP64) {
+        if (l.host_f32) k_load<double, float><<<g, 256, 0, st>>>(l);
+        else k_load<double, double><<<g, 256, 0, st>>>(l);
+    } else {
+        if (l.host_f32) k_load<float, float><<<g, 256, 0, st>>>(l);
+        else k_load<float, double><<<g, 256, 0, st>>>(l);
+    }
     return cudaGetLastError();
 }
 
@@ -207,10 +217,13 @@ cudaError_t launch_get(const GetArgs& g, cudaStream_t st)
     if (nb == 0) return cudaSuccess;
     k_get_count<<<(unsigned)nb, 1024, 0, st>>>(g.s_cell, g.base, g.nslots, g.block_count);
     k_get_scan<<<1, 1024, 0, st>>>(g.block_count, nb);
-    if (g.precision == PIC_FP64)
-        k_get_write<double><<<(unsigned)nb, 1024, 0, st>>>(g);
-    else
-        k_get_write<float><<<(unsigned)nb, 1024, 0, st>>>(g);
+    if (g.precision == PIC_FP64) {
+        if (g.host_f32) k_get_write<double, float><<<(unsigned)nb, 1024, 0, st>>>(g);
+        else k_get_write<double, double><<<(unsigned)nb, 1024, 0, st>>>(g);
+    } else {
+        if (g.host_f32) k_get_write<float, float><<<(unsigned)nb, 1024, 0, st>>>(g);
+        else k_get_write<float, double><<<(unsigned)nb, 1024, 0, st>>>(g);
+    }
     return cudaGetLastError();
 }
 

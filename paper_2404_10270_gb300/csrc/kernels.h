@@ -113,10 +113,11 @@ cudaError_t launch_sort_finish(const SortArgs& s, cudaStream_t st);
 // ---- I/O and diagnostics (io.cu) -------------------------------------------------
 struct LoadArgs {
     const int32_t* cell;
-    const double* off;
-    const double* vx;
-    const double* vy;
-    const double* vz;
+    const void* off;        // double, or float with host_f32
+    const void* vx;
+    const void* vy;
+    const void* vz;
+    int host_f32;
     const uint32_t* id;     // NULL: id0 + k
     const uint8_t* state;   // collision clocks, NULL: 0
     int64_t n;
@@ -147,10 +148,11 @@ struct GetArgs {
     double vscale_inv;      // dx/dt
     int precision;
     int32_t* cell;
-    double* off;
-    double* vx;
-    double* vy;
-    double* vz;
+    void* off;              // double, or float with host_f32
+    void* vx;
+    void* vy;
+    void* vz;
+    int host_f32;
     uint32_t* id;
     uint8_t* state;
     unsigned long long* block_count;  // scratch, ceil(nslots/1024)+1 entries
