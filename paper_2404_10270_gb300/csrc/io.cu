@@ -163,8 +163,15 @@ __global__ void k_kinetic(const SegParams* seg, int s0, const int32_t* cell, con
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P.cap; k += stride) {
         const int64_t g = P.base + k;
         if (cell[g] < 0) continue;
-        const double a = ux[g], b = uy[g], c = uz[g];
-        acc += a * a + b * b + c * c;
+        if (sizeof(T) == 4) {
+            // |u|^2 of a float state in float (two fused multiply-adds), summed in double:
+            // one FP64 operation per particle, the GB300's scarce pipe
+            const float a = (float)ux[g], b = (float)uy[g], c = (float)uz[g];
+            acc += (double)__fmaf_rn(a, a, __fmaf_rn(b, b, c * c));
+        } else {
+            const double a = ux[g], b = uy[g], c = uz[g];
+            acc += a * a + b * b + c * c;
+        }
     }
     for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
     __shared__ double sh[32];
