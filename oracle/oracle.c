@@ -28,10 +28,13 @@
  * whose candidate steps are drawn as geometric runs from Philox4x32-10 words with
  * integer thresholds, and whose process selection uses fixed integer slots; linear
  * (CIC) weights;
- * Gauss's law over the half cell at the wall nodes.  All arithmetic is FP64 and the
- * file is compiled without floating-point contraction; the one fused operation is
- * the gather's explicit fma() (the paper does not fix how its product-sum rounds;
- * a C compiler on FMA hardware contracts it to one rounding).
+ * Gauss's law over the half cell at the wall nodes.  All particle arithmetic is FP64
+ * and the file is compiled without floating-point contraction; the fused operations
+ * are the explicit fma() calls of the gather and the Boris cross products (the paper
+ * does not fix how a product-sum rounds; a C compiler on FMA hardware contracts it to
+ * one rounding).  The Poisson solve runs in binary128 and rounds its results to FP64
+ * once, so the field is the exact solution of the discrete problem to within that
+ * rounding (see orc_poisson).
  */
 #include "oracle.h"
 
@@ -357,37 +360,56 @@ static void deposit(orc_sim* s)
     }
 }
 
+/* IEEE binary128 for the field solve: long double where it is binary128 (aarch64
+ * Linux), else GCC's _Float128 (x86_64; +, -, *, / in libgcc's soft float). */
+#if defined(__LDBL_MANT_DIG__) && __LDBL_MANT_DIG__ == 113
+typedef long double quad;
+#else
+typedef _Float128 quad;
+#endif
+_Static_assert(sizeof(quad) == 16, "binary128 expected");
+
 int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* phi, double* E)
 {
     if (N < 1 || !rho || !phi || !E || !(dx > 0) || !(eps0 > 0)) return -1;
     const int M = N - 1; /* interior unknowns phi[1..N-1] */
-    phi[0] = 0.0;
-    phi[N] = 0.0;
+    /* The Thomas algorithm is backward stable, but its forward error in phi grows with
+     * the condition number of the tridiagonal matrix (~N^2): in FP64 it reaches ~1e-11
+     * of the field at N = 8192.  The recurrences are therefore carried in binary128
+     * (113-bit significand; the same error bound is then ~1e-26 at N = 65536) and every
+     * result is rounded to FP64 once, at the end: phi and E are the exact solution of
+     * the discrete problem for this rho, to within the final rounding. */
+    quad* q = (quad*)malloc((size_t)(N + 1) * sizeof(quad));   /* phi in binary128 */
+    quad* cp = (quad*)malloc((size_t)(N + 1) * sizeof(quad));
+    quad* dp = (quad*)malloc((size_t)(N + 1) * sizeof(quad));
+    if (!q || !cp || !dp) { free(q); free(cp); free(dp); return -2; }
+    q[0] = 0;
+    q[N] = 0;
     if (M >= 1) {
-        double* cp = (double*)malloc((size_t)(M + 1) * sizeof(double));
-        double* dp = (double*)malloc((size_t)(M + 1) * sizeof(double));
-        if (!cp || !dp) { free(cp); free(dp); return -2; }
         /* Thomas algorithm on a_i = -1, b_i = 2, c_i = -1, d_i = dx^2 rho_i / eps0 */
-        const double a = -1.0, b = 2.0, c = -1.0;
-        double d1 = dx * dx * rho[1] / eps0;
+        const quad a = -1, b = 2, c = -1;
+        const quad h2 = (quad)dx * (quad)dx / (quad)eps0;
         cp[1] = c / b;
-        dp[1] = d1 / b;
+        dp[1] = h2 * (quad)rho[1] / b;
         for (int i = 2; i <= M; ++i) {
-            const double di = dx * dx * rho[i] / eps0;
-            const double m = b - a * cp[i - 1];
+            const quad di = h2 * (quad)rho[i];
+            const quad m = b - a * cp[i - 1];
             cp[i] = c / m;
             dp[i] = (di - a * dp[i - 1]) / m;
         }
-        phi[M] = dp[M];
-        for (int i = M - 1; i >= 1; --i) phi[i] = dp[i] - cp[i] * phi[i + 1];
-        free(cp);
-        free(dp);
+        q[M] = dp[M];
+        for (int i = M - 1; i >= 1; --i) q[i] = dp[i] - cp[i] * q[i + 1];
     }
     /* E = -dphi/dx: centred inside; at a wall node Gauss's law over the half cell
      * next to the wall, whose charge per area is rho_wall * dx/2. */
-    for (int j = 1; j < N; ++j) E[j] = (phi[j - 1] - phi[j + 1]) / (2.0 * dx);
-    E[0] = -(phi[1] - phi[0]) / dx - rho[0] * dx / (2.0 * eps0);
-    E[N] = -(phi[N] - phi[N - 1]) / dx + rho[N] * dx / (2.0 * eps0);
+    const quad qdx = (quad)dx, half = (quad)dx / (2 * (quad)eps0);
+    for (int j = 1; j < N; ++j) E[j] = (double)((q[j - 1] - q[j + 1]) / (2 * qdx));
+    E[0] = (double)(-(q[1] - q[0]) / qdx - (quad)rho[0] * half);
+    E[N] = (double)(-(q[N] - q[N - 1]) / qdx + (quad)rho[N] * half);
+    for (int j = 0; j <= N; ++j) phi[j] = (double)q[j];
+    free(q);
+    free(cp);
+    free(dp);
     return 0;
 }
 
@@ -874,6 +896,14 @@ int orc_step(orc_sim* s, int64_t nsteps)
         int rc = one_step(s);
         if (rc) return rc;
     }
+    return 0;
+}
+
+int orc_set_step(orc_sim* s, int64_t step, uint32_t next_id)
+{
+    if (!s || step < 0) return -1;
+    s->step = step;
+    if (next_id > s->next_id) s->next_id = next_id;
     return 0;
 }
 

@@ -94,6 +94,11 @@ int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const doubl
 /* Advance nsteps time steps.  Returns 0 or a negative error. */
 int orc_step(orc_sim* s, int64_t nsteps);
 
+/* Continue a saved run: set the step counter (the next step is `step`, which keys its
+ * draws and places it on the collision clock's grid) and raise the next id for created
+ * particles to at least next_id.  Counters of walls and collisions are not touched. */
+int orc_set_step(orc_sim* s, int64_t step, uint32_t next_id);
+
 int64_t orc_count(const orc_sim* s, int32_t sp);
 /* Copy out species sp sorted by ascending id (capacity = orc_count). */
 int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx,
@@ -122,8 +127,9 @@ void orc_smooth(int32_t N, double* rho);
 
 /* Dirichlet Poisson problem of the field phase: -phi[j-1]+2phi[j]-phi[j+1] =
  * dx^2 rho[j]/eps0 for 1<=j<=N-1, phi[0]=phi[N]=0, by the Thomas algorithm, then
- * E = -grad(phi) (centred inside, Gauss half cell at the walls).  rho has N+1
- * entries; rho[0], rho[N] are half-cell (wall) densities.  Returns 0 or < 0. */
+ * E = -grad(phi) (centred inside, Gauss half cell at the walls).  The recurrences and
+ * E are carried in IEEE binary128 and rounded to FP64 once.  rho has N+1 entries;
+ * rho[0], rho[N] are half-cell (wall) densities.  Returns 0 or < 0. */
 int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* phi, double* E);
 
 #ifdef __cplusplus

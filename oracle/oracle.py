@@ -59,6 +59,7 @@ def lib():
         P = C.c_void_p
         L.orc_load.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P, P, P, P, P, P, P]
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
+        L.orc_set_step.argtypes = [C.c_void_p, C.c_int64, C.c_uint32]
         L.orc_count.restype = C.c_int64
         L.orc_count.argtypes = [C.c_void_p, C.c_int32]
         L.orc_get.argtypes = [C.c_void_p, C.c_int32, P, P, P, P, P, P, P]
@@ -161,6 +162,12 @@ class Oracle:
         rc = lib().orc_step(self._h, n)
         if rc:
             raise RuntimeError("orc_step failed: %d" % rc)
+
+    def set_step(self, step: int, next_id: int = 0) -> None:
+        """Continue a saved run at `step` with created ids from at least next_id."""
+        rc = lib().orc_set_step(self._h, step, next_id)
+        if rc:
+            raise RuntimeError("orc_set_step failed: %d" % rc)
 
     def particles(self, species: int) -> dict:
         n = lib().orc_count(self._h, species)

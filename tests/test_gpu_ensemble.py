@@ -5,20 +5,13 @@ checked particle by particle against the oracle, and two against the same instan
 alone (bit-identical).
 
 Tolerance.  Particles that took part in no ionization must meet the form's tolerance
-(FP64 1e-12, FP32 1e-5).  An ionization gives both outgoing electrons the speed
-sqrt((E - E_iz)/m): near threshold this divides the incident energy's rounding by
-E - E_iz, so a last-bit difference in the field (the oracle solves Poisson by Thomas,
-the GPU exactly in integers) is amplified by E/(E - E_iz).  Participants (the electron
-that ionized and both products) are therefore held to 100x the tolerance; the
-measured worst cases were 5.6e-12 (FP64, 20 steps) and 1.07e-5 (FP32, 10 steps), all
-for products moving at 2-15 % of the thermal speed.
-
-FP64 and the cell count.  The oracle's Thomas solve is backward stable but its forward
-error in the field grows with the condition number of the tridiagonal matrix, ~N^2:
-on noisy charge it is ~7e-14 of the rms field at N = 256, 1.7e-12 at 2048 and 1.9e-11
-at 8192 (against an exact rational solve), while the GPU's integer solve rounds once.
-The FP64 bound is therefore 1e-12 x max(1, (N/256)^2); at 256 cells it is the flat
-1e-12 that the 256-cell workload is held to over 100 steps."""
+(FP64 1e-12, FP32 1e-5) at every cell count: the oracle's Poisson solve is the exact
+solution rounded once (binary128 Thomas), like the GPU's integer solve.  An ionization
+gives both outgoing electrons the speed sqrt((E - E_iz)/m): near threshold this
+divides the incident energy's rounding by E - E_iz, so a last-bit difference in the
+field (the fixed-point deposit against the oracle's FP64 sum) is amplified by
+E/(E - E_iz).  Participants (the electron that ionized and both products) are
+therefore held to 100x the tolerance."""
 import concurrent.futures as cf
 
 import numpy as np
@@ -65,7 +58,7 @@ def test_ensemble_sampled_instances_match_oracle(ensemble, precision, steps, tol
         if precision == capi.FP64:
             np.testing.assert_array_equal(gm["collisions"], om["collisions"])
             np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
-        t = tol if precision == capi.FP32 else tol * max(1.0, (phys[i].ncells / 256.0) ** 2)
+        t = tol
         for s in range(2):
             ids, ex, ev, involved = ionization_errors(phys[i], g[s], o[s], s, n0, parents)
             assert ex.max() < t, (i, s, ex.max())

@@ -38,7 +38,7 @@ def test_full_size_one_step(full_case, precision, tol):
     sim.load_all(loads)
     g0 = sim.moments(0)
     scale = np.abs(m0["E"]).max()
-    np.testing.assert_allclose(g0["E"], m0["E"], rtol=0, atol=max(tol, 1e-7) * scale)
+    np.testing.assert_allclose(g0["E"], m0["E"], rtol=0, atol=tol * scale)
     sim.step(1)
     g1 = sim.moments(0)
     raw, unit = sim.charge_raw(0)

@@ -1,9 +1,11 @@
 """Pins of the oracle's density (cloud-in-cell) and field (Poisson) phases.
 
 * Poisson: against a dense LAPACK solve of the same tridiagonal system, against the
-  closed form phi = rho x (L - x) / (2 eps0) for uniform charge (exact for the
-  three-point Laplacian), and against Gauss's law over the whole gap,
-  E_N - E_0 = (integral of rho) / eps0.
+  exact rational solution (the discrete Green's function of the three-point Dirichlet
+  Laplacian, G(j, k) = min(j, k) (N - max(j, k)) / N, summed in Python integers) up
+  to 65,536 cells, against the closed form phi = rho x (L - x) / (2 eps0) for uniform
+  charge (exact for the three-point Laplacian), and against Gauss's law over the
+  whole gap, E_N - E_0 = (integral of rho) / eps0.
 * Deposit: linear weighting preserves total charge and the first moment (centre of
   charge) of every particle exactly; a uniform lattice deposits a uniform density.
 """
@@ -30,7 +32,76 @@ def test_poisson_matches_dense_solve(N):
         np.testing.assert_allclose(phi[1:N], ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("N", [4, 100, 1000])
+def _exact_solution(rho, dx, eps0):
+    """phi and E of the grounded three-point problem as exact rationals, rounded to
+    FP64 once.  phi_j = (dx^2/eps0) sum_k G(j, k) rho_k with the discrete Green's
+    function G(j, k) = min(j, k) (N - max(j, k)) / N, i.e.
+    phi_j = h2 [(N - j) sum_{k<=j} k rho_k + j sum_{k>j} (N - k) rho_k] / N,
+    with every rho_k an exact dyadic rational (scaled to integers by a common 2^K)."""
+    from fractions import Fraction
+    N = len(rho) - 1
+    fr = [Fraction(float(r)) for r in rho]
+    D = max(f.denominator for f in fr)
+    R = [f.numerator * (D // f.denominator) for f in fr]  # rho_k = R_k / D
+    S1 = [0] * (N + 1)   # sum_{1<=k<=j} k R_k
+    for j in range(1, N):
+        S1[j] = S1[j - 1] + j * R[j]
+    S2 = [0] * (N + 1)   # sum_{j<k<=N-1} (N - k) R_k
+    for j in range(N - 2, -1, -1):
+        S2[j] = S2[j + 1] + (N - (j + 1)) * R[j + 1]
+    h2 = Fraction(dx) ** 2 / Fraction(eps0)
+    scale = h2 / (N * D)
+    q = [scale * ((N - j) * S1[j] + j * S2[j]) for j in range(N + 1)]
+    q[0] = q[N] = Fraction(0)
+    fdx = Fraction(dx)
+    half = fdx / (2 * Fraction(eps0))
+    E = [Fraction(0)] * (N + 1)
+    for j in range(1, N):
+        E[j] = (q[j - 1] - q[j + 1]) / (2 * fdx)
+    E[0] = -(q[1] - q[0]) / fdx - fr[0] * half
+    E[N] = -(q[N] - q[N - 1]) / fdx + fr[N] * half
+    return np.array([float(v) for v in q]), np.array([float(v) for v in E])
+
+
+@pytest.mark.parametrize("N", [2, 257, 8192, 65536])
+def test_poisson_is_the_rounded_exact_solution(N):
+    """The oracle's Thomas solve (binary128, one final rounding) against the exact
+    rational solution: every phi and E within one unit in the last place (the exact
+    value rounded to FP64 is within half a unit; the binary128 recurrences add ~1e-25
+    relative).  An FP64 Thomas solve misses this by ~1e-11 at N = 8192."""
+    rng = np.random.default_rng(N + 11)
+    dx, eps0 = 0.5, 1.0
+    # a plasma-like charge: two nearly cancelling species densities
+    rho = rng.normal(1.0, 0.1, N + 1) - rng.normal(1.0, 0.1, N + 1)
+    phi, E = poisson(rho, dx, eps0)
+    ephi, eE = _exact_solution(rho, dx, eps0)
+    for got, want in ((phi, ephi), (E, eE)):
+        floor = 1e-22 * np.abs(want).max()
+        bad = np.abs(got - want) > np.spacing(np.abs(want)) + floor
+        assert not bad.any(), (np.nonzero(bad)[0][:5], got[bad][:3], want[bad][:3])
+
+
+def test_poisson_against_lapack_banded_at_8192():
+    """LAPACK's banded LU (gbsv) on the same system: its own forward error is bounded
+    by cond(A) eps ~ (4 N^2 / pi^2) eps of the solution's scale, which bounds the gap."""
+    from scipy.linalg import solve_banded
+    N = 8192
+    rng = np.random.default_rng(8192)
+    dx, eps0 = 0.5, 1.0
+    rho = rng.normal(size=N + 1)
+    phi, _ = poisson(rho, dx, eps0)
+    M = N - 1
+    ab = np.zeros((3, M))
+    ab[0, 1:] = -1.0
+    ab[1, :] = 2.0
+    ab[2, :-1] = -1.0
+    ref = solve_banded((1, 1), ab, dx * dx * rho[1:N] / eps0)
+    cond = 4.0 * N * N / np.pi ** 2
+    tol = 8 * cond * np.finfo(float).eps * np.abs(ref).max()
+    assert np.abs(phi[1:N] - ref).max() < tol
+
+
+@pytest.mark.parametrize("N", [4, 100, 1000, 65536])
 def test_poisson_uniform_charge_closed_form(N):
     dx, eps0, rho0 = 0.5, 1.0, 0.7
     L = N * dx
@@ -38,12 +109,13 @@ def test_poisson_uniform_charge_closed_form(N):
     phi, E = poisson(rho, dx, eps0)
     x = np.arange(N + 1) * dx
     exact = rho0 * x * (L - x) / (2 * eps0)
-    # forward error of any backward-stable solve: ~ cond(A) eps, cond(A) ~ N^2
-    tol = 4 * N * N * np.finfo(float).eps
+    # the oracle's solution is the exact one rounded once; the closed form evaluated
+    # in FP64 adds a few roundings of its own
+    tol = 4 * np.finfo(float).eps
     np.testing.assert_allclose(phi, exact, rtol=0, atol=tol * np.abs(exact).max())
     # E = -dphi/dx = rho0 (x - L/2) / eps0, also at both walls
     np.testing.assert_allclose(E, rho0 * (x - L / 2) / eps0, rtol=0,
-                               atol=tol * np.abs(exact).max() / dx)
+                               atol=tol * rho0 * L / eps0)
 
 
 def test_poisson_gauss_law_over_the_gap():
