@@ -131,6 +131,85 @@ class Clocks:
                 "samples": len(self.samples)}
 
 
+class NvmlClocks:
+    """NVML (through ctypes) sampling of the SM clock, its maximum and the clock-event
+    reasons every few milliseconds during the timed region, so that a region of a few
+    tens of milliseconds still gets many samples.  Raises if NVML is unavailable."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, dev: int, interval_s: float = 0.002):
+        import ctypes as C
+        self.C = C
+        L = C.CDLL("libnvidia-ml.so.1")
+        if L.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.L = L
+        h = C.c_void_p()
+        ok = False
+        try:  # the device torch uses, by UUID (CUDA and NVML indices may differ)
+            import torch
+            u = str(torch.cuda.get_device_properties(dev).uuid)
+            u = u if u.startswith("GPU-") else "GPU-" + u
+            ok = L.nvmlDeviceGetHandleByUUID(u.encode(), C.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok and L.nvmlDeviceGetHandleByIndex_v2(C.c_uint(dev), C.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.h = h
+        self.reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = C.c_uint()
+        self.max_mhz = float(mx.value) if L.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx)) == 0 else None
+        self.interval = interval_s
+        self.samples = []
+        self._stop = threading.Event()
+
+    def _one(self):
+        C = self.C
+        mhz, r = C.c_uint(), C.c_ulonglong()
+        if self.L.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) != 0:
+            return
+        if self.reasons_fn(self.h, C.byref(r)) != 0:
+            r.value = 0
+        self.samples.append((float(mhz.value), int(r.value)))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._one()
+            time.sleep(self.interval)
+
+    def __enter__(self):
+        self._one()
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=5)
+        self._one()
+
+    def summary(self):
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        sm = [m for m, _ in self.samples]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml"}
+
+
+def clock_sampler(dev: int):
+    """NVML sampling when the driver's library loads, else nvidia-smi."""
+    try:
+        return NvmlClocks(dev)
+    except Exception:
+        return Clocks(dev)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -217,13 +296,14 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
         return sum(sim.count(i, s) for i, p in enumerate(physs) for s in range(len(p.species)))
 
     live0 = live_total()
-    # timed region 1: the steps as pic_step runs them (CUDA-graph replay of whole sort
-    # cycles) -> value and ms_per_step
+    step0 = int(sim.moments(0)["step"])
+    # timed region 1: the steps as pic_step runs them (one CUDA-graph replay per window
+    # of steps inside a sort cycle) -> value and ms_per_step
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(dev) as clk:
+    with clock_sampler(dev) as clk:
         start.record()
         sim.step(steps)
         end.record()
@@ -286,6 +366,9 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
         "gpu_launches": kernels,
         "clocks": clk.summary(),
         "live": [live0, live1],
+        "first_timed_step": step0,
+        # steps of the window where every collision clock tests (multiples of 127)
+        "clock_test_steps": [t for t in range(step0, step0 + steps) if t % 127 == 0],
     }
 
 
@@ -397,7 +480,7 @@ def measure_small(args, stream):
         n1 = sum(sim.count(0, s) for s in range(2))
         sim.close()
         out[name] = {"value": (n0 + n1) / 2 * 1000 / (ms * 1e-3), "unit": UNIT,
-                     "us_per_step": ms, "steps": 1000}
+                     "us_per_step": ms * 1e3 / 1000, "steps": 1000}
     out["workload"] = "bounded_small: 256 cells, 100 ppc/species, 51,200 particles, 1000 steps"
     return out
 
@@ -624,28 +707,34 @@ def _run_ours(args, stream, rank, world, local):
                "sample": "FP64 CPU oracle, %d time steps of a %d-cell slice (%d particles, same "
                          "ppc and physics) of the workload, %.1f s" % (k, args.cpu_cells, ns, el)}
     if rank == 0:
+        roof = dict(res["roofline"])
+        if fp64:  # the FP64 form beside the FP32 one (the metric names both forms)
+            r64 = fp64["roofline"]
+            roof.update({"fp64_value": fp64["value"], "fp64_ms_per_step": fp64["ms_per_step"],
+                         "fp64_bound": r64["bound"], "fp64_frac": r64["frac"],
+                         "fp64_hbm_frac": r64["hbm"]["frac_of_measured"] if "hbm" in r64
+                         else r64["frac"]})
         line = {
             "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "bounded_large: %d cells, %d particles/cell/species, e+i "
-                                   "(m_i/m_e 100), elastic + charge-exchange MCC at 0.01 w_pe, "
-                                   "grounded absorbing walls, FP32 state, int64 fixed-point deposit, "
-                                   "FP64 Poisson, sort every %d steps" % (args.cells, args.ppc, args.sort),
+            "config": {"workload": "bounded_large: %d cells x %d ppc x (e, i), m_i/m_e 100, elastic + "
+                                   "CX at 0.01, absorbing walls" % (args.cells, args.ppc),
+                       "state": "FP32 particles, int64 fixed-point deposit, FP64 field",
                        "particles_per_gpu": n, "cells": args.cells, "sort_interval": args.sort,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state %.1f GB per GPU > L2 (no flush needed)" % (n * 24 / 1e9),
-                       "timing": "value: the timed steps as pic_step runs them (CUDA-graph replay of "
-                                 "sort cycles); roofline and kernel_ms: a second timed region of as "
-                                 "many steps with a CUDA event pair around every kernel"},
-            "roofline": res["roofline"],
+                       "timing": "value: pic_step as called (graph replay per window of a sort "
+                                 "cycle); roofline: 2nd region, events per kernel",
+                       "first_timed_step": res["first_timed_step"],
+                       "clock_test_steps_timed": res["clock_test_steps"]},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps,
-                    "what": "pic_load_particles_f32 from pinned host + %d steps + pic_moments + "
-                            "pic_get_particles_f32 to pinned host (the FP32 form's data as float: "
-                            "24 B per particle each way); median of 3 passes" % args.steps,
+                    "what": "load_f32 from pinned host + %d steps + moments + get_f32 to pinned "
+                            "host; median of 3" % args.steps,
                     "breakdown": e2e_parts},
             "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"],
@@ -657,6 +746,25 @@ def _run_ours(args, stream, rank, world, local):
             "small": small,
             "setup_s": setup_s,
         }
+        # compact copies of the other forms' and workloads' headline numbers, last on the
+        # line so that they are in any tail of the output
+        if fp64:
+            line["fp64_value"] = fp64["value"]
+            line["fp64_frac"] = roof["fp64_frac"]
+            line["fp64_bound"] = roof["fp64_bound"]
+        if paper:
+            for f in ("fp32", "fp64"):
+                line["paper_%s_value" % f] = paper[f]["value"]
+                line["paper_%s_frac" % f] = paper[f]["roofline"]["frac"]
+        if batched:
+            line["batched_value"] = batched["value"]
+            line["batched_frac"] = batched["roofline"]["frac"]
+        if subcycled:
+            line["subcycled_value"] = subcycled["value"]
+        if small:
+            line["small_fp32_us_per_step"] = small["fp32"]["us_per_step"]
+        line["fp32_frac"] = res["roofline"]["frac"]
+        line["clocks_samples"] = res["clocks"].get("samples")
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -216,8 +216,10 @@ PIC_API int pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int6
                               uint32_t* id, uint8_t* state, int32_t flags, int64_t* n_out);
 
 /* pic_get_particles into float offsets and velocities (each value formed in double, as
- * pic_get_particles returns it, and rounded once to float; an FP64-form offset just
- * below 1 can round to 1).  Same arguments and errors otherwise. */
+ * pic_get_particles returns it, and rounded once to float).  An FP64-form offset so
+ * close to 1 that it would round to 1.0f is returned as the largest float below 1
+ * (1 - 2^-24) in the same cell, so every read-back loads again.  Same arguments and
+ * errors otherwise. */
 PIC_API int pic_get_particles_f32(pic_handle* h, int32_t inst, int32_t species,
                                   int64_t capacity, int32_t* cell, float* off, float* vx,
                                   float* vy, float* vz, uint32_t* id, uint8_t* state,
@@ -265,9 +267,11 @@ PIC_API int pic_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t
  * captured, latency-critical loops in which an allocation could block or fragment,
  * and host frameworks that own all device memory through their own pools).
  * Computes, for one instance of `ncells` cells (at most 65536), the field E on nodes
- * 0..ncells from its fixed-point charge deposits, exactly as the handle's field phase
- * does: the grounded Dirichlet Poisson problem solved in 128-bit integers, E = -grad
- * phi with Gauss's law over the wall half cells.
+ * 0..ncells from its fixed-point charge deposits with the same arithmetic as the
+ * handle's field phase: the grounded Dirichlet Poisson problem solved in 128-bit
+ * integers, E = -grad phi with Gauss's law over the wall half cells.  The deposits are
+ * used as given: no density smoother is applied, so for an instance created with
+ * smooth = 1 the result is the field of the unfiltered charge, not the handle's E.
  *   charge  device array, nspecies x (ncells+1) int64, species-major: the per-node
  *           deposits in units where one particle adds `unit` (the layout and unit
  *           pic_charge_raw returns);
@@ -275,9 +279,11 @@ PIC_API int pic_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t
  *   eps0    vacuum permittivity;  E  device array of ncells+1 doubles (output);
  *   stream  borrowed cudaStream_t (NULL = default stream); the call only enqueues.
  * Allocates nothing: its scratch (one 128-bit sum per node) is a static device array
- * of the library, 1 MB on every GPU that loads it, held until the process exits.  The
- * first call on a device looks up that array's device address (with the device
- * current), so make the first call before any stream capture.  Every call on a device
+ * of the library, 1 MB on every GPU that loads it, held until the process exits.  A
+ * call whose stream is not capturing looks up that array's device address for the
+ * current device (so a device reset between calls is harmless); a call made while its
+ * stream is being captured reuses the address of the last such lookup on the device,
+ * so make the first call on a device before any stream capture.  Every call on a device
  * shares the array: calls that overlap on the GPU (other streams, other threads) race
  * and must be serialised by the caller.  Returns PIC_EINVAL for ncells outside
  * [1, 65536] or bad arguments, PIC_ECUDA if a launch fails; the message is available

@@ -32,15 +32,25 @@
  * and the file is compiled without floating-point contraction; the fused operations
  * are the explicit fma() calls of the gather and the Boris cross products (the paper
  * does not fix how a product-sum rounds; a C compiler on FMA hardware contracts it to
- * one rounding).  The Poisson solve runs in binary128 and rounds its results to FP64
- * once, so the field is the exact solution of the discrete problem to within that
- * rounding (see orc_poisson).
+ * one rounding).  The density and field phases run in binary128 (the node sums of the
+ * CIC weights, the charge density, the Poisson solve and E) and round E and phi to
+ * FP64 once, so the field is the exact solution of the discrete problem for the
+ * particles' positions to within that rounding (see deposit() and orc_poisson).
  */
 #include "oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* IEEE binary128 for the density and field phases: long double where it is binary128
+ * (aarch64 Linux), else GCC's _Float128 (x86_64; +, -, *, / in libgcc's soft float). */
+#if defined(__LDBL_MANT_DIG__) && __LDBL_MANT_DIG__ == 113
+typedef long double quad;
+#else
+typedef _Float128 quad;
+#endif
+_Static_assert(sizeof(quad) == 16, "binary128 expected");
 
 #define TWO_PI 6.283185307179586476925286766559
 #define ORC_GAP_MAX 127
@@ -151,9 +161,10 @@ struct orc_sim {
     int64_t* tfirst;
     int64_t tcap;
     /* grid */
-    double* dens;   /* nspecies * (N+1): summed CIC weights per node */
+    quad* dens;     /* nspecies * (N+1): summed CIC weights per node (binary128) */
     double* A;      /* nspecies * (N+1): pre-scaled acceleration on nodes */
-    double *phi, *E, *rho;
+    double *phi, *E;
+    quad* rho;      /* N+1: charge density of the field phase (binary128) */
     int fields_ready;
     /* counters */
     int64_t wall_count[ORC_MAX_SPECIES][2];
@@ -218,11 +229,11 @@ orc_sim* orc_create(const orc_params* p)
     s->p = *p;
     s->N = p->ncells;
     const int N = s->N, S = p->nspecies;
-    s->dens = (double*)calloc((size_t)S * (N + 1), sizeof(double));
+    s->dens = (quad*)calloc((size_t)S * (N + 1), sizeof(quad));
     s->A = (double*)calloc((size_t)S * (N + 1), sizeof(double));
     s->phi = (double*)calloc((size_t)(N + 1), sizeof(double));
     s->E = (double*)calloc((size_t)(N + 1), sizeof(double));
-    s->rho = (double*)calloc((size_t)(N + 1), sizeof(double));
+    s->rho = (quad*)calloc((size_t)(N + 1), sizeof(quad));
     if (!s->dens || !s->A || !s->phi || !s->E || !s->rho) {
         orc_destroy(s);
         return NULL;
@@ -338,19 +349,23 @@ int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const doubl
 
 /* ------------------------------------------------------------------------- */
 /* Density phase: cloud-in-cell weights, (1-f) to node j and f to node j+1, summed in
- * ascending id order per species. */
+ * ascending id order per species.  The weights and their sums are carried in binary128:
+ * 1 - f is exact there, and a node's sum of a few thousand weights of 53 bits stays
+ * within the 113-bit significand, so the node densities are the exact sums (an FP64
+ * sum of n weights errs by ~sqrt(n) ulp per node, which the field integrates over the
+ * N nodes). */
 static void deposit(orc_sim* s)
 {
     const int N = s->N;
     for (int sp = 0; sp < s->p.nspecies; ++sp) {
-        double* d = s->dens + (size_t)sp * (N + 1);
-        for (int j = 0; j <= N; ++j) d[j] = 0.0;
+        quad* d = s->dens + (size_t)sp * (N + 1);
+        for (int j = 0; j <= N; ++j) d[j] = 0;
         const orc_store* a = &s->st[sp];
         for (int64_t k = 0; k < a->n; ++k) {
             if (!a->alive[k]) continue;
             const int j = a->cell[k];
-            const double f = a->off[k];
-            d[j] += 1.0 - f;
+            const quad f = (quad)a->off[k];
+            d[j] += (quad)1 - f;
             d[j + 1] += f;
         }
         if (s->p.bc == ORC_BC_PERIODIC) { /* node N is node 0 */
@@ -360,18 +375,10 @@ static void deposit(orc_sim* s)
     }
 }
 
-/* IEEE binary128 for the field solve: long double where it is binary128 (aarch64
- * Linux), else GCC's _Float128 (x86_64; +, -, *, / in libgcc's soft float). */
-#if defined(__LDBL_MANT_DIG__) && __LDBL_MANT_DIG__ == 113
-typedef long double quad;
-#else
-typedef _Float128 quad;
-#endif
-_Static_assert(sizeof(quad) == 16, "binary128 expected");
-
-int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* phi, double* E)
+/* The Poisson solve and E of the field phase for a binary128 charge density (see
+ * orc_poisson). */
+static int poisson_q(int32_t N, double dx, double eps0, const quad* rho, double* phi, double* E)
 {
-    if (N < 1 || !rho || !phi || !E || !(dx > 0) || !(eps0 > 0)) return -1;
     const int M = N - 1; /* interior unknowns phi[1..N-1] */
     /* The Thomas algorithm is backward stable, but its forward error in phi grows with
      * the condition number of the tridiagonal matrix (~N^2): in FP64 it reaches ~1e-11
@@ -390,9 +397,9 @@ int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* ph
         const quad a = -1, b = 2, c = -1;
         const quad h2 = (quad)dx * (quad)dx / (quad)eps0;
         cp[1] = c / b;
-        dp[1] = h2 * (quad)rho[1] / b;
+        dp[1] = h2 * rho[1] / b;
         for (int i = 2; i <= M; ++i) {
-            const quad di = h2 * (quad)rho[i];
+            const quad di = h2 * rho[i];
             const quad m = b - a * cp[i - 1];
             cp[i] = c / m;
             dp[i] = (di - a * dp[i - 1]) / m;
@@ -404,8 +411,8 @@ int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* ph
      * next to the wall, whose charge per area is rho_wall * dx/2. */
     const quad qdx = (quad)dx, half = (quad)dx / (2 * (quad)eps0);
     for (int j = 1; j < N; ++j) E[j] = (double)((q[j - 1] - q[j + 1]) / (2 * qdx));
-    E[0] = (double)(-(q[1] - q[0]) / qdx - (quad)rho[0] * half);
-    E[N] = (double)(-(q[N] - q[N - 1]) / qdx + (quad)rho[N] * half);
+    E[0] = (double)(-(q[1] - q[0]) / qdx - rho[0] * half);
+    E[N] = (double)(-(q[N] - q[N - 1]) / qdx + rho[N] * half);
     for (int j = 0; j <= N; ++j) phi[j] = (double)q[j];
     free(q);
     free(cp);
@@ -413,20 +420,44 @@ int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* ph
     return 0;
 }
 
-/* Field phase: charge density from the deposit, Poisson solve, then the pre-scaled
- * accelerations A_s = c_s E used by the gather. */
+int orc_poisson(int32_t N, double dx, double eps0, const double* rho, double* phi, double* E)
+{
+    if (N < 1 || !rho || !phi || !E || !(dx > 0) || !(eps0 > 0)) return -1;
+    quad* r = (quad*)malloc((size_t)(N + 1) * sizeof(quad));
+    if (!r) return -2;
+    for (int j = 0; j <= N; ++j) r[j] = (quad)rho[j];
+    const int rc = poisson_q(N, dx, eps0, r, phi, E);
+    free(r);
+    return rc;
+}
+
 /* Density smoother (Section 2's "Density Smoother" phase): a 1-2-1 binomial filter
  * of the interior node densities rho[1..N-1], the wall nodes (half cells) kept. */
-void orc_smooth(int32_t N, double* rho)
+static void smooth_q(int32_t N, quad* rho)
 {
     if (N < 2) return;
-    double prev = rho[0];
+    const quad quarter = (quad)0.25, halfq = (quad)0.5;
+    quad prev = rho[0];
     for (int j = 1; j < N; ++j) {
-        const double cur = rho[j];
-        rho[j] = 0.25 * prev + 0.5 * cur + 0.25 * rho[j + 1];
+        const quad cur = rho[j];
+        rho[j] = quarter * prev + halfq * cur + quarter * rho[j + 1];
         prev = cur;
     }
 }
+
+void orc_smooth(int32_t N, double* rho)
+{
+    if (N < 2) return;
+    quad* r = (quad*)malloc((size_t)(N + 1) * sizeof(quad));
+    if (!r) return;
+    for (int j = 0; j <= N; ++j) r[j] = (quad)rho[j];
+    smooth_q(N, r);
+    for (int j = 0; j <= N; ++j) rho[j] = (double)r[j];
+    free(r);
+}
+
+/* Field phase: charge density from the deposit, Poisson solve, then the pre-scaled
+ * accelerations A_s = c_s E used by the gather. */
 
 static int solve_fields(orc_sim* s)
 {
@@ -434,21 +465,22 @@ static int solve_fields(orc_sim* s)
     const double dx = s->p.dx;
     if (s->p.field == ORC_FIELD_POISSON) {
         for (int j = 0; j <= N; ++j) {
-            double q = 0.0;
+            quad q = 0;
             for (int sp = 0; sp < S; ++sp)
-                q += s->p.sp[sp].charge * s->p.sp[sp].weight * s->dens[(size_t)sp * (N + 1) + j];
+                q += (quad)s->p.sp[sp].charge * (quad)s->p.sp[sp].weight *
+                     s->dens[(size_t)sp * (N + 1) + j];
             /* interior node: cell volume dx; wall node: half cell */
-            s->rho[j] = (j == 0 || j == N) ? q / (0.5 * dx) : q / dx;
+            s->rho[j] = (j == 0 || j == N) ? q / ((quad)0.5 * (quad)dx) : q / (quad)dx;
         }
-        if (s->p.smooth) orc_smooth(N, s->rho);
-        int rc = orc_poisson(N, dx, s->p.eps0, s->rho, s->phi, s->E);
+        if (s->p.smooth) smooth_q(N, s->rho);
+        int rc = poisson_q(N, dx, s->p.eps0, s->rho, s->phi, s->E);
         if (rc) return rc;
     } else {
         const double e = s->p.field == ORC_FIELD_EXTERNAL ? s->p.E_ext : 0.0;
         for (int j = 0; j <= N; ++j) {
             s->E[j] = e;
             s->phi[j] = -e * ((double)j * dx);
-            s->rho[j] = 0.0;
+            s->rho[j] = 0;
         }
     }
     for (int sp = 0; sp < S; ++sp)
@@ -955,11 +987,11 @@ int orc_moments_get(orc_sim* s, orc_moments* m, double* density, double* phi, do
             m->wall_energy[sp][w] = s->wall_energy[sp][w];
         }
         if (density) {
-            const double* d = s->dens + (size_t)sp * (N + 1);
-            const double wdx = s->p.sp[sp].weight / s->p.dx;
+            const quad* d = s->dens + (size_t)sp * (N + 1);
+            const quad wdx = (quad)s->p.sp[sp].weight / (quad)s->p.dx;
             for (int j = 0; j <= N; ++j) {
                 const int wall = (j == 0 || j == N) && s->p.bc != ORC_BC_PERIODIC;
-                density[(size_t)sp * (N + 1) + j] = wall ? 2.0 * wdx * d[j] : wdx * d[j];
+                density[(size_t)sp * (N + 1) + j] = (double)(wall ? 2 * wdx * d[j] : wdx * d[j]);
             }
         }
     }

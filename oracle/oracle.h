@@ -122,7 +122,7 @@ int orc_moments_get(orc_sim* s, orc_moments* m, double* density, double* phi, do
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
 /* Density smoother: 1-2-1 binomial filter of rho[1..N-1] in place (N+1 entries; the
- * wall entries rho[0], rho[N] are kept). */
+ * wall entries rho[0], rho[N] are kept), formed in binary128 and rounded once. */
 void orc_smooth(int32_t N, double* rho);
 
 /* Dirichlet Poisson problem of the field phase: -phi[j-1]+2phi[j]-phi[j+1] =

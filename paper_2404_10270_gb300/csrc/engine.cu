@@ -28,6 +28,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <sys/stat.h>
@@ -140,10 +141,18 @@ struct pic_handle {
     std::string tune_key;
     char gpu_name[256] = {0};
 
-    // CUDA graphs of one sort cycle (sort_interval steps + the sort), one per store copy
+    // CUDA graphs of the step windows pic_step has run: a window is a run of steps
+    // inside one sort cycle (at most to its sort step), keyed by the store copy it
+    // starts from, its first step's place in the cycle, its length and whether the step
+    // before it counted cells for the sort; each records the host state it ends in
+    struct Window {
+        cudaGraphExec_t exec = nullptr;
+        int end_cur = 0;
+        bool end_hist = false;
+        int64_t kernels = 0;
+    };
     bool graphs = true;
-    cudaGraphExec_t cycle[2] = {nullptr, nullptr};
-    int64_t cycle_kernels = 0;
+    std::map<std::tuple<int, int64_t, int64_t, bool>, Window> windows;
     bool profiling = false;
     struct Timed { int cls; cudaEvent_t a, b; };
     std::vector<Timed> timed;
@@ -656,11 +665,9 @@ void set_block(pic_handle* h, int nt)
 
 void drop_graphs(pic_handle* h)
 {
-    for (auto& g : h->cycle)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
+    for (auto& kv : h->windows)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    h->windows.clear();
 }
 
 // ---- autotuner ----------------------------------------------------------------------
@@ -1263,24 +1270,27 @@ int enqueue_step(pic_handle* h)
     return PIC_OK;
 }
 
-// Capture one sort cycle starting from store copy h->cur: sort_interval steps whose
-// last one ends with the sort (which makes the other copy current).  Every kernel
-// reads the step count and segment sizes from device memory, so the same graph
-// replays every cycle that starts from this copy.
-int capture_cycle(pic_handle* h)
+// Capture `len` steps from the current state (store copy h->cur, step h->step_h,
+// hist_ready) as one graph.  Every kernel reads the step count and segment sizes from
+// device memory, so the same graph replays every window that starts from the same copy
+// at the same place of a sort cycle.  The host state is put back; the window records
+// the state its steps end in.
+int capture_window(pic_handle* h, int64_t len, pic_handle::Window* w)
 {
     const int c0 = h->cur;
     const bool hr0 = h->hist_ready;
     const int64_t step0 = h->step_h, k0 = h->kernels;
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = PIC_OK;
-    for (int n = 0; n < h->sort_interval && rc == PIC_OK; ++n) rc = enqueue_step(h);
+    for (int64_t n = 0; n < len && rc == PIC_OK; ++n) rc = enqueue_step(h);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    w->end_cur = h->cur;
+    w->end_hist = h->hist_ready;
+    w->kernels = h->kernels - k0;
     h->step_h = step0;
     h->cur = c0;
     h->hist_ready = hr0;
-    h->cycle_kernels = h->kernels - k0;
     h->kernels = k0;
     if (rc != PIC_OK) {
         if (g) cudaGraphDestroy(g);
@@ -1294,7 +1304,7 @@ int capture_cycle(pic_handle* h)
     const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) return fail(h, PIC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
-    h->cycle[c0] = ex;
+    w->exec = ex;
     return PIC_OK;
 }
 
@@ -1353,14 +1363,26 @@ int pic_step(pic_handle* h, int64_t nsteps)
         }
         const bool graphs = h->graphs && !h->profiling && !h->tune_phase && K > 0 &&
                             h->stream != nullptr;
-        if (graphs && h->step_h % K == 0 && nsteps - n >= K) {
-            if (!h->cycle[h->cur] && (rc = capture_cycle(h))) return rc;
-            CUDA_TRY(h, cudaGraphLaunch(h->cycle[h->cur], h->stream));
-            h->kernels += h->cycle_kernels;
-            h->step_h += K;
-            h->cur = 1 - h->cur;
-            h->hist_ready = false;
-            n += K;
+        if (graphs) {
+            // the steps up to the end of this sort cycle (or of the call) as one graph
+            const int64_t p = h->step_h % K;
+            const int64_t len = std::min<int64_t>(K - p, nsteps - n);
+            const auto key = std::make_tuple(h->cur, p, len, h->hist_ready);
+            auto it = h->windows.find(key);
+            if (it == h->windows.end()) {
+                // a call pattern that keeps creating new windows (several sort
+                // intervals' worth of lengths) starts the cache over
+                if (h->windows.size() >= 256) drop_graphs(h);
+                pic_handle::Window w;
+                if ((rc = capture_window(h, len, &w))) return rc;
+                it = h->windows.emplace(key, w).first;
+            }
+            CUDA_TRY(h, cudaGraphLaunch(it->second.exec, h->stream));
+            h->kernels += it->second.kernels;
+            h->step_h += len;
+            h->cur = it->second.end_cur;
+            h->hist_ready = it->second.end_hist;
+            n += len;
             continue;
         }
         if ((rc = enqueue_step(h))) return rc;

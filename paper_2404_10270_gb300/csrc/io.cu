@@ -145,7 +145,12 @@ __global__ void k_get_write(const GetArgs g)
     if (g.cell) g.cell[o] = (int)(word & kCellMask);
     if (g.state) g.state[o] = (uint8_t)(word >> kClockShift);
     // in double, then rounded once to the caller's type
-    if (g.off) static_cast<H*>(g.off)[o] = (H)(double)static_cast<const T*>(g.s_off)[s];
+    if (g.off) {
+        H fo = (H)(double)static_cast<const T*>(g.s_off)[s];
+        // a double offset that rounds up to 1 in float stays in its cell, just below 1
+        if (fo >= H(1)) fo = (H)0.99999994f;
+        static_cast<H*>(g.off)[o] = fo;
+    }
     if (g.vx) static_cast<H*>(g.vx)[o] = (H)((double)static_cast<const T*>(g.s_ux)[s] * g.vscale_inv);
     if (g.vy) static_cast<H*>(g.vy)[o] = (H)((double)static_cast<const T*>(g.s_uy)[s] * g.vscale_inv);
     if (g.vz) static_cast<H*>(g.vz)[o] = (H)((double)static_cast<const T*>(g.s_uz)[s] * g.vscale_inv);

@@ -8,7 +8,8 @@
 // fixed-point charge deposits and the output array; the only scratch the solve
 // needs (one 128-bit prefix sum per node and one 128-bit total) lives in the
 // file-scope device array below, which every GPU that loads the library holds
-// until the process exits.  The math is the same as the handle's field phase:
+// until the process exits.  The math is the same as the handle's field phase (without
+// its optional density smoother: the deposits are used as given):
 //   Z_j = sum_s z_s D_s[j],  R_j = sum_{1<=k<=j, k<N} Z_k,  U = sum_{1<=k<N} (N-k) Z_k,
 //   E_j = lambda (N (R_{j-1} + R_j) - 2U)      (0 < j < N),
 //   E_0 = lambda (-2U - 2N Z_0),  E_N = lambda (2N R_{N-1} - 2U + 2N Z_N),
@@ -28,7 +29,8 @@ constexpr int kMaxDevices = 64;
 // Scratch shared by every call on a device: R_j for j = 0..N, then U.
 static __device__ __align__(256) i128 g_scratch[kNoAllocMaxNodes + 1];
 
-// Device address of g_scratch per device, looked up once with that device current.
+// Device address of g_scratch per device, from the last lookup made with that device
+// current and no capture in progress on the call's stream.
 std::mutex g_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
@@ -68,7 +70,9 @@ __device__ __forceinline__ i128 charge_at(const NoAllocArgs& a, int j)
     return z;
 }
 
-// One block of 1024 threads: R (inclusive prefix of the interior charge) and U.
+// One block of 1024 threads: R (inclusive prefix of the interior charge) and U.  Each
+// thread owns C consecutive nodes; their interior charges Z_j are formed once, kept in
+// the scratch slots R_j until the prefix overwrites them.
 __global__ void __launch_bounds__(1024) k_scan_noalloc(const NoAllocArgs a)
 {
     __shared__ i128 sh[33];
@@ -78,8 +82,8 @@ __global__ void __launch_bounds__(1024) k_scan_noalloc(const NoAllocArgs a)
     const int j0 = min(nn, (int)threadIdx.x * C), j1 = min(nn, j0 + C);
     i128 sum = 0, wsum = 0;
     for (int j = j0; j < j1; ++j) {
-        if (j == 0 || j == N) continue;
-        const i128 z = charge_at(a, j);
+        const i128 z = (j == 0 || j == N) ? (i128)0 : charge_at(a, j);
+        a.scratch[j] = z;
         sum += z;
         wsum += (i128)(N - j) * z;
     }
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(1024) k_scan_noalloc(const NoAllocArgs a)
         if (lane == 0) a.scratch[N + 1] = t;
     }
     for (int j = j0; j < j1; ++j) {
-        if (j != 0 && j != N) run += charge_at(a, j);
+        run += a.scratch[j];
         a.scratch[j] = run;
     }
 }
@@ -126,9 +130,12 @@ __global__ void k_emit_noalloc(const NoAllocArgs a)
     a.E[j] = a.lambda * i128_to_double(G);
 }
 
-// Set-up, once per device and with that device current: the device address of the
-// scratch array.  Host code must not hand the symbol itself to a kernel.
-int scratch_for_current_device(void** out, std::string* why)
+// The device address of the scratch array for the current device.  Host code must not
+// hand the symbol itself to a kernel.  Outside stream capture the address is looked up
+// on every call (cheap; a device reset or a new context reloads the module at another
+// address); during a capture the lookup could load the module inside it, so the address
+// of the last lookup on this device is reused and a first call under capture fails.
+int scratch_for_current_device(cudaStream_t st, void** out, std::string* why)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -140,8 +147,14 @@ int scratch_for_current_device(void** out, std::string* why)
         *why = "device index out of range";
         return PIC_EINVAL;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) {
+        *why = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e);
+        return PIC_ECUDA;
+    }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
@@ -149,6 +162,9 @@ int scratch_for_current_device(void** out, std::string* why)
             return PIC_ECUDA;
         }
         g_scratch_addr[dev] = p;
+    } else if (!g_scratch_addr[dev]) {
+        *why = "the first call on a device must not be made during stream capture";
+        return PIC_EINVAL;
     }
     *out = g_scratch_addr[dev];
     return PIC_OK;
@@ -181,7 +197,8 @@ extern "C" PIC_API int pic_field_solve_noalloc(int32_t ncells, int32_t nspecies,
     }
     void* scratch = nullptr;
     std::string why;
-    const int rc = scratch_for_current_device(&scratch, &why);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rc = scratch_for_current_device(st, &scratch, &why);
     if (rc != PIC_OK) {
         set_global_error("pic_field_solve_noalloc: " + why);
         return rc;
@@ -194,7 +211,6 @@ extern "C" PIC_API int pic_field_solve_noalloc(int32_t ncells, int32_t nspecies,
     a.lambda = delta / (2.0 * (double)ncells * (double)unit * eps0);
     a.scratch = static_cast<i128*>(scratch);
     a.E = E;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_scan_noalloc<<<1, 1024, 0, st>>>(a);
     k_emit_noalloc<<<(ncells + 1 + 255) / 256, 256, 0, st>>>(a);
     const cudaError_t e = cudaGetLastError();

@@ -7,7 +7,6 @@ import numpy as np
 import pytest
 
 from paper_2404_10270_gb300 import capi
-from paper_2404_10270_gb300 import workloads as W
 
 
 def gpu_available() -> bool:
@@ -77,43 +76,3 @@ def particle_errors(phys, gpu_parts, ora_parts):
         ev = (dv / np.maximum(vref, vth)).max()
         res.append((ex, ev))
     return res
-
-
-def oracle_with_ionization_record(phys, loads, steps):
-    """Oracle run that also returns the ids of every ionization participant: products
-    (ids beyond the load) and electrons that lost more than the threshold energy in one
-    step (the parents).  Ionization gives both outgoing electrons the speed
-    sqrt((E - E_iz)/m), which near threshold amplifies the incident energy's rounding by
-    E/(E - E_iz); tests hold these particles to a wider bound."""
-    from oracle.oracle import Oracle
-    o = Oracle(phys)
-    o.load_all(loads)
-    n0 = sum(len(x) for x in loads)
-    eiz = max([q.threshold for q in phys.processes if q.kind == W.PROC_IONIZE] + [0.0])
-    m_e = phys.species[0].mass
-    prev = by_id(o.particles(0))
-    parents = set()
-    for _ in range(steps):
-        o.step(1)
-        cur = by_id(o.particles(0))
-        old = cur["id"] < n0
-        idx = np.searchsorted(prev["id"], cur["id"][old])
-        e0 = 0.5 * m_e * (prev["vx"][idx] ** 2 + prev["vy"][idx] ** 2 + prev["vz"][idx] ** 2)
-        e1 = 0.5 * m_e * (cur["vx"][old] ** 2 + cur["vy"][old] ** 2 + cur["vz"][old] ** 2)
-        parents.update(cur["id"][old][e0 - e1 > eiz * (1 - 1e-6)].tolist())
-        prev = cur
-    return [o.particles(s) for s in range(2)], o.moments(), n0, parents
-
-
-def ionization_errors(phys, g, o, s, n0, parents):
-    g, o = by_id(g), by_id(o)
-    np.testing.assert_array_equal(g["id"], o["id"])
-    xg = (g["cell"] + g["off"]) * phys.dx
-    xo = (o["cell"] + o["off"]) * phys.dx
-    ex = np.abs(xg - xo) / phys.length
-    vth = (phys.species[s].temperature / phys.species[s].mass) ** 0.5
-    dv = np.sqrt((g["vx"] - o["vx"]) ** 2 + (g["vy"] - o["vy"]) ** 2 + (g["vz"] - o["vz"]) ** 2)
-    vref = np.sqrt(o["vx"] ** 2 + o["vy"] ** 2 + o["vz"] ** 2)
-    ids = o["id"]
-    involved = (ids >= n0) | np.isin(ids, np.fromiter(parents, np.int64, len(parents)))
-    return ids, ex, dv / np.maximum(vref, vth), involved

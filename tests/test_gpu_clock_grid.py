@@ -7,16 +7,14 @@ These runs cross that grid against the oracle: FP64 over 300 steps (grid steps 1
 and 254), ions subcycled by 4 over 520 steps (their own grid at step 511), and the
 FP32 form from a state saved at step 120 over 10 steps across step 127.  Integer state
 (collision clocks, collision counts, wall counts, live counts) must be identical;
-particles within the form's tolerance (FP64 1e-12, FP32 1e-5; ionization participants
-at 100x, see test_gpu_ensemble).
+every particle within the form's tolerance (FP64 1e-12, FP32 1e-5).
 """
 import numpy as np
 import pytest
 
 from paper_2404_10270_gb300 import capi
 from paper_2404_10270_gb300 import workloads as W
-from tests.gpu_common import (assert_same_clocks, by_id, ensure_built, ionization_errors,
-                              oracle_with_ionization_record, particle_errors, requires_gpu,
+from tests.gpu_common import (assert_same_clocks, ensure_built, particle_errors, requires_gpu,
                               run_gpu, run_oracle)
 
 pytestmark = [pytest.mark.gpu, requires_gpu]
@@ -48,15 +46,12 @@ def test_magnetized_source_fp64_300_steps():
     g = [sim.particles(0, s) for s in range(2)]
     gm = sim.moments(0)
     sim.close()
-    o, om, n0, parents = oracle_with_ionization_record(phys, loads, 300)
+    o, om = run_oracle(phys, loads, 300)
     _check_integers(gm, om)
     assert om["collisions"][1] > 0
     assert_same_clocks(g, o)
-    for s in range(2):
-        ids, ex, ev, involved = ionization_errors(phys, g[s], o[s], s, n0, parents)
-        assert ex.max() < 1e-12, (s, ex.max())
-        assert ev[~involved].max(initial=0.0) < 1e-12, (s, ev[~involved].max())
-        assert ev[involved].max(initial=0.0) < 1e-10, (s, ev[involved].max())
+    for s, (ex, ev) in enumerate(particle_errors(phys, g, o)):
+        assert ex < 1e-12 and ev < 1e-12, (s, ex, ev)
 
 
 def test_subcycled_ions_fp64_cross_their_own_grid():

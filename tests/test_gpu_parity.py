@@ -193,29 +193,36 @@ def test_results_do_not_depend_on_launch_shape_or_sort_interval():
         np.testing.assert_array_equal(ref[1]["collisions"], cur[1]["collisions"])
 
 
-def test_graph_replay_equals_direct_launches():
-    """pic_step replays a captured CUDA graph per sort cycle; with kernel timing on it
-    launches kernels one by one.  Both give identical results."""
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_graph_replay_equals_direct_launches(precision):
+    """pic_step replays one captured CUDA graph per window of steps inside a sort cycle
+    (cached by store copy, place in the cycle, length and whether the step before counted
+    cells for the sort); with kernel timing on it launches kernels one by one.  Calls of
+    3 + 17 steps, of one step at a time, and of mixed lengths that start mid-cycle all
+    give the direct launches' results."""
     ensure_built()
-    phys = W.magnetized_source(ncells=40, ppc=30, seed=14, nu=0.3, capacity_factor=3.0)
+    phys = W.magnetized_source(ncells=40, ppc=30, seed=14, nu=0.3, capacity_factor=3.0,
+                               B=2.0 if precision == capi.FP64 else 0.0)
     loads = W.initial_load(phys, seed=14)
     out = []
-    for profile in (False, True):
-        sim = capi.Sim(phys, precision=capi.FP64, sort_interval=4)
+    for calls in ("profile", (3, 17), (1,) * 20, (2, 5, 1, 6, 3, 3)):
+        sim = capi.Sim(phys, precision=precision, sort_interval=4)
         sim.load_all(loads)
-        if profile:
+        if calls == "profile":
             sim.profile(True)
-        sim.step(3)   # not aligned to the cycle: direct launches first
-        sim.step(17)  # four cycles through the graphs (when not profiling)
+            calls = (3, 17)
+        for n in calls:
+            sim.step(n)
         out.append(([by_id(sim.particles(0, s)) for s in range(2)], sim.moments(0)))
         sim.close()
-    (a, am), (b, bm) = out
-    for x, y in zip(a, b):
-        for k in x:
-            np.testing.assert_array_equal(x[k], y[k])
-    np.testing.assert_array_equal(am["E"], bm["E"])
-    np.testing.assert_array_equal(am["collisions"], bm["collisions"])
-    assert am["step"] == bm["step"] == 20
+    a, am = out[0]
+    for b, bm in out[1:]:
+        for x, y in zip(a, b):
+            for k in x:
+                np.testing.assert_array_equal(x[k], y[k])
+        np.testing.assert_array_equal(am["E"], bm["E"])
+        np.testing.assert_array_equal(am["collisions"], bm["collisions"])
+        assert am["step"] == bm["step"] == 20
 
 
 def test_autotuner_changes_nothing_but_speed(tmp_path, monkeypatch):
@@ -498,9 +505,7 @@ def test_rare_event_queue_overflow_is_reported():
 def test_magnetized_source_full_size(precision, steps, tol):
     """The magnetized workload at its full size: 4096 cells x 200 particles/cell/species
     (1,638,400 particles), oblique B, volume source, elastic + ionization + charge
-    exchange.  FP64 bound 1e-12, FP32 1e-5; ionization participants at 100x
-    (ill-conditioned near-threshold energy split)."""
-    from tests.gpu_common import ionization_errors, oracle_with_ionization_record
+    exchange.  FP64 bound 1e-12, FP32 1e-5, for every particle."""
     ensure_built()
     phys = W.magnetized_source(seed=1)
     loads = W.initial_load(phys, seed=1)
@@ -510,15 +515,12 @@ def test_magnetized_source_full_size(precision, steps, tol):
     g = [sim.particles(0, s) for s in range(2)]
     gm = sim.moments(0)
     sim.close()
-    o, om, n0, parents = oracle_with_ionization_record(phys, loads, steps)
+    o, om = run_oracle(phys, loads, steps)
     np.testing.assert_array_equal(gm["live"], om["live"])
     if precision == capi.FP64:
         np.testing.assert_array_equal(gm["collisions"], om["collisions"])
         np.testing.assert_array_equal(gm["wall_count"], om["wall_count"])
-    t = tol
-    for s in range(2):
-        ids, ex, ev, involved = ionization_errors(phys, g[s], o[s], s, n0, parents)
-        assert ex.max() < t, (s, ex.max())
-        assert ev[~involved].max(initial=0.0) < t, (s, ev[~involved].max())
-        assert ev[involved].max(initial=0.0) < 100 * t, (s, ev[involved].max())
+    assert om["collisions"][1] > 0  # ionization happened
+    for s, (ex, ev) in enumerate(particle_errors(phys, g, o)):
+        assert ex < tol and ev < tol, (s, ex, ev)
     assert_same_clocks(g, o)

@@ -24,31 +24,77 @@ def _unit_and_z(phys):
     return delta, [int(round(x / delta)) for x in qw]
 
 
-@pytest.mark.parametrize("precision", [capi.FP32, capi.FP64])
-def test_noalloc_field_matches_handle_field(precision):
+def _rho_from_raw(phys, raw, unit):
+    """Charge density on the nodes from the fixed-point deposits (wall nodes: half
+    cells), as the oracle's field phase takes it."""
+    q = sum(s.charge * s.weight * raw[k].astype(np.float64) / unit
+            for k, s in enumerate(phys.species))
+    vol = np.full(phys.ncells + 1, phys.dx)
+    vol[0] = vol[-1] = 0.5 * phys.dx
+    return q / vol
+
+
+def _solve(phys, dcharge, z, delta, unit, stream):
     import torch
+    N = phys.ncells
+    zc = (C.c_int32 * len(z))(*z)
+    dE = torch.full((N + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    rc = capi.lib().pic_field_solve_noalloc(N, len(z), dcharge.data_ptr(), zc, delta, unit,
+                                            phys.eps0, dE.data_ptr(), stream)
+    assert rc == 0, capi.lib().pic_last_error(None)
+    torch.cuda.synchronize()
+    return dE.cpu().numpy()
+
+
+@pytest.mark.parametrize("ncells,ppc", [(1, 8), (300, 40), (2047, 6), (65536, 2)])
+@pytest.mark.parametrize("precision", [capi.FP32, capi.FP64])
+def test_noalloc_field_matches_handle_field(precision, ncells, ppc):
+    """From one node per thread of its scan block (300) to several (2047) and the
+    maximum its static scratch holds (65,536 cells: the total U sits in the last slot),
+    and the single cell; two calls in a row on fresh deposits each time.  Compared with
+    the handle's field of the same deposits and with the oracle's solve of the charge
+    density they stand for."""
+    import torch
+    from oracle.oracle import poisson
     ensure_built()
-    phys = W.bounded_small(ncells=300, ppc=40, seed=6)
+    phys = W.bounded_small(ncells=ncells, ppc=ppc, seed=6)
     loads = W.initial_load(phys, seed=6)
     sim = capi.Sim(phys, precision=precision, sort_interval=10)
     sim.load_all(loads)
     delta, z = _unit_and_z(phys)
-    zc = (C.c_int32 * len(z))(*z)
-    N = phys.ncells
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):  # two calls in a row share the static scratch
         sim.step(7)
         raw, unit = sim.charge_raw(0)
         expect = sim.moments(0)["E"]
         dcharge = torch.from_numpy(raw.reshape(-1).copy()).cuda()
-        dE = torch.full((N + 1,), float("nan"), dtype=torch.float64, device="cuda")
-        rc = capi.lib().pic_field_solve_noalloc(N, len(z), dcharge.data_ptr(), zc, delta, unit,
-                                                phys.eps0, dE.data_ptr(), stream)
-        assert rc == 0, capi.lib().pic_last_error(None)
-        torch.cuda.synchronize()
-        got = dE.cpu().numpy()
-        np.testing.assert_allclose(got, expect, rtol=0, atol=1e-12 * np.abs(expect).max())
+        got = _solve(phys, dcharge, z, delta, unit, stream)
+        scale = max(np.abs(expect).max(), 1e-300)
+        np.testing.assert_allclose(got, expect, rtol=0, atol=1e-12 * scale)
+        _, Eo = poisson(_rho_from_raw(phys, raw, unit), phys.dx, phys.eps0)
+        np.testing.assert_allclose(got, Eo, rtol=0, atol=1e-12 * scale)
     sim.close()
+
+
+def test_noalloc_field_takes_the_deposits_unsmoothed():
+    """For an instance with the density smoother, the call still solves for the charge it
+    is given (no filter): the oracle's solve of the unfiltered density."""
+    import torch
+    from oracle.oracle import poisson
+    ensure_built()
+    phys = W.bounded_small(ncells=200, ppc=30, seed=9)
+    phys.smooth = 1
+    loads = W.initial_load(phys, seed=9)
+    sim = capi.Sim(phys, precision=capi.FP64, sort_interval=10)
+    sim.load_all(loads)
+    sim.step(5)
+    raw, unit = sim.charge_raw(0)
+    sim.close()
+    delta, z = _unit_and_z(phys)
+    dcharge = torch.from_numpy(raw.reshape(-1).copy()).cuda()
+    got = _solve(phys, dcharge, z, delta, unit, torch.cuda.current_stream().cuda_stream)
+    _, Eo = poisson(_rho_from_raw(phys, raw, unit), phys.dx, phys.eps0)
+    np.testing.assert_allclose(got, Eo, rtol=0, atol=1e-12 * np.abs(Eo).max())
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
