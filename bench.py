@@ -772,10 +772,12 @@ def _run_ours(args, stream, rank, world, local):
     return 0
 
 
-def profile_case(precision: str, sort_interval: int = 20) -> int:
+def profile_case(precision: str, sort_interval: int = 20, steps: int = 6) -> int:
     """The small case the ncu captures use: the bounded_large physics on 16,384 cells
-    (49,152,000 particles, state larger than L2), deposit-only launch + 6 steps.  With
-    sort_interval 5 the 6th mover launch (the 5th step's) is the one of a sort step."""
+    (49,152,000 particles, state larger than L2), deposit-only launch + `steps` steps.
+    The step that ends a sort cycle runs its own kernel (k_move_sort): with
+    sort_interval 20 and 20 steps it is the benchmark's sort step, after 19 steps of
+    drift."""
     __import__("__graft_entry__").build()
     from paper_2404_10270_gb300 import capi
     phys = W.bounded_large(ncells=16384)
@@ -783,7 +785,7 @@ def profile_case(precision: str, sort_interval: int = 20) -> int:
     sim = capi.Sim(phys, precision=capi.FP64 if precision == "f64" else capi.FP32,
                    sort_interval=sort_interval, block=256)
     sim.load_all(loads)
-    sim.step(6)
+    sim.step(steps)
     sim.sync()
     print("profile case ok", sim.count(0, 0) + sim.count(0, 1))
     sim.close()
@@ -852,14 +854,14 @@ def main():
                     help="run the small case the ncu captures use and exit")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--sort-step", action="store_true",
-                    help="with --profile-case: sort every 5 steps (the 6th mover launch sorts)")
+                    help="with --profile-case: 20 steps, sort every 20 (the last step sorts)")
     ap.add_argument("--profile-paper", type=int, default=0, metavar="STEPS",
                     help="run the paper's test case alone for STEPS steps and exit")
     ap.add_argument("--profile-ensemble", type=float, default=None, metavar="SCALE",
                     help="run the small batched case the ncu captures use and exit")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case(args.precision, 5 if args.sort_step else 20)
+        return profile_case(args.precision, 20, 20 if args.sort_step else 6)
     if args.profile_ensemble is not None:
         return profile_ensemble(args.profile_ensemble)
     if args.profile_paper:

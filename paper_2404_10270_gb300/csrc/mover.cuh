@@ -394,6 +394,135 @@ __device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4
     }
 }
 
+// Steps 1-5 of the time step for the four particles of one quad (a lane's share of
+// a tile): gather, push, move, walls, collision clock.  c, f, u* hold the quad's
+// state on entry and its new state on exit (cell word -1: left through a wall).  The
+// masks get one bit per quad position: collision candidate (cand), absorbed at the
+// low or high wall (wlo, whi), clock test left to the event kernel (tst).  The id
+// of a test draw comes from idq (SORT: already loaded) or from the store at `slot`.
+template <typename T, bool MAG, bool SORT, bool TEST>
+__device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams& P, bool smag,
+                                             int64_t step, int dgrid, int64_t slot,
+                                             const uint32_t idq[4], int c[4], T f[4], T ux[4],
+                                             T uy[4], T uz[4], unsigned& cand, unsigned& wlo,
+                                             unsigned& whi, unsigned& tst)
+{
+    using T2 = typename Prec<T>::T2;
+    const T2* const accp = static_cast<const T2*>(a.accel);
+    const int N = P.ncells;
+    const int bc = P.bc;
+    const int collides = P.collide;
+    const uint32_t key0 = P.key0, key1 = P.key1;
+    const int64_t node0 = P.node;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (c[k] < 0) continue;
+        int j = (int)((uint32_t)c[k] & kCellMask);
+        uint32_t clk = (uint32_t)c[k] >> kClockShift;
+        // 1. gather (Listing 7) from the node pair (A_j, A_{j+1} - A_j)
+        const T2 pr = __ldg(accp + node0 + j);
+        T fk = f[k];
+        const T acc = Prec<T>::fma_(fk, pr.y, pr.x);
+        // 2. push
+        if (!MAG || !smag) {
+            ux[k] = ux[k] + acc;
+        } else {
+            const T half = T(0.5) * acc;
+            const T t0 = Prec<T>::bt(P, 0), t1 = Prec<T>::bt(P, 1), t2 = Prec<T>::bt(P, 2);
+            const T s0 = Prec<T>::bs(P, 0), s1 = Prec<T>::bs(P, 1), s2 = Prec<T>::bs(P, 2);
+            const T mx = ux[k] + half, my = uy[k], mz = uz[k];
+            // v' = v + v x t, v+ = v + v' x s, each component as two fused
+            // multiply-adds (m_x + m_y t_z - m_z t_y = fma(m_y, t_z, fma(-m_z, t_y, m_x)))
+            const T px = Prec<T>::fma_(my, t2, Prec<T>::fma_(-mz, t1, mx));
+            const T py = Prec<T>::fma_(mz, t0, Prec<T>::fma_(-mx, t2, my));
+            const T pz = Prec<T>::fma_(mx, t1, Prec<T>::fma_(-my, t0, mz));
+            const T qx = Prec<T>::fma_(py, s2, Prec<T>::fma_(-pz, s1, mx));
+            const T qy = Prec<T>::fma_(pz, s0, Prec<T>::fma_(-px, s2, my));
+            const T qz = Prec<T>::fma_(px, s1, Prec<T>::fma_(-py, s0, mz));
+            ux[k] = qx + half;
+            uy[k] = qy;
+            uz[k] = qz;
+        }
+        if (!Prec<T>::finite(ux[k])) set_error(a.err, kErrNonFinite);
+        // 3. move (Listing 7: x += nstep*vx, x the in-cell offset)
+        Prec<T>::move(fk, ux[k], j);
+        f[k] = fk;
+        // 4. walls: periodic wrap here; an absorbed or re-injected particle
+        // leaves the store and the event kernel takes over
+        if (j < 0 || j >= N) {
+            if (bc == PIC_BC_PERIODIC) {
+                j %= N;
+                if (j < 0) j += N;
+            } else {
+                if (j < 0) wlo |= 1u << k; else whi |= 1u << k;
+                c[k] = -1;
+                continue;
+            }
+        }
+        // 5. null collision.  The candidate steps of a particle form a
+        // Bernoulli(P) sequence; its clock counts the steps to skip before the
+        // next event step.  At an event step without a pending candidate (a
+        // test), Philox word 0 gives the candidate-free run g from this step,
+        // cut at the next multiple of 127 (D steps away): g = 0 candidate now,
+        // g < D a candidate g steps later, g = D none before then.  The cut puts
+        // the tests of all particles on the same steps, so a warp runs them
+        // together.  Candidates go to the event kernel.
+        if (collides) {
+            if (clk & kClockCount) {
+                clk -= 1u;
+            } else if (clk & kClockPending) {
+                cand |= 1u << k;
+                clk = 0u;
+            } else if (!TEST) {
+                // a test off the common test steps (the clock of a particle that
+                // was a candidate in the last step, or was re-injected or created
+                // by ionization then): the event kernel draws it, with this
+                // step's counter
+                tst |= 1u << k;
+            } else {
+                // a test step: the id is read only here
+                const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
+                const uint4 w = draw(idk, step, kRngCollide, key0, key1);
+                const int g = min(gap_steps(P.gap, w.x), dgrid);
+                if (g == 0) {
+                    cand |= 1u << k;
+                    clk = 0u;
+                } else {
+                    clk = g < dgrid ? ((uint32_t)(g - 1) | kClockPending)
+                                    : (uint32_t)(dgrid - 1);
+                }
+            }
+        }
+        c[k] = (int)((uint32_t)j | (clk << kClockShift));
+    }
+}
+
+// Queue the quad's rare events for the event kernel (a few lanes of a few tiles per
+// step).  at[k]: the slot the particle occupies after this step (-1: none, nothing is
+// queued for it).
+__device__ __forceinline__ void queue_rare(const MoveArgs& a, int s, unsigned cand, unsigned wlo,
+                                           unsigned whi, unsigned tst, const int64_t at[4])
+{
+    const unsigned ev = cand | wlo | whi | tst;
+    if (!ev) return;
+    unsigned long long e = atomicAdd(a.rare_count, (unsigned long long)__popc(ev));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned bit = 1u << k;
+        if (!(ev & bit)) continue;
+        const uint32_t kind = (cand & bit) ? kRareCandidate
+                              : (tst & bit) ? kRareTest
+                              : (wlo & bit) ? kRareWallLow : kRareWallHigh;
+        if (at[k] < 0) {
+            // refused destination (capacity error latched): nothing to queue
+        } else if (e < (unsigned long long)a.rare_cap)
+            a.rare[e] = rare_pack(at[k], s, kind);
+        else
+            set_error(a.err, kErrEvents);
+        ++e;
+    }
+}
+
 // The fused time step.  Work unit: a warp tile of 32 quads (128 consecutive particles
 // of one segment); each lane owns one quad and moves it with 128-bit accesses.  Warps
 // walk the tiles of all segments independently (no block-level barrier), so every SM
@@ -402,27 +531,23 @@ __device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4
 // calls; walls and collision candidates are queued for the event kernel.
 // SUB: some species of the batch is subcycled (else every segment moves every step and
 // the clock grid is the global one, computed once).  MIXED (with MAG): the batch mixes
-// magnetized and unmagnetized instances, so the push is chosen per segment.  SORT: the
-// step that ends a sort cycle; every particle goes to its slot of the other store copy
-// (reserved from `cursor` by its cell at the start of the step, the order of a counting
-// sort) instead of back to its own.
+// magnetized and unmagnetized instances, so the push is chosen per segment.
 // TEST: the collision-clock test (a Philox draw and a table search) runs inline;
 // without it a particle whose clock needs a test is queued for the event kernel, which
-// keeps the common path free of the draw's code and registers.
-template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool SORT, bool TEST>
-__global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG || SORT, NT>::blocks)
+// keeps the common path free of the draw's code and registers.  (The step that ends a
+// sort cycle runs k_move_sort below instead.)
+template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool TEST>
+__global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
     using Q = typename Prec<T>::Q;
-    using T2 = typename Prec<T>::T2;
     const int lane = threadIdx.x & 31;
     T* const offp = static_cast<T*>(a.off);
     T* const uxp = static_cast<T*>(a.ux);
     T* const uyp = static_cast<T*>(a.uy);
     T* const uzp = static_cast<T*>(a.uz);
-    const T2* const accp = static_cast<const T2*>(a.accel);
     const int64_t step = MOVE ? *a.step : 0;
-    if (MOVE && !SORT && a.pair) {
+    if (MOVE && a.pair) {
         // every clock without a candidate tests on the multiples of kGapMax (a pair is
         // launched only when every colliding species moves on every step)
         const bool tstep = step % kGapMax == 0 || *a.test_all != 0;
@@ -457,10 +582,6 @@ k_move(const __grid_constant__ MoveArgs a)
             }
         }
         const SegParams& P = a.seg[s];
-        const int N = P.ncells;
-        const int bc = P.bc;
-        const int collides = P.collide;
-        const uint32_t key0 = P.key0, key1 = P.key1;
         const int64_t node0 = P.node;
         const int64_t quad = (tile - s_begin) * 32 + lane;
         const int64_t nq = a.seg_nmove[s] >> 2;
@@ -470,124 +591,22 @@ k_move(const __grid_constant__ MoveArgs a)
         int c[4] = {-1, -1, -1, -1};
         T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
         T uy[4] = {T(0), T(0), T(0), T(0)}, uz[4] = {T(0), T(0), T(0), T(0)};
-        uint32_t idq[4] = {0u, 0u, 0u, 0u};
+        const uint32_t idq[4] = {0u, 0u, 0u, 0u};
         if (act) {
             const int4 cc = __ldcs(reinterpret_cast<const int4*>(a.cell + slot));
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
             ld4(offp + slot, f);
-            if (SORT || (MOVE && (!SUB || moves))) ld4(uxp + slot, ux);
-            if (SORT || (MOVE && MAG && smag && (!SUB || moves))) {
+            if (MOVE && (!SUB || moves)) ld4(uxp + slot, ux);
+            if (MOVE && MAG && smag && (!SUB || moves)) {
                 ld4(uyp + slot, uy);
                 ld4(uzp + slot, uz);
             }
-            if (SORT) {
-                const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(a.id + slot));
-                idq[0] = ii.x; idq[1] = ii.y; idq[2] = ii.z; idq[3] = ii.w;
-            }
         }
-        // sort step: reserve each particle's slot by its cell at the start of the step
-        // (equal cells of a quad position grouped across the warp, one counter update per
-        // group); the reservations are waited for only after the move
-        unsigned grp[4] = {0u, 0u, 0u, 0u}, rbase[4] = {0u, 0u, 0u, 0u}, had = 0u;
-        if (SORT) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int key = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
-                grp[k] = __match_any_sync(0xffffffffu, key);
-                if (c[k] >= 0) had |= 1u << k;
-                if (c[k] >= 0 && lane == __ffs(grp[k]) - 1)
-                    rbase[k] = atomicAdd(a.cursor + node0 + key, (unsigned)__popc(grp[k]));
-            }
-        }
-        int64_t to[4] = {-1, -1, -1, -1};
-
         if (MOVE && (!SUB || moves)) {
             unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (c[k] < 0) continue;
-                int j = (int)((uint32_t)c[k] & kCellMask);
-                uint32_t clk = (uint32_t)c[k] >> kClockShift;
-                // 1. gather (Listing 7) from the node pair (A_j, A_{j+1} - A_j)
-                const T2 pr = __ldg(accp + node0 + j);
-                T fk = f[k];
-                const T acc = Prec<T>::fma_(fk, pr.y, pr.x);
-                // 2. push
-                if (!MAG || !smag) {
-                    ux[k] = ux[k] + acc;
-                } else {
-                    const T half = T(0.5) * acc;
-                    const T t0 = Prec<T>::bt(P, 0), t1 = Prec<T>::bt(P, 1), t2 = Prec<T>::bt(P, 2);
-                    const T s0 = Prec<T>::bs(P, 0), s1 = Prec<T>::bs(P, 1), s2 = Prec<T>::bs(P, 2);
-                    const T mx = ux[k] + half, my = uy[k], mz = uz[k];
-                    // v' = v + v x t, v+ = v + v' x s, each component as two fused
-                    // multiply-adds (m_x + m_y t_z - m_z t_y = fma(m_y, t_z, fma(-m_z, t_y, m_x)))
-                    const T px = Prec<T>::fma_(my, t2, Prec<T>::fma_(-mz, t1, mx));
-                    const T py = Prec<T>::fma_(mz, t0, Prec<T>::fma_(-mx, t2, my));
-                    const T pz = Prec<T>::fma_(mx, t1, Prec<T>::fma_(-my, t0, mz));
-                    const T qx = Prec<T>::fma_(py, s2, Prec<T>::fma_(-pz, s1, mx));
-                    const T qy = Prec<T>::fma_(pz, s0, Prec<T>::fma_(-px, s2, my));
-                    const T qz = Prec<T>::fma_(px, s1, Prec<T>::fma_(-py, s0, mz));
-                    ux[k] = qx + half;
-                    uy[k] = qy;
-                    uz[k] = qz;
-                }
-                if (!Prec<T>::finite(ux[k])) set_error(a.err, kErrNonFinite);
-                // 3. move (Listing 7: x += nstep*vx, x the in-cell offset)
-                Prec<T>::move(fk, ux[k], j);
-                f[k] = fk;
-                // 4. walls: periodic wrap here; an absorbed or re-injected particle
-                // leaves the store and the event kernel takes over
-                if (j < 0 || j >= N) {
-                    if (bc == PIC_BC_PERIODIC) {
-                        j %= N;
-                        if (j < 0) j += N;
-                    } else {
-                        if (j < 0) wlo |= 1u << k; else whi |= 1u << k;
-                        c[k] = -1;
-                        continue;
-                    }
-                }
-                // 5. null collision.  The candidate steps of a particle form a
-                // Bernoulli(P) sequence; its clock counts the steps to skip before the
-                // next event step.  At an event step without a pending candidate (a
-                // test), Philox word 0 gives the candidate-free run g from this step,
-                // cut at the next multiple of 127 (D steps away): g = 0 candidate now,
-                // g < D a candidate g steps later, g = D none before then.  The cut puts
-                // the tests of all particles on the same steps, so a warp runs them
-                // together.  Candidates go to the event kernel.
-                if (collides) {
-                    if (clk & kClockCount) {
-                        clk -= 1u;
-                    } else if (clk & kClockPending) {
-                        cand |= 1u << k;
-                        clk = 0u;
-                    } else if (!TEST) {
-                        // a test off the common test steps (the clock of a particle that
-                        // was a candidate in the last step, or was re-injected or created
-                        // by ionization then): the event kernel draws it, with this
-                        // step's counter
-                        tst |= 1u << k;
-                    } else {
-                        // a test step: the id is read only here
-                        const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
-                        const uint4 w = draw(idk, step, kRngCollide, key0, key1);
-                        const int g = min(gap_steps(P.gap, w.x), dgrid);
-                        if (g == 0) {
-                            cand |= 1u << k;
-                            clk = 0u;
-                        } else {
-                            clk = g < dgrid ? ((uint32_t)(g - 1) | kClockPending)
-                                            : (uint32_t)(dgrid - 1);
-                        }
-                    }
-                }
-                c[k] = (int)((uint32_t)j | (clk << kClockShift));
-            }
-            if (SORT) {
-                sort_destinations(a, P, grp, rbase, had, to);
-                sort_write<T>(a, to, c, f, ux, uy, uz, idq);
-            } else if (act) {
+            quad_physics<T, MAG, false, TEST>(a, P, smag, step, dgrid, slot, idq, c, f, ux, uy,
+                                              uz, cand, wlo, whi, tst);
+            if (act) {
                 __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
                 st4(offp + slot, f);
                 st4(uxp + slot, ux);
@@ -596,31 +615,8 @@ k_move(const __grid_constant__ MoveArgs a)
                     st4(uzp + slot, uz);
                 }
             }
-            // queue the quad's rare events (a few lanes of a few tiles per step)
-            const unsigned ev = cand | wlo | whi | tst;
-            if (ev) {
-                unsigned long long e = atomicAdd(a.rare_count, (unsigned long long)__popc(ev));
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned bit = 1u << k;
-                    if (!(ev & bit)) continue;
-                    const uint32_t kind = (cand & bit) ? kRareCandidate
-                                          : (tst & bit) ? kRareTest
-                                          : (wlo & bit) ? kRareWallLow : kRareWallHigh;
-                    if (SORT && to[k] < 0) {
-                        // refused destination (capacity error latched): nothing to queue
-                    } else if (e < (unsigned long long)a.rare_cap)
-                        a.rare[e] = rare_pack(SORT ? to[k] : slot + k, s, kind);
-                    else
-                        set_error(a.err, kErrEvents);
-                    ++e;
-                }
-            }
-        }
-        else if (SORT) {
-            // a segment that does not move this step (subcycling) is still sorted
-            sort_destinations(a, P, grp, rbase, had, to);
-            sort_write<T>(a, to, c, f, ux, uy, uz, idq);
+            const int64_t at[4] = {slot, slot + 1, slot + 2, slot + 3};
+            queue_rare(a, s, cand, wlo, whi, tst, at);
         }
         // 6. deposit of the (new) positions; an empty slot (cell word < 0) gets jd = -1
         int jd[4];
@@ -633,6 +629,302 @@ k_move(const __grid_constant__ MoveArgs a)
         warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0,
                         a.hist_out ? a.hist_out + node0 : nullptr);
     }
+}
+
+// ---- the step that ends a sort cycle -------------------------------------------------
+// Every particle present at the start of the step goes to its slot of the other store
+// copy, in the order of a counting sort by its cell at the start of the step (`cursor`:
+// each cell's next free slot, from the counts the step before made).  A block works on
+// NT/32 consecutive tiles at a time (a chunk of up to 128 NT/32 particles).  When the
+// chunk lies in one segment and its particles' start cells span fewer than kSortSpan
+// cells (the common case: the store was sorted one cycle ago), the block counts them
+// per cell in shared memory, reserves each cell's run with one global atomic per cell,
+// stages the moved particles in shared memory in that order and writes every run with
+// consecutive threads, so the scattered writes of a sort become coalesced runs of
+// about a cell's share of the chunk.  Otherwise (a chunk across two segments, or
+// particles spread widely) each warp reserves per cell and quad position and writes
+// its particles directly.
+constexpr int kSortSpan = 128;
+
+template <typename T, int NT>
+struct SortSmem {
+    static constexpr int NW = NT / 32;
+    static constexpr int C = NW * 128;  // particles of a chunk
+    // staged particles (off, ux, uy, uz in T; cell word, id; start-cell key), then the
+    // per-cell counts, run offsets in the chunk, global run starts, and the per-warp
+    // summaries (segment, lowest and highest start cell) of two consecutive chunks
+    static constexpr size_t bytes = (size_t)C * (4 * sizeof(T) + 4 + 4 + 2) +
+                                    (size_t)3 * kSortSpan * 4 + (size_t)2 * 3 * NW * 4;
+};
+
+template <typename T, int NT, bool MAG, bool SUB, bool MIXED>
+__global__ void __launch_bounds__(NT, MoveOccupancy<T, true, NT>::blocks)
+k_move_sort(const __grid_constant__ MoveArgs a)
+{
+    using Q = typename Prec<T>::Q;
+    constexpr int NW = NT / 32, C = NW * 128;
+    const unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const s_off = reinterpret_cast<T*>(smem_raw);
+    T* const s_ux = s_off + C;
+    T* const s_uy = s_ux + C;
+    T* const s_uz = s_uy + C;
+    int* const s_cell = reinterpret_cast<int*>(s_uz + C);
+    uint32_t* const s_id = reinterpret_cast<uint32_t*>(s_cell + C);
+    unsigned short* const s_key = reinterpret_cast<unsigned short*>(s_id + C);
+    int* const cnt = reinterpret_cast<int*>(s_key + C);
+    int* const pre = cnt + kSortSpan;
+    unsigned* const gb = reinterpret_cast<unsigned*>(pre + kSortSpan);
+    // per-warp summaries, double-buffered by chunk parity: a warp may write the next
+    // chunk's entry while another still reads this chunk's (the next chunk's first
+    // barrier keeps it from getting further ahead)
+    int* const wsum = reinterpret_cast<int*>(gb + kSortSpan);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    T* const offp = static_cast<T*>(a.off);
+    T* const uxp = static_cast<T*>(a.ux);
+    T* const uyp = static_cast<T*>(a.uy);
+    T* const uzp = static_cast<T*>(a.uz);
+    const int64_t step = *a.step;
+    const int64_t total = a.tile_start[a.nseg];
+    int s = 0;
+    int64_t s_begin = 0, s_end = -1;
+    bool moves = true, smag = MAG;
+    int dgrid = kGapMax - (int)(step % kGapMax);
+    // every warp of the block walks the same chunks, so the barriers below match
+    int parity = 0;
+    for (int64_t chunk = blockIdx.x; chunk * NW < total; chunk += gridDim.x, parity ^= 1) {
+        int* const wseg = wsum + parity * 3 * NW;
+        int* const wmin = wseg + NW;
+        int* const wmax = wmin + NW;
+        const int64_t tile = chunk * NW + warp;
+        const bool have = tile < total;
+        if (have && tile >= s_end) {
+            s = advance_segment(a.tile_start, a.nseg, s, tile);
+            s_begin = __ldg(a.tile_start + s);
+            s_end = __ldg(a.tile_start + s + 1);
+            if (MAG && MIXED) smag = a.seg[s].mag != 0;
+            if (SUB) {
+                const int ks = a.seg[s].nstep;
+                const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
+                moves = ks == 1 || q * ks == step + 1;
+                dgrid = kGapMax - (int)((q - 1) % kGapMax);
+            }
+        }
+        const SegParams& P = a.seg[s];
+        const int64_t quad = (tile - s_begin) * 32 + lane;
+        const bool act = have && quad < (a.seg_nmove[s] >> 2);
+        const int64_t slot = P.base + 4 * quad;
+
+        int c[4] = {-1, -1, -1, -1};
+        T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
+        T uy[4] = {T(0), T(0), T(0), T(0)}, uz[4] = {T(0), T(0), T(0), T(0)};
+        uint32_t idq[4] = {0u, 0u, 0u, 0u};
+        if (act) {
+            const int4 cc = __ldcs(reinterpret_cast<const int4*>(a.cell + slot));
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+            ld4(offp + slot, f);
+            ld4(uxp + slot, ux);
+            ld4(uyp + slot, uy);
+            ld4(uzp + slot, uz);
+            const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(a.id + slot));
+            idq[0] = ii.x; idq[1] = ii.y; idq[2] = ii.z; idq[3] = ii.w;
+        }
+        // start cells of the quad (-1: empty slot); the chunk's span and segments
+        int j0[4];
+        unsigned lmin = 0xFFFFFFFFu;
+        int lmax = -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            j0[k] = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1;
+            if (j0[k] >= 0) {
+                lmin = min(lmin, (unsigned)j0[k]);
+                lmax = max(lmax, j0[k]);
+            }
+        }
+        const unsigned wmn = __reduce_min_sync(FULL, lmin);
+        const int wmx = __reduce_max_sync(FULL, lmax);
+        if (lane == 0) {
+            wseg[warp] = wmx >= 0 ? s : -1;
+            wmin[warp] = (int)wmn;
+            wmax[warp] = wmx;
+        }
+        for (int i = threadIdx.x; i < kSortSpan; i += NT) cnt[i] = 0;
+        __syncthreads();
+        int bseg = -1, bmin = INT_MAX, bmax = -1;
+        bool one = true;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int ws = wseg[w];
+            if (ws < 0) continue;
+            if (bseg < 0) bseg = ws;
+            else if (ws != bseg) one = false;
+            bmin = min(bmin, wmin[w]);
+            bmax = max(bmax, wmax[w]);
+        }
+        const bool staged = one && bseg >= 0 && bmax - bmin < kSortSpan;
+        unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
+        int64_t to[4] = {-1, -1, -1, -1};
+        if (staged) {
+            const SegParams& B = a.seg[bseg];
+            // rank of each particle among the chunk's particles of its start cell: equal
+            // cells of a quad position grouped across the warp, one shared atomic a group
+            int key[4], rank[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                key[k] = j0[k] >= 0 ? j0[k] - bmin : -1;
+                const unsigned grp = __match_any_sync(FULL, key[k] >= 0 ? key[k] : kSortSpan + lane);
+                const int leader = __ffs(grp) - 1;
+                int base = 0;
+                if (key[k] >= 0 && lane == leader) base = atomicAdd(cnt + key[k], __popc(grp));
+                base = __shfl_sync(FULL, base, leader);
+                rank[k] = base + __popc(grp & lt);
+            }
+            __syncthreads();
+            // each cell's run: its offset in the chunk (scan of the counts) and its global
+            // start (one reservation per cell, waited for only after the move)
+            unsigned gres = 0;
+            if (threadIdx.x < kSortSpan) {
+                const int n = cnt[threadIdx.x];
+                if (n > 0) gres = atomicAdd(a.cursor + B.node + bmin + threadIdx.x, (unsigned)n);
+            }
+            if (warp == 0) {
+                int v[kSortSpan / 32], sum = 0;
+#pragma unroll
+                for (int i = 0; i < kSortSpan / 32; ++i) {
+                    v[i] = cnt[lane * (kSortSpan / 32) + i];
+                    sum += v[i];
+                }
+                int inc = sum;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(FULL, inc, d);
+                    if (lane >= d) inc += t;
+                }
+                int run = inc - sum;
+#pragma unroll
+                for (int i = 0; i < kSortSpan / 32; ++i) {
+                    pre[lane * (kSortSpan / 32) + i] = run;
+                    run += v[i];
+                }
+            }
+            if (!SUB || moves)
+                quad_physics<T, MAG, true, true>(a, P, smag, step, dgrid, slot, idq, c, f, ux,
+                                                 uy, uz, cand, wlo, whi, tst);
+            if (threadIdx.x < kSortSpan) gb[threadIdx.x] = gres;
+            __syncthreads();
+            // stage every particle at its place in the chunk's cell order
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (key[k] < 0) continue;
+                const int p = pre[key[k]] + rank[k];
+                s_off[p] = f[k];
+                s_ux[p] = ux[k];
+                s_uy[p] = uy[k];
+                s_uz[p] = uz[k];
+                s_cell[p] = c[k];
+                s_id[p] = idq[k];
+                s_key[p] = (unsigned short)key[k];
+                const int64_t r = (int64_t)gb[key[k]] + rank[k];
+                to[k] = r < B.cap ? B.base + r : -1;
+            }
+            queue_rare(a, bseg, cand, wlo, whi, tst, to);
+            // (read before the barrier: the next chunk clears the counts after it)
+            const int ntot = pre[kSortSpan - 1] + cnt[kSortSpan - 1];
+            __syncthreads();
+            // write the runs: consecutive threads, consecutive slots of a cell's run
+            T* const doff = static_cast<T*>(a.doff);
+            T* const dux = static_cast<T*>(a.dux);
+            T* const duy = static_cast<T*>(a.duy);
+            T* const duz = static_cast<T*>(a.duz);
+            for (int p = threadIdx.x; p < ntot; p += NT) {
+                const int kk = s_key[p];
+                const int64_t r = (int64_t)gb[kk] + (p - pre[kk]);
+                if (r >= B.cap) {  // a histogram that does not match the store: refused
+                    set_error(a.err, kErrCapacity);
+                    continue;
+                }
+                const int64_t g = B.base + r;
+                __stcs(a.dcell + g, s_cell[p]);
+                __stcs(doff + g, s_off[p]);
+                __stcs(dux + g, s_ux[p]);
+                __stcs(duy + g, s_uy[p]);
+                __stcs(duz + g, s_uz[p]);
+                __stcs(a.did + g, s_id[p]);
+            }
+        } else {
+            // per warp: reserve each particle's slot by its start cell (equal cells of a
+            // quad position grouped across the warp, one counter update per group)
+            unsigned grp[4] = {0u, 0u, 0u, 0u}, rbase[4] = {0u, 0u, 0u, 0u}, had = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int kk = j0[k] >= 0 ? j0[k] : -1 - lane;
+                grp[k] = __match_any_sync(FULL, kk);
+                if (j0[k] >= 0) had |= 1u << k;
+                if (j0[k] >= 0 && lane == __ffs(grp[k]) - 1)
+                    rbase[k] = atomicAdd(a.cursor + P.node + kk, (unsigned)__popc(grp[k]));
+            }
+            if (!SUB || moves)
+                quad_physics<T, MAG, true, true>(a, P, smag, step, dgrid, slot, idq, c, f, ux,
+                                                 uy, uz, cand, wlo, whi, tst);
+            sort_destinations(a, P, grp, rbase, had, to);
+            sort_write<T>(a, to, c, f, ux, uy, uz, idq);
+            queue_rare(a, s, cand, wlo, whi, tst, to);
+        }
+        // 6. deposit of the new positions
+        int jd[4];
+        Q qr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            jd[k] = (c[k] >> 31) | (int)((uint32_t)c[k] & kCellMask);
+            qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
+        }
+        warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + P.node, nullptr);
+    }
+}
+
+// Host side of k_move_sort: the launch with its shared memory, and the set-up of every
+// variant (the dynamic shared-memory limit, needed above 48 KB) with the occupancy the
+// grid is sized by.  The set-up runs when the handle sizes its grids, outside any
+// stream capture.
+template <typename T, int NT, bool MAG, bool SUB, bool MIXED>
+inline cudaError_t launch_sort_variant(const MoveArgs& a, int grid, cudaStream_t st)
+{
+    k_move_sort<T, NT, MAG, SUB, MIXED><<<grid, NT, SortSmem<T, NT>::bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int NT>
+inline cudaError_t launch_sort_step(const MoveArgs& a, bool mag, bool sub, bool mixed, int grid,
+                                    cudaStream_t st)
+{
+    if (!mag)
+        return sub ? launch_sort_variant<T, NT, false, true, false>(a, grid, st)
+                   : launch_sort_variant<T, NT, false, false, false>(a, grid, st);
+    if (mixed)
+        return sub ? launch_sort_variant<T, NT, true, true, true>(a, grid, st)
+                   : launch_sort_variant<T, NT, true, false, true>(a, grid, st);
+    return sub ? launch_sort_variant<T, NT, true, true, false>(a, grid, st)
+               : launch_sort_variant<T, NT, true, false, false>(a, grid, st);
+}
+
+template <typename T, int NT>
+inline int sort_step_blocks_per_sm(bool mag)
+{
+    const int sm = (int)SortSmem<T, NT>::bytes;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_move_sort<T, NT, false, false, false>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, false, true, false>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, false, false>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, true, false>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, false, true>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, true, true>, A, sm);
+    int n = 0;
+    if (e == cudaSuccess)
+        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_sort<T, NT, true, false, false>, NT, sm)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_sort<T, NT, false, false, false>, NT, sm);
+    return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace bitpic

@@ -5,15 +5,15 @@
 namespace bitpic {
 
 namespace {
-template <int NT, bool SUB, bool SORT, bool TEST>
+template <int NT, bool SUB>
 cudaError_t go_sub(const MoveArgs& a, bool mag, bool mixed, int grid, cudaStream_t st)
 {
     if (!mag)
-        k_move<double, NT, false, true, SUB, false, SORT, TEST><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, false, true, SUB, false, true><<<grid, NT, 0, st>>>(a);
     else if (mixed)
-        k_move<double, NT, true, true, SUB, true, SORT, TEST><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, true, true, SUB, true, true><<<grid, NT, 0, st>>>(a);
     else
-        k_move<double, NT, true, true, SUB, false, SORT, TEST><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, true, true, SUB, false, true><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -22,27 +22,22 @@ cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, boo
                int grid, cudaStream_t st)
 {
     if (!move) {
-        k_move<double, NT, false, false, false, false, false, true><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, false, false, false, false, true><<<grid, NT, 0, st>>>(a);
         return cudaGetLastError();
     }
-    if (sort)
-        return sub ? go_sub<NT, true, true, true>(a, mag, mixed, grid, st)
-                   : go_sub<NT, false, true, true>(a, mag, mixed, grid, st);
-    if (sub) return go_sub<NT, true, false, true>(a, mag, mixed, grid, st);
-    return go_sub<NT, false, false, true>(a, mag, mixed, grid, st);
+    if (sort) return launch_sort_step<double, NT>(a, mag, sub, mixed, grid, st);
+    if (sub) return go_sub<NT, true>(a, mag, mixed, grid, st);
+    return go_sub<NT, false>(a, mag, mixed, grid, st);
 }
 
 template <int NT>
 int occupancy(bool mag, bool sort)
 {
+    if (sort) return sort_step_blocks_per_sm<double, NT>(mag);
     int n = 0;
-    cudaError_t e;
-    if (sort)
-        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false, false, true, true>, NT, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true, false, false, true, true>, NT, 0);
-    else
-        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false, false, false, true>, NT, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true, false, false, false, true>, NT, 0);
+    const cudaError_t e =
+        mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false, false, true>, NT, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, false, true, false, false, true>, NT, 0);
     return e == cudaSuccess ? n : 0;
 }
 }  // namespace
