@@ -396,13 +396,13 @@ def measure_paper_case(args, stream, rank, world, local):
     loads = W.initial_load(phys, seed=1 + rank)
     n = sum(len(x) for x in loads)
     # algorithmic bytes per particle-step: e and D+ read/write cell word, offset, vx (24 B
-    # in FP32, 40 in FP64); D is read (cell word + offset) every step and rewritten on
-    # one step in 20
+    # in FP32, 40 in FP64) every step; D moves on one step in 20 (the same 24 / 40 B) and
+    # is not touched in between (nothing of it changes: its density is kept)
     out = {"workload": "ionization_case: %d cells x 100 ppc x (e, D+, D), periodic, no field, "
                        "elastic + excitation + ionization against the D particles" % args.paper_cells,
            "particles_per_gpu": n}
-    for name, prec, full, ro in (("fp32", capi.FP32, 24.0, 8.0), ("fp64", capi.FP64, 40.0, 12.0)):
-        bpp = (2 * full + (19 * ro + full) / 20) / 3
+    for name, prec, full in (("fp32", capi.FP32, 24.0), ("fp64", capi.FP64, 40.0)):
+        bpp = (2 * full + full / 20) / 3
         sim = capi.Sim(phys, precision=prec, sort_interval=phys.sort_interval, block=256,
                        stream=stream)
         sim.load_all(loads)

@@ -82,6 +82,16 @@ struct SegParams {
     int32_t mag;           // the instance has a magnetic field (Boris push)
 };
 
+// A segment whose fixed-point deposit is kept from step to step instead of being formed
+// anew: a neutral particle target that moves only on some steps (subcycled).  Its
+// charge is 0, so the kept deposit serves the density diagnostic alone; the mover
+// skips its tiles between its moves and, on a move, takes the old positions' share
+// away and adds the new one; a conversion into an ion takes the particle's share away.
+__host__ __device__ __forceinline__ bool deposit_kept(const SegParams& P)
+{
+    return P.is_target != 0 && P.nstep > 1;
+}
+
 constexpr int kChunk = 256;  // nodes per block of the field solve
 
 struct InstParams {

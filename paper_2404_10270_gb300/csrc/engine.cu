@@ -591,6 +591,8 @@ int ensure_fields(pic_handle* h)
     if (h->any_target && (rc = do_sort(h))) return rc;
     rc = launch_tiles_h(h);
     if (rc) return rc;
+    // a fresh deposit of every particle (kept deposits start over too)
+    CUDA_TRY(h, cudaMemsetAsync(h->dep, 0, sizeof(unsigned long long) * (size_t)h->seg_nodes, h->stream));
     if ((rc = launch_move(h, false))) return rc;
     {
         Span sp(h, 1);

@@ -207,11 +207,12 @@ __global__ void __launch_bounds__(kChunkThreads) k_field_emit(const FieldArgs f,
         z[t] = 0;
         if (j > N) continue;
         // the deposit hand-over: keep the last complete deposit, clear for the next step
+        // (a kept deposit, deposit_kept(), is updated in place instead)
         for (int k = 0; k < I.nseg; ++k) {
             const SegParams& P = f.seg[I.seg0 + k];
             const unsigned long long d = f.dep[P.node + j];
             f.dep_last[P.node + j] = d;
-            f.dep[P.node + j] = 0ull;
+            if (!deposit_kept(P)) f.dep[P.node + j] = 0ull;
             z[t] += (i128)I.z[k] * (i128)(long long)d;
         }
         if (I.smooth && poisson) z[t] = f.zs[I.inode + j];

@@ -267,7 +267,9 @@ __device__ __forceinline__ void st4(double* p, const double v[4])
 // total to HBM with one 64-bit reduction (no return value, so nothing waits on it).
 // jd = -1 marks an empty slot: as unsigned it is never the minimum of a live cell, as
 // signed never the maximum, and it matches no cell.
-template <typename Q>
+// NEG: take the quad's charge away instead (two's complement sums; the counts are not
+// touched), for a particle deposit that is kept from step to step and updated.
+template <typename Q, bool NEG = false>
 __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
                                              unsigned long long S,
                                              unsigned long long* __restrict__ gdep,
@@ -331,7 +333,7 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
         if (lane <= ncell) {
             const unsigned long long tot =
                 S * (unsigned long long)myn - myR + (lane > 0 ? prevR : 0ull);
-            if (tot != 0) atomicAdd(gdep + wmin + lane, tot);
+            if (tot != 0) atomicAdd(gdep + wmin + lane, NEG ? 0ull - tot : tot);
         }
         // the particles per cell, for a sort in the next step
         if (ghist && lane < ncell && myn != 0u) atomicAdd(ghist + wmin + lane, myn);
@@ -339,8 +341,9 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (jd[k] >= 0) {
-                atomicAdd(gdep + jd[k], S - (unsigned long long)qr[k]);
-                atomicAdd(gdep + jd[k] + 1, (unsigned long long)qr[k]);
+                const unsigned long long l = S - (unsigned long long)qr[k], r = qr[k];
+                atomicAdd(gdep + jd[k], NEG ? 0ull - l : l);
+                atomicAdd(gdep + jd[k] + 1, NEG ? 0ull - r : r);
                 if (ghist) atomicAdd(ghist + jd[k], 1u);
             }
     }
@@ -559,6 +562,7 @@ k_move(const __grid_constant__ MoveArgs a)
     int64_t s_begin = 0, s_end = -1;   // its tiles
     bool moves = MOVE;                 // the segment moves this step (subcycling)
     bool smag = MAG;                   // the segment's instance is magnetized
+    bool kept = false;                 // the segment's deposit is kept and updated (see below)
     // steps (of the segment's species) to the next multiple of kGapMax
     int dgrid = kGapMax - (int)(step % kGapMax);
     for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
@@ -579,8 +583,13 @@ k_move(const __grid_constant__ MoveArgs a)
                 const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
                 moves = ks == 1 || q * ks == step + 1;
                 dgrid = kGapMax - (int)((q - 1) % kGapMax);
+                kept = deposit_kept(a.seg[s]);
             }
         }
+        // a neutral particle target keeps its deposit from step to step (the field phase
+        // does not clear it; conversions into ions take their share away): between its
+        // moves nothing of it changes, so its tiles are skipped
+        if (MOVE && SUB && kept && !moves) continue;
         const SegParams& P = a.seg[s];
         const int64_t node0 = P.node;
         const int64_t quad = (tile - s_begin) * 32 + lane;
@@ -601,6 +610,18 @@ k_move(const __grid_constant__ MoveArgs a)
                 ld4(uyp + slot, uy);
                 ld4(uzp + slot, uz);
             }
+        }
+        if (MOVE && SUB && kept) {
+            // its move: the old positions' charge leaves the kept deposit (the new
+            // positions' joins it below), exactly as a fresh deposit would come out
+            int jd[4];
+            Q qr[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                jd[k] = (c[k] >> 31) | (int)((uint32_t)c[k] & kCellMask);
+                qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
+            }
+            warp_deposit<Q, true>(jd, qr, Prec<T>::S, a.dep + node0, nullptr);
         }
         if (MOVE && (!SUB || moves)) {
             unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
