@@ -540,15 +540,20 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
         const bool pair = move && !sort && !h->any_mag && h->precision == PIC_FP32 &&
                           h->total_cap >= h->pair_min && h->pair_ok;
         a.pair = pair ? 1 : 0;
+        // the step on which the neutral particle targets move (they all have the sort
+        // interval as their subcycling factor): the variant that updates their kept
+        // deposit; on the other steps their tiles are skipped
+        const bool kept = move && h->any_target && h->sort_interval > 1 &&
+                          (h->step_h + 1) % h->sort_interval == 0;
         for (int v = 0; v < (pair ? 2 : 1); ++v) {
             h->kernels += 1;
             const bool lean = v == 1;
             const cudaError_t e =
                 h->precision == PIC_FP64
-                    ? launch_move_f64(a, mag, move, h->any_subcycle, h->any_unmag, sort, h->nt,
-                                      grid, h->stream)
+                    ? launch_move_f64(a, mag, move, h->any_subcycle, h->any_unmag, sort, kept,
+                                      h->nt, grid, h->stream)
                     : launch_move_f32(a, mag, move, h->any_subcycle, h->any_unmag, sort, lean,
-                                      h->nt, grid, h->stream);
+                                      kept, h->nt, grid, h->stream);
             CUDA_TRY(h, e);
         }
     }

@@ -15,11 +15,13 @@ struct MoveArgs;
 // unmagnetized instances in one batch; `sort`: the step also sorts the store by cell
 // into the other copy (MoveArgs.cursor, .d*); `lean` (FP32, a plain step of a batch
 // without magnetic field): the variant that queues collision-clock tests for the event
-// kernel instead of drawing them inline.  Returns the launch error.
+// kernel instead of drawing them inline; `kept`: the neutral particle targets (whose
+// deposit is kept from step to step) move on this step (on the other steps their tiles
+// are skipped).  Returns the launch error.
 cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
-                            bool sort, bool lean, int nt, int grid, cudaStream_t st);
+                            bool sort, bool lean, bool kept, int nt, int grid, cudaStream_t st);
 cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
-                            bool sort, int nt, int grid, cudaStream_t st);
+                            bool sort, bool kept, int nt, int grid, cudaStream_t st);
 // The rare events the mover queued this step (events.cu): collision candidates, clock
 // tests and wall hits, one thread each, `grid` blocks of 128 threads.
 cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream_t st);

@@ -537,9 +537,13 @@ __device__ __forceinline__ void queue_rare(const MoveArgs& a, int s, unsigned ca
 // magnetized and unmagnetized instances, so the push is chosen per segment.
 // TEST: the collision-clock test (a Philox draw and a table search) runs inline;
 // without it a particle whose clock needs a test is queued for the event kernel, which
-// keeps the common path free of the draw's code and registers.  (The step that ends a
-// sort cycle runs k_move_sort below instead.)
-template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool TEST>
+// keeps the common path free of the draw's code and registers.  KEPT: the step on which
+// the neutral particle targets (whose deposit is kept, deposit_kept()) move; on every
+// other step their tiles are skipped (a separate variant, so that the update's
+// registers do not burden the common steps).  (The step that ends a sort cycle runs
+// k_move_sort below instead.)
+template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool TEST,
+          bool KEPT = false>
 __global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
@@ -562,7 +566,6 @@ k_move(const __grid_constant__ MoveArgs a)
     int64_t s_begin = 0, s_end = -1;   // its tiles
     bool moves = MOVE;                 // the segment moves this step (subcycling)
     bool smag = MAG;                   // the segment's instance is magnetized
-    bool kept = false;                 // the segment's deposit is kept and updated (see below)
     // steps (of the segment's species) to the next multiple of kGapMax
     int dgrid = kGapMax - (int)(step % kGapMax);
     for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
@@ -583,13 +586,16 @@ k_move(const __grid_constant__ MoveArgs a)
                 const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
                 moves = ks == 1 || q * ks == step + 1;
                 dgrid = kGapMax - (int)((q - 1) % kGapMax);
-                kept = deposit_kept(a.seg[s]);
+                // a neutral particle target keeps its deposit from step to step (the
+                // field phase does not clear it; conversions into ions take their share
+                // away): between its moves nothing of it changes, so the warp goes on
+                // with its first tile past the segment
+                if (!moves && deposit_kept(a.seg[s])) {
+                    tile += ((s_end - 1 - tile) / wstride) * wstride;
+                    continue;
+                }
             }
         }
-        // a neutral particle target keeps its deposit from step to step (the field phase
-        // does not clear it; conversions into ions take their share away): between its
-        // moves nothing of it changes, so its tiles are skipped
-        if (MOVE && SUB && kept && !moves) continue;
         const SegParams& P = a.seg[s];
         const int64_t node0 = P.node;
         const int64_t quad = (tile - s_begin) * 32 + lane;
@@ -611,7 +617,7 @@ k_move(const __grid_constant__ MoveArgs a)
                 ld4(uzp + slot, uz);
             }
         }
-        if (MOVE && SUB && kept) {
+        if (KEPT && MOVE && SUB && moves && deposit_kept(P)) {
             // its move: the old positions' charge leaves the kept deposit (the new
             // positions' joins it below), exactly as a fresh deposit would come out
             int jd[4];

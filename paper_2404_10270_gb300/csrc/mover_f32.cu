@@ -5,21 +5,21 @@
 namespace bitpic {
 
 namespace {
-template <int NT, bool SUB, bool TEST>
+template <int NT, bool SUB, bool TEST, bool KEPT>
 cudaError_t go_sub(const MoveArgs& a, bool mag, bool mixed, int grid, cudaStream_t st)
 {
     if (!mag)
-        k_move<float, NT, false, true, SUB, false, TEST><<<grid, NT, 0, st>>>(a);
+        k_move<float, NT, false, true, SUB, false, TEST, KEPT><<<grid, NT, 0, st>>>(a);
     else if (mixed)
-        k_move<float, NT, true, true, SUB, true, TEST><<<grid, NT, 0, st>>>(a);
+        k_move<float, NT, true, true, SUB, true, TEST, KEPT><<<grid, NT, 0, st>>>(a);
     else
-        k_move<float, NT, true, true, SUB, false, TEST><<<grid, NT, 0, st>>>(a);
+        k_move<float, NT, true, true, SUB, false, TEST, KEPT><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int NT>
 cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, bool sort,
-               bool lean, int grid, cudaStream_t st)
+               bool lean, bool kept, int grid, cudaStream_t st)
 {
     if (!move) {
         k_move<float, NT, false, false, false, false, true><<<grid, NT, 0, st>>>(a);
@@ -27,14 +27,17 @@ cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, boo
     }
     if (sort) return launch_sort_step<float, NT>(a, mag, sub, mixed, grid, st);
     if (lean && !mag) {
-        if (sub)
+        if (sub && kept)
+            k_move<float, NT, false, true, true, false, false, true><<<grid, NT, 0, st>>>(a);
+        else if (sub)
             k_move<float, NT, false, true, true, false, false><<<grid, NT, 0, st>>>(a);
         else
             k_move<float, NT, false, true, false, false, false><<<grid, NT, 0, st>>>(a);
         return cudaGetLastError();
     }
-    if (sub) return go_sub<NT, true, true>(a, mag, mixed, grid, st);
-    return go_sub<NT, false, true>(a, mag, mixed, grid, st);
+    if (sub && kept) return go_sub<NT, true, true, true>(a, mag, mixed, grid, st);
+    if (sub) return go_sub<NT, true, true, false>(a, mag, mixed, grid, st);
+    return go_sub<NT, false, true, false>(a, mag, mixed, grid, st);
 }
 
 template <int NT>
@@ -50,12 +53,12 @@ int occupancy(bool mag, bool sort)
 }  // namespace
 
 cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
-                            bool sort, bool lean, int nt, int grid, cudaStream_t st)
+                            bool sort, bool lean, bool kept, int nt, int grid, cudaStream_t st)
 {
     switch (nt) {
-        case 128: return go<128>(a, mag, move, sub, mixed, sort, lean, grid, st);
-        case 512: return go<512>(a, mag, move, sub, mixed, sort, lean, grid, st);
-        default: return go<256>(a, mag, move, sub, mixed, sort, lean, grid, st);
+        case 128: return go<128>(a, mag, move, sub, mixed, sort, lean, kept, grid, st);
+        case 512: return go<512>(a, mag, move, sub, mixed, sort, lean, kept, grid, st);
+        default: return go<256>(a, mag, move, sub, mixed, sort, lean, kept, grid, st);
     }
 }
 

@@ -5,29 +5,30 @@
 namespace bitpic {
 
 namespace {
-template <int NT, bool SUB>
+template <int NT, bool SUB, bool KEPT>
 cudaError_t go_sub(const MoveArgs& a, bool mag, bool mixed, int grid, cudaStream_t st)
 {
     if (!mag)
-        k_move<double, NT, false, true, SUB, false, true><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, false, true, SUB, false, true, KEPT><<<grid, NT, 0, st>>>(a);
     else if (mixed)
-        k_move<double, NT, true, true, SUB, true, true><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, true, true, SUB, true, true, KEPT><<<grid, NT, 0, st>>>(a);
     else
-        k_move<double, NT, true, true, SUB, false, true><<<grid, NT, 0, st>>>(a);
+        k_move<double, NT, true, true, SUB, false, true, KEPT><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int NT>
 cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, bool sort,
-               int grid, cudaStream_t st)
+               bool kept, int grid, cudaStream_t st)
 {
     if (!move) {
         k_move<double, NT, false, false, false, false, true><<<grid, NT, 0, st>>>(a);
         return cudaGetLastError();
     }
     if (sort) return launch_sort_step<double, NT>(a, mag, sub, mixed, grid, st);
-    if (sub) return go_sub<NT, true>(a, mag, mixed, grid, st);
-    return go_sub<NT, false>(a, mag, mixed, grid, st);
+    if (sub && kept) return go_sub<NT, true, true>(a, mag, mixed, grid, st);
+    if (sub) return go_sub<NT, true, false>(a, mag, mixed, grid, st);
+    return go_sub<NT, false, false>(a, mag, mixed, grid, st);
 }
 
 template <int NT>
@@ -43,12 +44,12 @@ int occupancy(bool mag, bool sort)
 }  // namespace
 
 cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
-                            bool sort, int nt, int grid, cudaStream_t st)
+                            bool sort, bool kept, int nt, int grid, cudaStream_t st)
 {
     switch (nt) {
-        case 128: return go<128>(a, mag, move, sub, mixed, sort, grid, st);
-        case 512: return go<512>(a, mag, move, sub, mixed, sort, grid, st);
-        default: return go<256>(a, mag, move, sub, mixed, sort, grid, st);
+        case 128: return go<128>(a, mag, move, sub, mixed, sort, kept, grid, st);
+        case 512: return go<512>(a, mag, move, sub, mixed, sort, kept, grid, st);
+        default: return go<256>(a, mag, move, sub, mixed, sort, kept, grid, st);
     }
 }
 
