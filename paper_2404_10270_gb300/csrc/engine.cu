@@ -82,6 +82,7 @@ struct pic_handle {
     bool any_target = false;       // some instance collides with neutral particles
     bool any_unmag = false;        // some instance has no magnetic field
     unsigned *tcount = nullptr, *treq = nullptr;  // target segment node arrays
+    int64_t* vlist = nullptr;                     // target nodes with requests this step
     int grid_victims = 0;
 
     SegParams* segd = nullptr;
@@ -426,6 +427,8 @@ MoveArgs move_args(pic_handle* h)
     a.rare_cap = h->rare_cap;
     a.tcount = h->tcount;
     a.treq = h->treq;
+    a.vlist = h->vlist;
+    a.vcap = h->any_target ? std::max<int64_t>(h->ev_total, 1) : 0;
     a.hist = h->hist;
     a.hist_out = nullptr;
     a.cursor = nullptr;
@@ -570,7 +573,7 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
         CUDA_TRY(h, launch_events(a, h->precision, h->grid_events, h->stream));
         if (h->any_target) {
             h->kernels += 1;
-            CUDA_TRY(h, launch_victims(a, h->precision, h->seg_nodes, h->grid_victims, h->stream));
+            CUDA_TRY(h, launch_victims(a, h->precision, h->grid_victims, h->stream));
         }
     }
     return PIC_OK;
@@ -979,7 +982,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     }
     h->sms = prop.multiProcessorCount;
     h->grid_events = (int)std::min<int64_t>((h->rare_cap + 127) / 128, (int64_t)16 * h->sms);
-    h->grid_victims = (int)std::min<int64_t>((h->seg_nodes + 127) / 128, (int64_t)16 * h->sms);
+    // one warp per requested target cell: at most the ionization events of a step
+    h->grid_victims = (int)std::min<int64_t>((std::max<int64_t>(h->ev_total, 1) + 3) / 4, (int64_t)4 * h->sms);
     std::snprintf(h->gpu_name, sizeof(h->gpu_name), "%s", prop.name);
     set_block(h, h->nt);
     if (h->tune_block || h->tune_sort) tune_begin(h);
@@ -1013,6 +1017,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK && h->any_smooth) rc = dalloc(h, &h->zs, (size_t)inode);
     if (rc == PIC_OK && h->any_target) rc = dalloc(h, &h->tcount, (size_t)snode);
     if (rc == PIC_OK && h->any_target) rc = dalloc(h, &h->treq, (size_t)snode);
+    if (rc == PIC_OK && h->any_target) rc = dalloc(h, &h->vlist, (size_t)std::max<int64_t>(ev, 1));
     if (rc == PIC_OK) rc = dalloc(h, &h->phi_d, (size_t)h->max_nodes);
     if (rc == PIC_OK) rc = dalloc(h, &h->segd, (size_t)h->nseg);
     if (rc == PIC_OK) rc = dalloc(h, &h->instd, (size_t)h->ninst);
@@ -1028,7 +1033,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->events, (size_t)std::max<int64_t>(ev, 1));
     if (rc == PIC_OK) rc = dalloc(h, &h->ev_count, (size_t)h->ninst);
     if (rc == PIC_OK) rc = dalloc(h, &h->rare, (size_t)h->rare_cap);
-    if (rc == PIC_OK) rc = dalloc(h, &h->rare_count, 1);
+    if (rc == PIC_OK) rc = dalloc(h, &h->rare_count, 2);
     if (rc == PIC_OK) rc = dalloc(h, &h->next_id, (size_t)h->ninst);
     if (rc == PIC_OK) rc = dalloc(h, &h->births_done, (size_t)h->ninst);
     h->cell_chunks = (h->max_nodes + 4095) / 4096;
@@ -1051,7 +1056,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         if (e == cudaSuccess) e = launch_fill_i32(h->st[b].cell, 0, slot, -1, s);
     }
     if (e == cudaSuccess) e = z(h->accel, (size_t)snode * 2 * T);
-    if (e == cudaSuccess) e = z(h->rare_count, 8);
+    if (e == cudaSuccess) e = z(h->rare_count, 16);
     if (e == cudaSuccess) e = z(h->dep, (size_t)snode * 8);
     if (e == cudaSuccess) e = z(h->dep_last, (size_t)snode * 8);
     if (e == cudaSuccess && h->any_target) e = z(h->tcount, (size_t)snode * 4);

@@ -13,13 +13,12 @@ cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_victims(const MoveArgs& a, int precision, int64_t nnodes, int grid,
-                           cudaStream_t st)
+cudaError_t launch_victims(const MoveArgs& a, int precision, int grid, cudaStream_t st)
 {
     if (precision == PIC_FP64)
-        k_victims<double><<<grid, 128, 0, st>>>(a, nnodes);
+        k_victims<double><<<grid, 128, 0, st>>>(a);
     else
-        k_victims<float><<<grid, 128, 0, st>>>(a, nnodes);
+        k_victims<float><<<grid, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

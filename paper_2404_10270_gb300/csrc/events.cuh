@@ -150,7 +150,13 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
             e.slot_e = ge;
             e.slot_i = -1;
             if (target) {
-                atomicAdd(a.treq + a.seg[Ii.tseg].node + j, 1u);
+                // the first request of a target cell puts it on the step's list
+                const int64_t tn = a.seg[Ii.tseg].node + j;
+                if (atomicAdd(a.treq + tn, 1u) == 0u) {
+                    const unsigned long long vi = atomicAdd(a.rare_count + 1, 1ull);
+                    if (vi < (unsigned long long)a.vcap) a.vlist[vi] = tn;
+                    else set_error(a.err, kErrCapacity);
+                }
             } else {
                 const uint4 ri = draw(id, step, kRngIonizeI, P.key0, P.key1);
                 T z0, z1, z2, z3;
@@ -312,12 +318,11 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
 // same id, position and physical velocity (x K_ion / K_target in cells per step),
 // collision clock 0.  The ion's charge joins this step's deposit and the target's
 // (charge 0, but counted in its density) leaves it.  A cell with fewer targets than
-// ionizations converts what it has.  Each warp looks at 32 nodes of the target segments
-// and, for every one with requests, scans the cell's range together (32 entries per
-// pass) for the next smallest live id.
+// ionizations converts what it has.  One warp per target cell on the step's request
+// list (k_events puts a cell there with its first request): it scans the cell's range
+// together (32 entries per pass) for the next smallest live id.
 template <typename T>
-__global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArgs a,
-                                                 int64_t nnodes)
+__global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArgs a)
 {
     const unsigned FULL = 0xffffffffu;
     T* const offp = static_cast<T*>(a.off);
@@ -325,18 +330,14 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
     T* const uyp = static_cast<T*>(a.uy);
     T* const uzp = static_cast<T*>(a.uz);
     const int lane = threadIdx.x & 31;
-    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t n0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; n0 < nnodes;
-         n0 += wstride) {
-        const int64_t mine = n0 + lane;
-        const unsigned myr = mine < nnodes ? a.treq[mine] : 0u;
-        unsigned todo = __ballot_sync(FULL, myr != 0u);
-        while (todo) {
-            const int L = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            const int64_t n = n0 + L;
-            const unsigned r = __shfl_sync(FULL, myr, L);
-            if (lane == L) a.treq[n] = 0u;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nv = (int64_t)min(a.rare_count[1], (unsigned long long)a.vcap);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nv; w += nw) {
+        const int64_t n = a.vlist[w];
+        const unsigned r = a.treq[n];
+        __syncwarp();
+        if (lane == 0) a.treq[n] = 0u;
+        {
             // the segment of node n (segments' node arrays are in increasing order)
             int lo = 0, hi = a.nseg - 1;
             while (lo < hi) {

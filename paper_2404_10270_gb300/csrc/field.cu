@@ -306,7 +306,10 @@ __global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned l
                                                 int64_t* seg_nmove, int64_t* tile_start, int nseg,
                                                 int tile_quads, unsigned long long* rare_count)
 {
-    if (threadIdx.x == 0) *rare_count = 0ull;
+    if (threadIdx.x == 0) {
+        rare_count[0] = 0ull;
+        rare_count[1] = 0ull;
+    }
     __shared__ i128 sh[33];
     const int C = (nseg + blockDim.x - 1) / blockDim.x;
     const int s0 = min(nseg, (int)threadIdx.x * C), s1 = min(nseg, s0 + C);

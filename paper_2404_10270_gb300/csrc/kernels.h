@@ -26,9 +26,8 @@ cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bo
 // tests and wall hits, one thread each, `grid` blocks of 128 threads.
 cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // Ionizations against neutral particle targets: convert the requested targets into
-// ions (events.cu); one thread per segment node, `nnodes` nodes in all.
-cudaError_t launch_victims(const MoveArgs& a, int precision, int64_t nnodes, int grid,
-                           cudaStream_t st);
+// ions (events.cu); one warp per target cell on the step's request list.
+cudaError_t launch_victims(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
 int move_blocks_per_sm_f32(bool mag, bool sort, int nt);
 int move_blocks_per_sm_f64(bool mag, bool sort, int nt);
@@ -65,7 +64,8 @@ cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* ph
 
 // Snapshot each segment's slot count, rounded up to a whole quad, as the count to
 // move, and build the tile prefix (tiles of `tile_quads` quads).
-// Also empties the rare-event queue of the coming step.
+// Also empties the rare-event queue and the target request list of the coming step
+// (rare_count[0] and [1]).
 cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
                          int64_t* tile_start, int nseg, int tile_quads,
                          unsigned long long* rare_count, cudaStream_t st);

@@ -75,13 +75,16 @@ struct MoveArgs {
     unsigned* err;
     const int64_t* step;
     uint64_t* rare;                     // queue of rare events of this step (rare_pack)
-    unsigned long long* rare_count;     // entries queued this step
+    unsigned long long* rare_count;     // [0]: entries queued this step, [1]: entries of vlist
     int64_t rare_cap;                   // queue entries
     // neutral particle targets (segment node arrays of the target segments): live
     // targets per cell as of the start of the step, ionization requests of the step,
     // and the sort histogram, which holds each cell's end position after a sort
     unsigned* tcount;
     unsigned* treq;
+    // the target nodes with ionization requests this step (each once), for k_victims
+    int64_t* vlist;
+    int64_t vcap;
     const unsigned* hist;
     // the sort folded into the time step: the step before a sort counts each cell's
     // particles at the end of the step into `hist_out` (null: no counting); the sort
