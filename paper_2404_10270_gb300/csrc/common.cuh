@@ -70,6 +70,7 @@ struct SegParams {
     double vneutral;       // sqrt(T_n/m_n) in cells/step
     double mratio;         // m_s / m_neutral (elastic energy transfer)
     uint32_t gap[kGapMax + 1];     // gap[g] = floor((1-P)^g 2^32), P = 1 - exp(-nu_max dt)
+    float glog;            // 1 / log2(1-P) (0 without collisions): first guess of gap_steps
     int32_t nproc;         // processes of this species (list order)
     int32_t proc[kMaxProc];        // instance-level index of each process
     int32_t kind[kMaxProc];        // PIC_PROC_*
@@ -158,15 +159,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Number of candidate-free steps, counted from the current one, that the word w
 // encodes: the largest g <= 127 with w < gap[g] (0 if none), so P(g >= k) = (1-P)^k.
-__device__ __forceinline__ int gap_steps(const uint32_t* __restrict__ gap, uint32_t w)
+// gap[g] ~ (1-P)^g 2^32, so g ~ log2(w 2^-32) / log2(1-P): that first guess (float
+// logarithm) is off by at most a step or so, and the table, non-increasing with
+// gap[0] = 2^32 - 1, then decides exactly in a read or two (instead of the seven
+// dependent reads of a binary search, at addresses that differ across the warp).
+__device__ __forceinline__ int gap_steps(const uint32_t* __restrict__ gap, float glog, uint32_t w)
 {
-    if (w < __ldg(gap + kGapMax)) return kGapMax;
-    int lo = 0, hi = kGapMax;  // w < gap[lo] (gap[0] = 2^32-1 > any w that got here), w >= gap[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (w < __ldg(gap + mid)) lo = mid; else hi = mid;
-    }
-    return lo;
+    const float t = (__log2f(fmaxf((float)w, 1.0f)) - 32.0f) * glog;
+    int g = (int)fminf(fmaxf(t, 0.0f), (float)kGapMax);
+    while (g > 0 && w >= __ldg(gap + g)) --g;
+    while (g < kGapMax && w < __ldg(gap + g + 1)) ++g;
+    return g;
 }
 
 // Draw of one purpose for particle `id` in step `step`.

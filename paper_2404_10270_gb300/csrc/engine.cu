@@ -92,10 +92,9 @@ struct pic_handle {
     void* accel = nullptr;
     unsigned long long *dep = nullptr, *dep_last = nullptr;
     double* E = nullptr;
-    i128* UN = nullptr;
     int nchunks = 0;
     int* chunk_inst = nullptr;
-    i128 *part_sum = nullptr, *part_w = nullptr, *part_off = nullptr;
+    i128 *part_sum = nullptr, *part_w = nullptr, *zfirst = nullptr;
     i128* zs = nullptr;  // smoothed node charges (instances with the density smoother)
     bool any_smooth = false;
     unsigned* hist = nullptr;
@@ -355,6 +354,8 @@ void seg_constants(const pic_instance& I, int s, SegParams* P)
         const double T = std::floor(std::exp(-(double)g * x) * 4294967296.0);
         P->gap[g] = T >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)T;
     }
+    // log2(1-P) = -x / ln 2
+    P->glog = x > 0.0 ? (float)(-0.69314718055994530942 / x) : 0.0f;
     P->nproc = 0;
     double cum = 0.0;
     for (int k = 0; k < I.nproc; ++k) {
@@ -484,12 +485,11 @@ FieldArgs field_args(pic_handle* h)
     f.seg_nodes = h->seg_nodes;
     f.precision = h->precision;
     f.E = h->E;
-    f.UN = h->UN;
     f.chunk_inst = h->chunk_inst;
     f.nchunks = h->nchunks;
     f.part_sum = h->part_sum;
     f.part_w = h->part_w;
-    f.part_off = h->part_off;
+    f.zfirst = h->zfirst;
     f.step = h->step_d;
     f.any_poisson = h->any_poisson ? 1 : 0;
     f.zs = h->zs;
@@ -604,7 +604,7 @@ int ensure_fields(pic_handle* h)
     if ((rc = launch_move(h, false))) return rc;
     {
         Span sp(h, 1);
-        h->kernels += h->any_poisson ? 3 : 1;
+        h->kernels += h->any_poisson ? 2 : 1;
         CUDA_TRY(h, launch_field(field_args(h), false, h->stream));
     }
     h->stale = false;
@@ -1009,11 +1009,10 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->dep_last, (size_t)snode);
     if (rc == PIC_OK) rc = dalloc(h, &h->hist, (size_t)snode);
     if (rc == PIC_OK) rc = dalloc(h, &h->E, (size_t)inode);
-    if (rc == PIC_OK) rc = dalloc(h, &h->UN, (size_t)h->ninst);
     if (rc == PIC_OK) rc = dalloc(h, &h->chunk_inst, (size_t)h->nchunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->part_sum, (size_t)h->nchunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->part_w, (size_t)h->nchunks);
-    if (rc == PIC_OK) rc = dalloc(h, &h->part_off, (size_t)h->nchunks);
+    if (rc == PIC_OK) rc = dalloc(h, &h->zfirst, (size_t)h->nchunks);
     if (rc == PIC_OK && h->any_smooth) rc = dalloc(h, &h->zs, (size_t)inode);
     if (rc == PIC_OK && h->any_target) rc = dalloc(h, &h->tcount, (size_t)snode);
     if (rc == PIC_OK && h->any_target) rc = dalloc(h, &h->treq, (size_t)snode);
@@ -1062,10 +1061,9 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (e == cudaSuccess && h->any_target) e = z(h->tcount, (size_t)snode * 4);
     if (e == cudaSuccess && h->any_target) e = z(h->treq, (size_t)snode * 4);
     if (e == cudaSuccess) e = z(h->E, (size_t)inode * 8);
-    if (e == cudaSuccess) e = z(h->UN, (size_t)h->ninst * 16);
     if (e == cudaSuccess) e = z(h->part_sum, (size_t)h->nchunks * 16);
     if (e == cudaSuccess) e = z(h->part_w, (size_t)h->nchunks * 16);
-    if (e == cudaSuccess) e = z(h->part_off, (size_t)h->nchunks * 16);
+    if (e == cudaSuccess) e = z(h->zfirst, (size_t)h->nchunks * 16);
     std::vector<int> ci((size_t)h->nchunks);
     for (int i = 0; i < h->ninst; ++i)
         for (int c = 0; c < h->insth[i].nchunk; ++c) ci[(size_t)h->insth[i].chunk0 + c] = i;
@@ -1274,7 +1272,7 @@ int enqueue_step(pic_handle* h)
     }
     {
         Span sp(h, 1);
-        h->kernels += h->any_poisson ? 3 : 1;
+        h->kernels += h->any_poisson ? 2 : 1;
         CUDA_TRY(h, launch_field(field_args(h), true, h->stream));
     }
     h->step_h += 1;

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                     const int ks = P.nstep;
                     const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
                     const int dgrid = kGapMax - (int)((q - 1) % kGapMax);
-                    const int g = min(gap_steps(P.gap, wd.x), dgrid);
+                    const int g = min(gap_steps(P.gap, P.glog, wd.x), dgrid);
                     now = g == 0;
                     const uint32_t clk = g == 0 ? 0u
                                          : g < dgrid ? ((uint32_t)(g - 1) | kClockPending)

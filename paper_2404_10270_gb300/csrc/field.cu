@@ -120,10 +120,13 @@ __device__ __forceinline__ i128 smoothed_charge(const FieldArgs& f, const InstPa
 }
 
 // The solve runs over chunks of kChunk nodes (one block each):
-//   k_field_partial  per chunk: S_c = sum of Z' and W_c = sum of (N-j) Z' over the chunk;
-//   k_field_chunks   per instance: exclusive prefix of S_c over its chunks, U = sum of W_c;
-//   k_field_emit     per chunk: in-block scan of Z' + chunk prefix = R_j, then E_j and the
-//                    accelerations; also hands the deposit over for the next step.
+//   k_field_partial  per chunk: S_c = sum of Z' and W_c = sum of (N-j) Z' over the chunk,
+//                    and the charge of its first node;
+//   k_field_emit     per chunk: the chunk's prefix (sum of S over the instance's earlier
+//                    chunks) and U = sum of W_c, an in-block scan of Z' + that prefix =
+//                    R_j, then E_j and the accelerations as node pairs (A_j, A_{j+1} - A_j),
+//                    A_{j+1} of the chunk's last node from the next chunk's first charge;
+//                    also hands the deposit over for the next step.
 constexpr int kChunkThreads = 256;
 constexpr int kChunkPer = 1;  // nodes per thread
 static_assert(kChunk == kChunkThreads * kChunkPer, "chunk layout");
@@ -160,31 +163,11 @@ __global__ void __launch_bounds__(kChunkThreads) k_field_partial(const FieldArgs
     if (threadIdx.x == 0) {
         f.part_sum[c] = S;
         f.part_w[c] = Wt;
+        // the charge of the chunk's first node (the walls' too), for the emit of the
+        // chunk before it
+        f.zfirst[c] = j0 <= N ? (I.smooth ? f.zs[I.inode + j0] : node_charge(f, I, j0, f.dep))
+                              : (i128)0;
     }
-}
-
-__global__ void __launch_bounds__(kChunkThreads) k_field_chunks(const FieldArgs f)
-{
-    __shared__ i128 sh[33];
-    const InstParams& I = f.inst[blockIdx.x];
-    if (I.field != PIC_FIELD_POISSON) return;
-    const int nc = I.nchunk;
-    const int C = (nc + blockDim.x - 1) / blockDim.x;
-    const int c0 = min(nc, (int)threadIdx.x * C), c1 = min(nc, c0 + C);
-    i128 sum = 0, wsum = 0;
-    for (int c = c0; c < c1; ++c) {
-        sum += f.part_sum[I.chunk0 + c];
-        wsum += f.part_w[I.chunk0 + c];
-    }
-    i128 tot;
-    i128 run = block_excl_scan(sum, &tot, sh);
-    const i128 U = block_sum(wsum, sh);
-    for (int c = c0; c < c1; ++c) {
-        const i128 v = f.part_sum[I.chunk0 + c];
-        f.part_off[I.chunk0 + c] = run;
-        run += v;
-    }
-    if (threadIdx.x == 0) f.UN[blockIdx.x] = U;
 }
 
 template <typename T>
@@ -219,45 +202,47 @@ __global__ void __launch_bounds__(kChunkThreads) k_field_emit(const FieldArgs f,
         if (j > 0 && j < N) run += z[t];
     }
     if (!poisson) return;  // uniform per block: one instance per chunk
-    i128 tot;
-    const i128 off = f.part_off[c] + block_excl_scan(run, &tot, sh);
-    const i128 U = f.UN[b];
-    const i128 NN = (i128)N;
-    i128 Rprev = off;  // R_{j0-1}
-    T* acc = static_cast<T*>(f.accel);
-#pragma unroll
-    for (int t = 0; t < kChunkPer; ++t) {
-        const int j = j0 + t;
-        if (j > N) break;
-        const i128 zi = (j > 0 && j < N) ? z[t] : (i128)0;
-        const i128 R = Rprev + zi;
-        i128 G;
-        if (j == 0)
-            G = -2 * U - 2 * NN * z[t];
-        else if (j == N)
-            G = 2 * NN * Rprev - 2 * U + 2 * NN * z[t];
-        else
-            G = NN * (Rprev + R) - 2 * U;
-        const double E = I.lambda * i128_to_double(G);
-        f.E[I.inode + j] = E;
-        for (int k = 0; k < I.nseg; ++k) {
-            const SegParams& P = f.seg[I.seg0 + k];
-            acc[2 * (P.node + j)] = (T)(P.accel * E);  // A_j of the pair; k_slopes adds the slope
-        }
-        Rprev = R;
+    // the chunk's prefix of the interior charge and U, from the chunk partials
+    i128 ps = 0, pw = 0;
+    for (int k = threadIdx.x; k < I.nchunk; k += blockDim.x) {
+        if (I.chunk0 + k < c) ps += f.part_sum[I.chunk0 + k];
+        pw += f.part_w[I.chunk0 + k];
     }
-}
-
-// Second member of every node pair: A_{j+1} - A_j, rounded in T from the two
-// rounded accelerations (the value the gather's difference would give).  One flat
-// pass over all segments' nodes; the entries past a segment's last cell are never
-// read by the gather.
-template <typename T>
-__global__ void __launch_bounds__(256) k_slopes(T* __restrict__ pairs, int64_t nnodes)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nnodes; n += stride)
-        pairs[2 * n + 1] = n + 1 < nnodes ? pairs[2 * n + 2] - pairs[2 * n] : T(0);
+    const i128 coff = block_sum(ps, sh);
+    const i128 U = block_sum(pw, sh);
+    i128 tot;
+    const i128 off = coff + block_excl_scan(run, &tot, sh);
+    const i128 NN = (i128)N;
+    // G of node j from R_{j-1}, Z_j: E_j = lambda G
+    auto numer = [&](int j, i128 Rprev, i128 zj) {
+        if (j == 0) return -2 * U - 2 * NN * zj;
+        if (j == N) return 2 * NN * Rprev - 2 * U + 2 * NN * zj;
+        return NN * (2 * Rprev + zj) - 2 * U;
+    };
+    __shared__ double sE[kChunkThreads + 1];
+    i128 Rprev = off;  // R_{j0-1}
+    const int j = j0;  // one node per thread
+    double E = 0.0;
+    if (j <= N) {
+        E = I.lambda * i128_to_double(numer(j, Rprev, z[0]));
+        f.E[I.inode + j] = E;
+        const i128 R = Rprev + ((j > 0 && j < N) ? z[0] : (i128)0);
+        sE[threadIdx.x] = E;
+        // the next chunk's first node (same instance), with the same integers as there
+        if (threadIdx.x == kChunkThreads - 1 && j < N)
+            sE[kChunkThreads] = I.lambda * i128_to_double(numer(j + 1, R, f.zfirst[c + 1]));
+    }
+    __syncthreads();
+    if (j > N) return;
+    T* acc = static_cast<T*>(f.accel);
+    const double En = j < N ? sE[threadIdx.x + 1] : 0.0;
+    for (int k = 0; k < I.nseg; ++k) {
+        const SegParams& P = f.seg[I.seg0 + k];
+        // the pair (A_j, A_{j+1} - A_j), the difference of the two rounded accelerations
+        const T A = (T)(P.accel * E);
+        acc[2 * (P.node + j)] = A;
+        acc[2 * (P.node + j) + 1] = j < N ? (T)(P.accel * En) - A : T(0);
+    }
 }
 
 // Potential for the diagnostics (one block, on demand), from the last complete
@@ -398,21 +383,11 @@ __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* e
 
 cudaError_t launch_field(const FieldArgs& f, bool advance_step, cudaStream_t st)
 {
-    if (f.any_poisson) {
-        k_field_partial<<<f.nchunks, kChunkThreads, 0, st>>>(f);
-        k_field_chunks<<<f.ninst, kChunkThreads, 0, st>>>(f);
-    }
+    if (f.any_poisson) k_field_partial<<<f.nchunks, kChunkThreads, 0, st>>>(f);
     if (f.precision == PIC_FP64)
         k_field_emit<double><<<f.nchunks, kChunkThreads, 0, st>>>(f, advance_step ? 1 : 0);
     else
         k_field_emit<float><<<f.nchunks, kChunkThreads, 0, st>>>(f, advance_step ? 1 : 0);
-    if (f.any_poisson) {
-        const int grid = (int)std::min<int64_t>((f.seg_nodes + 255) / 256, 4096);
-        if (f.precision == PIC_FP64)
-            k_slopes<double><<<grid, 256, 0, st>>>(static_cast<double*>(f.accel), f.seg_nodes);
-        else
-            k_slopes<float><<<grid, 256, 0, st>>>(static_cast<float*>(f.accel), f.seg_nodes);
-    }
     return cudaGetLastError();
 }
 

@@ -44,14 +44,13 @@ struct FieldArgs {
     int64_t seg_nodes;                // entries of the segment node arrays (all segments)
     int precision;                    // PIC_FP32 / PIC_FP64
     double* E;                        // per instance node arrays
-    i128* UN;                         // per instance: sum of R over nodes 0..N-1
     // chunks of kChunk nodes: instance of each chunk, and per chunk the partial
-    // sums of the interior charge, of the weighted charge, and the chunk's prefix
+    // sums of the interior charge and of the weighted charge, and its first node's charge
     const int* chunk_inst;
     int nchunks;
     i128* part_sum;
     i128* part_w;
-    i128* part_off;
+    i128* zfirst;
     int64_t* step;                    // incremented once per emit
     i128* zs;                         // per instance node arrays: 4x the smoothed node
                                       // charge (instances with the smoother), else unused

@@ -489,7 +489,7 @@ __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams&
                 // a test step: the id is read only here
                 const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
                 const uint4 w = draw(idk, step, kRngCollide, key0, key1);
-                const int g = min(gap_steps(P.gap, w.x), dgrid);
+                const int g = min(gap_steps(P.gap, P.glog, w.x), dgrid);
                 if (g == 0) {
                     cand |= 1u << k;
                     clk = 0u;
