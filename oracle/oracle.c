@@ -12,7 +12,8 @@
  *                                                    f*(...) + A[j] is one fma)
  *     2. push     u += a (B = 0), or the Boris rotation (B != 0)   (Section 2, mover)
  *     3. move     f += u; the integer part of f moves the particle across cells
- *                 (Listing 7: x += nstep*vx with x the in-cell offset)
+ *                 (Listing 7: x += nstep*vx with x the in-cell offset); a 2-D species
+ *                 also drifts in y (Listing 1: yp += nstep*vy)
  *     4. wall     absorbing walls with flux counters, periodic, or absorption followed
  *                 by volume re-injection                 (Section 2, plasma-wall phase)
  *     5. MCC      null-collision Monte Carlo against a uniform neutral background
@@ -121,6 +122,7 @@ typedef struct {
     uint32_t* id;
     unsigned char* alive;
     uint8_t* mcc;  /* collision clock: bits 0-6 steps to skip, bit 7 candidate pending */
+    double* yp;    /* y coordinate in cell units (Listing 1's yp; 0 unless sn2d) */
 } orc_store;
 
 typedef struct {
@@ -130,6 +132,7 @@ typedef struct {
     int32_t psp;        /* product ion species of the process */
     int32_t cell;
     double off;
+    double yp;          /* the parent's y coordinate */
     double e[3], i[3];  /* velocities (cells per step) */
 } orc_birth;
 
@@ -191,6 +194,7 @@ static int store_reserve(orc_store* a, int64_t cap)
 #define GROW(f, T) p = realloc(a->f, (size_t)nc * sizeof(T)); if (!p) return -2; a->f = (T*)p;
     GROW(cell, int32_t) GROW(off, double) GROW(ux, double) GROW(uy, double)
     GROW(uz, double) GROW(id, uint32_t) GROW(alive, unsigned char) GROW(mcc, uint8_t)
+    GROW(yp, double)
 #undef GROW
     a->cap = nc;
     return 0;
@@ -199,7 +203,7 @@ static int store_reserve(orc_store* a, int64_t cap)
 static void store_free(orc_store* a)
 {
     free(a->cell); free(a->off); free(a->ux); free(a->uy); free(a->uz);
-    free(a->id); free(a->alive); free(a->mcc);
+    free(a->id); free(a->alive); free(a->mcc); free(a->yp);
     memset(a, 0, sizeof(*a));
 }
 
@@ -222,7 +226,9 @@ orc_sim* orc_create(const orc_params* p)
     if (p->target < 0 || p->target > p->nspecies) return NULL;
     if (p->target > 0 && (p->sp[p->target - 1].charge != 0.0 || p->nref < 1)) return NULL;
     for (int i = 0; i < p->nspecies; ++i)
-        if (!(p->sp[i].mass > 0) || p->sp[i].nstep < 0 || p->sp[i].nstep > 4096) return NULL;
+        if (!(p->sp[i].mass > 0) || p->sp[i].nstep < 0 || p->sp[i].nstep > 4096 ||
+            p->sp[i].sn2d < 0 || p->sp[i].sn2d > 1)
+            return NULL;
 
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
@@ -312,7 +318,7 @@ static int cmp_id_at(const void* a, const void* b)
 
 int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const double* off,
              const double* vx, const double* vy, const double* vz, const uint32_t* id,
-             const uint8_t* mcc)
+             const uint8_t* mcc, const double* yp)
 {
     if (!s || sp < 0 || sp >= s->p.nspecies || n < 0) return -1;
     if (n > 0 && (!cell || !off || !vx || !vy || !vz)) return -1;
@@ -339,6 +345,7 @@ int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const doubl
         a->id[r] = order[r].id;
         a->alive[r] = 1;
         a->mcc[r] = mcc ? mcc[k] : 0;
+        a->yp[r] = (yp && s->p.sp[sp].sn2d) ? yp[k] : 0.0;
         if (order[r].id >= s->next_id) s->next_id = order[r].id + 1;
     }
     a->n = n;
@@ -659,6 +666,7 @@ static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel,
         b.psp = P->product;
         b.cell = a->cell[k];
         b.off = a->off[k];
+        b.yp = a->yp[k];
         b.e[0] = us * n2[0]; b.e[1] = us * n2[1]; b.e[2] = us * n2[2];
         /* the ion's velocity in its own species' units */
         const double vn = s->vneutral[P->product];
@@ -688,6 +696,7 @@ static void reinject(orc_sim* s, int sp, orc_store* a, int64_t k)
     a->cell[k] = j;
     a->off[k] = f;
     a->mcc[k] = 0;
+    a->yp[k] = 0.0; /* a re-injected particle starts its y coordinate anew */
     a->ux[k] = z0 * s->vinj[sp];
     a->uy[k] = z1 * s->vinj[sp];
     a->uz[k] = z2 * s->vinj[sp];
@@ -744,6 +753,7 @@ static int store_sort_by_id(orc_store* a)
         b.cell[r] = a->cell[k]; b.off[r] = a->off[k];
         b.ux[r] = a->ux[k]; b.uy[r] = a->uy[k]; b.uz[r] = a->uz[k];
         b.id[r] = a->id[k]; b.alive[r] = a->alive[k]; b.mcc[r] = a->mcc[k];
+        b.yp[r] = a->yp[k];
     }
     b.n = a->n;
     free(order);
@@ -782,6 +792,7 @@ static int convert_targets(orc_sim* s)
         ion->id[m] = a->id[v];
         ion->alive[m] = 1;
         ion->mcc[m] = 0;
+        ion->yp[m] = s->p.sp[b->psp].sn2d ? a->yp[v] : 0.0;
         a->alive[v] = 0;
         touched[b->psp] = 1;
     }
@@ -842,6 +853,9 @@ static int one_step(orc_sim* s)
             }
             a->cell[k] = j;
             a->off[k] = f;
+            /* the y drift of a 2-D species (Listing 1: yp += nstep*vy, with the velocity
+             * in cells per own step) */
+            if (s->p.sp[sp].sn2d) a->yp[k] += a->uy[k];
             /* 4. walls */
             int reinjected = 0;
             if (j < 0 || j >= N) {
@@ -895,6 +909,7 @@ static int one_step(orc_sim* s)
                 a->id[k] = base + (uint32_t)(per * r + c);
                 a->alive[k] = 1;
                 a->mcc[k] = 0;
+                a->yp[k] = s->p.sp[sp].sn2d ? b->yp : 0.0;
             }
         }
         s->next_id = base + (uint32_t)(per * s->nbirths);
@@ -909,6 +924,7 @@ static int one_step(orc_sim* s)
                 a->cell[m] = a->cell[k]; a->off[m] = a->off[k];
                 a->ux[m] = a->ux[k]; a->uy[m] = a->uy[k]; a->uz[m] = a->uz[k];
                 a->id[m] = a->id[k]; a->alive[m] = 1; a->mcc[m] = a->mcc[k];
+                a->yp[m] = a->yp[k];
             }
             ++m;
         }
@@ -946,7 +962,7 @@ int64_t orc_count(const orc_sim* s, int32_t sp)
 }
 
 int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx,
-            double* vy, double* vz, uint32_t* id, uint8_t* mcc)
+            double* vy, double* vz, uint32_t* id, uint8_t* mcc, double* yp)
 {
     if (!s || sp < 0 || sp >= s->p.nspecies) return -1;
     const orc_store* a = &s->st[sp];
@@ -959,6 +975,7 @@ int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx
         if (vz) vz[k] = a->uz[k] * iv;
         if (id) id[k] = a->id[k];
         if (mcc) mcc[k] = a->mcc[k];
+        if (yp) yp[k] = a->yp[k];
     }
     return 0;
 }

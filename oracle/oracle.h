@@ -45,7 +45,9 @@ typedef struct {
     int32_t nstep;      /* subcycling (Listing 7's x += nstep*vx): advanced with time step
                            nstep*dt on the steps n with (n+1) mod nstep = 0; 0 or 1 =
                            every step */
-    int32_t pad;
+    int32_t sn2d;       /* 1: the species also drifts in y (Listing 1: yp += nstep*vy), a
+                           coordinate in cell units parallel to the walls that nothing
+                           else depends on */
 } orc_species;
 
 typedef struct {
@@ -86,10 +88,11 @@ void orc_destroy(orc_sim* s);
 /* Replace species `sp` with n particles.  cell/off are the BIT1 (j, f) pair,
  * velocities are physical.  id == NULL assigns consecutive ids after all ids
  * loaded so far.  mcc: per-particle collision clock (bits 0-6 steps to skip, bit 7
- * candidate pending), NULL = 0 (the next step draws).  Returns 0 or a negative error. */
+ * candidate pending), NULL = 0 (the next step draws).  yp: the y coordinate (cell
+ * units) of an sn2d species, NULL = 0.  Returns 0 or a negative error. */
 int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const double* off,
              const double* vx, const double* vy, const double* vz, const uint32_t* id,
-             const uint8_t* mcc);
+             const uint8_t* mcc, const double* yp);
 
 /* Advance nsteps time steps.  Returns 0 or a negative error. */
 int orc_step(orc_sim* s, int64_t nsteps);
@@ -100,9 +103,10 @@ int orc_step(orc_sim* s, int64_t nsteps);
 int orc_set_step(orc_sim* s, int64_t step, uint32_t next_id);
 
 int64_t orc_count(const orc_sim* s, int32_t sp);
-/* Copy out species sp sorted by ascending id (capacity = orc_count). */
+/* Copy out species sp sorted by ascending id (capacity = orc_count); yp (cell units)
+ * is 0 for a species without sn2d. */
 int orc_get(const orc_sim* s, int32_t sp, int32_t* cell, double* off, double* vx,
-            double* vy, double* vz, uint32_t* id, uint8_t* mcc);
+            double* vy, double* vz, uint32_t* id, uint8_t* mcc, double* yp);
 
 typedef struct {
     int64_t step;

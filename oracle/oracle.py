@@ -19,7 +19,7 @@ MAX_PROC = 8
 
 class _Species(C.Structure):
     _fields_ = [("charge", C.c_double), ("mass", C.c_double), ("weight", C.c_double),
-                ("temperature", C.c_double), ("nstep", C.c_int32), ("pad", C.c_int32)]
+                ("temperature", C.c_double), ("nstep", C.c_int32), ("sn2d", C.c_int32)]
 
 
 class _Process(C.Structure):
@@ -57,12 +57,12 @@ def lib():
         L.orc_create.argtypes = [C.POINTER(_Params)]
         L.orc_destroy.argtypes = [C.c_void_p]
         P = C.c_void_p
-        L.orc_load.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P, P, P, P, P, P, P]
+        L.orc_load.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P, P, P, P, P, P, P, P]
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
         L.orc_set_step.argtypes = [C.c_void_p, C.c_int64, C.c_uint32]
         L.orc_count.restype = C.c_int64
         L.orc_count.argtypes = [C.c_void_p, C.c_int32]
-        L.orc_get.argtypes = [C.c_void_p, C.c_int32, P, P, P, P, P, P, P]
+        L.orc_get.argtypes = [C.c_void_p, C.c_int32, P, P, P, P, P, P, P, P]
         L.orc_moments_get.argtypes = [C.c_void_p, C.POINTER(_Moments), P, P, P]
         L.orc_philox4x32_10.argtypes = [P, P, P]
         L.orc_poisson.argtypes = [C.c_int32, C.c_double, C.c_double, P, P, P]
@@ -87,7 +87,7 @@ def params_struct(phys) -> _Params:
         p.B[k] = phys.B[k]
     p.T_neutral, p.m_neutral = phys.T_neutral, phys.m_neutral
     for i, s in enumerate(phys.species):
-        p.sp[i] = _Species(s.charge, s.mass, s.weight, s.temperature, s.nstep, 0)
+        p.sp[i] = _Species(s.charge, s.mass, s.weight, s.temperature, s.nstep, s.sn2d)
     p.nproc = len(phys.processes)
     p.smooth = phys.smooth
     for k, q in enumerate(phys.processes):
@@ -149,7 +149,9 @@ class Oracle:
                 np.ascontiguousarray(ld.vz, dtype=np.float64),
                 None if ld.id is None else np.ascontiguousarray(ld.id, dtype=np.uint32),
                 None if getattr(ld, "state", None) is None else
-                np.ascontiguousarray(ld.state, dtype=np.uint8)]
+                np.ascontiguousarray(ld.state, dtype=np.uint8),
+                None if getattr(ld, "yp", None) is None else
+                np.ascontiguousarray(ld.yp, dtype=np.float64)]
         rc = lib().orc_load(self._h, species, len(arrs[0]), *[_ptr(a) for a in arrs])
         if rc:
             raise ValueError("orc_load failed: %d" % rc)
@@ -173,9 +175,10 @@ class Oracle:
         n = lib().orc_count(self._h, species)
         out = dict(cell=np.zeros(n, np.int32), off=np.zeros(n), vx=np.zeros(n),
                    vy=np.zeros(n), vz=np.zeros(n), id=np.zeros(n, np.uint32),
-                   state=np.zeros(n, np.uint8))
+                   state=np.zeros(n, np.uint8), yp=np.zeros(n))
         rc = lib().orc_get(self._h, species, *[_ptr(out[k]) for k in
-                                                ("cell", "off", "vx", "vy", "vz", "id", "state")])
+                                                ("cell", "off", "vx", "vy", "vz", "id", "state",
+                                                 "yp")])
         if rc:
             raise RuntimeError("orc_get failed: %d" % rc)
         return out

@@ -48,6 +48,7 @@ class Species:
     ppc: int = 0                 # particles per cell at load time
     capacity_factor: float = 1.0  # slots reserved per loaded particle (creation slack)
     nstep: int = 1                # subcycling: advanced with nstep*dt on steps n, (n+1) % nstep == 0
+    sn2d: int = 0                 # 1: also drifts in y (yp += nstep*vy, yp in cell units)
 
 
 @dataclasses.dataclass
@@ -172,6 +173,8 @@ class Load:
     # collision clock per particle (bits 0-6 steps to skip, bit 7 candidate pending);
     # None = all zero, which is how a fresh load starts
     state: Optional[np.ndarray] = None
+    # y coordinate (cell units) of a species that drifts in y; None = 0
+    yp: Optional[np.ndarray] = None
 
     def __len__(self) -> int:
         return len(self.cell)
@@ -179,7 +182,8 @@ class Load:
     def take(self, idx) -> "Load":
         return Load(self.cell[idx], self.off[idx], self.vx[idx], self.vy[idx],
                     self.vz[idx], self.id[idx],
-                    None if self.state is None else self.state[idx])
+                    None if self.state is None else self.state[idx],
+                    None if self.yp is None else self.yp[idx])
 
 
 def initial_load(phys: Physics, seed: int = 1, cells=None) -> List[Load]:
