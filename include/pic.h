@@ -81,7 +81,13 @@ typedef struct {
                            (n+1) mod nstep = 0, so that every species is at the same time
                            at the multiples of nstep*dt, and deposited every step; 0 or
                            1 = every step (at most 4096) */
-    int32_t pad;
+    int32_t sn2d;       /* 1: a 2-D species that also drifts in y (Listing 1's
+                           yp += nstep*vy): a coordinate yp parallel to the walls, in cell
+                           units, advanced with the velocity after the push on the steps
+                           the species moves and used by nothing else (the field, walls and
+                           collisions are 1D); a re-injected particle restarts at yp = 0,
+                           ionization products start at their parent's yp.  Set and read
+                           with pic_load_yp / pic_get_yp.  0: no y coordinate */
 } pic_species;
 
 /* One collision process against the uniform neutral background (null-collision
@@ -190,6 +196,22 @@ PIC_API int pic_load_particles_f32(pic_handle* h, int32_t inst, int32_t species,
                                    const int32_t* cell, const float* off, const float* vx,
                                    const float* vy, const float* vz, const uint32_t* id,
                                    const uint8_t* state, int32_t flags);
+
+/* The y coordinates (cell units) of an sn2d species (see pic_species.sn2d), for the n
+ * particles of the last pic_load_particles(_f32) call of (instance, species) and in the
+ * same order; that call sets them to 0.  Only between that call and the next pic_step
+ * (else PIC_ESTATE for this call, the handle stays usable), n equal to that call's n
+ * (else PIC_EINVAL), a species with sn2d = 1 (else PIC_EINVAL).  flags: PIC_DEVICE when
+ * yp is device memory (else host memory, copied in before the call returns). */
+PIC_API int pic_load_yp(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                        const double* yp, int32_t flags);
+
+/* The y coordinates (cell units) of the live particles of (instance, species) in the
+ * order of pic_get_particles (storage order); *n_out receives their number, which must
+ * not exceed `capacity` (else PIC_ECAPACITY).  A species without sn2d gets zeros.
+ * flags: PIC_DEVICE when yp is device memory.  Synchronises. */
+PIC_API int pic_get_yp(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
+                       double* yp, int32_t flags, int64_t* n_out);
 
 /* Enqueue nsteps time steps of every instance on the handle's stream. */
 PIC_API int pic_step(pic_handle* h, int64_t nsteps);

@@ -29,7 +29,8 @@ STATUS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA",
 EXPORTS = ("pic_create", "pic_load_particles", "pic_load_particles_f32", "pic_step", "pic_sync",
            "pic_moments", "pic_count", "pic_get_particles", "pic_get_particles_f32",
            "pic_restore_counters", "pic_charge_raw", "pic_profile", "pic_kernel_time",
-           "pic_destroy", "pic_last_error", "pic_philox", "pic_field_solve_noalloc")
+           "pic_destroy", "pic_last_error", "pic_philox", "pic_field_solve_noalloc",
+           "pic_load_yp", "pic_get_yp")
 
 
 class PicError(RuntimeError):
@@ -41,7 +42,7 @@ class PicError(RuntimeError):
 class pic_species(C.Structure):
     _fields_ = [("charge", C.c_double), ("mass", C.c_double), ("weight", C.c_double),
                 ("temperature", C.c_double), ("capacity", C.c_int64), ("nstep", C.c_int32),
-                ("pad", C.c_int32)]
+                ("sn2d", C.c_int32)]
 
 
 class pic_process(C.Structure):
@@ -105,6 +106,8 @@ def lib():
         L.pic_last_error.restype = C.c_char_p
         L.pic_philox.argtypes = [C.c_uint64, P, P, I64, I32, P]
         L.pic_field_solve_noalloc.argtypes = [I32, I32, P, P, C.c_double, I64, C.c_double, P, P]
+        L.pic_load_yp.argtypes = [P, I32, I32, I64, P, I32]
+        L.pic_get_yp.argtypes = [P, I32, I32, I64, P, I32, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
 
@@ -151,7 +154,7 @@ def instance_struct(phys: W.Physics, capacity: Optional[Sequence[int]] = None) -
     for i, s in enumerate(phys.species):
         cap = capacity[i] if capacity is not None else int(s.ppc * phys.ncells * s.capacity_factor)
         I.sp[i] = pic_species(s.charge, s.mass, s.weight, s.temperature, max(int(cap), 4),
-                              s.nstep, 0)
+                              s.nstep, getattr(s, "sn2d", 0))
     I.nproc = len(phys.processes)
     I.smooth = phys.smooth
     for k, q in enumerate(phys.processes):
@@ -237,6 +240,12 @@ class Sim:
         fn = lib().pic_load_particles_f32 if f32 else lib().pic_load_particles
         _check(fn(self._h, inst, species, n, *[_ptr(a) for a in arrs], _ptr(ids), _ptr(st),
                   flags), self._h)
+        yp = getattr(ld, "yp", None)
+        if yp is not None and getattr(self.phys[inst].species[species], "sn2d", 0):
+            if isinstance(yp, np.ndarray):
+                yp = np.ascontiguousarray(yp, np.float64)
+            _check(lib().pic_load_yp(self._h, inst, species, n, _ptr(yp),
+                                     DEVICE if _on_device(yp) else 0), self._h)
 
     def load_all(self, loads: List, inst: int = 0) -> None:
         for s, ld in enumerate(loads):
@@ -269,6 +278,12 @@ class Sim:
                   *[_ptr(out[k]) for k in ("cell", "off", "vx", "vy", "vz", "id", "state")],
                   CELL_UNITS if cell_units else 0, C.byref(got)), self._h)
         assert got.value == n
+        # the y coordinates of a 2-D species (zeros for the others), same order
+        out["yp"] = np.zeros(n)
+        if getattr(self.phys[inst].species[species], "sn2d", 0):
+            _check(lib().pic_get_yp(self._h, inst, species, n, out["yp"].ctypes.data, 0,
+                                    C.byref(got)), self._h)
+            assert got.value == n
         return out
 
     def moments(self, inst: int = 0) -> dict:

@@ -81,6 +81,8 @@ struct SegParams {
     int32_t nstep;         // subcycling: moved on the steps n with (n+1) mod nstep = 0
     int32_t is_target;     // the instance's neutral particle target
     int32_t mag;           // the instance has a magnetic field (Boris push)
+    int32_t sn2d;          // the species also drifts in y (Listing 1: yp += nstep*vy)
+    int32_t pad;
 };
 
 // A segment whose fixed-point deposit is kept from step to step instead of being formed

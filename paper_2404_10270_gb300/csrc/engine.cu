@@ -51,6 +51,7 @@ struct Store {
     void* uy = nullptr;
     void* uz = nullptr;
     uint32_t* id = nullptr;
+    void* yp = nullptr;  // y coordinates of 2-D species (allocated only when some species has one)
 };
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -81,6 +82,9 @@ struct pic_handle {
     bool any_poisson = false, any_mag = false, any_ionize = false, any_subcycle = false;
     bool any_target = false;       // some instance collides with neutral particles
     bool any_unmag = false;        // some instance has no magnetic field
+    bool any_sn2d = false;         // some species drifts in y (pic_species.sn2d)
+    std::vector<int64_t> fresh_n;  // per segment: n of its last load while no step or field
+                                   // phase has run since (-1 otherwise), for pic_load_yp
     unsigned *tcount = nullptr, *treq = nullptr;  // target segment node arrays
     int64_t* vlist = nullptr;                     // target nodes with requests this step
     int grid_victims = 0;
@@ -284,6 +288,7 @@ int validate_instance(const pic_instance& I, int idx, std::string* why)
         if (I.sp[s].capacity < 0) return bad("negative capacity");
         if (!(I.sp[s].temperature >= 0)) return bad("temperature must be >= 0");
         if (I.sp[s].nstep < 0 || I.sp[s].nstep > 4096) return bad("nstep must be 0..4096");
+        if (I.sp[s].sn2d != 0 && I.sp[s].sn2d != 1) return bad("sn2d must be 0 or 1");
     }
     if (I.nproc < 0 || I.nproc > PIC_MAX_PROC) return bad("nproc must be 0..8");
     if (I.smooth != 0 && I.smooth != 1) return bad("smooth must be 0 or 1");
@@ -372,6 +377,7 @@ void seg_constants(const pic_instance& I, int s, SegParams* P)
     P->collide = (P->nproc > 0 && numax > 0.0) ? 1 : 0;
     P->key0 = (uint32_t)I.seed;
     P->key1 = (uint32_t)(I.seed >> 32);
+    P->sn2d = S.sn2d;
 }
 
 // Charge of each species as an exact integer multiple of a common unit delta
@@ -436,6 +442,8 @@ MoveArgs move_args(pic_handle* h)
     a.dcell = nullptr;
     a.doff = a.dux = a.duy = a.duz = nullptr;
     a.did = nullptr;
+    a.yp = S.yp;
+    a.dyp = nullptr;
     a.test_all = h->test_all;
     a.pair = 0;
     return a;
@@ -465,6 +473,7 @@ SortArgs sort_args(pic_handle* h)
         a.uy[b] = h->st[b].uy;
         a.uz[b] = h->st[b].uz;
         a.id[b] = h->st[b].id;
+        a.yp[b] = h->st[b].yp;
     }
     a.src = h->cur;
     a.max_cap = h->max_cap;
@@ -526,6 +535,7 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
         a.duy = D.uy;
         a.duz = D.uz;
         a.did = D.id;
+        a.dyp = D.yp;
     }
     {
         Span sp(h, sort ? 5 : 0);
@@ -567,6 +577,13 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
         h->cur = 1 - h->cur;
         a = move_args(h);  // the event kernels work on the sorted copy
     }
+    if (move && h->any_sn2d) {
+        // the y drift of 2-D species, with the velocities after the push (before the
+        // event kernel's collisions change them)
+        Span sd(h, 3);
+        h->kernels += 1;
+        CUDA_TRY(h, launch_drift_y(a, h->precision, 4 * h->sms, h->stream));
+    }
     if (move) {
         Span se(h, 3);
         h->kernels += 1;
@@ -594,6 +611,9 @@ int ensure_fields(pic_handle* h)
 {
     if (!h->stale) return PIC_OK;
     int rc;
+    // the field phase (with neutral targets a sort) may reorder the store: the order of
+    // the last loads is gone
+    std::fill(h->fresh_n.begin(), h->fresh_n.end(), (int64_t)-1);
     h->hist_ready = false;
     // a neutral particle target needs the cell ranges of a sorted store
     if (h->any_target && (rc = do_sort(h))) return rc;
@@ -893,8 +913,10 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         h->any_ionize |= ionize;
         if (I.B[0] != 0.0 || I.B[1] != 0.0 || I.B[2] != 0.0) h->any_mag = true;
         else h->any_unmag = true;
-        for (int s = 0; s < I.nspecies; ++s)
+        for (int s = 0; s < I.nspecies; ++s) {
             if (species_nstep(I, s) > 1) h->any_subcycle = true;
+            if (I.sp[s].sn2d) h->any_sn2d = true;
+        }
         for (int s = 0; s < I.nspecies; ++s) {
             SegParams P;
             std::memset(&P, 0, sizeof(P));
@@ -935,6 +957,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         h->insth.push_back(ip);
     }
     h->nseg = (int)h->segh.size();
+    h->fresh_n.assign((size_t)h->nseg, (int64_t)-1);
     if (h->nseg >= kMaxSegments) {
         h->last_error = "too many (instance, species) segments: at most " + std::to_string(kMaxSegments - 1);
         return bail(PIC_EINVAL);
@@ -1001,6 +1024,11 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         if ((rc = dalloc(h, &z, (size_t)slot * T))) break;
         if ((rc = dalloc(h, &st.id, (size_t)slot))) break;
         st.off = o; st.ux = x; st.uy = y; st.uz = z;
+        if (h->any_sn2d) {
+            char* q = nullptr;
+            if ((rc = dalloc(h, &q, (size_t)slot * T))) break;
+            st.yp = q;
+        }
     }
     char* acc = nullptr;
     if (rc == PIC_OK) rc = dalloc(h, &acc, (size_t)snode * 2 * T);  // (A_j, A_{j+1} - A_j) pairs
@@ -1052,6 +1080,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         if (e == cudaSuccess) e = z(h->st[b].uy, (size_t)slot * T);
         if (e == cudaSuccess) e = z(h->st[b].uz, (size_t)slot * T);
         if (e == cudaSuccess) e = z(h->st[b].id, (size_t)slot * 4);
+        if (e == cudaSuccess && h->st[b].yp) e = z(h->st[b].yp, (size_t)slot * T);
         if (e == cudaSuccess) e = launch_fill_i32(h->st[b].cell, 0, slot, -1, s);
     }
     if (e == cudaSuccess) e = z(h->accel, (size_t)snode * 2 * T);
@@ -1197,6 +1226,7 @@ int load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     l.s_uy = S.uy;
     l.s_uz = S.uz;
     l.s_id = S.id;
+    l.s_yp = S.yp;
     l.err = h->err;
     l.precision = h->precision;
     l.next_id = h->next_id + inst;
@@ -1219,6 +1249,7 @@ int load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h->stale = true;
     h->hist_ready = false;
+    h->fresh_n[si] = n;
     return PIC_OK;
 }
 
@@ -1326,6 +1357,7 @@ int pic_step(pic_handle* h, int64_t nsteps)
     if (rc) return rc;
     if (nsteps < 0) return fail(h, PIC_EINVAL, "pic_step: nsteps < 0");
     if ((rc = ensure_fields(h))) return rc;
+    std::fill(h->fresh_n.begin(), h->fresh_n.end(), (int64_t)-1);
     int64_t n = 0;
     while (n < nsteps) {
         const int64_t K = h->sort_interval;
@@ -1501,7 +1533,8 @@ namespace {
 // float with host_f32 (hb bytes per value).
 int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
                   int32_t* cell, void* off, void* vx, void* vy, void* vz, uint32_t* id,
-                  uint8_t* state, int32_t flags, int64_t* n_out, bool host_f32)
+                  uint8_t* state, int32_t flags, int64_t* n_out, bool host_f32,
+                  double* yp = nullptr)
 {
     const bool on_device = (flags & PIC_DEVICE) != 0;
     const size_t hb = host_f32 ? 4 : 8;
@@ -1523,7 +1556,7 @@ int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity
     const size_t n = (size_t)std::max<unsigned long long>(live, 1);
     char* tmp = nullptr;
     const size_t scratch = (size_t)(nb + 1) * 8;
-    const size_t outb = on_device ? 0 : n * (4 + hb * 4 + 4 + 1) + 8 * 16;
+    const size_t outb = on_device ? 0 : n * (4 + hb * 4 + 4 + 1 + 8) + 9 * 16;
     CUDA_TRY(h, io_buffer(h, scratch + outb + 16, &tmp));
     GetArgs g;
     const Store& S = h->st[h->cur];
@@ -1533,6 +1566,7 @@ int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity
     g.s_uy = S.uy;
     g.s_uz = S.uz;
     g.s_id = S.id;
+    g.s_yp = S.yp;
     g.base = P.base;
     g.nslots = (int64_t)nslots;
     g.vscale_inv = (flags & PIC_CELL_UNITS)
@@ -1544,6 +1578,7 @@ int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity
     g.host_f32 = host_f32 ? 1 : 0;
     if (on_device) {
         g.cell = cell; g.off = off; g.vx = vx; g.vy = vy; g.vz = vz; g.id = id; g.state = state;
+        g.yp = yp;
     } else {
         char* p = tmp + (scratch + 15) / 16 * 16;
         auto take = [&](size_t b) { char* d = p; p += (b + 15) / 16 * 16; return d; };
@@ -1554,6 +1589,7 @@ int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity
         g.vz = vz ? take(n * hb) : nullptr;
         g.id = id ? (uint32_t*)take(n * 4) : nullptr;
         g.state = state ? (uint8_t*)take(n) : nullptr;
+        g.yp = yp ? (double*)take(n * 8) : nullptr;
     }
     CUDA_TRY(h, launch_get(g, s));
     if (!on_device && live > 0) {
@@ -1565,6 +1601,7 @@ int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity
         if (vz) CUDA_TRY(h, cudaMemcpyAsync(vz, g.vz, m * hb, cudaMemcpyDeviceToHost, s));
         if (id) CUDA_TRY(h, cudaMemcpyAsync(id, g.id, m * 4, cudaMemcpyDeviceToHost, s));
         if (state) CUDA_TRY(h, cudaMemcpyAsync(state, g.state, m, cudaMemcpyDeviceToHost, s));
+        if (yp) CUDA_TRY(h, cudaMemcpyAsync(yp, g.yp, m * 8, cudaMemcpyDeviceToHost, s));
     }
     CUDA_TRY(h, cudaStreamSynchronize(s));
     return PIC_OK;
@@ -1585,6 +1622,44 @@ int pic_get_particles_f32(pic_handle* h, int32_t inst, int32_t species, int64_t 
 {
     return get_particles(h, inst, species, capacity, cell, off, vx, vy, vz, id, state, flags,
                          n_out, true);
+}
+
+int pic_load_yp(pic_handle* h, int32_t inst, int32_t species, int64_t n, const double* yp,
+                int32_t flags)
+{
+    int rc = check_state(h);
+    if (rc) return rc;
+    if (inst < 0 || inst >= h->ninst || species < 0 || species >= h->inst[inst].nspecies || n < 0 ||
+        (n > 0 && !yp))
+        return fail(h, PIC_EINVAL, "pic_load_yp: bad arguments");
+    if (!h->inst[inst].sp[species].sn2d)
+        return fail(h, PIC_EINVAL, "pic_load_yp: the species has no y coordinate (sn2d = 0)");
+    const int si = h->insth[inst].seg0 + species;
+    if (h->fresh_n[si] < 0) {
+        h->last_error = "pic_load_yp: only after pic_load_particles of the species, before the next "
+                        "pic_step, pic_moments or pic_charge_raw";
+        return PIC_ESTATE;  // the handle stays usable
+    }
+    if (n != h->fresh_n[si]) return fail(h, PIC_EINVAL, "pic_load_yp: n differs from the load's");
+    cudaStream_t s = h->stream;
+    const double* d = yp;
+    if (!(flags & PIC_DEVICE) && n > 0) {
+        char* p = nullptr;
+        CUDA_TRY(h, io_buffer(h, (size_t)n * 8, &p));
+        CUDA_TRY(h, cudaMemcpyAsync(p, yp, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        d = reinterpret_cast<const double*>(p);
+    }
+    CUDA_TRY(h, launch_set_yp(h->st[h->cur].yp, h->segh[si].base, d, n, h->precision, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    return PIC_OK;
+}
+
+int pic_get_yp(pic_handle* h, int32_t inst, int32_t species, int64_t capacity, double* yp,
+               int32_t flags, int64_t* n_out)
+{
+    if (!yp) return fail(h, PIC_EINVAL, "pic_get_yp: null output");
+    return get_particles(h, inst, species, capacity, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, flags & PIC_DEVICE, n_out, false, yp);
 }
 
 int pic_restore_counters(pic_handle* h, int64_t step, const uint64_t* next_id)

@@ -22,4 +22,13 @@ cudaError_t launch_victims(const MoveArgs& a, int precision, int grid, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t launch_drift_y(const MoveArgs& a, int precision, int grid, cudaStream_t st)
+{
+    if (precision == PIC_FP64)
+        k_drift_y<double><<<grid, 256, 0, st>>>(a);
+    else
+        k_drift_y<float><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace bitpic

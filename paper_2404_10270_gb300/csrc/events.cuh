@@ -51,7 +51,7 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, T* z0, T* z
 template <typename T>
 __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, int s,
                                     uint32_t id, int64_t step, int j, T f, T& ux, T& uy,
-                                    T& uz, uint32_t wsel, uint32_t wdens)
+                                    T& uz, uint32_t wsel, uint32_t wdens, int64_t pslot)
 {
     const InstParams& I = a.inst[P.inst];
     if (I.tseg >= 0) {
@@ -138,6 +138,10 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
             a.cell[ge] = j; off[ge] = f;
             vx[ge] = us * n2[0]; vy[ge] = us * n2[1]; vz[ge] = us * n2[2];
             a.id[ge] = 0xFFFFFFFFu;
+            // the products start at the parent's y coordinate (2-D species)
+            T* const ypp = static_cast<T*>(a.yp);
+            const T yparent = ypp ? ypp[pslot] : T(0);
+            if (ypp) ypp[ge] = P.sn2d ? yparent : T(0);
             atomicAdd(a.seg_live + s, 1ull);
             // the children's charge joins this step's deposit
             const uint64_t qr = Prec<T>::qright(f), ql = Prec<T>::S - qr;
@@ -167,6 +171,7 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
                 a.cell[gi] = j; off[gi] = f;
                 vx[gi] = z0 * vn; vy[gi] = z1 * vn; vz[gi] = z2 * vn;
                 a.id[gi] = 0xFFFFFFFFu;
+                if (ypp) ypp[gi] = Pi.sn2d ? yparent : T(0);
                 e.slot_i = gi;
                 atomicAdd(a.seg_live + si, 1ull);
                 atomicAdd(a.dep + Pi.node + j, (unsigned long long)ql);
@@ -277,7 +282,8 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                     vx = uxp[slot];
                     vy = uyp[slot];
                     vz = uzp[slot];
-                    const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y, wd.z);
+                    const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y, wd.z,
+                                             slot);
                     if (p >= 0) {
                         uxp[slot] = vx;
                         uyp[slot] = vy;
@@ -293,7 +299,9 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                 int j = kind == kRareWallLow ? -1 : P.ncells;
                 wkey = 2 * s + (kind == kRareWallLow ? 0 : 1);
                 if (wall_event<T>(a, P, s, id, step, j, f, vx, vy, vz) == 1) {
-                    // re-injected: back in the store with a fresh clock, deposited here
+                    // re-injected: back in the store with a fresh clock (and y coordinate),
+                    // deposited here
+                    if (a.yp) static_cast<T*>(a.yp)[slot] = T(0);
                     a.cell[slot] = j;
                     offp[slot] = f;
                     uxp[slot] = vx;
@@ -387,6 +395,7 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
                         uyp[gi] = uyp[v] * ratio;
                         uzp[gi] = uzp[v] * ratio;
                         a.id[gi] = wbest;
+                        if (a.yp) static_cast<T*>(a.yp)[gi] = Pi.sn2d ? static_cast<T*>(a.yp)[v] : T(0);
                         a.cell[v] = -1;
                         const uint64_t qr = Prec<T>::qright(fv), ql = Prec<T>::S - qr;
                         atomicAdd(a.dep + Pi.node + jv, (unsigned long long)ql);
@@ -401,6 +410,42 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
                 __syncwarp();
             }
         }
+    }
+}
+
+// The y drift of 2-D species (Listing 1: yp += nstep*vy), after the mover and before
+// the event kernel: every particle of such a species that moved this step (the store
+// copy the step leaves, its live particles), with its velocity after the push in cells
+// per own step.  A particle that left through a wall (empty in the store until the event
+// kernel re-injects it) gets no drift; re-injection starts its y coordinate anew.
+template <typename T>
+__global__ void __launch_bounds__(256) k_drift_y(const __grid_constant__ MoveArgs a)
+{
+    const int64_t step = *a.step;
+    T* const yp = static_cast<T*>(a.yp);
+    const T* const uy = static_cast<const T*>(a.uy);
+    const int64_t total = a.tile_start[a.nseg] * 128;  // tiles of 32 quads
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int s = 0;
+    int64_t s_begin = 0, s_end = -1;
+    bool on = false;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const int64_t tile = t >> 7;
+        if (tile >= s_end) {
+            s = advance_segment(a.tile_start, a.nseg, s, tile);
+            s_begin = __ldg(a.tile_start + s);
+            s_end = __ldg(a.tile_start + s + 1);
+            const int ks = a.seg[s].nstep;
+            on = a.seg[s].sn2d != 0 && (ks == 1 || (step + 1) % ks == 0);
+        }
+        if (!on) {  // on to this thread's first slot past the segment
+            t += ((s_end * 128 - 1 - t) / stride) * stride;
+            continue;
+        }
+        const int64_t k = (tile - s_begin) * 128 + (t & 127);
+        if (k >= a.seg_nmove[s]) continue;
+        const int64_t g = a.seg[s].base + k;
+        if (a.cell[g] >= 0) yp[g] = yp[g] + uy[g];
     }
 }
 

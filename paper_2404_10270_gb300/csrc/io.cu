@@ -50,6 +50,7 @@ __global__ void k_load(const LoadArgs l)
             uy[g] = l.vscale == 1.0 ? (T)vy : (T)(vy * l.vscale);
             uz[g] = l.vscale == 1.0 ? (T)vz : (T)(vz * l.vscale);
             l.s_id[g] = l.id ? l.id[k] : l.id0 + (uint32_t)k;
+            if (l.s_yp) static_cast<T*>(l.s_yp)[g] = T(0);
         } else {
             l.s_cell[g] = -1;
         }
@@ -155,6 +156,15 @@ __global__ void k_get_write(const GetArgs g)
     if (g.vy) static_cast<H*>(g.vy)[o] = (H)((double)static_cast<const T*>(g.s_uy)[s] * g.vscale_inv);
     if (g.vz) static_cast<H*>(g.vz)[o] = (H)((double)static_cast<const T*>(g.s_uz)[s] * g.vscale_inv);
     if (g.id) g.id[o] = g.s_id[s];
+    if (g.yp) g.yp[o] = g.s_yp ? (double)static_cast<const T*>(g.s_yp)[s] : 0.0;
+}
+
+template <typename T>
+__global__ void k_set_yp(T* yp, int64_t base, const double* in, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride)
+        yp[base + k] = (T)in[k];
 }
 
 template <typename T>
@@ -236,6 +246,17 @@ cudaError_t launch_get(const GetArgs& g, cudaStream_t st)
         if (g.host_f32) k_get_write<float, float><<<(unsigned)nb, 1024, 0, st>>>(g);
         else k_get_write<float, double><<<(unsigned)nb, 1024, 0, st>>>(g);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_yp(void* s_yp, int64_t base, const double* in, int64_t n, int precision,
+                          cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (precision == PIC_FP64)
+        k_set_yp<double><<<grid_for(n, 256), 256, 0, st>>>(static_cast<double*>(s_yp), base, in, n);
+    else
+        k_set_yp<float><<<grid_for(n, 256), 256, 0, st>>>(static_cast<float*>(s_yp), base, in, n);
     return cudaGetLastError();
 }
 

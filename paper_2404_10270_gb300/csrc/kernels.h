@@ -28,6 +28,8 @@ cudaError_t launch_events(const MoveArgs& a, int precision, int grid, cudaStream
 // Ionizations against neutral particle targets: convert the requested targets into
 // ions (events.cu); one warp per target cell on the step's request list.
 cudaError_t launch_victims(const MoveArgs& a, int precision, int grid, cudaStream_t st);
+// The y drift of 2-D species after the mover (MoveArgs.yp non-null), before the events.
+cudaError_t launch_drift_y(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
 int move_blocks_per_sm_f32(bool mag, bool sort, int nt);
 int move_blocks_per_sm_f64(bool mag, bool sort, int nt);
@@ -99,6 +101,7 @@ struct SortArgs {
     void* uy[2];
     void* uz[2];
     uint32_t* id[2];
+    void* yp[2];                      // y coordinates of 2-D species (null: none)
     int src;
     int64_t max_cap;                  // largest segment capacity
     int max_cells;
@@ -132,6 +135,7 @@ struct LoadArgs {
     void* s_uy;
     void* s_uz;
     uint32_t* s_id;
+    void* s_yp;             // y coordinates (null: no 2-D species): set to 0
     unsigned* err;
     int precision;
     unsigned long long* next_id;  // instance's next automatic id: raised to max(id) + 1
@@ -145,6 +149,7 @@ struct GetArgs {
     const void* s_uy;
     const void* s_uz;
     const uint32_t* s_id;
+    const void* s_yp;       // y coordinates (null: none)
     int64_t base, nslots;
     double vscale_inv;      // dx/dt
     int precision;
@@ -156,10 +161,15 @@ struct GetArgs {
     int host_f32;
     uint32_t* id;
     uint8_t* state;
+    double* yp;             // y coordinates out (double), or null
     unsigned long long* block_count;  // scratch, ceil(nslots/1024)+1 entries
     int64_t capacity;                 // entries of the output arrays
 };
 cudaError_t launch_get(const GetArgs& g, cudaStream_t st);
+
+// store yp[base + k] = in[k] (double in, the store's precision T), k < n
+cudaError_t launch_set_yp(void* s_yp, int64_t base, const double* in, int64_t n, int precision,
+                          cudaStream_t st);
 
 // sum of kefac |u|^2 over live particles of segments [s0, s0+ns) into out[ns]
 cudaError_t launch_kinetic(const SegParams* seg, int s0, int ns, int64_t max_slots,

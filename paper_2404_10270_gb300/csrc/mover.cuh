@@ -106,6 +106,10 @@ struct MoveArgs {
     void* duy;
     void* duz;
     uint32_t* did;
+    // y coordinates of 2-D species (null when no species has one): this store copy's,
+    // and the sort destination's
+    void* yp;
+    void* dyp;
 };
 
 template <typename T> struct Prec;
@@ -680,10 +684,10 @@ template <typename T, int NT>
 struct SortSmem {
     static constexpr int NW = NT / 32;
     static constexpr int C = NW * 128;  // particles of a chunk
-    // staged particles (off, ux, uy, uz in T; cell word, id; start-cell key), then the
-    // per-cell counts, run offsets in the chunk, global run starts, and the per-warp
+    // staged particles (off, ux, uy, uz, yp in T; cell word, id; start-cell key), then
+    // the per-cell counts, run offsets in the chunk, global run starts, and the per-warp
     // summaries (segment, lowest and highest start cell) of two consecutive chunks
-    static constexpr size_t bytes = (size_t)C * (4 * sizeof(T) + 4 + 4 + 2) +
+    static constexpr size_t bytes = (size_t)C * (5 * sizeof(T) + 4 + 4 + 2) +
                                     (size_t)3 * kSortSpan * 4 + (size_t)2 * 3 * NW * 4;
 };
 
@@ -699,7 +703,8 @@ k_move_sort(const __grid_constant__ MoveArgs a)
     T* const s_ux = s_off + C;
     T* const s_uy = s_ux + C;
     T* const s_uz = s_uy + C;
-    int* const s_cell = reinterpret_cast<int*>(s_uz + C);
+    T* const s_yp = s_uz + C;
+    int* const s_cell = reinterpret_cast<int*>(s_yp + C);
     uint32_t* const s_id = reinterpret_cast<uint32_t*>(s_cell + C);
     unsigned short* const s_key = reinterpret_cast<unsigned short*>(s_id + C);
     int* const cnt = reinterpret_cast<int*>(s_key + C);
@@ -856,6 +861,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                 s_cell[p] = c[k];
                 s_id[p] = idq[k];
                 s_key[p] = (unsigned short)key[k];
+                if (a.yp) s_yp[p] = static_cast<const T*>(a.yp)[slot + k];
                 const int64_t r = (int64_t)gb[key[k]] + rank[k];
                 to[k] = r < B.cap ? B.base + r : -1;
             }
@@ -882,6 +888,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                 __stcs(duy + g, s_uy[p]);
                 __stcs(duz + g, s_uz[p]);
                 __stcs(a.did + g, s_id[p]);
+                if (a.yp) static_cast<T*>(a.dyp)[g] = s_yp[p];
             }
         } else {
             // per warp: reserve each particle's slot by its start cell (equal cells of a
@@ -900,6 +907,12 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                                                  uy, uz, cand, wlo, whi, tst);
             sort_destinations(a, P, grp, rbase, had, to);
             sort_write<T>(a, to, c, f, ux, uy, uz, idq);
+            if (a.yp) {  // the y coordinates go along (read here, not held across the move)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (to[k] >= 0)
+                        static_cast<T*>(a.dyp)[to[k]] = static_cast<const T*>(a.yp)[slot + k];
+            }
             queue_rare(a, s, cand, wlo, whi, tst, to);
         }
         // 6. deposit of the new positions

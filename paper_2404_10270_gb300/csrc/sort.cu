@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
     T* duy = static_cast<T*>(a.uy[dst]);
     T* duz = static_cast<T*>(a.uz[dst]);
     uint32_t* did = a.id[dst];
+    const T* yps = static_cast<const T*>(a.yp[src]);
+    T* ypd = static_cast<T*>(a.yp[dst]);
     const int64_t total = a.tile_start[a.nseg];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
                 duy[to] = cur.vy[k];
                 duz[to] = cur.vz[k];
                 did[to] = cur.vi[k];
+                if (yps) ypd[to] = yps[cur.slot + k];
             }
         }
         cur = nxt;
