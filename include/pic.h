@@ -284,6 +284,17 @@ PIC_API const char* pic_last_error(const pic_handle* h);
 PIC_API int pic_philox(uint64_t key, const uint32_t* ctr, uint32_t* out, int64_t n,
                int32_t on_device, void* stream);
 
+/* Self-test of the bounds-checked device build (the library compiled with PIC_CHECKED,
+ * in which every index a kernel computes into a particle store, node array, queue or
+ * staging buffer is checked and a violation latches a status bit that the next
+ * synchronising call reports as PIC_ECUDA, the access skipped; the paper has no
+ * counterpart).  One thread asks for an index one past a range through that check; the
+ * check must refuse it (no access is made) and latch the bit.  Returns PIC_OK when it
+ * did, PIC_ECUDA when it did not or a launch failed, PIC_EINVAL in the normal build
+ * (which has no checks).  `stream`: borrowed cudaStream_t (NULL = default stream); the
+ * call synchronises it.  Message from pic_last_error(NULL). */
+PIC_API int pic_bounds_probe(void* stream);
+
 /* Allocation-free field solve (the paper has no counterpart; it exists for callers
  * that cannot allocate device memory: code running while a CUDA graph is being
  * captured, latency-critical loops in which an allocation could block or fragment,

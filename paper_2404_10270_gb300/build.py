@@ -18,6 +18,9 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_native")
 LIB = os.path.join(OUT, "libbitpic.so")
+# the bounds-checked device build (-DPIC_CHECKED): every index a kernel computes is
+# checked and a violation latches a status bit; for tests, not for speed
+LIB_CHECKED = os.path.join(OUT, "libbitpic_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {
@@ -46,15 +49,15 @@ def _deps():
     return files
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB) or os.environ.get("BITPIC_NVCC_EXTRA"):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib) or os.environ.get("BITPIC_NVCC_EXTRA"):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def _compile(unit: str, extra, verbose: bool) -> str:
-    obj = os.path.join(OUT, unit.replace(".cu", ".o"))
+def _compile(unit: str, extra, verbose: bool, outdir: str = OUT) -> str:
+    obj = os.path.join(outdir, unit.replace(".cu", ".o"))
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"),
            "-c", os.path.join(SRC, unit), "-o", obj, *extra]
@@ -69,21 +72,27 @@ def _compile(unit: str, extra, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libbitpic.so if any source is newer than the library."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link libbitpic.so (checked=True: libbitpic_checked.so, the
+    bounds-checked device build) if any source is newer than the library."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    outdir = os.path.join(OUT, "checked") if checked else OUT
+    os.makedirs(outdir, exist_ok=True)
+    extra = ["-DPIC_CHECKED"] if checked else []
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(lambda kv: _compile(kv[0], kv[1], verbose), UNITS.items()))
-    tmp = LIB + ".tmp%d" % os.getpid()
+        objs = list(ex.map(lambda kv: _compile(kv[0], kv[1] + extra, verbose, outdir),
+                           UNITS.items()))
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

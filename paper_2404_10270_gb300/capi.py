@@ -16,7 +16,8 @@ import numpy as np
 from . import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_native", "libbitpic.so")
+# $BITPIC_LIB selects another build of the library (the bounds-checked one, for tests)
+LIB_PATH = os.environ.get("BITPIC_LIB") or os.path.join(HERE, "_native", "libbitpic.so")
 
 MAX_SPECIES = 4
 MAX_PROC = 8
@@ -30,7 +31,7 @@ EXPORTS = ("pic_create", "pic_load_particles", "pic_load_particles_f32", "pic_st
            "pic_moments", "pic_count", "pic_get_particles", "pic_get_particles_f32",
            "pic_restore_counters", "pic_charge_raw", "pic_profile", "pic_kernel_time",
            "pic_destroy", "pic_last_error", "pic_philox", "pic_field_solve_noalloc",
-           "pic_load_yp", "pic_get_yp")
+           "pic_load_yp", "pic_get_yp", "pic_bounds_probe")
 
 
 class PicError(RuntimeError):
@@ -108,6 +109,7 @@ def lib():
         L.pic_field_solve_noalloc.argtypes = [I32, I32, P, P, C.c_double, I64, C.c_double, P, P]
         L.pic_load_yp.argtypes = [P, I32, I32, I64, P, I32]
         L.pic_get_yp.argtypes = [P, I32, I32, I64, P, I32, C.POINTER(C.c_int64)]
+        L.pic_bounds_probe.argtypes = [P]
         _lib = L
     return _lib
 

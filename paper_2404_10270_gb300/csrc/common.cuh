@@ -43,6 +43,7 @@ enum : unsigned {
     kErrInput = 4u,
     kErrEvents = 8u,
     kErrTimeout = 16u,
+    kErrBounds = 32u,  // the bounds-checked build refused an index (see in_range)
 };
 
 // Philox counter word 3: what a draw is for.
@@ -223,6 +224,24 @@ __device__ __forceinline__ i128 shfl_i128(i128 v, int src)
 }
 
 __device__ __forceinline__ void set_error(unsigned* err, unsigned bit) { atomicOr(err, bit); }
+
+// The bounds-checked device build (compiled with -DPIC_CHECKED): every index a kernel
+// computes into a particle store, a node array, a queue or a staging buffer is checked
+// against its range before it is used; a violation latches kErrBounds (reported by the
+// next synchronising call) and the access is skipped, so nothing traps.  In the normal
+// build the check is a constant true and costs nothing.
+#ifdef PIC_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool in_range(unsigned* err, int64_t i, int64_t lo, int64_t hi)
+{
+    if (!kChecked) return true;
+    if (i >= lo && i < hi) return true;
+    set_error(err, kErrBounds);
+    return false;
+}
 
 // Segment of tile t: the last s with tile_start[s] <= t (tile_start has nseg+1 entries).
 __device__ __forceinline__ int find_segment(const int64_t* __restrict__ tile_start, int nseg,

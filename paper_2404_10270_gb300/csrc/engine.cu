@@ -478,6 +478,7 @@ SortArgs sort_args(pic_handle* h)
     a.src = h->cur;
     a.max_cap = h->max_cap;
     a.max_cells = h->max_nodes - 1;
+    a.err = h->err;
     return a;
 }
 
@@ -661,6 +662,7 @@ int sync_check(pic_handle* h)
     else if (e & kErrNonFinite) { code = PIC_ENONFINITE; msg = "a particle velocity became non-finite"; }
     else if (e & kErrEvents) { code = PIC_ECAPACITY; msg = "the rare-event queue of a step (wall hits and collision candidates) overflowed"; }
     else if (e & kErrTimeout) { code = PIC_ETIMEOUT; msg = "a bounded device wait ran out"; }
+    else if (e & kErrBounds) { code = PIC_ECUDA; msg = "the bounds-checked build refused a device index"; }
     h->state = code;
     h->last_error = msg;
     return code;

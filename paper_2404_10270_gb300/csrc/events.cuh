@@ -250,8 +250,16 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
          w < n; w += stride) {
         const unsigned long long i = w + lane;
         int ckey = -1, wkey = -1;  // collision counter, wall counter
-        if (i < n) {
-            const uint64_t e = a.rare[i];
+        bool ok = i < n;
+        uint64_t e = 0;
+        if (ok) {
+            e = a.rare[i];
+            // (bounds-checked build: the entry's segment and slot)
+            const int s0 = (int)((e >> 2) & (uint64_t)(kMaxSegments - 1));
+            ok = in_range(a.err, s0, 0, a.nseg) &&
+                 in_range(a.err, (int64_t)(e >> 24), a.seg[s0].base, a.seg[s0].base + a.seg[s0].cap);
+        }
+        if (ok) {
             const uint32_t kind = (uint32_t)(e & 3u);
             const int s = (int)((e >> 2) & (uint64_t)(kMaxSegments - 1));
             const int64_t slot = (int64_t)(e >> 24);
@@ -260,7 +268,8 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
             // a clock test needs only the id and the cell word; the state is read when the
             // particle collides or left through a wall
             T f = T(0), vx = T(0), vy = T(0), vz = T(0);
-            if (kind == kRareCandidate || kind == kRareTest) {
+            if ((kind == kRareCandidate || kind == kRareTest) &&
+                in_range(a.err, (int)((uint32_t)a.cell[slot] & kCellMask), 0, P.ncells)) {
                 const int j = (int)((uint32_t)a.cell[slot] & kCellMask);
                 const uint4 wd = draw(id, step, kRngCollide, P.key0, P.key1);
                 bool now = kind == kRareCandidate;
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                         ckey = P.inst * kMaxProc + p;
                     }
                 }
-            } else {
+            } else if (kind == kRareWallLow || kind == kRareWallHigh) {
                 f = offp[slot];
                 vx = uxp[slot];
                 vy = uyp[slot];
@@ -357,8 +366,10 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
             const int j = (int)(n - P.node);
             const InstParams& I = a.inst[P.inst];
             const SegParams& Pi = a.seg[I.iseg];
+            if (!in_range(a.err, j, 0, P.ncells)) continue;  // (bounds-checked build only)
             const int64_t begin = P.base + (j > 0 ? (int64_t)a.hist[n - 1] : 0);
-            const int64_t end = P.base + (int64_t)a.hist[n];
+            int64_t end = P.base + (int64_t)a.hist[n];
+            if (!in_range(a.err, end - 1, begin - 1, P.base + P.cap)) end = begin;
             uint32_t last = 0;
             bool first = true;
             for (unsigned k = 0; k < r; ++k) {
@@ -444,6 +455,7 @@ __global__ void __launch_bounds__(256) k_drift_y(const __grid_constant__ MoveArg
         }
         const int64_t k = (tile - s_begin) * 128 + (t & 127);
         if (k >= a.seg_nmove[s]) continue;
+        if (!in_range(a.err, k, 0, a.seg[s].cap)) continue;  // (bounds-checked build only)
         const int64_t g = a.seg[s].base + k;
         if (a.cell[g] >= 0) yp[g] = yp[g] + uy[g];
     }

@@ -1,5 +1,7 @@
 // io.cu -- loading particles into the store, reading them back, diagnostics and the
 // stand-alone Philox kernel.
+#include <string>
+
 #include "kernels.h"
 #include "mover.cuh"
 
@@ -291,4 +293,50 @@ cudaError_t launch_fill_i32(int32_t* p, int64_t lo, int64_t hi, int32_t v, cudaS
     return cudaGetLastError();
 }
 
+// The bounds-checked build's self-test: one thread asks for entry kProbeN of a
+// kProbeN-entry range of g_probe_buf through in_range, which must refuse it (the array
+// has 2 kProbeN entries, so even an accepted index would stay inside it) and latch the
+// bit in g_probe_err.
+constexpr int kProbeN = 4;
+__device__ int g_probe_buf[2 * kProbeN];
+__device__ unsigned g_probe_err;
+
+__global__ void k_bounds_probe()
+{
+    if (in_range(&g_probe_err, kProbeN, 0, kProbeN)) g_probe_buf[kProbeN] = 1;
+}
+
+void set_global_error(const std::string& msg);
+
 }  // namespace bitpic
+
+extern "C" PIC_API int pic_bounds_probe(void* stream)
+{
+    using namespace bitpic;
+    set_global_error("");
+    if (!kChecked) {
+        set_global_error("pic_bounds_probe: not the bounds-checked build");
+        return PIC_EINVAL;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned zero = 0;
+    unsigned got = 0;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_probe_err, &zero, sizeof(zero), 0,
+                                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_bounds_probe<<<1, 1, 0, st>>>();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyFromSymbolAsync(&got, g_probe_err, sizeof(got), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_global_error(std::string("pic_bounds_probe: ") + cudaGetErrorString(e));
+        return PIC_ECUDA;
+    }
+    if (!(got & kErrBounds)) {
+        set_global_error("pic_bounds_probe: the check did not refuse the index");
+        return PIC_ECUDA;
+    }
+    return PIC_OK;
+}

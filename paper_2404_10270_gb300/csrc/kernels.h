@@ -105,6 +105,7 @@ struct SortArgs {
     int src;
     int64_t max_cap;                  // largest segment capacity
     int max_cells;
+    unsigned* err;                    // status word (the bounds-checked build's refusals)
 };
 // Grids are one resident wave of each kernel on `sms` multiprocessors.
 cudaError_t launch_sort(const SortArgs& s, int nt, int sms, cudaStream_t st);

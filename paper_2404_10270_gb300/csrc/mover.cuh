@@ -28,6 +28,7 @@
 // deposited here; a wall particle is deposited by the event kernel if it is
 // re-injected.
 #pragma once
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -429,6 +430,10 @@ __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams&
         if (c[k] < 0) continue;
         int j = (int)((uint32_t)c[k] & kCellMask);
         uint32_t clk = (uint32_t)c[k] >> kClockShift;
+        if (!in_range(a.err, j, 0, N)) {  // (bounds-checked build only)
+            c[k] = -1;
+            continue;
+        }
         // 1. gather (Listing 7) from the node pair (A_j, A_{j+1} - A_j)
         const T2 pr = __ldg(accp + node0 + j);
         T fk = f[k];
@@ -607,8 +612,8 @@ k_move(const __grid_constant__ MoveArgs a)
         const int64_t node0 = P.node;
         const int64_t quad = (tile - s_begin) * 32 + lane;
         const int64_t nq = a.seg_nmove[s] >> 2;
-        const bool act = quad < nq;
         const int64_t slot = P.base + 4 * quad;
+        const bool act = quad < nq && in_range(a.err, slot + 3, P.base, P.base + P.cap);
 
         int c[4] = {-1, -1, -1, -1};
         T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
@@ -632,6 +637,7 @@ k_move(const __grid_constant__ MoveArgs a)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 jd[k] = (c[k] >> 31) | (int)((uint32_t)c[k] & kCellMask);
+                if (jd[k] >= 0 && !in_range(a.err, jd[k], 0, P.ncells)) jd[k] = -1;
                 qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
             }
             warp_deposit<Q, true>(jd, qr, Prec<T>::S, a.dep + node0, nullptr);
@@ -658,6 +664,7 @@ k_move(const __grid_constant__ MoveArgs a)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             jd[k] = (c[k] >> 31) | (int)((uint32_t)c[k] & kCellMask);
+            if (jd[k] >= 0 && !in_range(a.err, jd[k], 0, P.ncells)) jd[k] = -1;
             qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
         }
         warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0,
@@ -680,18 +687,21 @@ k_move(const __grid_constant__ MoveArgs a)
 // its particles directly.
 constexpr int kSortSpan = 128;
 
-template <typename T, int NT>
+template <typename T, int NT, bool YP>
 struct SortSmem {
     static constexpr int NW = NT / 32;
     static constexpr int C = NW * 128;  // particles of a chunk
-    // staged particles (off, ux, uy, uz, yp in T; cell word, id; start-cell key), then
-    // the per-cell counts, run offsets in the chunk, global run starts, and the per-warp
-    // summaries (segment, lowest and highest start cell) of two consecutive chunks
-    static constexpr size_t bytes = (size_t)C * (5 * sizeof(T) + 4 + 4 + 2) +
+    // staged particles (off, ux, uy, uz and with YP yp in T; cell word, id; start-cell
+    // key), then the per-cell counts, run offsets in the chunk, global run starts, and
+    // the per-warp summaries (segment, lowest and highest start cell) of two consecutive
+    // chunks
+    static constexpr size_t bytes = (size_t)C * ((YP ? 5 : 4) * sizeof(T) + 4 + 4 + 2) +
                                     (size_t)3 * kSortSpan * 4 + (size_t)2 * 3 * NW * 4;
 };
 
-template <typename T, int NT, bool MAG, bool SUB, bool MIXED>
+// YP: some species drifts in y (MoveArgs.yp): the y coordinates are sorted with the
+// particles (a separate variant: carrying them costs the others registers).
+template <typename T, int NT, bool MAG, bool SUB, bool MIXED, bool YP>
 __global__ void __launch_bounds__(NT, MoveOccupancy<T, true, NT>::blocks)
 k_move_sort(const __grid_constant__ MoveArgs a)
 {
@@ -703,8 +713,8 @@ k_move_sort(const __grid_constant__ MoveArgs a)
     T* const s_ux = s_off + C;
     T* const s_uy = s_ux + C;
     T* const s_uz = s_uy + C;
-    T* const s_yp = s_uz + C;
-    int* const s_cell = reinterpret_cast<int*>(s_yp + C);
+    T* const s_yp = s_uz + C;  // (only with YP)
+    int* const s_cell = reinterpret_cast<int*>(s_yp + (YP ? C : 0));
     uint32_t* const s_id = reinterpret_cast<uint32_t*>(s_cell + C);
     unsigned short* const s_key = reinterpret_cast<unsigned short*>(s_id + C);
     int* const cnt = reinterpret_cast<int*>(s_key + C);
@@ -749,8 +759,9 @@ k_move_sort(const __grid_constant__ MoveArgs a)
         }
         const SegParams& P = a.seg[s];
         const int64_t quad = (tile - s_begin) * 32 + lane;
-        const bool act = have && quad < (a.seg_nmove[s] >> 2);
         const int64_t slot = P.base + 4 * quad;
+        const bool act = have && quad < (a.seg_nmove[s] >> 2) &&
+                         in_range(a.err, slot + 3, P.base, P.base + P.cap);
 
         int c[4] = {-1, -1, -1, -1};
         T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
@@ -773,6 +784,10 @@ k_move_sort(const __grid_constant__ MoveArgs a)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             j0[k] = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1;
+            if (j0[k] >= 0 && !in_range(a.err, j0[k], 0, P.ncells)) {  // (checked build)
+                j0[k] = -1;
+                c[k] = -1;
+            }
             if (j0[k] >= 0) {
                 lmin = min(lmin, (unsigned)j0[k]);
                 lmax = max(lmax, j0[k]);
@@ -854,6 +869,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
             for (int k = 0; k < 4; ++k) {
                 if (key[k] < 0) continue;
                 const int p = pre[key[k]] + rank[k];
+                if (!in_range(a.err, p, 0, C)) continue;  // (bounds-checked build only)
                 s_off[p] = f[k];
                 s_ux[p] = ux[k];
                 s_uy[p] = uy[k];
@@ -861,7 +877,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                 s_cell[p] = c[k];
                 s_id[p] = idq[k];
                 s_key[p] = (unsigned short)key[k];
-                if (a.yp) s_yp[p] = static_cast<const T*>(a.yp)[slot + k];
+                if (YP) s_yp[p] = static_cast<const T*>(a.yp)[slot + k];
                 const int64_t r = (int64_t)gb[key[k]] + rank[k];
                 to[k] = r < B.cap ? B.base + r : -1;
             }
@@ -888,7 +904,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                 __stcs(duy + g, s_uy[p]);
                 __stcs(duz + g, s_uz[p]);
                 __stcs(a.did + g, s_id[p]);
-                if (a.yp) static_cast<T*>(a.dyp)[g] = s_yp[p];
+                if (YP) static_cast<T*>(a.dyp)[g] = s_yp[p];
             }
         } else {
             // per warp: reserve each particle's slot by its start cell (equal cells of a
@@ -907,7 +923,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                                                  uy, uz, cand, wlo, whi, tst);
             sort_destinations(a, P, grp, rbase, had, to);
             sort_write<T>(a, to, c, f, ux, uy, uz, idq);
-            if (a.yp) {  // the y coordinates go along (read here, not held across the move)
+            if (YP) {  // the y coordinates go along
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (to[k] >= 0)
@@ -921,6 +937,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             jd[k] = (c[k] >> 31) | (int)((uint32_t)c[k] & kCellMask);
+            if (jd[k] >= 0 && !in_range(a.err, jd[k], 0, P.ncells)) jd[k] = -1;
             qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
         }
         warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + P.node, nullptr);
@@ -931,43 +948,62 @@ k_move_sort(const __grid_constant__ MoveArgs a)
 // variant (the dynamic shared-memory limit, needed above 48 KB) with the occupancy the
 // grid is sized by.  The set-up runs when the handle sizes its grids, outside any
 // stream capture.
-template <typename T, int NT, bool MAG, bool SUB, bool MIXED>
+template <typename T, int NT, bool MAG, bool SUB, bool MIXED, bool YP>
 inline cudaError_t launch_sort_variant(const MoveArgs& a, int grid, cudaStream_t st)
 {
-    k_move_sort<T, NT, MAG, SUB, MIXED><<<grid, NT, SortSmem<T, NT>::bytes, st>>>(a);
+    k_move_sort<T, NT, MAG, SUB, MIXED, YP><<<grid, NT, SortSmem<T, NT, YP>::bytes, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int NT, bool YP>
+inline cudaError_t launch_sort_step_yp(const MoveArgs& a, bool mag, bool sub, bool mixed,
+                                       int grid, cudaStream_t st)
+{
+    if (!mag)
+        return sub ? launch_sort_variant<T, NT, false, true, false, YP>(a, grid, st)
+                   : launch_sort_variant<T, NT, false, false, false, YP>(a, grid, st);
+    if (mixed)
+        return sub ? launch_sort_variant<T, NT, true, true, true, YP>(a, grid, st)
+                   : launch_sort_variant<T, NT, true, false, true, YP>(a, grid, st);
+    return sub ? launch_sort_variant<T, NT, true, true, false, YP>(a, grid, st)
+               : launch_sort_variant<T, NT, true, false, false, YP>(a, grid, st);
 }
 
 template <typename T, int NT>
 inline cudaError_t launch_sort_step(const MoveArgs& a, bool mag, bool sub, bool mixed, int grid,
                                     cudaStream_t st)
 {
-    if (!mag)
-        return sub ? launch_sort_variant<T, NT, false, true, false>(a, grid, st)
-                   : launch_sort_variant<T, NT, false, false, false>(a, grid, st);
-    if (mixed)
-        return sub ? launch_sort_variant<T, NT, true, true, true>(a, grid, st)
-                   : launch_sort_variant<T, NT, true, false, true>(a, grid, st);
-    return sub ? launch_sort_variant<T, NT, true, true, false>(a, grid, st)
-               : launch_sort_variant<T, NT, true, false, false>(a, grid, st);
+    return a.yp ? launch_sort_step_yp<T, NT, true>(a, mag, sub, mixed, grid, st)
+                : launch_sort_step_yp<T, NT, false>(a, mag, sub, mixed, grid, st);
 }
 
+template <typename T, int NT, bool YP>
+inline cudaError_t sort_step_setup(int* blocks_mag, int* blocks_plain)
+{
+    const int sm = (int)SortSmem<T, NT, YP>::bytes;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_move_sort<T, NT, false, false, false, YP>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, false, true, false, YP>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, false, false, YP>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, true, false, YP>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, false, true, YP>, A, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, true, true, YP>, A, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_mag, k_move_sort<T, NT, true, false, false, YP>, NT, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_plain, k_move_sort<T, NT, false, false, false, YP>, NT, sm);
+    return e;
+}
+
+// Blocks per SM the sort-step grid is sized by: the fewer of the two variants (with
+// and without the y coordinates), so that one grid serves both.
 template <typename T, int NT>
 inline int sort_step_blocks_per_sm(bool mag)
 {
-    const int sm = (int)SortSmem<T, NT>::bytes;
-    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_move_sort<T, NT, false, false, false>, A, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, false, true, false>, A, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, false, false>, A, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, true, false>, A, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, false, true>, A, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_move_sort<T, NT, true, true, true>, A, sm);
-    int n = 0;
-    if (e == cudaSuccess)
-        e = mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_sort<T, NT, true, false, false>, NT, sm)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_sort<T, NT, false, false, false>, NT, sm);
-    return e == cudaSuccess ? n : 0;
+    int m0 = 0, p0 = 0, m1 = 0, p1 = 0;
+    if (sort_step_setup<T, NT, false>(&m0, &p0) != cudaSuccess) return 0;
+    if (sort_step_setup<T, NT, true>(&m1, &p1) != cudaSuccess) return 0;
+    return mag ? std::min(m0, m1) : std::min(p0, p1);
 }
 
 }  // namespace bitpic

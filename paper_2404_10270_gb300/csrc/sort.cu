@@ -40,12 +40,14 @@ __global__ void __launch_bounds__(NT) k_hist(const SortArgs a)
         const int64_t quad = (tile - a.tile_start[s]) * 32 + lane;
         const int64_t nq = a.seg_nmove[s] >> 2;
         int c[4] = {-1, -1, -1, -1};
-        if (quad < nq) {
+        if (quad < nq && in_range(a.err, 4 * quad + 3, 0, P.cap)) {
             const int4 cc = *reinterpret_cast<const int4*>(cell + P.base + 4 * quad);
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+            if (c[k] >= 0 && !in_range(a.err, (int)((uint32_t)c[k] & kCellMask), 0, P.ncells))
+                c[k] = -1;  // (bounds-checked build only)
             // sort key: the cell index (empty slots get distinct keys and never group)
             const int key = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1 - lane;
             const unsigned grp = __match_any_sync(0xffffffffu, key);
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
         const int64_t quad = (tile - ls_begin) * 32 + lane;
         q.slot = a.seg[ls].base + 4 * quad;
         q.c[0] = q.c[1] = q.c[2] = q.c[3] = -1;
-        if (quad < (a.seg_nmove[ls] >> 2)) {
+        if (quad < (a.seg_nmove[ls] >> 2) && in_range(a.err, 4 * quad + 3, 0, a.seg[ls].cap)) {
             // the whole quad with 128-bit loads (the mover's access pattern)
             const int4 cc = __ldcs(reinterpret_cast<const int4*>(cell + q.slot));
             q.c[0] = cc.x; q.c[1] = cc.y; q.c[2] = cc.z; q.c[3] = cc.w;
@@ -209,6 +211,9 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
         int key[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+            if (cur.c[k] >= 0 &&
+                !in_range(a.err, (int)((uint32_t)cur.c[k] & kCellMask), 0, P.ncells))
+                cur.c[k] = -1;  // (bounds-checked build only)
             key[k] = cur.c[k] >= 0 ? (int)((uint32_t)cur.c[k] & kCellMask) : -1 - lane;
             grp[k] = __match_any_sync(0xffffffffu, key[k]);
         }
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const unsigned b = __shfl_sync(0xffffffffu, base[k], __ffs(grp[k]) - 1);
-            if (cur.c[k] >= 0) {
+            if (cur.c[k] >= 0 && in_range(a.err, (int64_t)b + __popc(grp[k] & lt), 0, P.cap)) {
                 const int64_t to = P.base + (int64_t)b + __popc(grp[k] & lt);
                 dcell[to] = cur.c[k];
                 doff[to] = cur.vo[k];
