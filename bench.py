@@ -573,9 +573,10 @@ def cpu_oracle_instances(physs, loads, steps):
 def _e2e_pass(sim, host, outs, phys, args, world):
     """One end-to-end pass through the public API: load every species from pinned host
     memory, args.steps steps, the moments, every particle read back to pinned host
-    memory.  The FP32 form's data travel as float (pic_load_particles_f32,
-    pic_get_particles_f32: 24 B per particle each way).  Returns (seconds, max over
-    ranks; breakdown; moments; bytes read back)."""
+    memory.  The FP32 form's data travel as float (pic_load_particles_f32: 20 B per
+    particle, the ids numbered on the device; pic_get_particles_f32: 24 B with the ids);
+    from pinned memory the library's load kernel reads the host arrays itself.
+    Returns (seconds, max over ranks; breakdown; moments; bytes read back)."""
     import ctypes as C
     import torch
     from paper_2404_10270_gb300 import capi
@@ -585,7 +586,8 @@ def _e2e_pass(sim, host, outs, phys, args, world):
     t0 = time.perf_counter()
     t_sp = []
     for s, h in enumerate(host):
-        sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz", "id")]))
+        # a fresh start: the library numbers the particles itself (the same ids)
+        sim.load(0, s, W.Load(*[h[k][1] for k in ("cell", "off", "vx", "vy", "vz")], None))
         t_sp.append(time.perf_counter())
     t_load = time.perf_counter()
     sim.step(args.steps)
@@ -633,7 +635,7 @@ def _run_ours(args, stream, rank, world, local):
         off32 = np.minimum(ld.off.astype(np.float32), np.float32(1.0) - np.float32(2.0 ** -24))
         host32.append({"cell": pinned(ld.cell), "off": pinned(off32),
                        "vx": pinned(ld.vx.astype(np.float32)), "vy": pinned(ld.vy.astype(np.float32)),
-                       "vz": pinned(ld.vz.astype(np.float32)), "id": pinned(ld.id)})
+                       "vz": pinned(ld.vz.astype(np.float32))})
         outs.append({k: pinned(np.zeros(m, dt))[1] for k, dt in
                      (("cell", np.int32), ("off", np.float32), ("vx", np.float32),
                       ("vy", np.float32), ("vz", np.float32), ("id", np.uint32))})
@@ -653,7 +655,7 @@ def _run_ours(args, stream, rank, world, local):
     e2e_passes.sort(key=lambda x: x[0])
     e2e_s, e2e_parts, mom, d2h = e2e_passes[1]
     e2e_value = n * world * args.steps / e2e_s
-    h2d = n * 24  # cell, id (4 B each) and four floats per particle
+    h2d = n * 20  # cell (4 B) and four floats per particle (the ids are numbered on the device)
     assert mom["step"] > 0
     e2e_parts["passes_s"] = [p[0] for p in e2e_passes]
 
@@ -733,8 +735,8 @@ def _run_ours(args, stream, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps,
-                    "what": "load_f32 from pinned host + %d steps + moments + get_f32 to pinned "
-                            "host; median of 3" % args.steps,
+                    "what": "load_f32 (no ids) from pinned host + %d steps + moments + get_f32 "
+                            "to pinned host; median of 3" % args.steps,
                     "breakdown": e2e_parts},
             "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"],
