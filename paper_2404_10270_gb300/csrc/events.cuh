@@ -370,19 +370,43 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
             const int64_t begin = P.base + (j > 0 ? (int64_t)a.hist[n - 1] : 0);
             int64_t end = P.base + (int64_t)a.hist[n];
             if (!in_range(a.err, end - 1, begin - 1, P.base + P.cap)) end = begin;
+            // a range of up to 128 targets (the usual ~nref) is read once, four entries per
+            // lane with their cell and id loads issued together, and every selection below
+            // works on registers; a longer range is scanned again for each conversion
+            const bool held = end - begin <= 128;
+            uint32_t hid[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t g = begin + lane + 32 * q;
+                hid[q] = 0xFFFFFFFFu;  // not live (no live target has this id: ids < 2^32 - 1)
+                if (held && g < end) {
+                    const int cg = a.cell[g];
+                    const uint32_t ig = a.id[g];
+                    if (cg >= 0) hid[q] = ig;
+                }
+            }
             uint32_t last = 0;
             bool first = true;
             for (unsigned k = 0; k < r; ++k) {
-                // the next smallest live id of the range, 32 entries per pass
+                // the next smallest live id of the range
                 uint32_t best = 0xFFFFFFFFu;
                 int64_t v = -1;
-                for (int64_t g0 = begin; g0 < end; g0 += 32) {
-                    const int64_t g = g0 + lane;
-                    if (g < end && a.cell[g] >= 0) {
-                        const uint32_t idg = a.id[g];
-                        if ((first || idg > last) && idg < best) {
-                            best = idg;
-                            v = g;
+                if (held) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (hid[q] != 0xFFFFFFFFu && (first || hid[q] > last) && hid[q] < best) {
+                            best = hid[q];
+                            v = begin + lane + 32 * q;
+                        }
+                } else {
+                    for (int64_t g0 = begin; g0 < end; g0 += 32) {
+                        const int64_t g = g0 + lane;
+                        if (g < end && a.cell[g] >= 0) {
+                            const uint32_t idg = a.id[g];
+                            if ((first || idg > last) && idg < best) {
+                                best = idg;
+                                v = g;
+                            }
                         }
                     }
                 }
