@@ -702,11 +702,14 @@ int collect_times(pic_handle* h)
 void set_block(pic_handle* h, int nt)
 {
     h->nt = nt;
-    const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, false, nt)
-                                             : move_blocks_per_sm_f32(h->any_mag, false, nt);
+    const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, false, false, nt)
+                                             : move_blocks_per_sm_f32(h->any_mag, false, false, nt);
     h->grid_move = h->sms * std::max(bps, 1);
-    const int bss = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, true, nt)
-                                             : move_blocks_per_sm_f32(h->any_mag, true, nt);
+    // (the sort step's variant with the y coordinates of 2-D species holds more shared
+    // memory a block)
+    const int bss = h->precision == PIC_FP64
+                        ? move_blocks_per_sm_f64(h->any_mag, true, h->any_sn2d, nt)
+                        : move_blocks_per_sm_f32(h->any_mag, true, h->any_sn2d, nt);
     h->grid_sort = h->sms * std::max(bss, 1);
 }
 

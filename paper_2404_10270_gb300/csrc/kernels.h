@@ -31,8 +31,8 @@ cudaError_t launch_victims(const MoveArgs& a, int precision, int grid, cudaStrea
 // The y drift of 2-D species after the mover (MoveArgs.yp non-null), before the events.
 cudaError_t launch_drift_y(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
-int move_blocks_per_sm_f32(bool mag, bool sort, int nt);
-int move_blocks_per_sm_f64(bool mag, bool sort, int nt);
+int move_blocks_per_sm_f32(bool mag, bool sort, bool yp, int nt);
+int move_blocks_per_sm_f64(bool mag, bool sort, bool yp, int nt);
 
 // ---- field phase and bookkeeping (field.cu) -------------------------------------
 struct FieldArgs {

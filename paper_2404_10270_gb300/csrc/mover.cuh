@@ -269,19 +269,44 @@ __device__ __forceinline__ void st4(double* p, const double v[4])
 // Warp-level deposit of four particles per lane.  With Q = rint(f S) the charge of
 // one particle is S - Q on node j and Q on node j+1, so the total on node c is
 //     S n_c - R_c + R_{c-1},   n_c = particles in cell c,  R_c = sum of their Q.
-// The warp's particles usually sit in a few neighbouring cells (they are sorted by
-// cell), so per occupied cell the warp forms n_c and R_c by register reductions; lane
-// l then owns node wmin + l, takes R_{c-1} from lane l-1 by shuffle, and adds the node
-// total to HBM with one 64-bit reduction (no return value, so nothing waits on it).
+// The warp forms n_c and R_c for every cell of its range [wmin, wmax]; lane l then
+// owns node wmin + l, takes R_{c-1} from lane l-1 by shuffle, and adds the node total
+// to HBM with one 64-bit reduction (no return value, so nothing waits on it).  A warp
+// whose particles sit in a few cells (the store was sorted recently) forms the sums by
+// register reductions, one round per cell; one whose particles have spread over more
+// cells (late in a sort cycle) adds each lane's runs of equal cells into a window of
+// 32 cells in shared memory (`win`, the warp's own, zero outside this call), which
+// costs the same few instructions whatever the spread; beyond 32 cells every particle
+// goes to HBM on its own.
 // jd = -1 marks an empty slot: as unsigned it is never the minimum of a live cell, as
 // signed never the maximum, and it matches no cell.
 // NEG: take the quad's charge away instead (two's complement sums; the counts are not
 // touched), for a particle deposit that is kept from step to step and updated.
+constexpr int kDepLoopCells = 6;  // register reductions up to this many cells
+
+// Words of a warp's deposit window: 32 counts and 32 charge sums (FP64: the 48-bit
+// charges as two 24-bit halves; a half summed over a tile of 128 stays below 2^31).
+template <typename Q>
+struct DepWin {
+    static constexpr int words = sizeof(Q) == 4 ? 64 : 96;
+};
+
+// Clear the warp's window (once, before its first deposit).
+template <typename Q>
+__device__ __forceinline__ void dep_win_clear(uint32_t* win)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < DepWin<Q>::words / 32; ++i) win[32 * i + lane] = 0u;
+    __syncwarp();
+}
+
 template <typename Q, bool NEG = false>
 __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
                                              unsigned long long S,
                                              unsigned long long* __restrict__ gdep,
-                                             unsigned* __restrict__ ghist)
+                                             unsigned* __restrict__ ghist,
+                                             uint32_t* __restrict__ win)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -300,42 +325,83 @@ __device__ __forceinline__ void warp_deposit(const int jd[4], const Q qr[4],
     if (ncell < 32) {
         unsigned long long myR = 0;  // R_c of cell wmin + lane
         uint32_t myn = 0;            // n_c of cell wmin + lane
-        for (int i = 0; i < ncell; ++i) {
-            const int cidx = wmin + i;
-            uint32_t n = 0;
-            if (sizeof(Q) == 4) {
-                uint32_t r = 0;  // at most 128 x 2^24 < 2^32
+        if (ncell <= kDepLoopCells) {
+            for (int i = 0; i < ncell; ++i) {
+                const int cidx = wmin + i;
+                uint32_t n = 0;
+                if (sizeof(Q) == 4) {
+                    uint32_t r = 0;  // at most 128 x 2^24 < 2^32
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const bool in = jd[k] == cidx;
-                    r += in ? (uint32_t)qr[k] : 0u;
-                    n += in ? 1u : 0u;
-                }
-                const uint32_t tr = __reduce_add_sync(FULL, r);
-                const uint32_t tn = __reduce_add_sync(FULL, n);
-                if (lane == i) {
-                    myR = tr;
-                    myn = tn;
-                }
-            } else {
-                // 48-bit charges: reduce the high and low 24-bit halves separately
-                uint32_t lo = 0, hi = 0;
+                    for (int k = 0; k < 4; ++k) {
+                        const bool in = jd[k] == cidx;
+                        r += in ? (uint32_t)qr[k] : 0u;
+                        n += in ? 1u : 0u;
+                    }
+                    const uint32_t tr = __reduce_add_sync(FULL, r);
+                    const uint32_t tn = __reduce_add_sync(FULL, n);
+                    if (lane == i) {
+                        myR = tr;
+                        myn = tn;
+                    }
+                } else {
+                    // 48-bit charges: reduce the high and low 24-bit halves separately
+                    uint32_t lo = 0, hi = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const bool in = jd[k] == cidx;
-                    const uint64_t q = in ? (uint64_t)qr[k] : 0ull;
-                    lo += (uint32_t)(q & 0xFFFFFFu);
-                    hi += (uint32_t)(q >> 24);
-                    n += in ? 1u : 0u;
-                }
-                const uint32_t tl = __reduce_add_sync(FULL, lo);
-                const uint32_t th = __reduce_add_sync(FULL, hi);
-                const uint32_t tn = __reduce_add_sync(FULL, n);
-                if (lane == i) {
-                    myR = ((unsigned long long)th << 24) + tl;
-                    myn = tn;
+                    for (int k = 0; k < 4; ++k) {
+                        const bool in = jd[k] == cidx;
+                        const uint64_t q = in ? (uint64_t)qr[k] : 0ull;
+                        lo += (uint32_t)(q & 0xFFFFFFu);
+                        hi += (uint32_t)(q >> 24);
+                        n += in ? 1u : 0u;
+                    }
+                    const uint32_t tl = __reduce_add_sync(FULL, lo);
+                    const uint32_t th = __reduce_add_sync(FULL, hi);
+                    const uint32_t tn = __reduce_add_sync(FULL, n);
+                    if (lane == i) {
+                        myR = ((unsigned long long)th << 24) + tl;
+                        myn = tn;
+                    }
                 }
             }
+        } else {
+            // each run of equal cells among the lane's four (consecutive) particles is
+            // added to the window once
+            uint32_t n = 0, lo = 0, hi = 0;
+            int cur = -1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (jd[k] != cur) {
+                    if (cur >= 0) {
+                        atomicAdd(win + (cur - wmin), n);
+                        atomicAdd(win + 32 + (cur - wmin), lo);
+                        if (sizeof(Q) == 8) atomicAdd(win + 64 + (cur - wmin), hi);
+                    }
+                    cur = jd[k];
+                    n = lo = hi = 0u;
+                }
+                if (jd[k] >= 0) {
+                    n += 1u;
+                    if (sizeof(Q) == 4) {
+                        lo += (uint32_t)qr[k];
+                    } else {
+                        lo += (uint32_t)((uint64_t)qr[k] & 0xFFFFFFu);
+                        hi += (uint32_t)((uint64_t)qr[k] >> 24);
+                    }
+                }
+            }
+            if (cur >= 0) {
+                atomicAdd(win + (cur - wmin), n);
+                atomicAdd(win + 32 + (cur - wmin), lo);
+                if (sizeof(Q) == 8) atomicAdd(win + 64 + (cur - wmin), hi);
+            }
+            __syncwarp();
+            myn = win[lane];
+            myR = win[32 + lane];
+            if (sizeof(Q) == 8) myR += (unsigned long long)win[64 + lane] << 24;
+            win[lane] = 0u;  // (lanes past the range read and write zeros)
+            win[32 + lane] = 0u;
+            if (sizeof(Q) == 8) win[64 + lane] = 0u;
+            __syncwarp();
         }
         const unsigned long long prevR = __shfl_up_sync(FULL, myR, 1);
         if (lane <= ncell) {
@@ -572,6 +638,9 @@ k_move(const __grid_constant__ MoveArgs a)
         const bool tstep = step % kGapMax == 0 || *a.test_all != 0;
         if (tstep != TEST) return;
     }
+    __shared__ uint32_t s_dwin[NT / 32][DepWin<Q>::words];  // the warps' deposit windows
+    uint32_t* const dwin = s_dwin[threadIdx.x >> 5];
+    dep_win_clear<Q>(dwin);
     const int64_t total = a.tile_start[a.nseg];
     const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
     int s = 0;                         // segment of the previous tile (tiles only increase)
@@ -640,7 +709,7 @@ k_move(const __grid_constant__ MoveArgs a)
                 if (jd[k] >= 0 && !in_range(a.err, jd[k], 0, P.ncells)) jd[k] = -1;
                 qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
             }
-            warp_deposit<Q, true>(jd, qr, Prec<T>::S, a.dep + node0, nullptr);
+            warp_deposit<Q, true>(jd, qr, Prec<T>::S, a.dep + node0, nullptr, dwin);
         }
         if (MOVE && (!SUB || moves)) {
             unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
@@ -668,7 +737,7 @@ k_move(const __grid_constant__ MoveArgs a)
             qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
         }
         warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + node0,
-                        a.hist_out ? a.hist_out + node0 : nullptr);
+                        a.hist_out ? a.hist_out + node0 : nullptr, dwin);
     }
 }
 
@@ -727,6 +796,9 @@ k_move_sort(const __grid_constant__ MoveArgs a)
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    __shared__ uint32_t s_dwin[NW][DepWin<Q>::words];  // the warps' deposit windows
+    uint32_t* const dwin = s_dwin[warp];
+    dep_win_clear<Q>(dwin);
     T* const offp = static_cast<T*>(a.off);
     T* const uxp = static_cast<T*>(a.ux);
     T* const uyp = static_cast<T*>(a.uy);
@@ -802,16 +874,20 @@ k_move_sort(const __grid_constant__ MoveArgs a)
         }
         for (int i = threadIdx.x; i < kSortSpan; i += NT) cnt[i] = 0;
         __syncthreads();
-        int bseg = -1, bmin = INT_MAX, bmax = -1;
-        bool one = true;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int ws = wseg[w];
-            if (ws < 0) continue;
-            if (bseg < 0) bseg = ws;
-            else if (ws != bseg) one = false;
-            bmin = min(bmin, wmin[w]);
-            bmax = max(bmax, wmax[w]);
+        // the chunk's segment (one if every warp's live particles are in the same one)
+        // and its span of start cells, from the per-warp summaries
+        int bseg, bmin, bmax;
+        bool one;
+        {
+            const int ws = lane < NW ? wseg[lane] : -1;
+            const int mn = ws >= 0 ? wmin[lane] : INT_MAX;
+            const int mx = ws >= 0 ? wmax[lane] : -1;
+            const int smax = __reduce_max_sync(FULL, ws);
+            const int smin = __reduce_min_sync(FULL, ws >= 0 ? ws : INT_MAX);
+            bseg = smax;
+            one = smax < 0 || smin == smax;
+            bmin = __reduce_min_sync(FULL, mn);
+            bmax = __reduce_max_sync(FULL, mx);
         }
         const bool staged = one && bseg >= 0 && bmax - bmin < kSortSpan;
         unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
@@ -940,7 +1016,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
             if (jd[k] >= 0 && !in_range(a.err, jd[k], 0, P.ncells)) jd[k] = -1;
             qr[k] = c[k] >= 0 ? (Q)Prec<T>::qright(f[k]) : (Q)0;
         }
-        warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + P.node, nullptr);
+        warp_deposit<Q>(jd, qr, Prec<T>::S, a.dep + P.node, nullptr, dwin);
     }
 }
 
@@ -995,15 +1071,15 @@ inline cudaError_t sort_step_setup(int* blocks_mag, int* blocks_plain)
     return e;
 }
 
-// Blocks per SM the sort-step grid is sized by: the fewer of the two variants (with
-// and without the y coordinates), so that one grid serves both.
+// Blocks per SM the sort-step grid is sized by (YP: the variant with the y coordinates,
+// launched when some species drifts in y; it holds more shared memory).
 template <typename T, int NT>
-inline int sort_step_blocks_per_sm(bool mag)
+inline int sort_step_blocks_per_sm(bool mag, bool yp)
 {
-    int m0 = 0, p0 = 0, m1 = 0, p1 = 0;
-    if (sort_step_setup<T, NT, false>(&m0, &p0) != cudaSuccess) return 0;
-    if (sort_step_setup<T, NT, true>(&m1, &p1) != cudaSuccess) return 0;
-    return mag ? std::min(m0, m1) : std::min(p0, p1);
+    int m = 0, p = 0;
+    const cudaError_t e = yp ? sort_step_setup<T, NT, true>(&m, &p) : sort_step_setup<T, NT, false>(&m, &p);
+    if (e != cudaSuccess) return 0;
+    return mag ? m : p;
 }
 
 }  // namespace bitpic

@@ -32,9 +32,9 @@ cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, boo
 }
 
 template <int NT>
-int occupancy(bool mag, bool sort)
+int occupancy(bool mag, bool sort, bool yp)
 {
-    if (sort) return sort_step_blocks_per_sm<double, NT>(mag);
+    if (sort) return sort_step_blocks_per_sm<double, NT>(mag, yp);
     int n = 0;
     const cudaError_t e =
         mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<double, NT, true, true, false, false, true>, NT, 0)
@@ -53,12 +53,12 @@ cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bo
     }
 }
 
-int move_blocks_per_sm_f64(bool mag, bool sort, int nt)
+int move_blocks_per_sm_f64(bool mag, bool sort, bool yp, int nt)
 {
     switch (nt) {
-        case 128: return occupancy<128>(mag, sort);
-        case 512: return occupancy<512>(mag, sort);
-        default: return occupancy<256>(mag, sort);
+        case 128: return occupancy<128>(mag, sort, yp);
+        case 512: return occupancy<512>(mag, sort, yp);
+        default: return occupancy<256>(mag, sort, yp);
     }
 }
 
