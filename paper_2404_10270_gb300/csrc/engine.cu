@@ -106,7 +106,7 @@ struct pic_handle {
     int64_t *seg_nmove = nullptr, *tile_start = nullptr;
     unsigned long long *wall_count = nullptr, *collisions = nullptr, *ev_count = nullptr,
                        *next_id = nullptr;
-    unsigned* births_done = nullptr;  // per instance: blocks of k_births that finished
+    uint32_t *birth_keys_a = nullptr, *birth_keys_b = nullptr;  // k_births: parent ids being sorted
     unsigned long long* cell_part = nullptr;  // sort: per segment and 4096-cell chunk
     int cell_chunks = 1;
     double* wall_energy = nullptr;
@@ -1082,7 +1082,8 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (rc == PIC_OK) rc = dalloc(h, &h->rare, (size_t)h->rare_cap);
     if (rc == PIC_OK) rc = dalloc(h, &h->rare_count, 2);
     if (rc == PIC_OK) rc = dalloc(h, &h->next_id, (size_t)h->ninst);
-    if (rc == PIC_OK) rc = dalloc(h, &h->births_done, (size_t)h->ninst);
+    if (rc == PIC_OK) rc = dalloc(h, &h->birth_keys_a, (size_t)std::max<int64_t>(h->ev_total, 1));
+    if (rc == PIC_OK) rc = dalloc(h, &h->birth_keys_b, (size_t)std::max<int64_t>(h->ev_total, 1));
     h->cell_chunks = (h->max_nodes + 4095) / 4096;
     if (rc == PIC_OK) rc = dalloc(h, &h->cell_part, (size_t)h->nseg * h->cell_chunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->err, 1);
@@ -1126,7 +1127,6 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (e == cudaSuccess) e = z(h->collisions, (size_t)h->ninst * kMaxProc * 8);
     if (e == cudaSuccess) e = z(h->ev_count, (size_t)h->ninst * 8);
     if (e == cudaSuccess) e = z(h->next_id, (size_t)h->ninst * 8);
-    if (e == cudaSuccess) e = z(h->births_done, (size_t)h->ninst * 4);
     if (e == cudaSuccess) e = z(h->err, 4);
     if (e == cudaSuccess) e = z(h->step_d, 8);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->test_all, 1, sizeof(int), s);
@@ -1334,7 +1334,8 @@ int enqueue_step(pic_handle* h)
         Span sp(h, 3);
         h->kernels += 1;
         CUDA_TRY(h, launch_births(h->instd, h->ninst, h->events, h->ev_count, h->next_id,
-                                  h->st[h->cur].id, h->err, h->births_done, h->stream));
+                                  h->st[h->cur].id, h->birth_keys_a, h->birth_keys_b, h->err,
+                                  h->stream));
     }
     {
         Span sp(h, 1);

@@ -24,7 +24,6 @@ namespace bitpic {
 namespace {
 
 constexpr int kFieldThreads = 1024;
-constexpr int kBirthParts = 16;  // blocks per instance that rank its ionization events
 
 __device__ __forceinline__ i128 warp_incl_scan(i128 v)
 {
@@ -324,16 +323,24 @@ __global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned l
 
 // Children of this step's ionization events are numbered after the largest id so
 // far: electron 2r, ion 2r+1, r = rank of the parent id among this step's events (with
-// a neutral particle target only the electron is new: id r).  Blocks (instance, part):
-// each part ranks a share of the instance's events against all of them; the last part
-// to finish advances the instance's next id.
-__global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* events,
-                                                unsigned long long* ev_count,
-                                                unsigned long long* next_id, uint32_t* id,
-                                                unsigned* err, unsigned* done)
+// a neutral particle target only the electron is new: id r).  One block per instance
+// sorts the parent ids (a stable least-significant-digit radix sort, 8 bits a pass,
+// as many passes as the largest id so far needs; the ids of one step are distinct)
+// and ranks every event by a binary search in the sorted ids, then advances the
+// instance's next id: O(n) work per pass for n events.
+constexpr int kBirthThreads = 1024;
+
+__global__ void __launch_bounds__(kBirthThreads) k_births(const InstParams* inst, Event* events,
+                                                          unsigned long long* ev_count,
+                                                          unsigned long long* next_id, uint32_t* id,
+                                                          uint32_t* keys_a, uint32_t* keys_b,
+                                                          unsigned* err)
 {
-    __shared__ uint32_t sp[1024];
-    __shared__ bool last;
+    constexpr int NW = kBirthThreads / 32;
+    __shared__ unsigned hist[256];     // digit counts of the pass
+    __shared__ unsigned run[256];      // next slot of each digit in the pass's output
+    __shared__ unsigned tot[256];      // digit counts of the tile
+    __shared__ unsigned short wcnt[NW][256];  // digit counts of each warp in the tile
     const int b = blockIdx.x;
     const InstParams& I = inst[b];
     const unsigned long long cnt = ev_count[b];
@@ -346,36 +353,93 @@ __global__ void __launch_bounds__(256) k_births(const InstParams* inst, Event* e
         if (threadIdx.x == 0) set_error(err, kErrCapacity);
         return;
     }
-    const int64_t stride = (int64_t)gridDim.y * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.y * blockDim.x; i0 < n; i0 += stride) {
-        const int64_t i = i0 + threadIdx.x;
-        const uint32_t p = i < n ? ev[i].parent : 0u;
-        int64_t rank = 0;
-        for (int64_t k0 = 0; k0 < n; k0 += 1024) {
-            const int64_t m = min((int64_t)1024, n - k0);
-            __syncthreads();
-            for (int64_t k = threadIdx.x; k < m; k += blockDim.x) sp[k] = ev[k0 + k].parent;
-            __syncthreads();
-            if (i < n)
-                for (int64_t k = 0; k < m; ++k) rank += sp[k] < p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+    uint32_t* buf[2] = {keys_a + I.ev_base, keys_b + I.ev_base};
+    // every parent id is below the next id: passes for its significant bytes
+    int passes = 0;
+    for (unsigned long long m = base > 0 ? base - 1 : 0; m != 0; m >>= 8) ++passes;
+    if (passes == 0) passes = 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        const uint32_t* src = buf[(pass + 1) & 1];
+        uint32_t* dst = buf[pass & 1];
+        auto key = [&](int64_t i) -> uint32_t { return pass == 0 ? ev[i].parent : src[i]; };
+        for (int d = threadIdx.x; d < 256; d += kBirthThreads) hist[d] = 0u;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < n; i += kBirthThreads)
+            atomicAdd(&hist[(key(i) >> shift) & 255u], 1u);
+        __syncthreads();
+        if (warp == 0) {  // exclusive scan of the 256 counts, 8 a lane
+            unsigned v[8], sum = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                v[k] = hist[lane * 8 + k];
+                sum += v[k];
+            }
+            unsigned inc = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned t = __shfl_up_sync(FULL, inc, d);
+                if (lane >= d) inc += t;
+            }
+            unsigned r = inc - sum;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                run[lane * 8 + k] = r;
+                r += v[k];
+            }
         }
-        if (i < n) {
-            // an event whose creation overflowed (already latched) has no slots
-            if (ev[i].slot_e >= 0) id[ev[i].slot_e] = (uint32_t)(base + per * (unsigned long long)rank);
-            if (per == 2ull && ev[i].slot_i >= 0)
-                id[ev[i].slot_i] = (uint32_t)(base + 2ull * (unsigned long long)rank + 1ull);
+        // tiles of kBirthThreads keys in index order: a key's place is its digit's next
+        // slot plus the keys of the same digit before it in the tile (earlier warps,
+        // then lower lanes), so equal digits keep their order
+        for (int64_t t0 = 0; t0 < n; t0 += kBirthThreads) {
+            for (int e = threadIdx.x; e < NW * 256; e += kBirthThreads) (&wcnt[0][0])[e] = 0;
+            __syncthreads();
+            const int64_t i = t0 + threadIdx.x;
+            const bool have = i < n;
+            const uint32_t k = have ? key(i) : 0u;
+            const int d = have ? (int)((k >> shift) & 255u) : 256 + lane;
+            const unsigned grp = __match_any_sync(FULL, d);
+            if (have && lane == __ffs(grp) - 1) wcnt[warp][d] = (unsigned short)__popc(grp);
+            __syncthreads();
+            if (threadIdx.x < 256) {  // per digit: the warps' counts become their offsets
+                unsigned r = 0;
+                for (int w = 0; w < NW; ++w) {
+                    const unsigned c = wcnt[w][threadIdx.x];
+                    wcnt[w][threadIdx.x] = (unsigned short)r;
+                    r += c;
+                }
+                tot[threadIdx.x] = r;
+            }
+            __syncthreads();
+            if (have) {
+                const unsigned at = run[d] + wcnt[warp][d] + __popc(grp & lt);
+                if (at < (unsigned)n) dst[at] = k;
+            }
+            __syncthreads();
+            if (threadIdx.x < 256) run[threadIdx.x] += tot[threadIdx.x];
         }
+        __syncthreads();
+    }
+    // rank of every event: its parent's place among the sorted ids
+    const uint32_t* sorted = buf[(passes - 1) & 1];
+    for (int64_t i = threadIdx.x; i < n; i += kBirthThreads) {
+        const uint32_t p = ev[i].parent;
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (sorted[mid] < p) lo = mid + 1; else hi = mid;
+        }
+        // an event whose creation overflowed (already latched) has no slots
+        if (ev[i].slot_e >= 0) id[ev[i].slot_e] = (uint32_t)(base + per * (unsigned long long)lo);
+        if (per == 2ull && ev[i].slot_i >= 0)
+            id[ev[i].slot_i] = (uint32_t)(base + 2ull * (unsigned long long)lo + 1ull);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(done + b, 1u) == gridDim.y - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
         next_id[b] = base + per * (unsigned long long)n;
         ev_count[b] = 0ull;
-        done[b] = 0u;
     }
 }
 
@@ -408,9 +472,10 @@ cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_
 
 cudaError_t launch_births(const InstParams* inst, int ninst, Event* events,
                           unsigned long long* ev_count, unsigned long long* next_id,
-                          uint32_t* id, unsigned* err, unsigned* done, cudaStream_t st)
+                          uint32_t* id, uint32_t* keys_a, uint32_t* keys_b, unsigned* err,
+                          cudaStream_t st)
 {
-    k_births<<<dim3(ninst, kBirthParts), 256, 0, st>>>(inst, events, ev_count, next_id, id, err, done);
+    k_births<<<ninst, kBirthThreads, 0, st>>>(inst, events, ev_count, next_id, id, keys_a, keys_b, err);
     return cudaGetLastError();
 }
 

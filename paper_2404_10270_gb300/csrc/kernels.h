@@ -75,7 +75,8 @@ cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_
 // `done`: one zeroed counter per instance (left zeroed).
 cudaError_t launch_births(const InstParams* inst, int ninst, Event* events,
                           unsigned long long* ev_count, unsigned long long* next_id,
-                          uint32_t* id, unsigned* err, unsigned* done, cudaStream_t st);
+                          uint32_t* id, uint32_t* keys_a, uint32_t* keys_b, unsigned* err,
+                          cudaStream_t st);
 
 // ---- sort (sort.cu) ---------------------------------------------------------------
 struct SortArgs {

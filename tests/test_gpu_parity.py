@@ -282,6 +282,25 @@ def test_magnetized_source_with_ionization_fp64_parity():
     assert_same_clocks(g, o)
 
 
+def test_thousands_of_ionizations_a_step_number_children_like_the_oracle():
+    """Several thousand ionizations a step with ids past 2^16: the children's ids (the
+    rank of each parent id among the step's events) come from a multi-tile, three-pass
+    sort of the parent ids and must equal the oracle's, particle by particle."""
+    phys = W.magnetized_source(ncells=512, ppc=100, seed=12, nu=3.0, capacity_factor=3.0)
+    loads = W.initial_load(phys, seed=12)
+    steps = 6
+    g, gm = run_gpu(phys, loads, steps, capi.FP64, sort_interval=4)
+    o, om = run_oracle(phys, loads, steps)
+    assert int(om["collisions"][1]) > 3 * 4096  # several tiles of events a step
+    np.testing.assert_array_equal(gm["collisions"], om["collisions"])
+    np.testing.assert_array_equal(gm["live"], om["live"])
+    assert gm["next_id"] == 2 * phys.ncells * 100 + 2 * int(om["collisions"][1])
+    assert 2 * phys.ncells * 100 > 1 << 16  # three passes of the sort
+    for s, (ex, ev) in enumerate(particle_errors(phys, g, o)):
+        assert ex < 1e-12 and ev < 1e-12, (s, ex, ev)
+    assert_same_clocks(g, o)
+
+
 @pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
 def test_checkpoint_restart_is_bit_identical(precision):
     """particles (cell units + collision clocks) + step + next ids reloaded into a
