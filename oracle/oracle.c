@@ -937,6 +937,20 @@ static int one_step(orc_sim* s)
     return 0;
 }
 
+/* The field of the next step supplied by the caller (E on the N+1 nodes) in place of
+ * the one the field phase formed: the gather then uses A_s = c_s E as usual.  A run split
+ * into subdomains solves the field jointly and hands each part the result. */
+int orc_set_field(orc_sim* s, const double* E)
+{
+    if (!s || !E) return -1;
+    const int N = s->N, S = s->p.nspecies;
+    for (int j = 0; j <= N; ++j) s->E[j] = E[j];
+    for (int sp = 0; sp < S; ++sp)
+        for (int j = 0; j <= N; ++j) s->A[(size_t)sp * (N + 1) + j] = s->accel[sp] * s->E[j];
+    s->fields_ready = 1;
+    return 0;
+}
+
 int orc_step(orc_sim* s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return -1;

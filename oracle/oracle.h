@@ -97,6 +97,10 @@ int orc_load(orc_sim* s, int32_t sp, int64_t n, const int32_t* cell, const doubl
 /* Advance nsteps time steps.  Returns 0 or a negative error. */
 int orc_step(orc_sim* s, int64_t nsteps);
 
+/* Use E (N+1 node values) as the field of the next step instead of the one formed from
+ * this instance's own particles (a run split into subdomains solves it jointly). */
+int orc_set_field(orc_sim* s, const double* E);
+
 /* Continue a saved run: set the step counter (the next step is `step`, which keys its
  * draws and places it on the collision clock's grid) and raise the next id for created
  * particles to at least next_id.  Counters of walls and collisions are not touched. */

@@ -59,6 +59,7 @@ def lib():
         P = C.c_void_p
         L.orc_load.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P, P, P, P, P, P, P, P]
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
+        L.orc_set_field.argtypes = [C.c_void_p, P]
         L.orc_set_step.argtypes = [C.c_void_p, C.c_int64, C.c_uint32]
         L.orc_count.restype = C.c_int64
         L.orc_count.argtypes = [C.c_void_p, C.c_int32]
@@ -164,6 +165,16 @@ class Oracle:
         rc = lib().orc_step(self._h, n)
         if rc:
             raise RuntimeError("orc_step failed: %d" % rc)
+
+    def set_field(self, E) -> None:
+        """Use E (N+1 node values) as the next step's field instead of the one formed
+        from this instance's own particles."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        if E.shape != (self.phys.ncells + 1,):
+            raise ValueError("E must have ncells + 1 entries")
+        rc = lib().orc_set_field(self._h, _ptr(E))
+        if rc:
+            raise RuntimeError("orc_set_field failed: %d" % rc)
 
     def set_step(self, step: int, next_id: int = 0) -> None:
         """Continue a saved run at `step` with created ids from at least next_id."""

@@ -1,0 +1,232 @@
+"""Host side of one instance split over several ranks by cells: the one-dimensional
+domain decomposition of the paper's Section 2, as designed for one process per GPU.
+
+Rank r of R owns the cells [c_r, c_{r+1}) and the nodes [c_r, c_{r+1}]; node c_r is
+shared with rank r-1.  Per step the ranks exchange, with torch.distributed (NCCL
+between GPUs; gloo on CPU in the tests):
+
+1. the fixed-point deposit of each shared node (a particle adds S - Q to node j and Q to
+   node j+1, Q = rint(f S)), int64, point to point with the neighbour and added:
+   integer addition, so the split deposit equals the whole one bit for bit;
+2. the field.  The Dirichlet solution of -phi_{i-1} + 2 phi_i - phi_{i+1} =
+   dx^2 rho_i / eps0, phi_0 = phi_N = 0, is
+       phi_i = (dx^2 / eps0) [((N - i) / N) L_i + (i / N) R_i],
+       L_i = sum_{1 <= k <= i} k rho_k,   R_i = sum_{i < k <= N-1} (N - k) rho_k,
+   a two-level scan: every rank sums its own interior nodes, one all-gather of the R
+   pairs of totals gives each rank the sums before and after it, and the potentials
+   next to its edges come from the neighbours in a second exchange.  E = -dphi/dx
+   (centred inside, Gauss's law over the half cell at a wall) is the exact value
+   rounded once;
+3. the particles that crossed an edge (cell, offset, velocities, id, collision
+   clock), point to point to the neighbour.
+
+The sums are exact (integers and rationals), so the field and the particles do not
+depend on the number of ranks.  The particle step itself is the library's mover; the
+tests drive this protocol with a CPU stepper per rank.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+S48 = 1 << 48  # fixed-point unit of one particle's charge (the FP64 form's)
+
+
+def partition(cell_counts: Sequence[int], world: int) -> List[int]:
+    """Cuts 0 = c_0 < c_1 < ... < c_R = N of N cells into `world` contiguous ranges
+    with about equal particle counts (each range at least one cell)."""
+    counts = np.asarray(cell_counts, dtype=np.int64)
+    N = len(counts)
+    if world < 1 or world > N:
+        raise ValueError("need 1 <= world <= ncells")
+    cum = np.concatenate([[0], np.cumsum(counts)])
+    total = int(cum[-1])
+    cuts = [0]
+    for r in range(1, world):
+        target = total * r / world
+        c = int(np.searchsorted(cum, target, side="left"))
+        c = max(c, cuts[-1] + 1)          # at least one cell per range
+        c = min(c, N - (world - r))       # and room for the ranges after it
+        cuts.append(c)
+    cuts.append(N)
+    return cuts
+
+
+def fixed_deposit(cell: np.ndarray, off: np.ndarray, lo: int, hi: int,
+                  S: int = S48) -> np.ndarray:
+    """Fixed-point cloud-in-cell deposit of particles in cells [lo, hi) on the nodes
+    lo..hi (int64): S - Q on node j, Q = rint(f S) (ties to even) on node j+1."""
+    dep = np.zeros(hi - lo + 1, dtype=np.int64)
+    if len(cell) == 0:
+        return dep
+    j = np.asarray(cell, dtype=np.int64) - lo
+    if j.min() < 0 or j.max() >= hi - lo:
+        raise ValueError("particle outside the subdomain")
+    Q = np.rint(np.asarray(off, dtype=np.float64) * float(S)).astype(np.int64)
+    np.add.at(dep, j, S - Q)
+    np.add.at(dep, j + 1, Q)
+    return dep
+
+
+class Subdomain:
+    """Rank `rank`'s part of an N-cell instance cut at `cuts` (from partition), with
+    the exchanges of one step.  `world` 1 (no torch.distributed needed) is the whole
+    instance, solved by the same arithmetic."""
+
+    def __init__(self, N: int, cuts: Sequence[int], rank: int, dx: float, eps0: float = 1.0):
+        self.N = int(N)
+        self.cuts = [int(c) for c in cuts]
+        self.world = len(self.cuts) - 1
+        self.rank = int(rank)
+        self.lo, self.hi = self.cuts[rank], self.cuts[rank + 1]
+        self.dx = Fraction(dx)
+        self.eps0 = Fraction(eps0)
+        if not (0 <= rank < self.world) or self.cuts[0] != 0 or self.cuts[-1] != N:
+            raise ValueError("bad cuts or rank")
+
+    # -- 1. the shared nodes' deposit -----------------------------------------------
+    def exchange_shared(self, dep: np.ndarray) -> np.ndarray:
+        """dep: int64 [species, hi - lo + 1], this rank's deposit on its nodes.  Returns
+        it with each shared node holding the sum of both neighbours' deposits."""
+        dep = np.array(dep, dtype=np.int64, copy=True)
+        if self.world == 1:
+            return dep
+        import torch
+        import torch.distributed as dist
+        ops, inbox = [], {}
+        for nb, col in ((self.rank - 1, 0), (self.rank + 1, -1)):
+            if 0 <= nb < self.world:
+                send = torch.from_numpy(np.ascontiguousarray(dep[:, col]))
+                recv = torch.zeros_like(send)
+                ops.append(dist.isend(send, nb))
+                ops.append(dist.irecv(recv, nb))
+                inbox[col] = recv
+        for op in ops:
+            op.wait()
+        for col, recv in inbox.items():
+            dep[:, col] += recv.numpy()
+        return dep
+
+    # -- 2. the field ---------------------------------------------------------------
+    def rho(self, dep: np.ndarray, qw: Sequence[float], S: int = S48) -> List[Fraction]:
+        """Exact charge density on the rank's nodes from the (exchanged) deposit: the
+        node charge sum_s q_s w_s dep_s / S over the cell (half the cell at a wall)."""
+        out = []
+        for n, j in enumerate(range(self.lo, self.hi + 1)):
+            q = sum((Fraction(c) * int(dep[s, n]) for s, c in enumerate(qw)), Fraction(0)) / S
+            vol = self.dx / 2 if j in (0, self.N) else self.dx
+            out.append(q / vol)
+        return out
+
+    def _gather(self, obj):
+        if self.world == 1:
+            return [obj]
+        import torch.distributed as dist
+        out = [None] * self.world
+        dist.all_gather_object(out, obj)
+        return out
+
+    def field(self, rho: List[Fraction]) -> np.ndarray:
+        """E on the nodes lo..hi (Dirichlet walls), the exact solution rounded once."""
+        N, lo, hi = self.N, self.lo, self.hi
+        r_at = lambda k: rho[k - lo]  # noqa: E731
+        own_lo = lo + 1 if self.rank > 0 else 1   # interior nodes this rank sums
+        own_hi = min(hi, N - 1)
+        T = sum((k * r_at(k) for k in range(own_lo, own_hi + 1)), Fraction(0))
+        U = sum(((N - k) * r_at(k) for k in range(own_lo, own_hi + 1)), Fraction(0))
+        tot = self._gather((T, U))
+        L = sum((t for t, _ in tot[:self.rank]), Fraction(0))      # L_{own_lo - 1}
+        R_after = sum((u for _, u in tot[self.rank + 1:]), Fraction(0))  # R_{own_hi}
+        # L_i and R_i on the rank's nodes
+        Ls, Rs = {}, {}
+        acc = L
+        for i in range(lo, hi + 1):
+            if own_lo <= i <= own_hi:
+                acc += i * r_at(i)
+            Ls[i] = acc
+        acc = R_after
+        for i in range(hi, lo - 1, -1):
+            Rs[i] = acc
+            if own_lo <= i <= own_hi:
+                acc += (N - i) * r_at(i)
+        h2 = self.dx * self.dx / self.eps0
+        phi = {i: h2 * (Fraction(N - i, N) * Ls[i] + Fraction(i, N) * Rs[i])
+               for i in range(lo, hi + 1)}
+        # the potentials one node outside the edges, from the neighbours
+        edges = self._gather((phi.get(lo + 1), phi.get(hi - 1)))
+        if self.rank > 0:
+            phi[lo - 1] = edges[self.rank - 1][1]
+        if self.rank < self.world - 1:
+            phi[hi + 1] = edges[self.rank + 1][0]
+        E = np.zeros(hi - lo + 1)
+        half = self.dx / (2 * self.eps0)
+        for i in range(lo, hi + 1):
+            if i == 0:
+                e = -(phi[1] - phi[0]) / self.dx - r_at(0) * half
+            elif i == N:
+                e = -(phi[N] - phi[N - 1]) / self.dx + r_at(N) * half
+            else:
+                e = (phi[i - 1] - phi[i + 1]) / (2 * self.dx)
+            E[i - lo] = float(e)  # rounded once
+        return E
+
+    # -- 3. the particles that crossed an edge ---------------------------------------
+    _FLOATS = ("off", "vx", "vy", "vz")
+    _INTS = ("cell", "id", "state")
+
+    def migrate(self, parts: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:
+        """parts: one species' particles of this rank after the step (cell, off, vx,
+        vy, vz, id, state).  Those now outside [lo, hi) go to the neighbour (at most one
+        subdomain away); returns the kept ones followed by the ones received."""
+        cell = np.asarray(parts["cell"])
+        left, right = cell < self.lo, cell >= self.hi
+        if (self.rank == 0 and left.any()) or (self.rank == self.world - 1 and right.any()):
+            raise ValueError("particle outside the instance")
+        if left.any() and self.rank > 0 and cell[left].min() < self.cuts[self.rank - 1]:
+            raise ValueError("particle crossed more than one subdomain")
+        if right.any() and self.rank < self.world - 1 and cell[right].max() >= self.cuts[self.rank + 2]:
+            raise ValueError("particle crossed more than one subdomain")
+        keep = ~(left | right)
+        out = {k: np.asarray(parts[k])[keep] for k in self._FLOATS + self._INTS}
+        if self.world == 1:
+            return out
+        import torch
+        import torch.distributed as dist
+
+        def pack(mask):
+            f = np.stack([np.asarray(parts[k], dtype=np.float64)[mask] for k in self._FLOATS], 1)
+            i = np.stack([np.asarray(parts[k]).astype(np.int64)[mask] for k in self._INTS], 1)
+            return torch.from_numpy(np.ascontiguousarray(f.reshape(-1, 4))), \
+                torch.from_numpy(np.ascontiguousarray(i.reshape(-1, 3)))
+
+        nbs = [(nb, m) for nb, m in ((self.rank - 1, left), (self.rank + 1, right))
+               if 0 <= nb < self.world]
+        # counts first, then the particles
+        ops, counts = [], {}
+        for nb, m in nbs:
+            counts[nb] = torch.zeros(1, dtype=torch.int64)
+            ops.append(dist.isend(torch.tensor([int(m.sum())], dtype=torch.int64), nb))
+            ops.append(dist.irecv(counts[nb], nb))
+        for op in ops:
+            op.wait()
+        ops, got = [], []
+        for nb, m in nbs:  # (nothing is sent or received for an empty list)
+            if m.any():
+                f, i = pack(m)
+                ops += [dist.isend(f, nb), dist.isend(i, nb)]
+            n = int(counts[nb][0])
+            if n > 0:
+                rf = torch.zeros((n, 4), dtype=torch.float64)
+                ri = torch.zeros((n, 3), dtype=torch.int64)
+                ops += [dist.irecv(rf, nb), dist.irecv(ri, nb)]
+                got.append((rf, ri))
+        for op in ops:
+            op.wait()
+        for rf, ri in got:
+            for c, k in enumerate(self._FLOATS):
+                out[k] = np.concatenate([out[k], rf[:, c].numpy()])
+            for c, k in enumerate(self._INTS):
+                out[k] = np.concatenate([out[k], ri[:, c].numpy().astype(out[k].dtype)])
+        return out

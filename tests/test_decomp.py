@@ -1,0 +1,207 @@
+"""The domain decomposition of one instance by cells (the paper's Section 2), on CPU:
+its host logic alone, then two gloo ranks, each stepping half of an instance with the
+oracle's particle step, the field solved jointly, against the oracle's undivided run.
+
+Velocities cross the oracle's interface in physical units; with dt/dx a power of two
+(here 1/8) that conversion is exact, so a particle that changes rank keeps its state
+bit for bit."""
+import os
+import socket
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from oracle.oracle import Oracle, poisson as oracle_poisson
+from paper_2404_10270_gb300 import workloads as W
+from paper_2404_10270_gb300.decomp import Subdomain, fixed_deposit, partition
+from tests.gpu_common import by_id
+
+STEPS = 40
+
+
+def _physics():
+    return W.bounded_small(ncells=64, ppc=40, seed=21, nu=0.2, dt=0.0625)
+
+
+def test_partition_covers_the_cells_and_balances():
+    rng = np.random.default_rng(0)
+    counts = rng.integers(0, 100, 500)
+    for world in (1, 2, 3, 7):
+        cuts = partition(counts, world)
+        assert cuts[0] == 0 and cuts[-1] == 500 and len(cuts) == world + 1
+        assert all(b > a for a, b in zip(cuts, cuts[1:]))
+        loads = [counts[a:b].sum() for a, b in zip(cuts, cuts[1:])]
+        assert max(loads) - min(loads) <= 2 * counts.max()
+    assert partition([0, 0, 5, 0], 4) == [0, 1, 2, 3, 4]  # one cell each at least
+    with pytest.raises(ValueError):
+        partition([1, 1], 3)
+
+
+def test_split_deposit_adds_up_to_the_whole_one():
+    rng = np.random.default_rng(1)
+    N, n = 50, 4000
+    cell = rng.integers(0, N, n)
+    off = rng.random(n)
+    whole = fixed_deposit(cell, off, 0, N)
+    cuts = [0, 17, 31, N]
+    total = np.zeros(N + 1, np.int64)
+    for a, b in zip(cuts, cuts[1:]):
+        m = (cell >= a) & (cell < b)
+        total[a:b + 1] += fixed_deposit(cell[m], off[m], a, b)
+    np.testing.assert_array_equal(total, whole)
+    assert whole.sum() == n * (1 << 48)  # every particle adds one unit
+
+
+def test_whole_instance_field_is_the_dirichlet_solution():
+    # uniform charge: phi_i = (dx^2 rho / eps0) i (N - i) / 2, E linear, exactly
+    N, dx = 16, 0.5
+    sub = Subdomain(N, [0, N], 0, dx)
+    rho = [Fraction(3, 4)] * (N + 1)
+    E = sub.field(rho)
+    for i in range(1, N):
+        # E_i = (phi_{i-1} - phi_{i+1}) / (2 dx) = (dx rho / eps0) (i - N/2)
+        assert E[i] == float(Fraction(dx) * Fraction(3, 4) * (i - Fraction(N, 2)))
+    # a random charge against the oracle's binary128 Thomas solve (both round once)
+    rng = np.random.default_rng(2)
+    rho = rng.normal(0, 1, N + 1)
+    E = sub.field([Fraction(float(r)) for r in rho])
+    _, E_o = oracle_poisson(rho, dx)
+    np.testing.assert_array_equal(E, E_o)
+
+
+def test_oracle_follows_a_supplied_field():
+    # the oracle handed its own field every step takes the same steps bit for bit
+    phys = _physics()
+    loads = W.initial_load(phys, seed=21)
+    a, b = Oracle(phys), Oracle(phys)
+    a.load_all(loads)
+    b.load_all(loads)
+    for _ in range(10):
+        b.set_field(a.moments()["E"])
+        a.step(1)
+        b.step(1)
+    for s in range(2):
+        pa, pb = by_id(a.particles(s)), by_id(b.particles(s))
+        for k in pa:
+            np.testing.assert_array_equal(pa[k], pb[k])
+    # and a supplied zero field is no field
+    c = Oracle(phys)
+    c.load_all(loads)
+    c.set_field(np.zeros(phys.ncells + 1))
+    c.step(1)
+    assert not np.array_equal(by_id(c.particles(0))["vx"], by_id(a.particles(0))["vx"])
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _joint_field(sub, parts, qw):
+    """This rank's E on all N+1 nodes (its own nodes set, zero elsewhere)."""
+    dep = np.stack([fixed_deposit(p["cell"], p["off"], sub.lo, sub.hi) for p in parts])
+    dep = sub.exchange_shared(dep)
+    E = np.zeros(sub.N + 1)
+    E[sub.lo:sub.hi + 1] = sub.field(sub.rho(dep, qw))
+    return E, dep
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        phys = _physics()
+        N = phys.ncells
+        loads = W.initial_load(phys, seed=21)
+        cuts = partition(np.bincount(np.concatenate([ld.cell for ld in loads]), minlength=N),
+                         world)
+        sub = Subdomain(N, cuts, rank, phys.dx, phys.eps0)
+        qw = [s.charge * s.weight for s in phys.species]
+        orc = Oracle(phys)  # the whole grid; only this rank's particles in it
+        for s, ld in enumerate(loads):
+            m = (ld.cell >= sub.lo) & (ld.cell < sub.hi)
+            orc.load(s, ld.take(m))
+        first = None
+        for n in range(STEPS):
+            parts = [orc.particles(s) for s in range(len(loads))]
+            E, dep = _joint_field(sub, parts, qw)
+            if n == 0:
+                first = (E[sub.lo:sub.hi + 1].copy(), dep)
+            orc.set_field(E)
+            orc.step(1)
+            # the particles that crossed an edge change rank; the rest are loaded back
+            for s in range(len(loads)):
+                p = sub.migrate(orc.particles(s))
+                orc.load(s, W.Load(p["cell"], p["off"], p["vx"], p["vy"], p["vz"],
+                                   p["id"].astype(np.uint32), p["state"].astype(np.uint8)))
+        m = orc.moments()
+        q.put((rank, cuts, first, [orc.particles(s) for s in range(len(loads))],
+               m["wall_count"], m["collisions"], m["live"]))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reproduce_the_undivided_oracle_run():
+    phys = _physics()
+    loads = W.initial_load(phys, seed=21)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    cuts = out[0][1]
+    assert 0 < cuts[1] < phys.ncells
+
+    # the joint deposit and field of the first step equal the undivided ones bit for bit
+    whole = Subdomain(phys.ncells, [0, phys.ncells], 0, phys.dx, phys.eps0)
+    parts = [dict(cell=ld.cell, off=ld.off) for ld in loads]
+    E1, dep1 = _joint_field(whole, parts, [s.charge * s.weight for s in phys.species])
+    for rank, c, (E_r, dep_r), *_ in out:
+        lo, hi = c[rank], c[rank + 1]
+        np.testing.assert_array_equal(E_r, E1[lo:hi + 1])
+        np.testing.assert_array_equal(dep_r, dep1[:, lo:hi + 1])
+
+    # against the oracle's own undivided run (its field in binary128 from the exact
+    # weights, the joint one from the fixed-point deposit): counters bit for bit,
+    # particles within the FP64 form's tolerance
+    o = Oracle(phys)
+    o.load_all(loads)
+    o.step(STEPS)
+    om = o.moments()
+    np.testing.assert_array_equal(out[0][4] + out[1][4], om["wall_count"])
+    np.testing.assert_array_equal(out[0][5] + out[1][5], om["collisions"])
+    np.testing.assert_array_equal(out[0][6] + out[1][6], om["live"])
+    assert om["collisions"].sum() > 0 and om["wall_count"].sum() > 0
+    L = phys.ncells
+    moved = 0
+    for s in range(len(phys.species)):
+        want = by_id(o.particles(s))
+        got = {k: np.concatenate([out[0][3][s][k], out[1][3][s][k]]) for k in want}
+        got = by_id(got)
+        np.testing.assert_array_equal(got["id"], want["id"])
+        np.testing.assert_array_equal(got["state"], want["state"])
+        x_got = got["cell"] + got["off"]
+        x_want = want["cell"] + want["off"]
+        assert np.abs(x_got - x_want).max() / L < 1e-12
+        vscale = max(np.abs(want["vx"]).max(), 1.0)
+        for k in ("vx", "vy", "vz"):
+            assert np.abs(got[k] - want[k]).max() / vscale < 1e-12
+        # some particles did change rank
+        ld = loads[s]
+        start = dict(zip(ld.id.tolist(), ld.cell.tolist()))
+        moved += sum((start[i] < cuts[1]) != (c < cuts[1])
+                     for i, c in zip(want["id"].tolist(), want["cell"].tolist()) if i in start)
+    assert moved > 0
