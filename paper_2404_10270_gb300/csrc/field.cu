@@ -325,10 +325,11 @@ __global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned l
 // far: electron 2r, ion 2r+1, r = rank of the parent id among this step's events (with
 // a neutral particle target only the electron is new: id r).  One block per instance
 // sorts the parent ids (a stable least-significant-digit radix sort, 8 bits a pass,
-// as many passes as the largest id so far needs; the ids of one step are distinct)
-// and ranks every event by a binary search in the sorted ids, then advances the
-// instance's next id: O(n) work per pass for n events.
+// as many passes as the largest id so far needs; the ids of one step are distinct;
+// in shared memory when they fit) and ranks every event by a binary search in the
+// sorted ids, then advances the instance's next id: O(n) work per pass for n events.
 constexpr int kBirthThreads = 1024;
+constexpr int kBirthSmemKeys = 3072;
 
 __global__ void __launch_bounds__(kBirthThreads) k_births(const InstParams* inst, Event* events,
                                                           unsigned long long* ev_count,
@@ -341,6 +342,7 @@ __global__ void __launch_bounds__(kBirthThreads) k_births(const InstParams* inst
     __shared__ unsigned run[256];      // next slot of each digit in the pass's output
     __shared__ unsigned tot[256];      // digit counts of the tile
     __shared__ unsigned short wcnt[NW][256];  // digit counts of each warp in the tile
+    __shared__ uint32_t skeys[2][kBirthSmemKeys];   // the keys of a small step
     const int b = blockIdx.x;
     const InstParams& I = inst[b];
     const unsigned long long cnt = ev_count[b];
@@ -355,15 +357,18 @@ __global__ void __launch_bounds__(kBirthThreads) k_births(const InstParams* inst
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
-    uint32_t* buf[2] = {keys_a + I.ev_base, keys_b + I.ev_base};
+    // a step with few events sorts in shared memory, a larger one in its buffers
+    const bool small = n <= kBirthSmemKeys;
+    uint32_t* const buf0 = small ? skeys[0] : keys_a + I.ev_base;
+    uint32_t* const buf1 = small ? skeys[1] : keys_b + I.ev_base;
     // every parent id is below the next id: passes for its significant bytes
     int passes = 0;
     for (unsigned long long m = base > 0 ? base - 1 : 0; m != 0; m >>= 8) ++passes;
     if (passes == 0) passes = 1;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        const uint32_t* src = buf[(pass + 1) & 1];
-        uint32_t* dst = buf[pass & 1];
+        const uint32_t* src = (pass & 1) ? buf0 : buf1;
+        uint32_t* dst = (pass & 1) ? buf1 : buf0;
         auto key = [&](int64_t i) -> uint32_t { return pass == 0 ? ev[i].parent : src[i]; };
         for (int d = threadIdx.x; d < 256; d += kBirthThreads) hist[d] = 0u;
         __syncthreads();
@@ -423,7 +428,7 @@ __global__ void __launch_bounds__(kBirthThreads) k_births(const InstParams* inst
         __syncthreads();
     }
     // rank of every event: its parent's place among the sorted ids
-    const uint32_t* sorted = buf[(passes - 1) & 1];
+    const uint32_t* sorted = ((passes - 1) & 1) ? buf1 : buf0;
     for (int64_t i = threadIdx.x; i < n; i += kBirthThreads) {
         const uint32_t p = ev[i].parent;
         int64_t lo = 0, hi = n;
