@@ -27,14 +27,30 @@ constexpr int kMaxProc = PIC_MAX_PROC;
 constexpr int kSegAlign = 64;  // slots
 
 // The cell word of a particle: bits 0-22 the cell index j, bits 23-29 the collision
-// clock count (steps to skip before the next collision event step), bit 30 "the next
-// event step is a collision candidate", bit 31 set = empty slot (the word is -1).
+// clock: the species' own step (the index of its moving steps, modulo 128) of its next
+// collision event step, bit 30 "that event step is a collision candidate", bit 31 set =
+// empty slot (the word is -1).  The event is at most kGapMax own steps ahead, so seven
+// bits name it; a step without an event or a cell change leaves the word as it is,
+// and the mover does not write it back.  Outside the library (loads, reads, the
+// oracle) the clock is the count of own steps to skip before that event step.
 constexpr uint32_t kCellMask = (1u << 23) - 1u;
 constexpr int kClockShift = 23;
-constexpr uint32_t kClockCount = 0x7Fu;
+constexpr uint32_t kClockDue = 0x7Fu;
 constexpr uint32_t kClockPending = 0x80u;
 constexpr int kGapMax = 127;
 constexpr int kMaxCells = (1 << 23) - 1;
+
+// The own-step index of the first step >= n on which a species with subcycling factor
+// K moves (it moves on the steps n' with (n'+1) mod K = 0, own index (n'+1)/K - 1).
+__host__ __device__ __forceinline__ int64_t own_step_from(int64_t n, int K)
+{
+    return (n + K) / K - 1;
+}
+// The clock bits of an event at own step `own` (pending: a candidate).
+__host__ __device__ __forceinline__ uint32_t clock_bits(int64_t own, bool pending)
+{
+    return ((uint32_t)(own & (int64_t)kClockDue) | (pending ? kClockPending : 0u)) << kClockShift;
+}
 
 // Device status word bits (latched, reported by synchronising calls).
 enum : unsigned {
@@ -94,6 +110,20 @@ struct SegParams {
 __host__ __device__ __forceinline__ bool deposit_kept(const SegParams& P)
 {
     return P.is_target != 0 && P.nstep > 1;
+}
+
+// The origin of a segment's clocks at step n (loads and reads count from it): its own
+// index of the next moving step.  A species without collisions never looks at its clock
+// and keeps the one it was loaded with, unchanged (origin 0).
+__host__ __device__ __forceinline__ int64_t clock_origin(const SegParams& P, int64_t n)
+{
+    return P.collide ? own_step_from(n, P.nstep) : 0;
+}
+// The cell word of a particle placed in cell j after the mover of step n (created,
+// re-injected, converted): its clock tests on the species' next moving step.
+__host__ __device__ __forceinline__ int fresh_word(const SegParams& P, int j, int64_t n)
+{
+    return (int)((uint32_t)j | clock_bits(clock_origin(P, n + 1), false));
 }
 
 constexpr int kChunk = 256;  // nodes per block of the field solve

@@ -1246,6 +1246,7 @@ int load_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
     l.host_f32 = host_f32 ? 1 : 0;
     l.id = did;
     l.state = dstate;
+    l.own0 = clock_origin(P, h->step_h);
     l.n = n;
     l.id0 = (uint32_t)id0;
     l.vscale = (flags & PIC_CELL_UNITS)
@@ -1608,6 +1609,7 @@ int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity
     g.s_yp = S.yp;
     g.base = P.base;
     g.nslots = (int64_t)nslots;
+    g.own0 = clock_origin(P, h->step_h);
     g.vscale_inv = (flags & PIC_CELL_UNITS)
                        ? 1.0
                        : h->inst[inst].dx / ((double)species_nstep(h->inst[inst], species) * h->inst[inst].dt);
@@ -1708,6 +1710,10 @@ int pic_restore_counters(pic_handle* h, int64_t step, const uint64_t* next_id)
     if (step < 0) return fail(h, PIC_EINVAL, "pic_restore_counters: step < 0");
     if ((rc = sync_check(h))) return rc;
     CUDA_TRY(h, cudaMemcpy(h->step_d, &step, 8, cudaMemcpyHostToDevice));
+    if (step != h->step_h) {
+        CUDA_TRY(h, launch_rebase_clocks(h->segd, h->nseg, h->st[h->cur].cell, h->step_h, step, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    }
     if (next_id) {
         for (int i = 0; i < h->ninst; ++i)
             if (next_id[i] > 0xFFFFFFFFull) return fail(h, PIC_EINVAL, "pic_restore_counters: next_id >= 2^32");

@@ -135,7 +135,9 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
             T* vx = static_cast<T*>(a.ux);
             T* vy = static_cast<T*>(a.uy);
             T* vz = static_cast<T*>(a.uz);
-            a.cell[ge] = j; off[ge] = f;
+            // fresh clocks: a test on the species' next moving step
+            a.cell[ge] = fresh_word(P, j, step);
+            off[ge] = f;
             vx[ge] = us * n2[0]; vy[ge] = us * n2[1]; vz[ge] = us * n2[2];
             a.id[ge] = 0xFFFFFFFFu;
             // the products start at the parent's y coordinate (2-D species)
@@ -168,7 +170,8 @@ __device__ __forceinline__ int collide(const MoveArgs& a, const SegParams& P, in
                 box_muller<T>(ri.z, ri.w, &z2, &z3);
                 const T vn = (T)Pi.vneutral;  // the ion's velocity in its own species' units
                 const int64_t gi = Pi.base + (int64_t)ki;
-                a.cell[gi] = j; off[gi] = f;
+                a.cell[gi] = fresh_word(Pi, j, step);
+                off[gi] = f;
                 vx[gi] = z0 * vn; vy[gi] = z1 * vn; vz[gi] = z2 * vn;
                 a.id[gi] = 0xFFFFFFFFu;
                 if (ypp) ypp[gi] = Pi.sn2d ? yparent : T(0);
@@ -281,10 +284,11 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                     const int dgrid = kGapMax - (int)((q - 1) % kGapMax);
                     const int g = min(gap_steps(P.gap, P.glog, wd.x), dgrid);
                     now = g == 0;
-                    const uint32_t clk = g == 0 ? 0u
-                                         : g < dgrid ? ((uint32_t)(g - 1) | kClockPending)
-                                                     : (uint32_t)(dgrid - 1);
-                    a.cell[slot] = (int)((uint32_t)j | (clk << kClockShift));
+                    // the next event: a test next step after a candidate now, else the
+                    // candidate g steps on, or the test at the grid step
+                    const int64_t mown = q - 1;
+                    a.cell[slot] = (int)((uint32_t)j | clock_bits(g == 0 ? mown + 1 : mown + g,
+                                                                  g > 0 && g < dgrid));
                 }
                 if (now) {
                     f = offp[slot];
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                     // re-injected: back in the store with a fresh clock (and y coordinate),
                     // deposited here
                     if (a.yp) static_cast<T*>(a.yp)[slot] = T(0);
-                    a.cell[slot] = j;
+                    a.cell[slot] = fresh_word(P, j, step);
                     offp[slot] = f;
                     uxp[slot] = vx;
                     uyp[slot] = vy;
@@ -347,6 +351,7 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
     T* const uyp = static_cast<T*>(a.uy);
     T* const uzp = static_cast<T*>(a.uz);
     const int lane = threadIdx.x & 31;
+    const int64_t step = *a.step;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nv = (int64_t)min(a.rare_count[1], (unsigned long long)a.vcap);
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nv; w += nw) {
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
                         const int jv = (int)((uint32_t)a.cell[v] & kCellMask);
                         const T fv = offp[v];
                         const T ratio = (T)I.tratio;
-                        a.cell[gi] = jv;
+                        a.cell[gi] = fresh_word(Pi, jv, step);
                         offp[gi] = fv;
                         uxp[gi] = uxp[v] * ratio;
                         uyp[gi] = uyp[v] * ratio;

@@ -43,9 +43,11 @@ __global__ void k_load(const LoadArgs l)
                     ft = (T)0.99999994f;
                 }
             }
-            // cell word: index | collision clock (bits 0-6 count, bit 7 pending)
+            // cell word: index | collision clock; the caller's clock counts the own
+            // steps to skip (bits 0-6) before the event step, the word names that step
             const uint32_t clk = l.state ? (uint32_t)l.state[k] : 0u;
-            l.s_cell[g] = ok ? (int)((uint32_t)cc | (clk << kClockShift)) : -1;
+            const uint32_t cb = clock_bits(l.own0 + (int64_t)(clk & kClockDue), (clk & kClockPending) != 0u);
+            l.s_cell[g] = ok ? (int)((uint32_t)cc | cb) : -1;
             off[g] = ft;
             const double vx = (double)in_vx[k], vy = (double)in_vy[k], vz = (double)in_vz[k];
             ux[g] = l.vscale == 1.0 ? (T)vx : (T)(vx * l.vscale);
@@ -66,6 +68,25 @@ __global__ void k_load(const LoadArgs l)
         const unsigned m = __reduce_max_sync(0xffffffffu, idmax);
         if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0)
             atomicMax(l.next_id, (unsigned long long)m + 1ull);
+    }
+}
+
+// The step counter moves from `from` to `to` (a restored run): every clock keeps its
+// distance from the species' next moving step, so its due step moves with it.
+__global__ void k_rebase_clocks(const SegParams* seg, int nseg, int32_t* cell, int64_t from,
+                                int64_t to)
+{
+    for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const SegParams& P = seg[s];
+        const uint32_t delta = (uint32_t)(clock_origin(P, to) - clock_origin(P, from)) & kClockDue;
+        if (delta == 0u) continue;
+        for (int64_t k = threadIdx.x; k < P.cap; k += blockDim.x) {
+            const int w = cell[P.base + k];
+            if (w < 0) continue;
+            const uint32_t u = (uint32_t)w;
+            const uint32_t due = ((u >> kClockShift) + delta) & kClockDue;
+            cell[P.base + k] = (int)((u & ~(kClockDue << kClockShift)) | (due << kClockShift));
+        }
     }
 }
 
@@ -146,7 +167,11 @@ __global__ void k_get_write(const GetArgs g)
     const int64_t s = g.base + k;
     const uint32_t word = (uint32_t)g.s_cell[s];
     if (g.cell) g.cell[o] = (int)(word & kCellMask);
-    if (g.state) g.state[o] = (uint8_t)(word >> kClockShift);
+    if (g.state) {  // the event step's distance from the next own step (mod 128)
+        const uint32_t clk = word >> kClockShift;
+        const uint32_t skip = (uint32_t)((int64_t)(clk & kClockDue) - g.own0) & kClockDue;
+        g.state[o] = (uint8_t)(skip | (clk & kClockPending));
+    }
     // in double, then rounded once to the caller's type
     if (g.off) {
         H fo = (H)(double)static_cast<const T*>(g.s_off)[s];
@@ -221,6 +246,13 @@ int grid_for(int64_t n, int nt, int cap = 152 * 32)
 }
 
 }  // namespace
+
+cudaError_t launch_rebase_clocks(const SegParams* seg, int nseg, int32_t* cell, int64_t from,
+                                 int64_t to, cudaStream_t st)
+{
+    k_rebase_clocks<<<nseg < 1024 ? nseg : 1024, 256, 0, st>>>(seg, nseg, cell, from, to);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_load(const LoadArgs& l, cudaStream_t st)
 {

@@ -125,7 +125,8 @@ struct LoadArgs {
     const void* vz;
     int host_f32;
     const uint32_t* id;     // NULL: id0 + k
-    const uint8_t* state;   // collision clocks, NULL: 0
+    const uint8_t* state;   // collision clocks (own steps to skip, bit 7 pending), NULL: 0
+    int64_t own0;           // the species' own index of its next moving step (clock origin)
     int64_t n;
     uint32_t id0;
     double vscale;          // dt/dx
@@ -143,6 +144,10 @@ struct LoadArgs {
     unsigned long long* next_id;  // instance's next automatic id: raised to max(id) + 1
 };
 cudaError_t launch_load(const LoadArgs& l, cudaStream_t st);
+// clocks kept at their distance from each species' next moving step when the step
+// counter is set from `from` to `to`
+cudaError_t launch_rebase_clocks(const SegParams* seg, int nseg, int32_t* cell, int64_t from,
+                                 int64_t to, cudaStream_t st);
 
 struct GetArgs {
     const int32_t* s_cell;
@@ -162,7 +167,8 @@ struct GetArgs {
     void* vz;
     int host_f32;
     uint32_t* id;
-    uint8_t* state;
+    uint8_t* state;         // collision clocks out, as own steps to skip (bit 7 pending)
+    int64_t own0;           // the species' own index of its next moving step (clock origin)
     double* yp;             // y coordinates out (double), or null
     unsigned long long* block_count;  // scratch, ceil(nslots/1024)+1 entries
     int64_t capacity;                 // entries of the output arrays

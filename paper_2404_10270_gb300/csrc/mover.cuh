@@ -475,14 +475,16 @@ __device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4
 // a tile): gather, push, move, walls, collision clock.  c, f, u* hold the quad's
 // state on entry and its new state on exit (cell word -1: left through a wall).  The
 // masks get one bit per quad position: collision candidate (cand), absorbed at the
-// low or high wall (wlo, whi), clock test left to the event kernel (tst).  The id
-// of a test draw comes from idq (SORT: already loaded) or from the store at `slot`.
+// low or high wall (wlo, whi), clock test left to the event kernel (tst), cell word
+// changed (chg).  mown is the species' own index of this step (its clock's time),
+// dgrid the own steps to its next multiple of kGapMax.  The id of a test draw comes
+// from idq (SORT: already loaded) or from the store at `slot`.
 template <typename T, bool MAG, bool SORT, bool TEST>
 __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams& P, bool smag,
-                                             int64_t step, int dgrid, int64_t slot,
+                                             int64_t step, int64_t mown, int dgrid, int64_t slot,
                                              const uint32_t idq[4], int c[4], T f[4], T ux[4],
                                              T uy[4], T uz[4], unsigned& cand, unsigned& wlo,
-                                             unsigned& whi, unsigned& tst)
+                                             unsigned& whi, unsigned& tst, unsigned& chg)
 {
     using T2 = typename Prec<T>::T2;
     const T2* const accp = static_cast<const T2*>(a.accel);
@@ -494,10 +496,12 @@ __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams&
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (c[k] < 0) continue;
+        const int cw = c[k];
         int j = (int)((uint32_t)c[k] & kCellMask);
         uint32_t clk = (uint32_t)c[k] >> kClockShift;
         if (!in_range(a.err, j, 0, N)) {  // (bounds-checked build only)
             c[k] = -1;
+            chg |= 1u << k;
             continue;
         }
         // 1. gather (Listing 7) from the node pair (A_j, A_{j+1} - A_j)
@@ -537,44 +541,40 @@ __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams&
             } else {
                 if (j < 0) wlo |= 1u << k; else whi |= 1u << k;
                 c[k] = -1;
+                chg |= 1u << k;
                 continue;
             }
         }
         // 5. null collision.  The candidate steps of a particle form a
-        // Bernoulli(P) sequence; its clock counts the steps to skip before the
-        // next event step.  At an event step without a pending candidate (a
-        // test), Philox word 0 gives the candidate-free run g from this step,
-        // cut at the next multiple of 127 (D steps away): g = 0 candidate now,
-        // g < D a candidate g steps later, g = D none before then.  The cut puts
-        // the tests of all particles on the same steps, so a warp runs them
-        // together.  Candidates go to the event kernel.
-        if (collides) {
-            if (clk & kClockCount) {
-                clk -= 1u;
-            } else if (clk & kClockPending) {
+        // Bernoulli(P) sequence; its clock names the own step of its next event
+        // step.  At an event step without a pending candidate (a test), Philox word
+        // 0 gives the candidate-free run g from this step, cut at the next multiple
+        // of 127 (D steps away): g = 0 candidate now, g < D a candidate g steps
+        // later, g = D none before then.  The cut puts the tests of all particles on
+        // the same steps, so a warp runs them together.  Candidates go to the event
+        // kernel.  Between events the clock, and so the word, does not change.
+        if (collides && (clk & kClockDue) == (uint32_t)(mown & (int64_t)kClockDue)) {
+            if (clk & kClockPending) {
                 cand |= 1u << k;
-                clk = 0u;
+                clk = (uint32_t)((mown + 1) & (int64_t)kClockDue);  // a test next step
             } else if (!TEST) {
                 // a test off the common test steps (the clock of a particle that
                 // was a candidate in the last step, or was re-injected or created
                 // by ionization then): the event kernel draws it, with this
-                // step's counter
+                // step's counter, and sets the clock
                 tst |= 1u << k;
             } else {
                 // a test step: the id is read only here
                 const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
                 const uint4 w = draw(idk, step, kRngCollide, key0, key1);
                 const int g = min(gap_steps(P.gap, P.glog, w.x), dgrid);
-                if (g == 0) {
-                    cand |= 1u << k;
-                    clk = 0u;
-                } else {
-                    clk = g < dgrid ? ((uint32_t)(g - 1) | kClockPending)
-                                    : (uint32_t)(dgrid - 1);
-                }
+                if (g == 0) cand |= 1u << k;
+                const int64_t due = g == 0 ? mown + 1 : mown + g;
+                clk = (uint32_t)(due & (int64_t)kClockDue) | (g > 0 && g < dgrid ? kClockPending : 0u);
             }
         }
         c[k] = (int)((uint32_t)j | (clk << kClockShift));
+        if (c[k] != cw) chg |= 1u << k;
     }
 }
 
@@ -649,6 +649,7 @@ k_move(const __grid_constant__ MoveArgs a)
     bool smag = MAG;                   // the segment's instance is magnetized
     // steps (of the segment's species) to the next multiple of kGapMax
     int dgrid = kGapMax - (int)(step % kGapMax);
+    int64_t mown = step;  // the segment's own index of this step (its clock's time)
     for (int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); tile < total;
          tile += wstride) {
         if (tile >= s_end) {
@@ -667,6 +668,7 @@ k_move(const __grid_constant__ MoveArgs a)
                 const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
                 moves = ks == 1 || q * ks == step + 1;
                 dgrid = kGapMax - (int)((q - 1) % kGapMax);
+                mown = q - 1;
                 // a neutral particle target keeps its deposit from step to step (the
                 // field phase does not clear it; conversions into ions take their share
                 // away): between its moves nothing of it changes, so the warp goes on
@@ -712,11 +714,16 @@ k_move(const __grid_constant__ MoveArgs a)
             warp_deposit<Q, true>(jd, qr, Prec<T>::S, a.dep + node0, nullptr, dwin);
         }
         if (MOVE && (!SUB || moves)) {
-            unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
-            quad_physics<T, MAG, false, TEST>(a, P, smag, step, dgrid, slot, idq, c, f, ux, uy,
-                                              uz, cand, wlo, whi, tst);
+            unsigned cand = 0, wlo = 0, whi = 0, tst = 0, chg = 0;
+            quad_physics<T, MAG, false, TEST>(a, P, smag, step, mown, dgrid, slot, idq, c, f, ux,
+                                              uy, uz, cand, wlo, whi, tst, chg);
+            // the cell words go back only where one of them changed (a cell crossing, a
+            // wall, a collision event: a few per cent of the particles a step), decided
+            // per 32-byte sector (two lanes) so that memory sees whole sectors
+            const bool wcell = (chg | __shfl_xor_sync(0xffffffffu, chg, 1)) != 0u;
             if (act) {
-                __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
+                if (wcell)
+                    __stcs(reinterpret_cast<int4*>(a.cell + slot), make_int4(c[0], c[1], c[2], c[3]));
                 st4(offp + slot, f);
                 st4(uxp + slot, ux);
                 if (MAG && smag) {
@@ -809,6 +816,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
     int64_t s_begin = 0, s_end = -1;
     bool moves = true, smag = MAG;
     int dgrid = kGapMax - (int)(step % kGapMax);
+    int64_t mown = step;  // the segment's own index of this step (its clock's time)
     // every warp of the block walks the same chunks, so the barriers below match
     int parity = 0;
     for (int64_t chunk = blockIdx.x; chunk * NW < total; chunk += gridDim.x, parity ^= 1) {
@@ -827,6 +835,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                 const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;
                 moves = ks == 1 || q * ks == step + 1;
                 dgrid = kGapMax - (int)((q - 1) % kGapMax);
+                mown = q - 1;
             }
         }
         const SegParams& P = a.seg[s];
@@ -890,7 +899,7 @@ k_move_sort(const __grid_constant__ MoveArgs a)
             bmax = __reduce_max_sync(FULL, mx);
         }
         const bool staged = one && bseg >= 0 && bmax - bmin < kSortSpan;
-        unsigned cand = 0, wlo = 0, whi = 0, tst = 0;
+        unsigned cand = 0, wlo = 0, whi = 0, tst = 0, chg = 0;  // (the sort writes every word)
         int64_t to[4] = {-1, -1, -1, -1};
         if (staged) {
             const SegParams& B = a.seg[bseg];
@@ -936,8 +945,8 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                 }
             }
             if (!SUB || moves)
-                quad_physics<T, MAG, true, true>(a, P, smag, step, dgrid, slot, idq, c, f, ux,
-                                                 uy, uz, cand, wlo, whi, tst);
+                quad_physics<T, MAG, true, true>(a, P, smag, step, mown, dgrid, slot, idq, c, f,
+                                                 ux, uy, uz, cand, wlo, whi, tst, chg);
             if (threadIdx.x < kSortSpan) gb[threadIdx.x] = gres;
             __syncthreads();
             // stage every particle at its place in the chunk's cell order
@@ -995,8 +1004,8 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                     rbase[k] = atomicAdd(a.cursor + P.node + kk, (unsigned)__popc(grp[k]));
             }
             if (!SUB || moves)
-                quad_physics<T, MAG, true, true>(a, P, smag, step, dgrid, slot, idq, c, f, ux,
-                                                 uy, uz, cand, wlo, whi, tst);
+                quad_physics<T, MAG, true, true>(a, P, smag, step, mown, dgrid, slot, idq, c, f,
+                                                 ux, uy, uz, cand, wlo, whi, tst, chg);
             sort_destinations(a, P, grp, rbase, had, to);
             sort_write<T>(a, to, c, f, ux, uy, uz, idq);
             if (YP) {  // the y coordinates go along
