@@ -140,7 +140,7 @@ struct pic_handle {
     bool tune_block = false, tune_sort = false;
     int tune_phase = 0;        // 0 idle/done, 1 block sizes, 2 sort intervals
     int tune_idx = 0;          // candidate being measured
-    double tune_best = 1e300;  // best cost per step so far (ms)
+    double tune_best = 1e300;  // best cost per particle-step so far (ms)
     int tune_best_val = 0;
     std::string tune_key;
     char gpu_name[256] = {0};
@@ -721,6 +721,19 @@ void drop_graphs(pic_handle* h)
 }
 
 // ---- autotuner ----------------------------------------------------------------------
+// Live particles of the whole handle (synchronises the stream).
+int live_total(pic_handle* h, double* out)
+{
+    std::vector<unsigned long long> live((size_t)h->nseg);
+    CUDA_TRY(h, cudaMemcpyAsync(live.data(), h->seg_live, 8 * (size_t)h->nseg, cudaMemcpyDeviceToHost,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    double t = 0.0;
+    for (unsigned long long v : live) t += (double)v;
+    *out = t;
+    return PIC_OK;
+}
+
 // The time step's results do not depend on the mover block size or on the sort interval
 // (deposits are integer, random draws are keyed by particle id, the sort only permutes),
 // so the tuner measures candidates on the first steps of the real run: one sort cycle
@@ -1400,6 +1413,10 @@ int pic_step(pic_handle* h, int64_t nsteps)
         const int64_t K = h->sort_interval;
         // autotuning: time one whole sort cycle per candidate on the real run
         if (h->tune_phase && K > 0 && h->step_h % K == 0 && nsteps - n >= K) {
+            // the cost per particle-step: sources and ionization change the particle
+            // count from one candidate's cycle to the next
+            double live0 = 0.0, live1 = 0.0;
+            if ((rc = live_total(h, &live0))) return rc;
             cudaEvent_t ea = take_event(h), eb = take_event(h);
             CUDA_TRY(h, cudaEventRecord(ea, h->stream));
             for (int64_t k = 0; k < K; ++k)
@@ -1411,7 +1428,8 @@ int pic_step(pic_handle* h, int64_t nsteps)
             h->event_pool.push_back(ea);
             h->event_pool.push_back(eb);
             n += K;
-            const double per = ms / (double)K;
+            if ((rc = live_total(h, &live1))) return rc;
+            const double per = ms / ((double)K * std::max(0.5 * (live0 + live1), 1.0));
             if (h->tune_phase == 1) {
                 if (per < h->tune_best) { h->tune_best = per; h->tune_best_val = h->nt; }
                 if (++h->tune_idx < 3) {
