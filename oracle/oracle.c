@@ -538,6 +538,31 @@ static int gap_steps(const orc_sim* s, int sp, uint32_t w)
 static int candidate(orc_sim* s, int sp, orc_store* a, int64_t k, uint32_t wsel,
                      uint32_t wdens);
 
+/* The clock of a particle whose next event step is a test on its own step m1 (after a
+ * candidate, a re-injection or a conversion into an ion): that test taken now, from
+ * the draw of its own step, since its outcome depends on the id and the step alone —
+ * the count from m1 to the event it schedules (a candidate g steps on, g < D, or the
+ * test at the next multiple of 127, g = D), exactly as the test on m1 would set it,
+ * one step earlier.  A species without collisions keeps clock 0. */
+static uint8_t clock_after(orc_sim* s, int sp, uint32_t id, int64_t m1)
+{
+    if (!s->collides[sp]) return 0;
+    const int64_t n1 = (m1 + 1) * s->nstep[sp] - 1;  /* the global step of own step m1 */
+    uint32_t w[4];
+    draw(s, id, n1, ORC_RNG_COLLIDE, w);
+    const int D = ORC_GAP_MAX - (int)(m1 % ORC_GAP_MAX);
+    int g = gap_steps(s, sp, w[0]);
+    if (g > D) g = D;
+    return (uint8_t)(g | (g < D ? 0x80 : 0));
+}
+
+/* own index of the first step >= n on which species sp moves */
+static int64_t own_from(const orc_sim* s, int sp, int64_t n)
+{
+    const int64_t K = s->nstep[sp];
+    return (n + K) / K - 1;
+}
+
 /* Collision phase for one particle (null-collision MCC).  Whether a step holds a
  * collision candidate is a Bernoulli(P) sequence per particle; instead of one draw per
  * step the particle carries its clock: C steps to skip, and whether the next event
@@ -575,7 +600,8 @@ static int collide(orc_sim* s, int sp, orc_store* a, int64_t k)
             return 0;
         }
     }
-    a->mcc[k] = 0;
+    /* the step after a candidate is a test */
+    a->mcc[k] = clock_after(s, sp, a->id[k], own_from(s, sp, s->step + 1));
     return candidate(s, sp, a, k, w[1], w[2]);
 }
 
@@ -695,7 +721,7 @@ static void reinject(orc_sim* s, int sp, orc_store* a, int64_t k)
     box_muller(q[0], q[1], &z2, &z3);
     a->cell[k] = j;
     a->off[k] = f;
-    a->mcc[k] = 0;
+    a->mcc[k] = clock_after(s, sp, a->id[k], own_from(s, sp, s->step + 1));
     a->yp[k] = 0.0; /* a re-injected particle starts its y coordinate anew */
     a->ux[k] = z0 * s->vinj[sp];
     a->uy[k] = z1 * s->vinj[sp];
@@ -791,7 +817,7 @@ static int convert_targets(orc_sim* s)
         ion->uz[m] = a->uz[v] * ratio;
         ion->id[m] = a->id[v];
         ion->alive[m] = 1;
-        ion->mcc[m] = 0;
+        ion->mcc[m] = clock_after(s, b->psp, a->id[v], own_from(s, b->psp, s->step + 1));
         ion->yp[m] = s->p.sp[b->psp].sn2d ? a->yp[v] : 0.0;
         a->alive[v] = 0;
         touched[b->psp] = 1;

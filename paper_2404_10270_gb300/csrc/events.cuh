@@ -16,6 +16,22 @@
 
 namespace bitpic {
 
+// The cell word of a particle in cell j whose next collision event is a clock test on
+// its species' own step m1: the test is drawn here already (word 0 of its counter, the
+// global step of own step m1), so the mover finds the outcome in the clock instead of
+// queueing the test: a candidate g own steps on (g < D), or the next test at the
+// species' next multiple of kGapMax (g = D).  Exactly what the test at m1 would set; a
+// species without collisions keeps clock 0.
+__device__ __forceinline__ int test_word(const SegParams& P, uint32_t id, int j, int64_t m1)
+{
+    if (!P.collide) return j;
+    const int64_t n1 = (m1 + 1) * (int64_t)P.nstep - 1;
+    const int dg = kGapMax - (int)(m1 % kGapMax);
+    const uint4 w = draw(id, n1, kRngCollide, P.key0, P.key1);
+    const int g = min(gap_steps(P.gap, P.glog, w.x), dg);
+    return (int)((uint32_t)j | clock_bits(m1 + g, g < dg));
+}
+
 // Unit vector uniform on the sphere, polar axis x (the wall normal).
 template <typename T>
 __device__ __forceinline__ void iso_dir(uint32_t w0, uint32_t w1, T n[3])
@@ -303,6 +319,10 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                         uzp[slot] = vz;
                         ckey = P.inst * kMaxProc + p;
                     }
+                    // a candidate is followed by a test on the next own step: drawn now
+                    const int ks = P.nstep;
+                    const int64_t q = ks == 1 ? step + 1 : (step + 1) / ks;  // own step q - 1
+                    a.cell[slot] = test_word(P, id, j, q);
                 }
             } else if (kind == kRareWallLow || kind == kRareWallHigh) {
                 f = offp[slot];
@@ -315,7 +335,7 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                     // re-injected: back in the store with a fresh clock (and y coordinate),
                     // deposited here
                     if (a.yp) static_cast<T*>(a.yp)[slot] = T(0);
-                    a.cell[slot] = fresh_word(P, j, step);
+                    a.cell[slot] = test_word(P, id, j, own_step_from(step + 1, P.nstep));
                     offp[slot] = f;
                     uxp[slot] = vx;
                     uyp[slot] = vy;
@@ -429,7 +449,7 @@ __global__ void __launch_bounds__(128) k_victims(const __grid_constant__ MoveArg
                         const int jv = (int)((uint32_t)a.cell[v] & kCellMask);
                         const T fv = offp[v];
                         const T ratio = (T)I.tratio;
-                        a.cell[gi] = fresh_word(Pi, jv, step);
+                        a.cell[gi] = test_word(Pi, wbest, jv, own_step_from(step + 1, Pi.nstep));
                         offp[gi] = fv;
                         uxp[gi] = uxp[v] * ratio;
                         uyp[gi] = uyp[v] * ratio;
