@@ -68,13 +68,8 @@ def profiled_traffic(kernel: str, precision: str):
         with open(path) as fh:
             d = json.load(fh)
         ent = d[precision]
-        from paper_2404_10270_gb300.build import SRC
-        import hashlib
-        h = hashlib.sha256()
-        for f in ("mover.cuh", "common.cuh", "mover_f32.cu", "mover_f64.cu"):
-            with open(os.path.join(SRC, f), "rb") as fh:
-                h.update(fh.read())
-        if ent.get("source_sha256") != h.hexdigest():
+        from paper_2404_10270_gb300.build import source_key
+        if ent.get("source_key") != source_key():
             return None
         return float(ent["dram_bytes_per_particle"])
     except Exception:

@@ -72,6 +72,21 @@ def _compile(unit: str, extra, verbose: bool, outdir: str = OUT) -> str:
     return obj
 
 
+def source_key(files=("mover.cuh", "common.cuh", "mover_f32.cu", "mover_f64.cu"), read=None) -> str:
+    """SHA-256 of the code of the given sources with comments and blank space removed: the
+    key under which measurements of the compiled kernels (ncu traffic) are kept, so that an
+    edit of a comment does not disown them."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in files:
+        text = read(f) if read else open(os.path.join(SRC, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
     """Compile and link libbitpic.so (checked=True: libbitpic_checked.so, the
     bounds-checked device build) if any source is newer than the library."""

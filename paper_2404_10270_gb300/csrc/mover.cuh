@@ -556,12 +556,14 @@ __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams&
         if (collides && (clk & kClockDue) == (uint32_t)(mown & (int64_t)kClockDue)) {
             if (clk & kClockPending) {
                 cand |= 1u << k;
-                clk = (uint32_t)((mown + 1) & (int64_t)kClockDue);  // a test next step
+                // a test next step (the event kernel draws it when it takes the
+                // candidate and puts its outcome in the clock)
+                clk = (uint32_t)((mown + 1) & (int64_t)kClockDue);
             } else if (!TEST) {
-                // a test off the common test steps (the clock of a particle that
-                // was a candidate in the last step, or was re-injected or created
-                // by ionization then): the event kernel draws it, with this
-                // step's counter, and sets the clock
+                // a test off the common test steps (the first clock of an ionization
+                // product, whose id the event kernel did not know yet, or of a loaded
+                // particle): the event kernel draws it, with this step's counter, and
+                // sets the clock
                 tst |= 1u << k;
             } else {
                 // a test step: the id is read only here
