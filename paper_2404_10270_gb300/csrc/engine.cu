@@ -126,6 +126,7 @@ struct pic_handle {
 
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;  // read-back: device-to-host copies beside the writes
     int64_t step_h = 0;
     bool stale = true;
     // the sort folded into the time step: the last step before a sort counted the
@@ -1030,6 +1031,10 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         }
         h->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        h->last_error = "cudaStreamCreate failed";
+        return bail(PIC_ECUDA);
+    }
     int dev = 0;
     cudaDeviceProp prop;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
@@ -1586,6 +1591,8 @@ int pic_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n)
 namespace {
 // pic_get_particles and pic_get_particles_f32: offsets and velocities in double, or in
 // float with host_f32 (hb bytes per value).
+constexpr int64_t kGetChunks = 8;  // read-back: write/copy overlap granularity
+
 int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity,
                   int32_t* cell, void* off, void* vx, void* vy, void* vz, uint32_t* id,
                   uint8_t* state, int32_t flags, int64_t* n_out, bool host_f32,
@@ -1650,17 +1657,44 @@ int get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t capacity
         g.state = state ? (uint8_t*)take(n) : nullptr;
         g.yp = yp ? (double*)take(n * 8) : nullptr;
     }
-    CUDA_TRY(h, launch_get(g, s));
-    if (!on_device && live > 0) {
-        const size_t m = (size_t)live;
-        if (cell) CUDA_TRY(h, cudaMemcpyAsync(cell, g.cell, m * 4, cudaMemcpyDeviceToHost, s));
-        if (off) CUDA_TRY(h, cudaMemcpyAsync(off, g.off, m * hb, cudaMemcpyDeviceToHost, s));
-        if (vx) CUDA_TRY(h, cudaMemcpyAsync(vx, g.vx, m * hb, cudaMemcpyDeviceToHost, s));
-        if (vy) CUDA_TRY(h, cudaMemcpyAsync(vy, g.vy, m * hb, cudaMemcpyDeviceToHost, s));
-        if (vz) CUDA_TRY(h, cudaMemcpyAsync(vz, g.vz, m * hb, cudaMemcpyDeviceToHost, s));
-        if (id) CUDA_TRY(h, cudaMemcpyAsync(id, g.id, m * 4, cudaMemcpyDeviceToHost, s));
-        if (state) CUDA_TRY(h, cudaMemcpyAsync(state, g.state, m, cudaMemcpyDeviceToHost, s));
-        if (yp) CUDA_TRY(h, cudaMemcpyAsync(yp, g.yp, m * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, launch_get_scan(g, s));
+    if (on_device || live == 0) {
+        CUDA_TRY(h, launch_get_write(g, 0, nb, s));
+    } else {
+        // the output offsets of the blocks on the host, then the writes in chunks: the
+        // copy stream moves each chunk's outputs to the host while the next is written
+        std::vector<unsigned long long> bc((size_t)nb + 1);
+        CUDA_TRY(h, cudaMemcpyAsync(bc.data(), g.block_count, 8 * (size_t)(nb + 1),
+                                    cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        const int64_t chunks = std::min<int64_t>(nb, kGetChunks);
+        std::vector<cudaEvent_t> evs;
+        auto span = [&](void* dst, const void* src, size_t elem, size_t o0, size_t o1) {
+            return cudaMemcpyAsync(static_cast<char*>(dst) + o0 * elem,
+                                   static_cast<const char*>(src) + o0 * elem, (o1 - o0) * elem,
+                                   cudaMemcpyDeviceToHost, h->copy_stream);
+        };
+        for (int64_t c = 0; c < chunks; ++c) {
+            const int64_t b0 = nb * c / chunks, b1 = nb * (c + 1) / chunks;
+            CUDA_TRY(h, launch_get_write(g, b0, b1 - b0, s));
+            cudaEvent_t ev = take_event(h);
+            evs.push_back(ev);
+            CUDA_TRY(h, cudaEventRecord(ev, s));
+            CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, ev, 0));
+            const size_t o0 = (size_t)std::min<unsigned long long>(bc[b0], live);
+            const size_t o1 = (size_t)std::min<unsigned long long>(bc[b1], live);
+            if (o1 <= o0) continue;
+            if (cell) CUDA_TRY(h, span(cell, g.cell, 4, o0, o1));
+            if (off) CUDA_TRY(h, span(off, g.off, hb, o0, o1));
+            if (vx) CUDA_TRY(h, span(vx, g.vx, hb, o0, o1));
+            if (vy) CUDA_TRY(h, span(vy, g.vy, hb, o0, o1));
+            if (vz) CUDA_TRY(h, span(vz, g.vz, hb, o0, o1));
+            if (id) CUDA_TRY(h, span(id, g.id, 4, o0, o1));
+            if (state) CUDA_TRY(h, span(state, g.state, 1, o0, o1));
+            if (yp) CUDA_TRY(h, span(yp, g.yp, 8, o0, o1));
+        }
+        CUDA_TRY(h, cudaStreamSynchronize(h->copy_stream));
+        for (cudaEvent_t ev : evs) h->event_pool.push_back(ev);
     }
     CUDA_TRY(h, cudaStreamSynchronize(s));
     return PIC_OK;
@@ -1804,6 +1838,7 @@ int pic_destroy(pic_handle* h)
     for (void* p : h->allocs) cudaFree(p);
     if (h->io) cudaFree(h->io);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     cudaGetLastError();
     delete h;
     return PIC_OK;

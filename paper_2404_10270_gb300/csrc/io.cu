@@ -143,7 +143,8 @@ __global__ void __launch_bounds__(1024) k_get_scan(unsigned long long* bc, int64
 template <typename T, typename H>
 __global__ void k_get_write(const GetArgs g)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t blk = g.block0 + blockIdx.x;  // this block's 1024 slots
+    const int64_t k = blk * (int64_t)blockDim.x + threadIdx.x;
     const bool live = k < g.nslots && g.s_cell[g.base + k] >= 0;
     const unsigned b = __ballot_sync(0xffffffffu, live);
     __shared__ int woff[32];
@@ -162,7 +163,7 @@ __global__ void k_get_write(const GetArgs g)
     if (!live) return;
     unsigned lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    const int64_t o = (int64_t)g.block_count[blockIdx.x] + woff[warp] + __popc(b & lt);
+    const int64_t o = (int64_t)g.block_count[blk] + woff[warp] + __popc(b & lt);
     if (o >= g.capacity) return;
     const int64_t s = g.base + k;
     const uint32_t word = (uint32_t)g.s_cell[s];
@@ -267,18 +268,26 @@ cudaError_t launch_load(const LoadArgs& l, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_get(const GetArgs& g, cudaStream_t st)
+cudaError_t launch_get_scan(const GetArgs& g, cudaStream_t st)
 {
     const int64_t nb = (g.nslots + 1023) / 1024;
     if (nb == 0) return cudaSuccess;
     k_get_count<<<(unsigned)nb, 1024, 0, st>>>(g.s_cell, g.base, g.nslots, g.block_count);
     k_get_scan<<<1, 1024, 0, st>>>(g.block_count, nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_write(GetArgs g, int64_t block0, int64_t nblocks, cudaStream_t st)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    g.block0 = block0;
+    const unsigned nb = (unsigned)nblocks;
     if (g.precision == PIC_FP64) {
-        if (g.host_f32) k_get_write<double, float><<<(unsigned)nb, 1024, 0, st>>>(g);
-        else k_get_write<double, double><<<(unsigned)nb, 1024, 0, st>>>(g);
+        if (g.host_f32) k_get_write<double, float><<<nb, 1024, 0, st>>>(g);
+        else k_get_write<double, double><<<nb, 1024, 0, st>>>(g);
     } else {
-        if (g.host_f32) k_get_write<float, float><<<(unsigned)nb, 1024, 0, st>>>(g);
-        else k_get_write<float, double><<<(unsigned)nb, 1024, 0, st>>>(g);
+        if (g.host_f32) k_get_write<float, float><<<nb, 1024, 0, st>>>(g);
+        else k_get_write<float, double><<<nb, 1024, 0, st>>>(g);
     }
     return cudaGetLastError();
 }

@@ -172,8 +172,14 @@ struct GetArgs {
     double* yp;             // y coordinates out (double), or null
     unsigned long long* block_count;  // scratch, ceil(nslots/1024)+1 entries
     int64_t capacity;                 // entries of the output arrays
+    int64_t block0;                   // first 1024-slot block of this write launch
 };
-cudaError_t launch_get(const GetArgs& g, cudaStream_t st);
+// Read-back in two phases: the live count of every 1024-slot block and their scan
+// (block_count[b] = the output index of block b's first live particle, total at [nb]),
+// then the compacted write of blocks [block0, block0 + nblocks), so that a caller can
+// copy the output of one range to the host while the next range is written.
+cudaError_t launch_get_scan(const GetArgs& g, cudaStream_t st);
+cudaError_t launch_get_write(GetArgs g, int64_t block0, int64_t nblocks, cudaStream_t st);
 
 // store yp[base + k] = in[k] (double in, the store's precision T), k < n
 cudaError_t launch_set_yp(void* s_yp, int64_t base, const double* in, int64_t n, int precision,
