@@ -57,3 +57,35 @@ def test_full_size_one_step(full_case, precision, tol):
         assert ex < tol and ev < tol, (s, ex, ev)
     for g, o in zip(gp, ora):
         np.testing.assert_array_equal(by_id(g)["state"], o["state"])
+
+
+def test_paper_case_full_size_fp64_one_cycle():
+    """The paper's test case at its benchmark size (100,000 cells x 100 particles per cell
+    x e, D+ and D = 30,000,000 particles; ionization depleting the D particles) over one
+    whole sort cycle of 20 steps: the D particles' one move, their separate sort and
+    every step's conversions of targets into ions, against the oracle (FP64: counts,
+    ids and clocks exact, particles within 1e-12)."""
+    from oracle.oracle import Oracle
+    ensure_built()
+    phys = W.ionization_case()
+    loads = W.initial_load(phys, seed=phys.seed)
+    steps = phys.sort_interval
+    o = Oracle(phys)
+    o.load_all(loads)
+    o.step(steps)
+    om = o.moments()
+    ora = [o.particles(s) for s in range(3)]
+    del o
+    sim = capi.Sim(phys, precision=capi.FP64, sort_interval=phys.sort_interval)
+    sim.load_all(loads)
+    sim.step(steps)
+    gm = sim.moments(0)
+    gp = [sim.particles(0, s) for s in range(3)]
+    sim.close()
+    assert om["collisions"][2] > 0  # targets were converted
+    np.testing.assert_array_equal(gm["live"], om["live"])
+    np.testing.assert_array_equal(gm["collisions"], om["collisions"])
+    for s, (ex, ev) in enumerate(particle_errors(phys, gp, ora)):
+        assert ex < 1e-12 and ev < 1e-12, (s, ex, ev)
+    for g, o in zip(gp, ora):
+        np.testing.assert_array_equal(by_id(g)["state"], by_id(o)["state"])
