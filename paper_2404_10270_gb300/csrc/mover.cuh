@@ -769,11 +769,11 @@ template <typename T, int NT, bool YP>
 struct SortSmem {
     static constexpr int NW = NT / 32;
     static constexpr int C = NW * 128;  // particles of a chunk
-    // staged particles (off, ux, uy, uz and with YP yp in T; cell word, id; start-cell
-    // key), then the per-cell counts, run offsets in the chunk, global run starts, and
+    // staged particles (off, ux, uy, uz and with YP yp in T; cell word, id; destination
+    // in the segment), then the per-cell counts, run offsets in the chunk, global run starts, and
     // the per-warp summaries (segment, lowest and highest start cell) of two consecutive
     // chunks
-    static constexpr size_t bytes = (size_t)C * ((YP ? 5 : 4) * sizeof(T) + 4 + 4 + 2) +
+    static constexpr size_t bytes = (size_t)C * ((YP ? 5 : 4) * sizeof(T) + 4 + 4 + 4) +
                                     (size_t)3 * kSortSpan * 4 + (size_t)2 * 3 * NW * 4;
 };
 
@@ -794,8 +794,8 @@ k_move_sort(const __grid_constant__ MoveArgs a)
     T* const s_yp = s_uz + C;  // (only with YP)
     int* const s_cell = reinterpret_cast<int*>(s_yp + (YP ? C : 0));
     uint32_t* const s_id = reinterpret_cast<uint32_t*>(s_cell + C);
-    unsigned short* const s_key = reinterpret_cast<unsigned short*>(s_id + C);
-    int* const cnt = reinterpret_cast<int*>(s_key + C);
+    uint32_t* const s_dst = s_id + C;
+    int* const cnt = reinterpret_cast<int*>(s_dst + C);
     int* const pre = cnt + kSortSpan;
     unsigned* const gb = reinterpret_cast<unsigned*>(pre + kSortSpan);
     // per-warp summaries, double-buffered by chunk parity: a warp may write the next
@@ -963,10 +963,10 @@ k_move_sort(const __grid_constant__ MoveArgs a)
                 s_uz[p] = uz[k];
                 s_cell[p] = c[k];
                 s_id[p] = idq[k];
-                s_key[p] = (unsigned short)key[k];
                 if (YP) s_yp[p] = static_cast<const T*>(a.yp)[slot + k];
                 const int64_t r = (int64_t)gb[key[k]] + rank[k];
                 to[k] = r < B.cap ? B.base + r : -1;
+                s_dst[p] = r < B.cap ? (uint32_t)r : 0xFFFFFFFFu;
             }
             queue_rare(a, bseg, cand, wlo, whi, tst, to);
             // (read before the barrier: the next chunk clears the counts after it)
@@ -977,14 +977,14 @@ k_move_sort(const __grid_constant__ MoveArgs a)
             T* const dux = static_cast<T*>(a.dux);
             T* const duy = static_cast<T*>(a.duy);
             T* const duz = static_cast<T*>(a.duz);
+#pragma unroll 4
             for (int p = threadIdx.x; p < ntot; p += NT) {
-                const int kk = s_key[p];
-                const int64_t r = (int64_t)gb[kk] + (p - pre[kk]);
-                if (r >= B.cap) {  // a histogram that does not match the store: refused
+                const uint32_t r = s_dst[p];
+                if (r == 0xFFFFFFFFu) {  // a histogram that does not match the store: refused
                     set_error(a.err, kErrCapacity);
                     continue;
                 }
-                const int64_t g = B.base + r;
+                const int64_t g = B.base + (int64_t)r;
                 __stcs(a.dcell + g, s_cell[p]);
                 __stcs(doff + g, s_off[p]);
                 __stcs(dux + g, s_ux[p]);
