@@ -115,6 +115,9 @@ struct pic_handle {
     unsigned long long* rare_count = nullptr;
     int grid_events = 0;
     unsigned* err = nullptr;
+    // the step count: [0] the step the kernels of a step read (set from [1] by k_tiles,
+    // the first kernel of every step), [1] the steps completed (the field phase of a
+    // step writes [0] + 1), so that the field phase may run beside the event kernels
     int64_t* step_d = nullptr;
     int* test_all = nullptr;  // nonzero: every clock may need a test in the next step (after a load)
     int64_t pair_min = (int64_t)1 << 24;  // particle slots from which plain FP32 steps use the mover pair
@@ -127,6 +130,12 @@ struct pic_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t copy_stream = nullptr;  // read-back: device-to-host copies beside the writes
+    // a step's event kernels run on side_stream beside its field phase when neither
+    // touches what the other reads or writes (no deposit from the event kernels:
+    // no volume source, no ionization, no neutral particle target); fork and join events
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool any_source = false;  // some instance re-injects through its walls (volume source)
     int64_t step_h = 0;
     bool stale = true;
     // the sort folded into the time step: the last step before a sort counted the
@@ -591,24 +600,30 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
         Span sp(h, 2);
         h->kernels += 1;
         CUDA_TRY(h, launch_sort_finish(sa, h->stream));
-        h->cur = 1 - h->cur;
-        a = move_args(h);  // the event kernels work on the sorted copy
+        h->cur = 1 - h->cur;  // the event kernels work on the sorted copy
     }
-    if (move && h->any_sn2d) {
-        // the y drift of 2-D species, with the velocities after the push (before the
-        // event kernel's collisions change them)
+    return PIC_OK;
+}
+
+// The event kernels of a time step, after its mover, on stream s: the y drift of 2-D
+// species (with the velocities after the push, before collisions change them), the
+// rare events, the conversions of neutral particle targets.  kCount: a re-injected
+// particle is counted in the cell histogram of the coming sort.
+int launch_step_events(pic_handle* h, int phase, cudaStream_t s)
+{
+    MoveArgs a = move_args(h);
+    if (phase == kCount) a.hist_out = h->hist;
+    if (h->any_sn2d) {
         Span sd(h, 3);
         h->kernels += 1;
-        CUDA_TRY(h, launch_drift_y(a, h->precision, 4 * h->sms, h->stream));
+        CUDA_TRY(h, launch_drift_y(a, h->precision, 4 * h->sms, s));
     }
-    if (move) {
-        Span se(h, 3);
+    Span se(h, 3);
+    h->kernels += 1;
+    CUDA_TRY(h, launch_events(a, h->precision, h->grid_events, s));
+    if (h->any_target) {
         h->kernels += 1;
-        CUDA_TRY(h, launch_events(a, h->precision, h->grid_events, h->stream));
-        if (h->any_target) {
-            h->kernels += 1;
-            CUDA_TRY(h, launch_victims(a, h->precision, h->grid_victims, h->stream));
-        }
+        CUDA_TRY(h, launch_victims(a, h->precision, h->grid_victims, s));
     }
     return PIC_OK;
 }
@@ -618,7 +633,7 @@ int launch_tiles_h(pic_handle* h)
     Span sp(h, 3);
     h->kernels += 1;
     CUDA_TRY(h, launch_tiles(h->segd, h->seg_n, h->seg_nmove, h->tile_start, h->nseg, 32,
-                             h->rare_count, h->stream));
+                             h->rare_count, h->step_d, h->stream));
     return PIC_OK;
 }
 
@@ -703,14 +718,17 @@ int collect_times(pic_handle* h)
 void set_block(pic_handle* h, int nt)
 {
     h->nt = nt;
+    // (FP32: plain steps of a batch with subcycling that the mover pair does not serve run
+    // the variant with subcycling and the inline clock test, built for fewer warps)
+    const bool subtest = h->any_subcycle && !(h->total_cap >= h->pair_min && h->pair_ok);
     const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, false, false, nt)
-                                             : move_blocks_per_sm_f32(h->any_mag, false, false, nt);
+                                             : move_blocks_per_sm_f32(h->any_mag, false, false, subtest, nt);
     h->grid_move = h->sms * std::max(bps, 1);
     // (the sort step's variant with the y coordinates of 2-D species holds more shared
     // memory a block)
     const int bss = h->precision == PIC_FP64
                         ? move_blocks_per_sm_f64(h->any_mag, true, h->any_sn2d, nt)
-                        : move_blocks_per_sm_f32(h->any_mag, true, h->any_sn2d, nt);
+                        : move_blocks_per_sm_f32(h->any_mag, true, h->any_sn2d, false, nt);
     h->grid_sort = h->sms * std::max(bss, 1);
 }
 
@@ -947,6 +965,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         h->any_ionize |= ionize;
         if (I.B[0] != 0.0 || I.B[1] != 0.0 || I.B[2] != 0.0) h->any_mag = true;
         else h->any_unmag = true;
+        if (I.bc == PIC_BC_SOURCE) h->any_source = true;
         for (int s = 0; s < I.nspecies; ++s) {
             if (species_nstep(I, s) > 1) h->any_subcycle = true;
             if (I.sp[s].sn2d) h->any_sn2d = true;
@@ -1031,8 +1050,11 @@ int pic_create(const pic_config* cfg, pic_handle** out)
         }
         h->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        h->last_error = "cudaStreamCreate failed";
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        h->last_error = "cudaStreamCreate / cudaEventCreate failed";
         return bail(PIC_ECUDA);
     }
     int dev = 0;
@@ -1105,7 +1127,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     h->cell_chunks = (h->max_nodes + 4095) / 4096;
     if (rc == PIC_OK) rc = dalloc(h, &h->cell_part, (size_t)h->nseg * h->cell_chunks);
     if (rc == PIC_OK) rc = dalloc(h, &h->err, 1);
-    if (rc == PIC_OK) rc = dalloc(h, &h->step_d, 1);
+    if (rc == PIC_OK) rc = dalloc(h, &h->step_d, 2);
     if (rc == PIC_OK) rc = dalloc(h, &h->test_all, 1);
     if (rc == PIC_OK) rc = dalloc(h, &h->kin, (size_t)PIC_MAX_SPECIES);
     if (rc) return bail(rc);
@@ -1146,7 +1168,7 @@ int pic_create(const pic_config* cfg, pic_handle** out)
     if (e == cudaSuccess) e = z(h->ev_count, (size_t)h->ninst * 8);
     if (e == cudaSuccess) e = z(h->next_id, (size_t)h->ninst * 8);
     if (e == cudaSuccess) e = z(h->err, 4);
-    if (e == cudaSuccess) e = z(h->step_d, 8);
+    if (e == cudaSuccess) e = z(h->step_d, 16);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->test_all, 1, sizeof(int), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->segd, h->segh.data(), sizeof(SegParams) * h->segh.size(),
@@ -1349,6 +1371,19 @@ int enqueue_step(pic_handle* h)
     if ((rc = launch_tiles_h(h))) return rc;
     if ((rc = launch_move(h, true, phase))) return rc;
     h->hist_ready = phase == kCount;
+    // the event kernels beside the field phase: they deposit nothing (no volume source,
+    // no ionization, no neutral particle target) and the field phase reads and writes
+    // only the deposit, the field and its own scratch (not when kernels are timed one
+    // by one)
+    const bool beside = !h->any_source && !h->any_ionize && !h->any_target && !h->profiling;
+    if (beside) {
+        CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
+        CUDA_TRY(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+        if ((rc = launch_step_events(h, phase, h->side_stream))) return rc;
+        CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side_stream));
+    } else {
+        if ((rc = launch_step_events(h, phase, h->stream))) return rc;
+    }
     if (h->any_ionize) {
         Span sp(h, 3);
         h->kernels += 1;
@@ -1361,6 +1396,7 @@ int enqueue_step(pic_handle* h)
         h->kernels += h->any_poisson ? 2 : 1;
         CUDA_TRY(h, launch_field(field_args(h), true, h->stream));
     }
+    if (beside) CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     h->step_h += 1;
     if (sort_after && (rc = do_sort(h))) return rc;
     return PIC_OK;
@@ -1525,7 +1561,7 @@ int pic_moments(pic_handle* h, int32_t inst, pic_moments_out* out, double* densi
     int64_t step = 0;
     std::vector<unsigned long long> live(ns), wc(2 * ns), col(kMaxProc);
     std::vector<double> we(2 * ns), kin(ns);
-    CUDA_TRY(h, cudaMemcpy(&step, h->step_d, 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(&step, h->step_d + 1, 8, cudaMemcpyDeviceToHost));
     CUDA_TRY(h, cudaMemcpy(live.data(), h->seg_live + ip.seg0, 8 * ns, cudaMemcpyDeviceToHost));
     CUDA_TRY(h, cudaMemcpy(wc.data(), h->wall_count + 2 * ip.seg0, 16 * ns, cudaMemcpyDeviceToHost));
     CUDA_TRY(h, cudaMemcpy(we.data(), h->wall_energy + 2 * ip.seg0, 16 * ns, cudaMemcpyDeviceToHost));
@@ -1761,7 +1797,8 @@ int pic_restore_counters(pic_handle* h, int64_t step, const uint64_t* next_id)
     if (rc) return rc;
     if (step < 0) return fail(h, PIC_EINVAL, "pic_restore_counters: step < 0");
     if ((rc = sync_check(h))) return rc;
-    CUDA_TRY(h, cudaMemcpy(h->step_d, &step, 8, cudaMemcpyHostToDevice));
+    const int64_t both[2] = {step, step};
+    CUDA_TRY(h, cudaMemcpy(h->step_d, both, 16, cudaMemcpyHostToDevice));
     if (step != h->step_h) {
         CUDA_TRY(h, launch_rebase_clocks(h->segd, h->nseg, h->st[h->cur].cell, h->step_h, step, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -1839,6 +1876,9 @@ int pic_destroy(pic_handle* h)
     if (h->io) cudaFree(h->io);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     cudaGetLastError();
     delete h;
     return PIC_OK;

@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(kChunkThreads) k_field_emit(const FieldArgs f,
 {
     __shared__ i128 sh[33];
     const int c = blockIdx.x;
-    if (advance && c == 0 && threadIdx.x == 0) *f.step += 1;
+    // the steps completed (the kernels of the next step read it once k_tiles has set it)
+    if (advance && c == 0 && threadIdx.x == 0) f.step[1] = f.step[0] + 1;
     const int b = f.chunk_inst[c];
     const InstParams& I = f.inst[b];
     const int N = I.ncells;
@@ -288,11 +289,13 @@ __global__ void __launch_bounds__(kFieldThreads) k_potential(const FieldArgs f, 
 
 __global__ void __launch_bounds__(1024) k_tiles(const SegParams* seg, unsigned long long* seg_n,
                                                 int64_t* seg_nmove, int64_t* tile_start, int nseg,
-                                                int tile_quads, unsigned long long* rare_count)
+                                                int tile_quads, unsigned long long* rare_count,
+                                                int64_t* step)
 {
     if (threadIdx.x == 0) {
         rare_count[0] = 0ull;
         rare_count[1] = 0ull;
+        step[0] = step[1];  // the step the kernels of this step read
     }
     __shared__ i128 sh[33];
     const int C = (nseg + blockDim.x - 1) / blockDim.x;
@@ -469,9 +472,10 @@ cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* ph
 
 cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
                          int64_t* tile_start, int nseg, int tile_quads,
-                         unsigned long long* rare_count, cudaStream_t st)
+                         unsigned long long* rare_count, int64_t* step, cudaStream_t st)
 {
-    k_tiles<<<1, 1024, 0, st>>>(seg, seg_n, seg_nmove, tile_start, nseg, tile_quads, rare_count);
+    k_tiles<<<1, 1024, 0, st>>>(seg, seg_n, seg_nmove, tile_start, nseg, tile_quads, rare_count,
+                                step);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,9 @@ cudaError_t launch_victims(const MoveArgs& a, int precision, int grid, cudaStrea
 // The y drift of 2-D species after the mover (MoveArgs.yp non-null), before the events.
 cudaError_t launch_drift_y(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
-int move_blocks_per_sm_f32(bool mag, bool sort, bool yp, int nt);
+// subtest: the grid of a batch whose plain steps run the variant with subcycling and the
+// inline clock test (a subcycled colliding species, or a batch below the mover pair's size)
+int move_blocks_per_sm_f32(bool mag, bool sort, bool yp, bool subtest, int nt);
 int move_blocks_per_sm_f64(bool mag, bool sort, bool yp, int nt);
 
 // ---- field phase and bookkeeping (field.cu) -------------------------------------
@@ -53,7 +55,7 @@ struct FieldArgs {
     i128* part_sum;
     i128* part_w;
     i128* zfirst;
-    int64_t* step;                    // incremented once per emit
+    int64_t* step;                    // [0] the step; an advancing emit sets [1] = [0] + 1
     i128* zs;                         // per instance node arrays: 4x the smoothed node
                                       // charge (instances with the smoother), else unused
     int any_poisson;
@@ -66,10 +68,10 @@ cudaError_t launch_potential(const FieldArgs& f, int inst, double dx, double* ph
 // Snapshot each segment's slot count, rounded up to a whole quad, as the count to
 // move, and build the tile prefix (tiles of `tile_quads` quads).
 // Also empties the rare-event queue and the target request list of the coming step
-// (rare_count[0] and [1]).
+// (rare_count[0] and [1]) and sets the step its kernels read: step[0] = step[1].
 cudaError_t launch_tiles(const SegParams* seg, unsigned long long* seg_n, int64_t* seg_nmove,
                          int64_t* tile_start, int nseg, int tile_quads,
-                         unsigned long long* rare_count, cudaStream_t st);
+                         unsigned long long* rare_count, int64_t* step, cudaStream_t st);
 
 // Number this step's ionization products by the rank of their parent id.
 // `done`: one zeroed counter per instance (left zeroed).

@@ -41,13 +41,14 @@ cudaError_t go(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed, boo
 }
 
 template <int NT>
-int occupancy(bool mag, bool sort, bool yp)
+int occupancy(bool mag, bool sort, bool yp, bool subtest)
 {
     if (sort) return sort_step_blocks_per_sm<float, NT>(mag, yp);
     int n = 0;
     const cudaError_t e =
         mag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, true, true, false, false, true>, NT, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false, false, true>, NT, 0);
+        : subtest ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, true, false, true>, NT, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<float, NT, false, true, false, false, true>, NT, 0);
     return e == cudaSuccess ? n : 0;
 }
 }  // namespace
@@ -62,12 +63,12 @@ cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bo
     }
 }
 
-int move_blocks_per_sm_f32(bool mag, bool sort, bool yp, int nt)
+int move_blocks_per_sm_f32(bool mag, bool sort, bool yp, bool subtest, int nt)
 {
     switch (nt) {
-        case 128: return occupancy<128>(mag, sort, yp);
-        case 512: return occupancy<512>(mag, sort, yp);
-        default: return occupancy<256>(mag, sort, yp);
+        case 128: return occupancy<128>(mag, sort, yp, subtest);
+        case 512: return occupancy<512>(mag, sort, yp, subtest);
+        default: return occupancy<256>(mag, sort, yp, subtest);
     }
 }
 
