@@ -143,6 +143,7 @@ struct pic_handle {
     // the host, and by the sort that used it); grid of the sorting mover
     bool hist_ready = false;
     int grid_sort = 0;
+    int grid_test = 0;  // grid of the mover pair's inline-test partner (FP32, no subcycling)
     int state = PIC_OK;
     std::string last_error;
 
@@ -587,12 +588,14 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
         for (int v = 0; v < (pair ? 2 : 1); ++v) {
             h->kernels += 1;
             const bool lean = v == 1;
+            // the pair's inline-test partner without subcycling: its own variant and grid
+            const bool gridv = pair && !lean && !h->any_subcycle;
             const cudaError_t e =
                 h->precision == PIC_FP64
                     ? launch_move_f64(a, mag, move, h->any_subcycle, h->any_unmag, sort, kept,
                                       h->nt, grid, h->stream)
                     : launch_move_f32(a, mag, move, h->any_subcycle, h->any_unmag, sort, lean,
-                                      kept, h->nt, grid, h->stream);
+                                      gridv, kept, h->nt, gridv ? h->grid_test : grid, h->stream);
             CUDA_TRY(h, e);
         }
     }
@@ -722,13 +725,15 @@ void set_block(pic_handle* h, int nt)
     // the variant with subcycling and the inline clock test, built for fewer warps)
     const bool subtest = h->any_subcycle && !(h->total_cap >= h->pair_min && h->pair_ok);
     const int bps = h->precision == PIC_FP64 ? move_blocks_per_sm_f64(h->any_mag, false, false, nt)
-                                             : move_blocks_per_sm_f32(h->any_mag, false, false, subtest, nt);
+                                             : move_blocks_per_sm_f32(h->any_mag, false, false, subtest, false, nt);
     h->grid_move = h->sms * std::max(bps, 1);
+    const int bts = h->precision == PIC_FP64 ? bps : move_blocks_per_sm_f32(false, false, false, false, true, nt);
+    h->grid_test = h->sms * std::max(bts, 1);
     // (the sort step's variant with the y coordinates of 2-D species holds more shared
     // memory a block)
     const int bss = h->precision == PIC_FP64
                         ? move_blocks_per_sm_f64(h->any_mag, true, h->any_sn2d, nt)
-                        : move_blocks_per_sm_f32(h->any_mag, true, h->any_sn2d, false, nt);
+                        : move_blocks_per_sm_f32(h->any_mag, true, h->any_sn2d, false, false, nt);
     h->grid_sort = h->sms * std::max(bss, 1);
 }
 

@@ -285,8 +285,15 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
             const SegParams& P = a.seg[s];
             const uint32_t id = a.id[slot];
             // a clock test needs only the id and the cell word; the state is read when the
-            // particle collides or left through a wall
+            // particle collides or left through a wall (a candidate and a wall hit need it
+            // in any case: read together with the id, one round trip to memory fewer)
             T f = T(0), vx = T(0), vy = T(0), vz = T(0);
+            if (kind != kRareTest) {
+                f = offp[slot];
+                vx = uxp[slot];
+                vy = uyp[slot];
+                vz = uzp[slot];
+            }
             if ((kind == kRareCandidate || kind == kRareTest) &&
                 in_range(a.err, (int)((uint32_t)a.cell[slot] & kCellMask), 0, P.ncells)) {
                 const int j = (int)((uint32_t)a.cell[slot] & kCellMask);
@@ -307,10 +314,12 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                                                                   g > 0 && g < dgrid));
                 }
                 if (now) {
-                    f = offp[slot];
-                    vx = uxp[slot];
-                    vy = uyp[slot];
-                    vz = uzp[slot];
+                    if (kind == kRareTest) {
+                        f = offp[slot];
+                        vx = uxp[slot];
+                        vy = uyp[slot];
+                        vz = uzp[slot];
+                    }
                     const int p = collide<T>(a, P, s, id, step, j, f, vx, vy, vz, wd.y, wd.z,
                                              slot);
                     if (p >= 0) {
@@ -325,10 +334,6 @@ __global__ void __launch_bounds__(128) k_events(const __grid_constant__ MoveArgs
                     a.cell[slot] = test_word(P, id, j, q);
                 }
             } else if (kind == kRareWallLow || kind == kRareWallHigh) {
-                f = offp[slot];
-                vx = uxp[slot];
-                vy = uyp[slot];
-                vz = uzp[slot];
                 int j = kind == kRareWallLow ? -1 : P.ncells;
                 wkey = 2 * s + (kind == kRareWallLow ? 0 : 1);
                 if (wall_event<T>(a, P, s, id, step, j, f, vx, vy, vz) == 1) {

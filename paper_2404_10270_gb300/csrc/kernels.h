@@ -15,11 +15,14 @@ struct MoveArgs;
 // unmagnetized instances in one batch; `sort`: the step also sorts the store by cell
 // into the other copy (MoveArgs.cursor, .d*); `lean` (FP32, a plain step of a batch
 // without magnetic field): the variant that queues collision-clock tests for the event
-// kernel instead of drawing them inline; `kept`: the neutral particle targets (whose
-// deposit is kept from step to step) move on this step (on the other steps their tiles
-// are skipped).  Returns the launch error.
+// kernel instead of drawing them inline; `gridv`: the inline-test partner of the mover
+// pair, which runs only on the steps where every clock tests (without subcycling: the
+// variant that draws a quad's four tests side by side); `kept`: the neutral particle
+// targets (whose deposit is kept from step to step) move on this step (on the other
+// steps their tiles are skipped).  Returns the launch error.
 cudaError_t launch_move_f32(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
-                            bool sort, bool lean, bool kept, int nt, int grid, cudaStream_t st);
+                            bool sort, bool lean, bool gridv, bool kept, int nt, int grid,
+                            cudaStream_t st);
 cudaError_t launch_move_f64(const MoveArgs& a, bool mag, bool move, bool sub, bool mixed,
                             bool sort, bool kept, int nt, int grid, cudaStream_t st);
 // The rare events the mover queued this step (events.cu): collision candidates, clock
@@ -32,8 +35,9 @@ cudaError_t launch_victims(const MoveArgs& a, int precision, int grid, cudaStrea
 cudaError_t launch_drift_y(const MoveArgs& a, int precision, int grid, cudaStream_t st);
 // resident blocks per SM of the mover variant (0 on error)
 // subtest: the grid of a batch whose plain steps run the variant with subcycling and the
-// inline clock test (a subcycled colliding species, or a batch below the mover pair's size)
-int move_blocks_per_sm_f32(bool mag, bool sort, bool yp, bool subtest, int nt);
+// inline clock test (a subcycled colliding species, or a batch below the mover pair's size);
+// gridv: the grid of the pair's inline-test partner without subcycling
+int move_blocks_per_sm_f32(bool mag, bool sort, bool yp, bool subtest, bool gridv, int nt);
 int move_blocks_per_sm_f64(bool mag, bool sort, bool yp, int nt);
 
 // ---- field phase and bookkeeping (field.cu) -------------------------------------

@@ -46,6 +46,12 @@ constexpr int kMoveMinWarps = BITPIC_MOVE_MIN_WARPS;  // resident warps per SM t
 // batch with a subcycled colliding species: 48 resident warps leave it 40 registers and
 // ~100 B of spills, 40 leave it 48 (measured 2.5 % faster a step on 196.6 M particles)
 constexpr int kMoveMinWarpsSubTest = BITPIC_MOVE_MIN_WARPS_SUBTEST;
+#ifndef BITPIC_MOVE_MIN_WARPS_GRID
+#define BITPIC_MOVE_MIN_WARPS_GRID 32
+#endif
+// the FP32 variant for the steps on which every clock without a candidate tests (GRID):
+// four draws in flight per lane want registers more than warps
+constexpr int kMoveMinWarpsGrid = BITPIC_MOVE_MIN_WARPS_GRID;
 #ifndef BITPIC_MOVE_MIN_WARPS64
 #define BITPIC_MOVE_MIN_WARPS64 32
 #endif
@@ -131,6 +137,7 @@ template <> struct Prec<float> {
     static constexpr int min_warps = kMoveMinWarps;  // memory bound: as many warps as fit
     static constexpr int min_warps_mag = kMoveMinWarpsMag;
     static constexpr int min_warps_subtest = kMoveMinWarpsSubTest;
+    static constexpr int min_warps_grid = kMoveMinWarpsGrid;
     static __device__ __forceinline__ uint64_t qright(float f)
     {
         return (uint64_t)__float2uint_rn(f * 16777216.0f);
@@ -173,6 +180,7 @@ template <> struct Prec<double> {
     static constexpr int min_warps = kMoveMinWarps64;  // FP64-pipe bound: registers first
     static constexpr int min_warps_mag = kMoveMinWarps64Mag;
     static constexpr int min_warps_subtest = kMoveMinWarps64;
+    static constexpr int min_warps_grid = kMoveMinWarps64;
     // rint(f 2^48) for f in [0, 1), ties to even, from the bits: f = m 2^(e-1075), so
     // f 2^48 = m / 2^(1027-e) rounded to nearest even (integer ALU only).
     static __device__ __forceinline__ uint64_t qright(double f)
@@ -244,10 +252,12 @@ template <> struct Prec<double> {
 };
 
 // Resident blocks per SM each mover variant is compiled for (its register budget).
-// SUBTEST: the variant with subcycling and the inline clock test.
-template <typename T, bool MAG, int NT, bool SUBTEST = false>
+// SUBTEST: the variant with subcycling and the inline clock test; GRID: the variant for
+// the steps on which every clock tests.
+template <typename T, bool MAG, int NT, bool SUBTEST = false, bool GRID = false>
 struct MoveOccupancy {
     static constexpr int warps = MAG ? Prec<T>::min_warps_mag
+                                 : GRID ? Prec<T>::min_warps_grid
                                  : SUBTEST ? Prec<T>::min_warps_subtest : Prec<T>::min_warps;
     static constexpr int blocks = warps / (NT / 32) > 0 ? warps / (NT / 32) : 1;
 };
@@ -489,13 +499,15 @@ __device__ __forceinline__ void sort_write(const MoveArgs& a, const int64_t to[4
 // low or high wall (wlo, whi), clock test left to the event kernel (tst), cell word
 // changed (chg).  mown is the species' own index of this step (its clock's time),
 // dgrid the own steps to its next multiple of kGapMax.  The id of a test draw comes
-// from idq (SORT: already loaded) or from the store at `slot`.
-template <typename T, bool MAG, bool SORT, bool TEST>
+// from idq (SORT: already loaded) or from the store at `slot`; PRE: the test's
+// candidate-free run (before the cut at dgrid) is already in gq.
+template <typename T, bool MAG, bool SORT, bool TEST, bool PRE = false>
 __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams& P, bool smag,
                                              int64_t step, int64_t mown, int dgrid, int64_t slot,
                                              const uint32_t idq[4], int c[4], T f[4], T ux[4],
                                              T uy[4], T uz[4], unsigned& cand, unsigned& wlo,
-                                             unsigned& whi, unsigned& tst, unsigned& chg)
+                                             unsigned& whi, unsigned& tst, unsigned& chg,
+                                             const int* gq = nullptr)
 {
     using T2 = typename Prec<T>::T2;
     const T2* const accp = static_cast<const T2*>(a.accel);
@@ -578,9 +590,14 @@ __device__ __forceinline__ void quad_physics(const MoveArgs& a, const SegParams&
                 tst |= 1u << k;
             } else {
                 // a test step: the id is read only here
-                const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
-                const uint4 w = draw(idk, step, kRngCollide, key0, key1);
-                const int g = min(gap_steps(P.gap, P.glog, w.x), dgrid);
+                int g;
+                if (PRE) {
+                    g = min(gq[k], dgrid);
+                } else {
+                    const uint32_t idk = SORT ? idq[k] : __ldg(a.id + slot + k);
+                    const uint4 w = draw(idk, step, kRngCollide, key0, key1);
+                    g = min(gap_steps(P.gap, P.glog, w.x), dgrid);
+                }
                 if (g == 0) cand |= 1u << k;
                 const int64_t due = g == 0 ? mown + 1 : mown + g;
                 clk = (uint32_t)(due & (int64_t)kClockDue) | (g > 0 && g < dgrid ? kClockPending : 0u);
@@ -634,8 +651,8 @@ __device__ __forceinline__ void queue_rare(const MoveArgs& a, int s, unsigned ca
 // registers do not burden the common steps).  (The step that ends a sort cycle runs
 // k_move_sort below instead.)
 template <typename T, int NT, bool MAG, bool MOVE, bool SUB, bool MIXED, bool TEST,
-          bool KEPT = false>
-__global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT, MOVE && SUB && TEST>::blocks)
+          bool KEPT = false, bool GRID = false>
+__global__ void __launch_bounds__(NT, MoveOccupancy<T, MAG, NT, MOVE && SUB && TEST, GRID>::blocks)
 k_move(const __grid_constant__ MoveArgs a)
 {
     using Q = typename Prec<T>::Q;
@@ -702,7 +719,7 @@ k_move(const __grid_constant__ MoveArgs a)
         int c[4] = {-1, -1, -1, -1};
         T f[4] = {T(0), T(0), T(0), T(0)}, ux[4] = {T(0), T(0), T(0), T(0)};
         T uy[4] = {T(0), T(0), T(0), T(0)}, uz[4] = {T(0), T(0), T(0), T(0)};
-        const uint32_t idq[4] = {0u, 0u, 0u, 0u};
+        uint32_t idq[4] = {0u, 0u, 0u, 0u};
         if (act) {
             const int4 cc = __ldcs(reinterpret_cast<const int4*>(a.cell + slot));
             c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
@@ -712,6 +729,21 @@ k_move(const __grid_constant__ MoveArgs a)
                 ld4(uyp + slot, uy);
                 ld4(uzp + slot, uz);
             }
+            if (GRID) {
+                const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(a.id + slot));
+                idq[0] = ii.x; idq[1] = ii.y; idq[2] = ii.z; idq[3] = ii.w;
+            }
+        }
+        // GRID: every clock without a candidate tests on this step, so the quad's four
+        // draws (and their table lookups) go first, side by side, while the state loads
+        // are in flight; a clock that does not test ignores its result
+        int gq[4] = {0, 0, 0, 0};
+        if (GRID && P.collide) {
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[k] = draw(idq[k], step, kRngCollide, P.key0, P.key1).x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gq[k] = gap_steps(P.gap, P.glog, w[k]);
         }
         if (KEPT && MOVE && SUB && moves && deposit_kept(P)) {
             // its move: the old positions' charge leaves the kept deposit (the new
@@ -728,8 +760,8 @@ k_move(const __grid_constant__ MoveArgs a)
         }
         if (MOVE && (!SUB || moves)) {
             unsigned cand = 0, wlo = 0, whi = 0, tst = 0, chg = 0;
-            quad_physics<T, MAG, false, TEST>(a, P, smag, step, mown, dgrid, slot, idq, c, f, ux,
-                                              uy, uz, cand, wlo, whi, tst, chg);
+            quad_physics<T, MAG, false, TEST, GRID>(a, P, smag, step, mown, dgrid, slot, idq, c, f,
+                                                    ux, uy, uz, cand, wlo, whi, tst, chg, gq);
             // the cell words go back only where one of them changed (a cell crossing, a
             // wall, a collision event: a few per cent of the particles a step), decided
             // per 32-byte sector (two lanes) so that memory sees whole sectors
