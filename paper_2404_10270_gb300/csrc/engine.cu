@@ -609,9 +609,9 @@ int launch_move(pic_handle* h, bool move, int phase = kPlain)
 }
 
 // The event kernels of a time step, after its mover, on stream s: the y drift of 2-D
-// species (with the velocities after the push, before collisions change them), the
-// rare events, the conversions of neutral particle targets.  kCount: a re-injected
-// particle is counted in the cell histogram of the coming sort.
+// species (with the velocities after the push, before collisions change them) and the
+// rare events.  kCount: a re-injected particle or an ionization product is counted in
+// the cell histogram of the coming sort.
 int launch_step_events(pic_handle* h, int phase, cudaStream_t s)
 {
     MoveArgs a = move_args(h);
@@ -624,10 +624,26 @@ int launch_step_events(pic_handle* h, int phase, cudaStream_t s)
     Span se(h, 3);
     h->kernels += 1;
     CUDA_TRY(h, launch_events(a, h->precision, h->grid_events, s));
-    if (h->any_target) {
-        h->kernels += 1;
-        CUDA_TRY(h, launch_victims(a, h->precision, h->grid_victims, s));
-    }
+    return PIC_OK;
+}
+
+// The conversions of neutral particle targets into ions requested by the event kernel.
+int launch_victims_h(pic_handle* h, cudaStream_t s)
+{
+    const MoveArgs a = move_args(h);
+    Span se(h, 3);
+    h->kernels += 1;
+    CUDA_TRY(h, launch_victims(a, h->precision, h->grid_victims, s));
+    return PIC_OK;
+}
+
+// The numbering of this step's ionization products (their ids).
+int launch_births_h(pic_handle* h, cudaStream_t s)
+{
+    Span sp(h, 3);
+    h->kernels += 1;
+    CUDA_TRY(h, launch_births(h->instd, h->ninst, h->events, h->ev_count, h->next_id,
+                              h->st[h->cur].id, h->birth_keys_a, h->birth_keys_b, h->err, s));
     return PIC_OK;
 }
 
@@ -1376,32 +1392,42 @@ int enqueue_step(pic_handle* h)
     if ((rc = launch_tiles_h(h))) return rc;
     if ((rc = launch_move(h, true, phase))) return rc;
     h->hist_ready = phase == kCount;
-    // the event kernels beside the field phase: they deposit nothing (no volume source,
-    // no ionization, no neutral particle target) and the field phase reads and writes
-    // only the deposit, the field and its own scratch (not when kernels are timed one
-    // by one)
-    const bool beside = !h->any_source && !h->any_ionize && !h->any_target && !h->profiling;
-    if (beside) {
-        CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
-        CUDA_TRY(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+    // Work that shares no word with the rest of the step runs on the side stream, forked
+    // after the mover or the event kernel and joined before the next step (not when
+    // kernels are timed one by one): the event kernels when they deposit nothing (no
+    // volume source, no ionization, no neutral particle target; the field phase reads
+    // and writes only the deposit, the field and its own scratch), else the numbering
+    // of ionization products (it writes only the products' ids and the next free id,
+    // which neither the target conversions nor the field phase read)
+    const bool side = !h->profiling;
+    const bool quiet = !h->any_source && !h->any_ionize && !h->any_target;
+    auto fork = [&]() -> cudaError_t {
+        cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+        return e == cudaSuccess ? cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0) : e;
+    };
+    bool joined = false;
+    if (quiet && side) {
+        CUDA_TRY(h, fork());
         if ((rc = launch_step_events(h, phase, h->side_stream))) return rc;
         CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side_stream));
+        joined = true;
     } else {
         if ((rc = launch_step_events(h, phase, h->stream))) return rc;
-    }
-    if (h->any_ionize) {
-        Span sp(h, 3);
-        h->kernels += 1;
-        CUDA_TRY(h, launch_births(h->instd, h->ninst, h->events, h->ev_count, h->next_id,
-                                  h->st[h->cur].id, h->birth_keys_a, h->birth_keys_b, h->err,
-                                  h->stream));
+        if (h->any_ionize && side) {
+            CUDA_TRY(h, fork());
+            if ((rc = launch_births_h(h, h->side_stream))) return rc;
+            CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side_stream));
+            joined = true;
+        }
+        if (h->any_target && (rc = launch_victims_h(h, h->stream))) return rc;
+        if (h->any_ionize && !side && (rc = launch_births_h(h, h->stream))) return rc;
     }
     {
         Span sp(h, 1);
         h->kernels += h->any_poisson ? 2 : 1;
         CUDA_TRY(h, launch_field(field_args(h), true, h->stream));
     }
-    if (beside) CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    if (joined) CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     h->step_h += 1;
     if (sort_after && (rc = do_sort(h))) return rc;
     return PIC_OK;
