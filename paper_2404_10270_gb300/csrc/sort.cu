@@ -139,105 +139,240 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_scan(const SortArgs a)
 }
 
 // One lane's quad in flight through the scatter.
-template <typename T>
-struct SortQuad {
-    int c[4];
-    T vo[4], vx[4], vy[4], vz[4];
-    uint32_t vi[4];
-    int s;
-    int64_t slot;
-};
-
-// Scatter.  Each warp keeps the loads of its next tile in flight while it reserves the
-// destinations of the current one (an atomic round trip through L2 per cell group),
-// so the reservation latency does not stall the stream of loads.
-template <typename T, int NT>
+// Scatter.  A block takes NT/32 consecutive tiles (a chunk of up to 128 NT/32
+// particles).  When the chunk lies in one segment and its particles' cells span fewer
+// than kSortSpan cells (the common case: the store was sorted one cycle ago), the block
+// ranks them per cell in shared memory, reserves each cell's run with one global atomic
+// per cell, stages the particles in shared memory in that order and writes every run
+// with consecutive threads, so the scattered writes become coalesced runs of about a
+// cell's share of the chunk (the same staging as the sort step's mover, without its
+// physics).  Otherwise each warp reserves per cell and quad position and writes its
+// particles directly.
+template <typename T, int NT, bool YP>
 __global__ void __launch_bounds__(NT) k_scatter(const SortArgs a)
 {
+    constexpr int NW = NT / 32, C = NW * 128;
+    const unsigned FULL = 0xffffffffu;
     const int src = a.src, dst = 1 - a.src;
     const int32_t* cell = a.cell[src];
     const T* off = static_cast<const T*>(a.off[src]);
     const T* ux = static_cast<const T*>(a.ux[src]);
     const T* uy = static_cast<const T*>(a.uy[src]);
     const T* uz = static_cast<const T*>(a.uz[src]);
+    const T* yps = static_cast<const T*>(a.yp[src]);
     const uint32_t* id = a.id[src];
     int32_t* dcell = a.cell[dst];
     T* doff = static_cast<T*>(a.off[dst]);
     T* dux = static_cast<T*>(a.ux[dst]);
     T* duy = static_cast<T*>(a.uy[dst]);
     T* duz = static_cast<T*>(a.uz[dst]);
-    uint32_t* did = a.id[dst];
-    const T* yps = static_cast<const T*>(a.yp[src]);
     T* ypd = static_cast<T*>(a.yp[dst]);
-    const int64_t total = a.tile_start[a.nseg];
-    const int lane = threadIdx.x & 31;
+    uint32_t* did = a.id[dst];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const s_off = reinterpret_cast<T*>(smem_raw);
+    T* const s_ux = s_off + C;
+    T* const s_uy = s_ux + C;
+    T* const s_uz = s_uy + C;
+    T* const s_yp = s_uz + C;  // (only with YP)
+    int* const s_cell = reinterpret_cast<int*>(s_yp + (YP ? C : 0));
+    uint32_t* const s_id = reinterpret_cast<uint32_t*>(s_cell + C);
+    uint32_t* const s_dst = s_id + C;
+    int* const cnt = reinterpret_cast<int*>(s_dst + C);
+    int* const pre = cnt + kSortSpan;
+    unsigned* const gb = reinterpret_cast<unsigned*>(pre + kSortSpan);
+    // per-warp summaries (segment, lowest and highest cell), double-buffered by chunk
+    // parity: a warp may write the next chunk's entry while another still reads these
+    int* const wsum = reinterpret_cast<int*>(gb + kSortSpan);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
-    int ls = 0;                            // segment walk of the loads (tiles only increase)
-    int64_t ls_begin = 0, ls_end = -1;
-    auto load = [&](int64_t tile, SortQuad<T>& q) {
-        if (tile >= ls_end) {
-            ls = advance_segment(a.tile_start, a.nseg, ls, tile);
-            ls_begin = __ldg(a.tile_start + ls);
-            ls_end = __ldg(a.tile_start + ls + 1);
+    const int64_t total = a.tile_start[a.nseg];
+    int s = 0;
+    int64_t s_begin = 0, s_end = -1;
+    int parity = 0;
+    // every warp of the block walks the same chunks, so the barriers below match
+    for (int64_t chunk = blockIdx.x; chunk * NW < total; chunk += gridDim.x, parity ^= 1) {
+        int* const wseg = wsum + parity * 3 * NW;
+        int* const wmin = wseg + NW;
+        int* const wmax = wmin + NW;
+        const int64_t tile = chunk * NW + warp;
+        const bool have = tile < total;
+        if (have && tile >= s_end) {
+            s = advance_segment(a.tile_start, a.nseg, s, tile);
+            s_begin = __ldg(a.tile_start + s);
+            s_end = __ldg(a.tile_start + s + 1);
         }
-        q.s = ls;
-        const int64_t quad = (tile - ls_begin) * 32 + lane;
-        q.slot = a.seg[ls].base + 4 * quad;
-        q.c[0] = q.c[1] = q.c[2] = q.c[3] = -1;
-        if (quad < (a.seg_nmove[ls] >> 2) && in_range(a.err, 4 * quad + 3, 0, a.seg[ls].cap)) {
+        const SegParams& P = a.seg[s];
+        const int64_t quad = (tile - s_begin) * 32 + lane;
+        const int64_t slot = P.base + 4 * quad;
+        int c[4] = {-1, -1, -1, -1};
+        T vo[4], vx[4], vy[4], vz[4], vyp[4];
+        uint32_t vi[4] = {0u, 0u, 0u, 0u};
+        if (have && quad < (a.seg_nmove[s] >> 2) && in_range(a.err, 4 * quad + 3, 0, P.cap)) {
             // the whole quad with 128-bit loads (the mover's access pattern)
-            const int4 cc = __ldcs(reinterpret_cast<const int4*>(cell + q.slot));
-            q.c[0] = cc.x; q.c[1] = cc.y; q.c[2] = cc.z; q.c[3] = cc.w;
-            ld4(off + q.slot, q.vo);
-            ld4(ux + q.slot, q.vx);
-            ld4(uy + q.slot, q.vy);
-            ld4(uz + q.slot, q.vz);
-            const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(id + q.slot));
-            q.vi[0] = ii.x; q.vi[1] = ii.y; q.vi[2] = ii.z; q.vi[3] = ii.w;
+            const int4 cc = __ldcs(reinterpret_cast<const int4*>(cell + slot));
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+            ld4(off + slot, vo);
+            ld4(ux + slot, vx);
+            ld4(uy + slot, vy);
+            ld4(uz + slot, vz);
+            const uint4 ii = __ldcs(reinterpret_cast<const uint4*>(id + slot));
+            vi[0] = ii.x; vi[1] = ii.y; vi[2] = ii.z; vi[3] = ii.w;
+            if (YP) ld4(yps + slot, vyp);
         }
-    };
-    int64_t tile = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
-    SortQuad<T> cur;
-    if (tile < total) load(tile, cur);
-    for (; tile < total; tile += wstride) {
-        SortQuad<T> nxt;
-        nxt.c[0] = nxt.c[1] = nxt.c[2] = nxt.c[3] = -1;
-        if (tile + wstride < total) load(tile + wstride, nxt);
-        const SegParams& P = a.seg[cur.s];
-        // group equal cells of each slot across the warp; the four reservations are
-        // independent, so they are all issued before the first one is waited for
-        unsigned grp[4], base[4];
-        int key[4];
+        // cells of the quad (-1: empty slot); the chunk's span and segments
+        int j[4];
+        unsigned lmin = 0xFFFFFFFFu;
+        int lmax = -1;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (cur.c[k] >= 0 &&
-                !in_range(a.err, (int)((uint32_t)cur.c[k] & kCellMask), 0, P.ncells))
-                cur.c[k] = -1;  // (bounds-checked build only)
-            key[k] = cur.c[k] >= 0 ? (int)((uint32_t)cur.c[k] & kCellMask) : -1 - lane;
-            grp[k] = __match_any_sync(0xffffffffu, key[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            base[k] = 0;
-            if (cur.c[k] >= 0 && lane == __ffs(grp[k]) - 1)
-                base[k] = atomicAdd(a.hist + P.node + key[k], (unsigned)__popc(grp[k]));
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const unsigned b = __shfl_sync(0xffffffffu, base[k], __ffs(grp[k]) - 1);
-            if (cur.c[k] >= 0 && in_range(a.err, (int64_t)b + __popc(grp[k] & lt), 0, P.cap)) {
-                const int64_t to = P.base + (int64_t)b + __popc(grp[k] & lt);
-                dcell[to] = cur.c[k];
-                doff[to] = cur.vo[k];
-                dux[to] = cur.vx[k];
-                duy[to] = cur.vy[k];
-                duz[to] = cur.vz[k];
-                did[to] = cur.vi[k];
-                if (yps) ypd[to] = yps[cur.slot + k];
+            j[k] = c[k] >= 0 ? (int)((uint32_t)c[k] & kCellMask) : -1;
+            if (j[k] >= 0 && !in_range(a.err, j[k], 0, P.ncells)) {  // (checked build)
+                j[k] = -1;
+                c[k] = -1;
+            }
+            if (j[k] >= 0) {
+                lmin = min(lmin, (unsigned)j[k]);
+                lmax = max(lmax, j[k]);
             }
         }
-        cur = nxt;
+        const unsigned wmn = __reduce_min_sync(FULL, lmin);
+        const int wmx = __reduce_max_sync(FULL, lmax);
+        if (lane == 0) {
+            wseg[warp] = wmx >= 0 ? s : -1;
+            wmin[warp] = (int)wmn;
+            wmax[warp] = wmx;
+        }
+        for (int i = threadIdx.x; i < kSortSpan; i += NT) cnt[i] = 0;
+        __syncthreads();
+        int bseg, bmin, bmax;
+        bool one;
+        {
+            const int ws = lane < NW ? wseg[lane] : -1;
+            const int mn = ws >= 0 ? wmin[lane] : INT_MAX;
+            const int mx = ws >= 0 ? wmax[lane] : -1;
+            const int smax = __reduce_max_sync(FULL, ws);
+            const int smin = __reduce_min_sync(FULL, ws >= 0 ? ws : INT_MAX);
+            bseg = smax;
+            one = smax < 0 || smin == smax;
+            bmin = __reduce_min_sync(FULL, mn);
+            bmax = __reduce_max_sync(FULL, mx);
+        }
+        const bool staged = one && bseg >= 0 && bmax - bmin < kSortSpan;
+        if (staged) {
+            const SegParams& B = a.seg[bseg];
+            // rank of each particle among the chunk's particles of its cell: equal cells
+            // of a quad position grouped across the warp, one shared atomic a group
+            int key[4], rank[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                key[k] = j[k] >= 0 ? j[k] - bmin : -1;
+                const unsigned grp = __match_any_sync(FULL, key[k] >= 0 ? key[k] : kSortSpan + lane);
+                const int leader = __ffs(grp) - 1;
+                int base = 0;
+                if (key[k] >= 0 && lane == leader) base = atomicAdd(cnt + key[k], __popc(grp));
+                base = __shfl_sync(FULL, base, leader);
+                rank[k] = base + __popc(grp & lt);
+            }
+            __syncthreads();
+            // each cell's run: its offset in the chunk (scan of the counts) and its global
+            // start (one reservation per cell on the cell's cursor)
+            if (threadIdx.x < kSortSpan) {
+                const int n = cnt[threadIdx.x];
+                gb[threadIdx.x] = n > 0 ? atomicAdd(a.hist + B.node + bmin + threadIdx.x, (unsigned)n) : 0u;
+            }
+            if (warp == 0) {
+                int v[kSortSpan / 32], sum = 0;
+#pragma unroll
+                for (int i = 0; i < kSortSpan / 32; ++i) {
+                    v[i] = cnt[lane * (kSortSpan / 32) + i];
+                    sum += v[i];
+                }
+                int inc = sum;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(FULL, inc, d);
+                    if (lane >= d) inc += t;
+                }
+                int run = inc - sum;
+#pragma unroll
+                for (int i = 0; i < kSortSpan / 32; ++i) {
+                    pre[lane * (kSortSpan / 32) + i] = run;
+                    run += v[i];
+                }
+            }
+            __syncthreads();
+            // stage every particle at its place in the chunk's cell order
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (key[k] < 0) continue;
+                const int p = pre[key[k]] + rank[k];
+                if (!in_range(a.err, p, 0, C)) continue;  // (bounds-checked build only)
+                s_off[p] = vo[k];
+                s_ux[p] = vx[k];
+                s_uy[p] = vy[k];
+                s_uz[p] = vz[k];
+                s_cell[p] = c[k];
+                s_id[p] = vi[k];
+                if (YP) s_yp[p] = vyp[k];
+                const int64_t r = (int64_t)gb[key[k]] + rank[k];
+                s_dst[p] = r < B.cap ? (uint32_t)r : 0xFFFFFFFFu;
+            }
+            // (read before the barrier: the next chunk clears the counts after it)
+            const int ntot = pre[kSortSpan - 1] + cnt[kSortSpan - 1];
+            __syncthreads();
+            // write the runs: consecutive threads, consecutive slots of a cell's run
+#pragma unroll 4
+            for (int p = threadIdx.x; p < ntot; p += NT) {
+                const uint32_t r = s_dst[p];
+                if (r == 0xFFFFFFFFu) {  // a histogram that does not match the store: refused
+                    set_error(a.err, kErrCapacity);
+                    continue;
+                }
+                const int64_t g = B.base + (int64_t)r;
+                __stcs(dcell + g, s_cell[p]);
+                __stcs(doff + g, s_off[p]);
+                __stcs(dux + g, s_ux[p]);
+                __stcs(duy + g, s_uy[p]);
+                __stcs(duz + g, s_uz[p]);
+                __stcs(did + g, s_id[p]);
+                if (YP) ypd[g] = s_yp[p];
+            }
+        } else {
+            // per warp: group equal cells of each quad position across the warp; the
+            // four reservations are independent, so they are all issued before the first
+            // one is waited for
+            unsigned grp[4], base[4];
+            int key[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                key[k] = j[k] >= 0 ? j[k] : -1 - lane;
+                grp[k] = __match_any_sync(FULL, key[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                base[k] = 0;
+                if (j[k] >= 0 && lane == __ffs(grp[k]) - 1)
+                    base[k] = atomicAdd(a.hist + P.node + key[k], (unsigned)__popc(grp[k]));
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned b = __shfl_sync(FULL, base[k], __ffs(grp[k]) - 1);
+                const int64_t r = (int64_t)b + __popc(grp[k] & lt);
+                if (j[k] < 0) continue;
+                if (r >= P.cap) {  // a histogram that does not match the store: refused
+                    set_error(a.err, kErrCapacity);
+                    continue;
+                }
+                const int64_t to = P.base + r;
+                dcell[to] = c[k];
+                doff[to] = vo[k];
+                dux[to] = vx[k];
+                duy[to] = vy[k];
+                duz[to] = vz[k];
+                did[to] = vi[k];
+                if (YP) ypd[to] = vyp[k];
+            }
+        }
     }
 }
 
@@ -291,6 +426,19 @@ __global__ void __launch_bounds__(256) k_target_counts(const SortArgs a)
     }
 }
 
+// The scatter with its shared memory (staging of a chunk), on one resident wave.
+template <typename T, int NT, bool YP>
+cudaError_t launch_scatter(const SortArgs& a, int sms, cudaStream_t st)
+{
+    const int sm = (int)SortSmem<T, NT, YP>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_scatter<T, NT, YP>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    int nb = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<T, NT, YP>, NT, sm);
+    if (e != cudaSuccess) return e;
+    k_scatter<T, NT, YP><<<std::max(nb, 1) * sms, NT, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NT>
 cudaError_t run_sort(const SortArgs& a, int sms, cudaStream_t st)
 {
@@ -298,10 +446,12 @@ cudaError_t run_sort(const SortArgs& a, int sms, cudaStream_t st)
     const dim3 cg(a.nseg, a.cell_chunks);
     k_cell_partial<<<cg, kCellThreads, 0, st>>>(a);
     k_cell_scan<<<cg, kCellThreads, 0, st>>>(a);
-    if (a.precision == PIC_FP64)
-        k_scatter<double, NT><<<one_wave(k_scatter<double, NT>, NT, sms), NT, 0, st>>>(a);
-    else
-        k_scatter<float, NT><<<one_wave(k_scatter<float, NT>, NT, sms), NT, 0, st>>>(a);
+    const bool yp = a.yp[a.src] != nullptr;
+    const cudaError_t e =
+        a.precision == PIC_FP64
+            ? (yp ? launch_scatter<double, NT, true>(a, sms, st) : launch_scatter<double, NT, false>(a, sms, st))
+            : (yp ? launch_scatter<float, NT, true>(a, sms, st) : launch_scatter<float, NT, false>(a, sms, st));
+    if (e != cudaSuccess) return e;
     k_sort_finish<<<a.nseg, 256, 0, st>>>(a);
     if (a.tcount)
         k_target_counts<<<(int)std::min<int64_t>((a.seg_nodes + 255) / 256, 64 * sms), 256, 0, st>>>(a);
