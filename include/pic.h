@@ -140,6 +140,8 @@ typedef struct {
     int32_t sort_interval;      /* sort by cell every this many steps; 0 = never;
                                    -1 = autotune (10, 20, 40 or 80) */
     int32_t block;              /* mover threads per block (128, 256, 512); 0 = autotune.
+                                   The step that ends a sort cycle has its own block size,
+                                   128 ($BITPIC_SORT_BLOCK: 128, 256 or 512).
                                    The autotuner times one sort cycle per candidate on the
                                    first steps of the run (results do not depend on either
                                    choice) and caches the choice per GPU and size bucket
