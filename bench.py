@@ -292,9 +292,11 @@ def measure_form(sim, phys, steps, warmup, n_particles, precision_name, rank, wo
     # pic_step captures a CUDA graph the first time it meets a window of steps (store copy,
     # place in the sort cycle, length): the warm-up ends on a cycle boundary and runs two
     # whole cycles more, so the timed steps replay graphs captured before the timing (80 is
-    # a multiple of every sort interval the autotuner picks)
+    # a multiple of every sort interval the autotuner picks; the step count is the
+    # handle's, which autotuning steps before this call have advanced)
     K = sort_interval
-    sim.step((-(warmup) % K) + 2 * K)
+    done = int(sim.moments(0)["step"])
+    sim.step((-done % K) + 2 * K)
     sim.sync()
     physs = phys if isinstance(phys, list) else [phys]
 
