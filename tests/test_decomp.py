@@ -1,5 +1,6 @@
 """The domain decomposition of one instance by cells (the paper's Section 2), on CPU:
-its host logic alone, then two gloo ranks, each stepping half of an instance with the
+its host logic alone, then two and three gloo ranks (with three, the middle one
+exchanges with both neighbours), each stepping its part of an instance with the
 oracle's particle step, the field solved jointly, against the oracle's undivided run.
 
 Velocities cross the oracle's interface in physical units; with dt/dx a power of two
@@ -149,13 +150,14 @@ def _rank(rank, world, port, q):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_reproduce_the_undivided_oracle_run():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_reproduce_the_undivided_oracle_run(world):
     phys = _physics()
     loads = W.initial_load(phys, seed=21)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
     out = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
@@ -163,7 +165,7 @@ def test_two_gloo_ranks_reproduce_the_undivided_oracle_run():
         p.join(timeout=60)
         assert p.exitcode == 0
     cuts = out[0][1]
-    assert 0 < cuts[1] < phys.ncells
+    assert len(cuts) == world + 1 and all(0 < c < phys.ncells for c in cuts[1:-1])
 
     # the joint deposit and field of the first step equal the undivided ones bit for bit
     whole = Subdomain(phys.ncells, [0, phys.ncells], 0, phys.dx, phys.eps0)
@@ -181,15 +183,15 @@ def test_two_gloo_ranks_reproduce_the_undivided_oracle_run():
     o.load_all(loads)
     o.step(STEPS)
     om = o.moments()
-    np.testing.assert_array_equal(out[0][4] + out[1][4], om["wall_count"])
-    np.testing.assert_array_equal(out[0][5] + out[1][5], om["collisions"])
-    np.testing.assert_array_equal(out[0][6] + out[1][6], om["live"])
+    np.testing.assert_array_equal(sum(o_[4] for o_ in out), om["wall_count"])
+    np.testing.assert_array_equal(sum(o_[5] for o_ in out), om["collisions"])
+    np.testing.assert_array_equal(sum(o_[6] for o_ in out), om["live"])
     assert om["collisions"].sum() > 0 and om["wall_count"].sum() > 0
     L = phys.ncells
     moved = 0
     for s in range(len(phys.species)):
         want = by_id(o.particles(s))
-        got = {k: np.concatenate([out[0][3][s][k], out[1][3][s][k]]) for k in want}
+        got = {k: np.concatenate([o_[3][s][k] for o_ in out]) for k in want}
         got = by_id(got)
         np.testing.assert_array_equal(got["id"], want["id"])
         np.testing.assert_array_equal(got["state"], want["state"])
@@ -202,6 +204,7 @@ def test_two_gloo_ranks_reproduce_the_undivided_oracle_run():
         # some particles did change rank
         ld = loads[s]
         start = dict(zip(ld.id.tolist(), ld.cell.tolist()))
-        moved += sum((start[i] < cuts[1]) != (c < cuts[1])
+        owner = lambda c: int(np.searchsorted(cuts, c, side="right")) - 1  # noqa: E731
+        moved += sum(owner(start[i]) != owner(c)
                      for i, c in zip(want["id"].tolist(), want["cell"].tolist()) if i in start)
     assert moved > 0
