@@ -995,6 +995,14 @@ int orc_set_step(orc_sim* s, int64_t step, uint32_t next_id)
     return 0;
 }
 
+int64_t orc_last_parents(const orc_sim* s, uint32_t* parents, int64_t cap)
+{
+    if (!s || cap < 0) return -1;
+    /* the births of the last step, sorted by parent id when their children were numbered */
+    for (int64_t r = 0; parents && r < s->nbirths && r < cap; ++r) parents[r] = s->births[r].parent;
+    return s->nbirths;
+}
+
 int64_t orc_count(const orc_sim* s, int32_t sp)
 {
     if (!s || sp < 0 || sp >= s->p.nspecies) return -1;

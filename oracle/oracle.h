@@ -106,6 +106,13 @@ int orc_set_field(orc_sim* s, const double* E);
  * particles to at least next_id.  Counters of walls and collisions are not touched. */
 int orc_set_step(orc_sim* s, int64_t step, uint32_t next_id);
 
+/* The parent ids of the last step's ionizations in ascending order (the order in which
+ * their children were numbered: the r-th parent's children have the r-th ids after the
+ * step's first new id).  Writes at most cap of them (parents may be NULL) and returns
+ * how many there were, or -1.  A run split into subdomains renumbers its children by
+ * the rank of their parent among every subdomain's parents. */
+int64_t orc_last_parents(const orc_sim* s, uint32_t* parents, int64_t cap);
+
 int64_t orc_count(const orc_sim* s, int32_t sp);
 /* Copy out species sp sorted by ascending id (capacity = orc_count); yp (cell units)
  * is 0 for a species without sn2d. */

@@ -61,6 +61,8 @@ def lib():
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
         L.orc_set_field.argtypes = [C.c_void_p, P]
         L.orc_set_step.argtypes = [C.c_void_p, C.c_int64, C.c_uint32]
+        L.orc_last_parents.restype = C.c_int64
+        L.orc_last_parents.argtypes = [C.c_void_p, P, C.c_int64]
         L.orc_count.restype = C.c_int64
         L.orc_count.argtypes = [C.c_void_p, C.c_int32]
         L.orc_get.argtypes = [C.c_void_p, C.c_int32, P, P, P, P, P, P, P, P]
@@ -181,6 +183,15 @@ class Oracle:
         rc = lib().orc_set_step(self._h, step, next_id)
         if rc:
             raise RuntimeError("orc_set_step failed: %d" % rc)
+
+    def last_parents(self) -> np.ndarray:
+        """Parent ids of the last step's ionizations, ascending (the order in which their
+        children were numbered)."""
+        n = lib().orc_last_parents(self._h, None, 0)
+        out = np.zeros(max(n, 0), np.uint32)
+        if n > 0:
+            lib().orc_last_parents(self._h, _ptr(out), n)
+        return out
 
     def particles(self, species: int) -> dict:
         n = lib().orc_count(self._h, species)

@@ -18,7 +18,13 @@ between GPUs; gloo on CPU in the tests):
    (centred inside, Gauss's law over the half cell at a wall) is the exact value
    rounded once;
 3. the particles that crossed an edge (cell, offset, velocities, id, collision
-   clock), point to point to the neighbour.
+   clock), point to point to the neighbour;
+4. the ids of the step's ionization products: the children of a step's ionizations are
+   numbered by the rank of their parent's id among all the step's ionizing parents of
+   the instance, so the ranks all-gather their parents' ids and each renumbers its own
+   children (a child's state comes from its parent's draws and its first collision-clock
+   test is drawn with its id only on the next step, so the renumbering between steps
+   leaves the undivided run's arithmetic as it is).
 
 The sums are exact (integers and rationals), so the field and the particles do not
 depend on the number of ranks.  The particle step itself is the library's mover; the
@@ -27,7 +33,7 @@ tests drive this protocol with a CPU stepper per rank.
 from __future__ import annotations
 
 from fractions import Fraction
-from typing import Dict, List, Optional, Sequence
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -230,3 +236,34 @@ class Subdomain:
             for c, k in enumerate(self._INTS):
                 out[k] = np.concatenate([out[k], ri[:, c].numpy().astype(out[k].dtype)])
         return out
+
+    # -- 4. the ids of this step's ionization products -------------------------------
+    def renumber_births(self, parts: List[Dict[str, np.ndarray]], parents: np.ndarray,
+                        base: int, per: int) -> Tuple[List[Dict[str, np.ndarray]], int]:
+        """parts: this rank's species after the step (every array kept as it is but the
+        ids); parents: the ids of this rank's ionizing parents of the step, ascending,
+        whose r-th one's children carry the ids base + per r + c (c = 0 the electron,
+        1 the ion; per = 1 with a neutral particle target, whose ion is a converted
+        target); base: the instance's first new id of the step, the same on every rank.
+        Returns the species with every child renumbered by its parent's rank among all
+        ranks' parents, and the instance's next free id."""
+        parents = np.asarray(parents, dtype=np.int64)
+        allp = np.sort(np.concatenate([np.asarray(p, dtype=np.int64)
+                                       for p in self._gather(parents)]))
+        if len(allp) and np.any(allp[1:] == allp[:-1]):
+            raise ValueError("an ionizing parent on two ranks")
+        rank_of = np.searchsorted(allp, parents)  # each local parent's rank among all
+        out = []
+        for p in parts:
+            q = dict(p)
+            ids = np.asarray(p["id"]).astype(np.int64)
+            new = ids >= base
+            if new.any():
+                k = ids[new] - base
+                r = k // per
+                if r.max() >= len(parents):
+                    raise ValueError("a new id without its parent")
+                ids[new] = base + per * rank_of[r] + k % per
+                q["id"] = ids.astype(np.asarray(p["id"]).dtype)
+            out.append(q)
+        return out, base + per * len(allp)

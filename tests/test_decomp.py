@@ -1,7 +1,9 @@
 """The domain decomposition of one instance by cells (the paper's Section 2), on CPU:
 its host logic alone, then two and three gloo ranks (with three, the middle one
 exchanges with both neighbours), each stepping its part of an instance with the
-oracle's particle step, the field solved jointly, against the oracle's undivided run.
+oracle's particle step, the field solved jointly, against the oracle's undivided run;
+with elastic + charge exchange, and with electron-impact ionization as well (the
+children renumbered by their parents' ranks over all subdomains).
 
 Velocities cross the oracle's interface in physical units; with dt/dx a power of two
 (here 1/8) that conversion is exact, so a particle that changes rank keeps its state
@@ -22,8 +24,11 @@ from tests.gpu_common import by_id
 STEPS = 40
 
 
-def _physics():
-    return W.bounded_small(ncells=64, ppc=40, seed=21, nu=0.2, dt=0.0625)
+def _physics(ionize=False):
+    phys = W.bounded_small(ncells=64, ppc=40, seed=21, nu=0.2, dt=0.0625)
+    if ionize:  # electron-impact ionization (threshold 13.6 eV / T_e 20 eV) into the ions
+        phys.processes.append(W.Process(W.PROC_IONIZE, 0, 0.2, 13.6 / 20.0, 1))
+    return phys
 
 
 def test_partition_covers_the_cells_and_balances():
@@ -72,6 +77,33 @@ def test_whole_instance_field_is_the_dirichlet_solution():
     np.testing.assert_array_equal(E, E_o)
 
 
+def test_births_are_renumbered_by_the_parents_rank_over_all_subdomains(monkeypatch):
+    # two subdomains' parents of one step: rank 0 had 3 and 11, rank 1 had 7; children
+    # of the r-th parent overall are base + 2r (electron) and base + 2r + 1 (ion)
+    base = 100
+    sub = Subdomain(16, [0, 8, 16], 0, 0.5)
+    monkeypatch.setattr(sub, "_gather", lambda obj: [np.array([3, 11]), np.array([7])])
+    e = dict(id=np.array([3, 11, 100, 102], np.uint32), cell=np.arange(4))
+    i = dict(id=np.array([5, 101, 103], np.uint32), cell=np.arange(3))
+    (e2, i2), nxt = sub.renumber_births([e, i], np.array([3, 11]), base, 2)
+    np.testing.assert_array_equal(e2["id"], [3, 11, 100, 104])  # parent 11 is 3rd overall
+    np.testing.assert_array_equal(i2["id"], [5, 101, 105])
+    np.testing.assert_array_equal(e2["cell"], e["cell"])
+    assert e2["id"].dtype == np.uint32 and nxt == base + 2 * 3
+    # with a neutral particle target one id a parent (the ion is a converted target)
+    (e3,), nxt = sub.renumber_births([dict(id=np.array([100, 101], np.uint32))],
+                                     np.array([3, 11]), base, 1)
+    np.testing.assert_array_equal(e3["id"], [100, 102])
+    assert nxt == base + 3
+    # a parent on two ranks, or a child without a parent, is refused
+    monkeypatch.setattr(sub, "_gather", lambda obj: [np.array([3, 11]), np.array([11])])
+    with pytest.raises(ValueError):
+        sub.renumber_births([e, i], np.array([3, 11]), base, 2)
+    monkeypatch.setattr(sub, "_gather", lambda obj: [np.array([3])])
+    with pytest.raises(ValueError):
+        sub.renumber_births([e, i], np.array([3]), base, 2)
+
+
 def test_oracle_follows_a_supplied_field():
     # the oracle handed its own field every step takes the same steps bit for bit
     phys = _physics()
@@ -112,13 +144,24 @@ def _joint_field(sub, parts, qw):
     return E, dep
 
 
-def _rank(rank, world, port, q):
+def _rank(rank, world, port, q, ionize):
+    try:
+        _rank_body(rank, world, port, q, ionize)
+    except BaseException as e:  # reported, so that the test fails at once
+        q.put((rank, "error", repr(e)))
+        raise
+
+
+def _rank_body(rank, world, port, q, ionize):
+    import datetime
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # a rank that fails leaves the others in a collective: they give up after a minute
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=60))
     try:
-        phys = _physics()
+        phys = _physics(ionize)
         N = phys.ncells
         loads = W.initial_load(phys, seed=21)
         cuts = partition(np.bincount(np.concatenate([ld.cell for ld in loads]), minlength=N),
@@ -129,6 +172,9 @@ def _rank(rank, world, port, q):
         for s, ld in enumerate(loads):
             m = (ld.cell >= sub.lo) & (ld.cell < sub.hi)
             orc.load(s, ld.take(m))
+        # the instance's next free id (every rank's created ids count from it)
+        base = int(max(ld.id.max() for ld in loads)) + 1
+        orc.set_step(0, base)
         first = None
         for n in range(STEPS):
             parts = [orc.particles(s) for s in range(len(loads))]
@@ -137,11 +183,15 @@ def _rank(rank, world, port, q):
                 first = (E[sub.lo:sub.hi + 1].copy(), dep)
             orc.set_field(E)
             orc.step(1)
-            # the particles that crossed an edge change rank; the rest are loaded back
+            # children numbered over all ranks' parents, then the particles that crossed
+            # an edge change rank; the rest are loaded back
+            parts, base = sub.renumber_births([orc.particles(s) for s in range(len(loads))],
+                                              orc.last_parents(), base, 2)
             for s in range(len(loads)):
-                p = sub.migrate(orc.particles(s))
+                p = sub.migrate(parts[s])
                 orc.load(s, W.Load(p["cell"], p["off"], p["vx"], p["vy"], p["vz"],
                                    p["id"].astype(np.uint32), p["state"].astype(np.uint8)))
+            orc.set_step(n + 1, base)
         m = orc.moments()
         q.put((rank, cuts, first, [orc.particles(s) for s in range(len(loads))],
                m["wall_count"], m["collisions"], m["live"]))
@@ -150,19 +200,29 @@ def _rank(rank, world, port, q):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("ionize", [False, True])
 @pytest.mark.parametrize("world", [2, 3])
-def test_gloo_ranks_reproduce_the_undivided_oracle_run(world):
-    phys = _physics()
+def test_gloo_ranks_reproduce_the_undivided_oracle_run(world, ionize):
+    phys = _physics(ionize)
     loads = W.initial_load(phys, seed=21)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, ionize), daemon=True)
+             for r in range(world)]
     for p in procs:
         p.start()
-    out = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    try:
+        got = [q.get(timeout=300) for _ in procs]
+        errors = [g for g in got if g[1] == "error"]
+        assert not errors, errors
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    out = sorted(got, key=lambda t: t[0])
     for p in procs:
-        p.join(timeout=60)
         assert p.exitcode == 0
     cuts = out[0][1]
     assert len(cuts) == world + 1 and all(0 < c < phys.ncells for c in cuts[1:-1])
@@ -187,6 +247,8 @@ def test_gloo_ranks_reproduce_the_undivided_oracle_run(world):
     np.testing.assert_array_equal(sum(o_[5] for o_ in out), om["collisions"])
     np.testing.assert_array_equal(sum(o_[6] for o_ in out), om["live"])
     assert om["collisions"].sum() > 0 and om["wall_count"].sum() > 0
+    if ionize:
+        assert om["collisions"][2] > 100  # children numbered over all subdomains
     L = phys.ncells
     moved = 0
     for s in range(len(phys.species)):
