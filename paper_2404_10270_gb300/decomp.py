@@ -79,9 +79,14 @@ def fixed_deposit(cell: np.ndarray, off: np.ndarray, lo: int, hi: int,
 class Subdomain:
     """Rank `rank`'s part of an N-cell instance cut at `cuts` (from partition), with
     the exchanges of one step.  `world` 1 (no torch.distributed needed) is the whole
-    instance, solved by the same arithmetic."""
+    instance, solved by the same arithmetic.  periodic: the instance's ends are joined
+    (node N is node 0), so the ranks form a ring: the last and the first share that
+    node, and a particle that wraps around goes to the rank at the other end (a periodic
+    instance has no Poisson solve with grounded walls, so no field is exchanged)."""
 
-    def __init__(self, N: int, cuts: Sequence[int], rank: int, dx: float, eps0: float = 1.0):
+    def __init__(self, N: int, cuts: Sequence[int], rank: int, dx: float, eps0: float = 1.0,
+                 periodic: bool = False):
+        self.periodic = bool(periodic)
         self.N = int(N)
         self.cuts = [int(c) for c in cuts]
         self.world = len(self.cuts) - 1
@@ -93,10 +98,18 @@ class Subdomain:
             raise ValueError("bad cuts or rank")
 
     # -- 1. the shared nodes' deposit -----------------------------------------------
+    def _ring(self):
+        """The distinct neighbours of a periodic rank: (left, right), left == right for two
+        ranks, none for one."""
+        R, r = self.world, self.rank
+        return [] if R == 1 else sorted({(r - 1) % R, (r + 1) % R})
+
     def exchange_shared(self, dep: np.ndarray) -> np.ndarray:
         """dep: int64 [species, hi - lo + 1], this rank's deposit on its nodes.  Returns
         it with each shared node holding the sum of both neighbours' deposits."""
         dep = np.array(dep, dtype=np.int64, copy=True)
+        if self.periodic:
+            return self._exchange_ring(dep)
         if self.world == 1:
             return dep
         import torch
@@ -113,6 +126,30 @@ class Subdomain:
             op.wait()
         for col, recv in inbox.items():
             dep[:, col] += recv.numpy()
+        return dep
+
+    def _exchange_ring(self, dep: np.ndarray) -> np.ndarray:
+        # the first column (node lo) is shared with the left neighbour's last column, the
+        # last (node hi) with the right neighbour's first; the tag says which edge a
+        # column is, so two ranks, each the other's left and right neighbour, match up
+        R, r = self.world, self.rank
+        if R == 1:  # node N is node 0 of the same rank
+            tot = dep[:, 0] + dep[:, -1]
+            dep[:, 0] = tot
+            dep[:, -1] = tot
+            return dep
+        import torch
+        import torch.distributed as dist
+        left, right = (r - 1) % R, (r + 1) % R
+        send_l = torch.from_numpy(np.ascontiguousarray(dep[:, 0]))
+        send_r = torch.from_numpy(np.ascontiguousarray(dep[:, -1]))
+        recv_l, recv_r = torch.zeros_like(send_l), torch.zeros_like(send_r)
+        ops = [dist.isend(send_l, left, tag=0), dist.isend(send_r, right, tag=1),
+               dist.irecv(recv_l, left, tag=1), dist.irecv(recv_r, right, tag=0)]
+        for op in ops:
+            op.wait()
+        dep[:, 0] += recv_l.numpy()
+        dep[:, -1] += recv_r.numpy()
         return dep
 
     # -- 2. the field ---------------------------------------------------------------
@@ -136,6 +173,8 @@ class Subdomain:
 
     def field(self, rho: List[Fraction]) -> np.ndarray:
         """E on the nodes lo..hi (Dirichlet walls), the exact solution rounded once."""
+        if self.periodic:
+            raise ValueError("a periodic instance has no grounded-wall Poisson solve")
         N, lo, hi = self.N, self.lo, self.hi
         r_at = lambda k: rho[k - lo]  # noqa: E731
         own_lo = lo + 1 if self.rank > 0 else 1   # interior nodes this rank sums
@@ -187,14 +226,26 @@ class Subdomain:
         vy, vz, id, state).  Those now outside [lo, hi) go to the neighbour (at most one
         subdomain away); returns the kept ones followed by the ones received."""
         cell = np.asarray(parts["cell"])
-        left, right = cell < self.lo, cell >= self.hi
-        if (self.rank == 0 and left.any()) or (self.rank == self.world - 1 and right.any()):
-            raise ValueError("particle outside the instance")
-        if left.any() and self.rank > 0 and cell[left].min() < self.cuts[self.rank - 1]:
-            raise ValueError("particle crossed more than one subdomain")
-        if right.any() and self.rank < self.world - 1 and cell[right].max() >= self.cuts[self.rank + 2]:
-            raise ValueError("particle crossed more than one subdomain")
-        keep = ~(left | right)
+        if self.periodic:
+            # (the particle step wraps cells into [0, N)): each goes to its owner, which
+            # must be this rank or a neighbour on the ring
+            owner = np.searchsorted(self.cuts, cell, side="right") - 1
+            away = owner != self.rank
+            if away.any() and not np.isin(owner[away], self._ring()).all():
+                raise ValueError("particle crossed more than one subdomain")
+            keep = ~away
+            sends = [(nb, owner == nb) for nb in self._ring()]
+        else:
+            left, right = cell < self.lo, cell >= self.hi
+            if (self.rank == 0 and left.any()) or (self.rank == self.world - 1 and right.any()):
+                raise ValueError("particle outside the instance")
+            if left.any() and self.rank > 0 and cell[left].min() < self.cuts[self.rank - 1]:
+                raise ValueError("particle crossed more than one subdomain")
+            if right.any() and self.rank < self.world - 1 and cell[right].max() >= self.cuts[self.rank + 2]:
+                raise ValueError("particle crossed more than one subdomain")
+            keep = ~(left | right)
+            sends = [(nb, m) for nb, m in ((self.rank - 1, left), (self.rank + 1, right))
+                     if 0 <= nb < self.world]
         out = {k: np.asarray(parts[k])[keep] for k in self._FLOATS + self._INTS}
         if self.world == 1:
             return out
@@ -207,8 +258,7 @@ class Subdomain:
             return torch.from_numpy(np.ascontiguousarray(f.reshape(-1, 4))), \
                 torch.from_numpy(np.ascontiguousarray(i.reshape(-1, 3)))
 
-        nbs = [(nb, m) for nb, m in ((self.rank - 1, left), (self.rank + 1, right))
-               if 0 <= nb < self.world]
+        nbs = sends
         # counts first, then the particles
         ops, counts = [], {}
         for nb, m in nbs:

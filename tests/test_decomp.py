@@ -3,7 +3,8 @@ its host logic alone, then two and three gloo ranks (with three, the middle one
 exchanges with both neighbours), each stepping its part of an instance with the
 oracle's particle step, the field solved jointly, against the oracle's undivided run;
 with elastic + charge exchange, and with electron-impact ionization as well (the
-children renumbered by their parents' ranks over all subdomains).
+children renumbered by their parents' ranks over all subdomains); and a periodic
+instance (no field solve), whose ranks form a ring.
 
 Velocities cross the oracle's interface in physical units; with dt/dx a power of two
 (here 1/8) that conversion is exact, so a particle that changes rank keeps its state
@@ -24,10 +25,13 @@ from tests.gpu_common import by_id
 STEPS = 40
 
 
-def _physics(ionize=False):
+def _physics(ionize=False, periodic=False):
     phys = W.bounded_small(ncells=64, ppc=40, seed=21, nu=0.2, dt=0.0625)
     if ionize:  # electron-impact ionization (threshold 13.6 eV / T_e 20 eV) into the ions
         phys.processes.append(W.Process(W.PROC_IONIZE, 0, 0.2, 13.6 / 20.0, 1))
+    if periodic:  # the ends joined; no grounded-wall field solve
+        phys.bc = W.BC_PERIODIC
+        phys.field = W.FIELD_NONE
     return phys
 
 
@@ -58,6 +62,19 @@ def test_split_deposit_adds_up_to_the_whole_one():
         total[a:b + 1] += fixed_deposit(cell[m], off[m], a, b)
     np.testing.assert_array_equal(total, whole)
     assert whole.sum() == n * (1 << 48)  # every particle adds one unit
+
+
+def test_one_periodic_rank_joins_node_n_to_node_0():
+    rng = np.random.default_rng(3)
+    N = 20
+    cell = rng.integers(0, N, 500)
+    off = rng.random(500)
+    dep = fixed_deposit(cell, off, 0, N)[None, :]
+    got = Subdomain(N, [0, N], 0, 0.5, periodic=True).exchange_shared(dep)
+    assert got[0, 0] == got[0, N] == dep[0, 0] + dep[0, N]
+    np.testing.assert_array_equal(got[0, 1:N], dep[0, 1:N])
+    with pytest.raises(ValueError):
+        Subdomain(N, [0, N], 0, 0.5, periodic=True).field([Fraction(0)] * (N + 1))
 
 
 def test_whole_instance_field_is_the_dirichlet_solution():
@@ -144,15 +161,15 @@ def _joint_field(sub, parts, qw):
     return E, dep
 
 
-def _rank(rank, world, port, q, ionize):
+def _rank(rank, world, port, q, ionize, periodic):
     try:
-        _rank_body(rank, world, port, q, ionize)
+        _rank_body(rank, world, port, q, ionize, periodic)
     except BaseException as e:  # reported, so that the test fails at once
         q.put((rank, "error", repr(e)))
         raise
 
 
-def _rank_body(rank, world, port, q, ionize):
+def _rank_body(rank, world, port, q, ionize, periodic):
     import datetime
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -161,12 +178,12 @@ def _rank_body(rank, world, port, q, ionize):
     dist.init_process_group("gloo", rank=rank, world_size=world,
                             timeout=datetime.timedelta(seconds=60))
     try:
-        phys = _physics(ionize)
+        phys = _physics(ionize, periodic)
         N = phys.ncells
         loads = W.initial_load(phys, seed=21)
         cuts = partition(np.bincount(np.concatenate([ld.cell for ld in loads]), minlength=N),
                          world)
-        sub = Subdomain(N, cuts, rank, phys.dx, phys.eps0)
+        sub = Subdomain(N, cuts, rank, phys.dx, phys.eps0, periodic=periodic)
         qw = [s.charge * s.weight for s in phys.species]
         orc = Oracle(phys)  # the whole grid; only this rank's particles in it
         for s, ld in enumerate(loads):
@@ -178,10 +195,16 @@ def _rank_body(rank, world, port, q, ionize):
         first = None
         for n in range(STEPS):
             parts = [orc.particles(s) for s in range(len(loads))]
-            E, dep = _joint_field(sub, parts, qw)
+            if periodic:  # the shared nodes' deposit only: no field solve
+                E = None
+                dep = sub.exchange_shared(np.stack(
+                    [fixed_deposit(p["cell"], p["off"], sub.lo, sub.hi) for p in parts]))
+            else:
+                E, dep = _joint_field(sub, parts, qw)
             if n == 0:
-                first = (E[sub.lo:sub.hi + 1].copy(), dep)
-            orc.set_field(E)
+                first = (None if E is None else E[sub.lo:sub.hi + 1].copy(), dep)
+            if E is not None:
+                orc.set_field(E)
             orc.step(1)
             # children numbered over all ranks' parents, then the particles that crossed
             # an edge change rank; the rest are loaded back
@@ -200,15 +223,15 @@ def _rank_body(rank, world, port, q, ionize):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ionize", [False, True])
+@pytest.mark.parametrize("ionize,periodic", [(False, False), (True, False), (True, True)])
 @pytest.mark.parametrize("world", [2, 3])
-def test_gloo_ranks_reproduce_the_undivided_oracle_run(world, ionize):
-    phys = _physics(ionize)
+def test_gloo_ranks_reproduce_the_undivided_oracle_run(world, ionize, periodic):
+    phys = _physics(ionize, periodic)
     loads = W.initial_load(phys, seed=21)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, q, ionize), daemon=True)
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, ionize, periodic), daemon=True)
              for r in range(world)]
     for p in procs:
         p.start()
@@ -228,12 +251,18 @@ def test_gloo_ranks_reproduce_the_undivided_oracle_run(world, ionize):
     assert len(cuts) == world + 1 and all(0 < c < phys.ncells for c in cuts[1:-1])
 
     # the joint deposit and field of the first step equal the undivided ones bit for bit
-    whole = Subdomain(phys.ncells, [0, phys.ncells], 0, phys.dx, phys.eps0)
+    whole = Subdomain(phys.ncells, [0, phys.ncells], 0, phys.dx, phys.eps0, periodic=periodic)
     parts = [dict(cell=ld.cell, off=ld.off) for ld in loads]
-    E1, dep1 = _joint_field(whole, parts, [s.charge * s.weight for s in phys.species])
+    if periodic:
+        E1 = None
+        dep1 = whole.exchange_shared(np.stack(
+            [fixed_deposit(p["cell"], p["off"], 0, phys.ncells) for p in parts]))
+    else:
+        E1, dep1 = _joint_field(whole, parts, [s.charge * s.weight for s in phys.species])
     for rank, c, (E_r, dep_r), *_ in out:
         lo, hi = c[rank], c[rank + 1]
-        np.testing.assert_array_equal(E_r, E1[lo:hi + 1])
+        if E1 is not None:
+            np.testing.assert_array_equal(E_r, E1[lo:hi + 1])
         np.testing.assert_array_equal(dep_r, dep1[:, lo:hi + 1])
 
     # against the oracle's own undivided run (its field in binary128 from the exact
@@ -246,17 +275,20 @@ def test_gloo_ranks_reproduce_the_undivided_oracle_run(world, ionize):
     np.testing.assert_array_equal(sum(o_[4] for o_ in out), om["wall_count"])
     np.testing.assert_array_equal(sum(o_[5] for o_ in out), om["collisions"])
     np.testing.assert_array_equal(sum(o_[6] for o_ in out), om["live"])
-    assert om["collisions"].sum() > 0 and om["wall_count"].sum() > 0
+    assert om["collisions"].sum() > 0 and (periodic or om["wall_count"].sum() > 0)
     if ionize:
         assert om["collisions"][2] > 100  # children numbered over all subdomains
     L = phys.ncells
-    moved = 0
+    moved = wrapped = 0
     for s in range(len(phys.species)):
         want = by_id(o.particles(s))
         got = {k: np.concatenate([o_[3][s][k] for o_ in out]) for k in want}
         got = by_id(got)
         np.testing.assert_array_equal(got["id"], want["id"])
         np.testing.assert_array_equal(got["state"], want["state"])
+        if periodic:  # no field: every particle's arithmetic is the undivided run's
+            for k in ("cell", "off", "vx", "vy", "vz"):
+                np.testing.assert_array_equal(got[k], want[k])
         x_got = got["cell"] + got["off"]
         x_want = want["cell"] + want["off"]
         assert np.abs(x_got - x_want).max() / L < 1e-12
@@ -269,4 +301,8 @@ def test_gloo_ranks_reproduce_the_undivided_oracle_run(world, ionize):
         owner = lambda c: int(np.searchsorted(cuts, c, side="right")) - 1  # noqa: E731
         moved += sum(owner(start[i]) != owner(c)
                      for i, c in zip(want["id"].tolist(), want["cell"].tolist()) if i in start)
+        # (periodic: some went around the ring's join, between the last rank and the first)
+        wrapped += sum(abs(c - start[i]) > L // 2
+                       for i, c in zip(want["id"].tolist(), want["cell"].tolist()) if i in start)
     assert moved > 0
+    assert (wrapped > 0) == periodic
