@@ -176,6 +176,7 @@ struct orc_sim {
     /* births of the current step */
     orc_birth* births;
     int64_t nbirths, capbirths;
+    int in_step;  /* between orc_step_loop and orc_step_finish */
 };
 
 static void draw(const orc_sim* s, uint32_t id, int64_t step, uint32_t purpose, uint32_t w[4])
@@ -828,7 +829,11 @@ static int convert_targets(orc_sim* s)
     return 0;
 }
 
-static int one_step(orc_sim* s)
+/* A time step in two halves: the particle loop (gather, push, move, walls, collisions;
+ * the ionizations recorded as births), then creation, the target conversions, the
+ * deposit and the field.  One step is the two in order; a run split into subdomains
+ * hands births between them in the middle (orc_births_take / orc_births_add). */
+static int step_loop(orc_sim* s)
 {
     const int N = s->N, S = s->p.nspecies;
     int rc = ensure_fields(s);
@@ -911,6 +916,13 @@ static int one_step(orc_sim* s)
             }
         }
     }
+    return 0;
+}
+
+static int step_finish(orc_sim* s)
+{
+    const int S = s->p.nspecies;
+    int rc;
     /* creation: children numbered by the rank of the parent id among this step's
      * ionizing parents; electron 2r, ion 2r+1 after the largest id so far (with a
      * particle target only the electron is new: id r; the ion is a converted target) */
@@ -963,6 +975,12 @@ static int one_step(orc_sim* s)
     return 0;
 }
 
+static int one_step(orc_sim* s)
+{
+    int rc = step_loop(s);
+    return rc ? rc : step_finish(s);
+}
+
 /* The field of the next step supplied by the caller (E on the N+1 nodes) in place of
  * the one the field phase formed: the gather then uses A_s = c_s E as usual.  A run split
  * into subdomains solves the field jointly and hands each part the result. */
@@ -979,7 +997,7 @@ int orc_set_field(orc_sim* s, const double* E)
 
 int orc_step(orc_sim* s, int64_t nsteps)
 {
-    if (!s || nsteps < 0) return -1;
+    if (!s || nsteps < 0 || s->in_step) return -1;
     for (int64_t n = 0; n < nsteps; ++n) {
         int rc = one_step(s);
         if (rc) return rc;
@@ -992,6 +1010,58 @@ int orc_set_step(orc_sim* s, int64_t step, uint32_t next_id)
     if (!s || step < 0) return -1;
     s->step = step;
     if (next_id > s->next_id) s->next_id = next_id;
+    return 0;
+}
+
+int orc_step_loop(orc_sim* s)
+{
+    if (!s || s->in_step) return -1;
+    int rc = step_loop(s);
+    if (!rc) s->in_step = 1;
+    return rc;
+}
+
+int orc_step_finish(orc_sim* s)
+{
+    if (!s || !s->in_step) return -1;
+    s->in_step = 0;
+    return step_finish(s);
+}
+
+int64_t orc_births_take(orc_sim* s, int32_t lo, int32_t hi, orc_birth_rec* out, int64_t cap)
+{
+    if (!s || !s->in_step || lo < 0 || hi > s->N || lo > hi || cap < 0) return -1;
+    int64_t m = 0, k = 0;
+    for (int64_t r = 0; r < s->nbirths; ++r) {
+        const orc_birth* b = &s->births[r];
+        if (b->cell >= lo && b->cell < hi) {
+            s->births[m++] = *b;
+            continue;
+        }
+        if (k >= cap) return -2;  /* (ask with cap large enough: at most nbirths) */
+        orc_birth_rec* o = &out[k++];
+        o->parent = b->parent;
+        o->esp = b->esp; o->isp = b->isp; o->psp = b->psp; o->cell = b->cell;
+        o->off = b->off; o->yp = b->yp;
+        for (int c = 0; c < 3; ++c) { o->e[c] = b->e[c]; o->i[c] = b->i[c]; }
+    }
+    s->nbirths = m;
+    return k;
+}
+
+int orc_births_add(orc_sim* s, const orc_birth_rec* in, int64_t n)
+{
+    if (!s || !s->in_step || n < 0 || (n > 0 && !in)) return -1;
+    for (int64_t k = 0; k < n; ++k) {
+        if (in[k].cell < 0 || in[k].cell >= s->N) return -1;
+        orc_birth b;
+        b.parent = in[k].parent;
+        b.esp = in[k].esp; b.isp = in[k].isp; b.psp = in[k].psp; b.cell = in[k].cell;
+        b.off = in[k].off; b.yp = in[k].yp;
+        for (int c = 0; c < 3; ++c) { b.e[c] = in[k].e[c]; b.i[c] = in[k].i[c]; }
+        int rc = add_birth(s, &b);
+        if (rc) return rc;
+    }
     return 0;
 }
 

@@ -106,6 +106,28 @@ int orc_set_field(orc_sim* s, const double* E);
  * particles to at least next_id.  Counters of walls and collisions are not touched. */
 int orc_set_step(orc_sim* s, int64_t step, uint32_t next_id);
 
+/* One time step in two halves, for a run split into subdomains: orc_step_loop moves
+ * every particle (gather, push, move, walls, collisions) and records the step's
+ * ionizations; orc_step_finish creates their products (converting neutral particle
+ * targets), deposits and solves the field.  orc_step is the two in order.  In between,
+ * orc_births_take removes the ionizations recorded in cells outside [lo, hi) and
+ * copies them to out (at most cap; returns how many, -2 if cap is too small), and
+ * orc_births_add appends ionizations recorded by another subdomain's loop in this
+ * subdomain's cells: their products are made here, with the step's own, in the order
+ * of their parents' ids. */
+typedef struct {
+    uint32_t parent;          /* the ionizing particle's id */
+    int32_t esp, isp, psp;    /* species of the new electron, of the new ion (-1: a
+                                 converted target), of the process's product ion */
+    int32_t cell;             /* where the products appear */
+    double off, yp;
+    double e[3], i[3];        /* their velocities (cells per own step) */
+} orc_birth_rec;
+int orc_step_loop(orc_sim* s);
+int orc_step_finish(orc_sim* s);
+int64_t orc_births_take(orc_sim* s, int32_t lo, int32_t hi, orc_birth_rec* out, int64_t cap);
+int orc_births_add(orc_sim* s, const orc_birth_rec* in, int64_t n);
+
 /* The parent ids of the last step's ionizations in ascending order (the order in which
  * their children were numbered: the r-th parent's children have the r-th ids after the
  * step's first new id).  Writes at most cap of them (parents may be NULL) and returns

@@ -61,6 +61,11 @@ def lib():
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
         L.orc_set_field.argtypes = [C.c_void_p, P]
         L.orc_set_step.argtypes = [C.c_void_p, C.c_int64, C.c_uint32]
+        L.orc_step_loop.argtypes = [C.c_void_p]
+        L.orc_step_finish.argtypes = [C.c_void_p]
+        L.orc_births_take.restype = C.c_int64
+        L.orc_births_take.argtypes = [C.c_void_p, C.c_int32, C.c_int32, P, C.c_int64]
+        L.orc_births_add.argtypes = [C.c_void_p, P, C.c_int64]
         L.orc_last_parents.restype = C.c_int64
         L.orc_last_parents.argtypes = [C.c_void_p, P, C.c_int64]
         L.orc_count.restype = C.c_int64
@@ -77,6 +82,13 @@ def lib():
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# one recorded ionization (orc_birth_rec), C layout
+BIRTH = np.dtype([("parent", np.uint32), ("esp", np.int32), ("isp", np.int32),
+                  ("psp", np.int32), ("cell", np.int32), ("pad", np.int32),
+                  ("off", np.float64), ("yp", np.float64), ("e", np.float64, (3,)),
+                  ("i", np.float64, (3,))], align=True)
 
 
 def params_struct(phys) -> _Params:
@@ -183,6 +195,36 @@ class Oracle:
         rc = lib().orc_set_step(self._h, step, next_id)
         if rc:
             raise RuntimeError("orc_set_step failed: %d" % rc)
+
+    def step_loop(self) -> None:
+        """The first half of a step: every particle moved, the ionizations recorded."""
+        rc = lib().orc_step_loop(self._h)
+        if rc:
+            raise RuntimeError("orc_step_loop failed: %d" % rc)
+
+    def step_finish(self) -> None:
+        """The second half: products, target conversions, deposit, field."""
+        rc = lib().orc_step_finish(self._h)
+        if rc:
+            raise RuntimeError("orc_step_finish failed: %d" % rc)
+
+    def births_take(self, lo: int, hi: int) -> np.ndarray:
+        """Between the halves: remove and return the ionizations recorded in cells
+        outside [lo, hi) (a structured array of BIRTH records)."""
+        cap = 1 << 20
+        out = np.zeros(cap, BIRTH)
+        n = lib().orc_births_take(self._h, lo, hi, _ptr(out), cap)
+        if n < 0:
+            raise RuntimeError("orc_births_take failed: %d" % n)
+        return out[:n].copy()
+
+    def births_add(self, recs: np.ndarray) -> None:
+        """Between the halves: ionizations recorded by another subdomain in this one's
+        cells, whose products are made here."""
+        recs = np.ascontiguousarray(recs, dtype=BIRTH)
+        rc = lib().orc_births_add(self._h, _ptr(recs) if len(recs) else None, len(recs))
+        if rc:
+            raise RuntimeError("orc_births_add failed: %d" % rc)
 
     def last_parents(self) -> np.ndarray:
         """Parent ids of the last step's ionizations, ascending (the order in which their

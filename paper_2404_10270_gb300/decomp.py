@@ -19,7 +19,15 @@ between GPUs; gloo on CPU in the tests):
    rounded once;
 3. the particles that crossed an edge (cell, offset, velocities, id, collision
    clock), point to point to the neighbour;
-4. the ids of the step's ionization products: the children of a step's ionizations are
+4. with neutral particle targets (the paper's test case), two more: before the step each
+   rank receives a copy of the neighbours' targets in the cell next to each of its edges
+   (a one-cell halo), so that an electron that crosses an edge during the step meets the
+   start-of-step target count of the cell it collides in; and between the particle loop
+   and the creation of products, an ionization recorded in a neighbour's cell goes to
+   that neighbour, which converts its targets for it together with its own (a cell's
+   first r_j targets by id, the requests in the order of their parents' ids); the halo
+   copies are dropped after the step;
+5. the ids of the step's ionization products: the children of a step's ionizations are
    numbered by the rank of their parent's id among all the step's ionizing parents of
    the instance, so the ranks all-gather their parents' ids and each renumbers its own
    children (a child's state comes from its parent's draws and its first collision-clock
@@ -317,3 +325,85 @@ class Subdomain:
                 q["id"] = ids.astype(np.asarray(p["id"]).dtype)
             out.append(q)
         return out, base + per * len(allp)
+
+    # -- 4. neutral particle targets: the halo and the ionizations handed over --------
+    def _neighbours(self) -> List[int]:
+        if self.periodic:
+            return self._ring()
+        return [nb for nb in (self.rank - 1, self.rank + 1) if 0 <= nb < self.world]
+
+    def _owner(self, cell: np.ndarray) -> np.ndarray:
+        return np.searchsorted(self.cuts, np.asarray(cell), side="right") - 1
+
+    def _swap(self, outgoing: Dict[int, np.ndarray], dtype) -> np.ndarray:
+        """Send each neighbour its structured array (counts first, then the bytes) and
+        return what the neighbours sent, concatenated."""
+        if self.world == 1:
+            return np.zeros(0, dtype)
+        import torch
+        import torch.distributed as dist
+        nbs = self._neighbours()
+        ops, counts = [], {}
+        for nb in nbs:
+            counts[nb] = torch.zeros(1, dtype=torch.int64)
+            ops.append(dist.isend(torch.tensor([len(outgoing.get(nb, ()))], dtype=torch.int64), nb))
+            ops.append(dist.irecv(counts[nb], nb))
+        for op in ops:
+            op.wait()
+        ops, got = [], []
+        for nb in nbs:
+            a = outgoing.get(nb)
+            if a is not None and len(a):
+                ops.append(dist.isend(torch.from_numpy(np.ascontiguousarray(a).view(np.uint8)), nb))
+            n = int(counts[nb][0])
+            if n > 0:
+                buf = torch.zeros(n * np.dtype(dtype).itemsize, dtype=torch.uint8)
+                ops.append(dist.irecv(buf, nb))
+                got.append(buf)
+        for op in ops:
+            op.wait()
+        if not got:
+            return np.zeros(0, dtype)
+        return np.concatenate([b.numpy().view(dtype) for b in got])
+
+    _PARTICLE = np.dtype([("cell", np.int64), ("off", np.float64), ("vx", np.float64),
+                          ("vy", np.float64), ("vz", np.float64), ("id", np.int64),
+                          ("state", np.int64)])
+
+    def halo(self, targets: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:
+        """targets: this rank's target particles at the start of the step.  Returns
+        copies of the neighbours' targets in the cells next to this rank's edges (for the
+        step only: they are neither moved for good nor converted here)."""
+        cell = np.asarray(targets["cell"])
+        N, lo, hi = self.N, self.lo, self.hi
+        out = {}
+        for nb in self._neighbours():
+            # the neighbour's halo cells on this rank's side: this rank's edge cells
+            nlo, nhi = self.cuts[nb], self.cuts[nb + 1]
+            edge = []
+            if lo == nhi % N if self.periodic else lo == nhi:
+                edge.append(lo)
+            if hi % N == nlo if self.periodic else hi == nlo:
+                edge.append(hi - 1)
+            m = np.isin(cell, edge)
+            a = np.zeros(int(m.sum()), self._PARTICLE)
+            for k in self._PARTICLE.names:
+                a[k] = np.asarray(targets[k])[m]
+            out[nb] = a
+        got = self._swap(out, self._PARTICLE)
+        res = {k: got[k] for k in self._PARTICLE.names}
+        res["cell"] = res["cell"].astype(np.int32)
+        res["id"] = res["id"].astype(np.uint32)
+        res["state"] = res["state"].astype(np.uint8)
+        return res
+
+    def hand_over_births(self, recs: np.ndarray) -> np.ndarray:
+        """recs: the ionizations this rank's particle loop recorded in cells outside its
+        own (a structured array with a `cell` field).  Sends each to the rank that owns
+        its cell (a neighbour) and returns those recorded elsewhere in this rank's
+        cells."""
+        owner = self._owner(recs["cell"]) if len(recs) else np.zeros(0, np.int64)
+        nbs = self._neighbours()
+        if len(recs) and not np.isin(owner, nbs).all():
+            raise ValueError("an ionization recorded beyond the neighbouring subdomains")
+        return self._swap({nb: recs[owner == nb] for nb in nbs}, recs.dtype)

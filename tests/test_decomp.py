@@ -3,8 +3,10 @@ its host logic alone, then two and three gloo ranks (with three, the middle one
 exchanges with both neighbours), each stepping its part of an instance with the
 oracle's particle step, the field solved jointly, against the oracle's undivided run;
 with elastic + charge exchange, and with electron-impact ionization as well (the
-children renumbered by their parents' ranks over all subdomains); and a periodic
-instance (no field solve), whose ranks form a ring.
+children renumbered by their parents' ranks over all subdomains); a periodic instance
+(no field solve), whose ranks form a ring; and the paper's own test case (periodic,
+neutral particle targets that ionization converts) with the target halo and the
+hand-over of ionizations recorded in a neighbour's cell.
 
 Velocities cross the oracle's interface in physical units; with dt/dx a power of two
 (here 1/8) that conversion is exact, so a particle that changes rank keeps its state
@@ -306,3 +308,105 @@ def test_gloo_ranks_reproduce_the_undivided_oracle_run(world, ionize, periodic):
                        for i, c in zip(want["id"].tolist(), want["cell"].tolist()) if i in start)
     assert moved > 0
     assert (wrapped > 0) == periodic
+
+
+def _paper_physics():
+    # the paper's test case on 64 cells; dt/dx = 1/8 and a target subcycling factor of 4
+    # keep the conversions of velocities at the oracle's interface exact
+    return W.ionization_case(ncells=64, ppc=40, nu_el=0.05, nu_exc=0.05, nu_iz=0.1, seed=27,
+                             sort_interval=4, dt=0.0625)
+
+
+def _paper_rank(rank, world, port, q):
+    try:
+        _paper_rank_body(rank, world, port, q)
+    except BaseException as e:  # reported, so that the test fails at once
+        q.put((rank, "error", repr(e)))
+        raise
+
+
+def _paper_rank_body(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        phys = _paper_physics()
+        N, S, t = phys.ncells, len(phys.species), phys.target - 1
+        loads = W.initial_load(phys, seed=27)
+        cuts = partition(np.bincount(np.concatenate([ld.cell for ld in loads]), minlength=N),
+                         world)
+        sub = Subdomain(N, cuts, rank, phys.dx, phys.eps0, periodic=True)
+        orc = Oracle(phys)
+        for s, ld in enumerate(loads):
+            m = (ld.cell >= sub.lo) & (ld.cell < sub.hi)
+            orc.load(s, ld.take(m))
+        base = int(max(ld.id.max() for ld in loads)) + 1
+        orc.set_step(0, base)
+        handed = 0
+        keys = ("cell", "off", "vx", "vy", "vz", "id", "state")
+        for n in range(STEPS):
+            own = orc.particles(t)
+            halo = sub.halo(own)
+            both = {k: np.concatenate([own[k], halo[k]]) for k in keys}
+            orc.load(t, W.Load(*[both[k] for k in keys]))
+            orc.step_loop()
+            away = orc.births_take(sub.lo, sub.hi)
+            handed += len(away)
+            orc.births_add(sub.hand_over_births(away))
+            orc.step_finish()
+            parts = [orc.particles(s) for s in range(S)]
+            keep = ~np.isin(parts[t]["id"], halo["id"])  # the halo copies go
+            parts[t] = {k: v[keep] for k, v in parts[t].items()}
+            parts, base = sub.renumber_births(parts, orc.last_parents(), base, 1)
+            for s in range(S):
+                p = sub.migrate(parts[s])
+                orc.load(s, W.Load(*[np.asarray(p[k]).astype(
+                    {"cell": np.int32, "id": np.uint32, "state": np.uint8}.get(k, np.float64))
+                    for k in keys]))
+            orc.set_step(n + 1, base)
+        m = orc.moments()
+        q.put((rank, cuts, handed, [orc.particles(s) for s in range(S)], m["collisions"],
+               m["live"]))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_reproduce_the_papers_test_case(world):
+    phys = _paper_physics()
+    loads = W.initial_load(phys, seed=27)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_paper_rank, args=(r, world, port, q), daemon=True)
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    try:
+        got = [q.get(timeout=300) for _ in procs]
+        errors = [g for g in got if g[1] == "error"]
+        assert not errors, errors
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    out = sorted(got, key=lambda t: t[0])
+    o = Oracle(phys)
+    o.load_all(loads)
+    o.step(STEPS)
+    om = o.moments()
+    np.testing.assert_array_equal(sum(r[4] for r in out), om["collisions"])
+    np.testing.assert_array_equal(sum(r[5] for r in out), om["live"])
+    assert om["collisions"][2] > 50  # ionizations converted neutrals into ions
+    assert om["live"][2] < len(loads[2])
+    assert sum(r[2] for r in out) > 0  # some were recorded in a neighbour's cell
+    for s in range(len(phys.species)):  # no field: every particle as undivided, bit for bit
+        want = by_id(o.particles(s))
+        got_s = by_id({k: np.concatenate([r[3][s][k] for r in out]) for k in want})
+        for k in ("id", "state", "cell", "off", "vx", "vy", "vz"):
+            np.testing.assert_array_equal(got_s[k], want[k], err_msg="species %d %s" % (s, k))
